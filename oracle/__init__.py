@@ -1,0 +1,210 @@
+"""CPU oracle for the gScan hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library's product path never
+does: it shares no code with the CUDA kernels and the two never import each
+other.
+
+Every function follows a passage of Mei, "gScan: Accelerating Graham Scan on
+the GPU" (arXiv 1508.05931), cited in its docstring, and is pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py`` to brute force,
+closed forms and invariants.  Pinning status per function:
+
+* ``hull``            pinned (O(n^3) brute force, closed forms, invariants)
+* ``extremes``        pinned (lexsort library routine, brute force)
+* ``quad_filter``     pinned (exact rational point-in-polygon, statistics)
+* ``sort_survivors``  pinned (numpy lexsort; a library primitive)
+* ``second_round``    pinned (triangle witnesses, hull superset, Section
+                      2.2.3's worked P_temp trace)
+* ``chain``           pinned (brute force on sorted input)
+* the learned-proposal MLP (``oracle.mlp``) is pinned by finite differences
+  and a closed-form tiny network.
+
+The C part (``hull_oracle.c``) is compiled with plain gcc, no vector
+intrinsics, by ``build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hull_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_hull.so")
+_lib = None
+
+COORD_LIMIT = 1 << 29
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc into oracle/_build/liboracle_hull.so."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    lib.oracle_range_ok.argtypes = [P, I64]
+    lib.oracle_range_ok.restype = ctypes.c_int
+    lib.oracle_chain.argtypes = [P, I64, ctypes.c_int, P]
+    lib.oracle_chain.restype = I64
+    lib.oracle_hull.argtypes = [P, I64, P]
+    lib.oracle_hull.restype = I64
+    lib.oracle_extremes.argtypes = [P, I64, P]
+    lib.oracle_extremes.restype = ctypes.c_int
+    lib.oracle_quad.argtypes = [P, I64, P]
+    lib.oracle_quad.restype = ctypes.c_int
+    lib.oracle_quad_filter.argtypes = [P, I64, P]
+    lib.oracle_quad_filter.restype = I64
+    lib.oracle_second_round.argtypes = [P, I64, P, P, P, P, P]
+    lib.oracle_second_round.restype = ctypes.c_int
+    lib.oracle_sort_xyi.argtypes = [P, I64]
+    lib.oracle_sort_xyi.restype = None
+    _lib = lib
+    return lib
+
+
+def _pts(xy) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def range_ok(xy) -> bool:
+    a = _pts(xy)
+    return bool(_load().oracle_range_ok(_ptr(a), a.shape[0]))
+
+
+def hull(xy) -> np.ndarray:
+    """Convex hull by definition (Section 1), Andrew's monotone chain over all
+    points; CCW input indices from the lexicographic minimum, collinear
+    boundary points excluded, smallest index among duplicates.
+    Raises ValueError for coordinates beyond +-2^29."""
+    a = _pts(xy)
+    n = a.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    h = _load().oracle_hull(_ptr(a), n, _ptr(out))
+    if h == -1:
+        raise ValueError("coordinate out of range")
+    if h < 0:
+        raise MemoryError("oracle allocation failed")
+    return out[:h].copy()
+
+
+def extremes(xy) -> np.ndarray:
+    """Section 2.1 step 1: [P_minx, P_maxx, P_miny, P_maxy] indices with
+    lexicographic ties and the smallest index."""
+    a = _pts(xy)
+    ext = np.full(4, -1, dtype=np.int32)
+    _load().oracle_extremes(_ptr(a), a.shape[0], _ptr(ext))
+    return ext
+
+
+def quad(xy) -> np.ndarray:
+    """Distinct corners (k, 2) of the first-round polygon, CCW from P_minx."""
+    a = _pts(xy)
+    poly = np.zeros(8, dtype=np.int32)
+    k = _load().oracle_quad(_ptr(a), a.shape[0], _ptr(poly))
+    return poly[: 2 * k].reshape(k, 2).copy()
+
+
+def quad_filter(xy) -> np.ndarray:
+    """Section 3.1: ascending indices of points NOT strictly inside the quad."""
+    a = _pts(xy)
+    keep = np.empty(max(a.shape[0], 1), dtype=np.int32)
+    s = _load().oracle_quad_filter(_ptr(a), a.shape[0], _ptr(keep))
+    return keep[:s].copy()
+
+
+def sort_survivors(xy, idx) -> np.ndarray:
+    """Section 2.1 step 4, with the lexicographic key: the survivors' indices
+    ordered by (x, y, idx) -- a stable sort of index-ordered survivors."""
+    a = _pts(xy)
+    idx = np.asarray(idx, dtype=np.int64)
+    order = np.lexsort((idx, a[idx, 1], a[idx, 0]))
+    return idx[order].astype(np.int32)
+
+
+def second_round(xy, sorted_idx):
+    """Figure 2 (Section 2.2) run sequentially over both regions of a list of
+    input indices sorted by (x, y, idx).  Returns (lower_idx, upper_idx,
+    l_pos) where the index lists are input indices in list order and l_pos
+    is the list position of P_l (-1 if every point equals P_0)."""
+    a = _pts(xy)
+    sidx = np.asarray(sorted_idx, dtype=np.int64)
+    m = sidx.shape[0]
+    xyi = np.empty((m, 3), dtype=np.int32)
+    xyi[:, :2] = a[sidx]
+    xyi[:, 2] = sidx
+    lo = np.empty(max(m, 1), dtype=np.int32)
+    up = np.empty(max(m, 1), dtype=np.int32)
+    nlo = ctypes.c_int64()
+    nup = ctypes.c_int64()
+    lp = ctypes.c_int64()
+    _load().oracle_second_round(_ptr(xyi), m, _ptr(lo), ctypes.byref(nlo), _ptr(up),
+                                ctypes.byref(nup), ctypes.byref(lp))
+    lo_pos = lo[: nlo.value]
+    up_pos = up[: nup.value]
+    return (sidx[lo_pos].astype(np.int32), sidx[up_pos].astype(np.int32), int(lp.value))
+
+
+def chain(xy_seq, sign: int) -> np.ndarray:
+    """Stack-based monotone chain (Section 2.1 step 8, Section 5.2) over a
+    sequence of points given in lexicographic order; sign +1 = lower chain,
+    -1 = upper chain walked left to right.  Returns kept positions."""
+    a = _pts(xy_seq)
+    m = a.shape[0]
+    xyi = np.zeros((m, 3), dtype=np.int32)
+    xyi[:, :2] = a
+    out = np.empty(max(m, 1), dtype=np.int32)
+    h = _load().oracle_chain(_ptr(xyi), m, int(sign), _ptr(out))
+    return out[:h].copy()
+
+
+def gscan_stages(xy):
+    """The method's stages in the paper's order (Section 2.1 steps 1-8),
+    each computed by the functions above.  Returns a dict of intermediates
+    and the final CCW hull built from the second-round survivors."""
+    a = _pts(xy)
+    n = a.shape[0]
+    out = {"n": n}
+    if n == 0:
+        out.update(ext=np.full(4, -1, np.int32), keep=np.zeros(0, np.int32),
+                   sorted=np.zeros(0, np.int32), lower=np.zeros(0, np.int32),
+                   upper=np.zeros(0, np.int32), hull=np.zeros(0, np.int32))
+        return out
+    out["ext"] = extremes(a)
+    keep = quad_filter(a)
+    out["keep"] = keep
+    srt = sort_survivors(a, keep)
+    out["sorted"] = srt
+    lo, up, lpos = second_round(a, srt)
+    out["lower"], out["upper"] = lo, up
+    if lpos < 0:
+        out["hull"] = srt[:1].copy()
+        return out
+    p0, pl = int(srt[0]), int(srt[lpos])
+    lo_seq = np.concatenate([[p0], lo, [pl]]).astype(np.int64)
+    up_seq = np.concatenate([[p0], up, [pl]]).astype(np.int64)
+    lc = lo_seq[chain(a[lo_seq], +1)]
+    uc = up_seq[chain(a[up_seq], -1)]
+    out["hull"] = np.concatenate([lc, uc[1:-1][::-1]]).astype(np.int32)
+    return out
