@@ -1,0 +1,305 @@
+"""Benchmark: exact 2D convex hull throughput (Mpoints/s) of the gScan hot
+path on GB300, one JSON line on stdout.
+
+A step is one pass of the whole pipeline (extremes, quadrilateral filter +
+compaction, radix sort, region split + second-round filter, device
+finalisation) over the paper-scale workload: two hulls of 20,000,000 int32
+points each, (a) uniform in the square [-2^29, 2^29)^2 and (b) uniform in
+the disk of radius 2^29.  Each input (160 MB) is larger than L2, and the two
+alternate, so every step reads cold inputs from HBM.
+
+--impl reference times the CPU oracle (the project's plain monotone chain)
+on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hull Mpoints/s at 20M int32 pts (plain gScan pipeline, square + disk)"
+UNIT = "Mpoints/s"
+WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk int32 points"
+# The paper's best 20M-point times for the same two workloads (Table 3 square
+# 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
+PAPER_MPTS = 40.0 / 0.8645
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=20_000_000, help="points per hull")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    from paper_1508_05931_gb300 import workloads as W
+    return [W.paper_square(n, 1), W.paper_disk(n, 2)]
+
+
+def cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return model
+
+
+def oracle_timing(sets, budget_s=20.0, sample_pts=None):
+    """Times the oracle (single-threaded) hull on the sets; returns
+    (points processed, seconds, sample description)."""
+    import oracle
+    oracle.build()
+    done, secs, parts = 0, 0.0, []
+    for pts in sets:
+        p = pts if sample_pts is None else pts[:sample_pts]
+        t = time.perf_counter()
+        oracle.hull(p)
+        dt = time.perf_counter() - t
+        done += len(p)
+        secs += dt
+        parts.append(len(p))
+        if secs > budget_s:
+            break
+    return done, secs, "oracle.hull (qsort + monotone chain, 1 thread) on %s points" % "+".join(map(str, parts))
+
+
+class ClockSampler:
+    def __init__(self, enabled, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        if not enabled:
+            return
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx = float(c[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, c[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sets = workload(args.n)
+    sample = 1_000_000
+    times = []
+    import oracle
+    oracle.build()
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        for pts in sets:
+            oracle.hull(pts[:sample])
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            times.append(dt)
+    pts_step = sample * len(sets)
+    secs = sum(times)
+    value = pts_step * len(times) / secs / 1e6
+    desc = "first %d points of each 20M set per step (oracle.hull, 1 thread)" % sample
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_MPTS,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                             "cpu": cpu_info()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_1508_05931_gb300 import build as _b
+    _b.build_library()
+    from paper_1508_05931_gb300 import hull
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sets = workload(args.n)
+    dev_sets = [torch.as_tensor(p).cuda() for p in sets]
+    out = torch.empty(args.n, dtype=torch.int32, device="cuda")
+    ctx = hull.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for t in dev_sets:
+            ctx.compute_raw(t, out, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ctx.set_profiling(True)
+    sampler = ClockSampler(not args.no_clocks and rank == 0, local)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pts_step = sum(len(p) for p in sets)
+    value = world * pts_step * args.steps / (ms / 1e3) / 1e6
+
+    # e2e: the same steps through the host entry point (pinned host input,
+    # H2D copy, compute, D2H of the vertex indices inside the timed region).
+    host_sets = [torch.as_tensor(p).pin_memory() for p in sets]
+    host_out = torch.empty(args.n, dtype=torch.int32).pin_memory()
+    h_counts = []
+
+    def host_step():
+        h_counts.clear()
+        for hp in host_sets:
+            r = ctx.compute_host(hp, out=host_out, stream=stream)
+            h_counts.append(len(r))
+
+    for _ in range(2):
+        host_step()
+    barrier()
+    t0 = time.perf_counter()
+    k_e2e = max(3, args.steps // 2)
+    for _ in range(k_e2e):
+        host_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * pts_step * k_e2e / e2e_s / 1e6
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # Dominant kernel: the radix pass.  Algorithmic bytes per launch = the
+    # survivors' keys and indices read once and written once (24 B each).
+    calls = max(prof["calls"], 1)
+    sort_ms = sum(prof["ms"]["sort_pass%d" % i] for i in range(8))
+    passes = max(prof["sort_passes"], 1)
+    surv = prof["survivors"]
+    # total bytes of all active pass launches (every hull here needs the same pass count)
+    sort_bytes = 24.0 * surv * (passes / calls)
+    achieved = sort_bytes / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else 0.0
+    stage_ms = {k: v / calls for k, v in prof["ms"].items()}
+    roofline = {"bound": "hbm", "kernel": "k3_onesweep (radix pass)", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
+                "traffic": None,
+                "algorithmic_bytes_per_launch": 24.0 * surv / calls,
+                "stage_ms_per_hull": stage_ms,
+                "k1_gbs": (8.0 * prof["points"] / calls) / (stage_ms["extremes"] / 1e3) / 1e9
+                if stage_ms["extremes"] > 0 else None,
+                "k2_gbs": ((8.0 * prof["points"] + 12.0 * surv) / calls) / (stage_ms["filter"] / 1e3) / 1e9
+                if stage_ms["filter"] > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_MPTS, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_step": pts_step, "hulls_per_step": len(sets),
+                       "l2": "inputs larger than L2 (160 MB each, alternating)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "survivors_per_hull": surv / calls,
+                       "second_round_per_hull": prof["second_round"] / calls},
+            "gpu_launches": args.steps * len(sets) * 12,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
+                    "d2h_bytes_per_step": 4 * sum(h_counts)},
+            "roofline": roofline}
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0 and not args.no_cpu_baseline:
+        done, secs, desc = oracle_timing(sets)
+        line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc, "cpu": cpu_info(), "nproc": os.cpu_count()}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * gbhull -- exact 2D convex hull on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of the gScan method (Mei, "gScan:
+ * Accelerating Graham Scan on the GPU", arXiv 1508.05931): extreme points
+ * (Section 2.1 step 1), quadrilateral filter (step 2, Section 3.1), sort
+ * (step 4, Section 3.3), region split and second-round filter (steps 5-7,
+ * Section 2.2, Figure 2, Section 3.4) and the finalisation (step 8), every
+ * step on the GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Points are int32 (x, y) pairs, array-of-structures, 8 bytes per point,
+ *     8-byte aligned (16-byte alignment enables 128-bit loads); every
+ *     coordinate must satisfy |x|, |y| <= 2^29, else HULL_ERANGE.
+ *   - Orientation tests are exact int64 cross products.
+ *   - A hull is the list of its strict vertices (collinear boundary points
+ *     excluded) as 0-based input indices, counter-clockwise, starting at the
+ *     lexicographically smallest (x, y); among equal points the smallest
+ *     index is reported.  n = 0 gives 0 vertices, one distinct point gives
+ *     1, collinear points give the 2 endpoints.
+ *   - Pointers named d_* are device pointers, h_* host pointers.  The
+ *     caller owns every buffer it passes; the library never frees or keeps
+ *     them past the call.  A context owns its device workspace (grown on
+ *     demand, freed by hull_destroy).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; calls that return a count to the
+ *     host synchronise that stream before returning.
+ *   - Errors never trap the GPU and leave no sticky CUDA error: device
+ *     waits are bounded and report HULL_ETIMEOUT; every device write is
+ *     bounds-checked.  A context is not thread-safe: use one per host
+ *     thread (or serialise calls).
+ */
+#ifndef GBHULL_H
+#define GBHULL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hull_ctx hull_ctx;
+
+typedef enum {
+  HULL_OK = 0,
+  HULL_EINVAL = 1,     /* null/negative/misaligned argument, n >= 2^30 */
+  HULL_ERANGE = 2,     /* a coordinate beyond +-2^29; outputs untouched */
+  HULL_ENOMEM = 3,     /* workspace allocation failed */
+  HULL_ECAPACITY = 4,  /* output capacity below the hull size; count still reported */
+  HULL_ETIMEOUT = 5,   /* a bounded device wait ran out; results invalid */
+  HULL_ECUDA = 6,      /* a CUDA runtime call failed */
+  HULL_EINTERNAL = 7   /* a device index left its buffer (write skipped) */
+} hull_status;
+
+typedef struct {
+  int proposal;       /* 0 = quadrilateral of the four extremes (the paper), 1 = learned */
+  int collect_stats;  /* 1 = keep survivor counts of the last call for hull_last_stats */
+  uint32_t spin_limit;/* iteration limit of every device wait; 0 = default (1 << 22) */
+  int reserved;
+} hull_config;
+
+typedef struct {
+  int64_t n;          /* input points */
+  int64_t s;          /* survivors of the first-round filter (Section 3.1) */
+  int64_t r_lower;    /* second-round survivors, region right of P_minx -> P_maxx */
+  int64_t r_upper;    /* second-round survivors, region left of it (Section 2.2) */
+  int64_t h;          /* hull vertices */
+  int32_t ext[4];     /* indices of P_minx, P_maxx, P_miny, P_maxy (Section 2.1 step 1) */
+  int32_t ncorner;    /* distinct corners of the filter polygon */
+  int32_t learned_used; /* 1 when the learned polygon replaced the quadrilateral */
+} hull_stats;
+
+/* Creates a context on CUDA device `device` (cfg NULL = defaults).
+ * *out receives the context; NULL on failure.  Errors: EINVAL, ECUDA. */
+hull_status hull_create(hull_ctx **out, int device, const hull_config *cfg);
+
+/* Frees the context and its workspace.  NULL-safe.  Synchronises the device
+ * work the context launched. */
+void hull_destroy(hull_ctx *ctx);
+
+/* Convex hull of n points (Section 1's problem; the gScan pipeline of
+ * Section 2.1).  d_xy: device int32[n][2], read-only.  d_out: device
+ * int32[cap] receiving the CCW vertex indices.  *h_count (host) receives the
+ * hull size on HULL_OK and on HULL_ECAPACITY (then d_out is untouched).
+ * Synchronises `stream` before returning.  n must be < 2^30. */
+hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out,
+                         int64_t cap, int64_t *h_count, void *stream);
+
+/* The same computation on host buffers: copies h_xy (n points, preferably
+ * pinned) to the device, computes, and copies the vertex indices back into
+ * h_out (host int32[cap]).  Same errors as hull_compute. */
+hull_status hull_compute_host(hull_ctx *ctx, const int32_t *h_xy, int64_t n, int32_t *h_out,
+                              int64_t cap, int64_t *h_count, void *stream);
+
+/* B independent hulls in one call.  d_offsets: device int64[B+1], instance
+ * b is points [d_offsets[b], d_offsets[b+1]) of d_xy (non-decreasing,
+ * d_offsets[0] = 0).  Vertex indices are relative to their instance and are
+ * written to d_out at d_out_offsets[b] (device int64[B+1], written by the
+ * call; d_out_offsets[B] = total vertices).  cap bounds the total.  Total
+ * points must be < 2^30 and every instance < 2^30.  Synchronises `stream`. */
+hull_status hull_compute_batched(hull_ctx *ctx, const int32_t *d_xy, const int64_t *d_offsets,
+                                 int32_t B, int32_t *d_out, int64_t cap, int64_t *d_out_offsets,
+                                 void *stream);
+
+/* Survivor counts and extremes of the last hull_compute (collect_stats=1). */
+hull_status hull_last_stats(const hull_ctx *ctx, hull_stats *out);
+
+/* Per-stage device time of hull_compute calls, measured with CUDA events
+ * recorded on the call's stream between the pipeline's kernels (profiling
+ * must be enabled with hull_set_profiling; accumulation restarts then). */
+#define HULL_NUM_STAGES 12
+typedef struct {
+  int64_t calls;                 /* hull_compute calls accumulated */
+  int64_t sort_passes;           /* radix passes that did work, summed over calls */
+  int64_t points;                /* input points, summed */
+  int64_t survivors;             /* first-round survivors, summed */
+  int64_t second_round;          /* second-round survivors, summed */
+  double ms[HULL_NUM_STAGES];    /* extremes, filter, sort pass 0..7, regions, final */
+} hull_profile;
+
+hull_status hull_set_profiling(hull_ctx *ctx, int enable);
+hull_status hull_get_profile(const hull_ctx *ctx, hull_profile *out);
+
+/* Short English text for a status code (static storage). */
+const char *hull_status_string(hull_status s);
+
+/* ---- stage entry points: each runs one step of the pipeline on its own,
+ * so that every step can be checked against a CPU restatement. ---- */
+
+/* Section 2.1 step 1 / Section 3.1: h_ext[4] (host) = indices of P_minx =
+ * argmin (x, y), P_maxx = argmax (x, y), P_miny = argmin (y, x), P_maxy =
+ * argmax (y, x), ties to the smallest index; n >= 1.  ERANGE is reported
+ * after h_ext is written. */
+hull_status hull_stage_extremes(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *h_ext,
+                                void *stream);
+
+/* Section 2.1 step 2 / Section 3.1: indices of the points not strictly
+ * inside the quadrilateral P_minx, P_miny, P_maxx, P_maxy (nothing is
+ * discarded when it has fewer than three distinct corners), ascending, into
+ * d_keep (device int32[n]); *h_s = their count. */
+hull_status hull_stage_filter(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_keep,
+                              int64_t *h_s, void *stream);
+
+/* Section 2.1 step 4 / Section 3.3: stable ascending sort of m (key, value)
+ * pairs: d_keys (device uint64[m]) and d_vals (device uint32[m]) are sorted
+ * in place (the workspace holds the ping-pong copies).  m < 2^30. */
+hull_status hull_stage_sort(hull_ctx *ctx, uint64_t *d_keys, uint32_t *d_vals, int64_t m,
+                            void *stream);
+
+/* Section 2.1 steps 5-7 / Figure 2: the second-round filter over m points
+ * already sorted by (x, y, index): d_xy (device int32[m][2]) in that order
+ * and d_idx (device int32[m]) their labels.  Writes the kept labels of the
+ * lower region (right of P_0 -> P_l) to d_lower and of the upper region to
+ * d_upper (device int32[m] each), in list order; counts in *h_lower,
+ * *h_upper. */
+hull_status hull_stage_second_round(hull_ctx *ctx, const int32_t *d_xy, const int32_t *d_idx,
+                                    int64_t m, int32_t *d_lower, int64_t *h_lower,
+                                    int32_t *d_upper, int64_t *h_upper, void *stream);
+
+/* Section 2.1 step 8: stack-based chains over m >= 2 distinct points in
+ * lexicographic order (d_xy device int32[m][2]).  d_out (device int32[cap])
+ * receives the lower chain's positions (first to last point, left turns)
+ * followed by the upper chain's positions reversed without its endpoints;
+ * *h_lower and *h_upper receive both chain lengths (endpoints included). */
+hull_status hull_stage_chain(hull_ctx *ctx, const int32_t *d_xy, int64_t m, int32_t *d_out,
+                             int64_t cap, int64_t *h_lower, int64_t *h_upper, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBHULL_H */

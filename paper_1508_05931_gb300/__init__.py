@@ -10,6 +10,6 @@ __all__ = ["hull", "workloads"]
 
 def __getattr__(name):
     if name == "hull":
-        from . import hull as _h
-        return _h
+        import importlib
+        return importlib.import_module(__name__ + ".hull")
     raise AttributeError(name)

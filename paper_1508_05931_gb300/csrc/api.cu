@@ -1,0 +1,543 @@
+// The C ABI (include/gbhull.h): contexts, workspace, argument checks, the
+// launch sequence of the pipeline and the per-stage entry points.
+#include <cstddef>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/gbhull.h"
+#include "hull_internal.cuh"
+#include "kernels.h"
+
+using namespace gbh;
+
+namespace {
+
+constexpr uint32_t kDefaultSpin = 1u << 22;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device workspace for up to `cap` points, carved out of one allocation.
+struct Workspace {
+  size_t cap = 0;
+  void* base = nullptr;
+  ExtPartial* partials = nullptr;
+  u64* keys[2] = {nullptr, nullptr};
+  u32* idx[2] = {nullptr, nullptr};
+  u64* st_filter = nullptr;
+  u64* st_sort = nullptr;
+  void* st_region = nullptr;
+  int2* lo_xy = nullptr; int* lo_idx = nullptr;
+  int2* up_xy = nullptr; int* up_idx = nullptr;
+  int2* h_xy[2] = {nullptr, nullptr};
+  int* h_idx[2] = {nullptr, nullptr};
+  u32* cnt[2] = {nullptr, nullptr};
+  int4* jobs = nullptr;
+  int* aux = nullptr;          // int32[cap]: labels for stage entry points
+};
+
+struct HostStage {
+  size_t cap = 0;
+  int32_t* d_in = nullptr;     // device copy of host points
+  int32_t* d_out = nullptr;    // device output for host calls
+};
+
+}  // namespace
+
+struct hull_ctx {
+  int device = 0;
+  hull_config cfg{};
+  int num_sms = 0;
+  int occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
+  Plan* plan = nullptr;        // device
+  Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
+  Workspace ws;
+  HostStage hs;
+  hull_stats last{};
+  // stage timing (hull_set_profiling)
+  bool prof = false;
+  bool prof_pending = false;
+  cudaEvent_t ev[HULL_NUM_STAGES + 1] = {};
+  hull_profile profile{};
+};
+
+namespace {
+
+constexpr size_t kSummaryBytes = offsetof(Plan, ctr);
+
+hull_status cuda_fail(cudaError_t e) {
+  (void)e;
+  cudaGetLastError();   // clear a non-sticky error so the context stays usable
+  return HULL_ECUDA;
+}
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void free_ws(Workspace& w) {
+  if (w.base) cudaFree(w.base);
+  w = Workspace{};
+}
+
+hull_status ensure_ws(hull_ctx* c, size_t n) {
+  if (n <= c->ws.cap && c->ws.base) return HULL_OK;
+  size_t cap = align_up(n < 65536 ? 65536 : n, 65536);
+  const size_t chunk = (size_t)k5_chunk();
+  const size_t t2 = (cap + k2_tile() - 1) / k2_tile() + 1;
+  const size_t t3 = (cap + k3_tile() - 1) / k3_tile() + 1;
+  const size_t t4 = (cap + k4_tile() - 1) / k4_tile() + 1;
+  const size_t slots = cap + 4 + 2 * chunk;
+  const size_t nchunks = slots / chunk + 2;
+  const size_t parts = (size_t)c->num_sms * 4 + 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_part = take(parts * sizeof(ExtPartial));
+  const size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8);
+  const size_t o_i0 = take(cap * 4), o_i1 = take(cap * 4);
+  const size_t o_sf = take(t2 * 8), o_ss = take(t3 * kRadix * 8), o_sr = take(t4 * k4_status_bytes());
+  const size_t status_end = off;
+  const size_t o_lxy = take((cap + 2) * 8), o_lid = take((cap + 2) * 4);
+  const size_t o_uxy = take((cap + 2) * 8), o_uid = take((cap + 2) * 4);
+  const size_t o_h0x = take(slots * 8), o_h0i = take(slots * 4);
+  const size_t o_h1x = take(slots * 8), o_h1i = take(slots * 4);
+  const size_t o_c0 = take(nchunks * 4), o_c1 = take(nchunks * 4);
+  const size_t o_jobs = take(nchunks * 16);
+  const size_t o_aux = take(cap * 4);
+  const size_t total = off;
+
+  cudaDeviceSynchronize();
+  free_ws(c->ws);
+  void* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) {
+    cudaGetLastError();
+    return HULL_ENOMEM;
+  }
+  // Look-back status words must start out matching no epoch.
+  if (cudaMemset(base, 0, status_end) != cudaSuccess) {
+    cudaFree(base);
+    return cuda_fail(cudaErrorUnknown);
+  }
+  char* b = static_cast<char*>(base);
+  Workspace& w = c->ws;
+  w.cap = cap;
+  w.base = base;
+  w.partials = reinterpret_cast<ExtPartial*>(b + o_part);
+  w.keys[0] = reinterpret_cast<u64*>(b + o_k0); w.keys[1] = reinterpret_cast<u64*>(b + o_k1);
+  w.idx[0] = reinterpret_cast<u32*>(b + o_i0);  w.idx[1] = reinterpret_cast<u32*>(b + o_i1);
+  w.st_filter = reinterpret_cast<u64*>(b + o_sf);
+  w.st_sort = reinterpret_cast<u64*>(b + o_ss);
+  w.st_region = b + o_sr;
+  w.lo_xy = reinterpret_cast<int2*>(b + o_lxy); w.lo_idx = reinterpret_cast<int*>(b + o_lid);
+  w.up_xy = reinterpret_cast<int2*>(b + o_uxy); w.up_idx = reinterpret_cast<int*>(b + o_uid);
+  w.h_xy[0] = reinterpret_cast<int2*>(b + o_h0x); w.h_idx[0] = reinterpret_cast<int*>(b + o_h0i);
+  w.h_xy[1] = reinterpret_cast<int2*>(b + o_h1x); w.h_idx[1] = reinterpret_cast<int*>(b + o_h1i);
+  w.cnt[0] = reinterpret_cast<u32*>(b + o_c0); w.cnt[1] = reinterpret_cast<u32*>(b + o_c1);
+  w.jobs = reinterpret_cast<int4*>(b + o_jobs);
+  w.aux = reinterpret_cast<int*>(b + o_aux);
+  return HULL_OK;
+}
+
+int grid_for(int occ, int num_sms, size_t work_tiles) {
+  size_t g = (size_t)occ * (size_t)num_sms;
+  if (work_tiles < g) g = work_tiles;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Copies the summary back, synchronises and maps device error bits.
+hull_status finish(hull_ctx* c, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(c->h_plan, c->plan, kSummaryBytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const Plan& p = *c->h_plan;
+  if (c->prof_pending) {
+    c->prof_pending = false;
+    hull_profile& f = c->profile;
+    for (int k = 0; k < HULL_NUM_STAGES; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) == cudaSuccess) f.ms[k] += ms;
+    }
+    cudaGetLastError();
+    f.calls += 1;
+    f.sort_passes += p.npasses;
+    f.points += p.n;
+    f.survivors += p.s;
+    f.second_round += (int64_t)p.r_lo + p.r_up;
+  }
+  if (c->cfg.collect_stats) {
+    c->last.n = p.n; c->last.s = p.s; c->last.r_lower = p.r_lo; c->last.r_upper = p.r_up;
+    c->last.h = p.h;
+    for (int j = 0; j < 4; ++j) c->last.ext[j] = p.ext_idx[j];
+    c->last.ncorner = p.ncorner;
+    c->last.learned_used = p.learned_used;
+  }
+  if (p.error & ERR_RANGE) return HULL_ERANGE;
+  if (p.error & ERR_TIMEOUT) return HULL_ETIMEOUT;
+  if (p.error & ERR_INTERNAL) return HULL_EINTERNAL;
+  if (p.error & ERR_CAPACITY) return HULL_ECAPACITY;
+  return HULL_OK;
+}
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+void mark(hull_ctx* c, int k, cudaStream_t st) {
+  if (c->prof_pending) cudaEventRecord(c->ev[k], st);
+}
+
+// K1 .. K4 of the pipeline on d_xy (n >= 1).
+hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) {
+  Workspace& w = c->ws;
+  mark(c, 0, st);
+  cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  mark(c, 1, st);
+  const size_t t2 = (n + k2_tile() - 1) / k2_tile();
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, grid_for(c->occ_k2, c->num_sms, t2), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  mark(c, 2, st);
+  const size_t t3 = (n + k3_tile() - 1) / k3_tile();
+  for (u32 p = 0; p < (u32)kMaxPasses; ++p) {
+    e = launch_k3(w.keys[p & 1], w.idx[p & 1], w.keys[(p + 1) & 1], w.idx[(p + 1) & 1], c->plan,
+                  w.st_sort, p, grid_for(c->occ_k3, c->num_sms, t3), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    mark(c, 3 + (int)p, st);
+  }
+  const size_t t4 = (n + k4_tile() - 1) / k4_tile();
+  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
+                w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, t4), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  mark(c, 3 + kMaxPasses, st);
+  return HULL_OK;
+}
+
+hull_status run_final(hull_ctx* c, const int2* lo_xy, const int* lo_idx, const int2* up_xy,
+                      const int* up_idx, size_t npoints_bound, int32_t* d_out, int64_t cap,
+                      cudaStream_t st) {
+  Workspace& w = c->ws;
+  const size_t chunks = (npoints_bound + 4) / (size_t)k5_chunk() + 2;
+  int grid = grid_for(c->occ_k5, c->num_sms, chunks < 64 ? 64 : chunks);
+  cudaError_t e = launch_k5(lo_xy, lo_idx, up_xy, up_idx, c->plan, w.h_xy[0], w.h_idx[0], w.h_xy[1],
+                            w.h_idx[1], w.cnt[0], w.cnt[1], w.jobs, d_out, (long long)cap, grid, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  mark(c, 4 + kMaxPasses, st);
+  return HULL_OK;
+}
+
+hull_status new_call_patch(hull_ctx* c, cudaStream_t st, PlanPatch p) {
+  p.new_call = 1;
+  p.spin_limit = c->cfg.spin_limit;
+  p.zero_counters = 1;
+  cudaError_t e = launch_plan_patch(c->plan, p, st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hull_status_string(hull_status s) {
+  switch (s) {
+    case HULL_OK: return "ok";
+    case HULL_EINVAL: return "invalid argument";
+    case HULL_ERANGE: return "coordinate out of range (|x|, |y| must be <= 2^29)";
+    case HULL_ENOMEM: return "device memory allocation failed";
+    case HULL_ECAPACITY: return "output capacity below the hull size";
+    case HULL_ETIMEOUT: return "a bounded device wait timed out";
+    case HULL_ECUDA: return "CUDA runtime error";
+    case HULL_EINTERNAL: return "internal index check failed";
+  }
+  return "unknown status";
+}
+
+hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
+  if (!out) return HULL_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+  if (device < 0 || device >= ndev) return HULL_EINVAL;
+  DevGuard g(device);
+  hull_ctx* c = new (std::nothrow) hull_ctx();
+  if (!c) return HULL_ENOMEM;
+  c->device = device;
+  if (cfg) c->cfg = *cfg;
+  if (c->cfg.spin_limit == 0) c->cfg.spin_limit = kDefaultSpin;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return cuda_fail(cudaErrorUnknown); }
+  c->num_sms = prop.multiProcessorCount;
+  if (k3_configure() != cudaSuccess || k5_configure(&c->occ_k5) != cudaSuccess ||
+      k2_occupancy(&c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
+      k4_occupancy(&c->occ_k4) != cudaSuccess) {
+    delete c;
+    return cuda_fail(cudaErrorUnknown);
+  }
+  if (c->occ_k5 < 1) { delete c; return HULL_ECUDA; }
+  if (cudaMalloc(&c->plan, sizeof(Plan)) != cudaSuccess) { delete c; return HULL_ENOMEM; }
+  if (cudaMemset(c->plan, 0, sizeof(Plan)) != cudaSuccess ||
+      cudaMallocHost(&c->h_plan, sizeof(Plan)) != cudaSuccess) {
+    cudaFree(c->plan);
+    delete c;
+    return HULL_ENOMEM;
+  }
+  std::memset(c->h_plan, 0, sizeof(Plan));
+  *out = c;
+  return HULL_OK;
+}
+
+void hull_destroy(hull_ctx* c) {
+  if (!c) return;
+  DevGuard g(c->device);
+  cudaDeviceSynchronize();
+  free_ws(c->ws);
+  if (c->hs.d_in) cudaFree(c->hs.d_in);
+  if (c->hs.d_out) cudaFree(c->hs.d_out);
+  for (int k = 0; k <= HULL_NUM_STAGES; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->plan) cudaFree(c->plan);
+  if (c->h_plan) cudaFreeHost(c->h_plan);
+  delete c;
+}
+
+hull_status hull_compute(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_out, int64_t cap,
+                         int64_t* h_count, void* stream) {
+  if (!c || !h_count || n < 0 || cap < 0 || n > (int64_t)kMaxN) return HULL_EINVAL;
+  if (n > 0 && (!d_xy || !aligned8(d_xy))) return HULL_EINVAL;
+  if (cap > 0 && !d_out) return HULL_EINVAL;
+  *h_count = 0;
+  if (n == 0) {
+    if (c->cfg.collect_stats) c->last = hull_stats{};
+    return HULL_OK;
+  }
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  c->prof_pending = c->prof;
+  r = run_front(c, d_xy, (u32)n, st);
+  if (r != HULL_OK) { c->prof_pending = false; return r; }
+  r = run_final(c, c->ws.lo_xy, c->ws.lo_idx, c->ws.up_xy, c->ws.up_idx, (size_t)n, d_out, cap, st);
+  if (r != HULL_OK) c->prof_pending = false;
+  if (r != HULL_OK) return r;
+  r = finish(c, st);
+  if (r == HULL_OK || r == HULL_ECAPACITY) *h_count = c->h_plan->h;
+  return r;
+}
+
+hull_status hull_compute_host(hull_ctx* c, const int32_t* h_xy, int64_t n, int32_t* h_out,
+                              int64_t cap, int64_t* h_count, void* stream) {
+  if (!c || !h_count || n < 0 || cap < 0 || n > (int64_t)kMaxN) return HULL_EINVAL;
+  if (n > 0 && !h_xy) return HULL_EINVAL;
+  if (cap > 0 && !h_out) return HULL_EINVAL;
+  *h_count = 0;
+  if (n == 0) return HULL_OK;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((size_t)n > c->hs.cap) {
+    cudaDeviceSynchronize();
+    if (c->hs.d_in) cudaFree(c->hs.d_in);
+    if (c->hs.d_out) cudaFree(c->hs.d_out);
+    c->hs = HostStage{};
+    size_t hc = align_up((size_t)n, 65536);
+    if (cudaMalloc(&c->hs.d_in, hc * 8) != cudaSuccess || cudaMalloc(&c->hs.d_out, hc * 4) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->hs.d_in) cudaFree(c->hs.d_in);
+      c->hs = HostStage{};
+      return HULL_ENOMEM;
+    }
+    c->hs.cap = hc;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->hs.d_in, h_xy, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int64_t h = 0;
+  hull_status r = hull_compute(c, c->hs.d_in, n, c->hs.d_out, (int64_t)c->hs.cap, &h, stream);
+  if (r != HULL_OK) return r;
+  *h_count = h;
+  if (h > cap) return HULL_ECAPACITY;
+  if (h > 0) {
+    e = cudaMemcpyAsync(h_out, c->hs.d_out, (size_t)h * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return HULL_OK;
+}
+
+hull_status hull_set_profiling(hull_ctx* c, int enable) {
+  if (!c) return HULL_EINVAL;
+  DevGuard g(c->device);
+  if (enable && !c->ev[0]) {
+    for (int k = 0; k <= HULL_NUM_STAGES; ++k)
+      if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+  }
+  c->prof = enable != 0;
+  c->profile = hull_profile{};
+  return HULL_OK;
+}
+
+hull_status hull_get_profile(const hull_ctx* c, hull_profile* out) {
+  if (!c || !out) return HULL_EINVAL;
+  *out = c->profile;
+  return HULL_OK;
+}
+
+hull_status hull_last_stats(const hull_ctx* c, hull_stats* out) {
+  if (!c || !out) return HULL_EINVAL;
+  *out = c->last;
+  return HULL_OK;
+}
+
+hull_status hull_stage_extremes(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* h_ext,
+                                void* stream) {
+  if (!c || !d_xy || !h_ext || n < 1 || n > (int64_t)kMaxN || !aligned8(d_xy)) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  cudaError_t e = launch_k1(d_xy, (u32)n, c->cfg.spin_limit, c->plan, c->ws.partials,
+                            k1_grid((u32)n, c->num_sms), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  for (int j = 0; j < 4; ++j) h_ext[j] = c->h_plan->ext_idx[j];
+  return r;
+}
+
+hull_status hull_stage_filter(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_keep,
+                              int64_t* h_s, void* stream) {
+  if (!c || !d_xy || !d_keep || !h_s || n < 1 || n > (int64_t)kMaxN || !aligned8(d_xy)) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  cudaError_t e = launch_k1(d_xy, (u32)n, c->cfg.spin_limit, c->plan, c->ws.partials,
+                            k1_grid((u32)n, c->num_sms), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t t2 = ((size_t)n + k2_tile() - 1) / k2_tile();
+  e = launch_k2(d_xy, c->plan, c->ws.keys[0], c->ws.idx[0], c->ws.st_filter,
+                grid_for(c->occ_k2, c->num_sms, t2), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  if (r != HULL_OK) return r;
+  *h_s = c->h_plan->s;
+  if (c->h_plan->s > 0) {
+    e = cudaMemcpyAsync(d_keep, c->ws.idx[0], (size_t)c->h_plan->s * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return HULL_OK;
+}
+
+hull_status hull_stage_sort(hull_ctx* c, uint64_t* d_keys, uint32_t* d_vals, int64_t m, void* stream) {
+  if (!c || m < 0 || m > (int64_t)kMaxN) return HULL_EINVAL;
+  if (m == 0) return HULL_OK;
+  if (!d_keys || !d_vals) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)m);
+  if (r != HULL_OK) return r;
+  Workspace& w = c->ws;
+  cudaError_t e = cudaMemcpyAsync(w.keys[0], d_keys, (size_t)m * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.idx[0], d_vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  PlanPatch p{};
+  p.zero_hist = 1; p.set_s = 1; p.s = (u32)m; p.set_npasses = 1; p.npasses = kMaxPasses;
+  r = new_call_patch(c, st, p);
+  if (r != HULL_OK) return r;
+  e = launch_hist(w.keys[0], c->plan, c->num_sms * 2, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t t3 = ((size_t)m + k3_tile() - 1) / k3_tile();
+  for (u32 pp = 0; pp < (u32)kMaxPasses; ++pp) {
+    e = launch_k3(w.keys[pp & 1], w.idx[pp & 1], w.keys[(pp + 1) & 1], w.idx[(pp + 1) & 1], c->plan,
+                  w.st_sort, pp, grid_for(c->occ_k3, c->num_sms, t3), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  // kMaxPasses is even: the result is back in buffer 0.
+  e = cudaMemcpyAsync(d_keys, w.keys[0], (size_t)m * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_vals, w.idx[0], (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return finish(c, st);
+}
+
+hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int32_t* d_idx, int64_t m,
+                                    int32_t* d_lower, int64_t* h_lower, int32_t* d_upper,
+                                    int64_t* h_upper, void* stream) {
+  if (!c || !d_xy || !d_idx || !d_lower || !d_upper || !h_lower || !h_upper || m < 1 ||
+      m > (int64_t)kMaxN || !aligned8(d_xy))
+    return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)m);
+  if (r != HULL_OK) return r;
+  Workspace& w = c->ws;
+  // K1 on the sorted list gives P_0 (first) and P_l (first of the last run)
+  // and the key layout; K2 with no polygon keeps every point in list order.
+  cudaError_t e = launch_k1(d_xy, (u32)m, c->cfg.spin_limit, c->plan, w.partials,
+                            k1_grid((u32)m, c->num_sms), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  PlanPatch p{};
+  p.set_ncorner = 1; p.ncorner = 0;
+  e = launch_plan_patch(c->plan, p, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t t = ((size_t)m + k2_tile() - 1) / k2_tile();
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, grid_for(c->occ_k2, c->num_sms, t), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  PlanPatch q{};
+  q.set_npasses = 1; q.npasses = 0;
+  e = launch_plan_patch(c->plan, q, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t t4 = ((size_t)m + k4_tile() - 1) / k4_tile();
+  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
+                w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, t4), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  // The region lists hold list positions at [1, r]; map them to labels.
+  e = launch_gather_labels(w.lo_idx, d_idx, &c->plan->r_lo, 1, d_lower, (u32)m, st);
+  if (e == cudaSuccess) e = launch_gather_labels(w.up_idx, d_idx, &c->plan->r_up, 1, d_upper, (u32)m, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  *h_lower = c->h_plan->r_lo;
+  *h_upper = c->h_plan->r_up;
+  return r;
+}
+
+hull_status hull_stage_chain(hull_ctx* c, const int32_t* d_xy, int64_t m, int32_t* d_out, int64_t cap,
+                             int64_t* h_lower, int64_t* h_upper, void* stream) {
+  if (!c || !d_xy || !h_lower || !h_upper || m < 2 || m > (int64_t)kMaxN / 2 || cap < 0 ||
+      (cap > 0 && !d_out) || !aligned8(d_xy))
+    return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)m * 2);
+  if (r != HULL_OK) return r;
+  Workspace& w = c->ws;
+  cudaError_t e = launch_iota(w.aux, (u32)m, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  PlanPatch p{};
+  p.set_r = 1; p.r_lo = (u32)m - 2; p.r_up = (u32)m - 2;
+  r = new_call_patch(c, st, p);
+  if (r != HULL_OK) return r;
+  const int2* xy = reinterpret_cast<const int2*>(d_xy);
+  r = run_final(c, xy, w.aux, xy, w.aux, (size_t)m * 2, d_out, cap, st);
+  if (r != HULL_OK) return r;
+  r = finish(c, st);
+  *h_lower = c->h_plan->h_lo;
+  *h_upper = c->h_plan->h_up;
+  return r;
+}
+
+hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t* d_offsets, int32_t B,
+                                 int32_t* d_out, int64_t cap, int64_t* d_out_offsets, void* stream) {
+  (void)c; (void)d_xy; (void)d_offsets; (void)B; (void)d_out; (void)cap; (void)d_out_offsets; (void)stream;
+  return HULL_EINVAL;
+}
+
+}  // extern "C"

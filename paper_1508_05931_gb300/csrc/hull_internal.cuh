@@ -1,0 +1,165 @@
+// Internal definitions shared by the sm_103a kernels of the hull pipeline.
+//
+// The pipeline follows Section 2.1 of Mei, "gScan: Accelerating Graham Scan
+// on the GPU" (arXiv 1508.05931), steps 1-8, every step on the device:
+//   K1 extremes (step 1)  ->  K2 quadrilateral filter + compaction (steps 2-3)
+//   -> K3 onesweep radix sort (step 4)  ->  K4 region split + second-round
+//   filter (steps 5-7, Figure 2 as an exclusive prefix-max scan)
+//   -> K5 monotone-chain finalisation (step 8).
+// A small device-resident Plan carries the sizes and parameters from one
+// kernel to the next, so the host never synchronises inside a call.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbh {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr int kCoordLimit = 1 << 29;     // |x|, |y| <= 2^29
+constexpr int kMaxCorners = 8;           // filter polygon: 4 (quad) or up to 8 (learned)
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;            // 64-bit keys / 8-bit digits
+constexpr u32 kMaxN = (1u << 30) - 1;    // look-back count fields are 30 bits
+
+// Error bits accumulated in Plan::error by the kernels.
+enum : u32 {
+  ERR_RANGE = 1u,       // a coordinate beyond +-2^29
+  ERR_TIMEOUT = 2u,     // a bounded device wait ran out
+  ERR_CAPACITY = 4u,    // output capacity below the hull size
+  ERR_INTERNAL = 8u,    // an index left its buffer (skipped, never written)
+};
+
+// Each call consumes kEpochStride epochs; look-back status words carry the
+// epoch in their top 32 bits so stale words from earlier calls never match.
+constexpr u32 kEpochStride = 16;
+enum EpochSlot : u32 { EP_FILTER = 1, EP_SORT0 = 2, EP_REGION = 2 + kMaxPasses, EP_FINAL = 3 + kMaxPasses };
+
+// Counters (dynamic tile ids, barriers), zeroed by K1 for every call.
+enum CounterSlot : int {
+  CTR_FILTER = 0,
+  CTR_SORT0 = 1,                          // .. CTR_SORT0 + kMaxPasses - 1
+  CTR_REGION = 1 + kMaxPasses,
+  CTR_FINAL_CHUNK = 2 + kMaxPasses,
+  CTR_FINAL_BAR = 3 + kMaxPasses,
+  CTR_FINAL_BAR_GEN = 4 + kMaxPasses,
+  kNumCounters = 16,
+};
+
+struct ExtPartial {
+  u64 key[4];
+  u32 idx[4];
+};
+
+struct Plan {
+  // summary fields first: the host copies back everything before `ctr`
+  u32 n;
+  u32 spin_limit;
+  u32 epoch;            // base epoch of the current call
+  u32 error;
+  u32 s;                // survivors of the first round
+  u32 r_lo, r_up;       // survivors of the second round per region
+  u32 h;                // hull size
+  u32 h_lo, h_up;       // chain lengths (including both endpoints)
+  int32_t ncorner;
+  int32_t learned_used; // 1 when a learned polygon replaced the quad
+  int32_t ext_idx[4];   // P_minx, P_maxx, P_miny, P_maxy
+  int32_t ext_x[4], ext_y[4];
+  int32_t cx[kMaxCorners], cy[kMaxCorners];
+  int32_t key_x0, key_y0;   // key origin (bounding-box minimum)
+  u32 ybits, kbits, npasses;
+  u32 k1_done;          // last-block counter of K1 (self-resetting)
+  // per-call scratch
+  u32 ctr[kNumCounters];
+  u32 hist[kMaxPasses][kRadix];   // digit histograms of the survivors' keys
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ u64 ld_acquire_u64(const u64* p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(u64* p, u64 v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u32 ld_volatile_u32(const u32* p) {
+  return *reinterpret_cast<const volatile u32*>(p);
+}
+__device__ __forceinline__ void flag_error(Plan* plan, u32 bit) { atomicOr(&plan->error, bit); }
+__device__ __forceinline__ bool aborted(const Plan* plan) {
+  return (ld_volatile_u32(&plan->error) & (ERR_TIMEOUT | ERR_INTERNAL)) != 0;
+}
+
+// Exact orientation (b - a) x (c - a) in int64.  Coordinates are bounded by
+// 2^29, so each difference fits in int32 and each product in 2^60.
+__device__ __forceinline__ long long orient(int ax, int ay, int bx, int by, int cx, int cy) {
+  int ux = bx - ax, uy = by - ay, vx = cx - ax, vy = cy - ay;
+  return (long long)ux * vy - (long long)uy * vx;
+}
+// Cross product of two direction vectors (differences of bounded points).
+__device__ __forceinline__ long long cross2(int ax, int ay, int bx, int by) {
+  return (long long)ax * by - (long long)ay * bx;
+}
+
+// Look-back status word: [epoch:32 | flag:2 | count:30].
+constexpr u32 ST_AGG = 1, ST_INCL = 2;
+__device__ __forceinline__ u64 make_status(u32 epoch, u32 flag, u32 count) {
+  return ((u64)epoch << 32) | ((u64)flag << 30) | (u64)(count & 0x3FFFFFFFu);
+}
+__device__ __forceinline__ u32 status_flag(u64 w, u32 epoch) {
+  return ((u32)(w >> 32) == epoch) ? (u32)((w >> 30) & 3u) : 0u;
+}
+__device__ __forceinline__ u32 status_count(u64 w) { return (u32)(w & 0x3FFFFFFFu); }
+
+// Back-off used inside bounded waits.
+__device__ __forceinline__ void spin_pause(u32 it) {
+  if (it > 64) __nanosleep(it > 4096 ? 256 : 32);
+}
+
+// Warp-cooperative decoupled look-back over a single count (K2).  Lane l
+// inspects tile (tile - 1 - l - 32*w) for windows w = 0, 1, ...; returns
+// the exclusive prefix of this tile, identical on all lanes.  On a timeout
+// (or another block's abort) sets ERR_TIMEOUT and returns 0.
+__device__ __forceinline__ u32 warp_lookback_count(u64* status, u32 tile, u32 epoch,
+                                                   Plan* plan, u32 spin_limit, bool* failed) {
+  const int lane = threadIdx.x & 31;
+  u32 excl = 0;
+  long long base = (long long)tile - 1;
+  *failed = false;
+  while (base >= 0) {
+    long long t = base - lane;
+    u64 w = 0;
+    u32 f = ST_INCL;   // lanes past tile 0 act as an empty inclusive prefix
+    if (t >= 0) {
+      u32 it = 0;
+      for (;;) {
+        w = ld_acquire_u64(&status[t]);
+        f = status_flag(w, epoch);
+        if (f != 0) break;
+        if (++it > spin_limit || aborted(plan)) { f = 0xFFu; break; }
+        spin_pause(it);
+      }
+    }
+    if (__any_sync(0xFFFFFFFFu, f == 0xFFu)) {
+      if (lane == 0) flag_error(plan, ERR_TIMEOUT);
+      *failed = true;
+      return 0;
+    }
+    u32 incl_mask = __ballot_sync(0xFFFFFFFFu, f == ST_INCL);
+    int stop = incl_mask ? (__ffs(incl_mask) - 1) : 31;   // nearest inclusive prefix
+    u32 c = (t >= 0 && lane <= stop) ? status_count(w) : 0u;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    excl += c;
+    if (incl_mask) break;
+    base -= 32;
+  }
+  return excl;
+}
+
+}  // namespace gbh

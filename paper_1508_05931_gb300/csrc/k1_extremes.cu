@@ -1,0 +1,228 @@
+// K1: the four extreme points (Section 2.1 step 1, Section 3.1).
+//
+// One streaming pass over the int32 (x, y) pairs with 128-bit loads (two
+// points per load).  Each candidate is a 64-bit lexicographic key plus the
+// input index; all four extremes are minima of (key, idx):
+//   P_minx: key (x, y)        P_maxx: complement of key (x, y)
+//   P_miny: key (y, x)        P_maxy: complement of key (y, x)
+// so ties resolve lexicographically and then to the smallest index.
+// Warp shuffles, then a block reduction, then the last block to finish
+// reduces the per-block partials and builds the Plan: the range check, the
+// counter-clockwise filter polygon, the radix-key layout, the epoch, and
+// zeroed counters and histograms for the kernels that follow.
+#include "hull_internal.cuh"
+#include "kernels.h"
+
+namespace gbh {
+
+namespace {
+
+__device__ __forceinline__ u32 ord(int v) { return (u32)v ^ 0x80000000u; }
+
+struct Best {
+  u64 k[4];
+  u32 i[4];
+};
+
+__device__ __forceinline__ void best_init(Best& b) {
+  #pragma unroll
+  for (int j = 0; j < 4; ++j) { b.k[j] = ~0ull; b.i[j] = 0xFFFFFFFFu; }
+}
+
+__device__ __forceinline__ bool lt_ki(u64 ka, u32 ia, u64 kb, u32 ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Points reach a thread in increasing index order, so a strict key
+// comparison keeps the smallest index among equal keys.
+__device__ __forceinline__ void consider(Best& b, int x, int y, u32 idx) {
+  u32 ox = ord(x), oy = ord(y);
+  u64 kxy = ((u64)ox << 32) | oy;
+  u64 kyx = ((u64)oy << 32) | ox;
+  if (kxy < b.k[0]) { b.k[0] = kxy; b.i[0] = idx; }
+  if (~kxy < b.k[1]) { b.k[1] = ~kxy; b.i[1] = idx; }
+  if (kyx < b.k[2]) { b.k[2] = kyx; b.i[2] = idx; }
+  if (~kyx < b.k[3]) { b.k[3] = ~kyx; b.i[3] = idx; }
+}
+
+__device__ __forceinline__ void merge_best(Best& a, const u64* k, const u32* i) {
+  #pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (lt_ki(k[j], i[j], a.k[j], a.i[j])) { a.k[j] = k[j]; a.i[j] = i[j]; }
+}
+
+__device__ __forceinline__ void warp_reduce(Best& b) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u64 k[4];
+    u32 i[4];
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      k[j] = __shfl_xor_sync(0xFFFFFFFFu, b.k[j], o);
+      i[j] = __shfl_xor_sync(0xFFFFFFFFu, b.i[j], o);
+    }
+    merge_best(b, k, i);
+  }
+}
+
+__device__ __forceinline__ u32 bitlen(u32 v) { return v ? 32u - (u32)__clz(v) : 0u; }
+
+// Builds the Plan from the final extremes (single thread).
+__device__ void finish_plan(Plan* plan, const Best& b) {
+  int ex[4], ey[4];
+  ex[0] = (int)(u32)((b.k[0] >> 32) ^ 0x80000000u);  ey[0] = (int)((u32)b.k[0] ^ 0x80000000u);
+  u64 k1 = ~b.k[1];
+  ex[1] = (int)(u32)((k1 >> 32) ^ 0x80000000u);      ey[1] = (int)((u32)k1 ^ 0x80000000u);
+  ey[2] = (int)(u32)((b.k[2] >> 32) ^ 0x80000000u);  ex[2] = (int)((u32)b.k[2] ^ 0x80000000u);
+  u64 k3 = ~b.k[3];
+  ey[3] = (int)(u32)((k3 >> 32) ^ 0x80000000u);      ex[3] = (int)((u32)k3 ^ 0x80000000u);
+  for (int j = 0; j < 4; ++j) { plan->ext_idx[j] = (int)b.i[j]; plan->ext_x[j] = ex[j]; plan->ext_y[j] = ey[j]; }
+
+  // The bounding box is spanned by the extremes, so the range check needs
+  // no per-point work.
+  // Starts the call's error word afresh.
+  bool bad = ex[0] < -kCoordLimit || ex[1] > kCoordLimit || ey[2] < -kCoordLimit || ey[3] > kCoordLimit;
+  plan->error = bad ? ERR_RANGE : 0u;
+
+  // Filter polygon: P_minx, P_miny, P_maxx, P_maxy (counter-clockwise along
+  // the hull), cyclically repeated corners removed.
+  const int order[4] = {0, 2, 1, 3};
+  int k = 0;
+  int cx[4], cy[4];
+  for (int j = 0; j < 4; ++j) {
+    int x = ex[order[j]], y = ey[order[j]];
+    if (k > 0 && cx[k - 1] == x && cy[k - 1] == y) continue;
+    cx[k] = x; cy[k] = y; ++k;
+  }
+  while (k > 1 && cx[k - 1] == cx[0] && cy[k - 1] == cy[0]) --k;
+  plan->ncorner = k;
+  for (int j = 0; j < k; ++j) { plan->cx[j] = cx[j]; plan->cy[j] = cy[j]; }
+
+  // Radix key: ((x - x0) << ybits) | (y - y0), order-isomorphic to the
+  // lexicographic (x, y) order; only the bits that vary are sorted.
+  plan->key_x0 = ex[0];
+  plan->key_y0 = ey[2];
+  u32 xr = (u32)(ex[1] - ex[0]);
+  u32 yr = (u32)(ey[3] - ey[2]);
+  u32 yb = bitlen(yr), xb = bitlen(xr);
+  plan->ybits = yb;
+  plan->kbits = xb + yb;
+  plan->npasses = (xb + yb + kRadixBits - 1) / kRadixBits;
+}
+
+template <int BLOCK, bool VEC>
+__global__ void __launch_bounds__(BLOCK)
+k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
+            ExtPartial* __restrict__ partials) {
+  Best b;
+  best_init(b);
+  const u32 tid = blockIdx.x * BLOCK + threadIdx.x;
+  const u32 nthreads = gridDim.x * BLOCK;
+  if (VEC) {
+    // 16-byte aligned: pair j holds points 2j and 2j + 1.
+    const int4* p4 = reinterpret_cast<const int4*>(xy);
+    const u32 npair = n >> 1;
+    u32 j = tid;
+    for (; j + 3 * nthreads < npair; j += 4 * nthreads) {
+      int4 v[4];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = p4[j + u * nthreads];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        u32 q = j + u * nthreads;
+        consider(b, v[u].x, v[u].y, 2 * q);
+        consider(b, v[u].z, v[u].w, 2 * q + 1);
+      }
+    }
+    for (; j < npair; j += nthreads) {
+      int4 v = p4[j];
+      consider(b, v.x, v.y, 2 * j);
+      consider(b, v.z, v.w, 2 * j + 1);
+    }
+    if ((n & 1u) && tid == 0) consider(b, xy[2 * (n - 1)], xy[2 * (n - 1) + 1], n - 1);
+  } else {
+    const int2* p2 = reinterpret_cast<const int2*>(xy);
+    for (u32 j = tid; j < n; j += nthreads) {
+      int2 v = p2[j];
+      consider(b, v.x, v.y, j);
+    }
+  }
+  warp_reduce(b);
+
+  constexpr int NW = BLOCK / 32;
+  __shared__ u64 sk[NW][4];
+  __shared__ u32 si[NW][4];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
+  __syncthreads();
+  if (wid == 0) {
+    best_init(b);
+    if (lane < NW) {
+      u64 k[4]; u32 i[4];
+      for (int q = 0; q < 4; ++q) { k[q] = sk[lane][q]; i[q] = si[lane][q]; }
+      merge_best(b, k, i);
+    }
+    warp_reduce(b);
+    if (lane == 0) {
+      ExtPartial* P = &partials[blockIdx.x];
+      for (int q = 0; q < 4; ++q) { P->key[q] = b.k[q]; P->idx[q] = b.i[q]; }
+      __threadfence();
+      u32 t = atomicAdd(&plan->k1_done, 1u);
+      am_last = (t == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!am_last) return;
+
+  // Last block: reduce all partials and build the Plan.
+  __threadfence();
+  best_init(b);
+  for (u32 p = threadIdx.x; p < gridDim.x; p += BLOCK) {
+    const volatile ExtPartial* P = &partials[p];
+    u64 k[4]; u32 i[4];
+    for (int q = 0; q < 4; ++q) { k[q] = P->key[q]; i[q] = P->idx[q]; }
+    merge_best(b, k, i);
+  }
+  warp_reduce(b);
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
+  __syncthreads();
+  // Zero the per-call counters and histograms for the later kernels.
+  for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&plan->hist[0][0])[q] = 0u;
+  for (int q = threadIdx.x; q < kNumCounters; q += BLOCK) plan->ctr[q] = 0u;
+  if (threadIdx.x == 0) {
+    best_init(b);
+    for (int w = 0; w < NW; ++w) merge_best(b, sk[w], si[w]);
+    plan->n = n;
+    plan->spin_limit = spin_limit;
+    finish_plan(plan, b);
+    plan->epoch += kEpochStride;
+    plan->s = 0; plan->r_lo = 0; plan->r_up = 0; plan->h = 0; plan->h_lo = 0; plan->h_up = 0;
+    plan->learned_used = 0;
+    plan->k1_done = 0;
+  }
+}
+
+}  // namespace
+
+int k1_grid(u32 n, int num_sms) {
+  const int block = 512;
+  long long want = ((long long)(n / 2) + block * 4 - 1) / (block * 4);
+  long long cap = (long long)num_sms * 4;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials,
+                      int grid, cudaStream_t st) {
+  const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
+  if (vec)
+    k1_extremes<512, true><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials);
+  else
+    k1_extremes<512, false><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace gbh

@@ -1,0 +1,326 @@
+// K5: the finalisation (Section 2.1 step 8; Sections 3 and 5.2 run it on
+// the CPU as a stack-based scan of the pre-sorted survivors).  Here it runs
+// on the device as a parallel monotone chain:
+//
+//   phase A  each block takes chunks of K5_CHUNK consecutive points of a
+//            chain, every thread builds the chain of its K5_LEAF points with
+//            the stack rule (pop while the turn is not strict), and warps
+//            merge adjacent sub-chains level by level in shared memory;
+//   phase B  adjacent chunk chains are merged level by level across the
+//            grid (ping-pong buffers, bounded grid barriers);
+//   output   lower chain, then the upper chain reversed without its two
+//            endpoints: counter-clockwise from the lexicographic minimum.
+//
+// Two chains over points that are lexicographically separated (every
+// point of A before every point of B) merge at their common tangent: with
+// t(i) the first j where a_i -> b_j -> b_j+1 turns strictly (the farthest
+// tangent point of B seen from a_i), the merged chain keeps a_0..a_i* and
+// b_t(i*).. where i* is the first i at which a_i+1 is on or beyond the line
+// a_i -> b_t(i).  Both predicates are monotone along convex chains, so a
+// warp finds i* by a 32-ary search whose probes each binary-search t.
+// sign = +1 builds the lower chain (left turns), -1 the upper chain.
+#include <cooperative_groups.h>
+
+#include "hull_internal.cuh"
+#include "kernels.h"
+
+namespace gbh {
+
+namespace {
+
+constexpr int K5_BLOCK = 512;
+constexpr int K5_WARPS = K5_BLOCK / 32;
+constexpr int K5_LEAF = 8;
+constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // 4096 points per chunk
+
+struct SmemChain {
+  const int* x;
+  const int* y;
+  __device__ __forceinline__ int2 operator()(int i) const { return make_int2(x[i], y[i]); }
+};
+struct GlobalChain {
+  const int2* xy;
+  __device__ __forceinline__ int2 operator()(int i) const { return __ldcg(&xy[i]); }
+};
+
+__device__ __forceinline__ long long turn(int sgn, int2 a, int2 b, int2 c) {
+  long long o = orient(a.x, a.y, b.x, b.y, c.x, c.y);
+  return sgn > 0 ? o : -o;
+}
+
+// First j in [0, beta - 1) with a strict turn a -> b_j -> b_j+1, else beta - 1.
+template <class Acc>
+__device__ int tangent(const Acc& B, int beta, int2 a, int sgn) {
+  int lo = 0, hi = beta - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (turn(sgn, a, B(mid), B(mid + 1)) > 0) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Warp-cooperative bridge search; all lanes return the same (i*, j*).
+template <class AccA, class AccB>
+__device__ void bridge(const AccA& A, int alpha, const AccB& B, int beta, int sgn, int& istar,
+                       int& jstar) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = alpha - 1;               // the predicate holds at hi
+  while (hi > lo) {
+    const int span = hi - lo;
+    const int q = (span <= 32) ? lo + lane : lo + (int)(((long long)span * lane) >> 5);
+    bool pv = true;
+    if (q < hi) {
+      const int2 a = A(q);
+      const int t = tangent(B, beta, a, sgn);
+      pv = turn(sgn, a, B(t), A(q + 1)) >= 0;
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, pv);
+    const int f = m ? (__ffs(m) - 1) : 32;
+    const int qprev = __shfl_sync(0xFFFFFFFFu, q, f > 0 ? f - 1 : 0);
+    const int qf = __shfl_sync(0xFFFFFFFFu, q, f < 32 ? f : 31);
+    if (f == 0) {
+      hi = lo;
+    } else {
+      lo = qprev + 1;
+      if (f < 32) hi = qf;
+    }
+  }
+  istar = lo;
+  jstar = tangent(B, beta, A(lo), sgn);
+}
+
+__device__ bool grid_barrier(Plan* plan, u32 spin) {
+  __syncthreads();
+  __shared__ int s_bar_fail;
+  if (threadIdx.x == 0) {
+    s_bar_fail = 0;
+    __threadfence();
+    volatile u32* genp = &plan->ctr[CTR_FINAL_BAR_GEN];
+    const u32 gen = *genp;
+    const u32 arrived = atomicAdd(&plan->ctr[CTR_FINAL_BAR], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      plan->ctr[CTR_FINAL_BAR] = 0u;
+      __threadfence();
+      atomicAdd(&plan->ctr[CTR_FINAL_BAR_GEN], 1u);
+    } else {
+      u32 it = 0;
+      while (*genp == gen) {
+        if (++it > spin || aborted(plan)) {
+          flag_error(plan, ERR_TIMEOUT);
+          s_bar_fail = 1;
+          break;
+        }
+        spin_pause(it);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_bar_fail == 0;
+}
+
+struct ChainSet {
+  const int2* in_xy[2];
+  const int* in_idx[2];
+  u32 m[2];          // points per chain
+  u32 nchunk[2];
+  u32 slot0[2];      // first slot of each chain in the ping-pong buffers
+};
+
+__global__ void __launch_bounds__(K5_BLOCK)
+k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
+         const int2* __restrict__ up_xy, const int* __restrict__ up_idx, Plan* plan,
+         int2* __restrict__ h0_xy, int* __restrict__ h0_idx, int2* __restrict__ h1_xy,
+         int* __restrict__ h1_idx, u32* __restrict__ cnt0, u32* __restrict__ cnt1,
+         int4* __restrict__ jobs, int* __restrict__ out, long long cap) {
+  extern __shared__ __align__(16) unsigned char k5_smem[];
+  int* sx = reinterpret_cast<int*>(k5_smem);
+  int* sy = sx + K5_CHUNK;
+  int* si = sy + K5_CHUNK;
+  __shared__ int s_cnt[K5_BLOCK];
+
+  if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL)) return;
+  const u32 spin = plan->spin_limit;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  ChainSet cs;
+  cs.in_xy[0] = lo_xy; cs.in_idx[0] = lo_idx;
+  cs.in_xy[1] = up_xy; cs.in_idx[1] = up_idx;
+  cs.m[0] = plan->r_lo + 2;
+  cs.m[1] = plan->r_up + 2;
+  for (int c = 0; c < 2; ++c) cs.nchunk[c] = (cs.m[c] + K5_CHUNK - 1) / K5_CHUNK;
+  cs.slot0[0] = 0;
+  cs.slot0[1] = cs.nchunk[0] * K5_CHUNK;
+
+  // Every point equal: the hull is the single point P_0.
+  {
+    const int2 a = lo_xy[0], b = lo_xy[cs.m[0] - 1];
+    if (cs.m[0] == 2 && cs.m[1] == 2 && a.x == b.x && a.y == b.y) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        plan->h = 1; plan->h_lo = 1; plan->h_up = 1;
+        if (cap >= 1) out[0] = lo_idx[0];
+        else flag_error(plan, ERR_CAPACITY);
+      }
+      return;
+    }
+  }
+
+  // ---------------- phase A: chunk chains in shared memory
+  const u32 total_chunks = cs.nchunk[0] + cs.nchunk[1];
+  for (u32 ch = blockIdx.x; ch < total_chunks; ch += gridDim.x) {
+    const int c = ch < cs.nchunk[0] ? 0 : 1;
+    const u32 local = c == 0 ? ch : ch - cs.nchunk[0];
+    const int sgn = c == 0 ? 1 : -1;
+    const u32 first = local * K5_CHUNK;
+    const int len = (int)min((u32)K5_CHUNK, cs.m[c] - first);
+    for (int i = threadIdx.x; i < len; i += K5_BLOCK) {
+      const int2 p = cs.in_xy[c][first + i];
+      sx[i] = p.x; sy[i] = p.y; si[i] = cs.in_idx[c][first + i];
+    }
+    __syncthreads();
+    {
+      const int b = threadIdx.x * K5_LEAF;
+      const int l = max(0, min(K5_LEAF, len - b));
+      int k = 0;
+      for (int i = 0; i < l; ++i) {
+        const int2 p = make_int2(sx[b + i], sy[b + i]);
+        const int pid = si[b + i];
+        while (k >= 2 && turn(sgn, make_int2(sx[b + k - 2], sy[b + k - 2]),
+                              make_int2(sx[b + k - 1], sy[b + k - 1]), p) <= 0)
+          --k;
+        sx[b + k] = p.x; sy[b + k] = p.y; si[b + k] = pid;
+        ++k;
+      }
+      s_cnt[threadIdx.x] = k;
+    }
+    __syncthreads();
+    const int nleaf = (len + K5_LEAF - 1) / K5_LEAF;
+    for (int step = 1; step < nleaf; step <<= 1) {
+      const int npair = (nleaf + 2 * step - 1) / (2 * step);
+      for (int p = wid; p < npair; p += K5_WARPS) {
+        const int la = 2 * p * step, lb = la + step;
+        if (lb >= nleaf) continue;
+        const int aBase = la * K5_LEAF, bBase = lb * K5_LEAF;
+        const int alpha = s_cnt[la], beta = s_cnt[lb];
+        SmemChain A{sx + aBase, sy + aBase}, B{sx + bBase, sy + bBase};
+        int is, js;
+        bridge(A, alpha, B, beta, sgn, is, js);
+        const int dst = aBase + is + 1, src = bBase + js, n2 = beta - js;
+        for (int o = 0; o < n2; o += 32) {
+          const int q = o + lane;
+          int vx = 0, vy = 0, vi = 0;
+          if (q < n2) { vx = sx[src + q]; vy = sy[src + q]; vi = si[src + q]; }
+          __syncwarp();
+          if (q < n2) { sx[dst + q] = vx; sy[dst + q] = vy; si[dst + q] = vi; }
+          __syncwarp();
+        }
+        if (lane == 0) s_cnt[la] = is + 1 + n2;
+      }
+      __syncthreads();
+    }
+    const int hc = s_cnt[0];
+    const u32 out0 = cs.slot0[c] + first;
+    for (int i = threadIdx.x; i < hc; i += K5_BLOCK) {
+      h0_xy[out0 + i] = make_int2(sx[i], sy[i]);
+      h0_idx[out0 + i] = si[i];
+    }
+    if (threadIdx.x == 0) cnt0[cs.slot0[c] / K5_CHUNK + local] = (u32)hc;
+    __syncthreads();
+  }
+
+  // ---------------- phase B: merge chunk chains across the grid
+  int2* cur_xy = h0_xy; int* cur_idx = h0_idx; u32* cur_cnt = cnt0;
+  int2* nxt_xy = h1_xy; int* nxt_idx = h1_idx; u32* nxt_cnt = cnt1;
+  const u32 maxchunks = max(cs.nchunk[0], cs.nchunk[1]);
+  const int gw = blockIdx.x * K5_WARPS + wid, nw = gridDim.x * K5_WARPS;
+  for (u32 step = 1; step < maxchunks; step <<= 1) {
+    if (!grid_barrier(plan, spin)) return;
+    // B1: one warp per pair of nodes (or a lone node carried over).
+    const u32 np0 = (cs.nchunk[0] + 2 * step - 1) / (2 * step);
+    const u32 np1 = (cs.nchunk[1] + 2 * step - 1) / (2 * step);
+    for (u32 job = gw; job < np0 + np1; job += nw) {
+      const int c = job < np0 ? 0 : 1;
+      const u32 p = c == 0 ? job : job - np0;
+      const int sgn = c == 0 ? 1 : -1;
+      const u32 ca = 2 * p * step, cb = ca + step;
+      const u32 gca = cs.slot0[c] / K5_CHUNK + ca;
+      const int alpha = (int)__ldcg(&cur_cnt[gca]);
+      int is = alpha - 1, js = 0, beta = 0;
+      if (cb < cs.nchunk[c]) {
+        const u32 gcb = cs.slot0[c] / K5_CHUNK + cb;
+        beta = (int)__ldcg(&cur_cnt[gcb]);
+        GlobalChain A{cur_xy + (size_t)gca * K5_CHUNK}, B{cur_xy + (size_t)gcb * K5_CHUNK};
+        bridge(A, alpha, B, beta, sgn, is, js);
+      }
+      if (lane == 0) {
+        jobs[job] = make_int4(is, js, beta, 0);
+        nxt_cnt[gca] = (u32)(is + 1 + (beta - js));
+      }
+    }
+    if (!grid_barrier(plan, spin)) return;
+    // B2: gather every merged node into the other buffer.
+    const u32 span = 2 * step * K5_CHUNK;
+    const u32 total_slots = (cs.nchunk[0] + cs.nchunk[1]) * K5_CHUNK;
+    for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < total_slots; q += gridDim.x * K5_BLOCK) {
+      const int c = q < cs.slot0[1] ? 0 : 1;
+      const u32 rel = q - cs.slot0[c];
+      const u32 p = rel / span, o = rel % span;
+      const u32 job = c == 0 ? p : np0 + p;
+      const int4 jd = __ldcg(&jobs[job]);
+      const u32 merged = (u32)(jd.x + 1 + (jd.z - jd.y));
+      if (o >= merged) continue;
+      const u32 abase = cs.slot0[c] + p * span;
+      u32 src;
+      if (o <= (u32)jd.x) src = abase + o;
+      else src = abase + step * K5_CHUNK + (u32)jd.y + (o - (u32)jd.x - 1);
+      nxt_xy[q] = __ldcg(&cur_xy[src]);
+      nxt_idx[q] = __ldcg(&cur_idx[src]);
+    }
+    int2* t0 = cur_xy; cur_xy = nxt_xy; nxt_xy = t0;
+    int* t1 = cur_idx; cur_idx = nxt_idx; nxt_idx = t1;
+    u32* t2 = cur_cnt; cur_cnt = nxt_cnt; nxt_cnt = t2;
+  }
+  if (!grid_barrier(plan, spin)) return;
+
+  // ---------------- output: lower chain, then the upper chain reversed
+  const u32 hl = __ldcg(&cur_cnt[0]);
+  const u32 hu = __ldcg(&cur_cnt[cs.slot0[1] / K5_CHUNK]);
+  const long long h = (long long)hl + (long long)hu - 2;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    plan->h = (u32)h; plan->h_lo = hl; plan->h_up = hu;
+    if (h > cap) flag_error(plan, ERR_CAPACITY);
+  }
+  if (h > cap) return;
+  for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < (u32)h; q += gridDim.x * K5_BLOCK) {
+    int v;
+    if (q < hl) v = __ldcg(&cur_idx[q]);
+    else v = __ldcg(&cur_idx[cs.slot0[1] + (hu - 2) - (q - hl)]);
+    out[q] = v;
+  }
+}
+
+}  // namespace
+
+int k5_chunk() { return K5_CHUNK; }
+size_t k5_dyn_smem() { return (size_t)K5_CHUNK * 3 * sizeof(int); }
+
+cudaError_t k5_configure(int* max_blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k5_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)k5_dyn_smem());
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k5_final, K5_BLOCK,
+                                                       k5_dyn_smem());
+}
+
+cudaError_t launch_k5(const int2* lo_xy, const int* lo_idx, const int2* up_xy, const int* up_idx,
+                      Plan* plan, int2* h0_xy, int* h0_idx, int2* h1_xy, int* h1_idx, u32* cnt0,
+                      u32* cnt1, int4* jobs, int* out, long long cap, int grid, cudaStream_t st) {
+  void* args[] = {(void*)&lo_xy, (void*)&lo_idx, (void*)&up_xy, (void*)&up_idx, (void*)&plan,
+                  (void*)&h0_xy, (void*)&h0_idx, (void*)&h1_xy, (void*)&h1_idx, (void*)&cnt0,
+                  (void*)&cnt1, (void*)&jobs, (void*)&out, (void*)&cap};
+  return cudaLaunchCooperativeKernel((const void*)k5_final, dim3(grid), dim3(K5_BLOCK), args,
+                                     k5_dyn_smem(), st);
+}
+
+}  // namespace gbh

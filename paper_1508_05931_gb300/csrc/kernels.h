@@ -1,0 +1,58 @@
+// Host-side launchers of the pipeline kernels (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hull_internal.cuh"
+
+namespace gbh {
+
+struct PlanPatch {
+  int new_call;        // bump the epoch, clear the error word, set spin_limit
+  int zero_hist;
+  int zero_counters;
+  int set_s, set_npasses, set_ncorner, set_r;
+  u32 spin_limit, s, npasses;
+  int ncorner;
+  u32 r_lo, r_up;
+};
+
+cudaError_t launch_plan_patch(Plan* plan, const PlanPatch& p, cudaStream_t st);
+cudaError_t launch_hist(const u64* keys, Plan* plan, int grid, cudaStream_t st);
+cudaError_t launch_iota(int* out, u32 m, cudaStream_t st);
+cudaError_t launch_gather_labels(const int* pos, const int* labels, const u32* count,
+                                 u32 skip_first, int* out, u32 cap, cudaStream_t st);
+
+// Resident blocks per SM of the persistent kernels (dynamic tile ids).
+cudaError_t k2_occupancy(int* blocks);
+cudaError_t k3_occupancy(int* blocks);
+cudaError_t k4_occupancy(int* blocks);
+
+int k1_grid(u32 n, int num_sms);
+cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials,
+                      int grid, cudaStream_t st);
+
+int k2_tile();
+cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
+                      int grid, cudaStream_t st);
+
+int k3_tile();
+size_t k3_dyn_smem();
+cudaError_t k3_configure();
+cudaError_t launch_k3(const u64* kin, const u32* iin, u64* kout, u32* iout, Plan* plan,
+                      u64* status, u32 pass, int grid, cudaStream_t st);
+
+int k4_tile();
+size_t k4_status_bytes();
+cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib, Plan* plan,
+                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
+                      cudaStream_t st);
+
+int k5_chunk();
+size_t k5_dyn_smem();
+cudaError_t k5_configure(int* max_blocks_per_sm);
+cudaError_t launch_k5(const int2* lo_xy, const int* lo_idx, const int2* up_xy, const int* up_idx,
+                      Plan* plan, int2* h0_xy, int* h0_idx, int2* h1_xy, int* h1_idx, u32* cnt0,
+                      u32* cnt1, int4* jobs, int* out, long long cap, int grid, cudaStream_t st);
+
+}  // namespace gbh

@@ -1,0 +1,297 @@
+"""Python binding of the gbhull C ABI (include/gbhull.h).
+
+Argument marshalling only: every step of the hull runs in the CUDA library
+``_lib/libgbhull.so``.  Importing this module fails loudly when that
+library is missing; there is no CPU fallback.  PyTorch supplies device
+memory and streams (tensor data pointers and ``torch.cuda`` streams are
+passed straight through).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB_PATH
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("libgbhull.so is not built (%s); run paper_1508_05931_gb300.build."
+                      "build_library() or __graft_entry__.build()" % _LIB_PATH)
+_lib = ctypes.CDLL(_LIB_PATH)
+
+HULL_OK, HULL_EINVAL, HULL_ERANGE, HULL_ENOMEM, HULL_ECAPACITY, HULL_ETIMEOUT, HULL_ECUDA, \
+    HULL_EINTERNAL = range(8)
+COORD_LIMIT = 1 << 29
+MAX_POINTS = (1 << 30) - 1
+
+
+class hull_config(ctypes.Structure):
+    _fields_ = [("proposal", ctypes.c_int), ("collect_stats", ctypes.c_int),
+                ("spin_limit", ctypes.c_uint32), ("reserved", ctypes.c_int)]
+
+
+class hull_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("s", ctypes.c_int64), ("r_lower", ctypes.c_int64),
+                ("r_upper", ctypes.c_int64), ("h", ctypes.c_int64), ("ext", ctypes.c_int32 * 4),
+                ("ncorner", ctypes.c_int32), ("learned_used", ctypes.c_int32)]
+
+
+NUM_STAGES = 12
+STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8)] + ["regions", "final"]
+
+
+class hull_profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("sort_passes", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("survivors", ctypes.c_int64), ("second_round", ctypes.c_int64),
+                ("ms", ctypes.c_double * NUM_STAGES)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_sig = {
+    "hull_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "hull_create": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(hull_config)], ctypes.c_int),
+    "hull_destroy": ([_P], None),
+    "hull_compute": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
+    "hull_compute_host": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
+    "hull_compute_batched": ([_P, _P, _P, ctypes.c_int32, _P, _I64, _P, _P], ctypes.c_int),
+    "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
+    "hull_set_profiling": ([_P, ctypes.c_int], ctypes.c_int),
+    "hull_get_profile": ([_P, ctypes.POINTER(hull_profile)], ctypes.c_int),
+    "hull_stage_extremes": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "hull_stage_filter": ([_P, _P, _I64, _P, _PI64, _P], ctypes.c_int),
+    "hull_stage_sort": ([_P, _P, _P, _I64, _P], ctypes.c_int),
+    "hull_stage_second_round": ([_P, _P, _P, _I64, _P, _PI64, _P, _PI64, _P], ctypes.c_int),
+    "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_sig)
+
+
+class HullError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where, hull_status_string(code), code))
+
+
+def hull_status_string(code: int) -> str:
+    return _lib.hull_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != HULL_OK:
+        raise HullError(code, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _as_points(pts, device):
+    torch = _torch()
+    if not isinstance(pts, torch.Tensor):
+        pts = torch.as_tensor(np.ascontiguousarray(np.asarray(pts, dtype=np.int32).reshape(-1, 2)))
+    if pts.dtype != torch.int32 or pts.dim() != 2 or pts.shape[1] != 2:
+        raise ValueError("points must be an int32 tensor of shape (n, 2)")
+    if not pts.is_cuda:
+        pts = pts.to(device)
+    return pts.contiguous()
+
+
+class Context:
+    """One hull_ctx: owns the device workspace for one GPU."""
+
+    def __init__(self, device: int = 0, proposal: int = 0, collect_stats: bool = False,
+                 spin_limit: int = 0):
+        self.device = int(device)
+        cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), 0)
+        h = ctypes.c_void_p()
+        _check(_lib.hull_create(ctypes.byref(h), self.device, ctypes.byref(cfg)), "hull_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.hull_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ hull
+    def compute(self, pts, out=None, stream=None):
+        """CCW hull vertex indices (int32 device tensor) of an (n, 2) int32
+        point tensor; see hull_compute."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        pts = _as_points(pts, dev)
+        n = pts.shape[0]
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cnt = ctypes.c_int64()
+        _check(_lib.hull_compute(self._h, _ptr(pts), n, _ptr(out), out.numel(), ctypes.byref(cnt),
+                                 _stream_handle(stream)), "hull_compute")
+        return out[: cnt.value]
+
+    def compute_raw(self, pts, out, stream=None) -> int:
+        """hull_compute on preallocated tensors; returns the vertex count."""
+        cnt = ctypes.c_int64()
+        _check(_lib.hull_compute(self._h, _ptr(pts), pts.shape[0], _ptr(out), out.numel(),
+                                 ctypes.byref(cnt), _stream_handle(stream)), "hull_compute")
+        return cnt.value
+
+    def compute_host(self, pts, out=None, stream=None) -> np.ndarray:
+        """Hull of host points (numpy or CPU tensor, ideally pinned) into a
+        host array; see hull_compute_host."""
+        torch = _torch()
+        if isinstance(pts, torch.Tensor):
+            src = pts.contiguous()
+            n = src.shape[0]
+            sp = _ptr(src)
+        else:
+            src = np.ascontiguousarray(np.asarray(pts, dtype=np.int32).reshape(-1, 2))
+            n = src.shape[0]
+            sp = src.ctypes.data_as(ctypes.c_void_p)
+        if out is None:
+            out = np.empty(max(n, 1), dtype=np.int32)
+        op = _ptr(out) if isinstance(out, torch.Tensor) else out.ctypes.data_as(ctypes.c_void_p)
+        cnt = ctypes.c_int64()
+        _check(_lib.hull_compute_host(self._h, sp, n, op, out.shape[0], ctypes.byref(cnt),
+                                      _stream_handle(stream)), "hull_compute_host")
+        return out[: cnt.value]
+
+    def compute_batched(self, pts, offsets, out=None, stream=None):
+        """B hulls; offsets int64 (B+1,).  Returns (indices, out_offsets)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        pts = _as_points(pts, dev)
+        offsets = torch.as_tensor(offsets, dtype=torch.int64).to(dev).contiguous()
+        b = offsets.numel() - 1
+        if out is None:
+            out = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=dev)
+        oo = torch.empty(b + 1, dtype=torch.int64, device=dev)
+        _check(_lib.hull_compute_batched(self._h, _ptr(pts), _ptr(offsets), b, _ptr(out), out.numel(),
+                                         _ptr(oo), _stream_handle(stream)), "hull_compute_batched")
+        return out, oo
+
+    def last_stats(self) -> dict:
+        st = hull_stats()
+        _check(_lib.hull_last_stats(self._h, ctypes.byref(st)), "hull_last_stats")
+        return {"n": st.n, "s": st.s, "r_lower": st.r_lower, "r_upper": st.r_upper, "h": st.h,
+                "ext": list(st.ext), "ncorner": st.ncorner, "learned_used": st.learned_used}
+
+    def set_profiling(self, enable: bool = True):
+        _check(_lib.hull_set_profiling(self._h, int(bool(enable))), "hull_set_profiling")
+
+    def profile(self) -> dict:
+        p = hull_profile()
+        _check(_lib.hull_get_profile(self._h, ctypes.byref(p)), "hull_get_profile")
+        return {"calls": p.calls, "sort_passes": p.sort_passes, "points": p.points,
+                "survivors": p.survivors, "second_round": p.second_round,
+                "ms": {STAGE_NAMES[k]: p.ms[k] for k in range(NUM_STAGES)}}
+
+    # ------------------------------------------------------------ stages
+    def stage_extremes(self, pts, stream=None) -> np.ndarray:
+        torch = _torch()
+        pts = _as_points(pts, torch.device("cuda", self.device))
+        ext = np.zeros(4, dtype=np.int32)
+        _check(_lib.hull_stage_extremes(self._h, _ptr(pts), pts.shape[0],
+                                        ext.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)),
+               "hull_stage_extremes")
+        return ext
+
+    def stage_filter(self, pts, stream=None):
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        pts = _as_points(pts, dev)
+        keep = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=dev)
+        s = ctypes.c_int64()
+        _check(_lib.hull_stage_filter(self._h, _ptr(pts), pts.shape[0], _ptr(keep), ctypes.byref(s),
+                                      _stream_handle(stream)), "hull_stage_filter")
+        return keep[: s.value]
+
+    def stage_sort(self, keys, vals, stream=None):
+        """Sorts (uint64 keys stored in an int64 tensor, int32 values) in place."""
+        torch = _torch()
+        assert keys.dtype == torch.int64 and vals.dtype == torch.int32 and keys.is_cuda
+        _check(_lib.hull_stage_sort(self._h, _ptr(keys), _ptr(vals), keys.numel(),
+                                    _stream_handle(stream)), "hull_stage_sort")
+        return keys, vals
+
+    def stage_second_round(self, xy_sorted, labels, stream=None):
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(xy_sorted, dev)
+        lab = torch.as_tensor(labels, dtype=torch.int32).to(dev).contiguous()
+        m = xy.shape[0]
+        lo = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        up = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        nl, nu = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hull_stage_second_round(self._h, _ptr(xy), _ptr(lab), m, _ptr(lo), ctypes.byref(nl),
+                                            _ptr(up), ctypes.byref(nu), _stream_handle(stream)),
+               "hull_stage_second_round")
+        return lo[: nl.value], up[: nu.value]
+
+    def stage_chain(self, xy_sorted, stream=None):
+        """Returns (lower chain positions, upper chain positions), both from
+        the first to the last point."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(xy_sorted, dev)
+        m = xy.shape[0]
+        out = torch.empty(2 * m, dtype=torch.int32, device=dev)
+        hl, hu = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hull_stage_chain(self._h, _ptr(xy), m, _ptr(out), out.numel(), ctypes.byref(hl),
+                                     ctypes.byref(hu), _stream_handle(stream)), "hull_stage_chain")
+        o = out.cpu().numpy()
+        lower = o[: hl.value]
+        inner = o[hl.value: hl.value + hu.value - 2][::-1]
+        upper = np.concatenate([[0], inner, [m - 1]]).astype(np.int32)
+        return lower.copy(), upper
+
+
+# Module-level C-ABI names (thin aliases).
+hull_create = _lib.hull_create
+hull_destroy = _lib.hull_destroy
+hull_compute = _lib.hull_compute
+hull_compute_host = _lib.hull_compute_host
+hull_compute_batched = _lib.hull_compute_batched
+hull_last_stats = _lib.hull_last_stats
+hull_set_profiling = _lib.hull_set_profiling
+hull_get_profile = _lib.hull_get_profile
+hull_stage_extremes = _lib.hull_stage_extremes
+hull_stage_filter = _lib.hull_stage_filter
+hull_stage_sort = _lib.hull_stage_sort
+hull_stage_second_round = _lib.hull_stage_second_round
+hull_stage_chain = _lib.hull_stage_chain

@@ -1,0 +1,175 @@
+"""End-to-end parity: hull_compute (all stages on the GPU) against the
+oracle's hull by definition, bit-exact, on the paper-shaped workloads at
+reduced and full size, degenerate inputs and the error paths."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_05931_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(hull_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hull_lib.Context(0, collect_stats=True)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_hull(ctx, pts):
+    return ctx.compute(dev(pts)).cpu().numpy()
+
+
+def test_degenerate_inputs(ctx):
+    assert gpu_hull(ctx, np.zeros((0, 2), np.int32)).tolist() == []
+    assert gpu_hull(ctx, [[5, 7]]).tolist() == [0]
+    assert gpu_hull(ctx, [[5, 7], [1, 2]]).tolist() == [1, 0]
+    assert gpu_hull(ctx, [[5, 7], [5, 7]]).tolist() == [0]
+    assert gpu_hull(ctx, [[3, 3]] * 9000).tolist() == [0]
+    col = np.array([[i * 2, i * 3] for i in np.random.default_rng(0).integers(-500, 500, 10000)], np.int32)
+    assert gpu_hull(ctx, col).tolist() == oracle.hull(col).tolist()
+    g = W.filled_grid(300, 200, -7, 9)
+    assert gpu_hull(ctx, g).tolist() == oracle.hull(g).tolist()
+    par = W.parabola_lattice(1 << 14)
+    assert gpu_hull(ctx, par).tolist() == list(range(len(par)))
+    lim = 1 << 29
+    edge = np.array([[lim, -lim], [-lim, lim], [0, 1], [lim, lim], [-lim, -lim]], np.int32)
+    assert gpu_hull(ctx, edge).tolist() == oracle.hull(edge).tolist()
+
+
+def test_random_small_sets(ctx):
+    rng = np.random.default_rng(42)
+    for t in range(300):
+        n = int(rng.integers(1, 3000))
+        span = int(rng.choice([1, 2, 5, 100, 1 << 20, 1 << 29]))
+        pts = rng.integers(-span, span + 1, size=(n, 2)).astype(np.int32)
+        assert gpu_hull(ctx, pts).tolist() == oracle.hull(pts).tolist(), (t, n, span)
+
+
+@pytest.mark.parametrize("n", [4095, 4096, 4097, 65536, 65537, 1_000_003])
+@pytest.mark.parametrize("gen", ["square", "disk", "ring", "gauss", "clusters", "ellipse"])
+def test_ragged_sizes(ctx, n, gen):
+    f = {"square": lambda: W.uniform_square(n, 1 << 29, n),
+         "disk": lambda: W.uniform_disk(n, 2.0 ** 29, n),
+         "ring": lambda: W.near_circle(n, 2.0 ** 20, n),
+         "gauss": lambda: W.gaussian(n, 2.0 ** 26, n),
+         "clusters": lambda: W.gaussian_clusters(n, n),
+         "ellipse": lambda: W.elliptic_disk(n, n)}[gen]
+    pts = f()
+    assert gpu_hull(ctx, pts).tolist() == oracle.hull(pts).tolist()
+
+
+def test_small_square_config(ctx):
+    pts = W.small_square()
+    h = gpu_hull(ctx, pts)
+    assert h.tolist() == oracle.hull(pts).tolist()
+    st = ctx.last_stats()
+    stages = oracle.gscan_stages(pts)
+    assert st["s"] == len(stages["keep"])
+    assert st["r_lower"] == len(stages["lower"]) and st["r_upper"] == len(stages["upper"])
+    assert st["ext"] == stages["ext"].tolist()
+
+
+@pytest.mark.parametrize("name", ["paper_square", "paper_disk", "adversarial_ring"])
+def test_full_size_configs(ctx, name):
+    pts = getattr(W, name)()
+    t = dev(pts)
+    out = torch.empty(len(pts), dtype=torch.int32, device="cuda")
+    h = ctx.compute(t, out=out).cpu().numpy()
+    assert h.tolist() == oracle.hull(pts).tolist()
+
+
+def test_determinism_repeated(ctx):
+    pts = W.uniform_disk(2_000_000, 2.0 ** 29, 77)
+    t = dev(pts)
+    ref = ctx.compute(t).cpu().numpy()
+    for _ in range(10):
+        assert np.array_equal(ctx.compute(t).cpu().numpy(), ref)
+
+
+def test_unaligned_input_view(ctx):
+    pts = W.uniform_square(300001, 1 << 29, 5)
+    view = dev(pts)[1:]
+    assert view.data_ptr() % 16 == 8
+    assert ctx.compute(view).cpu().numpy().tolist() == oracle.hull(pts[1:]).tolist()
+
+
+def test_host_entry_point(ctx):
+    pts = W.uniform_disk(500_000, 2.0 ** 29, 8)
+    pinned = torch.as_tensor(pts).pin_memory()
+    h = ctx.compute_host(pinned)
+    assert h.tolist() == oracle.hull(pts).tolist()
+    h2 = ctx.compute_host(pts)
+    assert h2.tolist() == oracle.hull(pts).tolist()
+
+
+def test_range_error(ctx, hull_lib):
+    lim = 1 << 29
+    bad = np.array([[0, 0], [lim + 1, 0], [3, 4]], np.int32)
+    with pytest.raises(hull_lib.HullError) as e:
+        ctx.compute(dev(bad))
+    assert e.value.code == hull_lib.HULL_ERANGE
+    bad2 = np.array([[0, -lim - 1], [1, 1]], np.int32)
+    with pytest.raises(hull_lib.HullError):
+        ctx.compute(dev(bad2))
+    # the context stays usable
+    ok = W.uniform_square(1000, 100, 1)
+    assert gpu_hull(ctx, ok).tolist() == oracle.hull(ok).tolist()
+
+
+def test_capacity_error_reports_count(ctx, hull_lib):
+    pts = W.uniform_disk(10000, 1e6, 3)
+    ref = oracle.hull(pts)
+    t = dev(pts)
+    out = torch.full((len(ref) - 1,), -5, dtype=torch.int32, device="cuda")
+    cnt = ctypes.c_int64()
+    rc = hull_lib._lib.hull_compute(ctx.handle, ctypes.c_void_p(t.data_ptr()), len(pts),
+                                    ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(cnt),
+                                    None)
+    torch.cuda.synchronize()
+    assert rc == hull_lib.HULL_ECAPACITY and cnt.value == len(ref)
+    assert bool((out == -5).all())
+
+
+def test_invalid_arguments(ctx, hull_lib):
+    cnt = ctypes.c_int64()
+    L = hull_lib._lib
+    assert L.hull_compute(ctx.handle, None, 10, None, 0, ctypes.byref(cnt), None) == hull_lib.HULL_EINVAL
+    assert L.hull_compute(ctx.handle, None, -1, None, 0, ctypes.byref(cnt), None) == hull_lib.HULL_EINVAL
+    t = dev(np.zeros((4, 2), np.int32))
+    assert L.hull_compute(ctx.handle, ctypes.c_void_p(t.data_ptr() + 4), 2, None, 0, ctypes.byref(cnt),
+                          None) == hull_lib.HULL_EINVAL
+    assert L.hull_compute(ctx.handle, ctypes.c_void_p(t.data_ptr()), 1 << 30, None, 0,
+                          ctypes.byref(cnt), None) == hull_lib.HULL_EINVAL
+
+
+def test_forced_wait_timeouts_recover(hull_lib):
+    """Fault injection from the host: a spin limit of one iteration makes any
+    device wait that is not satisfied at once give up; the call must report
+    HULL_ETIMEOUT (or succeed exactly) and never hang or trap, and a context
+    with the normal limit must keep working afterwards."""
+    pts = W.uniform_square(4_000_000, 1 << 29, 9)
+    ref = oracle.hull(pts)
+    t = dev(pts)
+    saw_timeout = False
+    with hull_lib.Context(0, spin_limit=1) as c:
+        for _ in range(3):
+            try:
+                h = c.compute(t).cpu().numpy()
+                assert h.tolist() == ref.tolist()
+            except hull_lib.HullError as e:
+                assert e.code == hull_lib.HULL_ETIMEOUT
+                saw_timeout = True
+    with hull_lib.Context(0) as c:
+        assert c.compute(t).cpu().numpy().tolist() == ref.tolist()
+    print("timeout observed:", saw_timeout)
