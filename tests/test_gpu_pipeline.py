@@ -23,6 +23,8 @@ def ctx(hull_lib):
 
 
 def dev(a):
+    if not isinstance(a, np.ndarray):
+        a = np.asarray(a, dtype=np.int32).reshape(-1, 2)
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
 

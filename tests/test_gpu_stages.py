@@ -20,6 +20,8 @@ def ctx(hull_lib):
 
 
 def dev(a):
+    if not isinstance(a, np.ndarray):
+        a = np.asarray(a, dtype=np.int32).reshape(-1, 2)
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
 
@@ -136,8 +138,8 @@ def test_chain_parity(ctx, m, gen):
     if gen == "random":
         u = np.unique(rand_pts(rng, m * 2, 1 << 29), axis=0)[:m]
     elif gen == "convex":
-        t = np.sort(rng.choice(np.arange(-(1 << 14), 1 << 14), size=m, replace=False))
-        u = np.stack([t, t * t // 4 - (1 << 26)], axis=1).astype(np.int32)
+        t = np.sort(rng.choice(np.arange(-(1 << 16), 1 << 16), size=m, replace=False)).astype(np.int64)
+        u = np.stack([t, t * t // 8 - (1 << 28)], axis=1).astype(np.int32)
     else:
         u = np.unique(rand_pts(rng, m * 4, 40), axis=0)[:m]
     if len(u) < 2:
