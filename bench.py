@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--n", type=int, default=20_000_000, help="points per hull")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one untimed hull per input set, for a profiler to capture; prints no JSON")
     return ap.parse_args()
 
 
@@ -197,6 +199,12 @@ def main():
     out = torch.empty(args.n, dtype=torch.int32, device="cuda")
     ctx = hull.Context(local)
     stream = torch.cuda.current_stream()
+    if args.profile:
+        for t in dev_sets:
+            ctx.compute_raw(t, out, stream)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
 
     def step():
         for t in dev_sets:
