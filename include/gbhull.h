@@ -122,6 +122,31 @@ typedef struct {
 hull_status hull_set_profiling(hull_ctx *ctx, int enable);
 hull_status hull_get_profile(const hull_ctx *ctx, hull_profile *out);
 
+/* ---- allocation-free entry point (no counterpart in the paper) ----
+ * For callers that must not allocate device memory: code that runs where
+ * cudaMalloc is forbidden or unsafe (a host callback, a memory-pool hook, a
+ * plug-in whose host application owns the device memory budget) or that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * imply.  Same computation and result as hull_compute, but it needs no
+ * context and allocates nothing (no cudaMalloc, cudaFree, pinned buffer or
+ * allocating library call): its scratch memory is one file-scope device
+ * array of HULL_NOALLOC_SCRATCH_BYTES that every GPU which loads this
+ * library holds until the process exits.
+ *   - n must be <= HULL_NOALLOC_MAX_POINTS, else HULL_EINVAL;
+ *   - runs on the current CUDA device; d_xy, d_out and h_count as in
+ *     hull_compute; synchronises `stream` before returning;
+ *   - all calls on a device share the array, which keeps the last call's
+ *     contents; each call clears what must start at zero before using it;
+ *     calls whose GPU work overlaps (other streams, other host threads on
+ *     the same device) race on the array and must be serialised;
+ *   - the first call on each device does a one-time set-up with that device
+ *     current (it resolves the array's device address and sets kernel
+ *     attributes); make that first call before any stream capture. */
+#define HULL_NOALLOC_MAX_POINTS 65536
+#define HULL_NOALLOC_SCRATCH_BYTES (6u << 20)
+hull_status hull_compute_noalloc(const int32_t *d_xy, int64_t n, int32_t *d_out, int64_t cap,
+                                 int64_t *h_count, void *stream);
+
 /* Short English text for a status code (static storage). */
 const char *hull_status_string(hull_status s);
 

@@ -58,6 +58,7 @@ _sig = {
     "hull_compute": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_compute_host": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_compute_batched": ([_P, _P, _P, ctypes.c_int32, _P, _I64, _P, _P], ctypes.c_int),
+    "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
     "hull_set_profiling": ([_P, ctypes.c_int], ctypes.c_int),
     "hull_get_profile": ([_P, ctypes.POINTER(hull_profile)], ctypes.c_int),
@@ -281,12 +282,26 @@ class Context:
         return lower.copy(), upper
 
 
+NOALLOC_MAX_POINTS = 65536
+
+
+def compute_noalloc(pts, out, stream=None) -> int:
+    """hull_compute_noalloc on the current device: pts an (n, 2) int32 CUDA
+    tensor with n <= NOALLOC_MAX_POINTS, out an int32 CUDA tensor; returns
+    the vertex count (indices in out[:count]).  Allocates nothing."""
+    cnt = ctypes.c_int64()
+    _check(_lib.hull_compute_noalloc(_ptr(pts), pts.shape[0], _ptr(out), out.numel(), ctypes.byref(cnt),
+                                     _stream_handle(stream)), "hull_compute_noalloc")
+    return cnt.value
+
+
 # Module-level C-ABI names (thin aliases).
 hull_create = _lib.hull_create
 hull_destroy = _lib.hull_destroy
 hull_compute = _lib.hull_compute
 hull_compute_host = _lib.hull_compute_host
 hull_compute_batched = _lib.hull_compute_batched
+hull_compute_noalloc = _lib.hull_compute_noalloc
 hull_last_stats = _lib.hull_last_stats
 hull_set_profiling = _lib.hull_set_profiling
 hull_get_profile = _lib.hull_get_profile
