@@ -35,6 +35,7 @@ struct Workspace {
   u32* cnt[2] = {nullptr, nullptr};
   int4* jobs = nullptr;
   int* aux = nullptr;          // int32[cap]: labels for stage entry points
+  unsigned char* mask = nullptr;  // first-round keep bits, one byte per 8 points
 };
 
 struct HostStage {
@@ -113,6 +114,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_c0 = take(nchunks * 4), o_c1 = take(nchunks * 4);
   const size_t o_jobs = take(nchunks * 16);
   const size_t o_aux = take(cap * 4);
+  const size_t o_mask = take(cap / 8 + 4096);
   const size_t total = off;
 
   cudaDeviceSynchronize();
@@ -144,6 +146,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.cnt[0] = reinterpret_cast<u32*>(b + o_c0); w.cnt[1] = reinterpret_cast<u32*>(b + o_c1);
   w.jobs = reinterpret_cast<int4*>(b + o_jobs);
   w.aux = reinterpret_cast<int*>(b + o_aux);
+  w.mask = reinterpret_cast<unsigned char*>(b + o_mask);
   return HULL_OK;
 }
 
@@ -203,7 +206,7 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
   if (e != cudaSuccess) return cuda_fail(e);
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, grid_for(c->occ_k2, c->num_sms, t2), st);
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2, c->num_sms, t2), st);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(c, 2, st);
   const size_t t3 = (n + k3_tile() - 1) / k3_tile();
@@ -215,7 +218,8 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
   }
   const size_t t4 = (n + k4_tile() - 1) / k4_tile();
   e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
-                w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, t4), st);
+                w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
+                grid_for(c->occ_k4, c->num_sms, t4), st);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(c, 3 + kMaxPasses, st);
   return HULL_OK;
@@ -422,7 +426,7 @@ hull_status hull_stage_filter(hull_ctx* c, const int32_t* d_xy, int64_t n, int32
                             k1_grid((u32)n, c->num_sms), st);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t2 = ((size_t)n + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, c->ws.keys[0], c->ws.idx[0], c->ws.st_filter,
+  e = launch_k2(d_xy, c->plan, c->ws.keys[0], c->ws.idx[0], c->ws.st_filter, c->ws.mask,
                 grid_for(c->occ_k2, c->num_sms, t2), st);
   if (e != cudaSuccess) return cuda_fail(e);
   r = finish(c, st);
@@ -489,7 +493,7 @@ hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int3
   e = launch_plan_patch(c->plan, p, st);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t = ((size_t)m + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, grid_for(c->occ_k2, c->num_sms, t), st);
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2, c->num_sms, t), st);
   if (e != cudaSuccess) return cuda_fail(e);
   PlanPatch q{};
   q.set_npasses = 1; q.npasses = 0;
@@ -497,7 +501,8 @@ hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int3
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t4 = ((size_t)m + k4_tile() - 1) / k4_tile();
   e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
-                w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, t4), st);
+                w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
+                grid_for(c->occ_k4, c->num_sms, t4), st);
   if (e != cudaSuccess) return cuda_fail(e);
   // The region lists hold list positions at [1, r]; map them to labels.
   e = launch_gather_labels(w.lo_idx, d_idx, &c->plan->r_lo, 1, d_lower, (u32)m, st);

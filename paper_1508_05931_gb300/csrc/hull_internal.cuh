@@ -43,7 +43,7 @@ enum CounterSlot : int {
   CTR_FILTER = 0,
   CTR_SORT0 = 1,                          // .. CTR_SORT0 + kMaxPasses - 1
   CTR_REGION = 1 + kMaxPasses,
-  CTR_FINAL_CHUNK = 2 + kMaxPasses,
+  CTR_REGION2 = 2 + kMaxPasses,
   CTR_FINAL_BAR = 3 + kMaxPasses,
   CTR_FINAL_BAR_GEN = 4 + kMaxPasses,
   kNumCounters = 16,
@@ -86,6 +86,16 @@ __device__ __forceinline__ u64 ld_acquire_u64(const u64* p) {
 }
 __device__ __forceinline__ void st_release_u64(u64* p, u64 v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Relaxed (gpu-scope) accesses for look-back words whose value is
+// self-contained (flag and count in one 64-bit word): no fence is needed.
+__device__ __forceinline__ u64 ld_relaxed_u64(const u64* p) {
+  u64 v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(u64* p, u64 v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ u32 ld_volatile_u32(const u32* p) {
   return *reinterpret_cast<const volatile u32*>(p);
@@ -138,7 +148,7 @@ __device__ __forceinline__ u32 warp_lookback_count(u64* status, u32 tile, u32 ep
     if (t >= 0) {
       u32 it = 0;
       for (;;) {
-        w = ld_acquire_u64(&status[t]);
+        w = ld_relaxed_u64(&status[t]);
         f = status_flag(w, epoch);
         if (f != 0) break;
         if (++it > spin_limit || aborted(plan)) { f = 0xFFu; break; }
@@ -158,6 +168,64 @@ __device__ __forceinline__ u32 warp_lookback_count(u64* status, u32 tile, u32 ep
     excl += c;
     if (incl_mask) break;
     base -= 32;
+  }
+  return excl;
+}
+
+// Block-wide decoupled look-back over a single count: thread i inspects
+// tile (tile - 1 - i - blockDim.x * w) in window w, so a round trip covers
+// blockDim.x predecessors.  Every thread of the block must call it; all get
+// the same exclusive prefix.  On a timeout (or another block's abort) sets
+// ERR_TIMEOUT and *failed.  `red` is shared scratch of >= blockDim.x / 32 + 2 words.
+__device__ __forceinline__ u32 block_lookback_count(const u64* status, u32 tile, u32 epoch,
+                                                    Plan* plan, u32 spin_limit, bool* failed,
+                                                    u32* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  u32 excl = 0;
+  long long base = (long long)tile - 1;
+  *failed = false;
+  while (base >= 0) {
+    const long long t = base - (long long)threadIdx.x;
+    u64 w = 0;
+    u32 f = 0;
+    bool bad = false;
+    if (t >= 0) {
+      u32 it = 0;
+      for (;;) {
+        w = ld_relaxed_u64(&status[t]);
+        f = status_flag(w, epoch);
+        if (f != 0) break;
+        if (++it > spin_limit || aborted(plan)) { bad = true; flag_error(plan, ERR_TIMEOUT); break; }
+        spin_pause(it);
+      }
+    }
+    // Nearest inclusive prefix: the lowest thread holding one.
+    const u32 incl = __ballot_sync(0xFFFFFFFFu, t >= 0 && f == ST_INCL);
+    if (threadIdx.x == 0) { red[nw] = 0xFFFFFFFFu; red[nw + 1] = 0u; }
+    __syncthreads();
+    if (lane == 0 && incl) atomicMin(&red[nw], (u32)(wid * 32 + __ffs(incl) - 1));
+    if (bad) red[nw + 1] = 1u;
+    __syncthreads();
+    const u32 stop = red[nw];
+    if (red[nw + 1]) {
+      if (threadIdx.x == 0) flag_error(plan, ERR_TIMEOUT);
+      *failed = true;
+      __syncthreads();
+      return 0;
+    }
+    u32 c = (t >= 0 && (u32)threadIdx.x <= stop) ? status_count(w) : 0u;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = c;
+    __syncthreads();
+    u32 sum = 0;
+    for (int q = 0; q < nw; ++q) sum += red[q];
+    excl += sum;
+    __syncthreads();
+    if (stop != 0xFFFFFFFFu) break;
+    base -= blockDim.x;
   }
   return excl;
 }

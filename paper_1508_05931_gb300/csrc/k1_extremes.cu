@@ -22,11 +22,15 @@ __device__ __forceinline__ u32 ord(int v) { return (u32)v ^ 0x80000000u; }
 struct Best {
   u64 k[4];
   u32 i[4];
+  // Current x of P_minx / P_maxx and y of P_miny / P_maxy candidates: a
+  // point strictly inside this box cannot change any extreme.
+  int bx0, bx1, by0, by1;
 };
 
 __device__ __forceinline__ void best_init(Best& b) {
   #pragma unroll
   for (int j = 0; j < 4; ++j) { b.k[j] = ~0ull; b.i[j] = 0xFFFFFFFFu; }
+  b.bx0 = 0x7FFFFFFF; b.bx1 = (int)0x80000000; b.by0 = 0x7FFFFFFF; b.by1 = (int)0x80000000;
 }
 
 __device__ __forceinline__ bool lt_ki(u64 ka, u32 ia, u64 kb, u32 ib) {
@@ -36,13 +40,25 @@ __device__ __forceinline__ bool lt_ki(u64 ka, u32 ia, u64 kb, u32 ib) {
 // Points reach a thread in increasing index order, so a strict key
 // comparison keeps the smallest index among equal keys.
 __device__ __forceinline__ void consider(Best& b, int x, int y, u32 idx) {
+  if (x > b.bx0 && x < b.bx1 && y > b.by0 && y < b.by1) return;
   u32 ox = ord(x), oy = ord(y);
   u64 kxy = ((u64)ox << 32) | oy;
   u64 kyx = ((u64)oy << 32) | ox;
-  if (kxy < b.k[0]) { b.k[0] = kxy; b.i[0] = idx; }
-  if (~kxy < b.k[1]) { b.k[1] = ~kxy; b.i[1] = idx; }
-  if (kyx < b.k[2]) { b.k[2] = kyx; b.i[2] = idx; }
-  if (~kyx < b.k[3]) { b.k[3] = ~kyx; b.i[3] = idx; }
+  if (kxy < b.k[0]) { b.k[0] = kxy; b.i[0] = idx; b.bx0 = min(b.bx0, x); }
+  if (~kxy < b.k[1]) { b.k[1] = ~kxy; b.i[1] = idx; b.bx1 = max(b.bx1, x); }
+  if (kyx < b.k[2]) { b.k[2] = kyx; b.i[2] = idx; b.by0 = min(b.by0, y); }
+  if (~kyx < b.k[3]) { b.k[3] = ~kyx; b.i[3] = idx; b.by1 = max(b.by1, y); }
+}
+
+// Two points at once: a single warp vote skips both when every lane's
+// points lie strictly inside that lane's current box (the common case).
+__device__ __forceinline__ void consider2(Best& b, int4 v, u32 idx) {
+  const bool out = !(v.x > b.bx0 && v.x < b.bx1 && v.y > b.by0 && v.y < b.by1) ||
+                   !(v.z > b.bx0 && v.z < b.bx1 && v.w > b.by0 && v.w < b.by1);
+  if (__any_sync(__activemask(), out)) {
+    consider(b, v.x, v.y, idx);
+    consider(b, v.z, v.w, idx + 1);
+  }
 }
 
 __device__ __forceinline__ void merge_best(Best& a, const u64* k, const u32* i) {
@@ -118,21 +134,46 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
   best_init(b);
   const u32 tid = blockIdx.x * BLOCK + threadIdx.x;
   const u32 nthreads = gridDim.x * BLOCK;
+  {
+    // Seed every thread's skip box with the bounding box of a strided
+    // sample: a point strictly inside the box spanned by input points
+    // cannot be an extreme.  (The sample points themselves still reach
+    // their owners as candidates: they lie on or outside that box.)
+    __shared__ int s_box[4];
+    if (threadIdx.x == 0) { s_box[0] = 0x7FFFFFFF; s_box[1] = (int)0x80000000; s_box[2] = 0x7FFFFFFF; s_box[3] = (int)0x80000000; }
+    __syncthreads();
+    const u32 step = n / BLOCK + 1;
+    const u32 j = threadIdx.x * step;
+    int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
+    if (j < n) {
+      const int2 p = reinterpret_cast<const int2*>(xy)[j];
+      x0 = x1 = p.x; y0 = y1 = p.y;
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x0 = min(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o));
+      x1 = max(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o));
+      y0 = min(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o));
+      y1 = max(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&s_box[0], x0); atomicMax(&s_box[1], x1);
+      atomicMin(&s_box[2], y0); atomicMax(&s_box[3], y1);
+    }
+    __syncthreads();
+    b.bx0 = s_box[0]; b.bx1 = s_box[1]; b.by0 = s_box[2]; b.by1 = s_box[3];
+  }
   if (VEC) {
     // 16-byte aligned: pair j holds points 2j and 2j + 1.
     const int4* p4 = reinterpret_cast<const int4*>(xy);
     const u32 npair = n >> 1;
     u32 j = tid;
-    for (; j + 3 * nthreads < npair; j += 4 * nthreads) {
-      int4 v[4];
+    for (; j + 7 * nthreads < npair; j += 8 * nthreads) {
+      int4 v[8];
       #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = p4[j + u * nthreads];
+      for (int u = 0; u < 8; ++u) v[u] = p4[j + u * nthreads];
       #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        u32 q = j + u * nthreads;
-        consider(b, v[u].x, v[u].y, 2 * q);
-        consider(b, v[u].z, v[u].w, 2 * q + 1);
-      }
+      for (int u = 0; u < 8; ++u) consider2(b, v[u], 2 * (j + u * nthreads));
     }
     for (; j < npair; j += nthreads) {
       int4 v = p4[j];
@@ -207,10 +248,20 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
 
 }  // namespace
 
+static int g_k1_occ = 0;
+
+// Enough blocks to cover the input, but never more than fit on the GPU at
+// once (a partial second wave would idle most SMs).
 int k1_grid(u32 n, int num_sms) {
   const int block = 512;
-  long long want = ((long long)(n / 2) + block * 4 - 1) / (block * 4);
-  long long cap = (long long)num_sms * 4;
+  if (g_k1_occ == 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1_extremes<512, true>, block, 0) != cudaSuccess || occ < 1)
+      occ = 1;
+    g_k1_occ = occ;
+  }
+  long long want = ((long long)(n / 2) + block * 8 - 1) / (block * 8);
+  long long cap = (long long)num_sms * g_k1_occ;
   if (want < 1) want = 1;
   return (int)(want < cap ? want : cap);
 }

@@ -5,12 +5,17 @@
 // A point is discarded when it lies strictly inside the filter polygon
 // (strictly left of every counter-clockwise edge, exact int64 orientation);
 // with fewer than three distinct corners nothing is discarded.  Survivors
-// are written as (key, idx) in ascending input order: warp ballots give the
-// ranks inside a tile and one decoupled look-back over tiles (dynamic tile
-// ids, so every awaited tile belongs to a running block) gives the tile's
-// output offset.  The digit histograms of the survivors' keys, needed by
-// every radix pass, are accumulated here as well, so the sort needs no
-// separate histogram pass.
+// are written as (key, idx) in ascending input order.  The compaction is
+// reduce-then-scan over chunks of K2_CHUNK points, so no block ever waits
+// for another:
+//   k2_count  counts each chunk's survivors (and the histogram of the first
+//             radix digit of their keys); the last block to finish turns
+//             the counts into exclusive chunk offsets;
+//   k2_write  writes each chunk's survivors (marked by k2_count in a
+//             one-bit-per-point mask) at the chunk's offset, ranked by warp
+//             ballots.  It walks the chunks in the reverse of k2_count's
+//             order so that the most recently read part of the input is
+//             still in L2.
 #include "hull_internal.cuh"
 #include "kernels.h"
 
@@ -19,12 +24,17 @@ namespace gbh {
 namespace {
 
 constexpr int K2_BLOCK = 256;
-constexpr int K2_PAIRS = 8;                          // int4 loads per thread per tile
-constexpr int K2_TILE = K2_BLOCK * K2_PAIRS * 2;     // 4096 points
+constexpr int K2_PAIRS = 4;                          // int4 loads per thread per chunk
+constexpr int K2_CHUNK = K2_BLOCK * K2_PAIRS * 2;    // 2048 points
 constexpr int K2_WARPS = K2_BLOCK / 32;
+static_assert(K2_PAIRS * K2_WARPS == 32, "one (round, warp) count per lane");
 
+// Edge j from corner c_j to c_j+1: orient(c_j, c_j+1, p) = ex*y - ey*x - c
+// with c = ex*ay - ey*ax, i.e. two 32x32->64 multiply-adds per edge (every
+// term is below 2^60 in magnitude for coordinates bounded by 2^29).
 struct Edges {
-  int ax[kMaxCorners], ay[kMaxCorners], ex[kMaxCorners], ey[kMaxCorners];
+  int ex[kMaxCorners], ney[kMaxCorners];
+  long long nc[kMaxCorners];
 };
 
 template <int K>
@@ -32,7 +42,7 @@ __device__ __forceinline__ bool strictly_inside(const Edges& E, int x, int y) {
   bool in = true;
   #pragma unroll
   for (int j = 0; j < K; ++j) {
-    long long o = (long long)E.ex[j] * (y - E.ay[j]) - (long long)E.ey[j] * (x - E.ax[j]);
+    const long long o = (long long)E.ex[j] * y + (long long)E.ney[j] * x + E.nc[j];
     in = in && (o > 0);
   }
   return in;
@@ -50,116 +60,188 @@ __device__ __forceinline__ bool inside_any(const Edges& E, int k, int x, int y) 
   }
 }
 
+__device__ __forceinline__ void load_edges(const Plan* plan, int k, Edges& E) {
+  #pragma unroll
+  for (int j = 0; j < kMaxCorners; ++j) {
+    const int jn = (j + 1 < k) ? j + 1 : 0;
+    const int jj = (j < k) ? j : 0;
+    const int ax = plan->cx[jj], ay = plan->cy[jj];
+    const int ex = plan->cx[jn] - ax, ey = plan->cy[jn] - ay;
+    E.ex[j] = ex;
+    E.ney[j] = -ey;
+    E.nc[j] = -((long long)ex * ay - (long long)ey * ax);
+  }
+}
+
+// Loads this thread's K2_PAIRS pairs of a chunk and tests them.
 template <bool VEC>
-__global__ void __launch_bounds__(K2_BLOCK)
-k2_filter(const int* __restrict__ xy, Plan* plan, u64* __restrict__ keys_out,
-          u32* __restrict__ idx_out, u64* __restrict__ status) {
-  __shared__ u32 s_hist[kMaxPasses * kRadix];
-  __shared__ u32 s_wcnt[K2_PAIRS * K2_WARPS];
-  __shared__ u32 s_excl;
-  __shared__ u32 s_tile;
-  __shared__ int s_fail;
+__device__ __forceinline__ void load_test(const int* __restrict__ xy, u32 n, u32 base,
+                                          const Edges& E, int k, int* px, int* py, bool* keep) {
+  #pragma unroll
+  for (int r = 0; r < K2_PAIRS; ++r) {
+    const u32 i0 = base + 2u * (r * K2_BLOCK + threadIdx.x);
+    if (VEC && i0 + 1 < n) {
+      const int4 v = *reinterpret_cast<const int4*>(xy + 2 * (size_t)i0);
+      px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+    } else {
+      int2 a = make_int2(0, 0), b = make_int2(0, 0);
+      if (i0 < n) a = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0);
+      if (i0 + 1 < n) b = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0 + 2);
+      px[2 * r] = a.x; py[2 * r] = a.y; px[2 * r + 1] = b.x; py[2 * r + 1] = b.y;
+    }
+    keep[2 * r] = (i0 < n) && !inside_any(E, k, px[2 * r], py[2 * r]);
+    keep[2 * r + 1] = (i0 + 1 < n) && !inside_any(E, k, px[2 * r + 1], py[2 * r + 1]);
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K2_BLOCK, 6)
+k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
+         unsigned char* __restrict__ mask) {
+  __shared__ u32 s_hist[kRadix];
+  __shared__ u32 s_red[K2_WARPS];
+  __shared__ bool s_last;
 
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
   const int k = plan->ncorner;
-  const u32 epoch = plan->epoch + EP_FILTER;
-  const u32 spin = plan->spin_limit;
   const int x0 = plan->key_x0, y0 = plan->key_y0;
   const u32 ybits = plan->ybits;
-  const u32 npasses = plan->npasses;
-  const u32 ntiles = (n + K2_TILE - 1) / K2_TILE;
+  const bool hist = plan->npasses > 0;
+  const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Edges E;
+  load_edges(plan, k, E);
+  for (int q = threadIdx.x; q < kRadix; q += K2_BLOCK) s_hist[q] = 0u;
+  __syncthreads();
+
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
+    bool keep[2 * K2_PAIRS];
+    load_test<VEC>(xy, n, c * (u32)K2_CHUNK, E, k, px, py, keep);
+    u32 cnt = 0, bits = 0;
+    #pragma unroll
+    for (int e = 0; e < 2 * K2_PAIRS; ++e) {
+      if (keep[e]) {
+        ++cnt;
+        bits |= 1u << e;
+        if (hist) {
+          const u64 key = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
+          atomicAdd(&s_hist[(u32)key & (kRadix - 1)], 1u);
+        }
+      }
+    }
+    mask[(size_t)c * K2_BLOCK + threadIdx.x] = (unsigned char)bits;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if (lane == 0) s_red[wid] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u32 t = 0;
+      for (int w = 0; w < K2_WARPS; ++w) t += s_red[w];
+      counts[c] = t;
+    }
+    __syncthreads();
+  }
+  if (hist)
+    for (u32 q = threadIdx.x; q < kRadix; q += K2_BLOCK)
+      if (s_hist[q]) atomicAdd(&plan->hist[0][q], s_hist[q]);
+
+  // The last block turns the chunk counts into exclusive offsets.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_FILTER], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const u32 per = (nchunks + K2_BLOCK - 1) / K2_BLOCK;
+  const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
+  u32 sum = 0;
+  for (u32 c = lo; c < hi; ++c) sum += *reinterpret_cast<volatile u32*>(&counts[c]);
+  u32 inc = sum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_red[wid] = inc;
+  __syncthreads();
+  u32 off = 0;
+  for (int w = 0; w < wid; ++w) off += s_red[w];
+  u32 run = off + inc - sum;
+  for (u32 c = lo; c < hi; ++c) {
+    const u32 v = *reinterpret_cast<volatile u32*>(&counts[c]);
+    counts[c] = run;
+    run += v;
+  }
+  if (threadIdx.x == K2_BLOCK - 1) plan->s = off + inc;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K2_BLOCK, 6)
+k2_write(const int* __restrict__ xy, Plan* plan, const u32* __restrict__ offsets,
+         const unsigned char* __restrict__ mask, u64* __restrict__ keys_out,
+         u32* __restrict__ idx_out) {
+  __shared__ u32 s_wcnt[K2_PAIRS * K2_WARPS];
+
+  if (plan->error & ERR_RANGE) return;
+  const u32 n = plan->n;
+  const u32 s = plan->s;
+  const int k = plan->ncorner;
+  const int x0 = plan->key_x0, y0 = plan->key_y0;
+  const u32 ybits = plan->ybits;
+  const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
+  (void)k;
 
-  Edges E;
-  #pragma unroll
-  for (int j = 0; j < kMaxCorners; ++j) {
-    int jn = (j + 1 < k) ? j + 1 : 0;
-    int jj = (j < k) ? j : 0;
-    E.ax[j] = plan->cx[jj];
-    E.ay[j] = plan->cy[jj];
-    E.ex[j] = plan->cx[jn] - plan->cx[jj];
-    E.ey[j] = plan->cy[jn] - plan->cy[jj];
-  }
-  for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += K2_BLOCK) s_hist[q] = 0u;
-
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(&plan->ctr[CTR_FILTER], 1u);
-    __syncthreads();
-    const u32 tile = s_tile;
-    if (tile >= ntiles) break;
-    const u32 base = tile * (u32)K2_TILE;
-
+  for (u32 q = blockIdx.x; q < nchunks; q += gridDim.x) {
+    const u32 c = nchunks - 1 - q;
+    const u32 base = c * (u32)K2_CHUNK;
+    const u32 bits = mask[(size_t)c * K2_BLOCK + threadIdx.x];
     int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
     bool keep[2 * K2_PAIRS];
     #pragma unroll
     for (int r = 0; r < K2_PAIRS; ++r) {
       const u32 i0 = base + 2u * (r * K2_BLOCK + threadIdx.x);
+      keep[2 * r] = (bits >> (2 * r)) & 1u;
+      keep[2 * r + 1] = (bits >> (2 * r + 1)) & 1u;
       if (VEC && i0 + 1 < n) {
-        int4 v = *reinterpret_cast<const int4*>(xy + 2 * (size_t)i0);
-        px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+        if (keep[2 * r] | keep[2 * r + 1]) {
+          const int4 v = *reinterpret_cast<const int4*>(xy + 2 * (size_t)i0);
+          px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+        } else {
+          px[2 * r] = py[2 * r] = px[2 * r + 1] = py[2 * r + 1] = 0;
+        }
       } else {
         int2 a = make_int2(0, 0), b = make_int2(0, 0);
         if (i0 < n) a = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0);
         if (i0 + 1 < n) b = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0 + 2);
         px[2 * r] = a.x; py[2 * r] = a.y; px[2 * r + 1] = b.x; py[2 * r + 1] = b.y;
       }
-      keep[2 * r] = (i0 < n) && !inside_any(E, k, px[2 * r], py[2 * r]);
-      keep[2 * r + 1] = (i0 + 1 < n) && !inside_any(E, k, px[2 * r + 1], py[2 * r + 1]);
     }
-
     // Ranks in (round, warp, lane, element) order, which is input order.
     u32 lane_pre[K2_PAIRS];
     #pragma unroll
     for (int r = 0; r < K2_PAIRS; ++r) {
-      u32 b0 = __ballot_sync(0xFFFFFFFFu, keep[2 * r]);
-      u32 b1 = __ballot_sync(0xFFFFFFFFu, keep[2 * r + 1]);
+      const u32 b0 = __ballot_sync(0xFFFFFFFFu, keep[2 * r]);
+      const u32 b1 = __ballot_sync(0xFFFFFFFFu, keep[2 * r + 1]);
       lane_pre[r] = __popc(b0 & lt_mask) + __popc(b1 & lt_mask);
       if (lane == 0) s_wcnt[r * K2_WARPS + wid] = __popc(b0) + __popc(b1);
     }
-    // Digit histograms of the survivors' keys for every radix pass.
-    #pragma unroll
-    for (int e = 0; e < 2 * K2_PAIRS; ++e) {
-      if (keep[e]) {
-        u64 key = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
-        for (u32 p = 0; p < npasses; ++p)
-          atomicAdd(&s_hist[p * kRadix + (u32)((key >> (p * kRadixBits)) & (kRadix - 1))], 1u);
-      }
-    }
     __syncthreads();
     if (wid == 0) {
-      // Exclusive scan of the 64 (round, warp) counts, two per lane.
-      u32 c0 = s_wcnt[2 * lane], c1 = s_wcnt[2 * lane + 1];
-      u32 sum = c0 + c1, inc = sum;
+      const u32 c0 = s_wcnt[lane];
+      u32 inc = c0;
       #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
         if (lane >= o) inc += t;
       }
-      u32 ex = inc - sum;
-      s_wcnt[2 * lane] = ex;
-      s_wcnt[2 * lane + 1] = ex + c0;
-      const u32 total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-      u32 excl = 0;
-      bool failed = false;
-      if (tile == 0) {
-        if (lane == 0) st_release_u64(&status[0], make_status(epoch, ST_INCL, total));
-      } else {
-        if (lane == 0) st_release_u64(&status[tile], make_status(epoch, ST_AGG, total));
-        excl = warp_lookback_count(status, tile, epoch, plan, spin, &failed);
-        if (lane == 0 && !failed) st_release_u64(&status[tile], make_status(epoch, ST_INCL, excl + total));
-      }
-      if (lane == 0) {
-        s_excl = excl;
-        s_fail = failed ? 1 : 0;
-        if (tile == ntiles - 1 && !failed) plan->s = excl + total;
-      }
+      s_wcnt[lane] = inc - c0;
     }
     __syncthreads();
-    if (s_fail) break;
-    const u32 excl = s_excl;
+    const u32 excl = offsets[c];
     #pragma unroll
     for (int r = 0; r < K2_PAIRS; ++r) {
       u32 pos = excl + s_wcnt[r * K2_WARPS + wid] + lane_pre[r];
@@ -167,7 +249,7 @@ k2_filter(const int* __restrict__ xy, Plan* plan, u64* __restrict__ keys_out,
       #pragma unroll
       for (int e = 0; e < 2; ++e) {
         if (keep[2 * r + e]) {
-          if (pos < n) {
+          if (pos < s) {
             keys_out[pos] = ((u64)(u32)(px[2 * r + e] - x0) << ybits) | (u64)(u32)(py[2 * r + e] - y0);
             idx_out[pos] = i0 + e;
           } else {
@@ -177,29 +259,31 @@ k2_filter(const int* __restrict__ xy, Plan* plan, u64* __restrict__ keys_out,
         }
       }
     }
-  }
-  __syncthreads();
-  for (u32 q = threadIdx.x; q < npasses * kRadix; q += K2_BLOCK) {
-    u32 c = s_hist[q];
-    if (c) atomicAdd(&(&plan->hist[0][0])[q], c);
+    __syncthreads();
   }
 }
 
 }  // namespace
 
-int k2_tile() { return K2_TILE; }
+int k2_tile() { return K2_CHUNK; }
 
 cudaError_t k2_occupancy(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k2_filter<true>, K2_BLOCK, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k2_write<true>, K2_BLOCK, 0);
 }
 
+// `status` holds one 32-bit count (then offset) per chunk; `mask` one byte
+// per thread and chunk (n / 8 bytes, rounded up to whole chunks).
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
-                      int grid, cudaStream_t st) {
+                      unsigned char* mask, int grid, cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
-  if (vec)
-    k2_filter<true><<<grid, K2_BLOCK, 0, st>>>(xy, plan, keys_out, idx_out, status);
-  else
-    k2_filter<false><<<grid, K2_BLOCK, 0, st>>>(xy, plan, keys_out, idx_out, status);
+  u32* counts = reinterpret_cast<u32*>(status);
+  if (vec) {
+    k2_count<true><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask);
+    k2_write<true><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
+  } else {
+    k2_count<false><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask);
+    k2_write<false><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
+  }
   return cudaGetLastError();
 }
 

@@ -1,15 +1,21 @@
 // K3: stable LSD radix sort of the survivors' (key, idx) pairs (Section 2.1
 // step 4, Section 3.3), one onesweep pass per 8-bit digit.
 //
-// The digit histograms of all passes were accumulated by K2, so every pass
-// is a single kernel: a block takes the next tile (dynamic id), ranks its
-// keys by digit with warp match/popc (stable: items are ranked in input
-// order), publishes its per-digit counts, resolves its global per-digit
-// offsets by a decoupled look-back (one thread per digit, bounded waits),
-// stages the tile in shared memory in digit order and writes it out, so
-// that consecutive threads write consecutive addresses within each digit.
-// Only the passes that the survivors' varying key bits need are run; the
-// others return at once, and the Plan records where the result ends up.
+// Each pass is one kernel.  A block takes the next tile (dynamic tile id,
+// the following one claimed in advance), counts the tile's digits per warp
+// with shared-memory atomics and publishes the tile's counts at once, so
+// that later tiles' look-backs find them early.  From the per-warp counts
+// every warp knows its first position per digit, so ranking (stable: items
+// in input order; lanes with equal digits found with ballots, the group's
+// positions reserved by one atomic of its highest lane) writes each key
+// straight to its place in a digit-ordered staging area in shared memory.
+// A decoupled look-back (one thread per digit, K3_WINDOW status words in
+// flight per step, bounded waits) gives the tile's global digit offsets,
+// and the staged tile is written out with consecutive threads on
+// consecutive addresses within each digit.  While it reads the keys a pass also counts the next
+// digit, so pass p + 1 starts with its histogram complete (K2 counts the
+// first digit).  Only the passes that the keys' varying bits need do work;
+// the others return at once, and the Plan records where the result is.
 #include "hull_internal.cuh"
 #include "kernels.h"
 
@@ -17,165 +23,230 @@ namespace gbh {
 
 namespace {
 
-constexpr int K3_BLOCK = 256;
+// Tuning knobs (tile shape and ranking primitive).
+#ifndef K3_ITEMS_CFG
+#define K3_ITEMS_CFG 16
+#endif
+#ifndef K3_MINBLOCKS_CFG
+#define K3_MINBLOCKS_CFG 3
+#endif
+#ifndef K3_RANK_BALLOT
+#define K3_RANK_BALLOT 1      // 1: find equal digits with 8 ballots, 0: with match.any
+#endif
+#ifndef K3_BLOCK_CFG
+#define K3_BLOCK_CFG 256
+#endif
+#ifndef K3_WINDOW_CFG
+#define K3_WINDOW_CFG 16
+#endif
+constexpr int K3_BLOCK = K3_BLOCK_CFG;
 constexpr int K3_WARPS = K3_BLOCK / 32;
-constexpr int K3_ITEMS = 16;
-constexpr int K3_TILE = K3_BLOCK * K3_ITEMS;      // 4096 keys
-constexpr int K3_WARP_ITEMS = 32 * K3_ITEMS;      // 512 keys per warp
-static_assert(K3_BLOCK == kRadix, "one thread per digit");
+constexpr int K3_ITEMS = K3_ITEMS_CFG;
+constexpr int K3_TILE = K3_BLOCK * K3_ITEMS;
+constexpr int K3_WARP_ITEMS = 32 * K3_ITEMS;
+constexpr int K3_WINDOW = K3_WINDOW_CFG;          // status words in flight per look-back step
+static_assert(K3_BLOCK == kRadix || K3_BLOCK == 2 * kRadix, "the first kRadix threads own a digit each");
+static_assert(K3_WARP_ITEMS <= 65535, "16-bit warp counters");
 
-__global__ void __launch_bounds__(K3_BLOCK, 3)
+__device__ __forceinline__ u32 digit_of(u64 k, u32 shift) { return (u32)(k >> shift) & (kRadix - 1); }
+
+// Lanes holding the same 8-bit digit (all 32 lanes take part).
+__device__ __forceinline__ u32 same_digit_lanes(u32 dg) {
+#if K3_RANK_BALLOT
+  u32 peers = 0xFFFFFFFFu;
+  #pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+#else
+  return __match_any_sync(0xFFFFFFFFu, dg);
+#endif
+}
+
+__global__ void __launch_bounds__(K3_BLOCK, K3_MINBLOCKS_CFG)
 k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
             u64* __restrict__ keys_out, u32* __restrict__ idx_out, Plan* plan,
             u64* __restrict__ status, u32 pass) {
   extern __shared__ __align__(16) unsigned char k3_smem[];
   u64* s_keys = reinterpret_cast<u64*>(k3_smem);
   u32* s_idx = reinterpret_cast<u32*>(k3_smem + K3_TILE * sizeof(u64));
-  __shared__ unsigned short s_whist[K3_WARPS][kRadix];
+  // Per-warp digit counts, then each warp's next free tile position per digit.
+  __shared__ u32 s_wpos[K3_WARPS][kRadix];
+  __shared__ u32 s_next[kRadix];      // next pass's digit histogram (block lifetime)
   __shared__ u32 s_gstart[kRadix];
-  __shared__ u32 s_tstart[kRadix];
   __shared__ u32 s_gbase[kRadix];
-  __shared__ u32 s_warp_tot[K3_WARPS];
-  __shared__ u32 s_tile;
+  __shared__ u32 s_warp_tot[kRadix / 32];
+  __shared__ u32 s_tile[2];
   __shared__ int s_fail;
 
-  if (pass >= plan->npasses || (plan->error & ERR_RANGE)) return;
+  const u32 npasses = plan->npasses;
+  if (pass >= npasses || (plan->error & ERR_RANGE)) return;
   const u32 s = plan->s;
   const u32 shift = pass * kRadixBits;
+  const bool count_next = pass + 1 < npasses;
+  const u32 nshift = shift + kRadixBits;
   const u32 epoch = plan->epoch + EP_SORT0 + pass;
   const u32 spin = plan->spin_limit;
   const u32 ntiles = (s + K3_TILE - 1) / K3_TILE;
-  const int d = threadIdx.x;      // this thread's digit in the per-digit phases
+  const int d = threadIdx.x & (kRadix - 1);      // digit owned in the per-digit phases
+  const bool owner = threadIdx.x < kRadix;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
+  u32* ctr = &plan->ctr[CTR_SORT0 + pass];
 
-  // Global exclusive start of every digit (block scan of the histogram).
-  {
-    u32 v = plan->hist[pass][d];
-    u32 inc = v;
+  // Global exclusive start of every digit (scan of the histogram by the
+  // digit owners).
+  u32 hv = 0, hinc = 0;
+  if (owner) {
+    hv = plan->hist[pass][d];
+    hinc = hv;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-      if (lane >= o) inc += t;
+      const u32 t = __shfl_up_sync(0xFFFFFFFFu, hinc, o);
+      if (lane >= o) hinc += t;
     }
-    if (lane == 31) s_warp_tot[wid] = inc;
-    __syncthreads();
+    if (lane == 31) s_warp_tot[wid] = hinc;
+    s_next[d] = 0;
+  }
+  if (threadIdx.x == 0) s_tile[0] = atomicAdd(ctr, 1u);
+  __syncthreads();
+  if (owner) {
     u32 off = 0;
     for (int w = 0; w < wid; ++w) off += s_warp_tot[w];
-    s_gstart[d] = off + inc - v;
+    s_gstart[d] = off + hinc - hv;
   }
 
-  for (;;) {
+  for (int buf = 0;; buf ^= 1) {
+    for (int q = threadIdx.x; q < K3_WARPS * kRadix; q += K3_BLOCK) (&s_wpos[0][0])[q] = 0u;
     __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(&plan->ctr[CTR_SORT0 + pass], 1u);
-    for (int w = 0; w < K3_WARPS; ++w) s_whist[w][d] = 0;
-    __syncthreads();
-    const u32 tile = s_tile;
+    const u32 tile = s_tile[buf];
     if (tile >= ntiles) break;
+    // Claim the following tile now; its id is read after this tile.
+    if (threadIdx.x == 0) s_tile[buf ^ 1] = atomicAdd(ctr, 1u);
     const u32 base = tile * (u32)K3_TILE;
     const u32 tile_n = min((u32)K3_TILE, s - base);
+    const bool full = tile_n == (u32)K3_TILE;
 
     u64 key[K3_ITEMS];
-    u32 idx[K3_ITEMS];
-    unsigned short rank[K3_ITEMS];
+    u32 idv[K3_ITEMS];
     const u32 wbase = base + wid * K3_WARP_ITEMS;
     #pragma unroll
     for (int it = 0; it < K3_ITEMS; ++it) {
-      u32 p = wbase + it * 32 + lane;
-      if (p < s) { key[it] = keys_in[p]; idx[it] = idx_in[p]; }
-      else { key[it] = 0; idx[it] = 0; }
+      const u32 p = wbase + it * 32 + lane;
+      const bool v = full || p < s;
+      key[it] = v ? keys_in[p] : 0ull;
+      idv[it] = v ? idx_in[p] : 0u;
     }
-    // Stable in-warp ranking, item by item in input order.
+    // Per-warp digit counts (and the next pass's histogram).
+    u32* wp = &s_wpos[wid][0];
     #pragma unroll
     for (int it = 0; it < K3_ITEMS; ++it) {
-      const bool valid = (wbase + it * 32 + lane) < s;
-      const u32 vmask = __ballot_sync(0xFFFFFFFFu, valid);
-      const u32 dg = (u32)(key[it] >> shift) & (kRadix - 1);
-      u32 peers = 0, before = 0;
-      if (valid) {
-        peers = __match_any_sync(vmask, dg);
-        before = s_whist[wid][dg];
+      if (full || wbase + it * 32 + lane < s) {
+        atomicAdd(&wp[digit_of(key[it], shift)], 1u);
+        if (count_next) atomicAdd(&s_next[digit_of(key[it], nshift)], 1u);
       }
-      __syncwarp();
-      if (valid) {
-        rank[it] = (unsigned short)(before + __popc(peers & lt_mask));
-        if (lane == 31 - __clz(peers)) s_whist[wid][dg] = (unsigned short)(before + __popc(peers));
+    }
+    __syncthreads();
+    // Per digit: tile count (published at once), tile-local start, and each
+    // warp's first position.
+    u32 cnt = 0, tinc = 0;
+    u64* st = status + (size_t)tile * kRadix + d;
+    if (owner) {
+      #pragma unroll
+      for (int w = 0; w < K3_WARPS; ++w) cnt += s_wpos[w][d];
+      st_relaxed_u64(st, make_status(epoch, tile == 0 ? ST_INCL : ST_AGG, cnt));
+      tinc = cnt;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xFFFFFFFFu, tinc, o);
+        if (lane >= o) tinc += t;
       }
-      __syncwarp();
+      if (lane == 31) s_warp_tot[wid] = tinc;
+    }
+    __syncthreads();
+    u32 tstart = 0;
+    if (owner) {
+      u32 off = 0;
+      for (int w = 0; w < wid; ++w) off += s_warp_tot[w];
+      tstart = off + tinc - cnt;
+      u32 run = tstart;
+      #pragma unroll
+      for (int w = 0; w < K3_WARPS; ++w) {
+        const u32 c = s_wpos[w][d];
+        s_wpos[w][d] = run;
+        run += c;
+      }
     }
     __syncthreads();
 
-    // Per digit: warp offsets, tile count, publish, look-back.
-    u32 cnt = 0;
+    // Stable ranking, item by item in input order, straight into the tile's
+    // digit-ordered staging area: the highest lane of each group of equal
+    // digits reserves the group's positions with one shared atomic.
     #pragma unroll
-    for (int w = 0; w < K3_WARPS; ++w) {
-      u32 c = s_whist[w][d];
-      s_whist[w][d] = (unsigned short)cnt;
-      cnt += c;
-    }
-    u64* st = status + (size_t)tile * kRadix + d;
-    if (tile == 0) st_release_u64(st, make_status(epoch, ST_INCL, cnt));
-    else st_release_u64(st, make_status(epoch, ST_AGG, cnt));
-    // Tile-local exclusive digit starts (block scan of cnt).
-    {
-      u32 inc = cnt;
-      #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= o) inc += t;
+    for (int it = 0; it < K3_ITEMS; ++it) {
+      const u32 dg = digit_of(key[it], shift);
+      const bool valid = full || (wbase + it * 32 + lane) < s;
+      u32 peers = same_digit_lanes(dg);
+      if (!full) peers &= __ballot_sync(0xFFFFFFFFu, valid);
+      const int leader = 31 - __clz(peers);
+      u32 pos = 0;
+      if (valid && lane == leader) pos = atomicAdd(&wp[dg], (u32)__popc(peers));
+      pos = __shfl_sync(0xFFFFFFFFu, pos, valid ? leader : lane) + __popc(peers & lt_mask);
+      if (valid) {
+        s_keys[pos] = key[it];
+        s_idx[pos] = idv[it];
       }
-      if (lane == 31) s_warp_tot[wid] = inc;
-      __syncthreads();
-      u32 off = 0;
-      for (int w = 0; w < wid; ++w) off += s_warp_tot[w];
-      s_tstart[d] = off + inc - cnt;
     }
+
+    // Decoupled look-back for this digit, K3_WINDOW predecessors per step.
     u32 excl = 0;
     bool fail = false;
-    if (tile > 0) {
-      long long t = (long long)tile - 1;
-      while (t >= 0) {
-        const u64* sp = status + (size_t)t * kRadix + d;
-        u64 w;
-        u32 f;
-        u32 it = 0;
-        for (;;) {
-          w = ld_acquire_u64(sp);
-          f = status_flag(w, epoch);
-          if (f != 0) break;
-          if (++it > spin || aborted(plan)) { fail = true; break; }
-          spin_pause(it);
+    if (owner) {
+      if (tile > 0) {
+        long long t = (long long)tile - 1;
+        bool done = false;
+        while (!done && !fail) {
+          u64 w[K3_WINDOW];
+          #pragma unroll
+          for (int k = 0; k < K3_WINDOW; ++k)
+            w[k] = (t - k >= 0) ? ld_relaxed_u64(status + (size_t)(t - k) * kRadix + d)
+                                : make_status(epoch, ST_INCL, 0);
+          #pragma unroll
+          for (int k = 0; k < K3_WINDOW; ++k) {
+            if (done || fail) break;
+            u32 f = status_flag(w[k], epoch);
+            u32 it = 0;
+            while (f == 0) {
+              if (++it > spin || aborted(plan)) { fail = true; break; }
+              spin_pause(it);
+              w[k] = ld_relaxed_u64(status + (size_t)(t - k) * kRadix + d);
+              f = status_flag(w[k], epoch);
+            }
+            if (fail) break;
+            excl += status_count(w[k]);
+            if (f == ST_INCL) done = true;
+          }
+          t -= K3_WINDOW;
         }
-        if (fail) break;
-        excl += status_count(w);
-        if (f == ST_INCL) break;
-        --t;
+        if (!fail) st_relaxed_u64(st, make_status(epoch, ST_INCL, excl + cnt));
       }
-      if (!fail) st_release_u64(st, make_status(epoch, ST_INCL, excl + cnt));
+      if (fail) flag_error(plan, ERR_TIMEOUT);
+      s_gbase[d] = s_gstart[d] + excl - tstart;
     }
-    if (fail) flag_error(plan, ERR_TIMEOUT);
-    s_gbase[d] = s_gstart[d] + excl - s_tstart[d];
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
     if (fail) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
 
-    // Stage the tile in digit order, then write it out.
-    #pragma unroll
-    for (int it = 0; it < K3_ITEMS; ++it) {
-      if (wbase + it * 32 + lane < s) {
-        const u32 dg = (u32)(key[it] >> shift) & (kRadix - 1);
-        const u32 lp = s_tstart[dg] + s_whist[wid][dg] + rank[it];
-        s_keys[lp] = key[it];
-        s_idx[lp] = idx[it];
-      }
-    }
-    __syncthreads();
+    // Write the digit-ordered tile out: consecutive threads, consecutive
+    // addresses within each digit.
     for (u32 j = threadIdx.x; j < tile_n; j += K3_BLOCK) {
       const u64 k = s_keys[j];
-      const u32 dg = (u32)(k >> shift) & (kRadix - 1);
-      const u32 gp = s_gbase[dg] + j;
+      const u32 gp = s_gbase[digit_of(k, shift)] + j;
       if (gp < s) {
         keys_out[gp] = k;
         idx_out[gp] = s_idx[j];
@@ -183,6 +254,10 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
         flag_error(plan, ERR_INTERNAL);
       }
     }
+  }
+  if (count_next && owner) {
+    const u32 c = s_next[d];
+    if (c) atomicAdd(&plan->hist[pass + 1][d], c);
   }
 }
 

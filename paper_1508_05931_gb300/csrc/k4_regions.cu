@@ -13,11 +13,18 @@
 // is always the point with the extreme direction seen so far, starting from
 // d(P_0).  All directions of a region lie in one half-plane, where the
 // cross product orders them totally, so "extreme so far" is an exclusive
-// prefix max (min) -- an associative scan.  It is computed here with one
-// decoupled look-back and gives exactly the survivors of the sequential
-// loop, for any tile size; duplicates of a kept point fall out as equal
-// directions.  Kept points are compacted stably per region with a second
-// look-back chained behind the first; the last tile adds P_0 and P_l.
+// prefix max (min) -- an associative scan -- and gives exactly the
+// survivors of the sequential loop; duplicates of a kept point fall out as
+// equal directions.
+//
+// Reduce-then-scan over chunks of K4_CHUNK sorted points (no block waits
+// for another):
+//   k4_agg      per-chunk extreme directions; the last block scans them into
+//               each chunk's exclusive prefix (starting from d(P_0));
+//   k4_keep     keep decisions, kept points staged per chunk, per-chunk kept
+//               counts; the last block scans the counts into offsets and
+//               adds P_0 and P_l to both region lists;
+//   k4_compact  moves the few kept points into the region lists in order.
 #include "hull_internal.cuh"
 #include "kernels.h"
 
@@ -26,37 +33,37 @@ namespace gbh {
 namespace {
 
 constexpr int K4_BLOCK = 256;
-constexpr int K4_ITEMS = 16;
-constexpr int K4_TILE = K4_BLOCK * K4_ITEMS;
+constexpr int K4_ITEMS = 8;
+constexpr int K4_CHUNK = K4_BLOCK * K4_ITEMS;      // 2048 sorted points
 constexpr int K4_WARPS = K4_BLOCK / 32;
 
-constexpr u32 K4_AGG = 1, K4_DIRP = 2, K4_FULL = 3;
-
-struct __align__(64) K4Status {
-  u64 flag;                 // [epoch:32 | state:32]
-  int agg[4];               // tile aggregate: lower max dir (x,y), upper min dir (x,y)
-  int inc[4];               // inclusive prefix of the same
-  u32 cnt[2];               // kept counts of this tile (lower, upper)
-  u32 inc_cnt[2];           // inclusive kept counts
-};
-static_assert(sizeof(K4Status) == 64, "status record size");
-
-// Direction pairs; (0, 0) marks "no element".
-struct Dir2 {
+// Extreme directions seen so far: lower region (counter-clockwise-most)
+// and upper region (clockwise-most).  d(P_0) is the identity of both
+// operations: every lower direction is strictly counter-clockwise of it and
+// every upper direction strictly clockwise, so no "empty" case exists.
+struct __align__(16) Dir2 {
   int lx, ly, ux, uy;
 };
 
-__device__ __forceinline__ bool is_empty(int x, int y) { return (x | y) == 0; }
+struct __align__(64) K4Chunk {
+  Dir2 agg;               // chunk aggregate
+  Dir2 excl;              // exclusive prefix over earlier chunks (with d(P_0))
+  uint2 cnt;              // kept points (lower, upper)
+  uint2 off;              // exclusive offsets of the same
+};
+static_assert(sizeof(K4Chunk) == 64, "chunk record size");
 
 // Lower region: keep the counter-clockwise-most direction (ties keep a).
 __device__ __forceinline__ void cmax(int& ax, int& ay, int bx, int by) {
-  if (is_empty(bx, by)) return;
-  if (is_empty(ax, ay) || cross2(ax, ay, bx, by) > 0) { ax = bx; ay = by; }
+  const bool t = cross2(ax, ay, bx, by) > 0;
+  ax = t ? bx : ax;
+  ay = t ? by : ay;
 }
 // Upper region: keep the clockwise-most direction (ties keep a).
 __device__ __forceinline__ void cmin(int& ax, int& ay, int bx, int by) {
-  if (is_empty(bx, by)) return;
-  if (is_empty(ax, ay) || cross2(ax, ay, bx, by) < 0) { ax = bx; ay = by; }
+  const bool t = cross2(ax, ay, bx, by) < 0;
+  ax = t ? bx : ax;
+  ay = t ? by : ay;
 }
 __device__ __forceinline__ void combine(Dir2& a, const Dir2& b) {
   cmax(a.lx, a.ly, b.lx, b.ly);
@@ -70,234 +77,287 @@ __device__ __forceinline__ Dir2 shfl_up_dir(const Dir2& v, int o) {
   r.uy = __shfl_up_sync(0xFFFFFFFFu, v.uy, o);
   return r;
 }
-
-__device__ __forceinline__ u32 wait_state(const K4Status* st, u32 epoch, u32 need, u32 spin,
-                                          Plan* plan, bool* fail) {
-  u32 it = 0;
-  for (;;) {
-    u64 w = ld_acquire_u64(&st->flag);
-    u32 state = ((u32)(w >> 32) == epoch) ? (u32)w : 0u;
-    if (state >= need) return state;
-    if (++it > spin || aborted(plan)) { *fail = true; return 0; }
-    spin_pause(it);
+// Inclusive warp scan under combine (earlier lanes first).
+__device__ __forceinline__ Dir2 warp_scan_dir(Dir2 v) {
+  const int lane = threadIdx.x & 31;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Dir2 t = shfl_up_dir(v, o);
+    if (lane >= o) { combine(t, v); v = t; }
   }
+  return v;
 }
 
-__global__ void __launch_bounds__(K4_BLOCK)
-k4_regions(const u64* __restrict__ keys_a, const u32* __restrict__ idx_a,
-           const u64* __restrict__ keys_b, const u32* __restrict__ idx_b, Plan* plan,
-           K4Status* __restrict__ status, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
-           int2* __restrict__ up_xy, int* __restrict__ up_idx) {
-  __shared__ Dir2 s_wdir[K4_WARPS];
-  __shared__ u32 s_wcnt[K4_WARPS][2];
-  __shared__ Dir2 s_tile_excl;
-  __shared__ u32 s_cnt_excl[2];
-  __shared__ u32 s_tile;
-  __shared__ int s_fail;
+struct Geo {
+  const u64* keys;
+  const u32* idxs;
+  u32 s, ybits;
+  u64 ymask;
+  int x0, y0, ax, ay, bx, by, ux, uy, d0x, d0y;
+};
 
-  if (plan->error & ERR_RANGE) return;
+__device__ __forceinline__ Geo make_geo(const Plan* plan, const u64* ka, const u32* ia,
+                                        const u64* kb, const u32* ib) {
+  Geo g;
   // The sort leaves its result in buffer a after an even number of passes.
   const bool in_b = (plan->npasses & 1u) != 0;
-  const u64* __restrict__ keys = in_b ? keys_b : keys_a;
-  const u32* __restrict__ idxs = in_b ? idx_b : idx_a;
-  const u32 s = plan->s;
-  const u32 epoch = plan->epoch + EP_REGION;
-  const u32 spin = plan->spin_limit;
-  const u32 ybits = plan->ybits;
-  const u64 ymask = ybits ? ((~0ull) >> (64 - ybits)) : 0ull;
-  const int x0 = plan->key_x0, y0 = plan->key_y0;
-  const int ax = plan->ext_x[0], ay = plan->ext_y[0];     // P_0 = P_minx
-  const int bx = plan->ext_x[1], by = plan->ext_y[1];     // P_l = P_maxx
-  const int ux = bx - ax, uy = by - ay;
-  const int d0x = ax - bx, d0y = ay - by;                 // d(P_0)
-  const u32 ntiles = (s + K4_TILE - 1) / K4_TILE;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  g.keys = in_b ? kb : ka;
+  g.idxs = in_b ? ib : ia;
+  g.s = plan->s;
+  g.ybits = plan->ybits;
+  g.ymask = g.ybits ? ((~0ull) >> (64 - g.ybits)) : 0ull;
+  g.x0 = plan->key_x0; g.y0 = plan->key_y0;
+  g.ax = plan->ext_x[0]; g.ay = plan->ext_y[0];     // P_0 = P_minx
+  g.bx = plan->ext_x[1]; g.by = plan->ext_y[1];     // P_l = P_maxx
+  g.ux = g.bx - g.ax; g.uy = g.by - g.ay;
+  g.d0x = g.ax - g.bx; g.d0y = g.ay - g.by;         // d(P_0)
+  return g;
+}
 
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(&plan->ctr[CTR_REGION], 1u);
-    __syncthreads();
-    const u32 tile = s_tile;
-    if (tile >= ntiles) break;
-    const u32 first = tile * (u32)K4_TILE + threadIdx.x * K4_ITEMS;
-
-    // Blocked arrangement: this thread owns K4_ITEMS consecutive items.
-    int px[K4_ITEMS], py[K4_ITEMS], pi[K4_ITEMS];
-    signed char side[K4_ITEMS];
+// Loads this thread's K4_ITEMS consecutive sorted points and classifies them.
+__device__ __forceinline__ void load_items(const Geo& g, u32 first, int* px, int* py, int* pi,
+                                           signed char* side, bool with_idx) {
+  u64 kk[K4_ITEMS];
+  if (first + K4_ITEMS <= g.s) {
+    const ulonglong2* kp = reinterpret_cast<const ulonglong2*>(g.keys + first);
+    #pragma unroll
+    for (int v = 0; v < K4_ITEMS / 2; ++v) { const ulonglong2 q = kp[v]; kk[2 * v] = q.x; kk[2 * v + 1] = q.y; }
+    if (with_idx) {
+      const int4* ip = reinterpret_cast<const int4*>(g.idxs + first);
+      #pragma unroll
+      for (int v = 0; v < K4_ITEMS / 4; ++v) {
+        const int4 q = ip[v];
+        pi[4 * v] = q.x; pi[4 * v + 1] = q.y; pi[4 * v + 2] = q.z; pi[4 * v + 3] = q.w;
+      }
+    }
+  } else {
     #pragma unroll
     for (int i = 0; i < K4_ITEMS; ++i) {
       const u32 p = first + i;
-      side[i] = 0;
-      px[i] = 0; py[i] = 0; pi[i] = 0;
-      if (p < s) {
-        const u64 k = keys[p];
-        px[i] = x0 + (int)(u32)(k >> ybits);
-        py[i] = y0 + (int)(u32)(k & ymask);
-        pi[i] = (int)idxs[p];
-        const long long o = cross2(ux, uy, px[i] - ax, py[i] - ay);
-        side[i] = (o < 0) ? -1 : (o > 0 ? 1 : 0);
-      }
+      kk[i] = p < g.s ? g.keys[p] : 0ull;
+      if (with_idx) pi[i] = p < g.s ? (int)g.idxs[p] : 0;
     }
-    Dir2 agg = {0, 0, 0, 0};
-    #pragma unroll
-    for (int i = 0; i < K4_ITEMS; ++i) {
-      if (side[i] < 0) cmax(agg.lx, agg.ly, px[i] - bx, py[i] - by);
-      else if (side[i] > 0) cmin(agg.ux, agg.uy, px[i] - bx, py[i] - by);
-    }
-    // Warp inclusive scan of the thread aggregates.
-    Dir2 inc = agg;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      Dir2 t = shfl_up_dir(inc, o);
-      if (lane >= o) {
-        Dir2 r = t;
-        combine(r, inc);
-        inc = r;
-      }
-    }
-    Dir2 lane_excl = shfl_up_dir(inc, 1);
-    if (lane == 0) lane_excl = Dir2{0, 0, 0, 0};
-    if (lane == 31) s_wdir[wid] = inc;
-    __syncthreads();
+  }
+  #pragma unroll
+  for (int i = 0; i < K4_ITEMS; ++i) {
+    px[i] = g.x0 + (int)(u32)(kk[i] >> g.ybits);
+    py[i] = g.y0 + (int)(u32)(kk[i] & g.ymask);
+    const long long o = cross2(g.ux, g.uy, px[i] - g.ax, py[i] - g.ay);
+    side[i] = (first + i >= g.s) ? 0 : ((o < 0) ? -1 : (o > 0 ? 1 : 0));
+  }
+}
 
-    // Tile aggregate, publish, look-back over directions.
+__device__ __forceinline__ Dir2 thread_agg(const Geo& g, const int* px, const int* py,
+                                           const signed char* side) {
+  Dir2 a = {g.d0x, g.d0y, g.d0x, g.d0y};
+  #pragma unroll
+  for (int i = 0; i < K4_ITEMS; ++i) {
+    if (side[i] < 0) cmax(a.lx, a.ly, px[i] - g.bx, py[i] - g.by);
+    else if (side[i] > 0) cmin(a.ux, a.uy, px[i] - g.bx, py[i] - g.by);
+  }
+  return a;
+}
+
+__device__ __forceinline__ bool last_block(Plan* plan, int ctr, bool* s_last) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = atomicAdd(&plan->ctr[ctr], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (*s_last) __threadfence();
+  return *s_last;
+}
+
+__global__ void __launch_bounds__(K4_BLOCK, 4)
+k4_agg(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
+       const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks) {
+  __shared__ Dir2 s_w[K4_WARPS];
+  __shared__ bool s_last;
+  if (plan->error & ERR_RANGE) return;
+  const Geo g = make_geo(plan, ka, ia, kb, ib);
+  const u32 nchunks = (g.s + K4_CHUNK - 1) / K4_CHUNK;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int px[K4_ITEMS], py[K4_ITEMS], pi[K4_ITEMS];
+    signed char side[K4_ITEMS];
+    load_items(g, c * K4_CHUNK + threadIdx.x * K4_ITEMS, px, py, pi, side, false);
+    Dir2 a = warp_scan_dir(thread_agg(g, px, py, side));
+    if (lane == 31) s_w[wid] = a;
+    __syncthreads();
     if (threadIdx.x == 0) {
-      Dir2 tagg = {0, 0, 0, 0};
-      for (int w = 0; w < K4_WARPS; ++w) combine(tagg, s_wdir[w]);
-      K4Status* me = &status[tile];
-      bool fail = false;
-      Dir2 excl = {d0x, d0y, d0x, d0y};
-      if (tile > 0) {
-        me->agg[0] = tagg.lx; me->agg[1] = tagg.ly; me->agg[2] = tagg.ux; me->agg[3] = tagg.uy;
-        st_release_u64(&me->flag, ((u64)epoch << 32) | K4_AGG);
-        Dir2 acc = {0, 0, 0, 0};
-        for (long long t = (long long)tile - 1; t >= 0; --t) {
-          const volatile K4Status* o = &status[t];
-          u32 stt = wait_state(&status[t], epoch, K4_AGG, spin, plan, &fail);
-          if (fail) break;
-          if (stt >= K4_DIRP) {
-            Dir2 v = {o->inc[0], o->inc[1], o->inc[2], o->inc[3]};
-            combine(acc, v);
-            break;
-          }
-          Dir2 v = {o->agg[0], o->agg[1], o->agg[2], o->agg[3]};
-          combine(acc, v);
-        }
-        excl = acc;
-      }
-      if (fail) flag_error(plan, ERR_TIMEOUT);
-      s_tile_excl = excl;
-      s_fail = fail ? 1 : 0;
+      Dir2 t = {g.d0x, g.d0y, g.d0x, g.d0y};
+      for (int w = 0; w < K4_WARPS; ++w) combine(t, s_w[w]);
+      chunks[c].agg = t;
     }
     __syncthreads();
-    if (s_fail) break;
+  }
+  if (!last_block(plan, CTR_REGION, &s_last)) return;
+  // Exclusive prefix of every chunk: per-thread segments, block scan.
+  const u32 per = (nchunks + K4_BLOCK - 1) / K4_BLOCK;
+  const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
+  Dir2 seg = {g.d0x, g.d0y, g.d0x, g.d0y};
+  for (u32 c = lo; c < hi; ++c) {
+    const volatile int* a = reinterpret_cast<const volatile int*>(&chunks[c].agg);
+    Dir2 v = {a[0], a[1], a[2], a[3]};
+    combine(seg, v);
+  }
+  Dir2 inc = warp_scan_dir(seg);
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  Dir2 run = {g.d0x, g.d0y, g.d0x, g.d0y};
+  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
+  Dir2 lex = shfl_up_dir(inc, 1);
+  if (lane > 0) combine(run, lex);
+  for (u32 c = lo; c < hi; ++c) {
+    chunks[c].excl = run;
+    const volatile int* a = reinterpret_cast<const volatile int*>(&chunks[c].agg);
+    Dir2 v = {a[0], a[1], a[2], a[3]};
+    combine(run, v);
+  }
+}
 
-    // This thread's exclusive prefix and the keep decisions.
-    Dir2 run = s_tile_excl;
-    for (int w = 0; w < wid; ++w) combine(run, s_wdir[w]);
-    combine(run, lane_excl);
+__global__ void __launch_bounds__(K4_BLOCK, 4)
+k4_keep(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
+        const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks,
+        int2* __restrict__ t_lo_xy, int* __restrict__ t_lo_idx, int2* __restrict__ t_up_xy,
+        int* __restrict__ t_up_idx, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
+        int2* __restrict__ up_xy, int* __restrict__ up_idx) {
+  __shared__ Dir2 s_w[K4_WARPS];
+  __shared__ u32 s_wc[K4_WARPS][2];
+  __shared__ bool s_last;
+  if (plan->error & ERR_RANGE) return;
+  const Geo g = make_geo(plan, ka, ia, kb, ib);
+  const u32 nchunks = (g.s + K4_CHUNK - 1) / K4_CHUNK;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int px[K4_ITEMS], py[K4_ITEMS], pi[K4_ITEMS];
+    signed char side[K4_ITEMS];
+    load_items(g, c * K4_CHUNK + threadIdx.x * K4_ITEMS, px, py, pi, side, true);
+    const Dir2 agg = thread_agg(g, px, py, side);
+    const Dir2 inc = warp_scan_dir(agg);
+    Dir2 lex = shfl_up_dir(inc, 1);
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    Dir2 run = chunks[c].excl;
+    for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
+    if (lane > 0) combine(run, lex);
     unsigned keep_lo = 0, keep_up = 0;
     #pragma unroll
     for (int i = 0; i < K4_ITEMS; ++i) {
-      const int vx = px[i] - bx, vy = py[i] - by;
+      const int vx = px[i] - g.bx, vy = py[i] - g.by;
       if (side[i] < 0) {
         if (cross2(run.lx, run.ly, vx, vy) > 0) { keep_lo |= 1u << i; run.lx = vx; run.ly = vy; }
       } else if (side[i] > 0) {
         if (cross2(run.ux, run.uy, vx, vy) < 0) { keep_up |= 1u << i; run.ux = vx; run.uy = vy; }
       }
     }
-    // Stable ranks of the kept points (block scan of two counts).
-    u32 c_lo = __popc(keep_lo), c_up = __popc(keep_up);
+    // Stable ranks of the kept points inside the chunk.
+    const u32 c_lo = __popc(keep_lo), c_up = __popc(keep_up);
     u32 i_lo = c_lo, i_up = c_up;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      u32 t0 = __shfl_up_sync(0xFFFFFFFFu, i_lo, o);
-      u32 t1 = __shfl_up_sync(0xFFFFFFFFu, i_up, o);
+      const u32 t0 = __shfl_up_sync(0xFFFFFFFFu, i_lo, o);
+      const u32 t1 = __shfl_up_sync(0xFFFFFFFFu, i_up, o);
       if (lane >= o) { i_lo += t0; i_up += t1; }
     }
-    if (lane == 31) { s_wcnt[wid][0] = i_lo; s_wcnt[wid][1] = i_up; }
+    if (lane == 31) { s_wc[wid][0] = i_lo; s_wc[wid][1] = i_up; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      u32 tl = 0, tu = 0;
-      for (int w = 0; w < K4_WARPS; ++w) {
-        u32 a0 = s_wcnt[w][0], a1 = s_wcnt[w][1];
-        s_wcnt[w][0] = tl; s_wcnt[w][1] = tu;
-        tl += a0; tu += a1;
-      }
-      K4Status* me = &status[tile];
-      Dir2 tinc = s_tile_excl;
-      Dir2 tagg = {0, 0, 0, 0};
-      for (int w = 0; w < K4_WARPS; ++w) combine(tagg, s_wdir[w]);
-      combine(tinc, tagg);
-      me->inc[0] = tinc.lx; me->inc[1] = tinc.ly; me->inc[2] = tinc.ux; me->inc[3] = tinc.uy;
-      me->cnt[0] = tl; me->cnt[1] = tu;
-      bool fail = false;
-      u32 e_lo = 0, e_up = 0;
-      if (tile == 0) {
-        me->inc_cnt[0] = tl; me->inc_cnt[1] = tu;
-        st_release_u64(&me->flag, ((u64)epoch << 32) | K4_FULL);
-      } else {
-        st_release_u64(&me->flag, ((u64)epoch << 32) | K4_DIRP);
-        for (long long t = (long long)tile - 1; t >= 0; --t) {
-          const volatile K4Status* o = &status[t];
-          u32 stt = wait_state(&status[t], epoch, K4_DIRP, spin, plan, &fail);
-          if (fail) break;
-          if (stt == K4_FULL) { e_lo += o->inc_cnt[0]; e_up += o->inc_cnt[1]; break; }
-          e_lo += o->cnt[0]; e_up += o->cnt[1];
-        }
-        if (!fail) {
-          me->inc_cnt[0] = e_lo + tl; me->inc_cnt[1] = e_up + tu;
-          st_release_u64(&me->flag, ((u64)epoch << 32) | K4_FULL);
-        }
-      }
-      if (fail) flag_error(plan, ERR_TIMEOUT);
-      s_fail = fail ? 1 : 0;
-      s_cnt_excl[0] = e_lo;
-      s_cnt_excl[1] = e_up;
-      if (tile == ntiles - 1 && !fail) {
-        const u32 r_lo = e_lo + tl, r_up = e_up + tu;
-        plan->r_lo = r_lo;
-        plan->r_up = r_up;
-        const int ia = plan->ext_idx[0], ib = plan->ext_idx[1];
-        lo_xy[0] = make_int2(ax, ay); lo_idx[0] = ia;
-        up_xy[0] = make_int2(ax, ay); up_idx[0] = ia;
-        if (r_lo + 1 < s + 2) { lo_xy[r_lo + 1] = make_int2(bx, by); lo_idx[r_lo + 1] = ib; }
-        if (r_up + 1 < s + 2) { up_xy[r_up + 1] = make_int2(bx, by); up_idx[r_up + 1] = ib; }
-      }
+    u32 wl = 0, wu = 0, tl = 0, tu = 0;
+    for (int w = 0; w < K4_WARPS; ++w) {
+      if (w < wid) { wl += s_wc[w][0]; wu += s_wc[w][1]; }
+      tl += s_wc[w][0]; tu += s_wc[w][1];
     }
-    __syncthreads();
-    if (s_fail) break;
-    u32 pos_lo = 1 + s_cnt_excl[0] + s_wcnt[wid][0] + (i_lo - c_lo);
-    u32 pos_up = 1 + s_cnt_excl[1] + s_wcnt[wid][1] + (i_up - c_up);
+    if (threadIdx.x == 0) chunks[c].cnt = make_uint2(tl, tu);
+    u32 pl = c * K4_CHUNK + wl + i_lo - c_lo;
+    u32 pu = c * K4_CHUNK + wu + i_up - c_up;
     #pragma unroll
     for (int i = 0; i < K4_ITEMS; ++i) {
-      if (keep_lo & (1u << i)) {
-        if (pos_lo < s + 1) { lo_xy[pos_lo] = make_int2(px[i], py[i]); lo_idx[pos_lo] = pi[i]; }
-        else flag_error(plan, ERR_INTERNAL);
-        ++pos_lo;
-      } else if (keep_up & (1u << i)) {
-        if (pos_up < s + 1) { up_xy[pos_up] = make_int2(px[i], py[i]); up_idx[pos_up] = pi[i]; }
-        else flag_error(plan, ERR_INTERNAL);
-        ++pos_up;
-      }
+      if (keep_lo & (1u << i)) { t_lo_xy[pl] = make_int2(px[i], py[i]); t_lo_idx[pl] = pi[i]; ++pl; }
+      else if (keep_up & (1u << i)) { t_up_xy[pu] = make_int2(px[i], py[i]); t_up_idx[pu] = pi[i]; ++pu; }
+    }
+    __syncthreads();
+  }
+  if (!last_block(plan, CTR_REGION2, &s_last)) return;
+  const u32 per = (nchunks + K4_BLOCK - 1) / K4_BLOCK;
+  const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
+  u32 sl = 0, su = 0;
+  for (u32 c = lo; c < hi; ++c) {
+    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
+    sl += q[0]; su += q[1];
+  }
+  u32 il = sl, iu = su;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t0 = __shfl_up_sync(0xFFFFFFFFu, il, o);
+    const u32 t1 = __shfl_up_sync(0xFFFFFFFFu, iu, o);
+    if (lane >= o) { il += t0; iu += t1; }
+  }
+  if (lane == 31) { s_wc[wid][0] = il; s_wc[wid][1] = iu; }
+  __syncthreads();
+  u32 ol = 0, ou = 0;
+  for (int w = 0; w < wid; ++w) { ol += s_wc[w][0]; ou += s_wc[w][1]; }
+  u32 rl = ol + il - sl, ru = ou + iu - su;
+  for (u32 c = lo; c < hi; ++c) {
+    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
+    const u32 a = q[0], b = q[1];
+    chunks[c].off = make_uint2(rl, ru);
+    rl += a; ru += b;
+  }
+  if (threadIdx.x == K4_BLOCK - 1) {
+    const u32 r_lo = ol + il, r_up = ou + iu;
+    plan->r_lo = r_lo;
+    plan->r_up = r_up;
+    const int i_a = plan->ext_idx[0], i_b = plan->ext_idx[1];
+    lo_xy[0] = make_int2(g.ax, g.ay); lo_idx[0] = i_a;
+    up_xy[0] = make_int2(g.ax, g.ay); up_idx[0] = i_a;
+    if (r_lo + 1 < g.s + 2) { lo_xy[r_lo + 1] = make_int2(g.bx, g.by); lo_idx[r_lo + 1] = i_b; }
+    if (r_up + 1 < g.s + 2) { up_xy[r_up + 1] = make_int2(g.bx, g.by); up_idx[r_up + 1] = i_b; }
+  }
+}
+
+__global__ void __launch_bounds__(K4_BLOCK)
+k4_compact(Plan* plan, const K4Chunk* __restrict__ chunks, const int2* __restrict__ t_lo_xy,
+           const int* __restrict__ t_lo_idx, const int2* __restrict__ t_up_xy,
+           const int* __restrict__ t_up_idx, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
+           int2* __restrict__ up_xy, int* __restrict__ up_idx) {
+  if (plan->error & ERR_RANGE) return;
+  const u32 s = plan->s;
+  const u32 nchunks = (s + K4_CHUNK - 1) / K4_CHUNK;
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint2 cnt = chunks[c].cnt, off = chunks[c].off;
+    for (u32 j = threadIdx.x; j < cnt.x; j += K4_BLOCK) {
+      const u32 d = 1 + off.x + j;
+      if (d < s + 1) { lo_xy[d] = t_lo_xy[c * K4_CHUNK + j]; lo_idx[d] = t_lo_idx[c * K4_CHUNK + j]; }
+      else flag_error(plan, ERR_INTERNAL);
+    }
+    for (u32 j = threadIdx.x; j < cnt.y; j += K4_BLOCK) {
+      const u32 d = 1 + off.y + j;
+      if (d < s + 1) { up_xy[d] = t_up_xy[c * K4_CHUNK + j]; up_idx[d] = t_up_idx[c * K4_CHUNK + j]; }
+      else flag_error(plan, ERR_INTERNAL);
     }
   }
 }
 
 }  // namespace
 
-int k4_tile() { return K4_TILE; }
+int k4_tile() { return K4_CHUNK; }
+size_t k4_status_bytes() { return sizeof(K4Chunk); }
 
 cudaError_t k4_occupancy(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k4_regions, K4_BLOCK, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k4_keep, K4_BLOCK, 0);
 }
-size_t k4_status_bytes() { return sizeof(K4Status); }
 
+// `status` holds one K4Chunk per chunk; t_* are staging areas of at least
+// ceil(s / K4_CHUNK) * K4_CHUNK slots each.
 cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib, Plan* plan,
-                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
+                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                      int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st) {
-  k4_regions<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, reinterpret_cast<K4Status*>(status),
-                                        lo_xy, lo_idx, up_xy, up_idx);
+  K4Chunk* ch = reinterpret_cast<K4Chunk*>(status);
+  k4_agg<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch);
+  k4_keep<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx,
+                                     lo_xy, lo_idx, up_xy, up_idx);
+  k4_compact<<<grid, K4_BLOCK, 0, st>>>(plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx,
+                                        up_xy, up_idx);
   return cudaGetLastError();
 }
 

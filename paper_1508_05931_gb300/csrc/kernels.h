@@ -34,7 +34,7 @@ cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtParti
 
 int k2_tile();
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
-                      int grid, cudaStream_t st);
+                      unsigned char* mask, int grid, cudaStream_t st);
 
 int k3_tile();
 size_t k3_dyn_smem();
@@ -45,7 +45,8 @@ cudaError_t launch_k3(const u64* kin, const u32* iin, u64* kout, u32* iout, Plan
 int k4_tile();
 size_t k4_status_bytes();
 cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib, Plan* plan,
-                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
+                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                      int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st);
 
 int k5_chunk();

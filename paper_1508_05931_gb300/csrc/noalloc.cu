@@ -65,6 +65,7 @@ struct Carve {
   int2* h_xy[2]; int* h_idx[2];
   u32* cnt[2];
   int4* jobs;
+  unsigned char* mask;
   size_t total;
 };
 
@@ -100,6 +101,7 @@ Carve carve(unsigned char* base, int num_sms) {
   }
   for (int b = 0; b < 2; ++b) c.cnt[b] = reinterpret_cast<u32*>(take(nchunks * 4));
   c.jobs = reinterpret_cast<int4*>(take(nchunks * 16));
+  c.mask = take(cap / 8 + 4096);
   c.total = off;
   return c;
 }
@@ -164,7 +166,7 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
     e = launch_k1(d_xy, un, 1u << 22, c.plan, c.partials, k1_grid(un, d->num_sms), st);
   const size_t t2 = (un + k2_tile() - 1) / k2_tile();
   if (e == cudaSuccess)
-    e = launch_k2(d_xy, c.plan, c.keys[0], c.idx[0], c.st_filter, grid_for(d->occ_k2, d->num_sms, t2), st);
+    e = launch_k2(d_xy, c.plan, c.keys[0], c.idx[0], c.st_filter, c.mask, grid_for(d->occ_k2, d->num_sms, t2), st);
   const size_t t3 = (un + k3_tile() - 1) / k3_tile();
   for (u32 p = 0; p < (u32)kMaxPasses && e == cudaSuccess; ++p)
     e = launch_k3(c.keys[p & 1], c.idx[p & 1], c.keys[(p + 1) & 1], c.idx[(p + 1) & 1], c.plan,
@@ -172,7 +174,8 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
   const size_t t4 = (un + k4_tile() - 1) / k4_tile();
   if (e == cudaSuccess)
     e = launch_k4(c.keys[0], c.idx[0], c.keys[1], c.idx[1], c.plan, c.st_region, c.lo_xy, c.lo_idx,
-                  c.up_xy, c.up_idx, grid_for(d->occ_k4, d->num_sms, t4), st);
+                  c.up_xy, c.up_idx, c.h_xy[0], c.h_idx[0], c.h_xy[1], c.h_idx[1],
+                  grid_for(d->occ_k4, d->num_sms, t4), st);
   const size_t chunks = (un + 4) / (size_t)k5_chunk() + 2;
   if (e == cudaSuccess)
     e = launch_k5(c.lo_xy, c.lo_idx, c.up_xy, c.up_idx, c.plan, c.h_xy[0], c.h_idx[0], c.h_xy[1],

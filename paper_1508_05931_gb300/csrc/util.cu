@@ -1,6 +1,6 @@
 // Small helper kernels: Plan set-up for the stage entry points, a
-// stand-alone digit histogram (for sorting arbitrary keys), index fills and
-// label gathers.
+// stand-alone first-digit histogram (for sorting arbitrary keys), index
+// fills and label gathers.
 #include "hull_internal.cuh"
 #include "kernels.h"
 
@@ -25,18 +25,17 @@ __global__ void k_plan_patch(Plan* plan, PlanPatch p) {
   if (p.set_r) { plan->r_lo = p.r_lo; plan->r_up = p.r_up; }
 }
 
+// Histogram of the first radix digit (each radix pass counts the next one).
 __global__ void k_hist(const u64* __restrict__ keys, Plan* plan) {
-  __shared__ u32 h[kMaxPasses * kRadix];
-  const u32 s = plan->s, np = plan->npasses;
-  for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += blockDim.x) h[q] = 0u;
+  __shared__ u32 h[kRadix];
+  const u32 s = plan->s;
+  for (int q = threadIdx.x; q < kRadix; q += blockDim.x) h[q] = 0u;
   __syncthreads();
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) {
-    const u64 k = keys[i];
-    for (u32 p = 0; p < np; ++p) atomicAdd(&h[p * kRadix + (u32)((k >> (p * kRadixBits)) & 255u)], 1u);
-  }
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x)
+    atomicAdd(&h[(u32)keys[i] & (kRadix - 1)], 1u);
   __syncthreads();
-  for (u32 q = threadIdx.x; q < np * kRadix; q += blockDim.x)
-    if (h[q]) atomicAdd(&(&plan->hist[0][0])[q], h[q]);
+  for (u32 q = threadIdx.x; q < kRadix; q += blockDim.x)
+    if (h[q]) atomicAdd(&plan->hist[0][q], h[q]);
 }
 
 __global__ void k_iota(int* out, u32 m) {
