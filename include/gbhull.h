@@ -57,7 +57,9 @@ typedef struct {
   int proposal;       /* 0 = quadrilateral of the four extremes (the paper), 1 = learned */
   int collect_stats;  /* 1 = keep survivor counts of the last call for hull_last_stats */
   uint32_t spin_limit;/* iteration limit of every device wait; 0 = default (1 << 22) */
-  int reserved;
+  int autotune;       /* 1 = time the batched kernel's block sizes per size bucket on first
+                         use and cache the choice (file: $GBHULL_AUTOTUNE_CACHE, else
+                         ~/.cache/gbhull_autotune.json); 0 = built-in defaults */
 } hull_config;
 
 typedef struct {
@@ -93,15 +95,23 @@ hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t 
 hull_status hull_compute_host(hull_ctx *ctx, const int32_t *h_xy, int64_t n, int32_t *h_out,
                               int64_t cap, int64_t *h_count, void *stream);
 
-/* B independent hulls in one call.  d_offsets: device int64[B+1], instance
- * b is points [d_offsets[b], d_offsets[b+1]) of d_xy (non-decreasing,
- * d_offsets[0] = 0).  Vertex indices are relative to their instance and are
- * written to d_out at d_out_offsets[b] (device int64[B+1], written by the
- * call; d_out_offsets[B] = total vertices).  cap bounds the total.  Total
- * points must be < 2^30 and every instance < 2^30.  Synchronises `stream`. */
+/* B independent hulls in one call (one persistent launch per size bucket:
+ * each block runs the whole pipeline on one instance at a time, instances
+ * taken largest first).  d_offsets: device int64[B+1], instance b is points
+ * [d_offsets[b], d_offsets[b+1]) of d_xy (non-decreasing, d_offsets[0] = 0).
+ * Vertex indices are relative to their instance and are written to d_out at
+ * d_out_offsets[b] (device int64[B+1], written by the call;
+ * d_out_offsets[B] = total vertices).  cap bounds the total (HULL_ECAPACITY
+ * leaves d_out untouched but still writes d_out_offsets).  Total points must
+ * be < 2^30 and every instance at most hull_batched_max_instance() points
+ * (else HULL_EINVAL).  Copies d_offsets to the host and synchronises
+ * `stream`. */
 hull_status hull_compute_batched(hull_ctx *ctx, const int32_t *d_xy, const int64_t *d_offsets,
                                  int32_t B, int32_t *d_out, int64_t cap, int64_t *d_out_offsets,
                                  void *stream);
+
+/* Largest instance size hull_compute_batched accepts. */
+int64_t hull_batched_max_instance(void);
 
 /* Survivor counts and extremes of the last hull_compute (collect_stats=1). */
 hull_status hull_last_stats(const hull_ctx *ctx, hull_stats *out);

@@ -1,10 +1,16 @@
 // The C ABI (include/gbhull.h): contexts, workspace, argument checks, the
 // launch sequence of the pipeline and the per-stage entry points.
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <sys/stat.h>
+#include <numeric>
+#include <string>
+#include <vector>
 
 #include "../../include/gbhull.h"
 #include "hull_internal.cuh"
@@ -44,6 +50,27 @@ struct HostStage {
   int32_t* d_out = nullptr;    // device output for host calls
 };
 
+// Workspace of the batched kernels: per-instance scratch slots and tables.
+struct BatchWs {
+  size_t cap_slots = 0, cap_b = 0;
+  void* base = nullptr;
+  u64* ka = nullptr; u64* kb = nullptr; u32* ia = nullptr; u32* ib = nullptr;
+  int2* lxy = nullptr; int* lidx = nullptr; int2* uxy = nullptr; int* uidx = nullptr;
+  int* out_tmp = nullptr;
+  long long* slot0 = nullptr;
+  int* order = nullptr;
+  u32* hcount = nullptr;
+  u32* ctl = nullptr;          // [0], [1]: queues; [2]: error bits
+  // pinned host staging
+  size_t h_cap = 0;
+  long long* h_off = nullptr;
+  long long* h_slot0 = nullptr;
+  int* h_order = nullptr;
+  u32* h_ctl = nullptr;
+};
+
+constexpr int64_t kSmallInstance = 16384;   // size bucket boundary
+
 }  // namespace
 
 struct hull_ctx {
@@ -61,6 +88,12 @@ struct hull_ctx {
   bool prof_pending = false;
   cudaEvent_t ev[HULL_NUM_STAGES + 1] = {};
   hull_profile profile{};
+  // batched mode
+  BatchWs bw;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t bev[2] = {nullptr, nullptr};
+  int occ_b256 = 1, occ_b512 = 1;
+  int tuned_block[2] = {0, 0};  // per bucket (small, large); 0 = not tuned yet
 };
 
 namespace {
@@ -246,6 +279,57 @@ hull_status new_call_patch(hull_ctx* c, cudaStream_t st, PlanPatch p) {
   return e == cudaSuccess ? HULL_OK : cuda_fail(e);
 }
 
+std::string autotune_path() {
+  const char* p = std::getenv("GBHULL_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* h = std::getenv("HOME");
+  return std::string(h && *h ? h : "/tmp") + "/.cache/gbhull_autotune.json";
+}
+
+std::string device_key(const hull_ctx* c) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return "unknown";
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  std::string k = prop.name;
+  for (char& ch : k)
+    if (ch == '"' || ch == '\\') ch = '_';
+  return k + "/sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "/drv" + std::to_string(drv);
+}
+
+// The cache is a flat JSON object {"<device>|batched_small": 256, ...}.
+void autotune_load(hull_ctx* c) {
+  FILE* f = std::fopen(autotune_path().c_str(), "r");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, r);
+  std::fclose(f);
+  const std::string dk = device_key(c);
+  const char* names[2] = {"batched_small", "batched_large"};
+  for (int b = 0; b < 2; ++b) {
+    const std::string key = "\"" + dk + "|" + names[b] + "\":";
+    const size_t pos = txt.find(key);
+    if (pos == std::string::npos) continue;
+    const int v = std::atoi(txt.c_str() + pos + key.size());
+    if (v == 256 || v == 512) c->tuned_block[b] = v;
+  }
+}
+
+void autotune_save(const hull_ctx* c) {
+  const std::string path = autotune_path();
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+  FILE* f = std::fopen(path.c_str(), "w");
+  if (!f) return;
+  const std::string dk = device_key(c);
+  std::fprintf(f, "{\"%s|batched_small\": %d, \"%s|batched_large\": %d}\n", dk.c_str(),
+               c->tuned_block[0] ? c->tuned_block[0] : 256, dk.c_str(),
+               c->tuned_block[1] ? c->tuned_block[1] : 256);
+  std::fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
@@ -286,6 +370,15 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
     return cuda_fail(cudaErrorUnknown);
   }
   if (c->occ_k5 < 1) { delete c; return HULL_ECUDA; }
+  if (batch_configure(&c->occ_b256, &c->occ_b512) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->bev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->bev[1], cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return cuda_fail(cudaErrorUnknown);
+  }
+  if (c->occ_b256 < 1) c->occ_b256 = 1;
+  if (c->occ_b512 < 1) c->occ_b512 = 1;
   if (cudaMalloc(&c->plan, sizeof(Plan)) != cudaSuccess) { delete c; return HULL_ENOMEM; }
   if (cudaMemset(c->plan, 0, sizeof(Plan)) != cudaSuccess ||
       cudaMallocHost(&c->h_plan, sizeof(Plan)) != cudaSuccess) {
@@ -307,6 +400,15 @@ void hull_destroy(hull_ctx* c) {
   if (c->hs.d_out) cudaFree(c->hs.d_out);
   for (int k = 0; k <= HULL_NUM_STAGES; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->bw.base) cudaFree(c->bw.base);
+  if (c->bw.slot0) cudaFree(c->bw.slot0);
+  if (c->bw.h_off) cudaFreeHost(c->bw.h_off);
+  if (c->bw.h_slot0) cudaFreeHost(c->bw.h_slot0);
+  if (c->bw.h_order) cudaFreeHost(c->bw.h_order);
+  if (c->bw.h_ctl) cudaFreeHost(c->bw.h_ctl);
+  for (int k = 0; k < 2; ++k)
+    if (c->bev[k]) cudaEventDestroy(c->bev[k]);
+  if (c->aux) cudaStreamDestroy(c->aux);
   if (c->plan) cudaFree(c->plan);
   if (c->h_plan) cudaFreeHost(c->h_plan);
   delete c;
@@ -539,10 +641,162 @@ hull_status hull_stage_chain(hull_ctx* c, const int32_t* d_xy, int64_t m, int32_
   return r;
 }
 
+int64_t hull_batched_max_instance(void) { return (int64_t)batch_max_instance(); }
+
 hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t* d_offsets, int32_t B,
                                  int32_t* d_out, int64_t cap, int64_t* d_out_offsets, void* stream) {
-  (void)c; (void)d_xy; (void)d_offsets; (void)B; (void)d_out; (void)cap; (void)d_out_offsets; (void)stream;
-  return HULL_EINVAL;
+  if (!c || B < 0 || cap < 0 || !d_offsets || !d_out_offsets || (cap > 0 && !d_out)) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchWs& w = c->bw;
+  if ((size_t)B + 1 > w.h_cap) {
+    if (w.h_off) cudaFreeHost(w.h_off);
+    if (w.h_slot0) cudaFreeHost(w.h_slot0);
+    if (w.h_order) cudaFreeHost(w.h_order);
+    if (w.h_ctl) cudaFreeHost(w.h_ctl);
+    w.h_off = nullptr; w.h_slot0 = nullptr; w.h_order = nullptr; w.h_ctl = nullptr; w.h_cap = 0;
+    const size_t hc = (size_t)B + 1024;
+    if (cudaMallocHost(&w.h_off, hc * 8) != cudaSuccess || cudaMallocHost(&w.h_slot0, hc * 8) != cudaSuccess ||
+        cudaMallocHost(&w.h_order, hc * 4) != cudaSuccess || cudaMallocHost(&w.h_ctl, 64) != cudaSuccess) {
+      cudaGetLastError();
+      return HULL_ENOMEM;
+    }
+    w.h_cap = hc;
+  }
+  cudaError_t e = cudaMemcpyAsync(w.h_off, d_offsets, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (w.h_off[0] != 0) return HULL_EINVAL;
+  const int64_t maxi = (int64_t)batch_max_instance();
+  const int64_t pad = batch_pad();
+  int64_t slots = 0;
+  std::vector<int> small, large;
+  for (int i = 0; i < B; ++i) {
+    const int64_t ni = w.h_off[i + 1] - w.h_off[i];
+    if (ni < 0 || ni > maxi || w.h_off[i + 1] > (int64_t)kMaxN) return HULL_EINVAL;
+    w.h_slot0[i] = slots;
+    slots += ni + pad;
+    (ni <= kSmallInstance ? small : large).push_back(i);
+  }
+  if (B == 0) {
+    long long zero = 0;
+    e = cudaMemcpyAsync(d_out_offsets, &zero, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+  }
+  if (!d_xy) return HULL_EINVAL;
+  auto by_size = [&](int a, int b) {
+    const int64_t na = w.h_off[a + 1] - w.h_off[a], nb = w.h_off[b + 1] - w.h_off[b];
+    return na != nb ? na > nb : a < b;
+  };
+  std::sort(large.begin(), large.end(), by_size);
+  std::sort(small.begin(), small.end(), by_size);
+  std::copy(large.begin(), large.end(), w.h_order);
+  std::copy(small.begin(), small.end(), w.h_order + large.size());
+  // Workspace.
+  if ((size_t)slots > w.cap_slots || (size_t)B > w.cap_b) {
+    cudaDeviceSynchronize();
+    if (w.base) cudaFree(w.base);
+    if (w.slot0) cudaFree(w.slot0);
+    w.base = nullptr; w.slot0 = nullptr; w.cap_slots = 0; w.cap_b = 0;
+    const size_t cs = std::max<size_t>((size_t)slots, (size_t)1 << 20);
+    const size_t bytes = cs * (8 + 8 + 4 + 4 + 8 + 4 + 8 + 4 + 4);
+    const size_t cb = (size_t)B + 1024;
+    if (cudaMalloc(&w.base, bytes) != cudaSuccess ||
+        cudaMalloc(&w.slot0, cb * 8 + cb * 4 + cb * 4 + 256) != cudaSuccess) {
+      cudaGetLastError();
+      if (w.base) cudaFree(w.base);
+      w.base = nullptr;
+      return HULL_ENOMEM;
+    }
+    char* b = static_cast<char*>(w.base);
+    w.ka = reinterpret_cast<u64*>(b); b += cs * 8;
+    w.kb = reinterpret_cast<u64*>(b); b += cs * 8;
+    w.lxy = reinterpret_cast<int2*>(b); b += cs * 8;
+    w.uxy = reinterpret_cast<int2*>(b); b += cs * 8;
+    w.ia = reinterpret_cast<u32*>(b); b += cs * 4;
+    w.ib = reinterpret_cast<u32*>(b); b += cs * 4;
+    w.lidx = reinterpret_cast<int*>(b); b += cs * 4;
+    w.uidx = reinterpret_cast<int*>(b); b += cs * 4;
+    w.out_tmp = reinterpret_cast<int*>(b);
+    char* t = reinterpret_cast<char*>(w.slot0);
+    w.order = reinterpret_cast<int*>(t + cb * 8);
+    w.hcount = reinterpret_cast<u32*>(t + cb * 8 + cb * 4);
+    w.ctl = reinterpret_cast<u32*>(t + cb * 16);
+    w.cap_slots = cs;
+    w.cap_b = (size_t)B;
+  }
+  e = cudaMemcpyAsync(w.slot0, w.h_slot0, (size_t)B * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.order, w.h_order, (size_t)B * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, 64, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+
+  BatchLaunch L{};
+  L.xy = d_xy; L.offsets = reinterpret_cast<const long long*>(d_offsets);
+  L.slot0 = w.slot0; L.ka = w.ka; L.kb = w.kb; L.ia = w.ia; L.ib = w.ib;
+  L.lxy = w.lxy; L.lidx = w.lidx; L.uxy = w.uxy; L.uidx = w.uidx;
+  L.out_tmp = w.out_tmp; L.hcount = w.hcount; L.error = w.ctl + 2;
+  const int nl = (int)large.size(), ns = (int)small.size();
+  auto run_bucket = [&](int bucket, int block, cudaStream_t s2, u32* queue) -> cudaError_t {
+    BatchLaunch M = L;
+    M.order = w.order + (bucket == 1 ? 0 : nl);
+    M.nb = bucket == 1 ? nl : ns;
+    M.queue = queue;
+    const int occ = block == 512 ? c->occ_b512 : c->occ_b256;
+    const int grid = std::max(1, std::min(M.nb, occ * c->num_sms));
+    return launch_batch(block, grid, M, s2);
+  };
+  // Autotuning: time each block size per bucket once, on this batch.
+  if (c->cfg.autotune && (c->tuned_block[0] == 0 || c->tuned_block[1] == 0)) {
+    autotune_load(c);
+    for (int bucket = 0; bucket < 2; ++bucket) {
+      if (c->tuned_block[bucket] != 0 || (bucket == 0 ? ns : nl) == 0) continue;
+      float best = 1e30f;
+      int best_b = 256;
+      cudaEvent_t t0, t1;
+      cudaEventCreate(&t0);
+      cudaEventCreate(&t1);
+      for (int rep = 0; rep < 2; ++rep) {
+        for (int blk : {256, 512}) {
+          cudaMemsetAsync(w.ctl, 0, 64, st);
+          cudaEventRecord(t0, st);
+          run_bucket(bucket, blk, st, w.ctl);
+          cudaEventRecord(t1, st);
+          cudaEventSynchronize(t1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, t0, t1);
+          if (rep == 1 && ms < best) { best = ms; best_b = blk; }
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      c->tuned_block[bucket] = best_b;
+    }
+    autotune_save(c);
+    e = cudaMemsetAsync(w.ctl, 0, 64, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const int blk_small = c->tuned_block[0] ? c->tuned_block[0] : 256;
+  const int blk_large = c->tuned_block[1] ? c->tuned_block[1] : 256;
+  // Large instances on the caller's stream, small ones concurrently on the
+  // context's second stream.
+  e = cudaEventRecord(c->bev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->bev[0], 0);
+  if (e == cudaSuccess && nl > 0) e = run_bucket(1, blk_large, st, w.ctl);
+  if (e == cudaSuccess && ns > 0) e = run_bucket(0, blk_small, c->aux, w.ctl + 1);
+  if (e == cudaSuccess) e = cudaEventRecord(c->bev[1], c->aux);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->bev[1], 0);
+  if (e == cudaSuccess)
+    e = launch_batch_output(w.hcount, w.slot0, w.out_tmp, B, reinterpret_cast<long long*>(d_out_offsets),
+                            d_out, (long long)cap, w.ctl + 2, c->num_sms * 4, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_ctl, w.ctl, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const u32 err = w.h_ctl[2];
+  if (err & ERR_RANGE) return HULL_ERANGE;
+  if (err & ERR_INTERNAL) return HULL_EINTERNAL;
+  if (err & ERR_CAPACITY) return HULL_ECAPACITY;
+  return HULL_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,636 @@
+// Batched hulls: many independent point sets in one persistent launch.
+//
+// Every block takes instances from a queue ordered largest first (so the
+// longest jobs start early and the small ones fill the tail) and runs the
+// whole pipeline of Section 2.1 on one instance by itself, each step as a
+// block-level loop over chunks in order, so no block ever waits for another:
+//   1. extremes (step 1): block reduction;
+//   2. quadrilateral filter + compaction (steps 2-3) with a running offset,
+//      plus the digit histograms of the survivors' keys;
+//   3. stable LSD radix sort (step 4): per 8-bit digit, tiles in order,
+//      per-warp early counts give each warp's positions, the highest lane of
+//      each group of equal digits reserves positions with one shared atomic;
+//   4. region split + second round (steps 5-7) as a running prefix
+//      max/min of directions seen from P_l (exactly Figure 2's survivors);
+//   5. lower and upper chains (step 8): chunks of the chain built in shared
+//      memory (per-thread stacks, warp bridge merges), then chunk chains
+//      merged level by level through global scratch.
+// Each instance owns a scratch region of its size plus a fixed pad; its
+// hull (CCW indices relative to the instance) is staged there and a second
+// kernel compacts all hulls into the output with their offsets.
+#include "chain.cuh"
+#include "hull_internal.cuh"
+#include "kernels.h"
+
+namespace gbh {
+
+using namespace chain;
+
+namespace {
+
+constexpr int BT_ITEMS = 16;        // sort keys per thread per tile
+constexpr int BT_FITEMS = 8;        // filter / second-round items per thread per chunk
+constexpr int BT_LEAF = 8;          // chain points per thread
+constexpr int BT_MAX_CHUNKS = 1024; // chain chunks per instance (bounds n_i)
+
+struct BestX {
+  u64 k[4];
+  u32 i[4];
+};
+
+__device__ __forceinline__ void bx_init(BestX& b) {
+  #pragma unroll
+  for (int j = 0; j < 4; ++j) { b.k[j] = ~0ull; b.i[j] = 0xFFFFFFFFu; }
+}
+__device__ __forceinline__ bool bx_lt(u64 ka, u32 ia, u64 kb, u32 ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+__device__ __forceinline__ void bx_point(BestX& b, int x, int y, u32 idx) {
+  const u32 ox = (u32)x ^ 0x80000000u, oy = (u32)y ^ 0x80000000u;
+  const u64 kxy = ((u64)ox << 32) | oy, kyx = ((u64)oy << 32) | ox;
+  if (kxy < b.k[0]) { b.k[0] = kxy; b.i[0] = idx; }
+  if (~kxy < b.k[1]) { b.k[1] = ~kxy; b.i[1] = idx; }
+  if (kyx < b.k[2]) { b.k[2] = kyx; b.i[2] = idx; }
+  if (~kyx < b.k[3]) { b.k[3] = ~kyx; b.i[3] = idx; }
+}
+__device__ __forceinline__ void bx_merge(BestX& a, const u64* k, const u32* i) {
+  #pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (bx_lt(k[j], i[j], a.k[j], a.i[j])) { a.k[j] = k[j]; a.i[j] = i[j]; }
+}
+__device__ __forceinline__ void bx_warp(BestX& b) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u64 k[4]; u32 i[4];
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      k[j] = __shfl_xor_sync(0xFFFFFFFFu, b.k[j], o);
+      i[j] = __shfl_xor_sync(0xFFFFFFFFu, b.i[j], o);
+    }
+    bx_merge(b, k, i);
+  }
+}
+
+__device__ __forceinline__ u32 bitlen32(u32 v) { return v ? 32u - (u32)__clz(v) : 0u; }
+
+// Per-instance parameters, built by thread 0 from the extremes.
+struct IPlan {
+  int ext_idx[4];
+  int ext_x[4], ext_y[4];
+  int ncorner;
+  int ex[4], ney[4];
+  long long nc[4];
+  int x0, y0;
+  u32 ybits, npasses;
+  int bad;
+};
+
+__device__ __forceinline__ u32 lanes_with_digit(u32 dg) {
+  u32 peers = 0xFFFFFFFFu;
+  #pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+struct Dir2b {
+  int lx, ly, ux, uy;
+};
+__device__ __forceinline__ void dcombine(Dir2b& a, const Dir2b& b) {
+  bool t = cross2(a.lx, a.ly, b.lx, b.ly) > 0;
+  a.lx = t ? b.lx : a.lx; a.ly = t ? b.ly : a.ly;
+  t = cross2(a.ux, a.uy, b.ux, b.uy) < 0;
+  a.ux = t ? b.ux : a.ux; a.uy = t ? b.uy : a.uy;
+}
+__device__ __forceinline__ Dir2b dshfl_up(const Dir2b& v, int o) {
+  Dir2b r;
+  r.lx = __shfl_up_sync(0xFFFFFFFFu, v.lx, o); r.ly = __shfl_up_sync(0xFFFFFFFFu, v.ly, o);
+  r.ux = __shfl_up_sync(0xFFFFFFFFu, v.ux, o); r.uy = __shfl_up_sync(0xFFFFFFFFu, v.uy, o);
+  return r;
+}
+
+template <int BLOCK>
+struct Smem {
+  static constexpr int W = BLOCK / 32;
+  static constexpr int CHUNK = BLOCK * BT_LEAF;   // chain points per shared-memory chunk
+  u32 wpos[W][kRadix];
+  u32 hist[kMaxPasses][kRadix];
+  u32 cur[kRadix];
+  u32 red[BT_FITEMS * W + 8];
+  Dir2b wdir[W];
+  u32 wcnt[W][2];
+  IPlan plan;
+  int inst;
+  u64 rk[W][4];
+  u32 ri[W][4];
+  int sx[CHUNK], sy[CHUNK], si[CHUNK];
+  int ccnt[BLOCK];                   // per-thread chain lengths inside a chunk
+  int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
+  int4 pair[BT_MAX_CHUNKS / 2];      // bridge results of one merge level
+};
+
+// Chain over m points (xy, idx) in lexicographic order.  Short chains are
+// built in shared memory and left there; longer ones are built in chunks
+// and merged through g0/g1.  Returns the chain length; *where receives 0
+// (shared memory), 1 (g0) or 2 (g1).
+template <int BLOCK>
+__device__ int build_chain(Smem<BLOCK>& S, const int2* xy, const int* idx, int m, int sgn,
+                           int2* g0xy, int* g0i, int2* g1xy, int* g1i, int* where) {
+  constexpr int CHUNK = Smem<BLOCK>::CHUNK;
+  constexpr int W = Smem<BLOCK>::W;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nch = (m + CHUNK - 1) / CHUNK;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int first = ch * CHUNK;
+    const int len = min(CHUNK, m - first);
+    for (int i = threadIdx.x; i < len; i += BLOCK) {
+      const int2 p = xy[first + i];
+      S.sx[i] = p.x; S.sy[i] = p.y; S.si[i] = idx[first + i];
+    }
+    __syncthreads();
+    const int b = threadIdx.x * BT_LEAF;
+    S.ccnt[threadIdx.x] = leaf_chain(S.sx, S.sy, S.si, b, max(0, min(BT_LEAF, len - b)), sgn);
+    __syncthreads();
+    const int nleaf = (len + BT_LEAF - 1) / BT_LEAF;
+    for (int step = 1; step < nleaf; step <<= 1) {
+      const int npair = (nleaf + 2 * step - 1) / (2 * step);
+      for (int p = wid; p < npair; p += W) {
+        const int la = 2 * p * step, lb = la + step;
+        if (lb >= nleaf) continue;
+        const int aB = la * BT_LEAF, bB = lb * BT_LEAF;
+        const int alpha = S.ccnt[la], beta = S.ccnt[lb];
+        SmemChain A{S.sx + aB, S.sy + aB}, Bc{S.sx + bB, S.sy + bB};
+        int is, js;
+        bridge(A, alpha, Bc, beta, sgn, is, js);
+        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
+        for (int o = 0; o < n2; o += 32) {
+          const int q = o + lane;
+          int vx = 0, vy = 0, vi = 0;
+          if (q < n2) { vx = S.sx[src + q]; vy = S.sy[src + q]; vi = S.si[src + q]; }
+          __syncwarp();
+          if (q < n2) { S.sx[dst + q] = vx; S.sy[dst + q] = vy; S.si[dst + q] = vi; }
+          __syncwarp();
+        }
+        if (lane == 0) S.ccnt[la] = is + 1 + n2;
+      }
+      __syncthreads();
+    }
+    const int hc = S.ccnt[0];
+    if (nch == 1) { *where = 0; return hc; }
+    for (int i = threadIdx.x; i < hc; i += BLOCK) {
+      g0xy[first + i] = make_int2(S.sx[i], S.sy[i]);
+      g0i[first + i] = S.si[i];
+    }
+    if (threadIdx.x == 0) S.chunk_cnt[ch] = hc;
+    __syncthreads();
+  }
+  // Merge chunk chains level by level (ping-pong through g0 / g1).
+  int2* cx = g0xy; int* ci = g0i; int2* nx = g1xy; int* ni = g1i;
+  int buf = 1;
+  for (int step = 1; step < nch; step <<= 1) {
+    const int np = (nch + 2 * step - 1) / (2 * step);
+    for (int p = wid; p < np; p += W) {
+      const int ca = 2 * p * step, cb = ca + step;
+      const int alpha = S.chunk_cnt[ca];
+      int is = alpha - 1, js = 0, beta = 0;
+      if (cb < nch) {
+        beta = S.chunk_cnt[cb];
+        GlobalChain A{cx + (size_t)ca * CHUNK}, Bc{cx + (size_t)cb * CHUNK};
+        bridge(A, alpha, Bc, beta, sgn, is, js);
+      }
+      if (lane == 0) S.pair[p] = make_int4(is, js, beta, 0);
+    }
+    __syncthreads();
+    for (int p = 0; p < np; ++p) {
+      const int4 pr = S.pair[p];
+      const int merged = pr.x + 1 + (pr.z - pr.y);
+      const size_t abase = (size_t)(2 * p * step) * CHUNK;
+      const size_t bbase = abase + (size_t)step * CHUNK;
+      for (int o = threadIdx.x; o < merged; o += BLOCK) {
+        const size_t src = (o <= pr.x) ? abase + o : bbase + pr.y + (o - pr.x - 1);
+        nx[abase + o] = __ldcg(&cx[src]);
+        ni[abase + o] = __ldcg(&ci[src]);
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < np; p += BLOCK) {
+      const int4 pr = S.pair[p];
+      S.chunk_cnt[2 * p * step] = pr.x + 1 + (pr.z - pr.y);
+    }
+    __syncthreads();
+    int2* t0 = cx; cx = nx; nx = t0;
+    int* t1 = ci; ci = ni; ni = t1;
+    buf ^= 1;
+  }
+  *where = buf == 1 ? 1 : 2;
+  return S.chunk_cnt[0];
+}
+
+struct BatchArgs {
+  const int* xy;
+  const long long* offsets;   // [B + 1]
+  const int* order;           // instances of this launch, largest first
+  int nb;
+  u32* queue;
+  const long long* slot0;     // [B] scratch region of each instance
+  u64* ka; u64* kb; u32* ia; u32* ib;
+  int2* lxy; int* lidx; int2* uxy; int* uidx;
+  int* out_tmp;
+  u32* hcount;                // [B]
+  u32* error;
+};
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char bt_smem[];
+  Smem<BLOCK>& S = *reinterpret_cast<Smem<BLOCK>*>(bt_smem);
+  constexpr int W = Smem<BLOCK>::W;
+  constexpr int TILE = BLOCK * BT_ITEMS;
+  constexpr int FCH = BLOCK * BT_FITEMS;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 lt_mask = (1u << lane) - 1u;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const u32 q = atomicAdd(a.queue, 1u);
+      S.inst = q < (u32)a.nb ? a.order[q] : -1;
+    }
+    __syncthreads();
+    const int inst = S.inst;
+    if (inst < 0) break;
+    const long long off = a.offsets[inst];
+    const u32 n = (u32)(a.offsets[inst + 1] - off);
+    const long long sl = a.slot0[inst];
+    const int2* P = reinterpret_cast<const int2*>(a.xy) + off;
+    if (n == 0) {
+      if (threadIdx.x == 0) a.hcount[inst] = 0;
+      __syncthreads();
+      continue;
+    }
+
+    // ---- 1. extremes
+    BestX b;
+    bx_init(b);
+    for (u32 j = threadIdx.x; j < n; j += BLOCK) {
+      const int2 p = P[j];
+      bx_point(b, p.x, p.y, j);
+    }
+    bx_warp(b);
+    if (lane == 0)
+      for (int q = 0; q < 4; ++q) { S.rk[wid][q] = b.k[q]; S.ri[wid][q] = b.i[q]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bx_init(b);
+      for (int w = 0; w < W; ++w) bx_merge(b, S.rk[w], S.ri[w]);
+      IPlan& pl = S.plan;
+      int ex[4], ey[4];
+      ex[0] = (int)(u32)((b.k[0] >> 32) ^ 0x80000000u); ey[0] = (int)((u32)b.k[0] ^ 0x80000000u);
+      u64 k1 = ~b.k[1];
+      ex[1] = (int)(u32)((k1 >> 32) ^ 0x80000000u); ey[1] = (int)((u32)k1 ^ 0x80000000u);
+      ey[2] = (int)(u32)((b.k[2] >> 32) ^ 0x80000000u); ex[2] = (int)((u32)b.k[2] ^ 0x80000000u);
+      u64 k3 = ~b.k[3];
+      ey[3] = (int)(u32)((k3 >> 32) ^ 0x80000000u); ex[3] = (int)((u32)k3 ^ 0x80000000u);
+      for (int j = 0; j < 4; ++j) { pl.ext_idx[j] = (int)b.i[j]; pl.ext_x[j] = ex[j]; pl.ext_y[j] = ey[j]; }
+      pl.bad = (ex[0] < -kCoordLimit || ex[1] > kCoordLimit || ey[2] < -kCoordLimit || ey[3] > kCoordLimit);
+      const int ord[4] = {0, 2, 1, 3};
+      int k = 0, cx[4], cy[4];
+      for (int j = 0; j < 4; ++j) {
+        const int x = ex[ord[j]], y = ey[ord[j]];
+        if (k > 0 && cx[k - 1] == x && cy[k - 1] == y) continue;
+        cx[k] = x; cy[k] = y; ++k;
+      }
+      while (k > 1 && cx[k - 1] == cx[0] && cy[k - 1] == cy[0]) --k;
+      pl.ncorner = k;
+      for (int j = 0; j < 4; ++j) {
+        const int jj = j < k ? j : 0, jn = (j + 1 < k) ? j + 1 : 0;
+        const int e_x = cx[jn] - cx[jj], e_y = cy[jn] - cy[jj];
+        pl.ex[j] = e_x; pl.ney[j] = -e_y;
+        pl.nc[j] = -((long long)e_x * cy[jj] - (long long)e_y * cx[jj]);
+      }
+      pl.x0 = ex[0]; pl.y0 = ey[2];
+      const u32 yb = bitlen32((u32)(ey[3] - ey[2])), xb = bitlen32((u32)(ex[1] - ex[0]));
+      pl.ybits = yb;
+      pl.npasses = (xb + yb + kRadixBits - 1) / kRadixBits;
+      if (pl.bad) atomicOr(a.error, ERR_RANGE);
+    }
+    for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
+    __syncthreads();
+    if (S.plan.bad) {
+      if (threadIdx.x == 0) a.hcount[inst] = 0;
+      __syncthreads();
+      continue;
+    }
+    const IPlan pl = S.plan;
+
+    // ---- 2. filter + compaction (+ digit histograms)
+    u32 run = 0;
+    for (u32 base = 0; base < n; base += FCH) {
+      int px[BT_FITEMS], py[BT_FITEMS];
+      bool keep[BT_FITEMS];
+      u32 pre[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + r * BLOCK + threadIdx.x;
+        px[r] = 0; py[r] = 0;
+        bool in = false;
+        if (j < n) {
+          const int2 p = P[j];
+          px[r] = p.x; py[r] = p.y;
+          in = pl.ncorner >= 3;
+          for (int e = 0; e < 4 && in; ++e) {
+            if (e >= pl.ncorner) break;
+            const long long o = (long long)pl.ex[e] * p.y + (long long)pl.ney[e] * p.x + pl.nc[e];
+            in = o > 0;
+          }
+        }
+        keep[r] = (j < n) && !in;
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, keep[r]);
+        pre[r] = __popc(bal & lt_mask);
+        if (lane == 0) S.red[r * W + wid] = __popc(bal);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        u32 t = 0;
+        for (int q = 0; q < BT_FITEMS * W; ++q) { const u32 c = S.red[q]; S.red[q] = t; t += c; }
+        S.red[BT_FITEMS * W] = t;
+      }
+      __syncthreads();
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        if (keep[r]) {
+          const u32 pos = run + S.red[r * W + wid] + pre[r];
+          const u64 key = ((u64)(u32)(px[r] - pl.x0) << pl.ybits) | (u64)(u32)(py[r] - pl.y0);
+          if (pos < n) {
+            a.ka[sl + pos] = key;
+            a.ia[sl + pos] = base + r * BLOCK + threadIdx.x;
+          }
+          for (u32 p = 0; p < pl.npasses; ++p)
+            atomicAdd(&S.hist[p][(u32)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+        }
+      }
+      run += S.red[BT_FITEMS * W];
+      __syncthreads();
+    }
+    const u32 s = run;
+
+    // ---- 3. stable LSD radix sort of (key, idx), tiles in order
+    u64* src_k = a.ka + sl; u32* src_i = a.ia + sl;
+    u64* dst_k = a.kb + sl; u32* dst_i = a.ib + sl;
+    for (u32 pass = 0; pass < pl.npasses; ++pass) {
+      const u32 shift = pass * kRadixBits;
+      // Exclusive start of every digit inside the instance's range.
+      u32 hv = 0, hinc = 0;
+      if (threadIdx.x < kRadix) {
+        hv = S.hist[pass][threadIdx.x];
+        hinc = hv;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 t = __shfl_up_sync(0xFFFFFFFFu, hinc, o);
+          if (lane >= o) hinc += t;
+        }
+        if (lane == 31) S.red[wid] = hinc;
+      }
+      __syncthreads();
+      if (threadIdx.x < kRadix) {
+        u32 o2 = 0;
+        for (int w = 0; w < wid; ++w) o2 += S.red[w];
+        S.cur[threadIdx.x] = o2 + hinc - hv;
+      }
+      __syncthreads();
+      for (u32 tb = 0; tb < s; tb += TILE) {
+        for (int q = threadIdx.x; q < W * kRadix; q += BLOCK) (&S.wpos[0][0])[q] = 0u;
+        __syncthreads();
+        u64 key[BT_ITEMS];
+        u32 idv[BT_ITEMS];
+        const u32 wb = tb + wid * 32 * BT_ITEMS;
+        #pragma unroll
+        for (int it = 0; it < BT_ITEMS; ++it) {
+          const u32 p = wb + it * 32 + lane;
+          key[it] = p < s ? src_k[p] : 0ull;
+          idv[it] = p < s ? src_i[p] : 0u;
+          if (p < s) atomicAdd(&S.wpos[wid][(u32)(key[it] >> shift) & (kRadix - 1)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kRadix) {
+          const int d = threadIdx.x;
+          u32 r2 = S.cur[d];
+          #pragma unroll
+          for (int w = 0; w < W; ++w) { const u32 c = S.wpos[w][d]; S.wpos[w][d] = r2; r2 += c; }
+          S.cur[d] = r2;
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int it = 0; it < BT_ITEMS; ++it) {
+          const u32 p = wb + it * 32 + lane;
+          const bool valid = p < s;
+          const u32 dg = (u32)(key[it] >> shift) & (kRadix - 1);
+          const u32 peers = lanes_with_digit(dg) & __ballot_sync(0xFFFFFFFFu, valid);
+          const int leader = 31 - __clz(peers);
+          u32 pos = 0;
+          if (valid && lane == leader) pos = atomicAdd(&S.wpos[wid][dg], (u32)__popc(peers));
+          pos = __shfl_sync(0xFFFFFFFFu, pos, valid ? leader : lane) + __popc(peers & lt_mask);
+          if (valid && pos < s) { dst_k[pos] = key[it]; dst_i[pos] = idv[it]; }
+        }
+        __syncthreads();
+      }
+      u64* tk = src_k; src_k = dst_k; dst_k = tk;
+      u32* ti = src_i; src_i = dst_i; dst_i = ti;
+    }
+    // sorted keys are in src_*
+
+    // ---- 4. region split + second round (running prefix of directions)
+    const int ax = pl.ext_x[0], ay = pl.ext_y[0], bxp = pl.ext_x[1], byp = pl.ext_y[1];
+    int2* LX = a.lxy + sl; int* LI = a.lidx + sl;
+    int2* UX = a.uxy + sl; int* UI = a.uidx + sl;
+    if (ax == bxp && ay == byp) {   // every point equal: one vertex
+      if (threadIdx.x == 0) { a.out_tmp[sl] = pl.ext_idx[0]; a.hcount[inst] = 1; }
+      __syncthreads();
+      continue;
+    }
+    const int ux = bxp - ax, uy = byp - ay, d0x = ax - bxp, d0y = ay - byp;
+    const u64 ymask = pl.ybits ? ((~0ull) >> (64 - pl.ybits)) : 0ull;
+    Dir2b R = {d0x, d0y, d0x, d0y};
+    u32 rl = 0, ru = 0;
+    for (u32 cb = 0; cb < s; cb += FCH) {
+      int px[BT_FITEMS], py[BT_FITEMS], pi[BT_FITEMS];
+      signed char side[BT_FITEMS];
+      const u32 first = cb + threadIdx.x * BT_FITEMS;
+      Dir2b ag = {d0x, d0y, d0x, d0y};
+      #pragma unroll
+      for (int i = 0; i < BT_FITEMS; ++i) {
+        const u32 p = first + i;
+        side[i] = 0; px[i] = 0; py[i] = 0; pi[i] = 0;
+        if (p < s) {
+          const u64 k = src_k[p];
+          px[i] = pl.x0 + (int)(u32)(k >> pl.ybits);
+          py[i] = pl.y0 + (int)(u32)(k & ymask);
+          pi[i] = (int)src_i[p];
+          const long long o = cross2(ux, uy, px[i] - ax, py[i] - ay);
+          side[i] = o < 0 ? -1 : (o > 0 ? 1 : 0);
+          const int vx = px[i] - bxp, vy = py[i] - byp;
+          if (side[i] < 0 && cross2(ag.lx, ag.ly, vx, vy) > 0) { ag.lx = vx; ag.ly = vy; }
+          if (side[i] > 0 && cross2(ag.ux, ag.uy, vx, vy) < 0) { ag.ux = vx; ag.uy = vy; }
+        }
+      }
+      Dir2b inc = ag;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        Dir2b t = dshfl_up(inc, o);
+        if (lane >= o) { dcombine(t, inc); inc = t; }
+      }
+      Dir2b lex = dshfl_up(inc, 1);
+      if (lane == 31) S.wdir[wid] = inc;
+      __syncthreads();
+      Dir2b runv = R;
+      for (int w = 0; w < wid; ++w) dcombine(runv, S.wdir[w]);
+      if (lane > 0) dcombine(runv, lex);
+      unsigned kl = 0, ku = 0;
+      #pragma unroll
+      for (int i = 0; i < BT_FITEMS; ++i) {
+        const int vx = px[i] - bxp, vy = py[i] - byp;
+        if (side[i] < 0) {
+          if (cross2(runv.lx, runv.ly, vx, vy) > 0) { kl |= 1u << i; runv.lx = vx; runv.ly = vy; }
+        } else if (side[i] > 0) {
+          if (cross2(runv.ux, runv.uy, vx, vy) < 0) { ku |= 1u << i; runv.ux = vx; runv.uy = vy; }
+        }
+      }
+      const u32 cl = __popc(kl), cu = __popc(ku);
+      u32 il = cl, iu = cu;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 t0 = __shfl_up_sync(0xFFFFFFFFu, il, o), t1 = __shfl_up_sync(0xFFFFFFFFu, iu, o);
+        if (lane >= o) { il += t0; iu += t1; }
+      }
+      if (lane == 31) { S.wcnt[wid][0] = il; S.wcnt[wid][1] = iu; }
+      __syncthreads();
+      u32 wl = 0, wu = 0, tl = 0, tu = 0;
+      Dir2b cagg = R;
+      for (int w = 0; w < W; ++w) {
+        if (w < wid) { wl += S.wcnt[w][0]; wu += S.wcnt[w][1]; }
+        tl += S.wcnt[w][0]; tu += S.wcnt[w][1];
+        dcombine(cagg, S.wdir[w]);
+      }
+      u32 pl0 = 1 + rl + wl + il - cl, pu0 = 1 + ru + wu + iu - cu;
+      #pragma unroll
+      for (int i = 0; i < BT_FITEMS; ++i) {
+        if (kl & (1u << i)) { if (pl0 < s + 1) { LX[pl0] = make_int2(px[i], py[i]); LI[pl0] = pi[i]; } ++pl0; }
+        else if (ku & (1u << i)) { if (pu0 < s + 1) { UX[pu0] = make_int2(px[i], py[i]); UI[pu0] = pi[i]; } ++pu0; }
+      }
+      R = cagg;
+      rl += tl; ru += tu;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      LX[0] = make_int2(ax, ay); LI[0] = pl.ext_idx[0];
+      UX[0] = make_int2(ax, ay); UI[0] = pl.ext_idx[0];
+      LX[rl + 1] = make_int2(bxp, byp); LI[rl + 1] = pl.ext_idx[1];
+      UX[ru + 1] = make_int2(bxp, byp); UI[ru + 1] = pl.ext_idx[1];
+    }
+    __syncthreads();
+
+    // ---- 5. chains (scratch: the sort buffers, free now), 6. staged output
+    int2* g0 = reinterpret_cast<int2*>(a.ka + sl);
+    int2* g1 = reinterpret_cast<int2*>(a.kb + sl);
+    int* g0i = reinterpret_cast<int*>(a.ia + sl);
+    int* g1i = reinterpret_cast<int*>(a.ib + sl);
+    int* out = a.out_tmp + sl;
+    int where = 0;
+    const int hl = build_chain<BLOCK>(S, LX, LI, (int)rl + 2, 1, g0, g0i, g1, g1i, &where);
+    for (int i = threadIdx.x; i < hl; i += BLOCK)
+      out[i] = where == 0 ? S.si[i] : (where == 1 ? __ldcg(&g0i[i]) : __ldcg(&g1i[i]));
+    __syncthreads();
+    const int hu = build_chain<BLOCK>(S, UX, UI, (int)ru + 2, -1, g0, g0i, g1, g1i, &where);
+    for (int k = threadIdx.x; k < hu - 2; k += BLOCK) {
+      const int q = hu - 2 - k;
+      out[hl + k] = where == 0 ? S.si[q] : (where == 1 ? __ldcg(&g0i[q]) : __ldcg(&g1i[q]));
+    }
+    if (threadIdx.x == 0) a.hcount[inst] = (u32)(hl + hu - 2);
+    __syncthreads();
+  }
+}
+
+// Output: exclusive scan of the hull sizes, then every hull copied to its
+// offset (single block for the scan, all blocks for the copy).
+__global__ void k_batch_scan(const u32* __restrict__ hcount, int B, long long* out_off, long long cap,
+                             u32* error) {
+  __shared__ long long s_w[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int per = (B + blockDim.x - 1) / blockDim.x;
+  const int lo = min(B, (int)threadIdx.x * per), hi = min(B, lo + per);
+  long long sum = 0;
+  for (int i = lo; i < hi; ++i) sum += hcount[i];
+  long long inc = sum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  long long off = 0;
+  for (int w = 0; w < wid; ++w) off += s_w[w];
+  long long r = off + inc - sum;
+  for (int i = lo; i < hi; ++i) { out_off[i] = r; r += hcount[i]; }
+  if (threadIdx.x == blockDim.x - 1) {
+    out_off[B] = off + inc;
+    if (off + inc > cap) atomicOr(error, ERR_CAPACITY);
+  }
+}
+
+__global__ void k_batch_copy(const u32* __restrict__ hcount, const long long* __restrict__ slot0,
+                             const int* __restrict__ out_tmp, const long long* __restrict__ out_off,
+                             int B, int* out, long long cap) {
+  if (out_off[B] > cap) return;
+  for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const u32 h = hcount[i];
+    const long long o = out_off[i], s0 = slot0[i];
+    for (u32 j = threadIdx.x; j < h; j += blockDim.x) out[o + j] = out_tmp[s0 + j];
+  }
+}
+
+}  // namespace
+
+int batch_pad() { return 2 * Smem<512>::CHUNK + 16; }
+int batch_max_instance() { return BT_MAX_CHUNKS * Smem<256>::CHUNK - 8; }
+
+size_t batch_smem(int block) {
+  return block == 512 ? sizeof(Smem<512>) : sizeof(Smem<256>);
+}
+
+cudaError_t batch_configure(int* occ256, int* occ512) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem<256>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(Smem<512>));
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ256, k_batch<256>, 256, sizeof(Smem<256>));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ512, k_batch<512>, 512, sizeof(Smem<512>));
+}
+
+cudaError_t launch_batch(int block, int grid, const BatchLaunch& L, cudaStream_t st) {
+  BatchArgs a;
+  a.xy = L.xy; a.offsets = L.offsets; a.order = L.order; a.nb = L.nb; a.queue = L.queue;
+  a.slot0 = L.slot0; a.ka = L.ka; a.kb = L.kb; a.ia = L.ia; a.ib = L.ib;
+  a.lxy = L.lxy; a.lidx = L.lidx; a.uxy = L.uxy; a.uidx = L.uidx;
+  a.out_tmp = L.out_tmp; a.hcount = L.hcount; a.error = L.error;
+  if (L.nb <= 0) return cudaSuccess;
+  if (block == 512) k_batch<512><<<grid, 512, sizeof(Smem<512>), st>>>(a);
+  else k_batch<256><<<grid, 256, sizeof(Smem<256>), st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_output(const u32* hcount, const long long* slot0, const int* out_tmp,
+                                int B, long long* out_off, int* out, long long cap, u32* error,
+                                int grid, cudaStream_t st) {
+  k_batch_scan<<<1, 1024, 0, st>>>(hcount, B, out_off, cap, error);
+  k_batch_copy<<<grid, 256, 0, st>>>(hcount, slot0, out_tmp, out_off, B, out, cap);
+  return cudaGetLastError();
+}
+
+}  // namespace gbh

@@ -1,0 +1,96 @@
+// Device helpers for monotone chains over lexicographically sorted points
+// (Section 2.1 step 8), shared by the single-hull finalisation (K5) and the
+// batched kernel: accessors, the turn test, the tangent search and the
+// warp-cooperative bridge search that merges two adjacent chains.
+//
+// Two chains over points that are lexicographically separated (every
+// point of A before every point of B) merge at their common tangent: with
+// t(i) the first j where a_i -> b_j -> b_j+1 turns strictly (the farthest
+// tangent point of B seen from a_i), the merged chain keeps a_0..a_i* and
+// b_t(i*).. where i* is the first i at which a_i+1 is on or beyond the line
+// a_i -> b_t(i).  Both predicates are monotone along convex chains, so a
+// warp finds i* by a 32-ary search whose probes each binary-search t.
+// sign = +1 builds the lower chain (left turns), -1 the upper chain.
+#pragma once
+
+#include "hull_internal.cuh"
+
+namespace gbh {
+namespace chain {
+
+struct SmemChain {
+  const int* x;
+  const int* y;
+  __device__ __forceinline__ int2 operator()(int i) const { return make_int2(x[i], y[i]); }
+};
+struct GlobalChain {
+  const int2* xy;
+  __device__ __forceinline__ int2 operator()(int i) const { return __ldcg(&xy[i]); }
+};
+
+__device__ __forceinline__ long long turn(int sgn, int2 a, int2 b, int2 c) {
+  long long o = orient(a.x, a.y, b.x, b.y, c.x, c.y);
+  return sgn > 0 ? o : -o;
+}
+
+// First j in [0, beta - 1) with a strict turn a -> b_j -> b_j+1, else beta - 1.
+template <class Acc>
+__device__ __forceinline__ int tangent(const Acc& B, int beta, int2 a, int sgn) {
+  int lo = 0, hi = beta - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (turn(sgn, a, B(mid), B(mid + 1)) > 0) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Warp-cooperative bridge search; all lanes return the same (i*, j*).
+template <class AccA, class AccB>
+__device__ __forceinline__ void bridge(const AccA& A, int alpha, const AccB& B, int beta, int sgn, int& istar,
+                       int& jstar) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = alpha - 1;               // the predicate holds at hi
+  while (hi > lo) {
+    const int span = hi - lo;
+    const int q = (span <= 32) ? lo + lane : lo + (int)(((long long)span * lane) >> 5);
+    bool pv = true;
+    if (q < hi) {
+      const int2 a = A(q);
+      const int t = tangent(B, beta, a, sgn);
+      pv = turn(sgn, a, B(t), A(q + 1)) >= 0;
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, pv);
+    const int f = m ? (__ffs(m) - 1) : 32;
+    const int qprev = __shfl_sync(0xFFFFFFFFu, q, f > 0 ? f - 1 : 0);
+    const int qf = __shfl_sync(0xFFFFFFFFu, q, f < 32 ? f : 31);
+    if (f == 0) {
+      hi = lo;
+    } else {
+      lo = qprev + 1;
+      if (f < 32) hi = qf;
+    }
+  }
+  istar = lo;
+  jstar = tangent(B, beta, A(lo), sgn);
+}
+
+// Stack-based chain of l <= K points held in shared memory at [b, b + l),
+// built in place (the stack never overtakes the read position).  Returns
+// the chain length.
+__device__ __forceinline__ int leaf_chain(int* sx, int* sy, int* si, int b, int l, int sgn) {
+  int k = 0;
+  for (int i = 0; i < l; ++i) {
+    const int2 p = make_int2(sx[b + i], sy[b + i]);
+    const int pid = si[b + i];
+    while (k >= 2 && turn(sgn, make_int2(sx[b + k - 2], sy[b + k - 2]),
+                          make_int2(sx[b + k - 1], sy[b + k - 1]), p) <= 0)
+      --k;
+    sx[b + k] = p.x; sy[b + k] = p.y; si[b + k] = pid;
+    ++k;
+  }
+  return k;
+}
+
+}  // namespace chain
+}  // namespace gbh

@@ -56,4 +56,27 @@ cudaError_t launch_k5(const int2* lo_xy, const int* lo_idx, const int2* up_xy, c
                       Plan* plan, int2* h0_xy, int* h0_idx, int2* h1_xy, int* h1_idx, u32* cnt0,
                       u32* cnt1, int4* jobs, int* out, long long cap, int grid, cudaStream_t st);
 
+struct BatchLaunch {
+  const int* xy;
+  const long long* offsets;
+  const int* order;
+  int nb;
+  u32* queue;
+  const long long* slot0;
+  u64* ka; u64* kb; u32* ia; u32* ib;
+  int2* lxy; int* lidx; int2* uxy; int* uidx;
+  int* out_tmp;
+  u32* hcount;
+  u32* error;
+};
+
+int batch_pad();
+int batch_max_instance();
+size_t batch_smem(int block);
+cudaError_t batch_configure(int* occ256, int* occ512);
+cudaError_t launch_batch(int block, int grid, const BatchLaunch& L, cudaStream_t st);
+cudaError_t launch_batch_output(const u32* hcount, const long long* slot0, const int* out_tmp,
+                                int B, long long* out_off, int* out, long long cap, u32* error,
+                                int grid, cudaStream_t st);
+
 }  // namespace gbh

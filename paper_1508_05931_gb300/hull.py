@@ -29,7 +29,7 @@ MAX_POINTS = (1 << 30) - 1
 
 class hull_config(ctypes.Structure):
     _fields_ = [("proposal", ctypes.c_int), ("collect_stats", ctypes.c_int),
-                ("spin_limit", ctypes.c_uint32), ("reserved", ctypes.c_int)]
+                ("spin_limit", ctypes.c_uint32), ("autotune", ctypes.c_int)]
 
 
 class hull_stats(ctypes.Structure):
@@ -60,6 +60,7 @@ _sig = {
     "hull_compute_batched": ([_P, _P, _P, ctypes.c_int32, _P, _I64, _P, _P], ctypes.c_int),
     "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
+    "hull_batched_max_instance": ([], ctypes.c_int64),
     "hull_set_profiling": ([_P, ctypes.c_int], ctypes.c_int),
     "hull_get_profile": ([_P, ctypes.POINTER(hull_profile)], ctypes.c_int),
     "hull_stage_extremes": ([_P, _P, _I64, _P, _P], ctypes.c_int),
@@ -122,9 +123,9 @@ class Context:
     """One hull_ctx: owns the device workspace for one GPU."""
 
     def __init__(self, device: int = 0, proposal: int = 0, collect_stats: bool = False,
-                 spin_limit: int = 0):
+                 spin_limit: int = 0, autotune: bool = False):
         self.device = int(device)
-        cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), 0)
+        cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), int(bool(autotune)))
         h = ctypes.c_void_p()
         _check(_lib.hull_create(ctypes.byref(h), self.device, ctypes.byref(cfg)), "hull_create")
         self._h = h
@@ -303,6 +304,7 @@ hull_compute_host = _lib.hull_compute_host
 hull_compute_batched = _lib.hull_compute_batched
 hull_compute_noalloc = _lib.hull_compute_noalloc
 hull_last_stats = _lib.hull_last_stats
+hull_batched_max_instance = _lib.hull_batched_max_instance
 hull_set_profiling = _lib.hull_set_profiling
 hull_get_profile = _lib.hull_get_profile
 hull_stage_extremes = _lib.hull_stage_extremes

@@ -1,0 +1,124 @@
+"""Batched mode: every instance's hull equals the oracle's, bit-exact, in a
+single hull_compute_batched call (mixed sizes across both size buckets,
+empty and degenerate instances, the uneven-size batch generator)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_05931_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(hull_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hull_lib.Context(0)
+    yield c
+    c.close()
+
+
+def run_batch(ctx, parts, cap=None):
+    offs = np.zeros(len(parts) + 1, np.int64)
+    offs[1:] = np.cumsum([len(p) for p in parts])
+    pts = np.concatenate(parts, axis=0) if parts else np.zeros((0, 2), np.int32)
+    t = torch.as_tensor(np.ascontiguousarray(pts, dtype=np.int32)).cuda()
+    out = torch.empty(max(cap if cap is not None else len(pts), 1), dtype=torch.int32, device="cuda")
+    o, oo = ctx.compute_batched(t, torch.as_tensor(offs), out=out)
+    return o.cpu().numpy(), oo.cpu().numpy()
+
+
+def check(parts, o, oo):
+    assert len(oo) == len(parts) + 1 and oo[0] == 0
+    for i, p in enumerate(parts):
+        got = o[oo[i]:oo[i + 1]]
+        assert got.tolist() == oracle.hull(p).tolist(), (i, len(p))
+
+
+def mixed_parts(seed):
+    rng = np.random.default_rng(seed)
+    parts = []
+    sizes = [0, 1, 2, 3, 5, 31, 100, 999, 2047, 2048, 2049, 4097, 16384, 16385, 50000, 120001, 300000]
+    for k, n in enumerate(sizes):
+        fam = k % 5
+        if fam == 0:
+            p = W.uniform_square(n, 1 << 29, seed + k)
+        elif fam == 1:
+            p = W.uniform_disk(n, 2.0 ** 29, seed + k)
+        elif fam == 2:
+            p = W.gaussian(n, 2.0 ** 26, seed + k)
+        elif fam == 3:
+            p = W.near_circle(n, 2.0 ** 18, seed + k)
+        else:
+            p = rng.integers(-3, 4, size=(n, 2)).astype(np.int32)
+        parts.append(p)
+    parts.append(np.array([[7, 7]] * 5000, np.int32))            # all identical
+    t = np.arange(-3000, 3000)
+    parts.append(np.stack([t * 2, t * 3], axis=1).astype(np.int32))  # collinear
+    parts.append(W.parabola_lattice(5000))                        # all vertices
+    return parts
+
+
+def test_mixed_batch(ctx):
+    parts = mixed_parts(3)
+    o, oo = run_batch(ctx, parts)
+    check(parts, o, oo)
+
+
+def test_single_and_empty_batch(ctx):
+    parts = [W.uniform_disk(77777, 1e6, 5)]
+    check(parts, *run_batch(ctx, parts))
+    o, oo = run_batch(ctx, [])
+    assert oo.tolist() == [0]
+
+
+def test_uneven_batch_generator(ctx):
+    pts, offs, fam = W.batch(b=300, seed=11, cap=2e7, lo=1e3, hi=3e5)
+    parts = [pts[offs[i]:offs[i + 1]] for i in range(len(offs) - 1)]
+    o, oo = run_batch(ctx, parts)
+    check(parts, o, oo)
+
+
+def test_batch_repeat_deterministic(ctx):
+    parts = mixed_parts(9)
+    a = run_batch(ctx, parts)
+    for _ in range(3):
+        b = run_batch(ctx, parts)
+        assert np.array_equal(a[0][:a[1][-1]], b[0][:b[1][-1]]) and np.array_equal(a[1], b[1])
+
+
+def test_batch_capacity_error(ctx, hull_lib):
+    parts = [W.uniform_disk(5000, 1e6, 1), W.uniform_square(5000, 1000, 2)]
+    total = sum(len(oracle.hull(p)) for p in parts)
+    with pytest.raises(hull_lib.HullError) as e:
+        run_batch(ctx, parts, cap=total - 1)
+    assert e.value.code == hull_lib.HULL_ECAPACITY
+
+
+def test_batch_range_error(ctx, hull_lib):
+    lim = 1 << 29
+    parts = [W.uniform_square(100, 10, 1), np.array([[0, 0], [lim + 1, 5]], np.int32)]
+    with pytest.raises(hull_lib.HullError) as e:
+        run_batch(ctx, parts)
+    assert e.value.code == hull_lib.HULL_ERANGE
+
+
+def test_batch_autotune(hull_lib, tmp_path):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    os.environ["GBHULL_AUTOTUNE_CACHE"] = str(tmp_path / "tune.json")
+    try:
+        parts = mixed_parts(21)
+        with hull_lib.Context(0, autotune=True) as c:
+            check(parts, *run_batch(c, parts))
+        assert (tmp_path / "tune.json").exists()
+        txt = (tmp_path / "tune.json").read_text()
+        assert "batched_small" in txt and "batched_large" in txt
+        with hull_lib.Context(0, autotune=True) as c:      # reads the cache
+            check(parts, *run_batch(c, parts))
+    finally:
+        del os.environ["GBHULL_AUTOTUNE_CACHE"]
