@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--n", type=int, default=20_000_000, help="points per hull")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed hull per input set, for a profiler to capture; prints no JSON")
     return ap.parse_args()
@@ -140,6 +141,36 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def bench_batched(hull, torch, stream, plain_value, args):
+    """4,096 uneven hulls (log-uniform sizes in [1e3, 1e6], total capped at
+    2.5e8 points, square / disk / Gaussian families) in one
+    hull_compute_batched call per step."""
+    from paper_1508_05931_gb300 import workloads as W
+    pts, offs, fam = W.batch()
+    dp = torch.as_tensor(pts).cuda()
+    do = torch.as_tensor(offs).cuda()
+    out = torch.empty(len(pts), dtype=torch.int32, device="cuda")
+    oo = torch.empty(len(offs), dtype=torch.int64, device="cuda")
+    with hull.Context(torch.cuda.current_device(), autotune=True) as c:
+        for _ in range(2):
+            c.compute_batched(dp, do, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, args.steps // 4)
+        e0.record(stream)
+        for _ in range(k):
+            _, oo = c.compute_batched(dp, do, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+    v = len(pts) / (ms / 1e3) / 1e6
+    return {"value": v, "unit": "Mpoints/s", "ms_per_batch": ms, "instances": len(offs) - 1,
+            "points": int(len(pts)), "hull_vertices": int(oo[-1].item()), "steps": k,
+            "vs_plain": v / plain_value,
+            "config": "4096 instances, sizes log-uniform [1e3,1e6] capped at 2.5e8 points total, "
+                      "families square/disk/gaussian(2^26), seed 4; one call per step, autotuned"}
 
 
 def run_reference(args, rank, world):
@@ -298,6 +329,8 @@ def main():
             "roofline": roofline}
     if clocks:
         line["clocks"] = clocks
+    if not args.no_batched:
+        line["batched"] = bench_batched(hull, torch, stream, value, args)
     if rank == 0 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -110,6 +110,43 @@ hull_status hull_compute_batched(hull_ctx *ctx, const int32_t *d_xy, const int64
                                  int32_t B, int32_t *d_out, int64_t cap, int64_t *d_out_offsets,
                                  void *stream);
 
+/* ---- learned filter proposal (the project's addition beside Section 3.1's
+ * quadrilateral): an MLP 64 -> 128 -> 128 -> 32 (ReLU) scores 32 directions
+ * from features of a strided sample of the input; the filter polygon is the
+ * exact hull of the quadrilateral's corners and the extremes of the 8 best
+ * directions (used when it encloses more area than the quadrilateral).
+ * Enabled by hull_config.proposal = 1 once parameters are set or loaded;
+ * without parameters the quadrilateral is used.  Parameters (FP32 master,
+ * FP16 at inference) are laid out W1[128][64], b1[128], W2[128][128],
+ * b2[128], W3[32][128], b3[32]. ---- */
+int64_t hull_mlp_num_params(void);
+hull_status hull_mlp_set_params(hull_ctx *ctx, const float *h_params, int64_t count);
+hull_status hull_mlp_get_params(const hull_ctx *ctx, float *h_params, int64_t count);
+/* Checkpoint: 8 uint32 header (magic "GBHL", version 1, 64, 128, 128, 32,
+ * parameter count, CRC-32 of the parameters) then the FP32 parameters. */
+hull_status hull_save_proposal(const hull_ctx *ctx, const char *path);
+hull_status hull_load_proposal(hull_ctx *ctx, const char *path);
+/* Features of the strided sample (d_feat device float[64]: 32 angular bins
+ * of point fractions, then 32 of maximum radius over the largest) and the
+ * sample's extreme point per direction j (d_ext int32[32] indices,
+ * d_ext_xy int32[32][2]); u_j = (cos 2 pi j/32, sin 2 pi j/32). */
+hull_status hull_learned_features(hull_ctx *ctx, const int32_t *d_xy, int64_t n, float *d_feat,
+                                  int32_t *d_ext, int32_t *d_ext_xy, void *stream);
+/* Training labels: h_labels[j] = fraction of points strictly inside
+ * hull(quadrilateral corners + extreme j) minus the fraction strictly inside
+ * the quadrilateral (*h_quad_frac), counted exactly. */
+hull_status hull_learned_labels(hull_ctx *ctx, const int32_t *d_xy, int64_t n, float *h_labels,
+                                float *h_quad_frac, void *stream);
+/* Forward pass of B feature rows (d_X device float[B][64]) into d_Z
+ * (device float[B][32]); gradient of the mean squared error against d_Y
+ * (device float[B][32]) into h_grad (host, hull_mlp_num_params floats);
+ * one Adam step (beta 0.9 / 0.999, eps 1e-8) at learning rate lr. */
+hull_status hull_mlp_forward(hull_ctx *ctx, const float *d_X, int32_t B, float *d_Z, void *stream);
+hull_status hull_mlp_gradient(hull_ctx *ctx, const float *d_X, const float *d_Y, int32_t B,
+                              float *h_grad, float *h_loss, void *stream);
+hull_status hull_mlp_train_step(hull_ctx *ctx, const float *d_X, const float *d_Y, int32_t B,
+                                float lr, float *h_loss, void *stream);
+
 /* Largest instance size hull_compute_batched accepts. */
 int64_t hull_batched_max_instance(void);
 

@@ -94,6 +94,22 @@ struct hull_ctx {
   cudaEvent_t bev[2] = {nullptr, nullptr};
   int occ_b256 = 1, occ_b512 = 1;
   int tuned_block[2] = {0, 0};  // per bucket (small, large); 0 = not tuned yet
+  // learned proposal
+  bool have_weights = false;
+  float* W = nullptr;           // FP32 master parameters
+  void* W16 = nullptr;          // FP16 copies used by inference / forward
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  int adam_step = 0;
+  float* feat = nullptr;        // 64 features
+  int* ext = nullptr;           // 32 direction extremes (indices)
+  int* ext_xy = nullptr;        // and their coordinates
+  unsigned long long* lab_cnt = nullptr;   // 33 label counters
+  float* d_loss = nullptr;
+  float* grad = nullptr;
+  size_t train_cap = 0;         // rows of the training scratch
+  float* act = nullptr;
+  float* scratch = nullptr;
 };
 
 namespace {
@@ -237,6 +253,13 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
   mark(c, 0, st);
   cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (c->cfg.proposal == 1 && c->have_weights) {
+    // Learned filter polygon: sampled features, MLP, exact hull of the
+    // chosen extremes and the quadrilateral's corners.
+    e = launch_features(d_xy, n, c->feat, c->ext, c->ext_xy, st);
+    if (e == cudaSuccess) e = launch_infer(c->feat, c->W16, c->ext_xy, c->plan, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
   e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2, c->num_sms, t2), st);
@@ -387,6 +410,24 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
     return HULL_ENOMEM;
   }
   std::memset(c->h_plan, 0, sizeof(Plan));
+  {
+    const size_t np = (size_t)mlp_num_params();
+    if (cudaMalloc(&c->W, np * 4) != cudaSuccess || cudaMalloc(&c->W16, np * 2) != cudaSuccess ||
+        cudaMalloc(&c->adam_m, np * 4) != cudaSuccess || cudaMalloc(&c->adam_v, np * 4) != cudaSuccess ||
+        cudaMalloc(&c->grad, np * 4) != cudaSuccess || cudaMalloc(&c->feat, 64 * 4) != cudaSuccess ||
+        cudaMalloc(&c->ext, 32 * 4) != cudaSuccess || cudaMalloc(&c->ext_xy, 64 * 4) != cudaSuccess ||
+        cudaMalloc(&c->lab_cnt, 33 * 8) != cudaSuccess || cudaMalloc(&c->d_loss, 16) != cudaSuccess) {
+      cudaGetLastError();
+      *out = c;
+      hull_destroy(c);
+      *out = nullptr;
+      return HULL_ENOMEM;
+    }
+    cudaMemset(c->W, 0, np * 4);
+    cudaMemset(c->W16, 0, np * 2);
+    cudaMemset(c->adam_m, 0, np * 4);
+    cudaMemset(c->adam_v, 0, np * 4);
+  }
   *out = c;
   return HULL_OK;
 }
@@ -400,6 +441,10 @@ void hull_destroy(hull_ctx* c) {
   if (c->hs.d_out) cudaFree(c->hs.d_out);
   for (int k = 0; k <= HULL_NUM_STAGES; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  for (void* p : {(void*)c->W, c->W16, (void*)c->adam_m, (void*)c->adam_v, (void*)c->grad, (void*)c->feat,
+                  (void*)c->ext, (void*)c->ext_xy, (void*)c->lab_cnt, (void*)c->d_loss, (void*)c->act,
+                  (void*)c->scratch})
+    if (p) cudaFree(p);
   if (c->bw.base) cudaFree(c->bw.base);
   if (c->bw.slot0) cudaFree(c->bw.slot0);
   if (c->bw.h_off) cudaFreeHost(c->bw.h_off);
@@ -639,6 +684,179 @@ hull_status hull_stage_chain(hull_ctx* c, const int32_t* d_xy, int64_t m, int32_
   *h_lower = c->h_plan->h_lo;
   *h_upper = c->h_plan->h_up;
   return r;
+}
+
+// ---------------------------------------------------------------- learned
+
+static uint32_t crc32_bytes(const void* data, size_t len) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < len; ++i) {
+    c ^= p[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return ~c;
+}
+
+int64_t hull_mlp_num_params(void) { return mlp_num_params(); }
+
+hull_status hull_mlp_set_params(hull_ctx* c, const float* h_params, int64_t count) {
+  if (!c || !h_params || count != mlp_num_params()) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaError_t e = cudaMemcpy(c->W, h_params, (size_t)count * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_to_half(c->W, c->W16, (int)count, nullptr);
+  if (e == cudaSuccess) e = cudaMemset(c->adam_m, 0, (size_t)count * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->adam_v, 0, (size_t)count * 4);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  c->adam_step = 0;
+  c->have_weights = true;
+  return HULL_OK;
+}
+
+hull_status hull_mlp_get_params(const hull_ctx* c, float* h_params, int64_t count) {
+  if (!c || !h_params || count != mlp_num_params()) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaError_t e = cudaMemcpy(h_params, c->W, (size_t)count * 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
+hull_status hull_save_proposal(const hull_ctx* c, const char* path) {
+  if (!c || !path) return HULL_EINVAL;
+  const int64_t np = mlp_num_params();
+  std::vector<float> w((size_t)np);
+  hull_status r = hull_mlp_get_params(c, w.data(), np);
+  if (r != HULL_OK) return r;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return HULL_EINVAL;
+  const uint32_t hdr[8] = {0x4C484247u /* "GBHL" */, 1u, 64u, 128u, 128u, 32u, (uint32_t)np,
+                           crc32_bytes(w.data(), w.size() * 4)};
+  const bool ok = std::fwrite(hdr, 4, 8, f) == 8 && std::fwrite(w.data(), 4, w.size(), f) == w.size();
+  std::fclose(f);
+  return ok ? HULL_OK : HULL_EINVAL;
+}
+
+hull_status hull_load_proposal(hull_ctx* c, const char* path) {
+  if (!c || !path) return HULL_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return HULL_EINVAL;
+  uint32_t hdr[8];
+  const int64_t np = mlp_num_params();
+  std::vector<float> w((size_t)np);
+  const bool ok = std::fread(hdr, 4, 8, f) == 8 && hdr[0] == 0x4C484247u && hdr[1] == 1u && hdr[2] == 64u &&
+                  hdr[3] == 128u && hdr[4] == 128u && hdr[5] == 32u && hdr[6] == (uint32_t)np &&
+                  std::fread(w.data(), 4, w.size(), f) == w.size();
+  std::fclose(f);
+  if (!ok || crc32_bytes(w.data(), w.size() * 4) != hdr[7]) return HULL_EINVAL;
+  return hull_mlp_set_params(c, w.data(), np);
+}
+
+hull_status hull_learned_features(hull_ctx* c, const int32_t* d_xy, int64_t n, float* d_feat,
+                                  int32_t* d_ext, int32_t* d_ext_xy, void* stream) {
+  if (!c || !d_xy || n < 1 || n > (int64_t)kMaxN || !aligned8(d_xy) || !d_feat || !d_ext || !d_ext_xy)
+    return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_features(d_xy, (u32)n, d_feat, d_ext, d_ext_xy, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
+hull_status hull_learned_labels(hull_ctx* c, const int32_t* d_xy, int64_t n, float* h_labels,
+                                float* h_quad_frac, void* stream) {
+  if (!c || !d_xy || n < 1 || n > (int64_t)kMaxN || !aligned8(d_xy) || !h_labels) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  // Quadrilateral from K1, the 32 extremes from K6, then exact counts.
+  cudaError_t e = launch_k1(d_xy, (u32)n, c->cfg.spin_limit, c->plan, c->ws.partials,
+                            k1_grid((u32)n, c->num_sms), st);
+  if (e == cudaSuccess) e = launch_features(d_xy, (u32)n, c->feat, c->ext, c->ext_xy, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  if (r != HULL_OK) return r;
+  int quad[8];
+  const int nq = c->h_plan->ncorner;
+  for (int j = 0; j < nq && j < 4; ++j) { quad[2 * j] = c->h_plan->cx[j]; quad[2 * j + 1] = c->h_plan->cy[j]; }
+  int* d_quad = c->ws.aux;
+  e = cudaMemcpyAsync(d_quad, quad, sizeof(quad), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lab_cnt, 0, 33 * 8, st);
+  if (e == cudaSuccess) e = launch_labels(d_xy, (u32)n, d_quad, nq, c->ext_xy, c->lab_cnt, c->num_sms * 4, st);
+  unsigned long long cnt[33];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, c->lab_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int j = 0; j < 32; ++j) h_labels[j] = (float)((double)((long long)cnt[j] - (long long)cnt[32]) / (double)n);
+  if (h_quad_frac) *h_quad_frac = (float)((double)cnt[32] / (double)n);
+  return HULL_OK;
+}
+
+static hull_status ensure_train(hull_ctx* c, int B) {
+  if ((size_t)B <= c->train_cap) return HULL_OK;
+  if (c->act) cudaFree(c->act);
+  if (c->scratch) cudaFree(c->scratch);
+  c->act = nullptr; c->scratch = nullptr; c->train_cap = 0;
+  const size_t rows = (size_t)B;
+  if (cudaMalloc(&c->act, rows * (128 + 128 + 32) * 4) != cudaSuccess ||
+      cudaMalloc(&c->scratch, rows * (128 + 128 + 32) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return HULL_ENOMEM;
+  }
+  c->train_cap = rows;
+  return HULL_OK;
+}
+
+hull_status hull_mlp_forward(hull_ctx* c, const float* d_X, int32_t B, float* d_Z, void* stream) {
+  if (!c || !d_X || !d_Z || B < 1) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_train(c, B);
+  if (r != HULL_OK) return r;
+  cudaError_t e = mlp_forward(c->W, d_X, B, c->act, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_Z, c->act + (size_t)B * 256, (size_t)B * 32 * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
+hull_status hull_mlp_gradient(hull_ctx* c, const float* d_X, const float* d_Y, int32_t B, float* h_grad,
+                              float* h_loss, void* stream) {
+  if (!c || !d_X || !d_Y || B < 1) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_train(c, B);
+  if (r != HULL_OK) return r;
+  cudaError_t e = mlp_forward(c->W, d_X, B, c->act, st);
+  if (e == cudaSuccess) e = mlp_backward(c->W, d_X, d_Y, B, c->act, c->grad, c->d_loss, c->scratch, st);
+  if (e == cudaSuccess && h_grad)
+    e = cudaMemcpyAsync(h_grad, c->grad, (size_t)mlp_num_params() * 4, cudaMemcpyDeviceToHost, st);
+  float loss = 0.f;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, c->d_loss, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (h_loss) *h_loss = loss;
+  return HULL_OK;
+}
+
+hull_status hull_mlp_train_step(hull_ctx* c, const float* d_X, const float* d_Y, int32_t B, float lr,
+                                float* h_loss, void* stream) {
+  if (!c || !d_X || !d_Y || B < 1 || !(lr > 0.f)) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_train(c, B);
+  if (r != HULL_OK) return r;
+  cudaError_t e = mlp_forward(c->W, d_X, B, c->act, st);
+  if (e == cudaSuccess) e = mlp_backward(c->W, d_X, d_Y, B, c->act, c->grad, c->d_loss, c->scratch, st);
+  if (e == cudaSuccess) e = mlp_adam(c->W, c->grad, c->adam_m, c->adam_v, c->adam_step + 1, lr, c->W16, st);
+  float loss = 0.f;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, c->d_loss, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  c->adam_step += 1;
+  c->have_weights = true;
+  if (h_loss) *h_loss = loss;
+  return HULL_OK;
 }
 
 int64_t hull_batched_max_instance(void) { return (int64_t)batch_max_instance(); }

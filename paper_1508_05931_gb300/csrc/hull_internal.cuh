@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace gbh {
@@ -19,7 +20,7 @@ typedef unsigned long long u64;
 typedef unsigned int u32;
 
 constexpr int kCoordLimit = 1 << 29;     // |x|, |y| <= 2^29
-constexpr int kMaxCorners = 8;           // filter polygon: 4 (quad) or up to 8 (learned)
+constexpr int kMaxCorners = 12;          // filter polygon: 4 (quad) or up to 12 (learned)
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;            // 64-bit keys / 8-bit digits

@@ -56,6 +56,10 @@ __device__ __forceinline__ bool inside_any(const Edges& E, int k, int x, int y) 
     case 6: return strictly_inside<6>(E, x, y);
     case 7: return strictly_inside<7>(E, x, y);
     case 8: return strictly_inside<8>(E, x, y);
+    case 9: return strictly_inside<9>(E, x, y);
+    case 10: return strictly_inside<10>(E, x, y);
+    case 11: return strictly_inside<11>(E, x, y);
+    case 12: return strictly_inside<12>(E, x, y);
     default: return false;
   }
 }

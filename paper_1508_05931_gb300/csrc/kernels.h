@@ -79,4 +79,17 @@ cudaError_t launch_batch_output(const u32* hcount, const long long* slot0, const
                                 int B, long long* out_off, int* out, long long cap, u32* error,
                                 int grid, cudaStream_t st);
 
+int mlp_num_params();
+cudaError_t launch_features(const int* xy, u32 n, float* feat, int* ext, int* ext_xy, cudaStream_t st);
+cudaError_t launch_infer(const float* feat, const void* w16, const int* ext_xy, Plan* plan,
+                         cudaStream_t st);
+cudaError_t launch_labels(const int* xy, u32 n, const int* quad, int nq, const int* ext_xy,
+                          unsigned long long* counts, int grid, cudaStream_t st);
+cudaError_t launch_to_half(const float* w, void* w16, int count, cudaStream_t st);
+cudaError_t mlp_forward(const float* W, const float* X, int B, float* act, cudaStream_t st);
+cudaError_t mlp_backward(const float* W, const float* X, const float* Y, int B, const float* act,
+                         float* grad, float* loss, float* scratch, cudaStream_t st);
+cudaError_t mlp_adam(float* W, const float* grad, float* m, float* v, int step, float lr,
+                     void* w16, cudaStream_t st);
+
 }  // namespace gbh

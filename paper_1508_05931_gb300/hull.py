@@ -61,6 +61,16 @@ _sig = {
     "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
     "hull_batched_max_instance": ([], ctypes.c_int64),
+    "hull_mlp_num_params": ([], ctypes.c_int64),
+    "hull_mlp_set_params": ([_P, _P, _I64], ctypes.c_int),
+    "hull_mlp_get_params": ([_P, _P, _I64], ctypes.c_int),
+    "hull_save_proposal": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "hull_load_proposal": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "hull_learned_features": ([_P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "hull_learned_labels": ([_P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "hull_mlp_forward": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "hull_mlp_gradient": ([_P, _P, _P, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
+    "hull_mlp_train_step": ([_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P, _P], ctypes.c_int),
     "hull_set_profiling": ([_P, ctypes.c_int], ctypes.c_int),
     "hull_get_profile": ([_P, ctypes.POINTER(hull_profile)], ctypes.c_int),
     "hull_stage_extremes": ([_P, _P, _I64, _P, _P], ctypes.c_int),
@@ -223,6 +233,70 @@ class Context:
                 "survivors": p.survivors, "second_round": p.second_round,
                 "ms": {STAGE_NAMES[k]: p.ms[k] for k in range(NUM_STAGES)}}
 
+    # ------------------------------------------------------------ learned
+    def mlp_set_params(self, params):
+        w = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        _check(_lib.hull_mlp_set_params(self._h, w.ctypes.data_as(ctypes.c_void_p), w.size),
+               "hull_mlp_set_params")
+
+    def mlp_get_params(self) -> np.ndarray:
+        w = np.empty(int(_lib.hull_mlp_num_params()), dtype=np.float32)
+        _check(_lib.hull_mlp_get_params(self._h, w.ctypes.data_as(ctypes.c_void_p), w.size),
+               "hull_mlp_get_params")
+        return w
+
+    def save_proposal(self, path: str):
+        _check(_lib.hull_save_proposal(self._h, os.fsencode(path)), "hull_save_proposal")
+
+    def load_proposal(self, path: str):
+        _check(_lib.hull_load_proposal(self._h, os.fsencode(path)), "hull_load_proposal")
+
+    def learned_features(self, pts, stream=None):
+        """(features float32[64], extreme indices int32[32], extreme xy int32[32, 2])."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        pts = _as_points(pts, dev)
+        f = torch.empty(64, dtype=torch.float32, device=dev)
+        e = torch.empty(32, dtype=torch.int32, device=dev)
+        exy = torch.empty((32, 2), dtype=torch.int32, device=dev)
+        _check(_lib.hull_learned_features(self._h, _ptr(pts), pts.shape[0], _ptr(f), _ptr(e), _ptr(exy),
+                                          _stream_handle(stream)), "hull_learned_features")
+        return f.cpu().numpy(), e.cpu().numpy(), exy.cpu().numpy()
+
+    def learned_labels(self, pts, stream=None):
+        """(labels float32[32], quadrilateral discard fraction)."""
+        torch = _torch()
+        pts = _as_points(pts, torch.device("cuda", self.device))
+        lab = np.empty(32, dtype=np.float32)
+        q = ctypes.c_float()
+        _check(_lib.hull_learned_labels(self._h, _ptr(pts), pts.shape[0], lab.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(q), _stream_handle(stream)), "hull_learned_labels")
+        return lab, q.value
+
+    def mlp_forward(self, X, stream=None):
+        torch = _torch()
+        X = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float32)).cuda(self.device)
+        Z = torch.empty((X.shape[0], 32), dtype=torch.float32, device=X.device)
+        _check(_lib.hull_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Z), _stream_handle(stream)),
+               "hull_mlp_forward")
+        return Z.cpu().numpy()
+
+    def mlp_gradient(self, X, Y, stream=None):
+        torch = _torch()
+        X = torch.as_tensor(np.ascontiguousarray(X, dtype=np.float32)).cuda(self.device)
+        Y = torch.as_tensor(np.ascontiguousarray(Y, dtype=np.float32)).cuda(self.device)
+        g = np.empty(int(_lib.hull_mlp_num_params()), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.hull_mlp_gradient(self._h, _ptr(X), _ptr(Y), X.shape[0], g.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(loss), _stream_handle(stream)), "hull_mlp_gradient")
+        return g, loss.value
+
+    def mlp_train_step(self, X_dev, Y_dev, lr: float, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(_lib.hull_mlp_train_step(self._h, _ptr(X_dev), _ptr(Y_dev), X_dev.shape[0], float(lr),
+                                        ctypes.byref(loss), _stream_handle(stream)), "hull_mlp_train_step")
+        return loss.value
+
     # ------------------------------------------------------------ stages
     def stage_extremes(self, pts, stream=None) -> np.ndarray:
         torch = _torch()
@@ -305,6 +379,16 @@ hull_compute_batched = _lib.hull_compute_batched
 hull_compute_noalloc = _lib.hull_compute_noalloc
 hull_last_stats = _lib.hull_last_stats
 hull_batched_max_instance = _lib.hull_batched_max_instance
+hull_mlp_train_step = _lib.hull_mlp_train_step
+hull_mlp_gradient = _lib.hull_mlp_gradient
+hull_mlp_forward = _lib.hull_mlp_forward
+hull_learned_labels = _lib.hull_learned_labels
+hull_learned_features = _lib.hull_learned_features
+hull_load_proposal = _lib.hull_load_proposal
+hull_save_proposal = _lib.hull_save_proposal
+hull_mlp_get_params = _lib.hull_mlp_get_params
+hull_mlp_set_params = _lib.hull_mlp_set_params
+hull_mlp_num_params = _lib.hull_mlp_num_params
 hull_set_profiling = _lib.hull_set_profiling
 hull_get_profile = _lib.hull_get_profile
 hull_stage_extremes = _lib.hull_stage_extremes
