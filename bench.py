@@ -33,6 +33,9 @@ WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk
 # The paper's best 20M-point times for the same two workloads (Table 3 square
 # 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
 PAPER_MPTS = 40.0 / 0.8645
+# Kernels per hull_compute: extremes, filter count + write, 8 radix passes,
+# region aggregate + keep + compact, finalisation.
+LAUNCHES_PER_HULL = 1 + 2 + 8 + 3 + 1
 
 
 def parse():
@@ -45,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed hull per input set, for a profiler to capture; prints no JSON")
     return ap.parse_args()
@@ -171,6 +175,95 @@ def bench_batched(hull, torch, stream, plain_value, args):
             "vs_plain": v / plain_value,
             "config": "4096 instances, sizes log-uniform [1e3,1e6] capped at 2.5e8 points total, "
                       "families square/disk/gaussian(2^26), seed 4; one call per step, autotuned"}
+
+
+def k3_traffic():
+    """DRAM bytes (read + write) of one radix pass from the committed ncu
+    capture, or None when the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k3_onesweep_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    if sha != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def _time_hulls(ctx, t, out, stream, torch, k):
+    for _ in range(2):
+        ctx.compute_raw(t, out, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        ctx.compute_raw(t, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = ctx.last_stats()
+    return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], st["learned_used"]
+
+
+def bench_learned(hull, torch, stream, args):
+    """Learned filter proposal vs the plain quadrilateral on the anisotropic
+    families at 20M points (single hull) and as a 1,024-instance batch of the
+    same 20M points.  The network is trained first, on the GPU, by the
+    library's own kernels (fixed seeds)."""
+    from paper_1508_05931_gb300 import learned as L
+    dev = torch.cuda.current_device()
+    res = {"families": {}}
+    with hull.Context(dev, proposal=1, collect_stats=True) as lc, hull.Context(dev, collect_stats=True) as pc:
+        t0 = time.perf_counter()
+        X, Y = L.make_dataset(lc, 192, seed0=1000, lo=1e5, hi=4e5)
+        t1 = time.perf_counter()
+        losses = L.train(lc, X, Y, steps=3000, lr=2e-3, batch=64)
+        torch.cuda.synchronize()
+        res["training"] = {"instances": 192, "steps": 3000, "data_s": t1 - t0,
+                           "train_s": time.perf_counter() - t1,
+                           "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-50:]))}
+        out = torch.empty(20_000_000, dtype=torch.int32, device="cuda")
+        names = ["anisotropic_gaussian", "elliptic_disk", "gaussian_clusters"]
+        k = max(3, args.steps // 4)
+        tot_p = tot_l = 0.0
+        for fam in range(3):
+            pts = torch.as_tensor(L.instance(fam, 20_000_000, 5 + fam)).cuda()
+            mp, dp_, _ = _time_hulls(pc, pts, out, stream, torch, k)
+            ml, dl, used = _time_hulls(lc, pts, out, stream, torch, k)
+            tot_p += mp; tot_l += ml
+            res["families"][names[fam]] = {"plain_ms": mp, "learned_ms": ml, "speedup": mp / ml,
+                                           "plain_discard": dp_, "learned_discard": dl, "learned_used": used,
+                                           "plain_mpts": 20.0 / mp * 1e3, "learned_mpts": 20.0 / ml * 1e3}
+            del pts
+        res["single_hull"] = {"plain_mpts": 60.0 / tot_p * 1e3, "learned_mpts": 60.0 / tot_l * 1e3,
+                              "speedup": tot_p / tot_l}
+        # 1,024-instance batch of the same families (19,531 points each)
+        parts = [L.instance(i % 3, 19531, 7000 + i) for i in range(1024)]
+        offs = np.zeros(1025, np.int64)
+        offs[1:] = np.cumsum([len(p) for p in parts])
+        bp = torch.as_tensor(np.concatenate(parts)).cuda()
+        bo = torch.as_tensor(offs).cuda()
+        bout = torch.empty(len(bp), dtype=torch.int32, device="cuda")
+        bres = {}
+        for name, c in (("plain", pc), ("learned", lc)):
+            for _ in range(2):
+                c.compute_batched(bp, bo, out=bout)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                c.compute_batched(bp, bo, out=bout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            bres[name] = {"ms": ms, "mpts": len(bp) / (ms / 1e3) / 1e6}
+        bres["speedup"] = bres["plain"]["ms"] / bres["learned"]["ms"]
+        bres["instances"] = 1024
+        bres["points"] = int(len(bp))
+        res["batch_1024"] = bres
+    return res
 
 
 def run_reference(args, rank, world):
@@ -307,7 +400,7 @@ def main():
     stage_ms = {k: v / calls for k, v in prof["ms"].items()}
     roofline = {"bound": "hbm", "kernel": "k3_onesweep (radix pass)", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                "traffic": None,
+                "traffic": k3_traffic(),
                 "algorithmic_bytes_per_launch": 24.0 * surv / calls,
                 "stage_ms_per_hull": stage_ms,
                 "k1_gbs": (8.0 * prof["points"] / calls) / (stage_ms["extremes"] / 1e3) / 1e9
@@ -323,7 +416,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "survivors_per_hull": surv / calls,
                        "second_round_per_hull": prof["second_round"] / calls},
-            "gpu_launches": args.steps * len(sets) * 12,
+            "gpu_launches": args.steps * len(sets) * LAUNCHES_PER_HULL,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
                     "d2h_bytes_per_step": 4 * sum(h_counts)},
             "roofline": roofline}
@@ -331,6 +424,8 @@ def main():
         line["clocks"] = clocks
     if not args.no_batched:
         line["batched"] = bench_batched(hull, torch, stream, value, args)
+    if not args.no_learned:
+        line["learned"] = bench_learned(hull, torch, stream, args)
     if rank == 0 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -126,7 +126,8 @@ hull_status hull_mlp_get_params(const hull_ctx *ctx, float *h_params, int64_t co
  * parameter count, CRC-32 of the parameters) then the FP32 parameters. */
 hull_status hull_save_proposal(const hull_ctx *ctx, const char *path);
 hull_status hull_load_proposal(hull_ctx *ctx, const char *path);
-/* Features of the strided sample (d_feat device float[64]: 32 angular bins
+/* Features of the strided sample i_k = floor(k n / S), S = min(n, 16384)
+ * (d_feat device float[64]: 32 angular bins
  * of point fractions, then 32 of maximum radius over the largest) and the
  * sample's extreme point per direction j (d_ext int32[32] indices,
  * d_ext_xy int32[32][2]); u_j = (cos 2 pi j/32, sin 2 pi j/32). */

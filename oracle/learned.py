@@ -1,7 +1,7 @@
 """CPU restatement of the learned-proposal features and labels -- TEST
 INFRASTRUCTURE ONLY.
 
-features: the strided sample i_k = floor(k n / S), S = min(n, 65536); its
+features: the strided sample i_k = floor(k n / S), S = min(n, 16384); its
 centre (float64 mean, then float32); for every sample point the angle of
 (p - c) in float32 split into 32 equal bins over (-pi, pi], the point
 fraction and the maximum radius per bin (radii normalised by the largest);
@@ -19,7 +19,7 @@ import numpy as np
 import oracle
 
 NB = 32
-SAMPLE = 65536
+SAMPLE = 16384
 
 
 def sample_indices(n: int) -> np.ndarray:

@@ -954,6 +954,7 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
   L.slot0 = w.slot0; L.ka = w.ka; L.kb = w.kb; L.ia = w.ia; L.ib = w.ib;
   L.lxy = w.lxy; L.lidx = w.lidx; L.uxy = w.uxy; L.uidx = w.uidx;
   L.out_tmp = w.out_tmp; L.hcount = w.hcount; L.error = w.ctl + 2;
+  L.w16 = (c->cfg.proposal == 1 && c->have_weights) ? c->W16 : nullptr;
   const int nl = (int)large.size(), ns = (int)small.size();
   auto run_bucket = [&](int bucket, int block, cudaStream_t s2, u32* queue) -> cudaError_t {
     BatchLaunch M = L;

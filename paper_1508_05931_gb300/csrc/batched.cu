@@ -21,6 +21,7 @@
 #include "chain.cuh"
 #include "hull_internal.cuh"
 #include "kernels.h"
+#include "learned_common.cuh"
 
 namespace gbh {
 
@@ -78,8 +79,9 @@ struct IPlan {
   int ext_idx[4];
   int ext_x[4], ext_y[4];
   int ncorner;
-  int ex[4], ney[4];
-  long long nc[4];
+  int ex[kMaxCorners], ney[kMaxCorners];
+  long long nc[kMaxCorners];
+  int learned;
   int x0, y0;
   u32 ybits, npasses;
   int bad;
@@ -126,8 +128,19 @@ struct Smem {
   int inst;
   u64 rk[W][4];
   u32 ri[W][4];
-  int sx[CHUNK], sy[CHUNK], si[CHUNK];
+  union {
+    struct {                         // chains (step 5)
+      int sx[CHUNK], sy[CHUNK], si[CHUNK];
+    };
+    struct {                         // learned proposal (step 1)
+      learned::FeatSmem feat;
+      learned::MlpSmem mlp;
+      int ext_xy[2 * learned::NB];
+      int ext_idx[learned::NB];
+    };
+  };
   int ccnt[BLOCK];                   // per-thread chain lengths inside a chunk
+  int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
   int4 pair[BT_MAX_CHUNKS / 2];      // bridge results of one merge level
 };
@@ -241,6 +254,7 @@ struct BatchArgs {
   int* out_tmp;
   u32* hcount;                // [B]
   u32* error;
+  const __half* w16;          // learned proposal weights (null: quadrilateral)
 };
 
 template <int BLOCK>
@@ -305,17 +319,43 @@ k_batch(BatchArgs a) {
       }
       while (k > 1 && cx[k - 1] == cx[0] && cy[k - 1] == cy[0]) --k;
       pl.ncorner = k;
-      for (int j = 0; j < 4; ++j) {
-        const int jj = j < k ? j : 0, jn = (j + 1 < k) ? j + 1 : 0;
-        const int e_x = cx[jn] - cx[jj], e_y = cy[jn] - cy[jj];
-        pl.ex[j] = e_x; pl.ney[j] = -e_y;
-        pl.nc[j] = -((long long)e_x * cy[jj] - (long long)e_y * cx[jj]);
-      }
+      pl.learned = 0;
+      for (int j = 0; j < k; ++j) { S.corner_x[j] = cx[j]; S.corner_y[j] = cy[j]; }
       pl.x0 = ex[0]; pl.y0 = ey[2];
       const u32 yb = bitlen32((u32)(ey[3] - ey[2])), xb = bitlen32((u32)(ex[1] - ex[0]));
       pl.ybits = yb;
       pl.npasses = (xb + yb + kRadixBits - 1) / kRadixBits;
       if (pl.bad) atomicOr(a.error, ERR_RANGE);
+    }
+    __syncthreads();
+    if (a.w16 != nullptr && !S.plan.bad) {
+      // Learned polygon: features of a sample of this instance, the MLP,
+      // the exact hull of the quadrilateral and the 8 chosen extremes.
+      const u32 smp = n < 4096u ? n : 4096u;
+      learned::block_features<BLOCK>(P, n, smp, S.feat, S.mlp.x, S.ext_xy, S.ext_idx);
+      learned::block_mlp(a.w16, S.mlp);
+      if (threadIdx.x == 0) {
+        int qx[4], qy[4], ox[kMaxCorners], oy[kMaxCorners];
+        const int nq = S.plan.ncorner < 4 ? S.plan.ncorner : 4;
+        for (int j = 0; j < nq; ++j) { qx[j] = S.corner_x[j]; qy[j] = S.corner_y[j]; }
+        const int k2 = learned::learned_polygon(S.mlp.z, S.ext_xy, qx, qy, nq, ox, oy);
+        if (k2 > 0) {
+          S.plan.ncorner = k2;
+          S.plan.learned = 1;
+          for (int j = 0; j < k2; ++j) { S.corner_x[j] = ox[j]; S.corner_y[j] = oy[j]; }
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      IPlan& pl = S.plan;
+      const int k = pl.ncorner;
+      for (int j = 0; j < kMaxCorners; ++j) {
+        const int jj = j < k ? j : 0, jn = (j + 1 < k) ? j + 1 : 0;
+        const int e_x = S.corner_x[jn] - S.corner_x[jj], e_y = S.corner_y[jn] - S.corner_y[jj];
+        pl.ex[j] = e_x; pl.ney[j] = -e_y;
+        pl.nc[j] = -((long long)e_x * S.corner_y[jj] - (long long)e_y * S.corner_x[jj]);
+      }
     }
     for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
     __syncthreads();
@@ -341,7 +381,7 @@ k_batch(BatchArgs a) {
           const int2 p = P[j];
           px[r] = p.x; py[r] = p.y;
           in = pl.ncorner >= 3;
-          for (int e = 0; e < 4 && in; ++e) {
+          for (int e = 0; e < kMaxCorners && in; ++e) {
             if (e >= pl.ncorner) break;
             const long long o = (long long)pl.ex[e] * p.y + (long long)pl.ney[e] * p.x + pl.nc[e];
             in = o > 0;
@@ -619,6 +659,7 @@ cudaError_t launch_batch(int block, int grid, const BatchLaunch& L, cudaStream_t
   a.slot0 = L.slot0; a.ka = L.ka; a.kb = L.kb; a.ia = L.ia; a.ib = L.ib;
   a.lxy = L.lxy; a.lidx = L.lidx; a.uxy = L.uxy; a.uidx = L.uidx;
   a.out_tmp = L.out_tmp; a.hcount = L.hcount; a.error = L.error;
+  a.w16 = reinterpret_cast<const __half*>(L.w16);
   if (L.nb <= 0) return cudaSuccess;
   if (block == 512) k_batch<512><<<grid, 512, sizeof(Smem<512>), st>>>(a);
   else k_batch<256><<<grid, 256, sizeof(Smem<256>), st>>>(a);

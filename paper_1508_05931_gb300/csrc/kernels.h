@@ -68,6 +68,7 @@ struct BatchLaunch {
   int* out_tmp;
   u32* hcount;
   u32* error;
+  const void* w16;   // learned proposal weights, or null
 };
 
 int batch_pad();

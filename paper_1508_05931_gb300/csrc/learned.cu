@@ -21,217 +21,47 @@
 
 #include "hull_internal.cuh"
 #include "kernels.h"
+#include "learned_common.cuh"
 
 namespace gbh {
 
+using namespace learned;
+
 namespace {
 
-constexpr int F_SAMPLE = 65536;
+constexpr int F_SAMPLE = 16384;
 constexpr int F_BLOCK = 512;
-constexpr int NB = 32;                   // angular bins / candidate directions
 
 __device__ __forceinline__ float fp16r(float w) { return __half2float(__float2half_rn(w)); }
 
-// ---------------------------------------------------------------- K6
+// K6: features and extremes of the sample of one input (one block).
 __global__ void __launch_bounds__(F_BLOCK)
 k6_features(const int* __restrict__ xy, u32 n, float* __restrict__ feat, int* __restrict__ ext,
             int* __restrict__ ext_xy) {
-  __shared__ double s_sum[2][F_BLOCK / 32];
-  __shared__ u32 s_cnt[NB];
-  __shared__ float s_maxr[NB];
-  __shared__ float s_best[NB][F_BLOCK / 32];
-  __shared__ u32 s_bidx[NB][F_BLOCK / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ FeatSmem sm;
+  __shared__ float s_x[D0];
   const u32 S = n < (u32)F_SAMPLE ? n : (u32)F_SAMPLE;
-  const int2* p2 = reinterpret_cast<const int2*>(xy);
-  // centre of the sample (float64 sums)
-  double sx = 0.0, sy = 0.0;
-  for (u32 k = threadIdx.x; k < S; k += F_BLOCK) {
-    const u32 i = (u32)(((unsigned long long)k * n) / S);
-    const int2 p = p2[i];
-    sx += p.x; sy += p.y;
-  }
-  #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sx += __shfl_xor_sync(0xFFFFFFFFu, sx, o);
-    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, o);
-  }
-  if (lane == 0) { s_sum[0][wid] = sx; s_sum[1][wid] = sy; }
-  if (threadIdx.x < NB) { s_cnt[threadIdx.x] = 0; s_maxr[threadIdx.x] = 0.f; }
-  __syncthreads();
-  double cx = 0.0, cy = 0.0;
-  for (int w = 0; w < F_BLOCK / 32; ++w) { cx += s_sum[0][w]; cy += s_sum[1][w]; }
-  cx /= (double)S; cy /= (double)S;
-  const float fcx = (float)cx, fcy = (float)cy;
-  // histogram and directional extremes
-  float best[NB];
-  u32 bidx[NB];
-  float ux[NB / 2], uy[NB / 2];
-  #pragma unroll
-  for (int j = 0; j < NB / 2; ++j) {
-    float sn, cs;
-    sincosf(6.283185307179586f * (float)j / (float)NB, &sn, &cs);
-    ux[j] = cs; uy[j] = sn;
-    best[j] = -INFINITY; best[j + NB / 2] = -INFINITY;
-    bidx[j] = 0xFFFFFFFFu; bidx[j + NB / 2] = 0xFFFFFFFFu;
-  }
-  for (u32 k = threadIdx.x; k < S; k += F_BLOCK) {
-    const u32 i = (u32)(((unsigned long long)k * n) / S);
-    const int2 p = p2[i];
-    const float dx = (float)p.x - fcx, dy = (float)p.y - fcy;
-    const float ang = atan2f(dy, dx);                  // (-pi, pi]
-    int b = (int)floorf((ang + 3.14159265358979f) * ((float)NB / 6.283185307179586f));
-    b = b < 0 ? 0 : (b >= NB ? NB - 1 : b);
-    atomicAdd(&s_cnt[b], 1u);
-    const float r = sqrtf(dx * dx + dy * dy);
-    atomicMax(reinterpret_cast<int*>(&s_maxr[b]), __float_as_int(r));   // r >= 0
-    const float fx = (float)p.x, fy = (float)p.y;
-    #pragma unroll
-    for (int j = 0; j < NB / 2; ++j) {
-      const float d = ux[j] * fx + uy[j] * fy;
-      if (d > best[j]) { best[j] = d; bidx[j] = i; }                 // direction j
-      if (-d > best[j + NB / 2]) { best[j + NB / 2] = -d; bidx[j + NB / 2] = i; }  // direction j + 16
-    }
-  }
-  // block argmax per direction (ties: smaller index)
-  #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    float v = best[j];
-    u32 ix = bidx[j];
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-      const u32 i2 = __shfl_xor_sync(0xFFFFFFFFu, ix, o);
-      if (v2 > v || (v2 == v && i2 < ix)) { v = v2; ix = i2; }
-    }
-    if (lane == 0) { s_best[j][wid] = v; s_bidx[j][wid] = ix; }
-  }
-  __syncthreads();
-  if (threadIdx.x < NB) {
-    const int j = threadIdx.x;
-    float v = -INFINITY;
-    u32 ix = 0xFFFFFFFFu;
-    for (int w = 0; w < F_BLOCK / 32; ++w) {
-      const float v2 = s_best[j][w];
-      const u32 i2 = s_bidx[j][w];
-      if (v2 > v || (v2 == v && i2 < ix)) { v = v2; ix = i2; }
-    }
-    ext[j] = (int)ix;
-    const int2 p = p2[ix];
-    ext_xy[2 * j] = p.x;
-    ext_xy[2 * j + 1] = p.y;
-    float mr = 0.f;
-    for (int q = 0; q < NB; ++q) mr = fmaxf(mr, s_maxr[q]);
-    feat[j] = (float)s_cnt[j] / (float)S;
-    feat[NB + j] = mr > 0.f ? s_maxr[j] / mr : 0.f;
-  }
+  block_features<F_BLOCK>(reinterpret_cast<const int2*>(xy), n, S, sm, s_x, ext_xy, ext);
+  if (threadIdx.x < D0) feat[threadIdx.x] = s_x[threadIdx.x];
 }
 
-// ---------------------------------------------------------------- polygon
-__device__ __forceinline__ long long orient64(int ax, int ay, int bx, int by, int cx, int cy) {
-  return (long long)(bx - ax) * (cy - ay) - (long long)(by - ay) * (cx - ax);
-}
-
-// Exact convex hull (strict vertices, CCW from the lexicographic minimum)
-// of m <= 16 points (px/py reordered in place; hx/hy need 2m + 1 slots);
-// single thread.  Returns the vertex count.
-__device__ int small_hull(int* px, int* py, int m, int* hx, int* hy) {
-  for (int i = 1; i < m; ++i) {                   // insertion sort (x, y)
-    const int x = px[i], y = py[i];
-    int j = i - 1;
-    while (j >= 0 && (px[j] > x || (px[j] == x && py[j] > y))) { px[j + 1] = px[j]; py[j + 1] = py[j]; --j; }
-    px[j + 1] = x; py[j + 1] = y;
-  }
-  int u = 0;
-  for (int i = 0; i < m; ++i)
-    if (u == 0 || px[u - 1] != px[i] || py[u - 1] != py[i]) { px[u] = px[i]; py[u] = py[i]; ++u; }
-  if (u <= 2) {
-    for (int i = 0; i < u; ++i) { hx[i] = px[i]; hy[i] = py[i]; }
-    return u;
-  }
-  int k = 0;
-  for (int i = 0; i < u; ++i) {
-    while (k >= 2 && orient64(hx[k - 2], hy[k - 2], hx[k - 1], hy[k - 1], px[i], py[i]) <= 0) --k;
-    hx[k] = px[i]; hy[k] = py[i]; ++k;
-  }
-  const int lower = k + 1;
-  for (int i = u - 2; i >= 0; --i) {
-    while (k >= lower && orient64(hx[k - 2], hy[k - 2], hx[k - 1], hy[k - 1], px[i], py[i]) <= 0) --k;
-    hx[k] = px[i]; hy[k] = py[i]; ++k;
-  }
-  return k - 1;
-}
-
-// Twice the signed area (shoelace, int64 / exact for |coords| <= 2^29).
-__device__ long long area2(const int* hx, const int* hy, int k) {
-  long long a = 0;
-  for (int i = 0; i < k; ++i) {
-    const int j = (i + 1) % k;
-    a += (long long)hx[i] * hy[j] - (long long)hx[j] * hy[i];
-  }
-  return a;
-}
-
-// ---------------------------------------------------------------- MLP
-constexpr int D0 = 64, D1 = 128, D2 = 128, D3 = 32;
-constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + D1 * D0, OFF_W2 = OFF_B1 + D1, OFF_B2 = OFF_W2 + D2 * D1,
-              OFF_W3 = OFF_B2 + D2, OFF_B3 = OFF_W3 + D3 * D2, N_PARAMS = OFF_B3 + D3;
-static_assert(N_PARAMS == 28960, "parameter count");
-
-// K8: inference on one feature vector and the filter polygon.  One block of
-// 128 threads.  Weights are the FP16 copies (as __half); FP32 accumulation.
+// K8: inference on one feature vector and the filter polygon (one block).
 __global__ void __launch_bounds__(128)
 k8_infer(const float* __restrict__ feat, const __half* __restrict__ w16, const int* __restrict__ ext_xy,
          Plan* plan) {
-  __shared__ float s_x[D0];
-  __shared__ float s_h1[D1];
-  __shared__ float s_h2[D2];
-  __shared__ float s_z[D3];
-  const int t = threadIdx.x;
+  __shared__ MlpSmem sm;
   if (plan->error & ERR_RANGE) return;
-  if (t < D0) s_x[t] = feat[t];
+  if (threadIdx.x < D0) sm.x[threadIdx.x] = feat[threadIdx.x];
   __syncthreads();
-  {
-    float a = __half2float(w16[OFF_B1 + t]);
-    for (int k = 0; k < D0; ++k) a = fmaf(__half2float(w16[OFF_W1 + t * D0 + k]), s_x[k], a);
-    s_h1[t] = fmaxf(a, 0.f);
-  }
-  __syncthreads();
-  {
-    float a = __half2float(w16[OFF_B2 + t]);
-    for (int k = 0; k < D1; ++k) a = fmaf(__half2float(w16[OFF_W2 + t * D1 + k]), s_h1[k], a);
-    s_h2[t] = fmaxf(a, 0.f);
-  }
-  __syncthreads();
-  if (t < D3) {
-    float a = __half2float(w16[OFF_B3 + t]);
-    for (int k = 0; k < D2; ++k) a = fmaf(__half2float(w16[OFF_W3 + t * D2 + k]), s_h2[k], a);
-    s_z[t] = a;
-  }
-  __syncthreads();
-  if (t != 0) return;
-  // top 8 of 32 scores (ties: lower j)
-  bool used[D3];
-  for (int j = 0; j < D3; ++j) used[j] = false;
-  int px[16], py[16], m = 0;
-  for (int j = 0; j < plan->ncorner && j < 4; ++j) { px[m] = plan->cx[j]; py[m] = plan->cy[j]; ++m; }
-  const int nq = m;
-  for (int pick = 0; pick < 8; ++pick) {
-    int bj = -1;
-    float bv = -INFINITY;
-    for (int j = 0; j < D3; ++j)
-      if (!used[j] && (s_z[j] > bv || bj < 0)) { bv = s_z[j]; bj = j; }
-    used[bj] = true;
-    px[m] = ext_xy[2 * bj]; py[m] = ext_xy[2 * bj + 1]; ++m;
-  }
-  int hx[32], hy[32];
-  int qx[4], qy[4];
+  block_mlp(w16, sm);
+  if (threadIdx.x != 0) return;
+  int qx[4], qy[4], ox[kMaxCorners], oy[kMaxCorners];
+  const int nq = plan->ncorner < 4 ? plan->ncorner : 4;
   for (int j = 0; j < nq; ++j) { qx[j] = plan->cx[j]; qy[j] = plan->cy[j]; }
-  const int k = small_hull(px, py, m, hx, hy);
-  const long long aq = nq >= 3 ? area2(qx, qy, nq) : 0;
-  if (k >= 3 && k <= kMaxCorners && area2(hx, hy, k) > aq) {
+  const int k = learned_polygon(sm.z, ext_xy, qx, qy, nq, ox, oy);
+  if (k > 0) {
     plan->ncorner = k;
-    for (int j = 0; j < k; ++j) { plan->cx[j] = hx[j]; plan->cy[j] = hy[j]; }
+    for (int j = 0; j < k; ++j) { plan->cx[j] = ox[j]; plan->cy[j] = oy[j]; }
     plan->learned_used = 1;
   }
 }

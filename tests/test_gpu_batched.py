@@ -122,3 +122,18 @@ def test_batch_autotune(hull_lib, tmp_path):
             check(parts, *run_batch(c, parts))
     finally:
         del os.environ["GBHULL_AUTOTUNE_CACHE"]
+
+
+def test_batch_learned_exact_and_discards_more(hull_lib):
+    """The learned polygon inside the batched kernel: exact hulls, and it
+    never discards less than the quadrilateral."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from oracle import mlp as OM
+    from paper_1508_05931_gb300 import learned as L
+    parts = [L.instance(k % 3, 20000 + 997 * k, 300 + k) for k in range(24)] + mixed_parts(5)
+    with hull_lib.Context(0, proposal=1) as c:
+        c.mlp_set_params(OM.init_params(11))
+        check(parts, *run_batch(c, parts))
+        c.mlp_set_params(np.zeros(OM.N_PARAMS, np.float32))
+        check(parts, *run_batch(c, parts))
