@@ -286,7 +286,7 @@ hull_status run_final(hull_ctx* c, const int2* lo_xy, const int* lo_idx, const i
                       cudaStream_t st) {
   Workspace& w = c->ws;
   const size_t chunks = (npoints_bound + 4) / (size_t)k5_chunk() + 2;
-  int grid = grid_for(c->occ_k5, c->num_sms, chunks < 64 ? 64 : chunks);
+  int grid = grid_for(c->occ_k5 < 4 ? c->occ_k5 : 4, c->num_sms, chunks < 64 ? 64 : chunks);
   cudaError_t e = launch_k5(lo_xy, lo_idx, up_xy, up_idx, c->plan, w.h_xy[0], w.h_idx[0], w.h_xy[1],
                             w.h_idx[1], w.cnt[0], w.cnt[1], w.jobs, d_out, (long long)cap, grid, st);
   if (e != cudaSuccess) return cuda_fail(e);

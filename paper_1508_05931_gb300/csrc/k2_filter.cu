@@ -48,22 +48,6 @@ __device__ __forceinline__ bool strictly_inside(const Edges& E, int x, int y) {
   return in;
 }
 
-__device__ __forceinline__ bool inside_any(const Edges& E, int k, int x, int y) {
-  switch (k) {
-    case 3: return strictly_inside<3>(E, x, y);
-    case 4: return strictly_inside<4>(E, x, y);
-    case 5: return strictly_inside<5>(E, x, y);
-    case 6: return strictly_inside<6>(E, x, y);
-    case 7: return strictly_inside<7>(E, x, y);
-    case 8: return strictly_inside<8>(E, x, y);
-    case 9: return strictly_inside<9>(E, x, y);
-    case 10: return strictly_inside<10>(E, x, y);
-    case 11: return strictly_inside<11>(E, x, y);
-    case 12: return strictly_inside<12>(E, x, y);
-    default: return false;
-  }
-}
-
 __device__ __forceinline__ void load_edges(const Plan* plan, int k, Edges& E) {
   #pragma unroll
   for (int j = 0; j < kMaxCorners; ++j) {
@@ -77,10 +61,11 @@ __device__ __forceinline__ void load_edges(const Plan* plan, int k, Edges& E) {
   }
 }
 
-// Loads this thread's K2_PAIRS pairs of a chunk and tests them.
-template <bool VEC>
-__device__ __forceinline__ void load_test(const int* __restrict__ xy, u32 n, u32 base,
-                                          const Edges& E, int k, int* px, int* py, bool* keep) {
+// Tests this thread's pairs of a chunk against a K-corner polygon (K known
+// at compile time: the corner count is uniform over the whole launch).
+template <bool VEC, int K>
+__device__ __forceinline__ void load_test_k(const int* __restrict__ xy, u32 n, u32 base,
+                                            const Edges& E, int* px, int* py, bool* keep) {
   #pragma unroll
   for (int r = 0; r < K2_PAIRS; ++r) {
     const u32 i0 = base + 2u * (r * K2_BLOCK + threadIdx.x);
@@ -93,36 +78,25 @@ __device__ __forceinline__ void load_test(const int* __restrict__ xy, u32 n, u32
       if (i0 + 1 < n) b = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0 + 2);
       px[2 * r] = a.x; py[2 * r] = a.y; px[2 * r + 1] = b.x; py[2 * r + 1] = b.y;
     }
-    keep[2 * r] = (i0 < n) && !inside_any(E, k, px[2 * r], py[2 * r]);
-    keep[2 * r + 1] = (i0 + 1 < n) && !inside_any(E, k, px[2 * r + 1], py[2 * r + 1]);
+    keep[2 * r] = (i0 < n) && !(K >= 3 && strictly_inside<K>(E, px[2 * r], py[2 * r]));
+    keep[2 * r + 1] = (i0 + 1 < n) && !(K >= 3 && strictly_inside<K>(E, px[2 * r + 1], py[2 * r + 1]));
   }
 }
 
-template <bool VEC>
-__global__ void __launch_bounds__(K2_BLOCK, 6)
-k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
-         unsigned char* __restrict__ mask) {
-  __shared__ u32 s_hist[kRadix];
-  __shared__ u32 s_red[K2_WARPS];
-  __shared__ bool s_last;
-
-  if (plan->error & ERR_RANGE) return;
+template <bool VEC, int K>
+__device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
+                                             unsigned char* __restrict__ mask, const Edges& E,
+                                             u32* s_hist, u32* s_red) {
   const u32 n = plan->n;
-  const int k = plan->ncorner;
   const int x0 = plan->key_x0, y0 = plan->key_y0;
   const u32 ybits = plan->ybits;
   const bool hist = plan->npasses > 0;
   const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  Edges E;
-  load_edges(plan, k, E);
-  for (int q = threadIdx.x; q < kRadix; q += K2_BLOCK) s_hist[q] = 0u;
-  __syncthreads();
-
   for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
     bool keep[2 * K2_PAIRS];
-    load_test<VEC>(xy, n, c * (u32)K2_CHUNK, E, k, px, py, keep);
+    load_test_k<VEC, K>(xy, n, c * (u32)K2_CHUNK, E, px, py, keep);
     u32 cnt = 0, bits = 0;
     #pragma unroll
     for (int e = 0; e < 2 * K2_PAIRS; ++e) {
@@ -146,6 +120,39 @@ k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
       counts[c] = t;
     }
     __syncthreads();
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K2_BLOCK, 6)
+k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
+         unsigned char* __restrict__ mask) {
+  __shared__ u32 s_hist[kRadix];
+  __shared__ u32 s_red[K2_WARPS];
+  __shared__ bool s_last;
+
+  if (plan->error & ERR_RANGE) return;
+  const u32 n = plan->n;
+  const int k = plan->ncorner;
+  const bool hist = plan->npasses > 0;
+  const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Edges E;
+  load_edges(plan, k, E);
+  for (int q = threadIdx.x; q < kRadix; q += K2_BLOCK) s_hist[q] = 0u;
+  __syncthreads();
+  switch (k) {
+    case 3: count_chunks<VEC, 3>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 4: count_chunks<VEC, 4>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 5: count_chunks<VEC, 5>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 6: count_chunks<VEC, 6>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 7: count_chunks<VEC, 7>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 8: count_chunks<VEC, 8>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 9: count_chunks<VEC, 9>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 10: count_chunks<VEC, 10>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 11: count_chunks<VEC, 11>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 12: count_chunks<VEC, 12>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    default: count_chunks<VEC, 0>(xy, plan, counts, mask, E, s_hist, s_red); break;
   }
   if (hist)
     for (u32 q = threadIdx.x; q < kRadix; q += K2_BLOCK)

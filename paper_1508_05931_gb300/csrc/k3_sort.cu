@@ -37,7 +37,7 @@ namespace {
 #define K3_BLOCK_CFG 256
 #endif
 #ifndef K3_WINDOW_CFG
-#define K3_WINDOW_CFG 16
+#define K3_WINDOW_CFG 8
 #endif
 constexpr int K3_BLOCK = K3_BLOCK_CFG;
 constexpr int K3_WARPS = K3_BLOCK / 32;
@@ -49,6 +49,14 @@ static_assert(K3_BLOCK == kRadix || K3_BLOCK == 2 * kRadix, "the first kRadix th
 static_assert(K3_WARP_ITEMS <= 65535, "16-bit warp counters");
 
 __device__ __forceinline__ u32 digit_of(u64 k, u32 shift) { return (u32)(k >> shift) & (kRadix - 1); }
+
+// Digit of pass P: a bit-field extract from one 32-bit half of the key.
+template <int P>
+__device__ __forceinline__ u32 digit_p(u64 k) {
+  if (P >= kMaxPasses) return 0u;
+  const u32 half = P < 4 ? (u32)k : (u32)(k >> 32);
+  return (half >> ((P & 3) * kRadixBits)) & (kRadix - 1);
+}
 
 // Lanes holding the same 8-bit digit (all 32 lanes take part).
 __device__ __forceinline__ u32 same_digit_lanes(u32 dg) {
@@ -66,10 +74,12 @@ __device__ __forceinline__ u32 same_digit_lanes(u32 dg) {
 #endif
 }
 
+template <int PASS>
 __global__ void __launch_bounds__(K3_BLOCK, K3_MINBLOCKS_CFG)
 k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
             u64* __restrict__ keys_out, u32* __restrict__ idx_out, Plan* plan,
-            u64* __restrict__ status, u32 pass) {
+            u64* __restrict__ status) {
+  constexpr u32 pass = PASS;
   extern __shared__ __align__(16) unsigned char k3_smem[];
   u64* s_keys = reinterpret_cast<u64*>(k3_smem);
   u32* s_idx = reinterpret_cast<u32*>(k3_smem + K3_TILE * sizeof(u64));
@@ -85,9 +95,7 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
   const u32 npasses = plan->npasses;
   if (pass >= npasses || (plan->error & ERR_RANGE)) return;
   const u32 s = plan->s;
-  const u32 shift = pass * kRadixBits;
   const bool count_next = pass + 1 < npasses;
-  const u32 nshift = shift + kRadixBits;
   const u32 epoch = plan->epoch + EP_SORT0 + pass;
   const u32 spin = plan->spin_limit;
   const u32 ntiles = (s + K3_TILE - 1) / K3_TILE;
@@ -145,8 +153,8 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
     #pragma unroll
     for (int it = 0; it < K3_ITEMS; ++it) {
       if (full || wbase + it * 32 + lane < s) {
-        atomicAdd(&wp[digit_of(key[it], shift)], 1u);
-        if (count_next) atomicAdd(&s_next[digit_of(key[it], nshift)], 1u);
+        atomicAdd(&wp[digit_p<PASS>(key[it])], 1u);
+        if (count_next) atomicAdd(&s_next[digit_p<PASS + 1>(key[it])], 1u);
       }
     }
     __syncthreads();
@@ -187,7 +195,7 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
     // digits reserves the group's positions with one shared atomic.
     #pragma unroll
     for (int it = 0; it < K3_ITEMS; ++it) {
-      const u32 dg = digit_of(key[it], shift);
+      const u32 dg = digit_p<PASS>(key[it]);
       const bool valid = full || (wbase + it * 32 + lane) < s;
       u32 peers = same_digit_lanes(dg);
       if (!full) peers &= __ballot_sync(0xFFFFFFFFu, valid);
@@ -246,7 +254,7 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
     // addresses within each digit.
     for (u32 j = threadIdx.x; j < tile_n; j += K3_BLOCK) {
       const u64 k = s_keys[j];
-      const u32 gp = s_gbase[digit_of(k, shift)] + j;
+      const u32 gp = s_gbase[digit_p<PASS>(k)] + j;
       if (gp < s) {
         keys_out[gp] = k;
         idx_out[gp] = s_idx[j];
@@ -266,18 +274,42 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
 int k3_tile() { return K3_TILE; }
 size_t k3_dyn_smem() { return (size_t)K3_TILE * (sizeof(u64) + sizeof(u32)); }
 
-cudaError_t k3_configure() {
-  return cudaFuncSetAttribute(k3_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int P>
+static cudaError_t configure_pass() {
+  return cudaFuncSetAttribute(k3_onesweep<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)k3_dyn_smem());
 }
 
+cudaError_t k3_configure() {
+  cudaError_t e = configure_pass<0>();
+  if (e == cudaSuccess) e = configure_pass<1>();
+  if (e == cudaSuccess) e = configure_pass<2>();
+  if (e == cudaSuccess) e = configure_pass<3>();
+  if (e == cudaSuccess) e = configure_pass<4>();
+  if (e == cudaSuccess) e = configure_pass<5>();
+  if (e == cudaSuccess) e = configure_pass<6>();
+  if (e == cudaSuccess) e = configure_pass<7>();
+  return e;
+}
+
 cudaError_t k3_occupancy(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k3_onesweep, K3_BLOCK, k3_dyn_smem());
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k3_onesweep<0>, K3_BLOCK, k3_dyn_smem());
 }
 
 cudaError_t launch_k3(const u64* kin, const u32* iin, u64* kout, u32* iout, Plan* plan,
                       u64* status, u32 pass, int grid, cudaStream_t st) {
-  k3_onesweep<<<grid, K3_BLOCK, k3_dyn_smem(), st>>>(kin, iin, kout, iout, plan, status, pass);
+  const size_t sm = k3_dyn_smem();
+  switch (pass) {
+    case 0: k3_onesweep<0><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 1: k3_onesweep<1><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 2: k3_onesweep<2><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 3: k3_onesweep<3><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 4: k3_onesweep<4><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 5: k3_onesweep<5><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 6: k3_onesweep<6><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    case 7: k3_onesweep<7><<<grid, K3_BLOCK, sm, st>>>(kin, iin, kout, iout, plan, status); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -30,7 +30,8 @@ constexpr int K5_WARPS = K5_BLOCK / 32;
 constexpr int K5_LEAF = 8;
 constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // 4096 points per chunk
 
-__device__ bool grid_barrier(Plan* plan, u32 spin) {
+// Barrier over the first `nblocks` blocks of the (co-resident) grid.
+__device__ bool grid_barrier(Plan* plan, u32 spin, u32 nblocks) {
   __syncthreads();
   __shared__ int s_bar_fail;
   if (threadIdx.x == 0) {
@@ -39,7 +40,7 @@ __device__ bool grid_barrier(Plan* plan, u32 spin) {
     volatile u32* genp = &plan->ctr[CTR_FINAL_BAR_GEN];
     const u32 gen = *genp;
     const u32 arrived = atomicAdd(&plan->ctr[CTR_FINAL_BAR], 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == nblocks) {
       plan->ctr[CTR_FINAL_BAR] = 0u;
       __threadfence();
       atomicAdd(&plan->ctr[CTR_FINAL_BAR_GEN], 1u);
@@ -106,9 +107,14 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     }
   }
 
-  // ---------------- phase A: chunk chains in shared memory
+  // Only as many blocks as the work needs take part (the same count on
+  // every block: it depends only on the Plan); the others leave now.
   const u32 total_chunks = cs.nchunk[0] + cs.nchunk[1];
-  for (u32 ch = blockIdx.x; ch < total_chunks; ch += gridDim.x) {
+  const u32 nblk = min(gridDim.x, max(16u, total_chunks));
+  if (blockIdx.x >= nblk) return;
+
+  // ---------------- phase A: chunk chains in shared memory
+  for (u32 ch = blockIdx.x; ch < total_chunks; ch += nblk) {
     const int c = ch < cs.nchunk[0] ? 0 : 1;
     const u32 local = c == 0 ? ch : ch - cs.nchunk[0];
     const int sgn = c == 0 ? 1 : -1;
@@ -162,9 +168,9 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
   int2* cur_xy = h0_xy; int* cur_idx = h0_idx; u32* cur_cnt = cnt0;
   int2* nxt_xy = h1_xy; int* nxt_idx = h1_idx; u32* nxt_cnt = cnt1;
   const u32 maxchunks = max(cs.nchunk[0], cs.nchunk[1]);
-  const int gw = blockIdx.x * K5_WARPS + wid, nw = gridDim.x * K5_WARPS;
+  const int gw = blockIdx.x * K5_WARPS + wid, nw = nblk * K5_WARPS;
   for (u32 step = 1; step < maxchunks; step <<= 1) {
-    if (!grid_barrier(plan, spin)) return;
+    if (!grid_barrier(plan, spin, nblk)) return;
     // B1: one warp per pair of nodes (or a lone node carried over).
     const u32 np0 = (cs.nchunk[0] + 2 * step - 1) / (2 * step);
     const u32 np1 = (cs.nchunk[1] + 2 * step - 1) / (2 * step);
@@ -187,11 +193,11 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
         nxt_cnt[gca] = (u32)(is + 1 + (beta - js));
       }
     }
-    if (!grid_barrier(plan, spin)) return;
+    if (!grid_barrier(plan, spin, nblk)) return;
     // B2: gather every merged node into the other buffer.
     const u32 span = 2 * step * K5_CHUNK;
     const u32 total_slots = (cs.nchunk[0] + cs.nchunk[1]) * K5_CHUNK;
-    for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < total_slots; q += gridDim.x * K5_BLOCK) {
+    for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < total_slots; q += nblk * K5_BLOCK) {
       const int c = q < cs.slot0[1] ? 0 : 1;
       const u32 rel = q - cs.slot0[c];
       const u32 p = rel / span, o = rel % span;
@@ -210,7 +216,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     int* t1 = cur_idx; cur_idx = nxt_idx; nxt_idx = t1;
     u32* t2 = cur_cnt; cur_cnt = nxt_cnt; nxt_cnt = t2;
   }
-  if (!grid_barrier(plan, spin)) return;
+  if (!grid_barrier(plan, spin, nblk)) return;
 
   // ---------------- output: lower chain, then the upper chain reversed
   const u32 hl = __ldcg(&cur_cnt[0]);
@@ -221,7 +227,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     if (h > cap) flag_error(plan, ERR_CAPACITY);
   }
   if (h > cap) return;
-  for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < (u32)h; q += gridDim.x * K5_BLOCK) {
+  for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < (u32)h; q += nblk * K5_BLOCK) {
     int v;
     if (q < hl) v = __ldcg(&cur_idx[q]);
     else v = __ldcg(&cur_idx[cs.slot0[1] + (hu - 2) - (q - hl)]);

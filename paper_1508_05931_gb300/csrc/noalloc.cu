@@ -180,7 +180,7 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
   if (e == cudaSuccess)
     e = launch_k5(c.lo_xy, c.lo_idx, c.up_xy, c.up_idx, c.plan, c.h_xy[0], c.h_idx[0], c.h_xy[1],
                   c.h_idx[1], c.cnt[0], c.cnt[1], c.jobs, d_out, (long long)cap,
-                  grid_for(d->occ_k5, d->num_sms, chunks < 64 ? 64 : chunks), st);
+                  grid_for(d->occ_k5 < 4 ? d->occ_k5 : 4, d->num_sms, chunks < 64 ? 64 : chunks), st);
   // Read the summary back into host stack memory (a pageable copy: no
   // pinned buffer is allocated) and wait for the stream.
   alignas(16) unsigned char summary[offsetof(Plan, ctr)];
