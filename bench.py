@@ -61,9 +61,28 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n):
+def workload(n, rank=0):
+    """The two input sets of one rank.  Every rank draws its own problems
+    (seeds 1+2r and 2+2r), so N ranks solve N independent pairs of hulls."""
     from paper_1508_05931_gb300 import workloads as W
-    return [W.paper_square(n, 1), W.paper_disk(n, 2)]
+    return [W.paper_square(n, 1 + 2 * rank), W.paper_disk(n, 2 + 2 * rank)]
+
+
+def max_over_ranks(dist, values, device="cpu"):
+    """Element-wise maximum of `values` over every rank (the slowest rank
+    sets the job's time); the values themselves with one process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_mpts(points_per_rank_step, world, steps, seconds):
+    """Whole-job throughput in Mpoints/s: the points all ranks processed
+    over the slowest rank's time."""
+    return world * points_per_rank_step * steps / seconds / 1e6
 
 
 def cpu_info():
@@ -318,7 +337,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    sets = workload(args.n)
+    sets = workload(args.n, rank)
     dev_sets = [torch.as_tensor(p).cuda() for p in sets]
     out = torch.empty(args.n, dtype=torch.int32, device="cuda")
     ctx = hull.Context(local)
@@ -349,12 +368,9 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = ctx.profile()
     ctx.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, [ms], "cuda")[0]
     pts_step = sum(len(p) for p in sets)
-    value = world * pts_step * args.steps / (ms / 1e3) / 1e6
+    value = job_mpts(pts_step, world, args.steps, ms / 1e3)
 
     # e2e: the same steps through the host entry point (pinned host input,
     # H2D copy, compute, D2H of the vertex indices inside the timed region).
@@ -376,8 +392,8 @@ def main():
     for _ in range(k_e2e):
         host_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = world * pts_step * k_e2e / e2e_s / 1e6
+    e2e_s = max_over_ranks(dist, [time.perf_counter() - t0], "cuda")[0]
+    e2e_val = job_mpts(pts_step, world, k_e2e, e2e_s)
 
     peaks = {}
     try:
@@ -422,11 +438,13 @@ def main():
             "roofline": roofline}
     if clocks:
         line["clocks"] = clocks
-    if not args.no_batched:
+    # The batched and learned sections and the CPU baseline are single-GPU
+    # measurements: with several ranks only the replicated plain pipeline runs.
+    if world == 1 and not args.no_batched:
         line["batched"] = bench_batched(hull, torch, stream, value, args)
-    if not args.no_learned:
+    if world == 1 and not args.no_learned:
         line["learned"] = bench_learned(hull, torch, stream, args)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc, "cpu": cpu_info(), "nproc": os.cpu_count()}
