@@ -77,7 +77,7 @@ struct hull_ctx {
   int device = 0;
   hull_config cfg{};
   int num_sms = 0;
-  int occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
+  int occ_k2c = 1, occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
   Plan* plan = nullptr;        // device
   Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
   Workspace ws;
@@ -262,7 +262,8 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
   }
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2, c->num_sms, t2), st);
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2c, c->num_sms, t2),
+                grid_for(c->occ_k2, c->num_sms, t2), st);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(c, 2, st);
   const size_t t3 = (n + k3_tile() - 1) / k3_tile();
@@ -386,8 +387,9 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return cuda_fail(cudaErrorUnknown); }
   c->num_sms = prop.multiProcessorCount;
-  if (k3_configure() != cudaSuccess || k5_configure(&c->occ_k5) != cudaSuccess ||
-      k2_occupancy(&c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
+  if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess ||
+      k5_configure(&c->occ_k5) != cudaSuccess ||
+      k2_occupancy(&c->occ_k2c, &c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
       k4_occupancy(&c->occ_k4) != cudaSuccess) {
     delete c;
     return cuda_fail(cudaErrorUnknown);
@@ -574,7 +576,7 @@ hull_status hull_stage_filter(hull_ctx* c, const int32_t* d_xy, int64_t n, int32
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t2 = ((size_t)n + k2_tile() - 1) / k2_tile();
   e = launch_k2(d_xy, c->plan, c->ws.keys[0], c->ws.idx[0], c->ws.st_filter, c->ws.mask,
-                grid_for(c->occ_k2, c->num_sms, t2), st);
+                grid_for(c->occ_k2c, c->num_sms, t2), grid_for(c->occ_k2, c->num_sms, t2), st);
   if (e != cudaSuccess) return cuda_fail(e);
   r = finish(c, st);
   if (r != HULL_OK) return r;
@@ -640,7 +642,8 @@ hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int3
   e = launch_plan_patch(c->plan, p, st);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t = ((size_t)m + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2, c->num_sms, t), st);
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2c, c->num_sms, t),
+                grid_for(c->occ_k2, c->num_sms, t), st);
   if (e != cudaSuccess) return cuda_fail(e);
   PlanPatch q{};
   q.set_npasses = 1; q.npasses = 0;

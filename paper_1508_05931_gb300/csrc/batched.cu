@@ -87,17 +87,6 @@ struct IPlan {
   int bad;
 };
 
-__device__ __forceinline__ u32 lanes_with_digit(u32 dg) {
-  u32 peers = 0xFFFFFFFFu;
-  #pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) {
-    const bool bit = (dg >> b) & 1u;
-    const u32 bal = __ballot_sync(0xFFFFFFFFu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
 struct Dir2b {
   int lx, ly, ux, uy;
 };
@@ -468,7 +457,7 @@ k_batch(BatchArgs a) {
           const u32 p = wb + it * 32 + lane;
           const bool valid = p < s;
           const u32 dg = (u32)(key[it] >> shift) & (kRadix - 1);
-          const u32 peers = lanes_with_digit(dg) & __ballot_sync(0xFFFFFFFFu, valid);
+          const u32 peers = warp_digit_peers(dg) & __ballot_sync(0xFFFFFFFFu, valid);
           const int leader = 31 - __clz(peers);
           u32 pos = 0;
           if (valid && lane == leader) pos = atomicAdd(&S.wpos[wid][dg], (u32)__popc(peers));

@@ -119,6 +119,70 @@ __device__ __forceinline__ long long cross2(int ax, int ay, int bx, int by) {
 
 // Look-back status word: [epoch:32 | flag:2 | count:30].
 constexpr u32 ST_AGG = 1, ST_INCL = 2;
+// ---- Bulk asynchronous copies (TMA, non-tensor) into shared memory.
+// One thread arms an mbarrier with the expected byte count and issues a
+// cp.async.bulk; consumers wait on the barrier's phase parity.  Source and
+// destination must be 16-byte aligned and the size a multiple of 16.
+constexpr u32 kBulkWaitLimit = 1u << 24;   // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ u32 smem_addr(const void* p) {
+  return (u32)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Makes initialised barriers visible to the async proxy (then __syncthreads).
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64* bar, u32 bytes) {
+  u64 state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
+  (void)state;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
+  u32 ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0u;
+}
+// Waits for the given phase of `bar` to complete; false if it did not within
+// kBulkWaitLimit rounds.
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity) {
+  for (u32 it = 0; it < kBulkWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Mask of the lanes whose 8-bit radix digit equals this lane's (all 32
+// lanes take part): eight ballots, each compared with this lane's own bit
+// made into a full mask.  Digit bits 7..4 become the byte sign bits of hi,
+// bits 3..0 those of lo (the shifted copies do not overlap, so the products
+// are plain ORs), and prmt with the sign flag in its selector replicates a
+// byte's sign bit over the whole word.
+__device__ __forceinline__ u32 warp_digit_peers(u32 dg) {
+  static_assert(kRadixBits == 8, "two words of four byte sign bits");
+  const u32 hi = dg * 0x08040201u;
+  const u32 lo = (dg << 4) * 0x08040201u;
+  u32 differ = 0u;
+  #pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const u32 sel = 0x8888u + 0x1111u * (u32)(b & 3);
+    u32 mine;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(mine) : "r"(b < 4 ? hi : lo), "r"(sel));
+    differ |= __ballot_sync(0xFFFFFFFFu, mine != 0u) ^ mine;
+  }
+  return ~differ;
+}
+
 __device__ __forceinline__ u64 make_status(u32 epoch, u32 flag, u32 count) {
   return ((u64)epoch << 32) | ((u64)flag << 30) | (u64)(count & 0x3FFFFFFFu);
 }

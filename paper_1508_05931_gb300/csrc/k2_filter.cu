@@ -28,6 +28,9 @@ constexpr int K2_PAIRS = 4;                          // int4 loads per thread pe
 constexpr int K2_CHUNK = K2_BLOCK * K2_PAIRS * 2;    // 2048 points
 constexpr int K2_WARPS = K2_BLOCK / 32;
 static_assert(K2_PAIRS * K2_WARPS == 32, "one (round, warp) count per lane");
+constexpr int K2_STAGES = 3;                          // chunks in flight per block (bulk copies)
+constexpr u32 K2_CHUNK_BYTES = K2_CHUNK * 2 * sizeof(int);   // 16 KB
+constexpr size_t K2_RING_BYTES = (size_t)K2_STAGES * K2_CHUNK_BYTES;
 
 // Edge j from corner c_j to c_j+1: orient(c_j, c_j+1, p) = ex*y - ey*x - c
 // with c = ex*ay - ey*ax, i.e. two 32x32->64 multiply-adds per edge (every
@@ -83,20 +86,58 @@ __device__ __forceinline__ void load_test_k(const int* __restrict__ xy, u32 n, u
   }
 }
 
-template <bool VEC, int K>
+// Tests this thread's pairs of a chunk staged in shared memory.
+template <int K>
+__device__ __forceinline__ void test_staged_k(const int4* __restrict__ chunk, const Edges& E,
+                                              int* px, int* py, bool* keep) {
+  #pragma unroll
+  for (int r = 0; r < K2_PAIRS; ++r) {
+    const int4 v = chunk[r * K2_BLOCK + threadIdx.x];
+    px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+    keep[2 * r] = !(K >= 3 && strictly_inside<K>(E, v.x, v.y));
+    keep[2 * r + 1] = !(K >= 3 && strictly_inside<K>(E, v.z, v.w));
+  }
+}
+
+// Issues the bulk copy of chunk c into ring stage st (one thread).
+__device__ __forceinline__ void k2_stage_chunk(const int* xy, u32 c, int4* ring, u64* bars, int st) {
+  mbar_arrive_expect_tx(&bars[st], K2_CHUNK_BYTES);
+  bulk_load(ring + (size_t)st * (K2_CHUNK / 2), xy + (size_t)c * 2 * K2_CHUNK, K2_CHUNK_BYTES, &bars[st]);
+}
+
+// Counts the survivors of this block's chunks (c = blockIdx.x + i * gridDim.x).
+// With BULK, every whole chunk arrives by a bulk copy into a K2_STAGES-deep
+// ring in shared memory, issued K2_STAGES chunks ahead; a partial last chunk
+// is read directly.
+template <bool VEC, bool BULK, int K>
 __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
                                              unsigned char* __restrict__ mask, const Edges& E,
-                                             u32* s_hist, u32* s_red) {
+                                             u32* s_hist, u32* s_red, int4* ring, u64* bars) {
   const u32 n = plan->n;
   const int x0 = plan->key_x0, y0 = plan->key_y0;
   const u32 ybits = plan->ybits;
   const bool hist = plan->npasses > 0;
   const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
+  const u32 nwhole = n / K2_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+  if (BULK && threadIdx.x == 0) {
+    #pragma unroll
+    for (int st = 0; st < K2_STAGES; ++st) {
+      const u32 c = blockIdx.x + st * gridDim.x;
+      if (c < nwhole) k2_stage_chunk(xy, c, ring, bars, st);
+    }
+  }
+  u32 i = 0;
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x, ++i) {
     int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
     bool keep[2 * K2_PAIRS];
-    load_test_k<VEC, K>(xy, n, c * (u32)K2_CHUNK, E, px, py, keep);
+    const int st = (int)(i % K2_STAGES);
+    if (BULK && c < nwhole) {
+      if (!mbar_wait(&bars[st], (i / K2_STAGES) & 1u)) flag_error(plan, ERR_TIMEOUT);
+      test_staged_k<K>(ring + (size_t)st * (K2_CHUNK / 2), E, px, py, keep);
+    } else {
+      load_test_k<VEC, K>(xy, n, c * (u32)K2_CHUNK, E, px, py, keep);
+    }
     u32 cnt = 0, bits = 0;
     #pragma unroll
     for (int e = 0; e < 2 * K2_PAIRS; ++e) {
@@ -118,18 +159,26 @@ __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* p
       u32 t = 0;
       for (int w = 0; w < K2_WARPS; ++w) t += s_red[w];
       counts[c] = t;
+      // Every thread has read stage st (barrier above): refill it.
+      if (BULK) {
+        const u32 cn = c + K2_STAGES * gridDim.x;
+        if (cn < nwhole) k2_stage_chunk(xy, cn, ring, bars, st);
+      }
     }
     __syncthreads();
   }
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(K2_BLOCK, 6)
+__global__ void __launch_bounds__(K2_BLOCK, 4)
 k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
          unsigned char* __restrict__ mask) {
+  extern __shared__ __align__(128) unsigned char k2_smem[];
   __shared__ u32 s_hist[kRadix];
   __shared__ u32 s_red[K2_WARPS];
   __shared__ bool s_last;
+  __shared__ __align__(8) u64 s_bars[K2_STAGES];
+  int4* ring = reinterpret_cast<int4*>(k2_smem);
 
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
@@ -140,19 +189,23 @@ k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
   Edges E;
   load_edges(plan, k, E);
   for (int q = threadIdx.x; q < kRadix; q += K2_BLOCK) s_hist[q] = 0u;
+  if (VEC && threadIdx.x == 0) {
+    for (int st = 0; st < K2_STAGES; ++st) mbar_init(&s_bars[st], 1u);
+    mbar_fence_init();
+  }
   __syncthreads();
   switch (k) {
-    case 3: count_chunks<VEC, 3>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 4: count_chunks<VEC, 4>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 5: count_chunks<VEC, 5>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 6: count_chunks<VEC, 6>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 7: count_chunks<VEC, 7>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 8: count_chunks<VEC, 8>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 9: count_chunks<VEC, 9>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 10: count_chunks<VEC, 10>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 11: count_chunks<VEC, 11>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    case 12: count_chunks<VEC, 12>(xy, plan, counts, mask, E, s_hist, s_red); break;
-    default: count_chunks<VEC, 0>(xy, plan, counts, mask, E, s_hist, s_red); break;
+    case 3: count_chunks<VEC, VEC, 3>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 4: count_chunks<VEC, VEC, 4>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 5: count_chunks<VEC, VEC, 5>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 6: count_chunks<VEC, VEC, 6>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 7: count_chunks<VEC, VEC, 7>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 8: count_chunks<VEC, VEC, 8>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 9: count_chunks<VEC, VEC, 9>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 10: count_chunks<VEC, VEC, 10>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 11: count_chunks<VEC, VEC, 11>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 12: count_chunks<VEC, VEC, 12>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    default: count_chunks<VEC, VEC, 0>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
   }
   if (hist)
     for (u32 q = threadIdx.x; q < kRadix; q += K2_BLOCK)
@@ -278,22 +331,36 @@ k2_write(const int* __restrict__ xy, Plan* plan, const u32* __restrict__ offsets
 
 int k2_tile() { return K2_CHUNK; }
 
-cudaError_t k2_occupancy(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k2_write<true>, K2_BLOCK, 0);
+cudaError_t k2_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k2_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)K2_RING_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k2_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_RING_BYTES);
+  return e;
+}
+
+cudaError_t k2_occupancy(int* count_blocks, int* write_blocks) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(count_blocks, k2_count<true>, K2_BLOCK,
+                                                                K2_RING_BYTES);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(write_blocks, k2_write<true>, K2_BLOCK, 0);
+  return e;
 }
 
 // `status` holds one 32-bit count (then offset) per chunk; `mask` one byte
 // per thread and chunk (n / 8 bytes, rounded up to whole chunks).
+// A 16-byte aligned input is counted through bulk copies (the ring is
+// allocated either way, so both instances share one occupancy).
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
-                      unsigned char* mask, int grid, cudaStream_t st) {
+                      unsigned char* mask, int grid_count, int grid_write, cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
   if (vec) {
-    k2_count<true><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask);
-    k2_write<true><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
+    k2_count<true><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask);
+    k2_write<true><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   } else {
-    k2_count<false><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask);
-    k2_write<false><<<grid, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
+    k2_count<false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask);
+    k2_write<false><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   }
   return cudaGetLastError();
 }

@@ -2,7 +2,7 @@
 // step 4, Section 3.3), one onesweep pass per 8-bit digit.
 //
 // Each pass is one kernel.  A block takes the next tile (dynamic tile id,
-// the following one claimed in advance), counts the tile's digits per warp
+// claimed when the block is ready to start it), counts the tile's digits per warp
 // with shared-memory atomics and publishes the tile's counts at once, so
 // that later tiles' look-backs find them early.  From the per-warp counts
 // every warp knows its first position per digit, so ranking (stable: items
@@ -31,13 +31,19 @@ namespace {
 #define K3_MINBLOCKS_CFG 3
 #endif
 #ifndef K3_RANK_BALLOT
-#define K3_RANK_BALLOT 1      // 1: find equal digits with 8 ballots, 0: with match.any
+#define K3_RANK_BALLOT 3      // lanes with equal digits, from 8 ballots compared with this lane's
+                              // bits as full masks made by prmt (3) or shifts (2), or with
+                              // selects (1); 0: match.any
 #endif
 #ifndef K3_BLOCK_CFG
 #define K3_BLOCK_CFG 256
 #endif
 #ifndef K3_WINDOW_CFG
 #define K3_WINDOW_CFG 8
+#endif
+#ifndef K3_CLAIM_CFG
+#define K3_CLAIM_CFG 1        // when a block claims its next tile: 0 while starting the current one,
+                              // 1 when it starts the next one, 2 after the current look-back
 #endif
 constexpr int K3_BLOCK = K3_BLOCK_CFG;
 constexpr int K3_WARPS = K3_BLOCK / 32;
@@ -60,7 +66,19 @@ __device__ __forceinline__ u32 digit_p(u64 k) {
 
 // Lanes holding the same 8-bit digit (all 32 lanes take part).
 __device__ __forceinline__ u32 same_digit_lanes(u32 dg) {
-#if K3_RANK_BALLOT
+#if K3_RANK_BALLOT == 3
+  return warp_digit_peers(dg);
+#elif K3_RANK_BALLOT == 2
+  // A lane differs from this one where some ballot differs from this
+  // lane's own bit (replicated to a full mask).
+  u32 differ = 0u;
+  #pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const u32 mine = 0u - ((dg >> b) & 1u);
+    differ |= __ballot_sync(0xFFFFFFFFu, mine != 0u) ^ mine;
+  }
+  return ~differ;
+#elif K3_RANK_BALLOT
   u32 peers = 0xFFFFFFFFu;
   #pragma unroll
   for (int b = 0; b < kRadixBits; ++b) {
@@ -119,7 +137,7 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
     if (lane == 31) s_warp_tot[wid] = hinc;
     s_next[d] = 0;
   }
-  if (threadIdx.x == 0) s_tile[0] = atomicAdd(ctr, 1u);
+  if (K3_CLAIM_CFG != 1 && threadIdx.x == 0) s_tile[0] = atomicAdd(ctr, 1u);
   __syncthreads();
   if (owner) {
     u32 off = 0;
@@ -128,12 +146,12 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
   }
 
   for (int buf = 0;; buf ^= 1) {
+    if (K3_CLAIM_CFG == 1 && threadIdx.x == 0) s_tile[buf] = atomicAdd(ctr, 1u);
     for (int q = threadIdx.x; q < K3_WARPS * kRadix; q += K3_BLOCK) (&s_wpos[0][0])[q] = 0u;
     __syncthreads();
     const u32 tile = s_tile[buf];
     if (tile >= ntiles) break;
-    // Claim the following tile now; its id is read after this tile.
-    if (threadIdx.x == 0) s_tile[buf ^ 1] = atomicAdd(ctr, 1u);
+    if (K3_CLAIM_CFG == 0 && threadIdx.x == 0) s_tile[buf ^ 1] = atomicAdd(ctr, 1u);
     const u32 base = tile * (u32)K3_TILE;
     const u32 tile_n = min((u32)K3_TILE, s - base);
     const bool full = tile_n == (u32)K3_TILE;
@@ -244,6 +262,9 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
       if (fail) flag_error(plan, ERR_TIMEOUT);
       s_gbase[d] = s_gstart[d] + excl - tstart;
     }
+    // A tile claimed before its block can start it holds up its successors'
+    // look-backs until it starts (mode 0 claims a whole tile ahead).
+    if (K3_CLAIM_CFG == 2 && threadIdx.x == 0) s_tile[buf ^ 1] = atomicAdd(ctr, 1u);
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
     if (fail) s_fail = 1;
@@ -252,14 +273,29 @@ k3_onesweep(const u64* __restrict__ keys_in, const u32* __restrict__ idx_in,
 
     // Write the digit-ordered tile out: consecutive threads, consecutive
     // addresses within each digit.
-    for (u32 j = threadIdx.x; j < tile_n; j += K3_BLOCK) {
-      const u64 k = s_keys[j];
-      const u32 gp = s_gbase[digit_p<PASS>(k)] + j;
-      if (gp < s) {
-        keys_out[gp] = k;
-        idx_out[gp] = s_idx[j];
-      } else {
-        flag_error(plan, ERR_INTERNAL);
+    if (full) {
+      #pragma unroll
+      for (int it = 0; it < K3_ITEMS; ++it) {
+        const u32 j = it * K3_BLOCK + threadIdx.x;
+        const u64 k = s_keys[j];
+        const u32 gp = s_gbase[digit_p<PASS>(k)] + j;
+        if (gp < s) {
+          keys_out[gp] = k;
+          idx_out[gp] = s_idx[j];
+        } else {
+          flag_error(plan, ERR_INTERNAL);
+        }
+      }
+    } else {
+      for (u32 j = threadIdx.x; j < tile_n; j += K3_BLOCK) {
+        const u64 k = s_keys[j];
+        const u32 gp = s_gbase[digit_p<PASS>(k)] + j;
+        if (gp < s) {
+          keys_out[gp] = k;
+          idx_out[gp] = s_idx[j];
+        } else {
+          flag_error(plan, ERR_INTERNAL);
+        }
       }
     }
   }

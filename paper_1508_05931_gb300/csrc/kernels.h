@@ -24,7 +24,7 @@ cudaError_t launch_gather_labels(const int* pos, const int* labels, const u32* c
                                  u32 skip_first, int* out, u32 cap, cudaStream_t st);
 
 // Resident blocks per SM of the persistent kernels (dynamic tile ids).
-cudaError_t k2_occupancy(int* blocks);
+cudaError_t k2_occupancy(int* count_blocks, int* write_blocks);
 cudaError_t k3_occupancy(int* blocks);
 cudaError_t k4_occupancy(int* blocks);
 
@@ -33,8 +33,9 @@ cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtParti
                       int grid, cudaStream_t st);
 
 int k2_tile();
+cudaError_t k2_configure();
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
-                      unsigned char* mask, int grid, cudaStream_t st);
+                      unsigned char* mask, int grid_count, int grid_write, cudaStream_t st);
 
 int k3_tile();
 size_t k3_dyn_smem();

@@ -44,7 +44,7 @@ struct NoAllocDevice {
   bool ready = false;
   unsigned char* base = nullptr;   // device address of g_noalloc_scratch
   int num_sms = 0;
-  int occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
+  int occ_k2c = 1, occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
 };
 
 NoAllocDevice g_dev[kMaxDevices];
@@ -125,8 +125,9 @@ hull_status noalloc_setup(int dev, NoAllocDevice** out) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) { cudaGetLastError(); return HULL_ECUDA; }
     if (carve(nullptr, prop.multiProcessorCount).total > kNoAllocBytes) return HULL_EINTERNAL;
-    if (k3_configure() != cudaSuccess || k5_configure(&d.occ_k5) != cudaSuccess ||
-        k2_occupancy(&d.occ_k2) != cudaSuccess || k3_occupancy(&d.occ_k3) != cudaSuccess ||
+    if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess ||
+        k5_configure(&d.occ_k5) != cudaSuccess ||
+        k2_occupancy(&d.occ_k2c, &d.occ_k2) != cudaSuccess || k3_occupancy(&d.occ_k3) != cudaSuccess ||
         k4_occupancy(&d.occ_k4) != cudaSuccess || d.occ_k5 < 1) {
       cudaGetLastError();
       return HULL_ECUDA;
@@ -166,7 +167,8 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
     e = launch_k1(d_xy, un, 1u << 22, c.plan, c.partials, k1_grid(un, d->num_sms), st);
   const size_t t2 = (un + k2_tile() - 1) / k2_tile();
   if (e == cudaSuccess)
-    e = launch_k2(d_xy, c.plan, c.keys[0], c.idx[0], c.st_filter, c.mask, grid_for(d->occ_k2, d->num_sms, t2), st);
+    e = launch_k2(d_xy, c.plan, c.keys[0], c.idx[0], c.st_filter, c.mask, grid_for(d->occ_k2c, d->num_sms, t2),
+                   grid_for(d->occ_k2, d->num_sms, t2), st);
   const size_t t3 = (un + k3_tile() - 1) / k3_tile();
   for (u32 p = 0; p < (u32)kMaxPasses && e == cudaSuccess; ++p)
     e = launch_k3(c.keys[p & 1], c.idx[p & 1], c.keys[(p + 1) & 1], c.idx[(p + 1) & 1], c.plan,
