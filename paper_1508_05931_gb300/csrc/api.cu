@@ -274,7 +274,7 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
     mark(c, 3 + (int)p, st);
   }
   const size_t t4 = (n + k4_tile() - 1) / k4_tile();
-  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
+  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, t4, w.lo_xy, w.lo_idx,
                 w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
                 grid_for(c->occ_k4, c->num_sms, t4), st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -650,7 +650,7 @@ hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int3
   e = launch_plan_patch(c->plan, q, st);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t4 = ((size_t)m + k4_tile() - 1) / k4_tile();
-  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, w.lo_xy, w.lo_idx,
+  e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, t4, w.lo_xy, w.lo_idx,
                 w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
                 grid_for(c->occ_k4, c->num_sms, t4), st);
   if (e != cudaSuccess) return cuda_fail(e);

@@ -135,11 +135,12 @@ __device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
 __device__ __forceinline__ void mbar_fence_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_arrive_expect_tx(u64* bar, u32 bytes) {
+// Returns the barrier state token (unused by the callers: they wait on parity).
+__device__ __forceinline__ u64 mbar_arrive_expect_tx(u64* bar, u32 bytes) {
   u64 state;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
                : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
-  (void)state;
+  return state;
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, u32 bytes, u64* bar) {
   asm volatile(

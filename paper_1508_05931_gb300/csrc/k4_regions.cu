@@ -17,13 +17,17 @@
 // survivors of the sequential loop; duplicates of a kept point fall out as
 // equal directions.
 //
-// Reduce-then-scan over chunks of K4_CHUNK sorted points (no block waits
-// for another):
-//   k4_agg      per-chunk extreme directions; the last block scans them into
-//               each chunk's exclusive prefix (starting from d(P_0));
-//   k4_keep     keep decisions, kept points staged per chunk, per-chunk kept
-//               counts; the last block scans the counts into offsets and
-//               adds P_0 and P_l to both region lists;
+// One pass over chunks of K4_CHUNK sorted points, taken in order through a
+// dynamic chunk id:
+//   k4_scan     per chunk: the extreme directions of each thread's points,
+//               of each warp and of the chunk (published at once), the
+//               exclusive prefix over earlier chunks by a decoupled
+//               look-back (one warp, 32 chunks per step, bounded waits; the
+//               operation is a maximum under a total order, so partial
+//               results combine in any order), then the keep decisions, the
+//               kept points staged per chunk and the per-chunk kept counts;
+//               the last block scans the counts into offsets and adds P_0
+//               and P_l to both region lists;
 //   k4_compact  moves the few kept points into the region lists in order.
 #include "hull_internal.cuh"
 #include "kernels.h"
@@ -45,11 +49,16 @@ struct __align__(16) Dir2 {
   int lx, ly, ux, uy;
 };
 
+// Look-back words: one direction per word, with a valid bit, so that a
+// single 64-bit load both finds and reads a published value.  Every
+// direction here has dx <= 0 (P_l has the largest x), so -dx takes 31 bits
+// and dy + 2^30 takes 32.  The words are cleared before each call.
 struct __align__(64) K4Chunk {
-  Dir2 agg;               // chunk aggregate
-  Dir2 excl;              // exclusive prefix over earlier chunks (with d(P_0))
+  u64 agg_lo, agg_up;     // chunk aggregate (lower, upper region)
+  u64 inc_lo, inc_up;     // inclusive prefix through this chunk (with d(P_0))
   uint2 cnt;              // kept points (lower, upper)
   uint2 off;              // exclusive offsets of the same
+  u64 pad[2];
 };
 static_assert(sizeof(K4Chunk) == 64, "chunk record size");
 
@@ -167,68 +176,97 @@ __device__ __forceinline__ bool last_block(Plan* plan, int ctr, bool* s_last) {
   return *s_last;
 }
 
-__global__ void __launch_bounds__(K4_BLOCK, 4)
-k4_agg(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
-       const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks) {
-  __shared__ Dir2 s_w[K4_WARPS];
-  __shared__ bool s_last;
-  if (plan->error & ERR_RANGE) return;
-  const Geo g = make_geo(plan, ka, ia, kb, ib);
-  const u32 nchunks = (g.s + K4_CHUNK - 1) / K4_CHUNK;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    int px[K4_ITEMS], py[K4_ITEMS], pi[K4_ITEMS];
-    signed char side[K4_ITEMS];
-    load_items(g, c * K4_CHUNK + threadIdx.x * K4_ITEMS, px, py, pi, side, false);
-    Dir2 a = warp_scan_dir(thread_agg(g, px, py, side));
-    if (lane == 31) s_w[wid] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Dir2 t = {g.d0x, g.d0y, g.d0x, g.d0y};
-      for (int w = 0; w < K4_WARPS; ++w) combine(t, s_w[w]);
-      chunks[c].agg = t;
+constexpr u64 kDirValid = 1ull << 63;
+__device__ __forceinline__ u64 pack_dir(int dx, int dy) {
+  return kDirValid | ((u64)(u32)(-dx) << 32) | (u64)(u32)(dy + (1 << 30));
+}
+__device__ __forceinline__ void unpack_dir(u64 w, int& dx, int& dy) {
+  dx = -(int)((w >> 32) & 0x7FFFFFFFu);
+  dy = (int)((long long)(u32)w - (1ll << 30));
+}
+__device__ __forceinline__ Dir2 shfl_xor_dir(const Dir2& v, int o) {
+  Dir2 r;
+  r.lx = __shfl_xor_sync(0xFFFFFFFFu, v.lx, o);
+  r.ly = __shfl_xor_sync(0xFFFFFFFFu, v.ly, o);
+  r.ux = __shfl_xor_sync(0xFFFFFFFFu, v.ux, o);
+  r.uy = __shfl_xor_sync(0xFFFFFFFFu, v.uy, o);
+  return r;
+}
+
+// Exclusive prefix of chunk c (one warp): lane l inspects chunk
+// base - l for base = c - 1, c - 33, ...; in each region every chunk up to
+// the nearest inclusive prefix contributes.  False (ERR_TIMEOUT set) if a
+// predecessor published nothing within the spin limit.
+__device__ __forceinline__ bool lookback_dir(K4Chunk* chunks, u32 c, Plan* plan, u32 spin,
+                                             Dir2 ident, Dir2* out) {
+  const int lane = threadIdx.x & 31;
+  Dir2 acc = ident;
+  bool done_lo = false, done_up = false;
+  long long base = (long long)c - 1;
+  while (base >= 0 && !(done_lo && done_up)) {
+    const long long t = base - lane;
+    // Before chunk 0 the identity acts as an inclusive prefix.
+    u64 il = kDirValid, iu = kDirValid, al = 0, au = 0;
+    bool bad = false;
+    if (t >= 0) {
+      K4Chunk* ch = &chunks[t];
+      u32 it = 0;
+      for (;;) {
+        il = ld_relaxed_u64(&ch->inc_lo); iu = ld_relaxed_u64(&ch->inc_up);
+        al = ld_relaxed_u64(&ch->agg_lo); au = ld_relaxed_u64(&ch->agg_up);
+        if (((il | al) & kDirValid) && ((iu | au) & kDirValid)) break;
+        if (++it > spin || aborted(plan)) { bad = true; break; }
+        spin_pause(it);
+      }
     }
-    __syncthreads();
+    if (__any_sync(0xFFFFFFFFu, bad)) {
+      if (lane == 0) flag_error(plan, ERR_TIMEOUT);
+      return false;
+    }
+    Dir2 v = ident;
+    const u32 ml = __ballot_sync(0xFFFFFFFFu, (il & kDirValid) != 0);
+    const u32 mu = __ballot_sync(0xFFFFFFFFu, (iu & kDirValid) != 0);
+    const int sl = ml ? (__ffs(ml) - 1) : 31, su = mu ? (__ffs(mu) - 1) : 31;
+    if (t >= 0 && !done_lo && lane <= sl) unpack_dir((il & kDirValid) ? il : al, v.lx, v.ly);
+    if (t >= 0 && !done_up && lane <= su) unpack_dir((iu & kDirValid) ? iu : au, v.ux, v.uy);
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const Dir2 w = shfl_xor_dir(v, o);
+      combine(v, w);
+    }
+    combine(acc, v);
+    done_lo = done_lo || ml != 0u;
+    done_up = done_up || mu != 0u;
+    base -= 32;
   }
-  if (!last_block(plan, CTR_REGION, &s_last)) return;
-  // Exclusive prefix of every chunk: per-thread segments, block scan.
-  const u32 per = (nchunks + K4_BLOCK - 1) / K4_BLOCK;
-  const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
-  Dir2 seg = {g.d0x, g.d0y, g.d0x, g.d0y};
-  for (u32 c = lo; c < hi; ++c) {
-    const volatile int* a = reinterpret_cast<const volatile int*>(&chunks[c].agg);
-    Dir2 v = {a[0], a[1], a[2], a[3]};
-    combine(seg, v);
-  }
-  Dir2 inc = warp_scan_dir(seg);
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  Dir2 run = {g.d0x, g.d0y, g.d0x, g.d0y};
-  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
-  Dir2 lex = shfl_up_dir(inc, 1);
-  if (lane > 0) combine(run, lex);
-  for (u32 c = lo; c < hi; ++c) {
-    chunks[c].excl = run;
-    const volatile int* a = reinterpret_cast<const volatile int*>(&chunks[c].agg);
-    Dir2 v = {a[0], a[1], a[2], a[3]};
-    combine(run, v);
-  }
+  *out = acc;
+  return true;
 }
 
 __global__ void __launch_bounds__(K4_BLOCK, 4)
-k4_keep(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
+k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
         const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks,
         int2* __restrict__ t_lo_xy, int* __restrict__ t_lo_idx, int2* __restrict__ t_up_xy,
         int* __restrict__ t_up_idx, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
         int2* __restrict__ up_xy, int* __restrict__ up_idx) {
   __shared__ Dir2 s_w[K4_WARPS];
+  __shared__ Dir2 s_excl;
   __shared__ u32 s_wc[K4_WARPS][2];
+  __shared__ u32 s_chunk;
+  __shared__ int s_fail;
   __shared__ bool s_last;
   if (plan->error & ERR_RANGE) return;
   const Geo g = make_geo(plan, ka, ia, kb, ib);
   const u32 nchunks = (g.s + K4_CHUNK - 1) / K4_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+  const u32 spin = plan->spin_limit;
+  const Dir2 ident = {g.d0x, g.d0y, g.d0x, g.d0y};
+  bool failed = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&plan->ctr[CTR_REGION], 1u);
+    __syncthreads();
+    const u32 c = s_chunk;
+    if (c >= nchunks) break;
     int px[K4_ITEMS], py[K4_ITEMS], pi[K4_ITEMS];
     signed char side[K4_ITEMS];
     load_items(g, c * K4_CHUNK + threadIdx.x * K4_ITEMS, px, py, pi, side, true);
@@ -237,7 +275,33 @@ k4_keep(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __res
     Dir2 lex = shfl_up_dir(inc, 1);
     if (lane == 31) s_w[wid] = inc;
     __syncthreads();
-    Dir2 run = chunks[c].excl;
+    // Warp 0: publish the chunk aggregate, look back, publish the prefix.
+    if (wid == 0) {
+      Dir2 t = ident;
+      #pragma unroll
+      for (int w = 0; w < K4_WARPS; ++w) combine(t, s_w[w]);
+      K4Chunk* ch = &chunks[c];
+      if (lane == 0) {
+        st_relaxed_u64(c == 0 ? &ch->inc_lo : &ch->agg_lo, pack_dir(t.lx, t.ly));
+        st_relaxed_u64(c == 0 ? &ch->inc_up : &ch->agg_up, pack_dir(t.ux, t.uy));
+      }
+      Dir2 excl = ident;
+      bool ok = true;
+      if (c > 0) ok = lookback_dir(chunks, c, plan, spin, ident, &excl);
+      if (lane == 0) {
+        s_fail = ok ? 0 : 1;
+        s_excl = excl;
+        if (ok && c > 0) {
+          Dir2 in = excl;
+          combine(in, t);
+          st_relaxed_u64(&ch->inc_lo, pack_dir(in.lx, in.ly));
+          st_relaxed_u64(&ch->inc_up, pack_dir(in.ux, in.uy));
+        }
+      }
+    }
+    __syncthreads();
+    if (s_fail) { failed = true; break; }
+    Dir2 run = s_excl;
     for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
     if (lane > 0) combine(run, lex);
     unsigned keep_lo = 0, keep_up = 0;
@@ -276,6 +340,7 @@ k4_keep(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __res
     }
     __syncthreads();
   }
+  if (failed) return;
   if (!last_block(plan, CTR_REGION2, &s_last)) return;
   const u32 per = (nchunks + K4_BLOCK - 1) / K4_BLOCK;
   const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
@@ -319,7 +384,7 @@ k4_compact(Plan* plan, const K4Chunk* __restrict__ chunks, const int2* __restric
            const int* __restrict__ t_lo_idx, const int2* __restrict__ t_up_xy,
            const int* __restrict__ t_up_idx, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
            int2* __restrict__ up_xy, int* __restrict__ up_idx) {
-  if (plan->error & ERR_RANGE) return;
+  if (plan->error & (ERR_RANGE | ERR_TIMEOUT)) return;
   const u32 s = plan->s;
   const u32 nchunks = (s + K4_CHUNK - 1) / K4_CHUNK;
   for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -343,18 +408,20 @@ int k4_tile() { return K4_CHUNK; }
 size_t k4_status_bytes() { return sizeof(K4Chunk); }
 
 cudaError_t k4_occupancy(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k4_keep, K4_BLOCK, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k4_scan, K4_BLOCK, 0);
 }
 
-// `status` holds one K4Chunk per chunk; t_* are staging areas of at least
-// ceil(s / K4_CHUNK) * K4_CHUNK slots each.
+// `status` holds one K4Chunk per chunk, `nrec` >= ceil(s / K4_CHUNK) of
+// them (cleared here); t_* are staging areas of at least nrec * K4_CHUNK
+// slots each.
 cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib, Plan* plan,
-                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                      void* status, size_t nrec, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
                       int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st) {
   K4Chunk* ch = reinterpret_cast<K4Chunk*>(status);
-  k4_agg<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch);
-  k4_keep<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx,
+  cudaError_t e = cudaMemsetAsync(status, 0, nrec * sizeof(K4Chunk), st);
+  if (e != cudaSuccess) return e;
+  k4_scan<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx,
                                      lo_xy, lo_idx, up_xy, up_idx);
   k4_compact<<<grid, K4_BLOCK, 0, st>>>(plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx,
                                         up_xy, up_idx);

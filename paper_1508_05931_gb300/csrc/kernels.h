@@ -46,7 +46,7 @@ cudaError_t launch_k3(const u64* kin, const u32* iin, u64* kout, u32* iout, Plan
 int k4_tile();
 size_t k4_status_bytes();
 cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib, Plan* plan,
-                      void* status, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                      void* status, size_t nrec, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
                       int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st);
 

@@ -175,7 +175,7 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
                   c.st_sort, p, grid_for(d->occ_k3, d->num_sms, t3), st);
   const size_t t4 = (un + k4_tile() - 1) / k4_tile();
   if (e == cudaSuccess)
-    e = launch_k4(c.keys[0], c.idx[0], c.keys[1], c.idx[1], c.plan, c.st_region, c.lo_xy, c.lo_idx,
+    e = launch_k4(c.keys[0], c.idx[0], c.keys[1], c.idx[1], c.plan, c.st_region, t4, c.lo_xy, c.lo_idx,
                   c.up_xy, c.up_idx, c.h_xy[0], c.h_idx[0], c.h_xy[1], c.h_idx[1],
                   grid_for(d->occ_k4, d->num_sms, t4), st);
   const size_t chunks = (un + 4) / (size_t)k5_chunk() + 2;
