@@ -157,29 +157,7 @@ __device__ int build_chain(Smem<BLOCK>& S, const int2* xy, const int* idx, int m
     S.ccnt[threadIdx.x] = leaf_chain(S.sx, S.sy, S.si, b, max(0, min(BT_LEAF, len - b)), sgn);
     __syncthreads();
     const int nleaf = (len + BT_LEAF - 1) / BT_LEAF;
-    for (int step = 1; step < nleaf; step <<= 1) {
-      const int npair = (nleaf + 2 * step - 1) / (2 * step);
-      for (int p = wid; p < npair; p += W) {
-        const int la = 2 * p * step, lb = la + step;
-        if (lb >= nleaf) continue;
-        const int aB = la * BT_LEAF, bB = lb * BT_LEAF;
-        const int alpha = S.ccnt[la], beta = S.ccnt[lb];
-        SmemChain A{S.sx + aB, S.sy + aB}, Bc{S.sx + bB, S.sy + bB};
-        int is, js;
-        bridge(A, alpha, Bc, beta, sgn, is, js);
-        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
-        for (int o = 0; o < n2; o += 32) {
-          const int q = o + lane;
-          int vx = 0, vy = 0, vi = 0;
-          if (q < n2) { vx = S.sx[src + q]; vy = S.sy[src + q]; vi = S.si[src + q]; }
-          __syncwarp();
-          if (q < n2) { S.sx[dst + q] = vx; S.sy[dst + q] = vy; S.si[dst + q] = vi; }
-          __syncwarp();
-        }
-        if (lane == 0) S.ccnt[la] = is + 1 + n2;
-      }
-      __syncthreads();
-    }
+    merge_tree<BT_LEAF>(S.sx, S.sy, S.si, S.ccnt, nleaf, sgn);
     const int hc = S.ccnt[0];
     if (nch == 1) { *where = 0; return hc; }
     for (int i = threadIdx.x; i < hc; i += BLOCK) {

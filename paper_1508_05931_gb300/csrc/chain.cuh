@@ -75,6 +75,27 @@ __device__ __forceinline__ void bridge(const AccA& A, int alpha, const AccB& B, 
   jstar = tangent(B, beta, A(lo), sgn);
 }
 
+// The same bridge found by one thread: starting from the last point of A
+// and the first of B, step back along A while a_i-1 -> a_i -> b_j does not
+// turn strictly and forward along B while a_i -> b_j -> b_j+1 does not,
+// until neither moves.  Both junction turns are then strict, so the line
+// a_i b_j is a common tangent of the two convex chains and the merged chain
+// is the same as bridge()'s.  The walk is short when the bridge lies near
+// the junction, as it does for chains of few points.
+template <class AccA, class AccB>
+__device__ __forceinline__ void walk_bridge(const AccA& A, int alpha, const AccB& B, int beta, int sgn,
+                                            int& istar, int& jstar) {
+  int i = alpha - 1, j = 0;
+  bool moved = true;
+  while (moved) {
+    moved = false;
+    while (i > 0 && turn(sgn, A(i - 1), A(i), B(j)) <= 0) { --i; moved = true; }
+    while (j < beta - 1 && turn(sgn, A(i), B(j), B(j + 1)) <= 0) { ++j; moved = true; }
+  }
+  istar = i;
+  jstar = j;
+}
+
 // Stack-based chain of l <= K points held in shared memory at [b, b + l),
 // built in place (the stack never overtakes the read position).  Returns
 // the chain length.
@@ -90,6 +111,61 @@ __device__ __forceinline__ int leaf_chain(int* sx, int* sy, int* si, int b, int 
     ++k;
   }
   return k;
+}
+
+#ifndef CHAIN_WALK_MAX
+#define CHAIN_WALK_MAX 64
+#endif
+
+// Merges nleaf leaf chains held in shared memory (leaf l at [l * LEAF, ...),
+// cnt[l] points) level by level into one chain at [0, cnt[0]).  While the
+// chains of a level come from at most CHAIN_WALK_MAX points each, one thread
+// merges a pair with walk_bridge; longer ones take a warp each (bridge).
+// Called by every thread of the block.
+template <int LEAF>
+__device__ __forceinline__ void merge_tree(int* sx, int* sy, int* si, int* cnt, int nleaf, int sgn) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nthreads = blockDim.x, nwarps = nthreads >> 5;
+  for (int step = 1; step < nleaf; step <<= 1) {
+    const int npair = (nleaf + 2 * step - 1) / (2 * step);
+    if (step * LEAF <= CHAIN_WALK_MAX) {
+      for (int p = threadIdx.x; p < npair; p += nthreads) {
+        const int la = 2 * p * step, lb = la + step;
+        if (lb >= nleaf) continue;
+        const int aB = la * LEAF, bB = lb * LEAF;
+        const int alpha = cnt[la], beta = cnt[lb];
+        SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
+        int is, js;
+        walk_bridge(A, alpha, B, beta, sgn, is, js);
+        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
+        for (int q = 0; q < n2; ++q) {
+          sx[dst + q] = sx[src + q]; sy[dst + q] = sy[src + q]; si[dst + q] = si[src + q];
+        }
+        cnt[la] = is + 1 + n2;
+      }
+    } else {
+      for (int p = wid; p < npair; p += nwarps) {
+        const int la = 2 * p * step, lb = la + step;
+        if (lb >= nleaf) continue;
+        const int aB = la * LEAF, bB = lb * LEAF;
+        const int alpha = cnt[la], beta = cnt[lb];
+        SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
+        int is, js;
+        bridge(A, alpha, B, beta, sgn, is, js);
+        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
+        for (int o = 0; o < n2; o += 32) {
+          const int q = o + lane;
+          int vx = 0, vy = 0, vi = 0;
+          if (q < n2) { vx = sx[src + q]; vy = sy[src + q]; vi = si[src + q]; }
+          __syncwarp();
+          if (q < n2) { sx[dst + q] = vx; sy[dst + q] = vy; si[dst + q] = vi; }
+          __syncwarp();
+        }
+        if (lane == 0) cnt[la] = is + 1 + n2;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace chain

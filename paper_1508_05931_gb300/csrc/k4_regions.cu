@@ -36,9 +36,12 @@ namespace gbh {
 
 namespace {
 
-constexpr int K4_BLOCK = 256;
+#ifndef K4_BLOCK_CFG
+#define K4_BLOCK_CFG 256
+#endif
+constexpr int K4_BLOCK = K4_BLOCK_CFG;
 constexpr int K4_ITEMS = 8;
-constexpr int K4_CHUNK = K4_BLOCK * K4_ITEMS;      // 2048 sorted points
+constexpr int K4_CHUNK = K4_BLOCK * K4_ITEMS;      // sorted points per chunk
 constexpr int K4_WARPS = K4_BLOCK / 32;
 
 // Extreme directions seen so far: lower region (counter-clockwise-most)
@@ -243,7 +246,7 @@ __device__ __forceinline__ bool lookback_dir(K4Chunk* chunks, u32 c, Plan* plan,
   return true;
 }
 
-__global__ void __launch_bounds__(K4_BLOCK, 4)
+__global__ void __launch_bounds__(K4_BLOCK, 1024 / K4_BLOCK)
 k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
         const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks,
         int2* __restrict__ t_lo_xy, int* __restrict__ t_lo_idx, int2* __restrict__ t_up_xy,

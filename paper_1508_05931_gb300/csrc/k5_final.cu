@@ -4,10 +4,15 @@
 //
 //   phase A  each block takes chunks of K5_CHUNK consecutive points of a
 //            chain, every thread builds the chain of its K5_LEAF points with
-//            the stack rule (pop while the turn is not strict), and warps
-//            merge adjacent sub-chains level by level in shared memory;
-//   phase B  adjacent chunk chains are merged level by level across the
-//            grid (ping-pong buffers, bounded grid barriers);
+//            the stack rule (pop while the turn is not strict), and adjacent
+//            sub-chains are merged level by level in shared memory (one
+//            thread per pair while they are short, then one warp per pair);
+//   phase B  when all chunk chains together fit in one block's shared
+//            memory (the usual case: a chunk's chain holds few of its
+//            points), block 0 gathers them after one grid barrier and merges
+//            them there level by level; otherwise adjacent chunk chains are
+//            merged level by level across the grid (ping-pong buffers,
+//            bounded grid barriers);
 //   output   lower chain, then the upper chain reversed without its two
 //            endpoints: counter-clockwise from the lexicographic minimum.
 //
@@ -25,10 +30,19 @@ using namespace chain;
 
 namespace {
 
-constexpr int K5_BLOCK = 512;
+#ifndef K5_BLOCK_CFG
+#define K5_BLOCK_CFG 1024
+#endif
+constexpr int K5_BLOCK = K5_BLOCK_CFG;
 constexpr int K5_WARPS = K5_BLOCK / 32;
-constexpr int K5_LEAF = 8;
-constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // 4096 points per chunk
+#ifndef K5_LEAF_CFG
+#define K5_LEAF_CFG 2
+#endif
+constexpr int K5_LEAF = K5_LEAF_CFG;
+constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // points per chunk
+// Points block 0 can hold for the shared-memory phase B (and the size of
+// every block's chunk buffer).
+constexpr int K5_SMEM_PTS = K5_CHUNK > 4096 ? K5_CHUNK : 4096;
 
 // Barrier over the first `nblocks` blocks of the (co-resident) grid.
 __device__ bool grid_barrier(Plan* plan, u32 spin, u32 nblocks) {
@@ -77,9 +91,11 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
          int4* __restrict__ jobs, int* __restrict__ out, long long cap) {
   extern __shared__ __align__(16) unsigned char k5_smem[];
   int* sx = reinterpret_cast<int*>(k5_smem);
-  int* sy = sx + K5_CHUNK;
-  int* si = sy + K5_CHUNK;
+  int* sy = sx + K5_SMEM_PTS;
+  int* si = sy + K5_SMEM_PTS;
   __shared__ int s_cnt[K5_BLOCK];
+  __shared__ int s_start[K5_BLOCK];
+  __shared__ int s_wsum[K5_WARPS];
 
   if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL)) return;
   const u32 spin = plan->spin_limit;
@@ -131,29 +147,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     }
     __syncthreads();
     const int nleaf = (len + K5_LEAF - 1) / K5_LEAF;
-    for (int step = 1; step < nleaf; step <<= 1) {
-      const int npair = (nleaf + 2 * step - 1) / (2 * step);
-      for (int p = wid; p < npair; p += K5_WARPS) {
-        const int la = 2 * p * step, lb = la + step;
-        if (lb >= nleaf) continue;
-        const int aBase = la * K5_LEAF, bBase = lb * K5_LEAF;
-        const int alpha = s_cnt[la], beta = s_cnt[lb];
-        SmemChain A{sx + aBase, sy + aBase}, B{sx + bBase, sy + bBase};
-        int is, js;
-        bridge(A, alpha, B, beta, sgn, is, js);
-        const int dst = aBase + is + 1, src = bBase + js, n2 = beta - js;
-        for (int o = 0; o < n2; o += 32) {
-          const int q = o + lane;
-          int vx = 0, vy = 0, vi = 0;
-          if (q < n2) { vx = sx[src + q]; vy = sy[src + q]; vi = si[src + q]; }
-          __syncwarp();
-          if (q < n2) { sx[dst + q] = vx; sy[dst + q] = vy; si[dst + q] = vi; }
-          __syncwarp();
-        }
-        if (lane == 0) s_cnt[la] = is + 1 + n2;
-      }
-      __syncthreads();
-    }
+    merge_tree<K5_LEAF>(sx, sy, si, s_cnt, nleaf, sgn);
     const int hc = s_cnt[0];
     const u32 out0 = cs.slot0[c] + first;
     for (int i = threadIdx.x; i < hc; i += K5_BLOCK) {
@@ -164,7 +158,82 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     __syncthreads();
   }
 
-  // ---------------- phase B: merge chunk chains across the grid
+  // ---------------- phase B, small case: one block, shared memory
+  if (!grid_barrier(plan, spin, nblk)) return;
+  if (total_chunks <= (u32)K5_BLOCK) {
+    // Chunk chain lengths and their exclusive prefix (same on every block).
+    const int len_c = threadIdx.x < total_chunks ? (int)__ldcg(&cnt0[threadIdx.x]) : 0;
+    int inc = len_c;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_wsum[wid] = inc;
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < K5_WARPS; ++w) {
+      if (w < wid) off += s_wsum[w];
+      tot += s_wsum[w];
+    }
+    if (tot <= K5_SMEM_PTS) {
+      if (blockIdx.x != 0) return;
+      s_cnt[threadIdx.x] = len_c;
+      s_start[threadIdx.x] = off + inc - len_c;
+      __syncthreads();
+      // Gather: warp w copies chunk chains w, w + K5_WARPS, ...
+      for (u32 ch = wid; ch < total_chunks; ch += K5_WARPS) {
+        const u32 src = ch < cs.nchunk[0] ? ch * K5_CHUNK : cs.slot0[1] + (ch - cs.nchunk[0]) * K5_CHUNK;
+        const int dst = s_start[ch];
+        for (int q = lane; q < s_cnt[ch]; q += 32) {
+          const int2 p = __ldcg(&h0_xy[src + q]);
+          sx[dst + q] = p.x; sy[dst + q] = p.y; si[dst + q] = __ldcg(&h0_idx[src + q]);
+        }
+      }
+      __syncthreads();
+      // Merge both regions' chains level by level (one warp per pair).
+      const int n0 = (int)cs.nchunk[0], n1 = (int)cs.nchunk[1];
+      for (int step = 1; step < max(n0, n1); step <<= 1) {
+        const int np0 = (n0 + 2 * step - 1) / (2 * step), np1 = (n1 + 2 * step - 1) / (2 * step);
+        for (int job = wid; job < np0 + np1; job += K5_WARPS) {
+          const int c = job < np0 ? 0 : 1;
+          const int p = c == 0 ? job : job - np0;
+          const int k0 = c == 0 ? 0 : n0, kn = c == 0 ? n0 : n1;
+          const int a = 2 * p * step, b = a + step;
+          if (b >= kn) continue;
+          const int ka = k0 + a, kb = k0 + b;
+          const int alpha = s_cnt[ka], beta = s_cnt[kb];
+          SmemChain A{sx + s_start[ka], sy + s_start[ka]}, B{sx + s_start[kb], sy + s_start[kb]};
+          int is, js;
+          bridge(A, alpha, B, beta, c == 0 ? 1 : -1, is, js);
+          const int dst = s_start[ka] + is + 1, src = s_start[kb] + js, n2 = beta - js;
+          for (int o = 0; o < n2; o += 32) {
+            const int q = o + lane;
+            int vx = 0, vy = 0, vi = 0;
+            if (q < n2) { vx = sx[src + q]; vy = sy[src + q]; vi = si[src + q]; }
+            __syncwarp();
+            if (q < n2) { sx[dst + q] = vx; sy[dst + q] = vy; si[dst + q] = vi; }
+            __syncwarp();
+          }
+          if (lane == 0) s_cnt[ka] = is + 1 + n2;
+        }
+        __syncthreads();
+      }
+      // Output: lower chain, then the upper chain reversed.
+      const int hl = s_cnt[0], hu = s_cnt[n0], ub = s_start[n0];
+      const long long h = (long long)hl + (long long)hu - 2;
+      if (threadIdx.x == 0) {
+        plan->h = (u32)h; plan->h_lo = (u32)hl; plan->h_up = (u32)hu;
+        if (h > cap) flag_error(plan, ERR_CAPACITY);
+      }
+      if (h > cap) return;
+      for (int q = threadIdx.x; q < (int)h; q += K5_BLOCK)
+        out[q] = q < hl ? si[q] : si[ub + (hu - 2) - (q - hl)];
+      return;
+    }
+  }
+
+  // ---------------- phase B, general case: merge chunk chains across the grid
   int2* cur_xy = h0_xy; int* cur_idx = h0_idx; u32* cur_cnt = cnt0;
   int2* nxt_xy = h1_xy; int* nxt_idx = h1_idx; u32* nxt_cnt = cnt1;
   const u32 maxchunks = max(cs.nchunk[0], cs.nchunk[1]);
@@ -238,7 +307,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
 }  // namespace
 
 int k5_chunk() { return K5_CHUNK; }
-size_t k5_dyn_smem() { return (size_t)K5_CHUNK * 3 * sizeof(int); }
+size_t k5_dyn_smem() { return (size_t)K5_SMEM_PTS * 3 * sizeof(int); }
 
 cudaError_t k5_configure(int* max_blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k5_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
