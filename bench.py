@@ -34,8 +34,9 @@ WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk
 # 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
 PAPER_MPTS = 40.0 / 0.8645
 # Kernels per hull_compute: extremes, filter count + write, 8 radix passes,
-# region aggregate + keep + compact, finalisation.
-LAUNCHES_PER_HULL = 1 + 2 + 8 + 3 + 1
+# region scan + compact, finalisation (the clearing of the region look-back
+# words is a memset, not one of these kernels).
+LAUNCHES_PER_HULL = 1 + 2 + 8 + 2 + 1
 
 
 def parse():
