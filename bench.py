@@ -374,15 +374,16 @@ def main():
     value = job_mpts(pts_step, world, args.steps, ms / 1e3)
 
     # e2e: the same steps through the host entry point (pinned host input,
-    # H2D copy, compute, D2H of the vertex indices inside the timed region).
+    # H2D copy, compute, D2H of the vertex indices inside the timed region):
+    # one hull_compute_host_multi call per step, which copies the second set
+    # while the first one's hull is computed.
     host_sets = [torch.as_tensor(p).pin_memory() for p in sets]
-    host_out = torch.empty(args.n, dtype=torch.int32).pin_memory()
+    host_outs = [torch.empty(len(p), dtype=torch.int32).pin_memory() for p in sets]
     h_counts = []
 
     def host_step():
         h_counts.clear()
-        for hp in host_sets:
-            r = ctx.compute_host(hp, out=host_out, stream=stream)
+        for r in ctx.compute_host_multi(host_sets, outs=host_outs, stream=stream):
             h_counts.append(len(r))
 
     for _ in range(2):
@@ -435,7 +436,7 @@ def main():
                        "second_round_per_hull": prof["second_round"] / calls},
             "gpu_launches": args.steps * len(sets) * LAUNCHES_PER_HULL,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
-                    "d2h_bytes_per_step": 4 * sum(h_counts)},
+                    "d2h_bytes_per_step": 4 * sum(h_counts), "api": "hull_compute_host_multi"},
             "roofline": roofline}
     if clocks:
         line["clocks"] = clocks

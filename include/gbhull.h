@@ -95,6 +95,19 @@ hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t 
 hull_status hull_compute_host(hull_ctx *ctx, const int32_t *h_xy, int64_t n, int32_t *h_out,
                               int64_t cap, int64_t *h_count, void *stream);
 
+/* Several independent hulls from host buffers in one call, pipelined: while
+ * the hull of input k is computed on `stream`, input k + 1 is copied to a
+ * second device staging buffer on the context's copy stream (inputs should
+ * be pinned for the copies to overlap).  For k in [0, count): h_xy[k] holds
+ * n[k] points (host int32[n[k]][2]); h_out[k] (host int32[cap[k]]) receives
+ * the CCW vertex indices and h_count[k] the hull size.  Stops at the first
+ * failing input and returns its status (its h_count is set as by
+ * hull_compute_host; later entries are set to 0).  count = 0 does nothing.
+ * Errors: those of hull_compute_host; EINVAL for count < 0 or NULL arrays. */
+hull_status hull_compute_host_multi(hull_ctx *ctx, int32_t count, const int32_t *const *h_xy,
+                                    const int64_t *n, int32_t *const *h_out, const int64_t *cap,
+                                    int64_t *h_count, void *stream);
+
 /* B independent hulls in one call (one persistent launch per size bucket:
  * each block runs the whole pipeline on one instance at a time, instances
  * taken largest first).  d_offsets: device int64[B+1], instance b is points

@@ -48,6 +48,9 @@ struct HostStage {
   size_t cap = 0;
   int32_t* d_in = nullptr;     // device copy of host points
   int32_t* d_out = nullptr;    // device output for host calls
+  int32_t* d_in2 = nullptr;    // second input buffer of hull_compute_host_multi (same cap)
+  cudaStream_t copy = nullptr; // copy stream of hull_compute_host_multi
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
 };
 
 // Workspace of the batched kernels: per-instance scratch slots and tables.
@@ -354,6 +357,41 @@ void autotune_save(const hull_ctx* c) {
   std::fclose(f);
 }
 
+// Device staging for the host entry points: input and output buffers of at
+// least n points (two input buffers, a copy stream and its events with
+// `pipelined`).  Growing synchronises the device.
+hull_status ensure_host_stage(hull_ctx* c, size_t n, bool pipelined) {
+  HostStage& hs = c->hs;
+  if (n > hs.cap || (pipelined && !hs.d_in2)) {
+    cudaDeviceSynchronize();
+    const size_t hc = align_up(n > hs.cap ? n : hs.cap, 65536);
+    if (hs.d_in) cudaFree(hs.d_in);
+    if (hs.d_out) cudaFree(hs.d_out);
+    if (hs.d_in2) cudaFree(hs.d_in2);
+    hs.d_in = hs.d_out = hs.d_in2 = nullptr;
+    hs.cap = 0;
+    bool ok = cudaMalloc(&hs.d_in, hc * 8) == cudaSuccess && cudaMalloc(&hs.d_out, hc * 4) == cudaSuccess;
+    if (ok && pipelined) ok = cudaMalloc(&hs.d_in2, hc * 8) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (hs.d_in) cudaFree(hs.d_in);
+      if (hs.d_out) cudaFree(hs.d_out);
+      if (hs.d_in2) cudaFree(hs.d_in2);
+      hs.d_in = hs.d_out = hs.d_in2 = nullptr;
+      return HULL_ENOMEM;
+    }
+    hs.cap = hc;
+  }
+  if (pipelined && !hs.copy) {
+    if (cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    for (int k = 0; k < 2; ++k)
+      if (cudaEventCreateWithFlags(&hs.copied[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&hs.consumed[k], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaErrorUnknown);
+  }
+  return HULL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -441,6 +479,12 @@ void hull_destroy(hull_ctx* c) {
   free_ws(c->ws);
   if (c->hs.d_in) cudaFree(c->hs.d_in);
   if (c->hs.d_out) cudaFree(c->hs.d_out);
+  if (c->hs.d_in2) cudaFree(c->hs.d_in2);
+  for (int k = 0; k < 2; ++k) {
+    if (c->hs.copied[k]) cudaEventDestroy(c->hs.copied[k]);
+    if (c->hs.consumed[k]) cudaEventDestroy(c->hs.consumed[k]);
+  }
+  if (c->hs.copy) cudaStreamDestroy(c->hs.copy);
   for (int k = 0; k <= HULL_NUM_STAGES; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : {(void*)c->W, c->W16, (void*)c->adam_m, (void*)c->adam_v, (void*)c->grad, (void*)c->feat,
@@ -495,20 +539,8 @@ hull_status hull_compute_host(hull_ctx* c, const int32_t* h_xy, int64_t n, int32
   if (n == 0) return HULL_OK;
   DevGuard g(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((size_t)n > c->hs.cap) {
-    cudaDeviceSynchronize();
-    if (c->hs.d_in) cudaFree(c->hs.d_in);
-    if (c->hs.d_out) cudaFree(c->hs.d_out);
-    c->hs = HostStage{};
-    size_t hc = align_up((size_t)n, 65536);
-    if (cudaMalloc(&c->hs.d_in, hc * 8) != cudaSuccess || cudaMalloc(&c->hs.d_out, hc * 4) != cudaSuccess) {
-      cudaGetLastError();
-      if (c->hs.d_in) cudaFree(c->hs.d_in);
-      c->hs = HostStage{};
-      return HULL_ENOMEM;
-    }
-    c->hs.cap = hc;
-  }
+  hull_status gr = ensure_host_stage(c, (size_t)n, false);
+  if (gr != HULL_OK) return gr;
   cudaError_t e = cudaMemcpyAsync(c->hs.d_in, h_xy, (size_t)n * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e);
   int64_t h = 0;
@@ -521,6 +553,69 @@ hull_status hull_compute_host(hull_ctx* c, const int32_t* h_xy, int64_t n, int32
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return HULL_OK;
+}
+
+hull_status hull_compute_host_multi(hull_ctx* c, int32_t count, const int32_t* const* h_xy,
+                                    const int64_t* n, int32_t* const* h_out, const int64_t* cap,
+                                    int64_t* h_count, void* stream) {
+  if (!c || count < 0) return HULL_EINVAL;
+  if (count == 0) return HULL_OK;
+  if (!h_xy || !n || !h_out || !cap || !h_count) return HULL_EINVAL;
+  for (int32_t k = 0; k < count; ++k) {
+    h_count[k] = 0;
+    if (n[k] < 0 || cap[k] < 0 || n[k] > (int64_t)kMaxN || (n[k] > 0 && !h_xy[k]) || (cap[k] > 0 && !h_out[k]))
+      return HULL_EINVAL;
+  }
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t nmax = 1;
+  for (int32_t k = 0; k < count; ++k) nmax = n[k] > nmax ? n[k] : nmax;
+  hull_status r = ensure_host_stage(c, (size_t)nmax, true);
+  if (r != HULL_OK) return r;
+  HostStage& hs = c->hs;
+  int32_t* buf[2] = {hs.d_in, hs.d_in2};
+  // The copy stream starts after everything already queued on `stream`.
+  cudaError_t e = cudaEventRecord(hs.consumed[0], st);
+  if (e == cudaSuccess) e = cudaEventRecord(hs.consumed[1], st);
+  auto issue_copy = [&](int32_t k) -> cudaError_t {
+    const int b = k & 1;
+    cudaError_t ce = cudaStreamWaitEvent(hs.copy, hs.consumed[b], 0);
+    if (ce == cudaSuccess && n[k] > 0)
+      ce = cudaMemcpyAsync(buf[b], h_xy[k], (size_t)n[k] * 8, cudaMemcpyHostToDevice, hs.copy);
+    if (ce == cudaSuccess) ce = cudaEventRecord(hs.copied[b], hs.copy);
+    return ce;
+  };
+  if (e == cudaSuccess) e = issue_copy(0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int32_t k = 0; k < count; ++k) {
+    const int b = k & 1;
+    // Input k + 1 goes into the other buffer once input k - 1 is done with it.
+    if (k + 1 < count) {
+      e = issue_copy(k + 1);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    e = cudaStreamWaitEvent(st, hs.copied[b], 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int64_t h = 0;
+    if (n[k] > 0) r = hull_compute(c, buf[b], n[k], hs.d_out, (int64_t)hs.cap, &h, stream);
+    e = cudaEventRecord(hs.consumed[b], st);
+    if (r != HULL_OK) {
+      cudaStreamSynchronize(hs.copy);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    h_count[k] = h;
+    if (h > cap[k]) {
+      cudaStreamSynchronize(hs.copy);
+      return HULL_ECAPACITY;
+    }
+    if (h > 0) {
+      e = cudaMemcpyAsync(h_out[k], hs.d_out, (size_t)h * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
   }
   return HULL_OK;
 }

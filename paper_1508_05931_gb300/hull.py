@@ -57,6 +57,7 @@ _sig = {
     "hull_destroy": ([_P], None),
     "hull_compute": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_compute_host": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
+    "hull_compute_host_multi": ([_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "hull_compute_batched": ([_P, _P, _P, ctypes.c_int32, _P, _I64, _P, _P], ctypes.c_int),
     "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
@@ -202,6 +203,34 @@ class Context:
         _check(_lib.hull_compute_host(self._h, sp, n, op, out.shape[0], ctypes.byref(cnt),
                                       _stream_handle(stream)), "hull_compute_host")
         return out[: cnt.value]
+
+    def compute_host_multi(self, pts_list, outs=None, stream=None) -> list:
+        """Hulls of several host point sets (numpy arrays or CPU tensors,
+        ideally pinned), the copy of each overlapping the previous hull;
+        see hull_compute_host_multi.  Returns one index array per input."""
+        torch = _torch()
+        k = len(pts_list)
+        srcs, ns, sps = [], [], []
+        for pts in pts_list:
+            if isinstance(pts, torch.Tensor):
+                src = pts.contiguous()
+                sps.append(int(src.data_ptr()))
+            else:
+                src = np.ascontiguousarray(np.asarray(pts, dtype=np.int32).reshape(-1, 2))
+                sps.append(src.ctypes.data)
+            srcs.append(src)
+            ns.append(src.shape[0])
+        if outs is None:
+            outs = [np.empty(max(n, 1), dtype=np.int32) for n in ns]
+        ops = [int(o.data_ptr()) if isinstance(o, torch.Tensor) else o.ctypes.data for o in outs]
+        arr_p = (ctypes.c_void_p * max(k, 1))(*sps)
+        arr_n = (ctypes.c_int64 * max(k, 1))(*ns)
+        arr_o = (ctypes.c_void_p * max(k, 1))(*ops)
+        arr_c = (ctypes.c_int64 * max(k, 1))(*[o.shape[0] for o in outs])
+        arr_h = (ctypes.c_int64 * max(k, 1))()
+        _check(_lib.hull_compute_host_multi(self._h, k, arr_p, arr_n, arr_o, arr_c, arr_h,
+                                            _stream_handle(stream)), "hull_compute_host_multi")
+        return [outs[i][: arr_h[i]] for i in range(k)]
 
     def compute_batched(self, pts, offsets, out=None, stream=None):
         """B hulls; offsets int64 (B+1,).  Returns (indices, out_offsets)."""
@@ -375,6 +404,7 @@ hull_create = _lib.hull_create
 hull_destroy = _lib.hull_destroy
 hull_compute = _lib.hull_compute
 hull_compute_host = _lib.hull_compute_host
+hull_compute_host_multi = _lib.hull_compute_host_multi
 hull_compute_batched = _lib.hull_compute_batched
 hull_compute_noalloc = _lib.hull_compute_noalloc
 hull_last_stats = _lib.hull_last_stats

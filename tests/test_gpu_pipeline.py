@@ -115,6 +115,30 @@ def test_host_entry_point(ctx):
     assert h2.tolist() == oracle.hull(pts).tolist()
 
 
+def test_host_multi_entry_point(ctx, hull_lib):
+    """Several host inputs in one pipelined call (the copy of input k + 1
+    overlaps the hull of input k): every result equals the oracle's, for
+    pinned and pageable inputs, an empty input, sizes that grow the staging
+    buffers, and a capacity failure that stops the sequence."""
+    sets = [W.uniform_disk(300_000, 2.0 ** 29, 21), np.zeros((0, 2), np.int32),
+            W.uniform_square(1_200_000, 1 << 29, 22), W.uniform_square(7, 1 << 20, 23),
+            W.uniform_disk(2_500_000, 2.0 ** 28, 24)]
+    refs = [oracle.hull(p).tolist() for p in sets]
+    pinned = [torch.as_tensor(p).pin_memory() for p in sets]
+    got = ctx.compute_host_multi(pinned)
+    assert [g.tolist() for g in got] == refs
+    got = ctx.compute_host_multi(sets)
+    assert [g.tolist() for g in got] == refs
+    assert ctx.compute_host_multi([]) == []
+    # the single-input host entry still works with the grown staging
+    assert ctx.compute_host(pinned[2]).tolist() == refs[2]
+    small = [np.empty(1, np.int32) for _ in sets]
+    with pytest.raises(hull_lib.HullError) as ei:
+        ctx.compute_host_multi(pinned, outs=small)
+    assert ei.value.code == hull_lib.HULL_ECAPACITY
+    assert ctx.compute_host_multi(pinned[:2])[0].tolist() == refs[0]
+
+
 def test_range_error(ctx, hull_lib):
     lim = 1 << 29
     bad = np.array([[0, 0], [lim + 1, 0], [3, 4]], np.int32)
