@@ -71,6 +71,8 @@ typedef struct {
   int32_t ext[4];     /* indices of P_minx, P_maxx, P_miny, P_maxy (Section 2.1 step 1) */
   int32_t ncorner;    /* distinct corners of the filter polygon */
   int32_t learned_used; /* 1 when the learned polygon replaced the quadrilateral */
+  int32_t sort_fallback; /* 1 when the bucket sort met a bin it cannot sort in shared memory
+                            and the call was rerun on the radix passes */
 } hull_stats;
 
 /* Creates a context on CUDA device `device` (cfg NULL = defaults).
@@ -85,7 +87,10 @@ void hull_destroy(hull_ctx *ctx);
  * Section 2.1).  d_xy: device int32[n][2], read-only.  d_out: device
  * int32[cap] receiving the CCW vertex indices.  *h_count (host) receives the
  * hull size on HULL_OK and on HULL_ECAPACITY (then d_out is untouched).
- * Synchronises `stream` before returning.  n must be < 2^30. */
+ * Synchronises `stream` before returning.  n must be < 2^30.  The survivors
+ * are sorted by the bucket sort (hull_stage_bucket_sort); an input it
+ * cannot handle in shared memory is rerun on the radix passes
+ * (hull_stats.sort_fallback), with the same result. */
 hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out,
                          int64_t cap, int64_t *h_count, void *stream);
 
@@ -177,7 +182,10 @@ typedef struct {
   int64_t points;                /* input points, summed */
   int64_t survivors;             /* first-round survivors, summed */
   int64_t second_round;          /* second-round survivors, summed */
-  double ms[HULL_NUM_STAGES];    /* extremes, filter, sort pass 0..7, regions, final */
+  double ms[HULL_NUM_STAGES];    /* extremes, filter, sort pass 0..7, regions, final; with
+                                    the bucket sort (the default) "filter" includes the scatter
+                                    of the survivors into bins, "sort pass 0" is the sort of the
+                                    bins and passes 1..7 are empty */
 } hull_profile;
 
 hull_status hull_set_profiling(hull_ctx *ctx, int enable);
@@ -233,6 +241,19 @@ hull_status hull_stage_filter(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int
  * in place (the workspace holds the ping-pong copies).  m < 2^30. */
 hull_status hull_stage_sort(hull_ctx *ctx, uint64_t *d_keys, uint32_t *d_vals, int64_t m,
                             void *stream);
+
+/* Section 2.1 step 4 / Section 3.3 as the hull pipeline runs it: the
+ * bucket sort of m (key, value) pairs, ascending by key and, among equal
+ * keys, by value -- the stable sort of hull_stage_sort whenever the values
+ * increase in input order, as the first round's survivor indices do.
+ * Pairs are binned by the top bits of the key and each group of bins is
+ * sorted in shared memory; if some bin cannot be (too many equal or nearly
+ * equal keys) the pairs are sorted by hull_stage_sort instead and
+ * *h_fallback (host, may be NULL) is set to 1, else 0.  d_keys (device
+ * uint64[m]) and d_vals (device uint32[m]) are sorted in place.
+ * m < 2^30. */
+hull_status hull_stage_bucket_sort(hull_ctx *ctx, uint64_t *d_keys, uint32_t *d_vals, int64_t m,
+                                   int32_t *h_fallback, void *stream);
 
 /* Section 2.1 steps 5-7 / Figure 2: the second-round filter over m points
  * already sorted by (x, y, index): d_xy (device int32[m][2]) in that order

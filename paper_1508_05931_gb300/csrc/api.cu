@@ -42,6 +42,13 @@ struct Workspace {
   int4* jobs = nullptr;
   int* aux = nullptr;          // int32[cap]: labels for stage entry points
   unsigned char* mask = nullptr;  // first-round keep bits, one byte per 8 points
+  // bucket sort
+  u32* rows = nullptr;         // per-block bin counts, then prefixes: [rows_cap][kBins]
+  size_t rows_cap = 0;
+  u32* bstart = nullptr;       // first position of every bin
+  uint2* groups = nullptr;     // (first position, first bin) per group, closing record
+  u32* bscratch = nullptr;     // per-block scratch of the large-bin split
+  unsigned long long* key_or = nullptr;
 };
 
 struct HostStage {
@@ -81,11 +88,13 @@ struct hull_ctx {
   hull_config cfg{};
   int num_sms = 0;
   int occ_k2c = 1, occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
+  int occ_k2b = 1, occ_kb = 1;  // bucket sort: K2 with bin rows, group sort
   Plan* plan = nullptr;        // device
   Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
   Workspace ws;
   HostStage hs;
   hull_stats last{};
+  int64_t fallbacks = 0;       // calls rerun on the radix passes
   // stage timing (hull_set_profiling)
   bool prof = false;
   bool prof_pending = false;
@@ -157,7 +166,9 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_part = take(parts * sizeof(ExtPartial));
   const size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8);
   const size_t o_i0 = take(cap * 4), o_i1 = take(cap * 4);
-  const size_t o_sf = take(t2 * 8), o_ss = take(t3 * kRadix * 8), o_sr = take(t4 * k4_status_bytes());
+  const size_t o_sf = take(t2 * 8), o_ss = take(t3 * kRadix * 8);
+  // Look-back records of K4's chunks, or of the bucket sort's groups (at most one per bin).
+  const size_t o_sr = take(std::max(t4, (size_t)kBins + 2) * k4_status_bytes());
   const size_t status_end = off;
   const size_t o_lxy = take((cap + 2) * 8), o_lid = take((cap + 2) * 4);
   const size_t o_uxy = take((cap + 2) * 8), o_uid = take((cap + 2) * 4);
@@ -167,6 +178,12 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_jobs = take(nchunks * 16);
   const size_t o_aux = take(cap * 4);
   const size_t o_mask = take(cap / 8 + 4096);
+  const size_t rows_cap = (size_t)c->num_sms * (size_t)std::max(c->occ_k2b, 2);
+  const size_t o_rows = take(rows_cap * kBins * 4);
+  const size_t o_bstart = take((size_t)kBins * 4);
+  const size_t o_groups = take(((size_t)kBins + 2) * 8);
+  const size_t o_bscr = take(bucket_scratch_words(c->num_sms * c->occ_kb) * 4);
+  const size_t o_kor = take(8);
   const size_t total = off;
 
   cudaDeviceSynchronize();
@@ -199,6 +216,12 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.jobs = reinterpret_cast<int4*>(b + o_jobs);
   w.aux = reinterpret_cast<int*>(b + o_aux);
   w.mask = reinterpret_cast<unsigned char*>(b + o_mask);
+  w.rows = reinterpret_cast<u32*>(b + o_rows);
+  w.rows_cap = rows_cap;
+  w.bstart = reinterpret_cast<u32*>(b + o_bstart);
+  w.groups = reinterpret_cast<uint2*>(b + o_groups);
+  w.bscratch = reinterpret_cast<u32*>(b + o_bscr);
+  w.key_or = reinterpret_cast<unsigned long long*>(b + o_kor);
   return HULL_OK;
 }
 
@@ -209,13 +232,20 @@ int grid_for(int occ, int num_sms, size_t work_tiles) {
   return (int)g;
 }
 
-// Copies the summary back, synchronises and maps device error bits.
-hull_status finish(hull_ctx* c, cudaStream_t st) {
+// Copies the summary back, synchronises and maps device error bits.  With
+// `fallback`, a bucket sort that met a bin too large for it (ERR_FALLBACK,
+// no other error) sets *fallback and returns HULL_OK without recording
+// anything: the caller reruns the call on the radix passes.
+hull_status finish(hull_ctx* c, cudaStream_t st, bool* fallback = nullptr) {
   cudaError_t e = cudaMemcpyAsync(c->h_plan, c->plan, kSummaryBytes, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
   const Plan& p = *c->h_plan;
+  if (fallback) {
+    *fallback = (p.error & ERR_FALLBACK) != 0 && (p.error & (ERR_RANGE | ERR_TIMEOUT)) == 0;
+    if (*fallback) return HULL_OK;
+  }
   if (c->prof_pending) {
     c->prof_pending = false;
     hull_profile& f = c->profile;
@@ -250,8 +280,10 @@ void mark(hull_ctx* c, int k, cudaStream_t st) {
   if (c->prof_pending) cudaEventRecord(c->ev[k], st);
 }
 
-// K1 .. K4 of the pipeline on d_xy (n >= 1).
-hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) {
+// K1 .. K4 of the pipeline on d_xy (n >= 1).  `bucket` selects the bucket
+// sort (K2 scatters the survivors into bins, one block sorts each group of
+// bins); otherwise K2 compacts them in index order for the radix passes.
+hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, bool bucket) {
   Workspace& w = c->ws;
   mark(c, 0, st);
   cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st);
@@ -265,16 +297,41 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st) 
   }
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
-  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2c, c->num_sms, t2),
-                grid_for(c->occ_k2, c->num_sms, t2), st);
-  if (e != cudaSuccess) return cuda_fail(e);
-  mark(c, 2, st);
-  const size_t t3 = (n + k3_tile() - 1) / k3_tile();
-  for (u32 p = 0; p < (u32)kMaxPasses; ++p) {
-    e = launch_k3(w.keys[p & 1], w.idx[p & 1], w.keys[(p + 1) & 1], w.idx[(p + 1) & 1], c->plan,
-                  w.st_sort, p, grid_for(c->occ_k3, c->num_sms, t3), st);
+  if (bucket) {
+    // Survivors scattered into bins, then one block per group of bins sorts
+    // it in shared memory and runs the second round on it at once.
+    const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
+    e = launch_k2_bins(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, w.rows, w.bstart, w.groups,
+                       w.st_region, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 3 + (int)p, st);
+    mark(c, 2, st);
+    e = launch_bucket_fused(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.groups, w.bscratch, w.st_region,
+                            w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx, w.up_xy, w.up_idx,
+                            c->occ_kb * c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int p = 0; p < kMaxPasses; ++p) mark(c, 3 + p, st);
+    e = launch_group_compact(c->plan, w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy,
+                             w.lo_idx, w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, kBins), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+#ifdef GBH_DEBUG_CHECKS
+    e = launch_check_regions(c->plan, w.lo_xy, w.up_xy, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+#endif
+    mark(c, 3 + kMaxPasses, st);
+    return HULL_OK;
+  } else {
+    e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2c, c->num_sms, t2),
+                  grid_for(c->occ_k2, c->num_sms, t2), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    mark(c, 2, st);
+    const size_t t3 = (n + k3_tile() - 1) / k3_tile();
+    for (u32 p = 0; p < (u32)kMaxPasses; ++p) {
+      e = launch_k3(w.keys[p & 1], w.idx[p & 1], w.keys[(p + 1) & 1], w.idx[(p + 1) & 1], c->plan,
+                    w.st_sort, p, grid_for(c->occ_k3, c->num_sms, t3), st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      mark(c, 3 + (int)p, st);
+    }
   }
   const size_t t4 = (n + k4_tile() - 1) / k4_tile();
   e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, t4, w.lo_xy, w.lo_idx,
@@ -425,14 +482,15 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return cuda_fail(cudaErrorUnknown); }
   c->num_sms = prop.multiProcessorCount;
-  if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess ||
+  if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess || bucket_configure() != cudaSuccess ||
+      k2_bins_occupancy(&c->occ_k2b) != cudaSuccess || bucket_occupancy(&c->occ_kb) != cudaSuccess ||
       k5_configure(&c->occ_k5) != cudaSuccess ||
       k2_occupancy(&c->occ_k2c, &c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
       k4_occupancy(&c->occ_k4) != cudaSuccess) {
     delete c;
     return cuda_fail(cudaErrorUnknown);
   }
-  if (c->occ_k5 < 1) { delete c; return HULL_ECUDA; }
+  if (c->occ_k5 < 1 || c->occ_k2b < 1 || c->occ_kb < 1) { delete c; return HULL_ECUDA; }
   if (batch_configure(&c->occ_b256, &c->occ_b512) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->bev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -519,14 +577,27 @@ hull_status hull_compute(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   hull_status r = ensure_ws(c, (size_t)n);
   if (r != HULL_OK) return r;
-  c->prof_pending = c->prof;
-  r = run_front(c, d_xy, (u32)n, st);
-  if (r != HULL_OK) { c->prof_pending = false; return r; }
-  r = run_final(c, c->ws.lo_xy, c->ws.lo_idx, c->ws.up_xy, c->ws.up_idx, (size_t)n, d_out, cap, st);
-  if (r != HULL_OK) c->prof_pending = false;
-  if (r != HULL_OK) return r;
-  r = finish(c, st);
-  if (r == HULL_OK || r == HULL_ECAPACITY) *h_count = c->h_plan->h;
+  // The bucket sort first; a bin it cannot sort in shared memory (heavily
+  // duplicated or extremely clustered input) reruns the call on the radix
+  // passes, which take any input.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool bucket = attempt == 0;
+    c->prof_pending = c->prof;
+    r = run_front(c, d_xy, (u32)n, st, bucket);
+    if (r != HULL_OK) { c->prof_pending = false; return r; }
+    r = run_final(c, c->ws.lo_xy, c->ws.lo_idx, c->ws.up_xy, c->ws.up_idx, (size_t)n, d_out, cap, st);
+    if (r != HULL_OK) c->prof_pending = false;
+    if (r != HULL_OK) return r;
+    bool fallback = false;
+    r = finish(c, st, bucket ? &fallback : nullptr);
+    if (fallback) {
+      c->fallbacks += 1;
+      continue;
+    }
+    if (c->cfg.collect_stats) c->last.sort_fallback = attempt;
+    if (r == HULL_OK || r == HULL_ECAPACITY) *h_count = c->h_plan->h;
+    return r;
+  }
   return r;
 }
 
@@ -714,6 +785,45 @@ hull_status hull_stage_sort(hull_ctx* c, uint64_t* d_keys, uint32_t* d_vals, int
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_vals, w.idx[0], (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e);
   return finish(c, st);
+}
+
+hull_status hull_stage_bucket_sort(hull_ctx* c, uint64_t* d_keys, uint32_t* d_vals, int64_t m,
+                                   int32_t* h_fallback, void* stream) {
+  if (!c || m < 0 || m > (int64_t)kMaxN) return HULL_EINVAL;
+  if (h_fallback) *h_fallback = 0;
+  if (m == 0) return HULL_OK;
+  if (!d_keys || !d_vals) return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)m);
+  if (r != HULL_OK) return r;
+  Workspace& w = c->ws;
+  cudaError_t e = cudaMemcpyAsync(w.keys[1], d_keys, (size_t)m * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.idx[1], d_vals, (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  PlanPatch p{};
+  p.set_s = 1; p.s = (u32)m;
+  r = new_call_patch(c, st, p);
+  if (r != HULL_OK) return r;
+  const int grid = std::min(array_hist_grid((u32)m, c->num_sms), (int)w.rows_cap);
+  e = launch_array_bins(w.keys[1], w.idx[1], (u32)m, c->plan, w.key_or, w.rows, w.bstart, w.groups, w.keys[0],
+                        w.idx[0], grid, st);
+  if (e == cudaSuccess)
+    e = launch_bucket_sort(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.groups, w.bscratch,
+                           c->occ_kb * c->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  bool fallback = false;
+  r = finish(c, st, &fallback);
+  if (r != HULL_OK) return r;
+  if (fallback) {
+    // The input is untouched: sort it on the radix passes instead.
+    if (h_fallback) *h_fallback = 1;
+    return hull_stage_sort(c, d_keys, d_vals, m, stream);
+  }
+  e = cudaMemcpyAsync(d_keys, w.keys[1], (size_t)m * 8, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_vals, w.idx[1], (size_t)m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
 }
 
 hull_status hull_stage_second_round(hull_ctx* c, const int32_t* d_xy, const int32_t* d_idx, int64_t m,

@@ -26,12 +26,25 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;            // 64-bit keys / 8-bit digits
 constexpr u32 kMaxN = (1u << 30) - 1;    // look-back count fields are 30 bits
 
+// Bucket sort of the survivors (the hull pipeline's sort): the first round
+// scatters every survivor into one of kBins bins by the top kBinBits of its
+// key; consecutive bins form groups of at most kGroupCap survivors, each
+// sorted in shared memory by one block (sub-bins of the next kSubBits key
+// bits, then the few keys of a sub-bin in place).
+constexpr int kBinBits = 13;
+constexpr int kBins = 1 << kBinBits;
+constexpr int kGroupCap = 8192;              // survivors sorted in shared memory at once
+constexpr int kGroupTarget = kGroupCap / 2;  // window of the group rule (see k3_bucket.cu)
+constexpr int kSubBits = 12;
+constexpr int kSubBins = 1 << kSubBits;
+
 // Error bits accumulated in Plan::error by the kernels.
 enum : u32 {
   ERR_RANGE = 1u,       // a coordinate beyond +-2^29
   ERR_TIMEOUT = 2u,     // a bounded device wait ran out
   ERR_CAPACITY = 4u,    // output capacity below the hull size
   ERR_INTERNAL = 8u,    // an index left its buffer (skipped, never written)
+  ERR_FALLBACK = 16u,   // a bin too large for the bucket sort: the call reruns on the radix passes
 };
 
 // Each call consumes kEpochStride epochs; look-back status words carry the
@@ -47,6 +60,8 @@ enum CounterSlot : int {
   CTR_REGION2 = 2 + kMaxPasses,
   CTR_FINAL_BAR = 3 + kMaxPasses,
   CTR_FINAL_BAR_GEN = 4 + kMaxPasses,
+  CTR_BIN_SCAN = 5 + kMaxPasses,          // last-block counter of the bin scan
+  CTR_BIN_GROUP = 6 + kMaxPasses,         // next group of the bucket sort
   kNumCounters = 16,
 };
 
@@ -72,6 +87,9 @@ struct Plan {
   int32_t cx[kMaxCorners], cy[kMaxCorners];
   int32_t key_x0, key_y0;   // key origin (bounding-box minimum)
   u32 ybits, kbits, npasses;
+  u32 sorted_in_b;      // 1: the sorted survivors are in the second key/index buffer
+  u32 fshift;           // bucket sort: bin = key >> fshift
+  u32 ngroups;          // bucket sort: groups of consecutive bins
   u32 k1_done;          // last-block counter of K1 (self-resetting)
   // per-call scratch
   u32 ctr[kNumCounters];
@@ -103,7 +121,7 @@ __device__ __forceinline__ u32 ld_volatile_u32(const u32* p) {
 }
 __device__ __forceinline__ void flag_error(Plan* plan, u32 bit) { atomicOr(&plan->error, bit); }
 __device__ __forceinline__ bool aborted(const Plan* plan) {
-  return (ld_volatile_u32(&plan->error) & (ERR_TIMEOUT | ERR_INTERNAL)) != 0;
+  return (ld_volatile_u32(&plan->error) & (ERR_TIMEOUT | ERR_INTERNAL | ERR_FALLBACK)) != 0;
 }
 
 // Exact orientation (b - a) x (c - a) in int64.  Coordinates are bounded by
@@ -146,6 +164,30 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, u32 bytes,
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// L2 eviction policies (createpolicy) for streaming reads that nothing
+// reads again (evict_first) and for scattered writes that should stay in L2
+// until their sectors are complete (evict_last).
+__device__ __forceinline__ u64 policy_evict_first() {
+  u64 p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ u64 policy_evict_last() {
+  u64 p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, u32 bytes, u64* bar, u64 pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint_u64(u64* p, u64 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint_u32(u32* p, u32 v, u64 pol) {
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
   u32 ok;

@@ -124,6 +124,9 @@ __device__ void finish_plan(Plan* plan, const Best& b) {
   plan->ybits = yb;
   plan->kbits = xb + yb;
   plan->npasses = (xb + yb + kRadixBits - 1) / kRadixBits;
+  plan->sorted_in_b = plan->npasses & 1u;
+  plan->fshift = xb + yb > (u32)kBinBits ? xb + yb - (u32)kBinBits : 0u;
+  plan->ngroups = 0;
 }
 
 template <int BLOCK, bool VEC>

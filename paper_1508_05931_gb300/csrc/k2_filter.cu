@@ -109,14 +109,15 @@ __device__ __forceinline__ void k2_stage_chunk(const int* xy, u32 c, int4* ring,
 // With BULK, every whole chunk arrives by a bulk copy into a K2_STAGES-deep
 // ring in shared memory, issued K2_STAGES chunks ahead; a partial last chunk
 // is read directly.
-template <bool VEC, bool BULK, int K>
+template <bool VEC, bool BULK, bool BINS, int K>
 __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
                                              unsigned char* __restrict__ mask, const Edges& E,
-                                             u32* s_hist, u32* s_red, int4* ring, u64* bars) {
+                                             u32* s_hist, u32* s_red, int4* ring, u64* bars, u32* s_bins) {
   const u32 n = plan->n;
   const int x0 = plan->key_x0, y0 = plan->key_y0;
   const u32 ybits = plan->ybits;
-  const bool hist = plan->npasses > 0;
+  const u32 fshift = plan->fshift;
+  const bool hist = !BINS && plan->npasses > 0;
   const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
   const u32 nwhole = n / K2_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -144,9 +145,10 @@ __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* p
       if (keep[e]) {
         ++cnt;
         bits |= 1u << e;
-        if (hist) {
+        if (hist || BINS) {
           const u64 key = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
-          atomicAdd(&s_hist[(u32)key & (kRadix - 1)], 1u);
+          if (BINS) atomicAdd(&s_bins[(u32)(key >> fshift)], 1u);
+          else atomicAdd(&s_hist[(u32)key & (kRadix - 1)], 1u);
         }
       }
     }
@@ -169,47 +171,57 @@ __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* p
   }
 }
 
-template <bool VEC>
+// With BINS, also counts the survivors per bin of the bucket sort (key >>
+// fshift) and stores the block's counts as row blockIdx.x of `rows`
+// (dynamic shared memory: the ring, then kBins counters).
+template <bool VEC, bool BINS>
 __global__ void __launch_bounds__(K2_BLOCK, 4)
 k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
-         unsigned char* __restrict__ mask) {
+         unsigned char* __restrict__ mask, u32* __restrict__ rows) {
   extern __shared__ __align__(128) unsigned char k2_smem[];
   __shared__ u32 s_hist[kRadix];
   __shared__ u32 s_red[K2_WARPS];
   __shared__ bool s_last;
   __shared__ __align__(8) u64 s_bars[K2_STAGES];
   int4* ring = reinterpret_cast<int4*>(k2_smem);
+  u32* s_bins = reinterpret_cast<u32*>(k2_smem + K2_RING_BYTES);
 
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
   const int k = plan->ncorner;
-  const bool hist = plan->npasses > 0;
+  const bool hist = !BINS && plan->npasses > 0;
   const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Edges E;
   load_edges(plan, k, E);
   for (int q = threadIdx.x; q < kRadix; q += K2_BLOCK) s_hist[q] = 0u;
+  if (BINS)
+    for (int q = threadIdx.x; q < kBins; q += K2_BLOCK) s_bins[q] = 0u;
   if (VEC && threadIdx.x == 0) {
     for (int st = 0; st < K2_STAGES; ++st) mbar_init(&s_bars[st], 1u);
     mbar_fence_init();
   }
   __syncthreads();
   switch (k) {
-    case 3: count_chunks<VEC, VEC, 3>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 4: count_chunks<VEC, VEC, 4>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 5: count_chunks<VEC, VEC, 5>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 6: count_chunks<VEC, VEC, 6>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 7: count_chunks<VEC, VEC, 7>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 8: count_chunks<VEC, VEC, 8>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 9: count_chunks<VEC, VEC, 9>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 10: count_chunks<VEC, VEC, 10>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 11: count_chunks<VEC, VEC, 11>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    case 12: count_chunks<VEC, VEC, 12>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
-    default: count_chunks<VEC, VEC, 0>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars); break;
+    case 3: count_chunks<VEC, VEC, BINS, 3>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 4: count_chunks<VEC, VEC, BINS, 4>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 5: count_chunks<VEC, VEC, BINS, 5>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 6: count_chunks<VEC, VEC, BINS, 6>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 7: count_chunks<VEC, VEC, BINS, 7>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 8: count_chunks<VEC, VEC, BINS, 8>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 9: count_chunks<VEC, VEC, BINS, 9>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 10: count_chunks<VEC, VEC, BINS, 10>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 11: count_chunks<VEC, VEC, BINS, 11>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    case 12: count_chunks<VEC, VEC, BINS, 12>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
+    default: count_chunks<VEC, VEC, BINS, 0>(xy, plan, counts, mask, E, s_hist, s_red, ring, s_bars, s_bins); break;
   }
   if (hist)
     for (u32 q = threadIdx.x; q < kRadix; q += K2_BLOCK)
       if (s_hist[q]) atomicAdd(&plan->hist[0][q], s_hist[q]);
+  if (BINS) {
+    __syncthreads();
+    for (u32 q = threadIdx.x; q < (u32)kBins; q += K2_BLOCK) rows[(size_t)blockIdx.x * kBins + q] = s_bins[q];
+  }
 
   // The last block turns the chunk counts into exclusive offsets.
   __threadfence();
@@ -327,23 +339,157 @@ k2_write(const int* __restrict__ xy, Plan* plan, const u32* __restrict__ offsets
   }
 }
 
+// The bucket sort's scatter: writes every survivor (marked by k2_count in
+// `mask`) as (key, index) into its bin.  Block i walks the same chunks as
+// block i of k2_count (in the reverse order, so that the part of the input
+// k2_count read last is still in L2), so its first position in bin b is
+// bstart[b] plus its row's prefix rows[i][b] (from k_binscan); positions
+// inside a bin are taken by shared-memory atomics, in no particular order
+// (the bin's sort orders by (key, index)).  No block waits for another.
+// Whole chunks and their mask bytes arrive by bulk copies into a
+// K2_STAGES-deep ring (evict-first: nothing reads the input again); the
+// scattered stores are marked evict-last so that the sectors that several
+// blocks fill piecewise stay in L2 until they are complete.
+constexpr u32 K2_MASK_BYTES = K2_BLOCK;                    // one byte per thread and chunk
+constexpr u32 K2_SC_STAGE = K2_CHUNK_BYTES + K2_MASK_BYTES;
+constexpr size_t K2_SC_SMEM = (size_t)K2_STAGES * K2_SC_STAGE + (size_t)kBins * sizeof(u32);
+
+__device__ __forceinline__ void k2_sc_stage(const int* xy, const unsigned char* mask, u32 c, unsigned char* ring,
+                                            u64* bars, int st, u64 pol) {
+  unsigned char* dst = ring + (size_t)st * K2_SC_STAGE;
+  mbar_arrive_expect_tx(&bars[st], K2_SC_STAGE);
+  bulk_load_hint(dst, xy + (size_t)c * 2 * K2_CHUNK, K2_CHUNK_BYTES, &bars[st], pol);
+  bulk_load_hint(dst + K2_CHUNK_BYTES, mask + (size_t)c * K2_BLOCK, K2_MASK_BYTES, &bars[st], pol);
+}
+
+// Scatters this thread's kept points of chunk c (keep bits `bits`, points
+// px/py in the thread's pair order).
+__device__ __forceinline__ void k2_scatter_points(Plan* plan, u32 c, u32 bits, const int* px, const int* py,
+                                                  int x0, int y0, u32 ybits, u32 fshift, u32 s, u32* s_cur,
+                                                  u64* keys_out, u32* idx_out, u64 pol) {
+  const u32 base = c * (u32)K2_CHUNK;
+  #pragma unroll
+  for (int e = 0; e < 2 * K2_PAIRS; ++e) {
+    if (!((bits >> e) & 1u)) continue;
+    const u32 i = base + 2u * ((e >> 1) * K2_BLOCK + threadIdx.x) + (u32)(e & 1);
+    const u64 key = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
+    const u32 pos = atomicAdd(&s_cur[(u32)(key >> fshift)], 1u);
+    if (pos < s) {
+      st_hint_u64(keys_out + pos, key, pol);
+      st_hint_u32(idx_out + pos, i, pol);
+    } else {
+      flag_error(plan, ERR_INTERNAL);
+    }
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K2_BLOCK, 2)
+k2_scatter(const int* __restrict__ xy, Plan* plan, const unsigned char* __restrict__ mask,
+           const u32* __restrict__ rows, const u32* __restrict__ bstart, u64* __restrict__ keys_out,
+           u32* __restrict__ idx_out) {
+  extern __shared__ __align__(128) unsigned char k2s_smem[];
+  __shared__ __align__(8) u64 s_bars[K2_STAGES];
+  unsigned char* ring = k2s_smem;
+  u32* s_cur = reinterpret_cast<u32*>(k2s_smem + (size_t)K2_STAGES * K2_SC_STAGE);
+  if (plan->error & ERR_RANGE) return;
+  const u32 n = plan->n;
+  const u32 s = plan->s;
+  const int x0 = plan->key_x0, y0 = plan->key_y0;
+  const u32 ybits = plan->ybits;
+  const u32 fshift = plan->fshift;
+  const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
+  const u32 G = gridDim.x, b0 = blockIdx.x;
+  const u64 pol_in = policy_evict_first();
+  const u64 pol_out = policy_evict_last();
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += K2_BLOCK)
+    s_cur[q] = bstart[q] + rows[(size_t)b0 * kBins + q];
+  // This block's chunks are b0 + k * G.  The whole ones (c < nring) go
+  // through the ring, last first; the rest are read directly.
+  const u32 nring = VEC ? n / K2_CHUNK : 0u;
+  const u32 kw = b0 < nring ? (nring - 1 - b0) / G + 1 : 0u;
+  const u32 kall = b0 < nchunks ? (nchunks - 1 - b0) / G + 1 : 0u;
+  auto ring_chunk = [&](u32 q) { return b0 + (kw - 1 - q) * G; };
+  if (VEC && threadIdx.x == 0) {
+    for (int st = 0; st < K2_STAGES; ++st) mbar_init(&s_bars[st], 1u);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (VEC && threadIdx.x == 0)
+    for (u32 q = 0; q < (u32)K2_STAGES && q < kw; ++q)
+      k2_sc_stage(xy, mask, ring_chunk(q), ring, s_bars, (int)q, pol_in);
+  for (u32 q = 0; q < kw; ++q) {
+    const int st = (int)(q % K2_STAGES);
+    if (!mbar_wait(&s_bars[st], (q / K2_STAGES) & 1u)) flag_error(plan, ERR_TIMEOUT);
+    const unsigned char* stage = ring + (size_t)st * K2_SC_STAGE;
+    const u32 bits = stage[K2_CHUNK_BYTES + threadIdx.x];
+    const int4* pts = reinterpret_cast<const int4*>(stage);
+    int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
+    #pragma unroll
+    for (int r = 0; r < K2_PAIRS; ++r) {
+      const int4 v = pts[r * K2_BLOCK + threadIdx.x];
+      px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+    }
+    k2_scatter_points(plan, ring_chunk(q), bits, px, py, x0, y0, ybits, fshift, s, s_cur, keys_out, idx_out,
+                      pol_out);
+    __syncthreads();   // every thread has read stage st: refill it
+    if (threadIdx.x == 0 && q + K2_STAGES < kw)
+      k2_sc_stage(xy, mask, ring_chunk(q + K2_STAGES), ring, s_bars, st, pol_in);
+  }
+  for (u32 k = kw; k < kall; ++k) {
+    const u32 c = b0 + k * G;
+    const u32 base = c * (u32)K2_CHUNK;
+    const u32 bits = mask[(size_t)c * K2_BLOCK + threadIdx.x];
+    int px[2 * K2_PAIRS], py[2 * K2_PAIRS];
+    #pragma unroll
+    for (int r = 0; r < K2_PAIRS; ++r) {
+      const u32 i0 = base + 2u * (r * K2_BLOCK + threadIdx.x);
+      int2 a = make_int2(0, 0), b = make_int2(0, 0);
+      if ((bits >> (2 * r)) & 1u) a = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0);
+      if ((bits >> (2 * r + 1)) & 1u) b = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0 + 2);
+      px[2 * r] = a.x; py[2 * r] = a.y; px[2 * r + 1] = b.x; py[2 * r + 1] = b.y;
+    }
+    k2_scatter_points(plan, c, bits, px, py, x0, y0, ybits, fshift, s, s_cur, keys_out, idx_out, pol_out);
+  }
+}
+
 }  // namespace
 
 int k2_tile() { return K2_CHUNK; }
 
+constexpr size_t K2_BINS_SMEM = K2_RING_BYTES + (size_t)kBins * sizeof(u32);
+
 cudaError_t k2_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k2_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k2_count<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)K2_RING_BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k2_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_RING_BYTES);
+    e = cudaFuncSetAttribute(k2_count<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)K2_RING_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k2_count<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_BINS_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k2_count<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_BINS_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k2_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_SC_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k2_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K2_SC_SMEM);
   return e;
 }
 
 cudaError_t k2_occupancy(int* count_blocks, int* write_blocks) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(count_blocks, k2_count<true>, K2_BLOCK,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(count_blocks, k2_count<true, false>, K2_BLOCK,
                                                                 K2_RING_BYTES);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(write_blocks, k2_write<true>, K2_BLOCK, 0);
+  return e;
+}
+
+cudaError_t k2_bins_occupancy(int* blocks) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k2_count<true, true>, K2_BLOCK, K2_BINS_SMEM);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k2_scatter<true>, K2_BLOCK, K2_SC_SMEM);
+  *blocks = a < b ? a : b;
   return e;
 }
 
@@ -356,12 +502,29 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
   if (vec) {
-    k2_count<true><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask);
+    k2_count<true, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr);
     k2_write<true><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   } else {
-    k2_count<false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask);
+    k2_count<false, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr);
     k2_write<false><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   }
+  return cudaGetLastError();
+}
+
+// First round for the bucket sort: k2_count with per-block bin rows, the
+// bin scan (k3_bucket.cu), then the scatter into bins, all with `grid`
+// blocks (the scatter walks the count's chunks; `rows` has grid rows).
+cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
+                           unsigned char* mask, u32* rows, u32* bstart, uint2* groups, void* recs, int grid,
+                           cudaStream_t st) {
+  const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
+  u32* counts = reinterpret_cast<u32*>(status);
+  if (vec) k2_count<true, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
+  else k2_count<false, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
+  cudaError_t e = launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, st);
+  if (e != cudaSuccess) return e;
+  if (vec) k2_scatter<true><<<grid, K2_BLOCK, K2_SC_SMEM, st>>>(xy, plan, mask, rows, bstart, keys_out, idx_out);
+  else k2_scatter<false><<<grid, K2_BLOCK, K2_SC_SMEM, st>>>(xy, plan, mask, rows, bstart, keys_out, idx_out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,883 @@
+// K3 of the hull pipeline: bucket sort of the first round's survivors
+// (Section 2.1 step 4, Section 3.3), ascending by (key, index).  The
+// survivors arrive in index order, so this order is exactly the stable sort
+// by key that the paper's sort_by_key gives; the key is the lexicographic
+// (x, y) key of K2.
+//
+// The sort needs two passes over the survivors instead of one per radix
+// digit:
+//   1. while K2 counts the survivors it also counts them per bin (the top
+//      kBinBits of the key), one histogram row per block; k_binscan turns
+//      the rows into each block's first position in every bin and groups
+//      consecutive bins, and K2's scatter pass writes every survivor into
+//      its bin (any order inside a bin);
+//   2. k3_bucket sorts each group in shared memory, one block per group:
+//      a counting pass over the next kSubBits key bits places every key in
+//      its sub-bin, and the few keys of each sub-bin are then ordered by
+//      (key, index) in place.  A group whose sub-bins are crowded (many
+//      equal or nearly equal keys) is sorted by a bitonic network instead.
+//
+// Groups: bin b starts a new group when floor(start_b / T) differs from
+// its predecessor's (T = kGroupTarget) or when it or its predecessor holds
+// more than T survivors.  A group of small bins then starts and ends inside
+// one window of T positions plus its last bin, so it holds fewer than 2T =
+// kGroupCap survivors; a larger bin is a group of its own.  A bin above
+// kGroupCap is split once more through global memory by its next kSubBits
+// key bits; if one of those sub-bins is still above kGroupCap (heavy
+// duplication, or a few points spread over a huge bounding box) the block
+// sets ERR_FALLBACK and the host reruns the call on the radix passes of
+// k3_sort.cu.
+#include "hull_internal.cuh"
+#include "kernels.h"
+#include "regions.cuh"
+
+#ifdef GBH_DEBUG_CHECKS
+#include <cstdio>
+#endif
+
+namespace gbh {
+
+namespace {
+
+constexpr int KB_BLOCK = 512;
+constexpr int KB_WARPS = KB_BLOCK / 32;
+constexpr int KB_ITEMS = kGroupCap / KB_BLOCK;     // keys per thread in a full group
+constexpr u32 kCrowded = 32;                       // largest sub-bin ordered by insertion
+constexpr int KB_SCAN_PER = (kSubBins) / KB_BLOCK; // sub-bin counters per thread in the scan
+static_assert(KB_SCAN_PER * KB_BLOCK == kSubBins, "whole counters per thread");
+static_assert(kGroupCap <= (1 << 13) && kSubBits <= 19, "rank and sub-bin packed in 32 bits");
+constexpr int kScratchWords = kSubBins + 1 + kSubBins / 32;   // per block: split starts, piece flags
+
+struct BucketSmem {
+  u64 key[kGroupCap];      // sorted pairs, slot phys(i) for position i
+  u32 val[kGroupCap];
+  u32 cnt[kSubBins + 1];
+  u32 wsum[KB_WARPS];
+  u32 misc[4];
+  // fused second round
+  Dir2 dirs[KB_WARPS];     // per-warp direction aggregates
+  Dir2 carry;              // prefix through the group's pieces scanned so far
+  u32 kwl[KB_WARPS][2];    // per-warp kept counts (lower, upper)
+  u32 kept[2];             // the group's kept points so far
+  int fail;
+};
+
+// Shared-memory slot of sorted position i: the low five bits are XORed
+// with the next five, so that threads reading consecutive runs of 8 or 16
+// positions hit different banks (a bijection inside every 32 slots).
+__device__ __forceinline__ u32 phys(u32 i) { return i ^ ((i >> 5) & 31u); }
+
+#ifdef GBH_DEBUG_CHECKS
+__device__ unsigned int g_dbg_reported = 0;
+#define DBG_REPORT(code, a, b, c, d)                                                                   \
+  do {                                                                                                  \
+    if (atomicCAS(&g_dbg_reported, 0u, 1u) == 0u)                                                       \
+      printf("GBH_DEBUG k3 check %d failed: block %d thread %d: %llu %llu %llu %llu\n", (int)(code),    \
+             (int)blockIdx.x, (int)threadIdx.x, (unsigned long long)(a), (unsigned long long)(b),      \
+             (unsigned long long)(c), (unsigned long long)(d));                                        \
+  } while (0)
+#endif
+
+__device__ __forceinline__ u32 ceil_log2(u32 v) { return v <= 1u ? 0u : 32u - __clz(v - 1u); }
+
+__device__ __forceinline__ bool pair_less(u64 ka, u32 va, u64 kb, u32 vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+// Exclusive scan of S.cnt[0..kSubBins) in place, S.cnt[kSubBins] = total.
+// Returns (on every thread) whether some counter exceeded kCrowded.
+__device__ __forceinline__ bool scan_counts(BucketSmem& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  u32 v[KB_SCAN_PER];
+  u32 sum = 0, mx = 0;
+  #pragma unroll
+  for (int j = 0; j < KB_SCAN_PER; ++j) {
+    v[j] = S.cnt[threadIdx.x * KB_SCAN_PER + j];
+    sum += v[j];
+    mx = max(mx, v[j]);
+  }
+  u32 inc = sum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) S.wsum[wid] = inc;
+  const bool crowded = __syncthreads_or(mx > kCrowded) != 0;
+  u32 run = inc - sum;
+  for (int w = 0; w < wid; ++w) run += S.wsum[w];
+  #pragma unroll
+  for (int j = 0; j < KB_SCAN_PER; ++j) {
+    S.cnt[threadIdx.x * KB_SCAN_PER + j] = run;
+    run += v[j];
+  }
+  if (threadIdx.x == KB_BLOCK - 1) S.cnt[kSubBins] = run;
+  __syncthreads();
+  return crowded;
+}
+
+// Orders S.key/S.val[a, b) by (key, value): straight insertion (b - a is
+// at most kCrowded).
+__device__ __forceinline__ void insertion(BucketSmem& S, u32 a, u32 b) {
+  for (u32 j = a + 1; j < b; ++j) {
+    const u64 k = S.key[phys(j)];
+    const u32 v = S.val[phys(j)];
+    u32 i = j;
+    while (i > a && pair_less(k, v, S.key[phys(i - 1)], S.val[phys(i - 1)])) {
+      S.key[phys(i)] = S.key[phys(i - 1)];
+      S.val[phys(i)] = S.val[phys(i - 1)];
+      --i;
+    }
+    S.key[phys(i)] = k;
+    S.val[phys(i)] = v;
+  }
+}
+
+// Bitonic network over S.key/S.val[0, m), padded to a power of two with
+// pairs above every real one ((key, value) pairs are distinct, so any
+// correct sort gives the same order).
+__device__ void bitonic(BucketSmem& S, u32 m) {
+  u32 P = 1;
+  while (P < m) P <<= 1;
+  for (u32 i = m + threadIdx.x; i < P; i += KB_BLOCK) {
+    S.key[phys(i)] = ~0ull;
+    S.val[phys(i)] = ~0u;
+  }
+  __syncthreads();
+  for (u32 k = 2; k <= P; k <<= 1) {
+    for (u32 j = k >> 1; j > 0; j >>= 1) {
+      for (u32 i = threadIdx.x; i < P; i += KB_BLOCK) {
+        const u32 l = i ^ j;
+        if (l > i) {
+          const u32 pi = phys(i), pl = phys(l);
+          const u64 ki = S.key[pi], kl = S.key[pl];
+          const u32 vi = S.val[pi], vl = S.val[pl];
+          const bool up = (i & k) == 0;
+          const bool swap = up ? pair_less(kl, vl, ki, vi) : pair_less(ki, vi, kl, vl);
+          if (swap) {
+            S.key[pi] = kl; S.key[pl] = ki;
+            S.val[pi] = vl; S.val[pl] = vi;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Source loads: through the read-only path when the source is not written
+// during the kernel (RO), else plain coherent loads.
+template <bool RO, typename T>
+__device__ __forceinline__ T load_src(const T* p) {
+  if (RO) return __ldg(p);
+  return *p;
+}
+
+// ---- the second round, fused (Section 2.2, Figure 2): geometry of the
+// split line P_0 -> P_l and of the directions d(p) = p - P_l.
+struct RG {
+  int x0, y0, ax, ay, bx, by, ux, uy;
+  u32 ybits;
+  u64 ymask;
+  Dir2 ident;
+};
+
+__device__ __forceinline__ RG make_rg(const Plan* plan) {
+  RG g;
+  g.x0 = plan->key_x0; g.y0 = plan->key_y0;
+  g.ybits = plan->ybits;
+  g.ymask = g.ybits ? ((~0ull) >> (64 - g.ybits)) : 0ull;
+  g.ax = plan->ext_x[0]; g.ay = plan->ext_y[0];     // P_0 = P_minx
+  g.bx = plan->ext_x[1]; g.by = plan->ext_y[1];     // P_l = P_maxx
+  g.ux = g.bx - g.ax; g.uy = g.by - g.ay;
+  g.ident = {g.ax - g.bx, g.ay - g.by, g.ax - g.bx, g.ay - g.by};
+  return g;
+}
+
+// Point of a key, and its region: -1 lower (right of P_0 -> P_l), +1 upper, 0 on the line.
+__device__ __forceinline__ int decode_side(const RG& g, u64 k, int& px, int& py) {
+  px = g.x0 + (int)(u32)(k >> g.ybits);
+  py = g.y0 + (int)(u32)(k & g.ymask);
+  const long long o = cross2(g.ux, g.uy, px - g.ax, py - g.ay);
+  return o < 0 ? -1 : (o > 0 ? 1 : 0);
+}
+
+__device__ __forceinline__ void add_dir(Dir2& a, const RG& g, u64 k) {
+  int px, py;
+  const int sd = decode_side(g, k, px, py);
+  if (sd < 0) cmax(a.lx, a.ly, px - g.bx, py - g.by);
+  else if (sd > 0) cmin(a.ux, a.uy, px - g.bx, py - g.by);
+}
+
+// Combines the block's per-thread aggregates; the result on every thread.
+__device__ __forceinline__ Dir2 block_total_dir(BucketSmem& S, Dir2 v, const Dir2& ident) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
+  __syncthreads();
+  if (lane == 0) S.dirs[wid] = v;
+  __syncthreads();
+  Dir2 t = ident;
+  #pragma unroll
+  for (int w = 0; w < KB_WARPS; ++w) combine(t, S.dirs[w]);
+  return t;
+}
+
+// Staging areas and records of the fused second round.
+struct Fused {
+  K4Chunk* recs;
+  int2* t_lo_xy; int* t_lo_idx; int2* t_up_xy; int* t_up_idx;
+  int2* lo_xy; int* lo_idx; int2* up_xy; int* up_idx;
+};
+
+// Publishes group g's aggregate (group 0 publishes it as its inclusive prefix).
+__device__ __forceinline__ void publish_agg(const Fused& F, u32 g, const Dir2& t) {
+  K4Chunk* r = &F.recs[g];
+  st_relaxed_u64(g == 0 ? &r->inc_lo : &r->agg_lo, pack_dir(t.lx, t.ly));
+  st_relaxed_u64(g == 0 ? &r->inc_up : &r->agg_up, pack_dir(t.ux, t.uy));
+}
+
+// Decoupled look-back over the records of groups before g with the whole
+// block: in each step thread i inspects group base - i (base = g - 1,
+// g - 1 - KB_BLOCK, ...), so one round trip covers KB_BLOCK predecessors
+// (with a few hundred groups in flight the nearest inclusive prefix is
+// usually that far back).  Per region, every group up to the nearest one
+// holding an inclusive prefix contributes (its aggregate, or that prefix);
+// the operation is a maximum under a total order, so the contributions
+// combine in any order.  Every thread calls it; the prefix is returned on
+// all.  False (ERR_TIMEOUT set) if a predecessor published nothing within
+// the spin limit.
+__device__ bool lookback_dir_block(BucketSmem& S, K4Chunk* recs, u32 g, Plan* plan, u32 spin, const Dir2& ident,
+                                   Dir2* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Dir2 acc = ident;
+  bool done_lo = false, done_up = false;
+  long long base = (long long)g - 1;
+  while (base >= 0 && !(done_lo && done_up)) {
+    const long long t = base - (long long)threadIdx.x;
+    // Before group 0 the identity acts as an inclusive prefix.
+    u64 il = kDirValid, iu = kDirValid, al = 0, au = 0;
+    bool bad = false;
+    if (t >= 0) {
+      K4Chunk* ch = &recs[t];
+      u32 it = 0;
+      for (;;) {
+        il = ld_relaxed_u64(&ch->inc_lo); iu = ld_relaxed_u64(&ch->inc_up);
+        al = ld_relaxed_u64(&ch->agg_lo); au = ld_relaxed_u64(&ch->agg_up);
+        if (((il | al) & kDirValid) && ((iu | au) & kDirValid)) break;
+        if (++it > spin || aborted(plan)) { bad = true; break; }
+        spin_pause(it);
+      }
+    }
+    if (threadIdx.x == 0) { S.misc[2] = 0xFFFFFFFFu; S.misc[3] = 0xFFFFFFFFu; }
+    if (__syncthreads_or(bad)) {
+      if (threadIdx.x == 0) flag_error(plan, ERR_TIMEOUT);
+      return false;
+    }
+    // The nearest inclusive prefix per region: the lowest thread holding one.
+    const u32 ml = __ballot_sync(0xFFFFFFFFu, (il & kDirValid) != 0);
+    const u32 mu = __ballot_sync(0xFFFFFFFFu, (iu & kDirValid) != 0);
+    if (lane == 0) {
+      if (ml) atomicMin(&S.misc[2], (u32)(wid * 32 + __ffs(ml) - 1));
+      if (mu) atomicMin(&S.misc[3], (u32)(wid * 32 + __ffs(mu) - 1));
+    }
+    __syncthreads();
+    const u32 sl = S.misc[2], su = S.misc[3];
+    Dir2 v = ident;
+    if (t >= 0 && !done_lo && (u32)threadIdx.x <= sl) unpack_dir((il & kDirValid) ? il : al, v.lx, v.ly);
+    if (t >= 0 && !done_up && (u32)threadIdx.x <= su) unpack_dir((iu & kDirValid) ? iu : au, v.ux, v.uy);
+    combine(acc, block_total_dir(S, v, ident));
+    done_lo = done_lo || sl != 0xFFFFFFFFu;
+    done_up = done_up || su != 0xFFFFFFFFu;
+    base -= KB_BLOCK;
+  }
+  *out = acc;
+  return true;
+}
+
+// Exclusive prefix of group g into S.carry (the whole block looks back;
+// group 0: the identity); publishes the inclusive prefix.  False on a
+// timeout.  Every thread calls it.
+__device__ bool group_prefix(BucketSmem& S, const Fused& F, u32 g, const Dir2& agg, const RG& rg, Plan* plan) {
+  Dir2 excl = rg.ident;
+  bool ok = true;
+  if (g > 0) ok = lookback_dir_block(S, F.recs, g, plan, plan->spin_limit, rg.ident, &excl);
+  if (threadIdx.x == 0) {
+    S.fail = ok ? 0 : 1;
+    S.carry = excl;
+    S.kept[0] = S.kept[1] = 0u;
+    if (ok && g > 0) {
+      Dir2 in = excl;
+      combine(in, agg);
+      K4Chunk* r = &F.recs[g];
+      st_relaxed_u64(&r->inc_lo, pack_dir(in.lx, in.ly));
+      st_relaxed_u64(&r->inc_up, pack_dir(in.ux, in.uy));
+    }
+  }
+  __syncthreads();
+  return S.fail == 0;
+}
+
+// Figure 2 over the m sorted pairs in shared memory, starting from the
+// prefix S.carry: keeps a point when its direction is strictly beyond the
+// running extreme of its region, stages the kept points from slot
+// `slot0 + S.kept[region]` and advances S.carry and S.kept.  Thread t
+// takes positions [t R, t R + R).
+__device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 s, const RG& rg, Plan* plan) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 R = (m + KB_BLOCK - 1) / KB_BLOCK;
+  const u32 p0 = min(m, threadIdx.x * R), p1 = min(m, p0 + R);
+  Dir2 agg = rg.ident;
+  for (u32 p = p0; p < p1; ++p) add_dir(agg, rg, S.key[phys(p)]);
+  const Dir2 inc = warp_scan_dir(agg);
+  const Dir2 lex = shfl_up_dir(inc, 1);
+  if (lane == 31) S.dirs[wid] = inc;
+  __syncthreads();
+  Dir2 run = S.carry;
+  for (int w = 0; w < wid; ++w) combine(run, S.dirs[w]);
+  if (lane > 0) combine(run, lex);
+  u32 keep_lo = 0, keep_up = 0;           // bit j: position p0 + j kept
+  for (u32 p = p0; p < p1; ++p) {
+    int px, py;
+    const int sd = decode_side(rg, S.key[phys(p)], px, py);
+    const int vx = px - rg.bx, vy = py - rg.by;
+    const u32 bit = 1u << (p - p0);
+    if (sd < 0) {
+      if (cross2(run.lx, run.ly, vx, vy) > 0) { keep_lo |= bit; run.lx = vx; run.ly = vy; }
+    } else if (sd > 0) {
+      if (cross2(run.ux, run.uy, vx, vy) < 0) { keep_up |= bit; run.ux = vx; run.uy = vy; }
+    }
+  }
+  const u32 c_lo = __popc(keep_lo), c_up = __popc(keep_up);
+  u32 i_lo = c_lo, i_up = c_up;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t0 = __shfl_up_sync(0xFFFFFFFFu, i_lo, o);
+    const u32 t1 = __shfl_up_sync(0xFFFFFFFFu, i_up, o);
+    if (lane >= o) { i_lo += t0; i_up += t1; }
+  }
+  if (lane == 31) { S.kwl[wid][0] = i_lo; S.kwl[wid][1] = i_up; }
+  __syncthreads();
+  u32 wl = 0, wu = 0, tl = 0, tu = 0;
+  for (int w = 0; w < KB_WARPS; ++w) {
+    if (w < wid) { wl += S.kwl[w][0]; wu += S.kwl[w][1]; }
+    tl += S.kwl[w][0]; tu += S.kwl[w][1];
+  }
+  u32 pl = slot0 + S.kept[0] + wl + i_lo - c_lo;
+  u32 pu = slot0 + S.kept[1] + wu + i_up - c_up;
+  for (u32 p = p0; p < p1; ++p) {
+    const u32 bit = 1u << (p - p0);
+    if (!((keep_lo | keep_up) & bit)) continue;
+    int px, py;
+    decode_side(rg, S.key[phys(p)], px, py);
+    const int idx = (int)S.val[phys(p)];
+    if (keep_lo & bit) {
+      if (pl < s) { F.t_lo_xy[pl] = make_int2(px, py); F.t_lo_idx[pl] = idx; } else flag_error(plan, ERR_INTERNAL);
+      ++pl;
+    } else {
+      if (pu < s) { F.t_up_xy[pu] = make_int2(px, py); F.t_up_idx[pu] = idx; } else flag_error(plan, ERR_INTERNAL);
+      ++pu;
+    }
+  }
+  // The piece's total prefix (the last thread's running value covers every
+  // position) and kept counts, for the next piece of the same group.
+  __syncthreads();
+  if (threadIdx.x == KB_BLOCK - 1) {
+    S.carry = run;
+    S.kept[0] += tl;
+    S.kept[1] += tu;
+  }
+  __syncthreads();
+}
+
+// Sorts the m <= kGroupCap pairs at [base, base + m) of (sk, sv), whose keys
+// lie in [klo, klo + 2^span), into shared memory (position i in slot
+// phys(i)), ordered by (key, value).  With AGG, also returns on every thread
+// the direction aggregate of the pairs (order-free, from the first load).
+// Every thread of the block calls it.
+template <bool RO, bool AGG>
+__device__ Dir2 sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
+                               u32 span, Plan* plan, const RG& rg, const Fused* F = nullptr, u32 g = 0) {
+  const u32 sh = span > (u32)kSubBits ? span - (u32)kSubBits : 0u;
+  for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
+  __syncthreads();
+  u32 pk[KB_ITEMS];
+  Dir2 agg = rg.ident;
+  #pragma unroll
+  for (int it = 0; it < KB_ITEMS; ++it) {
+    const u32 i = it * KB_BLOCK + threadIdx.x;
+    pk[it] = 0xFFFFFFFFu;
+    if (i < m) {
+      const u64 k = load_src<RO>(sk + base + i);
+      if (AGG) add_dir(agg, rg, k);
+      const u64 d64 = (k - klo) >> sh;
+      if (d64 < (u64)kSubBins) {
+        const u32 d = (u32)d64;
+        pk[it] = (d << 13) | atomicAdd(&S.cnt[d], 1u);
+      } else {
+        flag_error(plan, ERR_INTERNAL);
+      }
+    }
+  }
+  Dir2 total = rg.ident;
+  if (AGG) {
+    // The aggregate is out before the sort, so later groups' look-backs
+    // need not wait for it.
+    total = block_total_dir(S, agg, rg.ident);
+    if (threadIdx.x == 0) publish_agg(*F, g, total);
+  }
+  const bool crowded = scan_counts(S);
+#ifdef GBH_DEBUG_CHECKS
+  if (S.cnt[kSubBins] != m) {
+    if (threadIdx.x == 0) DBG_REPORT(2, base, m, S.cnt[kSubBins], span);
+    flag_error(plan, ERR_INTERNAL);
+  }
+#endif
+  #pragma unroll
+  for (int it = 0; it < KB_ITEMS; ++it) {
+    const u32 i = it * KB_BLOCK + threadIdx.x;
+    if (i < m && pk[it] != 0xFFFFFFFFu) {
+      const u32 p = phys(S.cnt[pk[it] >> 13] + (pk[it] & 8191u));
+      S.key[p] = load_src<RO>(sk + base + i);
+      S.val[p] = load_src<RO>(sv + base + i);
+    }
+  }
+  __syncthreads();
+  if (!crowded) {
+    for (u32 d = threadIdx.x; d < (u32)kSubBins; d += KB_BLOCK) {
+      const u32 a = S.cnt[d], b = S.cnt[d + 1];
+      if (b - a > 1u) insertion(S, a, b);
+    }
+  } else {
+    bitonic(S, m);
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ void write_out(BucketSmem& S, u64* dk, u32* dv, u32 base, u32 m) {
+  for (u32 i = threadIdx.x; i < m; i += KB_BLOCK) {
+    dk[base + i] = S.key[phys(i)];
+    dv[base + i] = S.val[phys(i)];
+  }
+  __syncthreads();
+}
+
+// A bin of m > kGroupCap pairs at [base, base + m) of (ak, av), keys in
+// [klo, klo + 2^span): split by the next kSubBits key bits into (bk, bv),
+// then sort the pieces of consecutive sub-bins in place there (FUSED: scan
+// them in order instead of writing them back).  `scratch` holds this
+// block's sub-bin starts and piece flags.
+template <bool FUSED>
+__device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __restrict__ av,
+                        u64* bk, u32* bv, u32 base, u32 m, u64 klo, u32 span, u32* scratch,
+                        Plan* plan, const RG& rg, const Fused& F, u32 g) {
+  const u32 sh = span > (u32)kSubBits ? span - (u32)kSubBits : 0u;
+  u32* gstart = scratch;                     // kSubBins + 1
+  u32* gflag = scratch + kSubBins + 1;       // kSubBins / 32 words
+  for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
+  __syncthreads();
+  Dir2 agg = rg.ident;
+  for (u32 i = threadIdx.x; i < m; i += KB_BLOCK) {
+    const u64 k = ak[base + i];
+    if (FUSED) add_dir(agg, rg, k);
+    const u64 d64 = (k - klo) >> sh;
+    if (d64 < (u64)kSubBins) atomicAdd(&S.cnt[(u32)d64], 1u);
+    else flag_error(plan, ERR_INTERNAL);
+  }
+  Dir2 total = rg.ident;
+  if (FUSED) {
+    total = block_total_dir(S, agg, rg.ident);
+    if (threadIdx.x == 0) publish_agg(F, g, total);
+  }
+  scan_counts(S);
+  // Piece flags (the group rule again, over sub-bins) and the starts.
+  const u32 T = (u32)kGroupTarget;
+  for (u32 d0 = 0; d0 < (u32)kSubBins; d0 += KB_BLOCK) {
+    const u32 d = d0 + threadIdx.x;
+    const u32 st = S.cnt[d], cn = S.cnt[d + 1] - st;
+    const u32 pst = d ? S.cnt[d - 1] : 0u, pcn = st - pst;
+    const bool f = d == 0 || st / T != pst / T || cn > T || pcn > T;
+    const u32 bal = __ballot_sync(0xFFFFFFFFu, f);
+    if ((threadIdx.x & 31) == 0) gflag[d >> 5] = bal;
+    gstart[d] = st;
+  }
+  if (threadIdx.x == 0) gstart[kSubBins] = S.cnt[kSubBins];
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < m; i += KB_BLOCK) {
+    const u64 k = ak[base + i];
+    const u64 d64 = (k - klo) >> sh;
+    if (d64 >= (u64)kSubBins) continue;
+    const u32 p = atomicAdd(&S.cnt[(u32)d64], 1u);
+    if (p < m) {
+      bk[base + p] = k;
+      bv[base + p] = av[base + i];
+    } else {
+      flag_error(plan, ERR_INTERNAL);
+    }
+  }
+  __syncthreads();
+  if (FUSED && !group_prefix(S, F, g, total, rg, plan)) return;
+  // Pieces [d0, d1): from one flagged sub-bin to the next.
+  u32 d0 = 0;
+  while (d0 < (u32)kSubBins) {
+    if (threadIdx.x == 0) {
+      u32 d1 = d0 + 1;
+      while (d1 < (u32)kSubBins) {
+        const u32 w = gflag[d1 >> 5] >> (d1 & 31);
+        if (w) { d1 += __ffs(w) - 1; break; }
+        d1 = (d1 | 31u) + 1u;
+      }
+      S.misc[0] = d1 < (u32)kSubBins ? d1 : (u32)kSubBins;
+    }
+    __syncthreads();
+    const u32 d1 = S.misc[0];
+    const u32 ps = gstart[d0], pm = gstart[d1] - ps;
+    __syncthreads();
+#ifdef GBH_DEBUG_CHECKS
+    if (ps + pm > m || d1 <= d0 || d1 > (u32)kSubBins) {
+      if (threadIdx.x == 0) { DBG_REPORT(3, ps, pm, m, ((u64)d0 << 32) | d1); flag_error(plan, ERR_INTERNAL); }
+      return;
+    }
+#endif
+    if (pm > (u32)kGroupCap) {
+      if (threadIdx.x == 0) flag_error(plan, ERR_FALLBACK);
+      return;
+    }
+    if (pm > 0) {
+      sort_into_smem<false, false>(S, bk, bv, base + ps, pm, klo + ((u64)d0 << sh), sh + ceil_log2(d1 - d0),
+                                   plan, rg);
+      if (FUSED) scan_piece(S, F, pm, base, plan->s, rg, plan);
+      else write_out(S, bk, bv, base + ps, pm);
+    }
+    d0 = d1;
+  }
+}
+
+// One block per group of consecutive bins, taken in order from a counter.
+// The survivors are in (ak, av), binned.  Without FUSED the sorted result
+// goes to (bk, bv).  With FUSED the second round runs on each sorted group
+// at once: the group publishes its direction aggregate as soon as it has
+// read its pairs, finds its exclusive prefix by a decoupled look-back over
+// the earlier groups (bounded waits), and stages only its kept points; the
+// last block turns the groups' kept counts into offsets (then
+// launch_group_compact moves the kept points into the region lists).
+template <bool FUSED>
+__global__ void __launch_bounds__(KB_BLOCK, 2)
+k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* bv, Plan* plan,
+          const uint2* __restrict__ groups, u32* __restrict__ scratch, Fused F) {
+  extern __shared__ __align__(16) unsigned char kb_smem[];
+  BucketSmem& S = *reinterpret_cast<BucketSmem*>(kb_smem);
+  __shared__ bool s_last;
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
+  const u32 ng = plan->ngroups;
+  const u32 fshift = plan->fshift;
+  const u32 s = plan->s;
+  const RG rg = make_rg(plan);
+  u32* my_scratch = scratch + (size_t)blockIdx.x * kScratchWords;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const u32 g = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
+      S.misc[1] = (ld_volatile_u32(&plan->error) & (ERR_FALLBACK | ERR_TIMEOUT)) ? ng : g;
+    }
+    __syncthreads();
+    const u32 g = S.misc[1];
+    __syncthreads();
+    if (g >= ng) break;
+    const uint2 a = groups[g], b = groups[g + 1];   // (first position, first bin)
+    const u32 m = b.x - a.x;
+#ifdef GBH_DEBUG_CHECKS
+    if (b.x < a.x || b.x > s || b.y <= a.y || b.y > (u32)kBins) {
+      if (threadIdx.x == 0) { DBG_REPORT(1, g, ng, ((u64)a.x << 32) | a.y, ((u64)b.x << 32) | b.y); flag_error(plan, ERR_INTERNAL); }
+      break;
+    }
+#endif
+    const u64 klo = (u64)a.y << fshift;
+    const u32 span = fshift + ceil_log2(b.y - a.y);
+    if (m <= (u32)kGroupCap) {
+      if (FUSED) {
+        Dir2 total = rg.ident;
+        if (m > 0) total = sort_into_smem<true, true>(S, ak, av, a.x, m, klo, span, plan, rg, &F, g);
+        else if (threadIdx.x == 0) publish_agg(F, g, total);
+        if (!group_prefix(S, F, g, total, rg, plan)) break;
+        if (m > 0) scan_piece(S, F, m, a.x, s, rg, plan);
+      } else if (m > 0) {
+        sort_into_smem<true, false>(S, ak, av, a.x, m, klo, span, plan, rg);
+        write_out(S, bk, bv, a.x, m);
+      }
+    } else {
+      big_bin<FUSED>(S, ak, av, bk, bv, a.x, m, klo, span, my_scratch, plan, rg, F, g);
+    }
+    if (FUSED && threadIdx.x == 0) {
+      F.recs[g].cnt = make_uint2(S.kept[0], S.kept[1]);
+      F.recs[g].base = a.x;
+    }
+  }
+  if (!FUSED) return;
+  // The last block to finish turns the kept counts into offsets.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_REGION2], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  region_offsets(plan, F.recs, ng, s, &S.kwl[0][0], F.lo_xy, F.lo_idx, F.up_xy, F.up_idx);
+}
+
+// Per-bin prefix over the histogram rows (one per K2 block): row r, bin b
+// becomes the number of bin-b survivors of rows before r; bstart[b] first
+// receives the bin totals, and the last block turns them into the bins'
+// first positions and writes the groups (first position, first bin), with a
+// closing record (s, kBins) after the last group.
+constexpr int BS_BLOCK = 256;
+constexpr int BS_BINS = 32;                 // bins per block (one per lane)
+constexpr int BS_WARPS = BS_BLOCK / 32;
+constexpr int BS_PER = kBins / BS_BLOCK;    // bins per thread in the last block (a flag word each)
+static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole slices of at most 32 bins per thread");
+
+__global__ void __launch_bounds__(BS_BLOCK)
+k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
+          uint2* __restrict__ groups, K4Chunk* __restrict__ recs) {
+  __shared__ u32 s_part[BS_WARPS][BS_BINS];
+  __shared__ u32 s_w[BS_WARPS];
+  __shared__ u32 s_last_st[BS_BLOCK], s_last_cn[BS_BLOCK];
+  __shared__ bool s_last;
+  if (plan->error & ERR_RANGE) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 bin = blockIdx.x * BS_BINS + lane;
+  // Clear the look-back records of the fused second round (one per group,
+  // at most one group per bin): 8 words per record.
+  if (recs)
+    for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
+      reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
+  const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
+  const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
+  u32 sum = 0;
+  for (u32 r = r0; r < r1; ++r) sum += rows[(size_t)r * kBins + bin];
+  s_part[wid][lane] = sum;
+  __syncthreads();
+  u32 run = 0, tot = 0;
+  for (int w = 0; w < BS_WARPS; ++w) {
+    if (w < wid) run += s_part[w][lane];
+    tot += s_part[w][lane];
+  }
+  for (u32 r = r0; r < r1; ++r) {
+    const u32 v = rows[(size_t)r * kBins + bin];
+    rows[(size_t)r * kBins + bin] = run;
+    run += v;
+  }
+  if (wid == 0) bstart[bin] = tot;
+
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_BIN_SCAN], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // Last block: bin starts and groups.  Thread t owns bins [32t, 32t + 32).
+  u32 cn[BS_PER], st[BS_PER];
+  u32 tsum = 0;
+  #pragma unroll
+  for (int j = 0; j < BS_PER; ++j) {
+    cn[j] = ld_volatile_u32(&bstart[threadIdx.x * BS_PER + j]);
+    tsum += cn[j];
+  }
+  u32 inc = tsum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  u32 acc = inc - tsum;
+  for (int w = 0; w < wid; ++w) acc += s_w[w];
+  #pragma unroll
+  for (int j = 0; j < BS_PER; ++j) { st[j] = acc; acc += cn[j]; }
+  s_last_st[threadIdx.x] = st[BS_PER - 1];
+  s_last_cn[threadIdx.x] = cn[BS_PER - 1];
+  __syncthreads();
+  const u32 T = (u32)kGroupTarget;
+  u32 flags = 0;
+  #pragma unroll
+  for (int j = 0; j < BS_PER; ++j) {
+    const u32 b = threadIdx.x * BS_PER + j;
+    u32 pst, pcn;
+    if (j) { pst = st[j - 1]; pcn = cn[j - 1]; }
+    else if (threadIdx.x) { pst = s_last_st[threadIdx.x - 1]; pcn = s_last_cn[threadIdx.x - 1]; }
+    else { pst = 0; pcn = 0; }
+    const bool f = b == 0 || st[j] / T != pst / T || cn[j] > T || pcn > T;
+    flags |= (u32)f << j;
+  }
+  const u32 nf = __popc(flags);
+  u32 finc = nf;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, finc, o);
+    if (lane >= o) finc += t;
+  }
+  __syncthreads();
+  if (lane == 31) s_w[wid] = finc;
+  __syncthreads();
+  u32 g = finc - nf;
+  for (int w = 0; w < wid; ++w) g += s_w[w];
+  #pragma unroll
+  for (int j = 0; j < BS_PER; ++j) {
+    const u32 b = threadIdx.x * BS_PER + j;
+    bstart[b] = st[j];
+    if (flags & (1u << j)) groups[g++] = make_uint2(st[j], b);
+  }
+  if (threadIdx.x == BS_BLOCK - 1) {
+    groups[g] = make_uint2(acc, (u32)kBins);
+    plan->ngroups = g;
+    plan->npasses = 0;        // no radix passes on this path;
+    plan->sorted_in_b = 1;    // k3_bucket leaves the sorted survivors in the second buffer
+  }
+}
+
+// ---- the same sort over an arbitrary key array (the stage entry point):
+// key bits from an OR of all keys, then per-block bin rows over chunks of
+// KA_CHUNK keys (chunk c in block c mod grid), the bin scan, and a scatter
+// over the same chunks.
+constexpr int KA_BLOCK = 256;
+constexpr int KA_CHUNK = 4096;
+
+__global__ void __launch_bounds__(KA_BLOCK)
+k3_array_keyor(const u64* __restrict__ keys, Plan* plan, unsigned long long* key_or) {
+  const u32 s = plan->s;
+  u64 v = 0;
+  for (u32 i = blockIdx.x * KA_BLOCK + threadIdx.x; i < s; i += gridDim.x * KA_BLOCK) v |= keys[i];
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicOr(key_or, (unsigned long long)v);
+}
+
+__global__ void __launch_bounds__(KA_BLOCK)
+k3_array_hist(const u64* __restrict__ keys, Plan* plan, const unsigned long long* key_or,
+              u32* __restrict__ rows) {
+  extern __shared__ u32 h[];
+  const u32 s = plan->s;
+  const u64 o = *key_or;
+  const u32 kbits = o ? 64u - (u32)__clzll((long long)o) : 0u;
+  const u32 fshift = kbits > (u32)kBinBits ? kbits - (u32)kBinBits : 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) plan->fshift = fshift;
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += KA_BLOCK) h[q] = 0u;
+  __syncthreads();
+  for (u32 c = blockIdx.x; (size_t)c * KA_CHUNK < s; c += gridDim.x)
+    for (u32 i = c * KA_CHUNK + threadIdx.x; i < min(s, (c + 1) * (u32)KA_CHUNK); i += KA_BLOCK)
+      atomicAdd(&h[(u32)(keys[i] >> fshift)], 1u);
+  __syncthreads();
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += KA_BLOCK) rows[(size_t)blockIdx.x * kBins + q] = h[q];
+}
+
+__global__ void __launch_bounds__(KA_BLOCK)
+k3_array_scatter(const u64* __restrict__ keys, const u32* __restrict__ vals, Plan* plan,
+                 const u32* __restrict__ rows, const u32* __restrict__ bstart, u64* __restrict__ ok,
+                 u32* __restrict__ ov) {
+  extern __shared__ u32 cur[];
+  const u32 s = plan->s;
+  const u32 fshift = plan->fshift;
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += KA_BLOCK)
+    cur[q] = bstart[q] + rows[(size_t)blockIdx.x * kBins + q];
+  __syncthreads();
+  for (u32 c = blockIdx.x; (size_t)c * KA_CHUNK < s; c += gridDim.x)
+    for (u32 i = c * KA_CHUNK + threadIdx.x; i < min(s, (c + 1) * (u32)KA_CHUNK); i += KA_BLOCK) {
+      const u64 k = keys[i];
+      const u32 p = atomicAdd(&cur[(u32)(k >> fshift)], 1u);
+      if (p < s) { ok[p] = k; ov[p] = vals[i]; }
+      else flag_error(plan, ERR_INTERNAL);
+    }
+}
+
+#ifdef GBH_DEBUG_CHECKS
+// Region lists must be strictly increasing in (x, y) from P_0 to P_l.
+__global__ void k_check_regions(const Plan* plan, const int2* lo_xy, const int2* up_xy) {
+  for (int c = 0; c < 2; ++c) {
+    const int2* L = c ? up_xy : lo_xy;
+    const u32 r = c ? plan->r_up : plan->r_lo;
+    if (r > plan->s) { if (threadIdx.x == 0 && blockIdx.x == 0) DBG_REPORT(10 + c, r, plan->s, 0, 0); return; }
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i + 1 < r + 2; i += gridDim.x * blockDim.x) {
+      const int2 p = L[i], q = L[i + 1];
+      if (!(p.x < q.x || (p.x == q.x && p.y < q.y))) DBG_REPORT(20 + c, i, r, ((u64)(u32)p.x << 32) | (u32)p.y, ((u64)(u32)q.x << 32) | (u32)q.y);
+    }
+  }
+}
+#endif
+
+}  // namespace
+
+#ifdef GBH_DEBUG_CHECKS
+cudaError_t launch_check_regions(const Plan* plan, const int2* lo_xy, const int2* up_xy, cudaStream_t st) {
+  k_check_regions<<<64, 256, 0, st>>>(plan, lo_xy, up_xy);
+  return cudaGetLastError();
+}
+#endif
+
+size_t bucket_smem() { return sizeof(BucketSmem); }
+size_t bucket_scratch_words(int blocks) { return (size_t)blocks * kScratchWords; }
+
+cudaError_t bucket_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k3_bucket<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(BucketSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k3_bucket<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BucketSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k3_array_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kBins * 4);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k3_array_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kBins * 4);
+  return e;
+}
+
+cudaError_t bucket_occupancy(int* blocks) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k3_bucket<false>, KB_BLOCK, sizeof(BucketSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k3_bucket<true>, KB_BLOCK, sizeof(BucketSmem));
+  *blocks = a < b ? a : b;
+  return e;
+}
+
+cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
+                           cudaStream_t st) {
+  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, nrows, plan, bstart, groups,
+                                                  reinterpret_cast<K4Chunk*>(recs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
+                               const uint2* groups, u32* scratch, int grid, cudaStream_t st) {
+  Fused F{};
+  k3_bucket<false><<<grid, KB_BLOCK, sizeof(BucketSmem), st>>>(ak, av, bk, bv, plan, groups, scratch, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_fused(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
+                                const uint2* groups, u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx,
+                                int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy,
+                                int* up_idx, int grid, cudaStream_t st) {
+  Fused F{reinterpret_cast<K4Chunk*>(recs), t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
+  k3_bucket<true><<<grid, KB_BLOCK, sizeof(BucketSmem), st>>>(ak, av, bk, bv, plan, groups, scratch, F);
+  return cudaGetLastError();
+}
+
+int array_hist_grid(u32 m, int num_sms) {
+  const u32 chunks = (m + KA_CHUNK - 1) / KA_CHUNK;
+  const u32 g = (u32)num_sms * 2u;
+  return (int)(chunks < 1 ? 1 : (chunks < g ? chunks : g));
+}
+
+cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* plan,
+                              unsigned long long* key_or, u32* rows, u32* bstart, uint2* groups,
+                              u64* ok, u32* ov, int grid, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(key_or, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k3_array_keyor<<<grid, KA_BLOCK, 0, st>>>(keys, plan, key_or);
+  k3_array_hist<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, plan, key_or, rows);
+  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr);
+  k3_array_scatter<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, vals, plan, rows, bstart, ok, ov);
+  (void)m;
+  return cudaGetLastError();
+}
+
+}  // namespace gbh

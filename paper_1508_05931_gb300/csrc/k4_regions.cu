@@ -31,6 +31,7 @@
 //   k4_compact  moves the few kept points into the region lists in order.
 #include "hull_internal.cuh"
 #include "kernels.h"
+#include "regions.cuh"
 
 namespace gbh {
 
@@ -44,62 +45,6 @@ constexpr int K4_ITEMS = 8;
 constexpr int K4_CHUNK = K4_BLOCK * K4_ITEMS;      // sorted points per chunk
 constexpr int K4_WARPS = K4_BLOCK / 32;
 
-// Extreme directions seen so far: lower region (counter-clockwise-most)
-// and upper region (clockwise-most).  d(P_0) is the identity of both
-// operations: every lower direction is strictly counter-clockwise of it and
-// every upper direction strictly clockwise, so no "empty" case exists.
-struct __align__(16) Dir2 {
-  int lx, ly, ux, uy;
-};
-
-// Look-back words: one direction per word, with a valid bit, so that a
-// single 64-bit load both finds and reads a published value.  Every
-// direction here has dx <= 0 (P_l has the largest x), so -dx takes 31 bits
-// and dy + 2^30 takes 32.  The words are cleared before each call.
-struct __align__(64) K4Chunk {
-  u64 agg_lo, agg_up;     // chunk aggregate (lower, upper region)
-  u64 inc_lo, inc_up;     // inclusive prefix through this chunk (with d(P_0))
-  uint2 cnt;              // kept points (lower, upper)
-  uint2 off;              // exclusive offsets of the same
-  u64 pad[2];
-};
-static_assert(sizeof(K4Chunk) == 64, "chunk record size");
-
-// Lower region: keep the counter-clockwise-most direction (ties keep a).
-__device__ __forceinline__ void cmax(int& ax, int& ay, int bx, int by) {
-  const bool t = cross2(ax, ay, bx, by) > 0;
-  ax = t ? bx : ax;
-  ay = t ? by : ay;
-}
-// Upper region: keep the clockwise-most direction (ties keep a).
-__device__ __forceinline__ void cmin(int& ax, int& ay, int bx, int by) {
-  const bool t = cross2(ax, ay, bx, by) < 0;
-  ax = t ? bx : ax;
-  ay = t ? by : ay;
-}
-__device__ __forceinline__ void combine(Dir2& a, const Dir2& b) {
-  cmax(a.lx, a.ly, b.lx, b.ly);
-  cmin(a.ux, a.uy, b.ux, b.uy);
-}
-__device__ __forceinline__ Dir2 shfl_up_dir(const Dir2& v, int o) {
-  Dir2 r;
-  r.lx = __shfl_up_sync(0xFFFFFFFFu, v.lx, o);
-  r.ly = __shfl_up_sync(0xFFFFFFFFu, v.ly, o);
-  r.ux = __shfl_up_sync(0xFFFFFFFFu, v.ux, o);
-  r.uy = __shfl_up_sync(0xFFFFFFFFu, v.uy, o);
-  return r;
-}
-// Inclusive warp scan under combine (earlier lanes first).
-__device__ __forceinline__ Dir2 warp_scan_dir(Dir2 v) {
-  const int lane = threadIdx.x & 31;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    Dir2 t = shfl_up_dir(v, o);
-    if (lane >= o) { combine(t, v); v = t; }
-  }
-  return v;
-}
-
 struct Geo {
   const u64* keys;
   const u32* idxs;
@@ -111,8 +56,9 @@ struct Geo {
 __device__ __forceinline__ Geo make_geo(const Plan* plan, const u64* ka, const u32* ia,
                                         const u64* kb, const u32* ib) {
   Geo g;
-  // The sort leaves its result in buffer a after an even number of passes.
-  const bool in_b = (plan->npasses & 1u) != 0;
+  // Buffer a holds the result after an even number of radix passes, b
+  // after an odd number or after the bucket sort.
+  const bool in_b = plan->sorted_in_b != 0;
   g.keys = in_b ? kb : ka;
   g.idxs = in_b ? ib : ia;
   g.s = plan->s;
@@ -170,82 +116,6 @@ __device__ __forceinline__ Dir2 thread_agg(const Geo& g, const int* px, const in
   return a;
 }
 
-__device__ __forceinline__ bool last_block(Plan* plan, int ctr, bool* s_last) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) *s_last = atomicAdd(&plan->ctr[ctr], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (*s_last) __threadfence();
-  return *s_last;
-}
-
-constexpr u64 kDirValid = 1ull << 63;
-__device__ __forceinline__ u64 pack_dir(int dx, int dy) {
-  return kDirValid | ((u64)(u32)(-dx) << 32) | (u64)(u32)(dy + (1 << 30));
-}
-__device__ __forceinline__ void unpack_dir(u64 w, int& dx, int& dy) {
-  dx = -(int)((w >> 32) & 0x7FFFFFFFu);
-  dy = (int)((long long)(u32)w - (1ll << 30));
-}
-__device__ __forceinline__ Dir2 shfl_xor_dir(const Dir2& v, int o) {
-  Dir2 r;
-  r.lx = __shfl_xor_sync(0xFFFFFFFFu, v.lx, o);
-  r.ly = __shfl_xor_sync(0xFFFFFFFFu, v.ly, o);
-  r.ux = __shfl_xor_sync(0xFFFFFFFFu, v.ux, o);
-  r.uy = __shfl_xor_sync(0xFFFFFFFFu, v.uy, o);
-  return r;
-}
-
-// Exclusive prefix of chunk c (one warp): lane l inspects chunk
-// base - l for base = c - 1, c - 33, ...; in each region every chunk up to
-// the nearest inclusive prefix contributes.  False (ERR_TIMEOUT set) if a
-// predecessor published nothing within the spin limit.
-__device__ __forceinline__ bool lookback_dir(K4Chunk* chunks, u32 c, Plan* plan, u32 spin,
-                                             Dir2 ident, Dir2* out) {
-  const int lane = threadIdx.x & 31;
-  Dir2 acc = ident;
-  bool done_lo = false, done_up = false;
-  long long base = (long long)c - 1;
-  while (base >= 0 && !(done_lo && done_up)) {
-    const long long t = base - lane;
-    // Before chunk 0 the identity acts as an inclusive prefix.
-    u64 il = kDirValid, iu = kDirValid, al = 0, au = 0;
-    bool bad = false;
-    if (t >= 0) {
-      K4Chunk* ch = &chunks[t];
-      u32 it = 0;
-      for (;;) {
-        il = ld_relaxed_u64(&ch->inc_lo); iu = ld_relaxed_u64(&ch->inc_up);
-        al = ld_relaxed_u64(&ch->agg_lo); au = ld_relaxed_u64(&ch->agg_up);
-        if (((il | al) & kDirValid) && ((iu | au) & kDirValid)) break;
-        if (++it > spin || aborted(plan)) { bad = true; break; }
-        spin_pause(it);
-      }
-    }
-    if (__any_sync(0xFFFFFFFFu, bad)) {
-      if (lane == 0) flag_error(plan, ERR_TIMEOUT);
-      return false;
-    }
-    Dir2 v = ident;
-    const u32 ml = __ballot_sync(0xFFFFFFFFu, (il & kDirValid) != 0);
-    const u32 mu = __ballot_sync(0xFFFFFFFFu, (iu & kDirValid) != 0);
-    const int sl = ml ? (__ffs(ml) - 1) : 31, su = mu ? (__ffs(mu) - 1) : 31;
-    if (t >= 0 && !done_lo && lane <= sl) unpack_dir((il & kDirValid) ? il : al, v.lx, v.ly);
-    if (t >= 0 && !done_up && lane <= su) unpack_dir((iu & kDirValid) ? iu : au, v.ux, v.uy);
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const Dir2 w = shfl_xor_dir(v, o);
-      combine(v, w);
-    }
-    combine(acc, v);
-    done_lo = done_lo || ml != 0u;
-    done_up = done_up || mu != 0u;
-    base -= 32;
-  }
-  *out = acc;
-  return true;
-}
-
 __global__ void __launch_bounds__(K4_BLOCK, 1024 / K4_BLOCK)
 k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __restrict__ kb,
         const u32* __restrict__ ib, Plan* plan, K4Chunk* __restrict__ chunks,
@@ -258,7 +128,7 @@ k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __res
   __shared__ u32 s_chunk;
   __shared__ int s_fail;
   __shared__ bool s_last;
-  if (plan->error & ERR_RANGE) return;
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
   const Geo g = make_geo(plan, ka, ia, kb, ib);
   const u32 nchunks = (g.s + K4_CHUNK - 1) / K4_CHUNK;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -333,7 +203,7 @@ k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __res
       if (w < wid) { wl += s_wc[w][0]; wu += s_wc[w][1]; }
       tl += s_wc[w][0]; tu += s_wc[w][1];
     }
-    if (threadIdx.x == 0) chunks[c].cnt = make_uint2(tl, tu);
+    if (threadIdx.x == 0) { chunks[c].cnt = make_uint2(tl, tu); chunks[c].base = c * K4_CHUNK; }
     u32 pl = c * K4_CHUNK + wl + i_lo - c_lo;
     u32 pu = c * K4_CHUNK + wu + i_up - c_up;
     #pragma unroll
@@ -345,61 +215,32 @@ k4_scan(const u64* __restrict__ ka, const u32* __restrict__ ia, const u64* __res
   }
   if (failed) return;
   if (!last_block(plan, CTR_REGION2, &s_last)) return;
-  const u32 per = (nchunks + K4_BLOCK - 1) / K4_BLOCK;
-  const u32 lo = min(nchunks, threadIdx.x * per), hi = min(nchunks, lo + per);
-  u32 sl = 0, su = 0;
-  for (u32 c = lo; c < hi; ++c) {
-    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
-    sl += q[0]; su += q[1];
-  }
-  u32 il = sl, iu = su;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 t0 = __shfl_up_sync(0xFFFFFFFFu, il, o);
-    const u32 t1 = __shfl_up_sync(0xFFFFFFFFu, iu, o);
-    if (lane >= o) { il += t0; iu += t1; }
-  }
-  if (lane == 31) { s_wc[wid][0] = il; s_wc[wid][1] = iu; }
-  __syncthreads();
-  u32 ol = 0, ou = 0;
-  for (int w = 0; w < wid; ++w) { ol += s_wc[w][0]; ou += s_wc[w][1]; }
-  u32 rl = ol + il - sl, ru = ou + iu - su;
-  for (u32 c = lo; c < hi; ++c) {
-    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
-    const u32 a = q[0], b = q[1];
-    chunks[c].off = make_uint2(rl, ru);
-    rl += a; ru += b;
-  }
-  if (threadIdx.x == K4_BLOCK - 1) {
-    const u32 r_lo = ol + il, r_up = ou + iu;
-    plan->r_lo = r_lo;
-    plan->r_up = r_up;
-    const int i_a = plan->ext_idx[0], i_b = plan->ext_idx[1];
-    lo_xy[0] = make_int2(g.ax, g.ay); lo_idx[0] = i_a;
-    up_xy[0] = make_int2(g.ax, g.ay); up_idx[0] = i_a;
-    if (r_lo + 1 < g.s + 2) { lo_xy[r_lo + 1] = make_int2(g.bx, g.by); lo_idx[r_lo + 1] = i_b; }
-    if (r_up + 1 < g.s + 2) { up_xy[r_up + 1] = make_int2(g.bx, g.by); up_idx[r_up + 1] = i_b; }
-  }
+  region_offsets(plan, chunks, nchunks, g.s, &s_wc[0][0], lo_xy, lo_idx, up_xy, up_idx);
 }
 
+// Moves the kept points staged per record (from slot base) into the region
+// lists in order.  Records: K4's chunks, or the bucket sort's groups
+// (GROUPS: their number is plan->ngroups).
+template <bool GROUPS>
 __global__ void __launch_bounds__(K4_BLOCK)
 k4_compact(Plan* plan, const K4Chunk* __restrict__ chunks, const int2* __restrict__ t_lo_xy,
            const int* __restrict__ t_lo_idx, const int2* __restrict__ t_up_xy,
            const int* __restrict__ t_up_idx, int2* __restrict__ lo_xy, int* __restrict__ lo_idx,
            int2* __restrict__ up_xy, int* __restrict__ up_idx) {
-  if (plan->error & (ERR_RANGE | ERR_TIMEOUT)) return;
+  if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_FALLBACK)) return;
   const u32 s = plan->s;
-  const u32 nchunks = (s + K4_CHUNK - 1) / K4_CHUNK;
-  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+  const u32 nrec = GROUPS ? plan->ngroups : (s + K4_CHUNK - 1) / K4_CHUNK;
+  for (u32 c = blockIdx.x; c < nrec; c += gridDim.x) {
     const uint2 cnt = chunks[c].cnt, off = chunks[c].off;
+    const u32 base = chunks[c].base;
     for (u32 j = threadIdx.x; j < cnt.x; j += K4_BLOCK) {
       const u32 d = 1 + off.x + j;
-      if (d < s + 1) { lo_xy[d] = t_lo_xy[c * K4_CHUNK + j]; lo_idx[d] = t_lo_idx[c * K4_CHUNK + j]; }
+      if (d < s + 1 && base + j < s) { lo_xy[d] = t_lo_xy[base + j]; lo_idx[d] = t_lo_idx[base + j]; }
       else flag_error(plan, ERR_INTERNAL);
     }
     for (u32 j = threadIdx.x; j < cnt.y; j += K4_BLOCK) {
       const u32 d = 1 + off.y + j;
-      if (d < s + 1) { up_xy[d] = t_up_xy[c * K4_CHUNK + j]; up_idx[d] = t_up_idx[c * K4_CHUNK + j]; }
+      if (d < s + 1 && base + j < s) { up_xy[d] = t_up_xy[base + j]; up_idx[d] = t_up_idx[base + j]; }
       else flag_error(plan, ERR_INTERNAL);
     }
   }
@@ -426,8 +267,17 @@ cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib
   if (e != cudaSuccess) return e;
   k4_scan<<<grid, K4_BLOCK, 0, st>>>(ka, ia, kb, ib, plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx,
                                      lo_xy, lo_idx, up_xy, up_idx);
-  k4_compact<<<grid, K4_BLOCK, 0, st>>>(plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx,
-                                        up_xy, up_idx);
+  k4_compact<false><<<grid, K4_BLOCK, 0, st>>>(plan, ch, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx,
+                                               up_xy, up_idx);
+  return cudaGetLastError();
+}
+
+// The compaction after the bucket sort's fused second round (one record per group).
+cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_lo_xy, const int* t_lo_idx,
+                                 const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,
+                                 int2* up_xy, int* up_idx, int grid, cudaStream_t st) {
+  k4_compact<true><<<grid, K4_BLOCK, 0, st>>>(plan, reinterpret_cast<const K4Chunk*>(status), t_lo_xy, t_lo_idx,
+                                              t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx);
   return cudaGetLastError();
 }
 

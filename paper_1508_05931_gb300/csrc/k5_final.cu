@@ -97,7 +97,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
   __shared__ int s_start[K5_BLOCK];
   __shared__ int s_wsum[K5_WARPS];
 
-  if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL)) return;
+  if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL | ERR_FALLBACK)) return;
   const u32 spin = plan->spin_limit;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 

@@ -37,6 +37,38 @@ cudaError_t k2_configure();
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
                       unsigned char* mask, int grid_count, int grid_write, cudaStream_t st);
 
+// Bucket sort (the pipeline's sort): K2 with bin rows + bin scan + scatter,
+// then one block per group of bins (k3_bucket.cu).
+cudaError_t k2_bins_occupancy(int* blocks);
+cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
+                           unsigned char* mask, u32* rows, u32* bstart, uint2* groups, void* recs, int grid,
+                           cudaStream_t st);
+size_t bucket_smem();
+size_t bucket_scratch_words(int blocks);
+cudaError_t bucket_configure();
+cudaError_t bucket_occupancy(int* blocks);
+cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
+                           cudaStream_t st);
+cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
+                               const uint2* groups, u32* scratch, int grid, cudaStream_t st);
+// The bucket sort with the second round (K4's scan) run on each sorted
+// group; `recs` are K4's look-back records (one per group, cleared by the
+// bin scan), t_* its staging areas, then launch_group_compact.
+cudaError_t launch_bucket_fused(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
+                                const uint2* groups, u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx,
+                                int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy,
+                                int* up_idx, int grid, cudaStream_t st);
+#ifdef GBH_DEBUG_CHECKS
+cudaError_t launch_check_regions(const Plan* plan, const int2* lo_xy, const int2* up_xy, cudaStream_t st);
+#endif
+cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_lo_xy, const int* t_lo_idx,
+                                 const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,
+                                 int2* up_xy, int* up_idx, int grid, cudaStream_t st);
+int array_hist_grid(u32 m, int num_sms);
+cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* plan,
+                              unsigned long long* key_or, u32* rows, u32* bstart, uint2* groups,
+                              u64* ok, u32* ov, int grid, cudaStream_t st);
+
 int k3_tile();
 size_t k3_dyn_smem();
 cudaError_t k3_configure();

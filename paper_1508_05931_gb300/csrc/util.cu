@@ -20,7 +20,7 @@ __global__ void k_plan_patch(Plan* plan, PlanPatch p) {
     plan->spin_limit = p.spin_limit;
   }
   if (p.set_s) plan->s = p.s;
-  if (p.set_npasses) plan->npasses = p.npasses;
+  if (p.set_npasses) { plan->npasses = p.npasses; plan->sorted_in_b = p.npasses & 1u; }
   if (p.set_ncorner) plan->ncorner = p.ncorner;
   if (p.set_r) { plan->r_lo = p.r_lo; plan->r_up = p.r_up; }
 }

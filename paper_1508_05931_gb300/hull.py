@@ -35,7 +35,8 @@ class hull_config(ctypes.Structure):
 class hull_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("s", ctypes.c_int64), ("r_lower", ctypes.c_int64),
                 ("r_upper", ctypes.c_int64), ("h", ctypes.c_int64), ("ext", ctypes.c_int32 * 4),
-                ("ncorner", ctypes.c_int32), ("learned_used", ctypes.c_int32)]
+                ("ncorner", ctypes.c_int32), ("learned_used", ctypes.c_int32),
+                ("sort_fallback", ctypes.c_int32)]
 
 
 NUM_STAGES = 12
@@ -77,6 +78,7 @@ _sig = {
     "hull_stage_extremes": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "hull_stage_filter": ([_P, _P, _I64, _P, _PI64, _P], ctypes.c_int),
     "hull_stage_sort": ([_P, _P, _P, _I64, _P], ctypes.c_int),
+    "hull_stage_bucket_sort": ([_P, _P, _P, _I64, ctypes.POINTER(ctypes.c_int32), _P], ctypes.c_int),
     "hull_stage_second_round": ([_P, _P, _P, _I64, _P, _PI64, _P, _PI64, _P], ctypes.c_int),
     "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
 }
@@ -250,7 +252,8 @@ class Context:
         st = hull_stats()
         _check(_lib.hull_last_stats(self._h, ctypes.byref(st)), "hull_last_stats")
         return {"n": st.n, "s": st.s, "r_lower": st.r_lower, "r_upper": st.r_upper, "h": st.h,
-                "ext": list(st.ext), "ncorner": st.ncorner, "learned_used": st.learned_used}
+                "ext": list(st.ext), "ncorner": st.ncorner, "learned_used": st.learned_used,
+                "sort_fallback": st.sort_fallback}
 
     def set_profiling(self, enable: bool = True):
         _check(_lib.hull_set_profiling(self._h, int(bool(enable))), "hull_set_profiling")
@@ -354,6 +357,17 @@ class Context:
                                     _stream_handle(stream)), "hull_stage_sort")
         return keys, vals
 
+    def stage_bucket_sort(self, keys, vals, stream=None):
+        """Sorts (uint64 keys stored in an int64 tensor, int32 values) in place
+        by (key, value) with the pipeline's bucket sort; returns True when it
+        handed the pairs to the radix passes."""
+        torch = _torch()
+        assert keys.dtype == torch.int64 and vals.dtype == torch.int32 and keys.is_cuda
+        fb = ctypes.c_int32(0)
+        _check(_lib.hull_stage_bucket_sort(self._h, _ptr(keys), _ptr(vals), keys.numel(), ctypes.byref(fb),
+                                           _stream_handle(stream)), "hull_stage_bucket_sort")
+        return bool(fb.value)
+
     def stage_second_round(self, xy_sorted, labels, stream=None):
         torch = _torch()
         dev = torch.device("cuda", self.device)
@@ -424,5 +438,6 @@ hull_get_profile = _lib.hull_get_profile
 hull_stage_extremes = _lib.hull_stage_extremes
 hull_stage_filter = _lib.hull_stage_filter
 hull_stage_sort = _lib.hull_stage_sort
+hull_stage_bucket_sort = _lib.hull_stage_bucket_sort
 hull_stage_second_round = _lib.hull_stage_second_round
 hull_stage_chain = _lib.hull_stage_chain

@@ -89,6 +89,24 @@ def test_full_size_configs(ctx, name):
     out = torch.empty(len(pts), dtype=torch.int32, device="cuda")
     h = ctx.compute(t, out=out).cpu().numpy()
     assert h.tolist() == oracle.hull(pts).tolist()
+    assert ctx.last_stats()["sort_fallback"] == 0
+
+
+def test_sort_fallback_only_when_needed(ctx):
+    """The bucket sort takes the paper-shaped inputs itself; identical or
+    heavily duplicated points (a bin it cannot split) are rerun on the radix
+    passes, with the same hull."""
+    for pts in (W.uniform_square(300_000, 1 << 29, 11), W.uniform_disk(300_000, 2.0 ** 29, 12),
+                W.near_circle(400_000, 2.0 ** 28, 13)):
+        assert gpu_hull(ctx, pts).tolist() == oracle.hull(pts).tolist()
+        assert ctx.last_stats()["sort_fallback"] == 0
+    same = np.full((20000, 2), 77, np.int32)
+    assert gpu_hull(ctx, same).tolist() == [0]
+    assert ctx.last_stats()["sort_fallback"] == 1
+    rng = np.random.default_rng(9)
+    few = rng.integers(-1000, 1000, size=(40, 2)).astype(np.int32)
+    dup = few[rng.integers(0, 40, size=400_000)]
+    assert gpu_hull(ctx, dup).tolist() == oracle.hull(dup).tolist()
 
 
 def test_determinism_repeated(ctx):

@@ -97,6 +97,63 @@ def test_sort_parity(ctx, m, kind):
     assert np.array_equal(vt.cpu().numpy(), vals[order])
 
 
+def _bucket_keys(rng, m, kind):
+    if kind == "random":            # full 64-bit keys: many small bins, insertion path
+        return rng.integers(0, 2 ** 63, size=m, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=m).astype(np.uint64)
+    if kind == "equal":             # one bin: bitonic path up to 8192 keys, then the radix passes
+        return np.full(m, 12345, dtype=np.uint64)
+    if kind == "lowbits":           # 16 distinct keys: crowded sub-bins
+        return rng.integers(0, 16, size=m).astype(np.uint64)
+    if kind == "dups":              # ~1000 distinct keys, each a bin of its own
+        return (rng.integers(0, 1000, size=m).astype(np.uint64) << np.uint64(40)) + np.uint64(7)
+    if kind == "bigbin":            # a third of the keys in the first bin: split once more
+        k = rng.integers(0, 2 ** 61, size=m, dtype=np.uint64)
+        third = m // 3
+        k[:third] = rng.integers(0, 2 ** 47, size=third, dtype=np.uint64)
+        return rng.permutation(k)
+    if kind == "lattice":           # the pipeline's keys of a small uniform square
+        pts = W.uniform_square(m, 1 << 20, m)
+        x = pts[:, 0].astype(np.int64) - pts[:, 0].min()
+        y = pts[:, 1].astype(np.int64) - pts[:, 1].min()
+        yb = int(y.max()).bit_length()
+        return ((x << yb) | y).astype(np.uint64)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("m", [1, 2, 100, 4097, 8192, 8193, 100003, 1000001])
+@pytest.mark.parametrize("kind", ["random", "equal", "lowbits", "dups", "bigbin", "lattice"])
+def test_bucket_sort_parity(ctx, m, kind):
+    """The pipeline's bucket sort orders (key, value) pairs by key, then
+    value; with values ascending in input order (as the first round's
+    survivor indices are) that is the stable sort by key."""
+    rng = np.random.default_rng(m * 13 + len(kind))
+    keys = _bucket_keys(rng, m, kind)
+    vals = np.arange(m, dtype=np.int32)
+    kt = dev(keys.view(np.int64))
+    vt = dev(vals)
+    fell_back = ctx.stage_bucket_sort(kt, vt)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(kt.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(vt.cpu().numpy(), vals[order])
+    # Only a bin of more than 8192 keys that its next 12 key bits cannot
+    # split (equal keys here) hands the pairs to the radix passes.
+    expect_fb = (kind == "equal" and m > 8192) or (kind == "lowbits" and m > 16 * 8192)
+    assert fell_back == expect_fb
+
+
+def test_bucket_sort_values_break_ties(ctx):
+    """Among equal keys the smaller value comes first, whatever the input order."""
+    rng = np.random.default_rng(3)
+    m = 50000
+    keys = rng.integers(0, 300, size=m).astype(np.uint64) << np.uint64(33)
+    vals = rng.permutation(m).astype(np.int32)
+    kt, vt = dev(keys.view(np.int64)), dev(vals)
+    assert not ctx.stage_bucket_sort(kt, vt)
+    order = np.lexsort((vals, keys))
+    assert np.array_equal(kt.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(vt.cpu().numpy(), vals[order])
+
+
 def _sorted_input(pts):
     srt = oracle.sort_survivors(pts, np.arange(len(pts)))
     return pts[srt], srt
