@@ -298,16 +298,17 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
   if (bucket) {
-    // Survivors scattered into bins, then one block per group of bins sorts
-    // it in shared memory and runs the second round on it at once.
+    // Survivors scattered into bins, every group's direction aggregate and
+    // their prefixes, then one block per group of bins sorts it in shared
+    // memory and runs the second round on it from its prefix.
     const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
     e = launch_k2_bins(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, w.rows, w.bstart, w.groups,
                        w.st_region, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
-    e = launch_bucket_fused(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.groups, w.bscratch, w.st_region,
-                            w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx, w.up_xy, w.up_idx,
-                            c->occ_kb * c->num_sms, st);
+    e = launch_bucket_decide(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.groups, w.bscratch,
+                             w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
+                             w.up_xy, w.up_idx, c->occ_kb * c->num_sms, c->num_sms * 8, st);
     if (e != cudaSuccess) return cuda_fail(e);
     for (int p = 0; p < kMaxPasses; ++p) mark(c, 3 + p, st);
     e = launch_group_compact(c->plan, w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy,

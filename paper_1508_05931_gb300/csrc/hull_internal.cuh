@@ -31,11 +31,17 @@ constexpr u32 kMaxN = (1u << 30) - 1;    // look-back count fields are 30 bits
 // key; consecutive bins form groups of at most kGroupCap survivors, each
 // sorted in shared memory by one block (sub-bins of the next kSubBits key
 // bits, then the few keys of a sub-bin in place).
+#ifndef GBH_GROUP_CAP
+#define GBH_GROUP_CAP 8192
+#endif
+#ifndef GBH_SUB_BITS
+#define GBH_SUB_BITS 12
+#endif
 constexpr int kBinBits = 13;
 constexpr int kBins = 1 << kBinBits;
-constexpr int kGroupCap = 8192;              // survivors sorted in shared memory at once
+constexpr int kGroupCap = GBH_GROUP_CAP;     // survivors sorted in shared memory at once
 constexpr int kGroupTarget = kGroupCap / 2;  // window of the group rule (see k3_bucket.cu)
-constexpr int kSubBits = 12;
+constexpr int kSubBits = GBH_SUB_BITS;
 constexpr int kSubBins = 1 << kSubBits;
 
 // Error bits accumulated in Plan::error by the kernels.

@@ -39,7 +39,11 @@ namespace gbh {
 
 namespace {
 
-constexpr int KB_BLOCK = 512;
+#ifndef GBH_KB_BLOCK
+#define GBH_KB_BLOCK 512
+#endif
+constexpr int KB_BLOCK = GBH_KB_BLOCK;
+constexpr int KB_MIN_BLOCKS = 1024 / KB_BLOCK;      // resident blocks per SM the registers allow
 constexpr int KB_WARPS = KB_BLOCK / 32;
 constexpr int KB_ITEMS = kGroupCap / KB_BLOCK;     // keys per thread in a full group
 constexpr u32 kCrowded = 32;                       // largest sub-bin ordered by insertion
@@ -54,12 +58,11 @@ struct BucketSmem {
   u32 cnt[kSubBins + 1];
   u32 wsum[KB_WARPS];
   u32 misc[4];
-  // fused second round
+  // second round
   Dir2 dirs[KB_WARPS];     // per-warp direction aggregates
-  Dir2 carry;              // prefix through the group's pieces scanned so far
+  Dir2 carry;              // prefix through the group's positions scanned so far
   u32 kwl[KB_WARPS][2];    // per-warp kept counts (lower, upper)
   u32 kept[2];             // the group's kept points so far
-  int fail;
 };
 
 // Shared-memory slot of sorted position i: the low five bits are XORed
@@ -210,114 +213,16 @@ __device__ __forceinline__ void add_dir(Dir2& a, const RG& g, u64 k) {
   else if (sd > 0) cmin(a.ux, a.uy, px - g.bx, py - g.by);
 }
 
-// Combines the block's per-thread aggregates; the result on every thread.
-__device__ __forceinline__ Dir2 block_total_dir(BucketSmem& S, Dir2 v, const Dir2& ident) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
-  __syncthreads();
-  if (lane == 0) S.dirs[wid] = v;
-  __syncthreads();
-  Dir2 t = ident;
-  #pragma unroll
-  for (int w = 0; w < KB_WARPS; ++w) combine(t, S.dirs[w]);
-  return t;
-}
 
-// Staging areas and records of the fused second round.
+// The second round run by the pipeline's sort: every group's record holds
+// its exclusive prefix (k_group_agg, k_group_prefix) and receives its kept
+// counts; kept points are staged in t_* and the last block turns the counts
+// into offsets and fills both ends of the region lists.
 struct Fused {
   K4Chunk* recs;
   int2* t_lo_xy; int* t_lo_idx; int2* t_up_xy; int* t_up_idx;
   int2* lo_xy; int* lo_idx; int2* up_xy; int* up_idx;
 };
-
-// Publishes group g's aggregate (group 0 publishes it as its inclusive prefix).
-__device__ __forceinline__ void publish_agg(const Fused& F, u32 g, const Dir2& t) {
-  K4Chunk* r = &F.recs[g];
-  st_relaxed_u64(g == 0 ? &r->inc_lo : &r->agg_lo, pack_dir(t.lx, t.ly));
-  st_relaxed_u64(g == 0 ? &r->inc_up : &r->agg_up, pack_dir(t.ux, t.uy));
-}
-
-// Decoupled look-back over the records of groups before g with the whole
-// block: in each step thread i inspects group base - i (base = g - 1,
-// g - 1 - KB_BLOCK, ...), so one round trip covers KB_BLOCK predecessors
-// (with a few hundred groups in flight the nearest inclusive prefix is
-// usually that far back).  Per region, every group up to the nearest one
-// holding an inclusive prefix contributes (its aggregate, or that prefix);
-// the operation is a maximum under a total order, so the contributions
-// combine in any order.  Every thread calls it; the prefix is returned on
-// all.  False (ERR_TIMEOUT set) if a predecessor published nothing within
-// the spin limit.
-__device__ bool lookback_dir_block(BucketSmem& S, K4Chunk* recs, u32 g, Plan* plan, u32 spin, const Dir2& ident,
-                                   Dir2* out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  Dir2 acc = ident;
-  bool done_lo = false, done_up = false;
-  long long base = (long long)g - 1;
-  while (base >= 0 && !(done_lo && done_up)) {
-    const long long t = base - (long long)threadIdx.x;
-    // Before group 0 the identity acts as an inclusive prefix.
-    u64 il = kDirValid, iu = kDirValid, al = 0, au = 0;
-    bool bad = false;
-    if (t >= 0) {
-      K4Chunk* ch = &recs[t];
-      u32 it = 0;
-      for (;;) {
-        il = ld_relaxed_u64(&ch->inc_lo); iu = ld_relaxed_u64(&ch->inc_up);
-        al = ld_relaxed_u64(&ch->agg_lo); au = ld_relaxed_u64(&ch->agg_up);
-        if (((il | al) & kDirValid) && ((iu | au) & kDirValid)) break;
-        if (++it > spin || aborted(plan)) { bad = true; break; }
-        spin_pause(it);
-      }
-    }
-    if (threadIdx.x == 0) { S.misc[2] = 0xFFFFFFFFu; S.misc[3] = 0xFFFFFFFFu; }
-    if (__syncthreads_or(bad)) {
-      if (threadIdx.x == 0) flag_error(plan, ERR_TIMEOUT);
-      return false;
-    }
-    // The nearest inclusive prefix per region: the lowest thread holding one.
-    const u32 ml = __ballot_sync(0xFFFFFFFFu, (il & kDirValid) != 0);
-    const u32 mu = __ballot_sync(0xFFFFFFFFu, (iu & kDirValid) != 0);
-    if (lane == 0) {
-      if (ml) atomicMin(&S.misc[2], (u32)(wid * 32 + __ffs(ml) - 1));
-      if (mu) atomicMin(&S.misc[3], (u32)(wid * 32 + __ffs(mu) - 1));
-    }
-    __syncthreads();
-    const u32 sl = S.misc[2], su = S.misc[3];
-    Dir2 v = ident;
-    if (t >= 0 && !done_lo && (u32)threadIdx.x <= sl) unpack_dir((il & kDirValid) ? il : al, v.lx, v.ly);
-    if (t >= 0 && !done_up && (u32)threadIdx.x <= su) unpack_dir((iu & kDirValid) ? iu : au, v.ux, v.uy);
-    combine(acc, block_total_dir(S, v, ident));
-    done_lo = done_lo || sl != 0xFFFFFFFFu;
-    done_up = done_up || su != 0xFFFFFFFFu;
-    base -= KB_BLOCK;
-  }
-  *out = acc;
-  return true;
-}
-
-// Exclusive prefix of group g into S.carry (the whole block looks back;
-// group 0: the identity); publishes the inclusive prefix.  False on a
-// timeout.  Every thread calls it.
-__device__ bool group_prefix(BucketSmem& S, const Fused& F, u32 g, const Dir2& agg, const RG& rg, Plan* plan) {
-  Dir2 excl = rg.ident;
-  bool ok = true;
-  if (g > 0) ok = lookback_dir_block(S, F.recs, g, plan, plan->spin_limit, rg.ident, &excl);
-  if (threadIdx.x == 0) {
-    S.fail = ok ? 0 : 1;
-    S.carry = excl;
-    S.kept[0] = S.kept[1] = 0u;
-    if (ok && g > 0) {
-      Dir2 in = excl;
-      combine(in, agg);
-      K4Chunk* r = &F.recs[g];
-      st_relaxed_u64(&r->inc_lo, pack_dir(in.lx, in.ly));
-      st_relaxed_u64(&r->inc_up, pack_dir(in.ux, in.uy));
-    }
-  }
-  __syncthreads();
-  return S.fail == 0;
-}
 
 // Figure 2 over the m sorted pairs in shared memory, starting from the
 // prefix S.carry: keeps a point when its direction is strictly beyond the
@@ -391,26 +296,35 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
   __syncthreads();
 }
 
+
+// Starts group g's second round from its exclusive prefix (one thread).
+__device__ __forceinline__ void start_group(BucketSmem& S, const Fused& F, u32 g) {
+  Dir2 e;
+  unpack_dir(F.recs[g].inc_lo, e.lx, e.ly);
+  unpack_dir(F.recs[g].inc_up, e.ux, e.uy);
+  S.carry = e;
+  S.kept[0] = S.kept[1] = 0u;
+}
+
+
 // Sorts the m <= kGroupCap pairs at [base, base + m) of (sk, sv), whose keys
 // lie in [klo, klo + 2^span), into shared memory (position i in slot
 // phys(i)), ordered by (key, value).  With AGG, also returns on every thread
 // the direction aggregate of the pairs (order-free, from the first load).
 // Every thread of the block calls it.
-template <bool RO, bool AGG>
-__device__ Dir2 sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
-                               u32 span, Plan* plan, const RG& rg, const Fused* F = nullptr, u32 g = 0) {
+template <bool RO>
+__device__ void sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
+                               u32 span, Plan* plan) {
   const u32 sh = span > (u32)kSubBits ? span - (u32)kSubBits : 0u;
   for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
   __syncthreads();
   u32 pk[KB_ITEMS];
-  Dir2 agg = rg.ident;
   #pragma unroll
   for (int it = 0; it < KB_ITEMS; ++it) {
     const u32 i = it * KB_BLOCK + threadIdx.x;
     pk[it] = 0xFFFFFFFFu;
     if (i < m) {
       const u64 k = load_src<RO>(sk + base + i);
-      if (AGG) add_dir(agg, rg, k);
       const u64 d64 = (k - klo) >> sh;
       if (d64 < (u64)kSubBins) {
         const u32 d = (u32)d64;
@@ -419,13 +333,6 @@ __device__ Dir2 sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
         flag_error(plan, ERR_INTERNAL);
       }
     }
-  }
-  Dir2 total = rg.ident;
-  if (AGG) {
-    // The aggregate is out before the sort, so later groups' look-backs
-    // need not wait for it.
-    total = block_total_dir(S, agg, rg.ident);
-    if (threadIdx.x == 0) publish_agg(*F, g, total);
   }
   const bool crowded = scan_counts(S);
 #ifdef GBH_DEBUG_CHECKS
@@ -453,7 +360,6 @@ __device__ Dir2 sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
     bitonic(S, m);
   }
   __syncthreads();
-  return total;
 }
 
 __device__ __forceinline__ void write_out(BucketSmem& S, u64* dk, u32* dv, u32 base, u32 m) {
@@ -466,10 +372,10 @@ __device__ __forceinline__ void write_out(BucketSmem& S, u64* dk, u32* dv, u32 b
 
 // A bin of m > kGroupCap pairs at [base, base + m) of (ak, av), keys in
 // [klo, klo + 2^span): split by the next kSubBits key bits into (bk, bv),
-// then sort the pieces of consecutive sub-bins in place there (FUSED: scan
-// them in order instead of writing them back).  `scratch` holds this
-// block's sub-bin starts and piece flags.
-template <bool FUSED>
+// then sort the pieces of consecutive sub-bins in place there (DECIDE: run
+// the second round over each sorted piece in order instead of writing it
+// back).  `scratch` holds this block's sub-bin starts and piece flags.
+template <bool DECIDE>
 __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __restrict__ av,
                         u64* bk, u32* bv, u32 base, u32 m, u64 klo, u32 span, u32* scratch,
                         Plan* plan, const RG& rg, const Fused& F, u32 g) {
@@ -478,18 +384,11 @@ __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __
   u32* gflag = scratch + kSubBins + 1;       // kSubBins / 32 words
   for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
   __syncthreads();
-  Dir2 agg = rg.ident;
   for (u32 i = threadIdx.x; i < m; i += KB_BLOCK) {
     const u64 k = ak[base + i];
-    if (FUSED) add_dir(agg, rg, k);
     const u64 d64 = (k - klo) >> sh;
     if (d64 < (u64)kSubBins) atomicAdd(&S.cnt[(u32)d64], 1u);
     else flag_error(plan, ERR_INTERNAL);
-  }
-  Dir2 total = rg.ident;
-  if (FUSED) {
-    total = block_total_dir(S, agg, rg.ident);
-    if (threadIdx.x == 0) publish_agg(F, g, total);
   }
   scan_counts(S);
   // Piece flags (the group rule again, over sub-bins) and the starts.
@@ -518,7 +417,6 @@ __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __
     }
   }
   __syncthreads();
-  if (FUSED && !group_prefix(S, F, g, total, rg, plan)) return;
   // Pieces [d0, d1): from one flagged sub-bin to the next.
   u32 d0 = 0;
   while (d0 < (u32)kSubBins) {
@@ -546,25 +444,22 @@ __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __
       return;
     }
     if (pm > 0) {
-      sort_into_smem<false, false>(S, bk, bv, base + ps, pm, klo + ((u64)d0 << sh), sh + ceil_log2(d1 - d0),
-                                   plan, rg);
-      if (FUSED) scan_piece(S, F, pm, base, plan->s, rg, plan);
+      sort_into_smem<false>(S, bk, bv, base + ps, pm, klo + ((u64)d0 << sh), sh + ceil_log2(d1 - d0), plan);
+      if (DECIDE) scan_piece(S, F, pm, base, plan->s, rg, plan);
       else write_out(S, bk, bv, base + ps, pm);
     }
     d0 = d1;
   }
 }
 
-// One block per group of consecutive bins, taken in order from a counter.
-// The survivors are in (ak, av), binned.  Without FUSED the sorted result
-// goes to (bk, bv).  With FUSED the second round runs on each sorted group
-// at once: the group publishes its direction aggregate as soon as it has
-// read its pairs, finds its exclusive prefix by a decoupled look-back over
-// the earlier groups (bounded waits), and stages only its kept points; the
-// last block turns the groups' kept counts into offsets (then
-// launch_group_compact moves the kept points into the region lists).
-template <bool FUSED>
-__global__ void __launch_bounds__(KB_BLOCK, 2)
+// One block per group of consecutive bins, taken from a counter.  The
+// survivors are in (ak, av), binned.  Without DECIDE the sorted result goes
+// to (bk, bv).  With DECIDE (the hull pipeline) the second round runs on
+// each sorted group at once, from the group's exclusive prefix in its
+// record: only the kept points leave the block; the last block turns the
+// groups' kept counts into offsets (then launch_group_compact).
+template <bool DECIDE>
+__global__ void __launch_bounds__(KB_BLOCK, KB_MIN_BLOCKS)
 k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* bv, Plan* plan,
           const uint2* __restrict__ groups, u32* __restrict__ scratch, Fused F) {
   extern __shared__ __align__(16) unsigned char kb_smem[];
@@ -579,7 +474,8 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   for (;;) {
     if (threadIdx.x == 0) {
       const u32 g = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
-      S.misc[1] = (ld_volatile_u32(&plan->error) & (ERR_FALLBACK | ERR_TIMEOUT)) ? ng : g;
+      S.misc[1] = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : g;
+      if (DECIDE && g < ng) start_group(S, F, g);
     }
     __syncthreads();
     const u32 g = S.misc[1];
@@ -596,25 +492,20 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
     const u64 klo = (u64)a.y << fshift;
     const u32 span = fshift + ceil_log2(b.y - a.y);
     if (m <= (u32)kGroupCap) {
-      if (FUSED) {
-        Dir2 total = rg.ident;
-        if (m > 0) total = sort_into_smem<true, true>(S, ak, av, a.x, m, klo, span, plan, rg, &F, g);
-        else if (threadIdx.x == 0) publish_agg(F, g, total);
-        if (!group_prefix(S, F, g, total, rg, plan)) break;
-        if (m > 0) scan_piece(S, F, m, a.x, s, rg, plan);
-      } else if (m > 0) {
-        sort_into_smem<true, false>(S, ak, av, a.x, m, klo, span, plan, rg);
-        write_out(S, bk, bv, a.x, m);
+      if (m > 0) {
+        sort_into_smem<true>(S, ak, av, a.x, m, klo, span, plan);
+        if (DECIDE) scan_piece(S, F, m, a.x, s, rg, plan);
+        else write_out(S, bk, bv, a.x, m);
       }
     } else {
-      big_bin<FUSED>(S, ak, av, bk, bv, a.x, m, klo, span, my_scratch, plan, rg, F, g);
+      big_bin<DECIDE>(S, ak, av, bk, bv, a.x, m, klo, span, my_scratch, plan, rg, F, g);
     }
-    if (FUSED && threadIdx.x == 0) {
+    if (DECIDE && threadIdx.x == 0) {
       F.recs[g].cnt = make_uint2(S.kept[0], S.kept[1]);
       F.recs[g].base = a.x;
     }
   }
-  if (!FUSED) return;
+  if (!DECIDE) return;
   // The last block to finish turns the kept counts into offsets.
   __threadfence();
   __syncthreads();
@@ -623,6 +514,72 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   if (!s_last) return;
   __threadfence();
   region_offsets(plan, F.recs, ng, s, &S.kwl[0][0], F.lo_xy, F.lo_idx, F.up_xy, F.up_idx);
+}
+
+// Direction aggregate of every group of bins (its points in any order):
+// one block per group at a time, keys read once, coalesced.
+constexpr int GA_BLOCK = 256;
+__global__ void __launch_bounds__(GA_BLOCK)
+k_group_agg(const u64* __restrict__ keys, Plan* plan, const uint2* __restrict__ groups, K4Chunk* __restrict__ recs) {
+  __shared__ Dir2 s_w[GA_BLOCK / 32];
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
+  const u32 ng = plan->ngroups;
+  const RG rg = make_rg(plan);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (u32 g = blockIdx.x; g < ng; g += gridDim.x) {
+    const u32 a = groups[g].x, b = groups[g + 1].x;
+    Dir2 v = rg.ident;
+    for (u32 i = a + threadIdx.x; i < b; i += GA_BLOCK) add_dir(v, rg, keys[i]);
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
+    if (lane == 0) s_w[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Dir2 t = rg.ident;
+      for (int w = 0; w < GA_BLOCK / 32; ++w) combine(t, s_w[w]);
+      recs[g].agg_lo = pack_dir(t.lx, t.ly);
+      recs[g].agg_up = pack_dir(t.ux, t.uy);
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive prefixes of the groups' direction aggregates (one block):
+// record g's inclusive words receive the combination of the aggregates of
+// groups 0 .. g - 1 with d(P_0) (the identity).  Thread t takes a
+// contiguous slice of groups.
+constexpr int GP_BLOCK = 1024;
+__global__ void __launch_bounds__(GP_BLOCK)
+k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
+  __shared__ Dir2 s_w[GP_BLOCK / 32];
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
+  const u32 ng = plan->ngroups;
+  const RG rg = make_rg(plan);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 per = (ng + GP_BLOCK - 1) / GP_BLOCK;
+  const u32 g0 = min(ng, threadIdx.x * per), g1 = min(ng, g0 + per);
+  Dir2 t = rg.ident;
+  for (u32 g = g0; g < g1; ++g) {
+    Dir2 v;
+    unpack_dir(recs[g].agg_lo, v.lx, v.ly);
+    unpack_dir(recs[g].agg_up, v.ux, v.uy);
+    combine(t, v);
+  }
+  const Dir2 inc = warp_scan_dir(t);
+  Dir2 lex = shfl_up_dir(inc, 1);
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  Dir2 run = rg.ident;
+  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
+  if (lane > 0) combine(run, lex);
+  for (u32 g = g0; g < g1; ++g) {
+    recs[g].inc_lo = pack_dir(run.lx, run.ly);
+    recs[g].inc_up = pack_dir(run.ux, run.uy);
+    Dir2 v;
+    unpack_dir(recs[g].agg_lo, v.lx, v.ly);
+    unpack_dir(recs[g].agg_up, v.ux, v.uy);
+    combine(run, v);
+  }
 }
 
 // Per-bin prefix over the histogram rows (one per K2 block): row r, bin b
@@ -852,11 +809,14 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_fused(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
-                                const uint2* groups, u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx,
-                                int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy,
-                                int* up_idx, int grid, cudaStream_t st) {
-  Fused F{reinterpret_cast<K4Chunk*>(recs), t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
+cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
+                                 u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
+                                 int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
+                                 int agg_grid, cudaStream_t st) {
+  K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
+  Fused F{R, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
+  k_group_agg<<<agg_grid, GA_BLOCK, 0, st>>>(ak, plan, groups, R);
+  k_group_prefix<<<1, GP_BLOCK, 0, st>>>(plan, R);
   k3_bucket<true><<<grid, KB_BLOCK, sizeof(BucketSmem), st>>>(ak, av, bk, bv, plan, groups, scratch, F);
   return cudaGetLastError();
 }

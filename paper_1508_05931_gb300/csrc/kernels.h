@@ -51,16 +51,15 @@ cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2*
                            cudaStream_t st);
 cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
                                const uint2* groups, u32* scratch, int grid, cudaStream_t st);
-// The bucket sort with the second round (K4's scan) run on each sorted
-// group; `recs` are K4's look-back records (one per group, cleared by the
-// bin scan), t_* its staging areas, then launch_group_compact.
-cudaError_t launch_bucket_fused(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
-                                const uint2* groups, u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx,
-                                int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy,
-                                int* up_idx, int grid, cudaStream_t st);
-#ifdef GBH_DEBUG_CHECKS
-cudaError_t launch_check_regions(const Plan* plan, const int2* lo_xy, const int2* up_xy, cudaStream_t st);
-#endif
+// The pipeline's bucket sort with the second round: every group's
+// direction aggregate into its record of `recs` (one per group, cleared by
+// the bin scan), their exclusive prefixes (one block), then the sort of
+// every group with the second round run on it (kept points into the t_*
+// staging areas; then launch_group_compact).
+cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
+                                 u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
+                                 int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
+                                 int agg_grid, cudaStream_t st);
 cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_lo_xy, const int* t_lo_idx,
                                  const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,
                                  int2* up_xy, int* up_idx, int grid, cudaStream_t st);
