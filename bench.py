@@ -33,10 +33,12 @@ WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk
 # The paper's best 20M-point times for the same two workloads (Table 3 square
 # 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
 PAPER_MPTS = 40.0 / 0.8645
-# Kernels per hull_compute: extremes, filter count + write, 8 radix passes,
-# region scan + compact, finalisation (the clearing of the region look-back
-# words is a memset, not one of these kernels).
-LAUNCHES_PER_HULL = 1 + 2 + 8 + 2 + 1
+# Kernels per hull_compute with the bucket sort: extremes, filter count, bin
+# scan, scatter into coarse bins, split into bins, group prefixes, sort (+
+# second round), compaction, finalisation.  A call rerun on the radix passes adds extremes,
+# filter count + write, 8 radix passes, region scan + compact, finalisation.
+LAUNCHES_PER_HULL = 9
+LAUNCHES_PER_RADIX_RERUN = 1 + 2 + 8 + 2 + 1
 
 
 def parse():
@@ -197,20 +199,65 @@ def bench_batched(hull, torch, stream, plain_value, args):
                       "families square/disk/gaussian(2^26), seed 4; one call per step, autotuned"}
 
 
-def k3_traffic():
-    """DRAM bytes (read + write) of one radix pass from the committed ncu
-    capture, or None when the kernel source changed since it was taken."""
+def kernel_traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed
+    ncu capture (profiles/<kernel>_traffic.json), scaled to `units` (the
+    survivors or points of the bench's launch, from the same record), or
+    None when there is no capture or a source file it covers changed since."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "k3_onesweep_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")) as f:
             rec = json.load(f)
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-    except (OSError, ValueError, KeyError):
-        return None
-    if sha != rec.get("source_sha256"):
+        for src, want in rec["sources"].items():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+    except (OSError, ValueError, KeyError, AttributeError):
         return None
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+# Kernel(s) behind each profile stage of the bucket-sort path, and the
+# algorithmic bytes each moves per hull: n points, s first-round survivors,
+# r second-round survivors (8 B per point, 12 B per (key, index) pair).
+STAGE_KERNELS = {
+    "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n),
+    "filter": ("k2_count + k_binscan", lambda n, s, r: 8.0 * n),
+    "scatter": ("k2_scatter", lambda n, s, r: 8.0 * n + 12.0 * s),
+    "split": ("k3_split + k_group_prefix", lambda n, s, r: 24.0 * s),
+    "sort": ("k3_bucket", lambda n, s, r: 12.0 * s + 12.0 * r),
+    "regions": ("k4_compact", lambda n, s, r: 24.0 * r),
+    "final": ("k5_final", lambda n, s, r: 12.0 * r),
+}
+
+
+def roofline_of(prof, hbm, peak_src):
+    """Achieved algorithmic bandwidth of every stage (CUDA events on the
+    launch stream, recorded by the library between kernels) and the
+    roofline entry of the dominant one (the longest stage)."""
+    calls = max(prof["calls"], 1)
+    n, s, r = prof["points"] / calls, prof["survivors"] / calls, prof["second_round"] / calls
+    stage_ms = {k: v / calls for k, v in prof["ms"].items() if not k.startswith("-")}
+    if prof["radix_calls"]:
+        return {"bound": "hbm", "kernel": "mixed (calls rerun on the radix passes)", "achieved": None,
+                "peak": hbm, "unit": "GB/s", "frac": None, "peak_source": peak_src, "traffic": None,
+                "stage_ms_per_hull": stage_ms}
+    kernels = {}
+    for name, (kern, nbytes) in STAGE_KERNELS.items():
+        ms = stage_ms.get(name, 0.0)
+        b = nbytes(n, s, r)
+        kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b,
+                         "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else None}
+    dom = max(("scatter", "sort", "filter", "extremes", "split"), key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    achieved = d["gbs"] or 0.0
+    return {"bound": "hbm", "kernel": d["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": peak_src,
+            "traffic": kernel_traffic(d["kernel"].split()[0]),
+            "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
+            "stage_ms_per_hull": stage_ms, "stages": kernels,
+            "pipeline_gbs": sum(k["algorithmic_bytes"] for k in kernels.values())
+            / (sum(stage_ms.values()) / 1e3) / 1e9 if sum(stage_ms.values()) > 0 else None}
 
 
 def _time_hulls(ctx, t, out, stream, torch, k):
@@ -406,25 +453,9 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    # Dominant kernel: the radix pass.  Algorithmic bytes per launch = the
-    # survivors' keys and indices read once and written once (24 B each).
+    roofline = roofline_of(prof, hbm, peak_src)
     calls = max(prof["calls"], 1)
-    sort_ms = sum(prof["ms"]["sort_pass%d" % i] for i in range(8))
-    passes = max(prof["sort_passes"], 1)
     surv = prof["survivors"]
-    # total bytes of all active pass launches (every hull here needs the same pass count)
-    sort_bytes = 24.0 * surv * (passes / calls)
-    achieved = sort_bytes / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else 0.0
-    stage_ms = {k: v / calls for k, v in prof["ms"].items()}
-    roofline = {"bound": "hbm", "kernel": "k3_onesweep (radix pass)", "achieved": achieved,
-                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                "traffic": k3_traffic(),
-                "algorithmic_bytes_per_launch": 24.0 * surv / calls,
-                "stage_ms_per_hull": stage_ms,
-                "k1_gbs": (8.0 * prof["points"] / calls) / (stage_ms["extremes"] / 1e3) / 1e9
-                if stage_ms["extremes"] > 0 else None,
-                "k2_gbs": ((8.0 * prof["points"] + 12.0 * surv) / calls) / (stage_ms["filter"] / 1e3) / 1e9
-                if stage_ms["filter"] > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -434,7 +465,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "survivors_per_hull": surv / calls,
                        "second_round_per_hull": prof["second_round"] / calls},
-            "gpu_launches": args.steps * len(sets) * LAUNCHES_PER_HULL,
+            "gpu_launches": prof["calls"] * LAUNCHES_PER_HULL + prof["radix_calls"] * LAUNCHES_PER_RADIX_RERUN,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
                     "d2h_bytes_per_step": 4 * sum(h_counts), "api": "hull_compute_host_multi"},
             "roofline": roofline}

@@ -178,14 +178,18 @@ hull_status hull_last_stats(const hull_ctx *ctx, hull_stats *out);
 #define HULL_NUM_STAGES 12
 typedef struct {
   int64_t calls;                 /* hull_compute calls accumulated */
+  int64_t radix_calls;           /* of those, calls sorted by the radix passes (the rerun of a
+                                    call whose bins the bucket sort could not take) */
   int64_t sort_passes;           /* radix passes that did work, summed over calls */
   int64_t points;                /* input points, summed */
   int64_t survivors;             /* first-round survivors, summed */
   int64_t second_round;          /* second-round survivors, summed */
-  double ms[HULL_NUM_STAGES];    /* extremes, filter, sort pass 0..7, regions, final; with
-                                    the bucket sort (the default) "filter" includes the scatter
-                                    of the survivors into bins, "sort pass 0" is the sort of the
-                                    bins and passes 1..7 are empty */
+  double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): extremes,
+                                    filter (first round counted, bins scanned), scatter (survivors
+                                    into coarse bins), split (coarse bins into bins, their aggregates,
+                                    the groups' prefixes), sort (groups sorted, second round),
+                                    5 empty slots, regions (compaction), final; on the radix
+                                    passes: extremes, filter, radix pass 0..7, regions, final */
 } hull_profile;
 
 hull_status hull_set_profiling(hull_ctx *ctx, int enable);
@@ -254,6 +258,11 @@ hull_status hull_stage_sort(hull_ctx *ctx, uint64_t *d_keys, uint32_t *d_vals, i
  * m < 2^30. */
 hull_status hull_stage_bucket_sort(hull_ctx *ctx, uint64_t *d_keys, uint32_t *d_vals, int64_t m,
                                    int32_t *h_fallback, void *stream);
+
+/* The largest number of pairs the bucket sort orders in one block's shared
+ * memory: a bin above it is split once more by its next key bits, and a
+ * piece of it still above it sends the call to the radix passes. */
+int64_t hull_bucket_group_cap(void);
 
 /* Section 2.1 steps 5-7 / Figure 2: the second-round filter over m points
  * already sorted by (x, y, index): d_xy (device int32[m][2]) in that order

@@ -48,6 +48,8 @@ struct Workspace {
   u32* bstart = nullptr;       // first position of every bin
   uint2* groups = nullptr;     // (first position, first bin) per group, closing record
   u32* bscratch = nullptr;     // per-block scratch of the large-bin split
+  u64* bagg = nullptr;         // per bin: direction aggregates (lower, upper)
+  u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   unsigned long long* key_or = nullptr;
 };
 
@@ -88,7 +90,7 @@ struct hull_ctx {
   hull_config cfg{};
   int num_sms = 0;
   int occ_k2c = 1, occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
-  int occ_k2b = 1, occ_kb = 1;  // bucket sort: K2 with bin rows, group sort
+  int occ_k2b = 1, occ_kb = 1, occ_sp = 1;  // bucket sort: K2 with bin rows, group sort, split
   Plan* plan = nullptr;        // device
   Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
   Workspace ws;
@@ -164,8 +166,10 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_part = take(parts * sizeof(ExtPartial));
-  const size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8);
-  const size_t o_i0 = take(cap * 4), o_i1 = take(cap * 4);
+  // Key and index arrays have 64 bytes to spare past their end: the bucket
+  // sort's bulk copies round their sizes up to 16 bytes.
+  const size_t o_k0 = take(cap * 8 + 64), o_k1 = take(cap * 8 + 64);
+  const size_t o_i0 = take(cap * 4 + 64), o_i1 = take(cap * 4 + 64);
   const size_t o_sf = take(t2 * 8), o_ss = take(t3 * kRadix * 8);
   // Look-back records of K4's chunks, or of the bucket sort's groups (at most one per bin).
   const size_t o_sr = take(std::max(t4, (size_t)kBins + 2) * k4_status_bytes());
@@ -184,6 +188,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_groups = take(((size_t)kBins + 2) * 8);
   const size_t o_bscr = take(bucket_scratch_words(c->num_sms * c->occ_kb) * 4);
   const size_t o_kor = take(8);
+  const size_t o_bagg = take((size_t)kBins * 16);
+  const size_t o_fcur = take((size_t)kBins * 4);
   const size_t total = off;
 
   cudaDeviceSynchronize();
@@ -222,6 +228,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.groups = reinterpret_cast<uint2*>(b + o_groups);
   w.bscratch = reinterpret_cast<u32*>(b + o_bscr);
   w.key_or = reinterpret_cast<unsigned long long*>(b + o_kor);
+  w.bagg = reinterpret_cast<u64*>(b + o_bagg);
+  w.fcur = reinterpret_cast<u32*>(b + o_fcur);
   return HULL_OK;
 }
 
@@ -255,6 +263,7 @@ hull_status finish(hull_ctx* c, cudaStream_t st, bool* fallback = nullptr) {
     }
     cudaGetLastError();
     f.calls += 1;
+    f.radix_calls += p.sorted_in_b && p.ngroups ? 0 : 1;
     f.sort_passes += p.npasses;
     f.points += p.n;
     f.survivors += p.s;
@@ -301,16 +310,27 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // Survivors scattered into bins, every group's direction aggregate and
     // their prefixes, then one block per group of bins sorts it in shared
     // memory and runs the second round on it from its prefix.
+    // Profile slots: 1 filter (count + bin scan), 2 scatter (coarse bins),
+    // 3 split (fine bins, their aggregates, group prefixes), 4 sort (+ second
+    // round), 5..9 empty, 10 compaction.
     const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
-    e = launch_k2_bins(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, w.rows, w.bstart, w.groups,
-                       w.st_region, g2, st);
+    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bstart, w.groups, w.st_region, w.bagg, w.fcur,
+                       g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
-    e = launch_bucket_decide(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.groups, w.bscratch,
-                             w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
-                             w.up_xy, w.up_idx, c->occ_kb * c->num_sms, c->num_sms * 8, st);
+    e = launch_k2_bins_scatter(d_xy, c->plan, w.keys[0], w.idx[0], w.mask, w.rows, w.bstart, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    for (int p = 0; p < kMaxPasses; ++p) mark(c, 3 + p, st);
+    mark(c, 3, st);
+    e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.bagg,
+                     c->occ_sp * c->num_sms, st);
+    if (e == cudaSuccess) e = launch_group_prefix(c->plan, w.groups, w.st_region, w.bagg, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    mark(c, 4, st);
+    e = launch_bucket_decide(w.keys[1], w.idx[1], w.keys[0], w.idx[0], c->plan, w.groups, w.bscratch,
+                             w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
+                             w.up_xy, w.up_idx, c->occ_kb * c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int p = 5; p <= 2 + kMaxPasses; ++p) mark(c, p, st);
     e = launch_group_compact(c->plan, w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy,
                              w.lo_idx, w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, kBins), st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -485,13 +505,14 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   c->num_sms = prop.multiProcessorCount;
   if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess || bucket_configure() != cudaSuccess ||
       k2_bins_occupancy(&c->occ_k2b) != cudaSuccess || bucket_occupancy(&c->occ_kb) != cudaSuccess ||
+      split_occupancy(&c->occ_sp) != cudaSuccess ||
       k5_configure(&c->occ_k5) != cudaSuccess ||
       k2_occupancy(&c->occ_k2c, &c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
       k4_occupancy(&c->occ_k4) != cudaSuccess) {
     delete c;
     return cuda_fail(cudaErrorUnknown);
   }
-  if (c->occ_k5 < 1 || c->occ_k2b < 1 || c->occ_kb < 1) { delete c; return HULL_ECUDA; }
+  if (c->occ_k5 < 1 || c->occ_k2b < 1 || c->occ_kb < 1 || c->occ_sp < 1) { delete c; return HULL_ECUDA; }
   if (batch_configure(&c->occ_b256, &c->occ_b512) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->bev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -787,6 +808,8 @@ hull_status hull_stage_sort(hull_ctx* c, uint64_t* d_keys, uint32_t* d_vals, int
   if (e != cudaSuccess) return cuda_fail(e);
   return finish(c, st);
 }
+
+int64_t hull_bucket_group_cap(void) { return kGroupCap; }
 
 hull_status hull_stage_bucket_sort(hull_ctx* c, uint64_t* d_keys, uint32_t* d_vals, int64_t m,
                                    int32_t* h_fallback, void* stream) {

@@ -42,6 +42,11 @@ constexpr int kBins = 1 << kBinBits;
 constexpr int kGroupCap = GBH_GROUP_CAP;     // survivors sorted in shared memory at once
 constexpr int kGroupTarget = kGroupCap / 2;  // window of the group rule (see k3_bucket.cu)
 constexpr int kSubBits = GBH_SUB_BITS;
+// The first round scatters into kCoarse coarse bins (the top kCoarseBits of
+// a bin); k3_split then spreads every coarse bin over its fine bins.
+constexpr int kCoarseBits = 8;
+constexpr int kCoarse = 1 << kCoarseBits;
+constexpr int kFinePerCoarse = kBins / kCoarse;
 constexpr int kSubBins = 1 << kSubBits;
 
 // Error bits accumulated in Plan::error by the kernels.
@@ -68,6 +73,7 @@ enum CounterSlot : int {
   CTR_FINAL_BAR_GEN = 4 + kMaxPasses,
   CTR_BIN_SCAN = 5 + kMaxPasses,          // last-block counter of the bin scan
   CTR_BIN_GROUP = 6 + kMaxPasses,         // next group of the bucket sort
+  CTR_SPLIT = 7 + kMaxPasses,             // next tile of the coarse-to-fine split
   kNumCounters = 16,
 };
 

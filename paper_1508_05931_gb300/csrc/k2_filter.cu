@@ -339,20 +339,21 @@ k2_write(const int* __restrict__ xy, Plan* plan, const u32* __restrict__ offsets
   }
 }
 
-// The bucket sort's scatter: writes every survivor (marked by k2_count in
-// `mask`) as (key, index) into its bin.  Block i walks the same chunks as
-// block i of k2_count (in the reverse order, so that the part of the input
-// k2_count read last is still in L2), so its first position in bin b is
-// bstart[b] plus its row's prefix rows[i][b] (from k_binscan); positions
-// inside a bin are taken by shared-memory atomics, in no particular order
-// (the bin's sort orders by (key, index)).  No block waits for another.
-// Whole chunks and their mask bytes arrive by bulk copies into a
-// K2_STAGES-deep ring (evict-first: nothing reads the input again); the
-// scattered stores are marked evict-last so that the sectors that several
-// blocks fill piecewise stay in L2 until they are complete.
+// The bucket sort's first scatter: writes every survivor (marked by
+// k2_count in `mask`) as (key, index) into its coarse bin (kCoarse of them,
+// each the union of kFinePerCoarse consecutive bins).  Block i walks the
+// same chunks as block i of k2_count (in the reverse order, so that the part
+// of the input k2_count read last is still in L2); its run in coarse bin c
+// starts at bstart of c's first bin plus the sum over c's bins of its row's
+// prefixes rows[i][b] (from k_binscan), and grows one survivor at a time
+// (positions by shared-memory atomics, in no particular order), so every
+// block has only one partly written sector per coarse bin at a time and L2
+// completes it before it leaves.  No block waits for another.  Whole chunks
+// and their mask bytes arrive by bulk copies into a K2_STAGES-deep ring
+// (evict-first: nothing reads the input again); the stores are marked
+// evict-last.  k3_split then spreads every coarse bin over its bins.
 constexpr u32 K2_MASK_BYTES = K2_BLOCK;                    // one byte per thread and chunk
 constexpr u32 K2_SC_STAGE = K2_CHUNK_BYTES + K2_MASK_BYTES;
-constexpr size_t K2_SC_SMEM = (size_t)K2_STAGES * K2_SC_STAGE + (size_t)kBins * sizeof(u32);
 
 __device__ __forceinline__ void k2_sc_stage(const int* xy, const unsigned char* mask, u32 c, unsigned char* ring,
                                             u64* bars, int st, u64 pol) {
@@ -362,25 +363,81 @@ __device__ __forceinline__ void k2_sc_stage(const int* xy, const unsigned char* 
   bulk_load_hint(dst + K2_CHUNK_BYTES, mask + (size_t)c * K2_BLOCK, K2_MASK_BYTES, &bars[st], pol);
 }
 
-// Scatters this thread's kept points of chunk c (keep bits `bits`, points
-// px/py in the thread's pair order).
-__device__ __forceinline__ void k2_scatter_points(Plan* plan, u32 c, u32 bits, const int* px, const int* py,
-                                                  int x0, int y0, u32 ybits, u32 fshift, u32 s, u32* s_cur,
-                                                  u64* keys_out, u32* idx_out, u64 pol) {
+// Shared memory of k2_scatter after the ring: the chunk's survivors in
+// coarse-bin order, and per coarse bin the block's cursor, the chunk's
+// count, first staging slot and first global position.
+struct K2ScatterSmem {
+  u64 key[K2_CHUNK];
+  u32 idx[K2_CHUNK];
+  u32 cur[kCoarse];
+  u32 cnt[kCoarse];
+  u32 lst[kCoarse];
+  u32 gb[kCoarse];
+  u32 wsum[K2_WARPS];
+};
+constexpr size_t K2_SC_SMEM = (size_t)K2_STAGES * K2_SC_STAGE + sizeof(K2ScatterSmem);
+static_assert(kCoarse == K2_BLOCK, "one thread per coarse bin");
+
+// Scatters the kept points of chunk c (this thread's keep bits `bits` and
+// points px/py in its pair order; every thread of the block calls it):
+// ranks within the chunk per coarse bin, one reservation per coarse bin on
+// the block's cursor, the chunk staged in coarse-bin order, then written
+// with consecutive threads on consecutive positions.
+__device__ __forceinline__ void k2_scatter_chunk(Plan* plan, u32 c, u32 bits, const int* px, const int* py, int x0,
+                                                 int y0, u32 ybits, u32 cshift, u32 s, K2ScatterSmem& S,
+                                                 u64* keys_out, u32* idx_out, u64 pol) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 base = c * (u32)K2_CHUNK;
+  u64 key[2 * K2_PAIRS];
+  u32 rk[2 * K2_PAIRS];
   #pragma unroll
   for (int e = 0; e < 2 * K2_PAIRS; ++e) {
-    if (!((bits >> e) & 1u)) continue;
-    const u32 i = base + 2u * ((e >> 1) * K2_BLOCK + threadIdx.x) + (u32)(e & 1);
-    const u64 key = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
-    const u32 pos = atomicAdd(&s_cur[(u32)(key >> fshift)], 1u);
+    key[e] = ((u64)(u32)(px[e] - x0) << ybits) | (u64)(u32)(py[e] - y0);
+    rk[e] = ((bits >> e) & 1u) ? atomicAdd(&S.cnt[(u32)(key[e] >> cshift)], 1u) : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  {
+    const u32 cb = threadIdx.x;                      // this thread's coarse bin
+    const u32 n = S.cnt[cb];
+    u32 inc = n;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) S.wsum[wid] = inc;
+    __syncthreads();
+    u32 off = inc - n;
+    for (int w = 0; w < wid; ++w) off += S.wsum[w];
+    S.lst[cb] = off;
+    S.gb[cb] = S.cur[cb];
+    S.cur[cb] += n;
+  }
+  __syncthreads();
+  u32 total = 0;
+  for (int w = 0; w < K2_WARPS; ++w) total += S.wsum[w];
+  #pragma unroll
+  for (int e = 0; e < 2 * K2_PAIRS; ++e) {
+    if (rk[e] != 0xFFFFFFFFu) {
+      const u32 p = S.lst[(u32)(key[e] >> cshift)] + rk[e];
+      S.key[p] = key[e];
+      S.idx[p] = base + 2u * ((e >> 1) * K2_BLOCK + threadIdx.x) + (u32)(e & 1);
+    }
+  }
+  __syncthreads();
+  for (u32 j = threadIdx.x; j < total; j += K2_BLOCK) {
+    const u64 k = S.key[j];
+    const u32 cb = (u32)(k >> cshift);
+    const u32 pos = S.gb[cb] + (j - S.lst[cb]);
     if (pos < s) {
-      st_hint_u64(keys_out + pos, key, pol);
-      st_hint_u32(idx_out + pos, i, pol);
+      st_hint_u64(keys_out + pos, k, pol);
+      st_hint_u32(idx_out + pos, S.idx[j], pol);
     } else {
       flag_error(plan, ERR_INTERNAL);
     }
   }
+  S.cnt[threadIdx.x] = 0u;          // read by everyone before the barrier above
+  __syncthreads();
 }
 
 template <bool VEC>
@@ -391,19 +448,26 @@ k2_scatter(const int* __restrict__ xy, Plan* plan, const unsigned char* __restri
   extern __shared__ __align__(128) unsigned char k2s_smem[];
   __shared__ __align__(8) u64 s_bars[K2_STAGES];
   unsigned char* ring = k2s_smem;
-  u32* s_cur = reinterpret_cast<u32*>(k2s_smem + (size_t)K2_STAGES * K2_SC_STAGE);
+  K2ScatterSmem& S = *reinterpret_cast<K2ScatterSmem*>(k2s_smem + (size_t)K2_STAGES * K2_SC_STAGE);
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
   const u32 s = plan->s;
   const int x0 = plan->key_x0, y0 = plan->key_y0;
   const u32 ybits = plan->ybits;
-  const u32 fshift = plan->fshift;
+  const u32 cshift = plan->fshift + (u32)(kBinBits - kCoarseBits);
   const u32 nchunks = (n + K2_CHUNK - 1) / K2_CHUNK;
   const u32 G = gridDim.x, b0 = blockIdx.x;
   const u64 pol_in = policy_evict_first();
   const u64 pol_out = policy_evict_last();
-  for (u32 q = threadIdx.x; q < (u32)kBins; q += K2_BLOCK)
-    s_cur[q] = bstart[q] + rows[(size_t)b0 * kBins + q];
+  {
+    const u32 cb = threadIdx.x;
+    const u32* row = rows + (size_t)b0 * kBins + (size_t)cb * kFinePerCoarse;
+    u32 sum = bstart[cb * kFinePerCoarse];
+    #pragma unroll 8
+    for (int f = 0; f < kFinePerCoarse; ++f) sum += row[f];
+    S.cur[cb] = sum;
+    S.cnt[cb] = 0u;
+  }
   // This block's chunks are b0 + k * G.  The whole ones (c < nring) go
   // through the ring, last first; the rest are read directly.
   const u32 nring = VEC ? n / K2_CHUNK : 0u;
@@ -430,9 +494,8 @@ k2_scatter(const int* __restrict__ xy, Plan* plan, const unsigned char* __restri
       const int4 v = pts[r * K2_BLOCK + threadIdx.x];
       px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
     }
-    k2_scatter_points(plan, ring_chunk(q), bits, px, py, x0, y0, ybits, fshift, s, s_cur, keys_out, idx_out,
-                      pol_out);
-    __syncthreads();   // every thread has read stage st: refill it
+    // Every thread has read stage st (the chunk's first barrier follows).
+    k2_scatter_chunk(plan, ring_chunk(q), bits, px, py, x0, y0, ybits, cshift, s, S, keys_out, idx_out, pol_out);
     if (threadIdx.x == 0 && q + K2_STAGES < kw)
       k2_sc_stage(xy, mask, ring_chunk(q + K2_STAGES), ring, s_bars, st, pol_in);
   }
@@ -449,7 +512,7 @@ k2_scatter(const int* __restrict__ xy, Plan* plan, const unsigned char* __restri
       if ((bits >> (2 * r + 1)) & 1u) b = *reinterpret_cast<const int2*>(xy + 2 * (size_t)i0 + 2);
       px[2 * r] = a.x; py[2 * r] = a.y; px[2 * r + 1] = b.x; py[2 * r + 1] = b.y;
     }
-    k2_scatter_points(plan, c, bits, px, py, x0, y0, ybits, fshift, s, s_cur, keys_out, idx_out, pol_out);
+    k2_scatter_chunk(plan, c, bits, px, py, x0, y0, ybits, cshift, s, S, keys_out, idx_out, pol_out);
   }
 }
 
@@ -511,18 +574,24 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
   return cudaGetLastError();
 }
 
-// First round for the bucket sort: k2_count with per-block bin rows, the
-// bin scan (k3_bucket.cu), then the scatter into bins, all with `grid`
-// blocks (the scatter walks the count's chunks; `rows` has grid rows).
-cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
-                           unsigned char* mask, u32* rows, u32* bstart, uint2* groups, void* recs, int grid,
-                           cudaStream_t st) {
+// First round for the bucket sort: k2_count with per-block bin rows, then
+// the bin scan (k3_bucket.cu); launch_k2_bins_scatter then writes the
+// survivors into their bins with the same `grid` (the scatter walks the
+// count's chunks; `rows` has grid rows).
+cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bstart,
+                           uint2* groups, void* recs, u64* bagg, u32* fcur, int grid, cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
   if (vec) k2_count<true, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
   else k2_count<false, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
-  cudaError_t e = launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, st);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, bagg, fcur, st);
+}
+
+cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,
+                                   const u32* rows, const u32* bstart, int grid, cudaStream_t st) {
+  const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   if (vec) k2_scatter<true><<<grid, K2_BLOCK, K2_SC_SMEM, st>>>(xy, plan, mask, rows, bstart, keys_out, idx_out);
   else k2_scatter<false><<<grid, K2_BLOCK, K2_SC_SMEM, st>>>(xy, plan, mask, rows, bstart, keys_out, idx_out);
   return cudaGetLastError();

@@ -43,7 +43,7 @@ namespace {
 #define GBH_KB_BLOCK 512
 #endif
 constexpr int KB_BLOCK = GBH_KB_BLOCK;
-constexpr int KB_MIN_BLOCKS = 1024 / KB_BLOCK;      // resident blocks per SM the registers allow
+constexpr int KB_MIN_BLOCKS = 2;                    // two blocks per SM (the shared-memory arrays)
 constexpr int KB_WARPS = KB_BLOCK / 32;
 constexpr int KB_ITEMS = kGroupCap / KB_BLOCK;     // keys per thread in a full group
 constexpr u32 kCrowded = 32;                       // largest sub-bin ordered by insertion
@@ -60,6 +60,8 @@ struct BucketSmem {
   u32 misc[4];
   // second round
   Dir2 dirs[KB_WARPS];     // per-warp direction aggregates
+  Dir2 wex[KB_WARPS];      // and their exclusive prefixes (from the group's prefix)
+  Dir2 wtot;               // prefix through the whole piece
   Dir2 carry;              // prefix through the group's positions scanned so far
   u32 kwl[KB_WARPS][2];    // per-warp kept counts (lower, upper)
   u32 kept[2];             // the group's kept points so far
@@ -229,29 +231,61 @@ struct Fused {
 // running extreme of its region, stages the kept points from slot
 // `slot0 + S.kept[region]` and advances S.carry and S.kept.  Thread t
 // takes positions [t R, t R + R).
+//
+// One pass per thread keeps loc = the extreme of S.carry and its positions
+// so far, and marks the positions strictly beyond loc (candidates; loc
+// then becomes theirs).  A position that is not a candidate lies within
+// loc, hence within the true running extreme, and is dropped.  Because the
+// true running extreme before position p is the thread's exclusive prefix
+// E combined with its earlier positions, and S.carry lies within E, it
+// equals E combined with loc at p, i.e. with the previous candidate's
+// direction: the second pass only visits the candidates.  The scan across
+// threads combines the loc values (S.carry is idempotent under the
+// combination, so that is E).
 __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 s, const RG& rg, Plan* plan) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 R = (m + KB_BLOCK - 1) / KB_BLOCK;
   const u32 p0 = min(m, threadIdx.x * R), p1 = min(m, p0 + R);
-  Dir2 agg = rg.ident;
-  for (u32 p = p0; p < p1; ++p) add_dir(agg, rg, S.key[phys(p)]);
-  const Dir2 inc = warp_scan_dir(agg);
-  const Dir2 lex = shfl_up_dir(inc, 1);
-  if (lane == 31) S.dirs[wid] = inc;
-  __syncthreads();
-  Dir2 run = S.carry;
-  for (int w = 0; w < wid; ++w) combine(run, S.dirs[w]);
-  if (lane > 0) combine(run, lex);
-  u32 keep_lo = 0, keep_up = 0;           // bit j: position p0 + j kept
+  const Dir2 carry = S.carry;
+  Dir2 loc = carry;
+  u32 cand = 0;                                   // bit j: position p0 + j is a candidate
   for (u32 p = p0; p < p1; ++p) {
     int px, py;
     const int sd = decode_side(rg, S.key[phys(p)], px, py);
     const int vx = px - rg.bx, vy = py - rg.by;
-    const u32 bit = 1u << (p - p0);
     if (sd < 0) {
-      if (cross2(run.lx, run.ly, vx, vy) > 0) { keep_lo |= bit; run.lx = vx; run.ly = vy; }
+      if (cross2(loc.lx, loc.ly, vx, vy) > 0) { cand |= 1u << (p - p0); loc.lx = vx; loc.ly = vy; }
     } else if (sd > 0) {
-      if (cross2(run.ux, run.uy, vx, vy) < 0) { keep_up |= bit; run.ux = vx; run.uy = vy; }
+      if (cross2(loc.ux, loc.uy, vx, vy) < 0) { cand |= 1u << (p - p0); loc.ux = vx; loc.uy = vy; }
+    }
+  }
+  // Exclusive prefix of this thread: warp scan, then the warps' totals.
+  const Dir2 inc = warp_scan_dir(loc);
+  const Dir2 lex = shfl_up_dir(inc, 1);
+  if (lane == 31) S.dirs[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    Dir2 w = lane < KB_WARPS ? S.dirs[lane] : carry;
+    const Dir2 wi = warp_scan_dir(w);
+    const Dir2 we = shfl_up_dir(wi, 1);
+    if (lane < KB_WARPS) S.wex[lane] = lane > 0 ? we : carry;
+    if (lane == KB_WARPS - 1) S.wtot = wi;
+  }
+  __syncthreads();
+  Dir2 ex = S.wex[wid];
+  if (lane > 0) combine(ex, lex);
+  // Second pass: the candidates only.
+  u32 keep_lo = 0, keep_up = 0;
+  Dir2 prev = ex;                                 // E combined with the last candidate of each region
+  for (u32 c = cand; c; c &= c - 1) {
+    const u32 j = __ffs(c) - 1;
+    int px, py;
+    const int sd = decode_side(rg, S.key[phys(p0 + j)], px, py);
+    const int vx = px - rg.bx, vy = py - rg.by;
+    if (sd < 0) {
+      if (cross2(prev.lx, prev.ly, vx, vy) > 0) { keep_lo |= 1u << j; prev.lx = vx; prev.ly = vy; }
+    } else {
+      if (cross2(prev.ux, prev.uy, vx, vy) < 0) { keep_up |= 1u << j; prev.ux = vx; prev.uy = vy; }
     }
   }
   const u32 c_lo = __popc(keep_lo), c_up = __popc(keep_up);
@@ -271,13 +305,12 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
   }
   u32 pl = slot0 + S.kept[0] + wl + i_lo - c_lo;
   u32 pu = slot0 + S.kept[1] + wu + i_up - c_up;
-  for (u32 p = p0; p < p1; ++p) {
-    const u32 bit = 1u << (p - p0);
-    if (!((keep_lo | keep_up) & bit)) continue;
+  for (u32 c = keep_lo | keep_up; c; c &= c - 1) {
+    const u32 j = __ffs(c) - 1;
     int px, py;
-    decode_side(rg, S.key[phys(p)], px, py);
-    const int idx = (int)S.val[phys(p)];
-    if (keep_lo & bit) {
+    decode_side(rg, S.key[phys(p0 + j)], px, py);
+    const int idx = (int)S.val[phys(p0 + j)];
+    if (keep_lo & (1u << j)) {
       if (pl < s) { F.t_lo_xy[pl] = make_int2(px, py); F.t_lo_idx[pl] = idx; } else flag_error(plan, ERR_INTERNAL);
       ++pl;
     } else {
@@ -285,17 +318,15 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
       ++pu;
     }
   }
-  // The piece's total prefix (the last thread's running value covers every
-  // position) and kept counts, for the next piece of the same group.
+  // The piece's prefix for the next piece of the same group, and the kept counts.
   __syncthreads();
-  if (threadIdx.x == KB_BLOCK - 1) {
-    S.carry = run;
+  if (threadIdx.x == 0) {
+    S.carry = S.wtot;
     S.kept[0] += tl;
     S.kept[1] += tu;
   }
   __syncthreads();
 }
-
 
 // Starts group g's second round from its exclusive prefix (one thread).
 __device__ __forceinline__ void start_group(BucketSmem& S, const Fused& F, u32 g) {
@@ -516,39 +547,213 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   region_offsets(plan, F.recs, ng, s, &S.kwl[0][0], F.lo_xy, F.lo_idx, F.up_xy, F.up_idx);
 }
 
-// Direction aggregate of every group of bins (its points in any order):
-// one block per group at a time, keys read once, coalesced.
-constexpr int GA_BLOCK = 256;
-__global__ void __launch_bounds__(GA_BLOCK)
-k_group_agg(const u64* __restrict__ keys, Plan* plan, const uint2* __restrict__ groups, K4Chunk* __restrict__ recs) {
-  __shared__ Dir2 s_w[GA_BLOCK / 32];
+// Keeps in *addr the extreme of its direction and (dx, dy): the
+// counter-clockwise-most for sgn > 0 (lower region), the clockwise-most for
+// sgn < 0 (upper).  A compare-and-swap loop (a word without its valid bit
+// holds nothing yet); every failed swap means another thread stored a
+// strictly more extreme direction, so the loop ends; it is bounded all the
+// same (ERR_TIMEOUT).
+__device__ __forceinline__ void cas_max_dir(u64* addr, int dx, int dy, int sgn, Plan* plan) {
+  const u64 cand = pack_dir(dx, dy);
+  u64 old = ld_relaxed_u64(addr);
+  for (u32 it = 0; it < 4096u; ++it) {
+    if (old & kDirValid) {
+      int ox, oy;
+      unpack_dir(old, ox, oy);
+      const long long c = cross2(ox, oy, dx, dy);
+      if (sgn > 0 ? c <= 0 : c >= 0) return;
+    }
+    const u64 prev = atomicCAS(reinterpret_cast<unsigned long long*>(addr), old, cand);
+    if (prev == old) return;
+    old = prev;
+  }
+  flag_error(plan, ERR_TIMEOUT);
+}
+
+// The second scatter of the bucket sort: spreads every coarse bin of
+// (ak, av) over its kFinePerCoarse bins in (bk, bv).  Work comes in tiles
+// of SP_TILE consecutive pairs of one coarse bin (a tile counter; any
+// order).  A tile is ordered by bin in shared memory (counting), each of
+// its bins reserves its run with one atomic on that bin's cursor (fcur,
+// starting at the bin's first position), and the runs are written with
+// consecutive threads on consecutive addresses.  With the tile ordered by
+// bin, one warp per bin also folds the tile's points into the bin's
+// direction aggregates (bagg: lower and upper word per bin) for the second
+// round's prefixes.
+constexpr int SP_BLOCK = 512;
+constexpr int SP_ITEMS = 8;
+constexpr int SP_TILE = SP_BLOCK * SP_ITEMS;
+constexpr int SP_WARPS = SP_BLOCK / 32;
+static_assert(kFinePerCoarse == 32, "one lane per bin of a coarse bin");
+static_assert(kCoarse <= SP_BLOCK, "one thread per coarse bin");
+static_assert(SP_TILE <= 8192, "tile rank packed in 13 bits");
+constexpr size_t SP_SMEM = (size_t)SP_TILE * (sizeof(u64) + sizeof(u32));
+
+__global__ void __launch_bounds__(SP_BLOCK, 2)
+k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict__ bk, u32* __restrict__ bv,
+         Plan* plan, const u32* __restrict__ bstart, u32* __restrict__ fcur, u64* __restrict__ bagg) {
+  extern __shared__ __align__(16) unsigned char sp_smem[];   // SP_TILE keys, then SP_TILE indices
+  u64* s_key = reinterpret_cast<u64*>(sp_smem);
+  u32* s_idx = reinterpret_cast<u32*>(sp_smem + SP_TILE * sizeof(u64));
+  __shared__ u32 s_tiles[kCoarse + 1];
+  __shared__ u32 s_cnt[kFinePerCoarse], s_lst[kFinePerCoarse + 1], s_gb[kFinePerCoarse];
+  __shared__ u32 s_w[SP_WARPS];
+  __shared__ u32 s_t, s_c;
   if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
-  const u32 ng = plan->ngroups;
+  const u32 s = plan->s, fshift = plan->fshift;
   const RG rg = make_rg(plan);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (u32 g = blockIdx.x; g < ng; g += gridDim.x) {
-    const u32 a = groups[g].x, b = groups[g + 1].x;
-    Dir2 v = rg.ident;
-    for (u32 i = a + threadIdx.x; i < b; i += GA_BLOCK) add_dir(v, rg, keys[i]);
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
-    if (lane == 0) s_w[wid] = v;
+  // Tiles per coarse bin and their exclusive prefix.
+  u32 nt = 0;
+  if (threadIdx.x < kCoarse) {
+    const u32 c = threadIdx.x;
+    const u32 cs = bstart[c * kFinePerCoarse];
+    const u32 ce = c + 1 < (u32)kCoarse ? bstart[(c + 1) * kFinePerCoarse] : s;
+    nt = (ce - cs + SP_TILE - 1) / SP_TILE;
+  }
+  u32 inc = nt;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  u32 off = 0, tot = 0;
+  for (int w = 0; w < SP_WARPS; ++w) {
+    if (w < wid) off += s_w[w];
+    tot += s_w[w];
+  }
+  if (threadIdx.x < kCoarse) s_tiles[threadIdx.x] = off + inc - nt;
+  if (threadIdx.x == 0) s_tiles[kCoarse] = tot;
+  for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      Dir2 t = rg.ident;
-      for (int w = 0; w < GA_BLOCK / 32; ++w) combine(t, s_w[w]);
-      recs[g].agg_lo = pack_dir(t.lx, t.ly);
-      recs[g].agg_up = pack_dir(t.ux, t.uy);
+      const u32 t = atomicAdd(&plan->ctr[CTR_SPLIT], 1u);
+      s_t = t;
+      if (t < tot) {
+        u32 lo = 0, hi = kCoarse - 1;       // largest c with s_tiles[c] <= t
+        while (lo < hi) {
+          const u32 mid = (lo + hi + 1) >> 1;
+          if (s_tiles[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        s_c = lo;
+      }
+    }
+    if (threadIdx.x < kFinePerCoarse) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const u32 t = s_t;
+    if (t >= tot) break;
+    const u32 c = s_c;
+    const u32 cs = bstart[c * kFinePerCoarse];
+    const u32 ce = c + 1 < (u32)kCoarse ? bstart[(c + 1) * kFinePerCoarse] : s;
+    const u32 start = cs + (t - s_tiles[c]) * (u32)SP_TILE;
+    const u32 n = start < ce ? min((u32)SP_TILE, ce - start) : 0u;
+    u64 key[SP_ITEMS];
+    u32 idx[SP_ITEMS], pk[SP_ITEMS];
+    #pragma unroll
+    for (int it = 0; it < SP_ITEMS; ++it) {
+      const u32 i = it * SP_BLOCK + threadIdx.x;
+      pk[it] = 0xFFFFFFFFu;
+      key[it] = 0ull;
+      idx[it] = 0u;
+      if (i < n) {
+        key[it] = ak[start + i];
+        idx[it] = av[start + i];
+        const u32 f = (u32)(key[it] >> fshift);
+        if ((f >> (kBinBits - kCoarseBits)) == c) {
+          const u32 d = f & (kFinePerCoarse - 1);
+          pk[it] = (d << 13) | atomicAdd(&s_cnt[d], 1u);
+        } else {
+          flag_error(plan, ERR_INTERNAL);
+        }
+      }
     }
     __syncthreads();
+    if (wid == 0) {
+      const u32 cn = s_cnt[lane];
+      u32 x = cn;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      s_lst[lane] = x - cn;
+      if (lane == 31) s_lst[kFinePerCoarse] = x;
+      s_gb[lane] = cn ? atomicAdd(&fcur[c * kFinePerCoarse + lane], cn) : 0u;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int it = 0; it < SP_ITEMS; ++it) {
+      if (pk[it] != 0xFFFFFFFFu) {
+        const u32 p = s_lst[pk[it] >> 13] + (pk[it] & 8191u);
+        s_key[p] = key[it];
+        s_idx[p] = idx[it];
+      }
+    }
+    __syncthreads();
+    const u32 placed = s_lst[kFinePerCoarse];
+    for (u32 j = threadIdx.x; j < placed; j += SP_BLOCK) {
+      const u64 k = s_key[j];
+      const u32 d = (u32)(k >> fshift) & (kFinePerCoarse - 1);
+      const u32 pos = s_gb[d] + (j - s_lst[d]);
+      if (pos < s) {
+        bk[pos] = k;
+        bv[pos] = s_idx[j];
+      } else {
+        flag_error(plan, ERR_INTERNAL);
+      }
+    }
+    // One warp per bin: the tile's contribution to the bin's aggregates
+    // (lanes 0 and 1 update the two words at once).
+    for (u32 d = wid; d < (u32)kFinePerCoarse; d += SP_WARPS) {
+      const u32 a = s_lst[d], b = s_lst[d + 1];
+      if (a == b) continue;
+      Dir2 v = rg.ident;
+      for (u32 j = a + lane; j < b; j += 32) add_dir(v, rg, s_key[j]);
+      #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
+      u64* w = bagg + 2 * (size_t)(c * kFinePerCoarse + d);
+      if (lane == 0 && (v.lx != rg.ident.lx || v.ly != rg.ident.ly)) cas_max_dir(w, v.lx, v.ly, 1, plan);
+      if (lane == 1 && (v.ux != rg.ident.ux || v.uy != rg.ident.uy)) cas_max_dir(w + 1, v.ux, v.uy, -1, plan);
+    }
   }
 }
 
-// Exclusive prefixes of the groups' direction aggregates (one block):
-// record g's inclusive words receive the combination of the aggregates of
-// groups 0 .. g - 1 with d(P_0) (the identity).  Thread t takes a
-// contiguous slice of groups.
+// Exclusive prefixes of the groups' direction aggregates: a group's
+// aggregate is the combination of its bins' aggregates (bagg, from
+// k3_split; k_group_agg_bins), then one block gives record g's inclusive
+// words the combination of the aggregates of groups 0 .. g - 1 with d(P_0)
+// (the identity).  Thread t takes a contiguous slice of groups.
 constexpr int GP_BLOCK = 1024;
+
+// One warp per group: its bins' aggregates combined into its record.
+constexpr int GB_BLOCK = 256;
+__global__ void __launch_bounds__(GB_BLOCK)
+k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
+                 const u64* __restrict__ bagg) {
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
+  const u32 ng = plan->ngroups;
+  const RG rg = make_rg(plan);
+  const int lane = threadIdx.x & 31;
+  const u32 g = blockIdx.x * (GB_BLOCK / 32) + (threadIdx.x >> 5);
+  if (g >= ng) return;
+  Dir2 t = rg.ident;
+  for (u32 b = groups[g].y + lane; b < groups[g + 1].y; b += 32) {
+    const u64 wl = bagg[2 * (size_t)b], wu = bagg[2 * (size_t)b + 1];
+    Dir2 v = rg.ident;
+    if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
+    if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
+    combine(t, v);
+  }
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
+  if (lane == 0) {
+    recs[g].agg_lo = pack_dir(t.lx, t.ly);
+    recs[g].agg_up = pack_dir(t.ux, t.uy);
+  }
+}
+
 __global__ void __launch_bounds__(GP_BLOCK)
 k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
   __shared__ Dir2 s_w[GP_BLOCK / 32];
@@ -558,11 +763,13 @@ k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 per = (ng + GP_BLOCK - 1) / GP_BLOCK;
   const u32 g0 = min(ng, threadIdx.x * per), g1 = min(ng, g0 + per);
+  Dir2 agg[4];
   Dir2 t = rg.ident;
   for (u32 g = g0; g < g1; ++g) {
     Dir2 v;
     unpack_dir(recs[g].agg_lo, v.lx, v.ly);
     unpack_dir(recs[g].agg_up, v.ux, v.uy);
+    if (g - g0 < 4) agg[g - g0] = v;
     combine(t, v);
   }
   const Dir2 inc = warp_scan_dir(t);
@@ -576,8 +783,12 @@ k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
     recs[g].inc_lo = pack_dir(run.lx, run.ly);
     recs[g].inc_up = pack_dir(run.ux, run.uy);
     Dir2 v;
-    unpack_dir(recs[g].agg_lo, v.lx, v.ly);
-    unpack_dir(recs[g].agg_up, v.ux, v.uy);
+    if (g - g0 < 4) {
+      v = agg[g - g0];
+    } else {
+      unpack_dir(recs[g].agg_lo, v.lx, v.ly);
+      unpack_dir(recs[g].agg_up, v.ux, v.uy);
+    }
     combine(run, v);
   }
 }
@@ -595,7 +806,8 @@ static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole 
 
 __global__ void __launch_bounds__(BS_BLOCK)
 k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
-          uint2* __restrict__ groups, K4Chunk* __restrict__ recs) {
+          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u64* __restrict__ bagg,
+          u32* __restrict__ fcur) {
   __shared__ u32 s_part[BS_WARPS][BS_BINS];
   __shared__ u32 s_w[BS_WARPS];
   __shared__ u32 s_last_st[BS_BLOCK], s_last_cn[BS_BLOCK];
@@ -608,6 +820,9 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   if (recs)
     for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
       reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
+  // and the bins' direction aggregates (two words per bin).
+  if (bagg)
+    for (u32 q = threadIdx.x; q < BS_BINS * 2u; q += BS_BLOCK) bagg[(size_t)blockIdx.x * BS_BINS * 2 + q] = 0ull;
   const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
   const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
   u32 sum = 0;
@@ -683,6 +898,7 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   for (int j = 0; j < BS_PER; ++j) {
     const u32 b = threadIdx.x * BS_PER + j;
     bstart[b] = st[j];
+    if (fcur) fcur[b] = st[j];
     if (flags & (1u << j)) groups[g++] = make_uint2(st[j], b);
   }
   if (threadIdx.x == BS_BLOCK - 1) {
@@ -780,6 +996,8 @@ cudaError_t bucket_configure() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k3_bucket<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BucketSmem));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k3_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k3_array_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kBins * 4);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k3_array_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kBins * 4);
@@ -795,10 +1013,10 @@ cudaError_t bucket_occupancy(int* blocks) {
   return e;
 }
 
-cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
-                           cudaStream_t st) {
+cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs, u64* bagg,
+                           u32* fcur, cudaStream_t st) {
   k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, nrows, plan, bstart, groups,
-                                                  reinterpret_cast<K4Chunk*>(recs));
+                                                  reinterpret_cast<K4Chunk*>(recs), bagg, fcur);
   return cudaGetLastError();
 }
 
@@ -809,14 +1027,28 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
   return cudaGetLastError();
 }
 
+cudaError_t launch_split(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const u32* bstart, u32* fcur,
+                         u64* bagg, int grid, cudaStream_t st) {
+  k3_split<<<grid, SP_BLOCK, SP_SMEM, st>>>(ak, av, bk, bv, plan, bstart, fcur, bagg);
+  return cudaGetLastError();
+}
+
+cudaError_t split_occupancy(int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k3_split, SP_BLOCK, SP_SMEM);
+}
+
+cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* bagg, cudaStream_t st) {
+  K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
+  k_group_agg_bins<<<(kBins + GB_BLOCK / 32 - 1) / (GB_BLOCK / 32), GB_BLOCK, 0, st>>>(plan, R, groups, bagg);
+  k_group_prefix<<<1, GP_BLOCK, 0, st>>>(plan, R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
                                  u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
                                  int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
-                                 int agg_grid, cudaStream_t st) {
-  K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
-  Fused F{R, t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
-  k_group_agg<<<agg_grid, GA_BLOCK, 0, st>>>(ak, plan, groups, R);
-  k_group_prefix<<<1, GP_BLOCK, 0, st>>>(plan, R);
+                                 cudaStream_t st) {
+  Fused F{reinterpret_cast<K4Chunk*>(recs), t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
   k3_bucket<true><<<grid, KB_BLOCK, sizeof(BucketSmem), st>>>(ak, av, bk, bv, plan, groups, scratch, F);
   return cudaGetLastError();
 }
@@ -834,7 +1066,8 @@ cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* pla
   if (e != cudaSuccess) return e;
   k3_array_keyor<<<grid, KA_BLOCK, 0, st>>>(keys, plan, key_or);
   k3_array_hist<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, plan, key_or, rows);
-  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr);
+  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr, nullptr,
+                                                  nullptr);
   k3_array_scatter<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, vals, plan, rows, bstart, ok, ov);
   (void)m;
   return cudaGetLastError();

@@ -40,12 +40,16 @@ class hull_stats(ctypes.Structure):
 
 
 NUM_STAGES = 12
-STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8)] + ["regions", "final"]
+# Stage slots of hull_profile.ms on the bucket-sort path (the default) and on
+# the radix-pass path (a call whose bins the bucket sort could not take).
+STAGE_NAMES = ["extremes", "filter", "scatter", "split", "sort"] + ["-%d" % i for i in range(5, 10)] + [
+    "regions", "final"]
+RADIX_STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8)] + ["regions", "final"]
 
 
 class hull_profile(ctypes.Structure):
-    _fields_ = [("calls", ctypes.c_int64), ("sort_passes", ctypes.c_int64), ("points", ctypes.c_int64),
-                ("survivors", ctypes.c_int64), ("second_round", ctypes.c_int64),
+    _fields_ = [("calls", ctypes.c_int64), ("radix_calls", ctypes.c_int64), ("sort_passes", ctypes.c_int64),
+                ("points", ctypes.c_int64), ("survivors", ctypes.c_int64), ("second_round", ctypes.c_int64),
                 ("ms", ctypes.c_double * NUM_STAGES)]
 
 
@@ -63,6 +67,7 @@ _sig = {
     "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
     "hull_batched_max_instance": ([], ctypes.c_int64),
+    "hull_bucket_group_cap": ([], ctypes.c_int64),
     "hull_mlp_num_params": ([], ctypes.c_int64),
     "hull_mlp_set_params": ([_P, _P, _I64], ctypes.c_int),
     "hull_mlp_get_params": ([_P, _P, _I64], ctypes.c_int),
@@ -261,9 +266,10 @@ class Context:
     def profile(self) -> dict:
         p = hull_profile()
         _check(_lib.hull_get_profile(self._h, ctypes.byref(p)), "hull_get_profile")
-        return {"calls": p.calls, "sort_passes": p.sort_passes, "points": p.points,
+        names = STAGE_NAMES if p.radix_calls == 0 else RADIX_STAGE_NAMES
+        return {"calls": p.calls, "radix_calls": p.radix_calls, "sort_passes": p.sort_passes, "points": p.points,
                 "survivors": p.survivors, "second_round": p.second_round,
-                "ms": {STAGE_NAMES[k]: p.ms[k] for k in range(NUM_STAGES)}}
+                "ms": {names[k]: p.ms[k] for k in range(NUM_STAGES)}}
 
     # ------------------------------------------------------------ learned
     def mlp_set_params(self, params):
@@ -423,6 +429,7 @@ hull_compute_batched = _lib.hull_compute_batched
 hull_compute_noalloc = _lib.hull_compute_noalloc
 hull_last_stats = _lib.hull_last_stats
 hull_batched_max_instance = _lib.hull_batched_max_instance
+hull_bucket_group_cap = _lib.hull_bucket_group_cap
 hull_mlp_train_step = _lib.hull_mlp_train_step
 hull_mlp_gradient = _lib.hull_mlp_gradient
 hull_mlp_forward = _lib.hull_mlp_forward

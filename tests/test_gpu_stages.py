@@ -100,7 +100,7 @@ def test_sort_parity(ctx, m, kind):
 def _bucket_keys(rng, m, kind):
     if kind == "random":            # full 64-bit keys: many small bins, insertion path
         return rng.integers(0, 2 ** 63, size=m, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=m).astype(np.uint64)
-    if kind == "equal":             # one bin: bitonic path up to 8192 keys, then the radix passes
+    if kind == "equal":             # one bin: bitonic path up to the group cap, then the radix passes
         return np.full(m, 12345, dtype=np.uint64)
     if kind == "lowbits":           # 16 distinct keys: crowded sub-bins
         return rng.integers(0, 16, size=m).astype(np.uint64)
@@ -122,7 +122,7 @@ def _bucket_keys(rng, m, kind):
 
 @pytest.mark.parametrize("m", [1, 2, 100, 4097, 8192, 8193, 100003, 1000001])
 @pytest.mark.parametrize("kind", ["random", "equal", "lowbits", "dups", "bigbin", "lattice"])
-def test_bucket_sort_parity(ctx, m, kind):
+def test_bucket_sort_parity(ctx, hull_lib, m, kind):
     """The pipeline's bucket sort orders (key, value) pairs by key, then
     value; with values ascending in input order (as the first round's
     survivor indices are) that is the stable sort by key."""
@@ -135,9 +135,11 @@ def test_bucket_sort_parity(ctx, m, kind):
     order = np.argsort(keys, kind="stable")
     assert np.array_equal(kt.cpu().numpy().view(np.uint64), keys[order])
     assert np.array_equal(vt.cpu().numpy(), vals[order])
-    # Only a bin of more than 8192 keys that its next 12 key bits cannot
-    # split (equal keys here) hands the pairs to the radix passes.
-    expect_fb = (kind == "equal" and m > 8192) or (kind == "lowbits" and m > 16 * 8192)
+    # Only a bin of more keys than one block sorts in shared memory that its
+    # next key bits cannot split (equal keys here) hands the pairs to the
+    # radix passes.
+    cap = hull_lib.hull_bucket_group_cap()
+    expect_fb = (kind == "equal" and m > cap) or (kind == "lowbits" and m > 16 * cap)
     assert fell_back == expect_fb
 
 
