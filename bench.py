@@ -199,11 +199,11 @@ def bench_batched(hull, torch, stream, plain_value, args):
                       "families square/disk/gaussian(2^26), seed 4; one call per step, autotuned"}
 
 
-def kernel_traffic(kernel):
+def kernel_traffic(kernel, units):
     """DRAM bytes (read + write) per launch of `kernel` from the committed
-    ncu capture (profiles/<kernel>_traffic.json), scaled to `units` (the
-    survivors or points of the bench's launch, from the same record), or
-    None when there is no capture or a source file it covers changed since."""
+    ncu capture (profiles/<kernel>_traffic.json), scaled from the units
+    (survivors) of the captured launch to `units`, or None when there is no
+    capture or a source file it covers changed since."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")) as f:
@@ -212,9 +212,9 @@ def kernel_traffic(kernel):
             with open(os.path.join(ROOT, src), "rb") as f:
                 if hashlib.sha256(f.read()).hexdigest() != want:
                     return None
-    except (OSError, ValueError, KeyError, AttributeError):
+        return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * units / rec["units"]
+    except (OSError, ValueError, KeyError, AttributeError, TypeError, ZeroDivisionError):
         return None
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
 # Kernel(s) behind each profile stage of the bucket-sort path, and the
@@ -253,7 +253,7 @@ def roofline_of(prof, hbm, peak_src):
     achieved = d["gbs"] or 0.0
     return {"bound": "hbm", "kernel": d["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": kernel_traffic(d["kernel"].split()[0]),
+            "traffic": kernel_traffic(d["kernel"].split()[0], s),
             "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
             "stage_ms_per_hull": stage_ms, "stages": kernels,
             "pipeline_gbs": sum(k["algorithmic_bytes"] for k in kernels.values())
