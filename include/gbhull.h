@@ -274,6 +274,20 @@ hull_status hull_stage_second_round(hull_ctx *ctx, const int32_t *d_xy, const in
                                     int64_t m, int32_t *d_lower, int64_t *h_lower,
                                     int32_t *d_upper, int64_t *h_upper, void *stream);
 
+/* The front of hull_compute on n points (d_xy device int32[n][2]):
+ * extremes, quadrilateral filter, sort and the second-round filter
+ * (Section 2.1 steps 1-7, Figure 2), fused as in hull_compute.  Writes the
+ * labels (input indices) of the points the second round keeps in the lower
+ * region to d_lower (device int32[lower_cap]) and in the upper region to
+ * d_upper (device int32[upper_cap]), each in sorted (x, y, index) order
+ * without P_0 and P_l; h_counts (host int64[2]) receives both counts and
+ * *h_fallback (if not NULL) whether the call was rerun on the radix passes.
+ * HULL_ECAPACITY when a list does not fit (counts still set, buffers
+ * untouched).  Synchronises `stream`. */
+hull_status hull_stage_regions(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_lower,
+                               int64_t lower_cap, int32_t *d_upper, int64_t upper_cap,
+                               int64_t *h_counts, int32_t *h_fallback, void *stream);
+
 /* Section 2.1 step 8: stack-based chains over m >= 2 distinct points in
  * lexicographic order (d_xy device int32[m][2]).  d_out (device int32[cap])
  * receives the lower chain's positions (first to last point, left turns)

@@ -623,6 +623,44 @@ hull_status hull_compute(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d
   return r;
 }
 
+hull_status hull_stage_regions(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_lower,
+                               int64_t lower_cap, int32_t* d_upper, int64_t upper_cap, int64_t* h_counts,
+                               int32_t* h_fallback, void* stream) {
+  if (!c || !h_counts || n < 0 || lower_cap < 0 || upper_cap < 0 || n > (int64_t)kMaxN) return HULL_EINVAL;
+  if (n > 0 && (!d_xy || !aligned8(d_xy))) return HULL_EINVAL;
+  if ((lower_cap > 0 && !d_lower) || (upper_cap > 0 && !d_upper)) return HULL_EINVAL;
+  h_counts[0] = h_counts[1] = 0;
+  if (h_fallback) *h_fallback = 0;
+  if (n == 0) return HULL_OK;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool bucket = attempt == 0;
+    c->prof_pending = false;
+    r = run_front(c, d_xy, (u32)n, st, bucket);
+    if (r != HULL_OK) return r;
+    bool fallback = false;
+    r = finish(c, st, bucket ? &fallback : nullptr);
+    if (fallback) continue;
+    if (r != HULL_OK) return r;
+    if (h_fallback) *h_fallback = attempt;
+    const int64_t rl = c->h_plan->r_lo, ru = c->h_plan->r_up;
+    h_counts[0] = rl;
+    h_counts[1] = ru;
+    if (rl > lower_cap || ru > upper_cap) return HULL_ECAPACITY;
+    cudaError_t e = cudaSuccess;
+    if (rl > 0) e = cudaMemcpyAsync(d_lower, c->ws.lo_idx + 1, (size_t)rl * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && ru > 0)
+      e = cudaMemcpyAsync(d_upper, c->ws.up_idx + 1, (size_t)ru * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+  }
+  return r;
+}
+
 hull_status hull_compute_host(hull_ctx* c, const int32_t* h_xy, int64_t n, int32_t* h_out,
                               int64_t cap, int64_t* h_count, void* stream) {
   if (!c || !h_count || n < 0 || cap < 0 || n > (int64_t)kMaxN) return HULL_EINVAL;

@@ -46,7 +46,10 @@ constexpr int KB_BLOCK = GBH_KB_BLOCK;
 constexpr int KB_MIN_BLOCKS = 2;                    // two blocks per SM (the shared-memory arrays)
 constexpr int KB_WARPS = KB_BLOCK / 32;
 constexpr int KB_ITEMS = kGroupCap / KB_BLOCK;     // keys per thread in a full group
-constexpr u32 kCrowded = 32;                       // largest sub-bin ordered by insertion
+constexpr int KB_HALF = KB_ITEMS / 2;              // keys loaded per batch
+static_assert(KB_HALF * 2 == KB_ITEMS, "two load batches");
+constexpr u32 kCrowded = 32;                       // largest sub-bin ordered by rank counting
+constexpr u32 kBinnedMax = 32;                     // most pairs a thread scans unsorted (one mask bit each)
 constexpr int KB_SCAN_PER = (kSubBins) / KB_BLOCK; // sub-bin counters per thread in the scan
 static_assert(KB_SCAN_PER * KB_BLOCK == kSubBins, "whole counters per thread");
 static_assert(kGroupCap <= (1 << 13) && kSubBits <= 19, "rank and sub-bin packed in 32 bits");
@@ -57,10 +60,9 @@ struct BucketSmem {
   u32 val[kGroupCap];
   u32 cnt[kSubBins + 1];
   u32 wsum[KB_WARPS];
-  u32 misc[4];
+  u32 misc[8];             // [0] big-bin piece end, [1] claimed group, [2..4] sub-bin map
   // second round
-  Dir2 dirs[KB_WARPS];     // per-warp direction aggregates
-  Dir2 wex[KB_WARPS];      // and their exclusive prefixes (from the group's prefix)
+  Dir2 dirs[KB_WARPS];     // per-warp direction aggregates (each includes the piece's prefix)
   Dir2 wtot;               // prefix through the whole piece
   Dir2 carry;              // prefix through the group's positions scanned so far
   u32 kwl[KB_WARPS][2];    // per-warp kept counts (lower, upper)
@@ -89,9 +91,26 @@ __device__ __forceinline__ bool pair_less(u64 ka, u32 va, u64 kb, u32 vb) {
   return ka < kb || (ka == kb && va < vb);
 }
 
+// Sum of the values of warps [0, wid): every lane passes warp `lane`'s
+// value (lanes >= KB_WARPS pass anything); a scan across the lanes.
+__device__ __forceinline__ u32 warps_before(u32 x, int wid) {
+  const int lane = threadIdx.x & 31;
+  if (lane >= KB_WARPS) x = 0u;
+  #pragma unroll
+  for (int o = 1; o < KB_WARPS; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += t;
+  }
+  const u32 b = __shfl_sync(0xFFFFFFFFu, x, wid > 0 ? wid - 1 : 0);
+  return wid > 0 ? b : 0u;
+}
+
 // Exclusive scan of S.cnt[0..kSubBins) in place, S.cnt[kSubBins] = total.
-// Returns (on every thread) whether some counter exceeded kCrowded.
-__device__ __forceinline__ bool scan_counts(BucketSmem& S) {
+// Returns (on every thread) kCrowdedFlag when some counter exceeds kCrowded
+// and kHeavyFlag when the KB_SCAN_PER counters of some thread sum to more
+// than kBinnedMax (a crowded sub-bin makes its thread heavy too).
+constexpr int kCrowdedFlag = 1, kHeavyFlag = 2;
+__device__ __forceinline__ int scan_counts(BucketSmem& S) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
   u32 v[KB_SCAN_PER];
@@ -109,9 +128,10 @@ __device__ __forceinline__ bool scan_counts(BucketSmem& S) {
     if (lane >= o) inc += t;
   }
   if (lane == 31) S.wsum[wid] = inc;
-  const bool crowded = __syncthreads_or(mx > kCrowded) != 0;
-  u32 run = inc - sum;
-  for (int w = 0; w < wid; ++w) run += S.wsum[w];
+  const int flags = (mx > kCrowded ? kCrowdedFlag : 0) | (sum > kBinnedMax ? kHeavyFlag : 0);
+  int st = __syncthreads_or(flags) != 0 ? kHeavyFlag : 0;
+  if (st) st |= __syncthreads_or(flags & kCrowdedFlag) != 0 ? kCrowdedFlag : 0;
+  u32 run = inc - sum + warps_before(S.wsum[lane < KB_WARPS ? lane : 0], wid);
   #pragma unroll
   for (int j = 0; j < KB_SCAN_PER; ++j) {
     S.cnt[threadIdx.x * KB_SCAN_PER + j] = run;
@@ -119,24 +139,7 @@ __device__ __forceinline__ bool scan_counts(BucketSmem& S) {
   }
   if (threadIdx.x == KB_BLOCK - 1) S.cnt[kSubBins] = run;
   __syncthreads();
-  return crowded;
-}
-
-// Orders S.key/S.val[a, b) by (key, value): straight insertion (b - a is
-// at most kCrowded).
-__device__ __forceinline__ void insertion(BucketSmem& S, u32 a, u32 b) {
-  for (u32 j = a + 1; j < b; ++j) {
-    const u64 k = S.key[phys(j)];
-    const u32 v = S.val[phys(j)];
-    u32 i = j;
-    while (i > a && pair_less(k, v, S.key[phys(i - 1)], S.val[phys(i - 1)])) {
-      S.key[phys(i)] = S.key[phys(i - 1)];
-      S.val[phys(i)] = S.val[phys(i - 1)];
-      --i;
-    }
-    S.key[phys(i)] = k;
-    S.val[phys(i)] = v;
-  }
+  return st;
 }
 
 // Bitonic network over S.key/S.val[0, m), padded to a power of two with
@@ -177,6 +180,36 @@ template <bool RO, typename T>
 __device__ __forceinline__ T load_src(const T* p) {
   if (RO) return __ldg(p);
   return *p;
+}
+
+// Sub-bin of a key offset in [0, top]: the offset cut or widened to
+// exactly 32 significant bits (x), then the high word of x * M, where
+// M is at most kSubBins 2^32 / (largest x + 1).  Monotone in the offset, it
+// spreads the whole range evenly over the kSubBins sub-bins (a shift by a
+// power of two would leave up to half of them empty and crowd the rest).
+struct SubMap {
+  u32 esh, lsh, M;
+};
+
+__device__ __forceinline__ SubMap make_submap(u64 top) {
+  SubMap f;
+  const u32 kb = top ? 64u - (u32)__clzll((long long)top) : 0u;
+  f.esh = kb > 32u ? kb - 32u : 0u;
+  f.lsh = (kb > 0u && kb < 32u) ? 32u - kb : 0u;
+  // M <= kSubBins 2^32 / (xmax + 1) from the top 12 bits of xmax (which is
+  // in [2^31, 2^32) when kb > 0): y 2^20 > xmax, within 1/2048 of it.
+  const u32 y = (u32)(((top >> f.esh) << f.lsh) >> 20) + 1u;
+  f.M = kb ? ((u32)kSubBins << 12) / y : 0u;
+  return f;
+}
+
+// Largest offset of nb >= 1 consecutive units of 2^sh keys (2^64 - 1 at most).
+__device__ __forceinline__ u64 span_top(u32 nb, u32 sh) {
+  return ((u64)(nb - 1u) << sh) + ((1ull << sh) - 1ull);
+}
+
+__device__ __forceinline__ u32 sub_of(const SubMap& f, u64 off) {
+  return __umulhi((u32)(off >> f.esh) << f.lsh, f.M);
 }
 
 // ---- the second round, fused (Section 2.2, Figure 2): geometry of the
@@ -226,37 +259,87 @@ struct Fused {
   int2* lo_xy; int* lo_idx; int2* up_xy; int* up_idx;
 };
 
-// Figure 2 over the m sorted pairs in shared memory, starting from the
-// prefix S.carry: keeps a point when its direction is strictly beyond the
-// running extreme of its region, stages the kept points from slot
-// `slot0 + S.kept[region]` and advances S.carry and S.kept.  Thread t
-// takes positions [t R, t R + R).
+// Next position to visit among the bits of `mask` (bit j: position p0 + j),
+// in (key, value) order.  Sorted pairs: the lowest bit.  Binned pairs (a
+// thread's positions are whole sub-bins, in sub-bin order, each in any
+// order inside): the smallest (key, value) among the bits that share the
+// lowest bit's sub-bin.
+__device__ __forceinline__ u32 next_visit(const BucketSmem& S, u32 mask, u32 p0, bool binned, const SubMap& f,
+                                          u64 klo) {
+  const u32 j0 = __ffs(mask) - 1;
+  u32 rest = mask & (mask - 1u);
+  if (!binned || !rest) return j0;
+  u64 bk = S.key[phys(p0 + j0)];
+  u32 bv = S.val[phys(p0 + j0)];
+  const u32 e = S.cnt[sub_of(f, bk - klo) + 1] - p0;   // end of that sub-bin, at most 32
+  if (e < 32u) rest &= (1u << e) - 1u;
+  u32 best = j0;
+  for (; rest; rest &= rest - 1u) {
+    const u32 j = __ffs(rest) - 1;
+    const u64 kj = S.key[phys(p0 + j)];
+    const u32 vj = S.val[phys(p0 + j)];
+    if (pair_less(kj, vj, bk, bv)) { best = j; bk = kj; bv = vj; }
+  }
+  return best;
+}
+
+// Figure 2 over the m pairs in shared memory, starting from the prefix
+// S.carry: keeps a point when its direction is strictly beyond the running
+// extreme of its region, stages the kept points from slot
+// `slot0 + S.kept[region]` and advances S.carry and S.kept.  Sorted pairs:
+// thread t takes positions [t R, t R + R).  Binned pairs (sorted by
+// sub-bin only; klo and the sub-bin map of sort_into_smem give each key's
+// sub-bin): thread t takes its KB_SCAN_PER sub-bins, whole.
 //
 // One pass per thread keeps loc = the extreme of S.carry and its positions
-// so far, and marks the positions strictly beyond loc (candidates; loc
-// then becomes theirs).  A position that is not a candidate lies within
-// loc, hence within the true running extreme, and is dropped.  Because the
-// true running extreme before position p is the thread's exclusive prefix
-// E combined with its earlier positions, and S.carry lies within E, it
-// equals E combined with loc at p, i.e. with the previous candidate's
-// direction: the second pass only visits the candidates.  The scan across
-// threads combines the loc values (S.carry is idempotent under the
-// combination, so that is E).
-__device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 s, const RG& rg, Plan* plan) {
+// so far, and marks as candidates the positions strictly beyond lsb, the
+// extreme through the sub-bins before the position's own (sorted pairs:
+// every position is a sub-bin, lsb = loc).  A position that is not a
+// candidate lies within lsb, i.e. within the directions of points before
+// it in the true order, and is dropped whatever the order inside its
+// sub-bin.  So the true running extreme before a position is the thread's
+// exclusive prefix E combined with the candidates before it, and the
+// second pass visits the candidates only, each sub-bin's in (key, value)
+// order.  The scan across threads combines the loc values (S.carry is
+// idempotent under the combination, so that is E).
+__device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 s, const RG& rg, Plan* plan,
+                           bool binned, u64 klo) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 R = (m + KB_BLOCK - 1) / KB_BLOCK;
-  const u32 p0 = min(m, threadIdx.x * R), p1 = min(m, p0 + R);
+  const SubMap f = {S.misc[2], S.misc[3], S.misc[4]};
+  u32 p0, p1;
+  if (binned) {
+    p0 = S.cnt[threadIdx.x * KB_SCAN_PER];
+    p1 = S.cnt[threadIdx.x * KB_SCAN_PER + KB_SCAN_PER];
+  } else {
+    const u32 R = (m + KB_BLOCK - 1) / KB_BLOCK;
+    p0 = min(m, threadIdx.x * R);
+    p1 = min(m, p0 + R);
+  }
   const Dir2 carry = S.carry;
-  Dir2 loc = carry;
+  Dir2 loc = carry, lsb = carry;
   u32 cand = 0;                                   // bit j: position p0 + j is a candidate
+  u32 dprev = 0xFFFFFFFFu;
   for (u32 p = p0; p < p1; ++p) {
+    const u64 k = S.key[phys(p)];
+    if (binned) {
+      const u32 d = sub_of(f, k - klo);
+      if (d != dprev) { lsb = loc; dprev = d; }
+    } else {
+      lsb = loc;
+    }
     int px, py;
-    const int sd = decode_side(rg, S.key[phys(p)], px, py);
+    const int sd = decode_side(rg, k, px, py);
     const int vx = px - rg.bx, vy = py - rg.by;
     if (sd < 0) {
-      if (cross2(loc.lx, loc.ly, vx, vy) > 0) { cand |= 1u << (p - p0); loc.lx = vx; loc.ly = vy; }
+      if (cross2(lsb.lx, lsb.ly, vx, vy) > 0) {
+        cand |= 1u << (p - p0);
+        if (cross2(loc.lx, loc.ly, vx, vy) > 0) { loc.lx = vx; loc.ly = vy; }
+      }
     } else if (sd > 0) {
-      if (cross2(loc.ux, loc.uy, vx, vy) < 0) { cand |= 1u << (p - p0); loc.ux = vx; loc.uy = vy; }
+      if (cross2(lsb.ux, lsb.uy, vx, vy) < 0) {
+        cand |= 1u << (p - p0);
+        if (cross2(loc.ux, loc.uy, vx, vy) < 0) { loc.ux = vx; loc.uy = vy; }
+      }
     }
   }
   // Exclusive prefix of this thread: warp scan, then the warps' totals.
@@ -264,21 +347,19 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
   const Dir2 lex = shfl_up_dir(inc, 1);
   if (lane == 31) S.dirs[wid] = inc;
   __syncthreads();
-  if (wid == 0) {
-    Dir2 w = lane < KB_WARPS ? S.dirs[lane] : carry;
-    const Dir2 wi = warp_scan_dir(w);
-    const Dir2 we = shfl_up_dir(wi, 1);
-    if (lane < KB_WARPS) S.wex[lane] = lane > 0 ? we : carry;
-    if (lane == KB_WARPS - 1) S.wtot = wi;
-  }
-  __syncthreads();
-  Dir2 ex = S.wex[wid];
+  // Every warp scans the warps' aggregates itself (each includes S.carry,
+  // which the combination absorbs, so lanes past the warps may pass it).
+  const Dir2 wi = warp_scan_dir<KB_WARPS>(lane < KB_WARPS ? S.dirs[lane] : carry);
+  Dir2 ex = shfl_dir(wi, wid > 0 ? wid - 1 : 0);
+  if (wid == 0) ex = carry;
+  if (wid == 0 && lane == KB_WARPS - 1) S.wtot = wi;
   if (lane > 0) combine(ex, lex);
-  // Second pass: the candidates only.
+  // Second pass: the candidates only, in (key, value) order.
   u32 keep_lo = 0, keep_up = 0;
-  Dir2 prev = ex;                                 // E combined with the last candidate of each region
-  for (u32 c = cand; c; c &= c - 1) {
-    const u32 j = __ffs(c) - 1;
+  Dir2 prev = ex;                                 // E combined with the candidates visited so far
+  for (u32 c = cand; c;) {
+    const u32 j = next_visit(S, c, p0, binned, f, klo);
+    c &= ~(1u << j);
     int px, py;
     const int sd = decode_side(rg, S.key[phys(p0 + j)], px, py);
     const int vx = px - rg.bx, vy = py - rg.by;
@@ -298,15 +379,14 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
   }
   if (lane == 31) { S.kwl[wid][0] = i_lo; S.kwl[wid][1] = i_up; }
   __syncthreads();
-  u32 wl = 0, wu = 0, tl = 0, tu = 0;
-  for (int w = 0; w < KB_WARPS; ++w) {
-    if (w < wid) { wl += S.kwl[w][0]; wu += S.kwl[w][1]; }
-    tl += S.kwl[w][0]; tu += S.kwl[w][1];
-  }
+  const int wl_src = lane < KB_WARPS ? lane : 0;
+  const u32 wl = warps_before(S.kwl[wl_src][0], wid), wu = warps_before(S.kwl[wl_src][1], wid);
+  const u32 tl = warps_before(S.kwl[wl_src][0], KB_WARPS), tu = warps_before(S.kwl[wl_src][1], KB_WARPS);
   u32 pl = slot0 + S.kept[0] + wl + i_lo - c_lo;
   u32 pu = slot0 + S.kept[1] + wu + i_up - c_up;
-  for (u32 c = keep_lo | keep_up; c; c &= c - 1) {
-    const u32 j = __ffs(c) - 1;
+  for (u32 c = keep_lo | keep_up; c;) {
+    const u32 j = next_visit(S, c, p0, binned, f, klo);
+    c &= ~(1u << j);
     int px, py;
     decode_side(rg, S.key[phys(p0 + j)], px, py);
     const int idx = (int)S.val[phys(p0 + j)];
@@ -339,58 +419,141 @@ __device__ __forceinline__ void start_group(BucketSmem& S, const Fused& F, u32 g
 
 
 // Sorts the m <= kGroupCap pairs at [base, base + m) of (sk, sv), whose keys
-// lie in [klo, klo + 2^span), into shared memory (position i in slot
-// phys(i)), ordered by (key, value).  With AGG, also returns on every thread
-// the direction aggregate of the pairs (order-free, from the first load).
-// Every thread of the block calls it.
+// lie in [klo, klo + ktop], into shared memory (position i in slot
+// phys(i)), ordered by (key, value).  Every thread of the block calls it.
+// With allow_binned, when no thread's KB_SCAN_PER sub-bins hold more than
+// kBinnedMax pairs, it stops once the pairs are in sub-bin order and
+// returns true (binned: the pairs of a sub-bin in any order).
 template <bool RO>
-__device__ void sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
-                               u32 span, Plan* plan) {
-  const u32 sh = span > (u32)kSubBits ? span - (u32)kSubBits : 0u;
+__device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
+                               u64 ktop, Plan* plan, bool allow_binned) {
+  if (threadIdx.x == 0) {
+    const SubMap f = make_submap(ktop);
+    S.misc[2] = f.esh; S.misc[3] = f.lsh; S.misc[4] = f.M;
+  }
   for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
   __syncthreads();
+  const SubMap f = {S.misc[2], S.misc[3], S.misc[4]};
+  // Rank: every key's sub-bin and its arrival rank there.  The keys of a
+  // batch are loaded before any of them is counted, so that the loads are
+  // in flight together.
   u32 pk[KB_ITEMS];
   #pragma unroll
-  for (int it = 0; it < KB_ITEMS; ++it) {
-    const u32 i = it * KB_BLOCK + threadIdx.x;
-    pk[it] = 0xFFFFFFFFu;
-    if (i < m) {
-      const u64 k = load_src<RO>(sk + base + i);
-      const u64 d64 = (k - klo) >> sh;
-      if (d64 < (u64)kSubBins) {
-        const u32 d = (u32)d64;
-        pk[it] = (d << 13) | atomicAdd(&S.cnt[d], 1u);
-      } else {
-        flag_error(plan, ERR_INTERNAL);
+  for (int h = 0; h < 2; ++h) {
+    #pragma unroll
+    for (int q = 0; q < KB_HALF; ++q) pk[h * KB_HALF + q] = 0xFFFFFFFFu;
+    if (h > 0 && m <= (u32)(KB_HALF * KB_BLOCK)) continue;
+    u64 kk[KB_HALF];
+    #pragma unroll
+    for (int q = 0; q < KB_HALF; ++q) {
+      const u32 i = (h * KB_HALF + q) * KB_BLOCK + threadIdx.x;
+      kk[q] = i < m ? load_src<RO>(sk + base + i) : 0ull;
+    }
+    #pragma unroll
+    for (int q = 0; q < KB_HALF; ++q) {
+      const u32 i = (h * KB_HALF + q) * KB_BLOCK + threadIdx.x;
+      if (i < m) {
+        const u64 off = kk[q] - klo;
+        if (off <= ktop) {
+          const u32 d = sub_of(f, off);
+          pk[h * KB_HALF + q] = (d << 13) | atomicAdd(&S.cnt[d], 1u);
+        } else {
+          flag_error(plan, ERR_INTERNAL);
+        }
       }
     }
   }
-  const bool crowded = scan_counts(S);
+  const int st = scan_counts(S);
 #ifdef GBH_DEBUG_CHECKS
   if (S.cnt[kSubBins] != m) {
-    if (threadIdx.x == 0) DBG_REPORT(2, base, m, S.cnt[kSubBins], span);
+    if (threadIdx.x == 0) DBG_REPORT(2, base, m, S.cnt[kSubBins], ktop);
     flag_error(plan, ERR_INTERNAL);
   }
 #endif
+  // Place: the pairs of a batch are loaded together, then stored.
   #pragma unroll
-  for (int it = 0; it < KB_ITEMS; ++it) {
-    const u32 i = it * KB_BLOCK + threadIdx.x;
-    if (i < m && pk[it] != 0xFFFFFFFFu) {
-      const u32 p = phys(S.cnt[pk[it] >> 13] + (pk[it] & 8191u));
-      S.key[p] = load_src<RO>(sk + base + i);
-      S.val[p] = load_src<RO>(sv + base + i);
+  for (int h = 0; h < 2; ++h) {
+    if (h > 0 && m <= (u32)(KB_HALF * KB_BLOCK)) continue;
+    u64 kk[KB_HALF];
+    u32 vv[KB_HALF];
+    #pragma unroll
+    for (int q = 0; q < KB_HALF; ++q) {
+      const u32 i = (h * KB_HALF + q) * KB_BLOCK + threadIdx.x;
+      kk[q] = 0ull;
+      vv[q] = 0u;
+      if (i < m) {
+        kk[q] = load_src<RO>(sk + base + i);
+        vv[q] = load_src<RO>(sv + base + i);
+      }
+    }
+    #pragma unroll
+    for (int q = 0; q < KB_HALF; ++q) {
+      const u32 t = pk[h * KB_HALF + q];
+      if (t != 0xFFFFFFFFu) {
+        const u32 p = phys(S.cnt[t >> 13] + (t & 8191u));
+        S.key[p] = kk[q];
+        S.val[p] = vv[q];
+      }
     }
   }
   __syncthreads();
-  if (!crowded) {
-    for (u32 d = threadIdx.x; d < (u32)kSubBins; d += KB_BLOCK) {
-      const u32 a = S.cnt[d], b = S.cnt[d + 1];
-      if (b - a > 1u) insertion(S, a, b);
+  if (allow_binned && !(st & kHeavyFlag)) return true;
+  if (!(st & kCrowdedFlag)) {
+    // Order every sub-bin by (key, value): each pair of a sub-bin of two or
+    // more counts the pairs of its sub-bin below it (its rank there); after
+    // a barrier the pairs not yet at their rank move there, reloaded from
+    // the source.
+    #pragma unroll
+    for (int it = 0; it < KB_ITEMS; ++it) {
+      const u32 t = pk[it];
+      u32 np = 0xFFFFFFFFu;
+      if (t != 0xFFFFFFFFu) {
+        const u32 d = t >> 13, rk = t & 8191u;
+        const u32 a = S.cnt[d], c = S.cnt[d + 1] - a;
+        if (c > 1u) {
+          const u32 ps = phys(a + rk);
+          const u64 k = S.key[ps];
+          const u32 v = S.val[ps];
+          u32 r = 0;
+          for (u32 j = 0; j < c; ++j) {
+            const u32 q = phys(a + j);
+            r += pair_less(S.key[q], S.val[q], k, v) ? 1u : 0u;
+          }
+          if (r != rk) np = a + r;
+        }
+      }
+      pk[it] = np;
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h > 0 && m <= (u32)(KB_HALF * KB_BLOCK)) continue;
+      u64 kk[KB_HALF];
+      u32 vv[KB_HALF];
+      #pragma unroll
+      for (int q = 0; q < KB_HALF; ++q) {
+        const u32 i = (h * KB_HALF + q) * KB_BLOCK + threadIdx.x;
+        kk[q] = 0ull;
+        vv[q] = 0u;
+        if (pk[h * KB_HALF + q] != 0xFFFFFFFFu) {
+          kk[q] = load_src<RO>(sk + base + i);
+          vv[q] = load_src<RO>(sv + base + i);
+        }
+      }
+      #pragma unroll
+      for (int q = 0; q < KB_HALF; ++q) {
+        const u32 f = pk[h * KB_HALF + q];
+        if (f != 0xFFFFFFFFu) {
+          S.key[phys(f)] = kk[q];
+          S.val[phys(f)] = vv[q];
+        }
+      }
     }
   } else {
     bitonic(S, m);
   }
   __syncthreads();
+  return false;
 }
 
 __device__ __forceinline__ void write_out(BucketSmem& S, u64* dk, u32* dv, u32 base, u32 m) {
@@ -475,8 +638,9 @@ __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __
       return;
     }
     if (pm > 0) {
-      sort_into_smem<false>(S, bk, bv, base + ps, pm, klo + ((u64)d0 << sh), sh + ceil_log2(d1 - d0), plan);
-      if (DECIDE) scan_piece(S, F, pm, base, plan->s, rg, plan);
+      const u64 plo = klo + ((u64)d0 << sh);
+      const bool binned = sort_into_smem<false>(S, bk, bv, base + ps, pm, plo, span_top(d1 - d0, sh), plan, DECIDE);
+      if (DECIDE) scan_piece(S, F, pm, base, plan->s, rg, plan, binned, plo);
       else write_out(S, bk, bv, base + ps, pm);
     }
     d0 = d1;
@@ -502,11 +666,18 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   const u32 s = plan->s;
   const RG rg = make_rg(plan);
   u32* my_scratch = scratch + (size_t)blockIdx.x * kScratchWords;
+  // Thread 0 claims each group one iteration ahead, so that the claim's
+  // round trip overlaps the current group.
+  u32 g_next = 0;
+  if (threadIdx.x == 0) g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
   for (;;) {
     if (threadIdx.x == 0) {
-      const u32 g = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
-      S.misc[1] = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : g;
-      if (DECIDE && g < ng) start_group(S, F, g);
+      const u32 g = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : min(g_next, ng);
+      S.misc[1] = g;
+      if (g < ng) {
+        g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
+        if (DECIDE) start_group(S, F, g);
+      }
     }
     __syncthreads();
     const u32 g = S.misc[1];
@@ -524,8 +695,8 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
     const u32 span = fshift + ceil_log2(b.y - a.y);
     if (m <= (u32)kGroupCap) {
       if (m > 0) {
-        sort_into_smem<true>(S, ak, av, a.x, m, klo, span, plan);
-        if (DECIDE) scan_piece(S, F, m, a.x, s, rg, plan);
+        const bool binned = sort_into_smem<true>(S, ak, av, a.x, m, klo, span_top(b.y - a.y, fshift), plan, DECIDE);
+        if (DECIDE) scan_piece(S, F, m, a.x, s, rg, plan, binned, klo);
         else write_out(S, bk, bv, a.x, m);
       }
     } else {

@@ -57,11 +57,21 @@ __device__ __forceinline__ Dir2 shfl_up_dir(const Dir2& v, int o) {
   r.uy = __shfl_up_sync(0xFFFFFFFFu, v.uy, o);
   return r;
 }
-// Inclusive warp scan under combine (earlier lanes first).
+__device__ __forceinline__ Dir2 shfl_dir(const Dir2& v, int src) {
+  Dir2 r;
+  r.lx = __shfl_sync(0xFFFFFFFFu, v.lx, src);
+  r.ly = __shfl_sync(0xFFFFFFFFu, v.ly, src);
+  r.ux = __shfl_sync(0xFFFFFFFFu, v.ux, src);
+  r.uy = __shfl_sync(0xFFFFFFFFu, v.uy, src);
+  return r;
+}
+// Inclusive warp scan under combine (earlier lanes first); lanes below W
+// see exactly the lanes before them, W a power of two <= 32.
+template <int W = 32>
 __device__ __forceinline__ Dir2 warp_scan_dir(Dir2 v) {
   const int lane = threadIdx.x & 31;
   #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
+  for (int o = 1; o < W; o <<= 1) {
     Dir2 t = shfl_up_dir(v, o);
     if (lane >= o) { combine(t, v); v = t; }
   }

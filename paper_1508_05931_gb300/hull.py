@@ -85,6 +85,8 @@ _sig = {
     "hull_stage_sort": ([_P, _P, _P, _I64, _P], ctypes.c_int),
     "hull_stage_bucket_sort": ([_P, _P, _P, _I64, ctypes.POINTER(ctypes.c_int32), _P], ctypes.c_int),
     "hull_stage_second_round": ([_P, _P, _P, _I64, _P, _PI64, _P, _PI64, _P], ctypes.c_int),
+    "hull_stage_regions": ([_P, _P, _I64, _P, _I64, _P, _I64, _PI64, ctypes.POINTER(ctypes.c_int32), _P],
+                           ctypes.c_int),
     "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
 }
 for _name, (_args, _res) in _sig.items():
@@ -388,6 +390,21 @@ class Context:
                "hull_stage_second_round")
         return lo[: nl.value], up[: nu.value]
 
+    def stage_regions(self, pts, stream=None):
+        """The second-round survivors of the fused pipeline front on `pts`:
+        (lower labels, upper labels, fell back to the radix passes)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(pts, dev)
+        n = xy.shape[0]
+        lo = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        up = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cnt = (ctypes.c_int64 * 2)()
+        fb = ctypes.c_int32()
+        _check(_lib.hull_stage_regions(self._h, _ptr(xy), n, _ptr(lo), lo.numel(), _ptr(up), up.numel(), cnt,
+                                       ctypes.byref(fb), _stream_handle(stream)), "hull_stage_regions")
+        return lo[: cnt[0]], up[: cnt[1]], bool(fb.value)
+
     def stage_chain(self, xy_sorted, stream=None):
         """Returns (lower chain positions, upper chain positions), both from
         the first to the last point."""
@@ -447,4 +464,5 @@ hull_stage_filter = _lib.hull_stage_filter
 hull_stage_sort = _lib.hull_stage_sort
 hull_stage_bucket_sort = _lib.hull_stage_bucket_sort
 hull_stage_second_round = _lib.hull_stage_second_round
+hull_stage_regions = _lib.hull_stage_regions
 hull_stage_chain = _lib.hull_stage_chain

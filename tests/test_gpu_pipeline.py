@@ -82,6 +82,31 @@ def test_small_square_config(ctx):
     assert st["ext"] == stages["ext"].tolist()
 
 
+def _front_points(gen, n):
+    rng = np.random.default_rng(n + len(gen))
+    return {"square": lambda: W.uniform_square(n, 1 << 29, n),
+            "disk": lambda: W.uniform_disk(n, 2.0 ** 29, n),
+            "ring": lambda: W.near_circle(n, 2.0 ** 20, n),
+            "gauss": lambda: W.gaussian(n, 2.0 ** 26, n),
+            "clusters": lambda: W.gaussian_clusters(n, n),
+            "ties": lambda: rng.integers(-60, 61, size=(n, 2)).astype(np.int32),
+            "strip": lambda: np.stack([rng.integers(-3, 4, n), rng.integers(-(1 << 29), 1 << 29, n)],
+                                      axis=1).astype(np.int32)}[gen]()
+
+
+@pytest.mark.parametrize("n", [4097, 65537, 300_001, 1_000_003])
+@pytest.mark.parametrize("gen", ["square", "disk", "ring", "gauss", "clusters", "ties", "strip"])
+def test_fused_second_round_lists(ctx, n, gen):
+    """The second round fused into the sort (Figure 2 run on every sorted
+    or binned group from its prefix) keeps exactly the oracle's points, in
+    the oracle's order, in both regions."""
+    pts = _front_points(gen, n)
+    lo, up, _ = ctx.stage_regions(dev(pts))
+    ref = oracle.gscan_stages(pts)
+    assert np.array_equal(lo.cpu().numpy(), ref["lower"])
+    assert np.array_equal(up.cpu().numpy(), ref["upper"])
+
+
 @pytest.mark.parametrize("name", ["paper_square", "paper_disk", "adversarial_ring"])
 def test_full_size_configs(ctx, name):
     pts = getattr(W, name)()
