@@ -48,7 +48,8 @@ struct Workspace {
   u32* bstart = nullptr;       // first position of every bin
   uint2* groups = nullptr;     // (first position, first bin) per group, closing record
   u32* bscratch = nullptr;     // per-block scratch of the large-bin split
-  u64* bagg = nullptr;         // per bin: direction aggregates (lower, upper)
+  u64* tagg = nullptr;         // per split tile and bin: direction aggregates (lower, upper)
+  u32* ctiles = nullptr;       // first split tile of every coarse bin
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   unsigned long long* key_or = nullptr;
 };
@@ -188,7 +189,9 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_groups = take(((size_t)kBins + 2) * 8);
   const size_t o_bscr = take(bucket_scratch_words(c->num_sms * c->occ_kb) * 4);
   const size_t o_kor = take(8);
-  const size_t o_bagg = take((size_t)kBins * 16);
+  const size_t tiles_cap = cap / (size_t)split_tile() + (size_t)kCoarse + 1;
+  const size_t o_tagg = take(tiles_cap * 2 * kFinePerCoarse * 8);
+  const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
   const size_t o_fcur = take((size_t)kBins * 4);
   const size_t total = off;
 
@@ -228,7 +231,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.groups = reinterpret_cast<uint2*>(b + o_groups);
   w.bscratch = reinterpret_cast<u32*>(b + o_bscr);
   w.key_or = reinterpret_cast<unsigned long long*>(b + o_kor);
-  w.bagg = reinterpret_cast<u64*>(b + o_bagg);
+  w.tagg = reinterpret_cast<u64*>(b + o_tagg);
+  w.ctiles = reinterpret_cast<u32*>(b + o_ctiles);
   w.fcur = reinterpret_cast<u32*>(b + o_fcur);
   return HULL_OK;
 }
@@ -314,16 +318,15 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // 3 split (fine bins, their aggregates, group prefixes), 4 sort (+ second
     // round), 5..9 empty, 10 compaction.
     const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
-    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bstart, w.groups, w.st_region, w.bagg, w.fcur,
-                       g2, st);
+    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bstart, w.groups, w.st_region, w.fcur, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
     e = launch_k2_bins_scatter(d_xy, c->plan, w.keys[0], w.idx[0], w.mask, w.rows, w.bstart, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 3, st);
-    e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.bagg,
+    e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.tagg, w.ctiles,
                      c->occ_sp * c->num_sms, st);
-    if (e == cudaSuccess) e = launch_group_prefix(c->plan, w.groups, w.st_region, w.bagg, st);
+    if (e == cudaSuccess) e = launch_group_prefix(c->plan, w.groups, w.st_region, w.tagg, w.ctiles, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 4, st);
     e = launch_bucket_decide(w.keys[1], w.idx[1], w.keys[0], w.idx[0], c->plan, w.groups, w.bscratch,

@@ -579,14 +579,14 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 // survivors into their bins with the same `grid` (the scatter walks the
 // count's chunks; `rows` has grid rows).
 cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bstart,
-                           uint2* groups, void* recs, u64* bagg, u32* fcur, int grid, cudaStream_t st) {
+                           uint2* groups, void* recs, u32* fcur, int grid, cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
   if (vec) k2_count<true, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
   else k2_count<false, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, bagg, fcur, st);
+  return launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, fcur, st);
 }
 
 cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,

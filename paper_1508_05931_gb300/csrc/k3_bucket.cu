@@ -718,39 +718,19 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   region_offsets(plan, F.recs, ng, s, &S.kwl[0][0], F.lo_xy, F.lo_idx, F.up_xy, F.up_idx);
 }
 
-// Keeps in *addr the extreme of its direction and (dx, dy): the
-// counter-clockwise-most for sgn > 0 (lower region), the clockwise-most for
-// sgn < 0 (upper).  A compare-and-swap loop (a word without its valid bit
-// holds nothing yet); every failed swap means another thread stored a
-// strictly more extreme direction, so the loop ends; it is bounded all the
-// same (ERR_TIMEOUT).
-__device__ __forceinline__ void cas_max_dir(u64* addr, int dx, int dy, int sgn, Plan* plan) {
-  const u64 cand = pack_dir(dx, dy);
-  u64 old = ld_relaxed_u64(addr);
-  for (u32 it = 0; it < 4096u; ++it) {
-    if (old & kDirValid) {
-      int ox, oy;
-      unpack_dir(old, ox, oy);
-      const long long c = cross2(ox, oy, dx, dy);
-      if (sgn > 0 ? c <= 0 : c >= 0) return;
-    }
-    const u64 prev = atomicCAS(reinterpret_cast<unsigned long long*>(addr), old, cand);
-    if (prev == old) return;
-    old = prev;
-  }
-  flag_error(plan, ERR_TIMEOUT);
-}
-
 // The second scatter of the bucket sort: spreads every coarse bin of
 // (ak, av) over its kFinePerCoarse bins in (bk, bv).  Work comes in tiles
-// of SP_TILE consecutive pairs of one coarse bin (a tile counter; any
-// order).  A tile is ordered by bin in shared memory (counting), each of
-// its bins reserves its run with one atomic on that bin's cursor (fcur,
-// starting at the bin's first position), and the runs are written with
+// of SP_TILE consecutive pairs of one coarse bin (tile ids in coarse-bin
+// order, claimed from a counter one tile ahead).  A tile is ordered by bin
+// in shared memory (counting), each of its bins reserves its run with one
+// atomic on that bin's cursor (fcur, starting at the bin's first position;
+// the reservation overlaps the placement), and the runs are written with
 // consecutive threads on consecutive addresses.  With the tile ordered by
-// bin, one warp per bin also folds the tile's points into the bin's
-// direction aggregates (bagg: lower and upper word per bin) for the second
-// round's prefixes.
+// bin, one warp per bin also folds the tile's points into the tile's
+// direction aggregates of that bin: tagg[64 t + 2 d] (lower) and
+// [64 t + 2 d + 1] (upper), 0 when the tile has no point of that bin and
+// region; ctiles[c] = the first tile of coarse bin c (ctiles[kCoarse] = all
+// tiles), written by block 0.
 constexpr int SP_BLOCK = 512;
 constexpr int SP_ITEMS = 8;
 constexpr int SP_TILE = SP_BLOCK * SP_ITEMS;
@@ -762,7 +742,8 @@ constexpr size_t SP_SMEM = (size_t)SP_TILE * (sizeof(u64) + sizeof(u32));
 
 __global__ void __launch_bounds__(SP_BLOCK, 2)
 k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict__ bk, u32* __restrict__ bv,
-         Plan* plan, const u32* __restrict__ bstart, u32* __restrict__ fcur, u64* __restrict__ bagg) {
+         Plan* plan, const u32* __restrict__ bstart, u32* __restrict__ fcur, u64* __restrict__ tagg,
+         u32* __restrict__ ctiles) {
   extern __shared__ __align__(16) unsigned char sp_smem[];   // SP_TILE keys, then SP_TILE indices
   u64* s_key = reinterpret_cast<u64*>(sp_smem);
   u32* s_idx = reinterpret_cast<u32*>(sp_smem + SP_TILE * sizeof(u64));
@@ -774,6 +755,8 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
   const u32 s = plan->s, fshift = plan->fshift;
   const RG rg = make_rg(plan);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  u32 t_next = 0;
+  if (threadIdx.x == 0) t_next = atomicAdd(&plan->ctr[CTR_SPLIT], 1u);
   // Tiles per coarse bin and their exclusive prefix.
   u32 nt = 0;
   if (threadIdx.x < kCoarse) {
@@ -795,14 +778,21 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
     if (w < wid) off += s_w[w];
     tot += s_w[w];
   }
-  if (threadIdx.x < kCoarse) s_tiles[threadIdx.x] = off + inc - nt;
-  if (threadIdx.x == 0) s_tiles[kCoarse] = tot;
+  if (threadIdx.x < kCoarse) {
+    s_tiles[threadIdx.x] = off + inc - nt;
+    if (blockIdx.x == 0) ctiles[threadIdx.x] = off + inc - nt;
+  }
+  if (threadIdx.x == 0) {
+    s_tiles[kCoarse] = tot;
+    if (blockIdx.x == 0) ctiles[kCoarse] = tot;
+  }
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      const u32 t = atomicAdd(&plan->ctr[CTR_SPLIT], 1u);
+      const u32 t = t_next;
       s_t = t;
       if (t < tot) {
+        t_next = atomicAdd(&plan->ctr[CTR_SPLIT], 1u);
         u32 lo = 0, hi = kCoarse - 1;       // largest c with s_tiles[c] <= t
         while (lo < hi) {
           const u32 mid = (lo + hi + 1) >> 1;
@@ -822,15 +812,22 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
     const u32 n = start < ce ? min((u32)SP_TILE, ce - start) : 0u;
     u64 key[SP_ITEMS];
     u32 idx[SP_ITEMS], pk[SP_ITEMS];
+    // The tile's pairs are loaded together, then counted.
     #pragma unroll
     for (int it = 0; it < SP_ITEMS; ++it) {
       const u32 i = it * SP_BLOCK + threadIdx.x;
-      pk[it] = 0xFFFFFFFFu;
       key[it] = 0ull;
       idx[it] = 0u;
       if (i < n) {
         key[it] = ak[start + i];
         idx[it] = av[start + i];
+      }
+    }
+    #pragma unroll
+    for (int it = 0; it < SP_ITEMS; ++it) {
+      const u32 i = it * SP_BLOCK + threadIdx.x;
+      pk[it] = 0xFFFFFFFFu;
+      if (i < n) {
         const u32 f = (u32)(key[it] >> fshift);
         if ((f >> (kBinBits - kCoarseBits)) == c) {
           const u32 d = f & (kFinePerCoarse - 1);
@@ -841,6 +838,7 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
       }
     }
     __syncthreads();
+    u32 gb = 0;
     if (wid == 0) {
       const u32 cn = s_cnt[lane];
       u32 x = cn;
@@ -851,7 +849,7 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
       }
       s_lst[lane] = x - cn;
       if (lane == 31) s_lst[kFinePerCoarse] = x;
-      s_gb[lane] = cn ? atomicAdd(&fcur[c * kFinePerCoarse + lane], cn) : 0u;
+      gb = cn ? atomicAdd(&fcur[c * kFinePerCoarse + lane], cn) : 0u;   // used after the placement
     }
     __syncthreads();
     #pragma unroll
@@ -862,6 +860,7 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
         s_idx[p] = idx[it];
       }
     }
+    if (wid == 0) s_gb[lane] = gb;
     __syncthreads();
     const u32 placed = s_lst[kFinePerCoarse];
     for (u32 j = threadIdx.x; j < placed; j += SP_BLOCK) {
@@ -875,47 +874,54 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
         flag_error(plan, ERR_INTERNAL);
       }
     }
-    // One warp per bin: the tile's contribution to the bin's aggregates
-    // (lanes 0 and 1 update the two words at once).
+    // One warp per bin: the tile's aggregates of the bin (plain stores; a
+    // word without its valid bit holds nothing).
     for (u32 d = wid; d < (u32)kFinePerCoarse; d += SP_WARPS) {
       const u32 a = s_lst[d], b = s_lst[d + 1];
-      if (a == b) continue;
       Dir2 v = rg.ident;
       for (u32 j = a + lane; j < b; j += 32) add_dir(v, rg, s_key[j]);
       #pragma unroll
       for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
-      u64* w = bagg + 2 * (size_t)(c * kFinePerCoarse + d);
-      if (lane == 0 && (v.lx != rg.ident.lx || v.ly != rg.ident.ly)) cas_max_dir(w, v.lx, v.ly, 1, plan);
-      if (lane == 1 && (v.ux != rg.ident.ux || v.uy != rg.ident.uy)) cas_max_dir(w + 1, v.ux, v.uy, -1, plan);
+      u64* w = tagg + (size_t)t * (2 * kFinePerCoarse) + 2 * d;
+      if (lane == 0) w[0] = (v.lx != rg.ident.lx || v.ly != rg.ident.ly) ? pack_dir(v.lx, v.ly) : 0ull;
+      if (lane == 1) w[1] = (v.ux != rg.ident.ux || v.uy != rg.ident.uy) ? pack_dir(v.ux, v.uy) : 0ull;
     }
   }
 }
 
 // Exclusive prefixes of the groups' direction aggregates: a group's
-// aggregate is the combination of its bins' aggregates (bagg, from
-// k3_split; k_group_agg_bins), then one block gives record g's inclusive
-// words the combination of the aggregates of groups 0 .. g - 1 with d(P_0)
-// (the identity).  Thread t takes a contiguous slice of groups.
+// aggregate is the combination of the tile aggregates of its bins (tagg,
+// ctiles from k3_split; k_group_agg_bins), then one block gives record g's
+// inclusive words the combination of the aggregates of groups 0 .. g - 1
+// with d(P_0) (the identity).  Thread t takes a contiguous slice of groups.
 constexpr int GP_BLOCK = 1024;
 
-// One warp per group: its bins' aggregates combined into its record.
+// One warp per group: the aggregates of its bins in every tile of their
+// coarse bins, combined into its record.
 constexpr int GB_BLOCK = 256;
 __global__ void __launch_bounds__(GB_BLOCK)
 k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
-                 const u64* __restrict__ bagg) {
+                 const u64* __restrict__ tagg, const u32* __restrict__ ctiles) {
   if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
   const u32 ng = plan->ngroups;
   const RG rg = make_rg(plan);
   const int lane = threadIdx.x & 31;
   const u32 g = blockIdx.x * (GB_BLOCK / 32) + (threadIdx.x >> 5);
   if (g >= ng) return;
+  const u32 b0 = groups[g].y, b1 = groups[g + 1].y;
   Dir2 t = rg.ident;
-  for (u32 b = groups[g].y + lane; b < groups[g + 1].y; b += 32) {
-    const u64 wl = bagg[2 * (size_t)b], wu = bagg[2 * (size_t)b + 1];
-    Dir2 v = rg.ident;
-    if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
-    if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
-    combine(t, v);
+  for (u32 c = b0 / kFinePerCoarse; c * kFinePerCoarse < b1; ++c) {
+    const u32 lo = max(b0, c * kFinePerCoarse), hi = min(b1, (c + 1) * kFinePerCoarse);
+    const u32 nb = hi - lo, t0 = ctiles[c], ntl = ctiles[c + 1] - t0;
+    for (u32 e = lane; e < nb * ntl; e += 32) {
+      const u32 tile = t0 + e / nb, d = (lo - c * kFinePerCoarse) + e % nb;
+      const u64* w = tagg + (size_t)tile * (2 * kFinePerCoarse) + 2 * d;
+      const u64 wl = w[0], wu = w[1];
+      Dir2 v = rg.ident;
+      if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
+      if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
+      combine(t, v);
+    }
   }
   #pragma unroll
   for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
@@ -977,8 +983,7 @@ static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole 
 
 __global__ void __launch_bounds__(BS_BLOCK)
 k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
-          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u64* __restrict__ bagg,
-          u32* __restrict__ fcur) {
+          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u32* __restrict__ fcur) {
   __shared__ u32 s_part[BS_WARPS][BS_BINS];
   __shared__ u32 s_w[BS_WARPS];
   __shared__ u32 s_last_st[BS_BLOCK], s_last_cn[BS_BLOCK];
@@ -991,9 +996,6 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   if (recs)
     for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
       reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
-  // and the bins' direction aggregates (two words per bin).
-  if (bagg)
-    for (u32 q = threadIdx.x; q < BS_BINS * 2u; q += BS_BLOCK) bagg[(size_t)blockIdx.x * BS_BINS * 2 + q] = 0ull;
   const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
   const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
   u32 sum = 0;
@@ -1184,10 +1186,10 @@ cudaError_t bucket_occupancy(int* blocks) {
   return e;
 }
 
-cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs, u64* bagg,
+cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
                            u32* fcur, cudaStream_t st) {
   k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, nrows, plan, bstart, groups,
-                                                  reinterpret_cast<K4Chunk*>(recs), bagg, fcur);
+                                                  reinterpret_cast<K4Chunk*>(recs), fcur);
   return cudaGetLastError();
 }
 
@@ -1199,18 +1201,22 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
 }
 
 cudaError_t launch_split(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const u32* bstart, u32* fcur,
-                         u64* bagg, int grid, cudaStream_t st) {
-  k3_split<<<grid, SP_BLOCK, SP_SMEM, st>>>(ak, av, bk, bv, plan, bstart, fcur, bagg);
+                         u64* tagg, u32* ctiles, int grid, cudaStream_t st) {
+  k3_split<<<grid, SP_BLOCK, SP_SMEM, st>>>(ak, av, bk, bv, plan, bstart, fcur, tagg, ctiles);
   return cudaGetLastError();
 }
+
+int split_tile() { return SP_TILE; }
 
 cudaError_t split_occupancy(int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k3_split, SP_BLOCK, SP_SMEM);
 }
 
-cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* bagg, cudaStream_t st) {
+cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
+                                cudaStream_t st) {
   K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
-  k_group_agg_bins<<<(kBins + GB_BLOCK / 32 - 1) / (GB_BLOCK / 32), GB_BLOCK, 0, st>>>(plan, R, groups, bagg);
+  k_group_agg_bins<<<(kBins + GB_BLOCK / 32 - 1) / (GB_BLOCK / 32), GB_BLOCK, 0, st>>>(plan, R, groups, tagg,
+                                                                                      ctiles);
   k_group_prefix<<<1, GP_BLOCK, 0, st>>>(plan, R);
   return cudaGetLastError();
 }
@@ -1237,8 +1243,7 @@ cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* pla
   if (e != cudaSuccess) return e;
   k3_array_keyor<<<grid, KA_BLOCK, 0, st>>>(keys, plan, key_or);
   k3_array_hist<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, plan, key_or, rows);
-  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr, nullptr,
-                                                  nullptr);
+  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr, nullptr);
   k3_array_scatter<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, vals, plan, rows, bstart, ok, ov);
   (void)m;
   return cudaGetLastError();

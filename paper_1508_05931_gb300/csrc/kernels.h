@@ -41,19 +41,23 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 // then one block per group of bins (k3_bucket.cu).
 cudaError_t k2_bins_occupancy(int* blocks);
 cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bstart,
-                           uint2* groups, void* recs, u64* bagg, u32* fcur, int grid, cudaStream_t st);
+                           uint2* groups, void* recs, u32* fcur, int grid, cudaStream_t st);
 cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,
                                    const u32* rows, const u32* bstart, int grid, cudaStream_t st);
 size_t bucket_smem();
 size_t bucket_scratch_words(int blocks);
 cudaError_t bucket_configure();
 cudaError_t bucket_occupancy(int* blocks);
-cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs, u64* bagg,
+cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
                            u32* fcur, cudaStream_t st);
-// Coarse bins (ak, av) spread over their bins into (bk, bv), with the bins'
-// direction aggregates (bagg) and cursors (fcur, seeded by the bin scan).
+// Coarse bins (ak, av) spread over their bins into (bk, bv) through the
+// bins' cursors (fcur, seeded by the bin scan), with every tile's direction
+// aggregates per bin (tagg: 2 split_tile()-tile words per bin of the tile's
+// coarse bin, at most ceil(s / split_tile()) + kCoarse tiles) and the first
+// tile of every coarse bin (ctiles, kCoarse + 1 words).
+int split_tile();
 cudaError_t launch_split(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const u32* bstart, u32* fcur,
-                         u64* bagg, int grid, cudaStream_t st);
+                         u64* tagg, u32* ctiles, int grid, cudaStream_t st);
 cudaError_t split_occupancy(int* blocks);
 cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
                                const uint2* groups, u32* scratch, int grid, cudaStream_t st);
@@ -62,7 +66,8 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
 // the bin scan) and their exclusive prefixes (one block), then the sort of
 // every group with the second round run on it (kept points into the t_*
 // staging areas; then launch_group_compact).
-cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* bagg, cudaStream_t st);
+cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
+                                cudaStream_t st);
 cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
                                  u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
                                  int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
