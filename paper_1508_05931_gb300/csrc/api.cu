@@ -50,6 +50,7 @@ struct Workspace {
   u32* bscratch = nullptr;     // per-block scratch of the large-bin split
   u64* tagg = nullptr;         // per split tile and bin: direction aggregates (lower, upper)
   u32* ctiles = nullptr;       // first split tile of every coarse bin
+  u32* bcnt = nullptr;         // bins' totals, then coarse-bin cursors (k2_count)
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   unsigned long long* key_or = nullptr;
 };
@@ -192,6 +193,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t tiles_cap = cap / (size_t)split_tile() + (size_t)kCoarse + 1;
   const size_t o_tagg = take(tiles_cap * 2 * kFinePerCoarse * 8);
   const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
+  const size_t o_bcnt = take(((size_t)kBins + kCoarse) * 4);
   const size_t o_fcur = take((size_t)kBins * 4);
   const size_t total = off;
 
@@ -233,6 +235,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.key_or = reinterpret_cast<unsigned long long*>(b + o_kor);
   w.tagg = reinterpret_cast<u64*>(b + o_tagg);
   w.ctiles = reinterpret_cast<u32*>(b + o_ctiles);
+  w.bcnt = reinterpret_cast<u32*>(b + o_bcnt);
   w.fcur = reinterpret_cast<u32*>(b + o_fcur);
   return HULL_OK;
 }
@@ -318,7 +321,7 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // 3 split (fine bins, their aggregates, group prefixes), 4 sort (+ second
     // round), 5..9 empty, 10 compaction.
     const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
-    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bstart, w.groups, w.st_region, w.fcur, g2, st);
+    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bcnt, w.bstart, w.groups, w.fcur, g2, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
     e = launch_k2_bins_scatter(d_xy, c->plan, w.keys[0], w.idx[0], w.mask, w.rows, w.bstart, g2, st);

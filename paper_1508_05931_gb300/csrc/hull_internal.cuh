@@ -195,6 +195,17 @@ __device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, u32 b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
       ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
 }
+// Read-only loads with an L2 eviction policy.
+__device__ __forceinline__ u64 ld_hint_u64(const u64* p, u64 pol) {
+  u64 v;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ u32 ld_hint_u32(const u32* p, u64 pol) {
+  u32 v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ void st_hint_u64(u64* p, u64 v, u64 pol) {
   asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
 }

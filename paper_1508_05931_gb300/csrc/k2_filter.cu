@@ -153,14 +153,18 @@ __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* p
       }
     }
     mask[(size_t)c * K2_BLOCK + threadIdx.x] = (unsigned char)bits;
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-    if (lane == 0) s_red[wid] = cnt;
+    if (!BINS) {          // chunk counts for the stable compaction (the bin rows replace them)
+      #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+      if (lane == 0) s_red[wid] = cnt;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      u32 t = 0;
-      for (int w = 0; w < K2_WARPS; ++w) t += s_red[w];
-      counts[c] = t;
+      if (!BINS) {
+        u32 t = 0;
+        for (int w = 0; w < K2_WARPS; ++w) t += s_red[w];
+        counts[c] = t;
+      }
       // Every thread has read stage st (barrier above): refill it.
       if (BULK) {
         const u32 cn = c + K2_STAGES * gridDim.x;
@@ -172,12 +176,16 @@ __device__ __forceinline__ void count_chunks(const int* __restrict__ xy, Plan* p
 }
 
 // With BINS, also counts the survivors per bin of the bucket sort (key >>
-// fshift) and stores the block's counts as row blockIdx.x of `rows`
-// (dynamic shared memory: the ring, then kBins counters).
+// fshift; dynamic shared memory: the ring, then kBins counters), adds them
+// to the bins' totals btot, and reserves the block's run in every coarse
+// bin (kFinePerCoarse consecutive bins) from the coarse cursors ccur: row
+// blockIdx.x of `rows` (kCoarse words) receives the run's offset in its
+// coarse bin.  btot and ccur start at zero.
 template <bool VEC, bool BINS>
 __global__ void __launch_bounds__(K2_BLOCK, 4)
 k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
-         unsigned char* __restrict__ mask, u32* __restrict__ rows) {
+         unsigned char* __restrict__ mask, u32* __restrict__ rows, u32* __restrict__ btot,
+         u32* __restrict__ ccur) {
   extern __shared__ __align__(128) unsigned char k2_smem[];
   __shared__ u32 s_hist[kRadix];
   __shared__ u32 s_red[K2_WARPS];
@@ -219,8 +227,19 @@ k2_count(const int* __restrict__ xy, Plan* plan, u32* __restrict__ counts,
     for (u32 q = threadIdx.x; q < kRadix; q += K2_BLOCK)
       if (s_hist[q]) atomicAdd(&plan->hist[0][q], s_hist[q]);
   if (BINS) {
+    // k_binstart turns the totals into bin starts and sets the survivor count.
     __syncthreads();
-    for (u32 q = threadIdx.x; q < (u32)kBins; q += K2_BLOCK) rows[(size_t)blockIdx.x * kBins + q] = s_bins[q];
+    for (u32 q = threadIdx.x; q < (u32)kBins; q += K2_BLOCK) {
+      const u32 v = s_bins[q];
+      if (v) atomicAdd(&btot[q], v);
+    }
+    for (u32 cb = threadIdx.x; cb < (u32)kCoarse; cb += K2_BLOCK) {
+      u32 cs = 0;
+      #pragma unroll 8
+      for (u32 f = 0; f < (u32)kFinePerCoarse; ++f) cs += s_bins[cb * kFinePerCoarse + ((f + cb) & (kFinePerCoarse - 1))];
+      rows[(size_t)blockIdx.x * kCoarse + cb] = cs ? atomicAdd(&ccur[cb], cs) : 0u;
+    }
+    return;
   }
 
   // The last block turns the chunk counts into exclusive offsets.
@@ -344,8 +363,8 @@ k2_write(const int* __restrict__ xy, Plan* plan, const u32* __restrict__ offsets
 // each the union of kFinePerCoarse consecutive bins).  Block i walks the
 // same chunks as block i of k2_count (in the reverse order, so that the part
 // of the input k2_count read last is still in L2); its run in coarse bin c
-// starts at bstart of c's first bin plus the sum over c's bins of its row's
-// prefixes rows[i][b] (from k_binscan), and grows one survivor at a time
+// starts at bstart of c's first bin plus the offset k2_count reserved for
+// block i in c (rows[i][c]), and grows one survivor at a time
 // (positions by shared-memory atomics, in no particular order), so every
 // block has only one partly written sector per coarse bin at a time and L2
 // completes it before it leaves.  No block waits for another.  Whole chunks
@@ -461,11 +480,7 @@ k2_scatter(const int* __restrict__ xy, Plan* plan, const unsigned char* __restri
   const u64 pol_out = policy_evict_last();
   {
     const u32 cb = threadIdx.x;
-    const u32* row = rows + (size_t)b0 * kBins + (size_t)cb * kFinePerCoarse;
-    u32 sum = bstart[cb * kFinePerCoarse];
-    #pragma unroll 8
-    for (int f = 0; f < kFinePerCoarse; ++f) sum += row[f];
-    S.cur[cb] = sum;
+    S.cur[cb] = bstart[cb * kFinePerCoarse] + rows[(size_t)b0 * kCoarse + cb];
     S.cnt[cb] = 0u;
   }
   // This block's chunks are b0 + k * G.  The whole ones (c < nring) go
@@ -565,28 +580,34 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
   if (vec) {
-    k2_count<true, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr);
+    k2_count<true, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr, nullptr, nullptr);
     k2_write<true><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   } else {
-    k2_count<false, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr);
+    k2_count<false, false><<<grid_count, K2_BLOCK, K2_RING_BYTES, st>>>(xy, plan, counts, mask, nullptr, nullptr, nullptr);
     k2_write<false><<<grid_write, K2_BLOCK, 0, st>>>(xy, plan, counts, mask, keys_out, idx_out);
   }
   return cudaGetLastError();
 }
 
-// First round for the bucket sort: k2_count with per-block bin rows, then
-// the bin scan (k3_bucket.cu); launch_k2_bins_scatter then writes the
-// survivors into their bins with the same `grid` (the scatter walks the
-// count's chunks; `rows` has grid rows).
-cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bstart,
-                           uint2* groups, void* recs, u32* fcur, int grid, cudaStream_t st) {
+// First round for the bucket sort: k2_count with the bins' totals and every
+// block's coarse-bin offsets (rows: grid rows of kCoarse words; bcnt: kBins
+// totals then kCoarse cursors, cleared here), then the bin starts and groups
+// (k3_bucket.cu); launch_k2_bins_scatter then writes the survivors into
+// their coarse bins with the same `grid` (the scatter walks the count's
+// chunks).
+cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bcnt,
+                           u32* bstart, uint2* groups, u32* fcur, int grid, cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   u32* counts = reinterpret_cast<u32*>(status);
-  if (vec) k2_count<true, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
-  else k2_count<false, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows);
-  cudaError_t e = cudaGetLastError();
+  u32* btot = bcnt;
+  u32* ccur = bcnt + kBins;
+  cudaError_t e = cudaMemsetAsync(bcnt, 0, ((size_t)kBins + kCoarse) * sizeof(u32), st);
   if (e != cudaSuccess) return e;
-  return launch_binscan(rows, (u32)grid, plan, bstart, groups, recs, fcur, st);
+  if (vec) k2_count<true, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows, btot, ccur);
+  else k2_count<false, true><<<grid, K2_BLOCK, K2_BINS_SMEM, st>>>(xy, plan, counts, mask, rows, btot, ccur);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_binstart(btot, plan, bstart, groups, fcur, st);
 }
 
 cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,

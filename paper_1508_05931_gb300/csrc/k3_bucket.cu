@@ -470,7 +470,9 @@ __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
     flag_error(plan, ERR_INTERNAL);
   }
 #endif
-  // Place: the pairs of a batch are loaded together, then stored.
+  // Place: the pairs of a batch are loaded together, then stored (the last
+  // read of a read-only source: evict-first).
+  const u64 pol_last = policy_evict_first();
   #pragma unroll
   for (int h = 0; h < 2; ++h) {
     if (h > 0 && m <= (u32)(KB_HALF * KB_BLOCK)) continue;
@@ -482,8 +484,8 @@ __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
       kk[q] = 0ull;
       vv[q] = 0u;
       if (i < m) {
-        kk[q] = load_src<RO>(sk + base + i);
-        vv[q] = load_src<RO>(sv + base + i);
+        kk[q] = RO ? ld_hint_u64(sk + base + i, pol_last) : sk[base + i];
+        vv[q] = RO ? ld_hint_u32(sv + base + i, pol_last) : sv[base + i];
       }
     }
     #pragma unroll
@@ -755,6 +757,7 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
   const u32 s = plan->s, fshift = plan->fshift;
   const RG rg = make_rg(plan);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u64 pol_in = policy_evict_first();    // the coarse bins are dead once split
   u32 t_next = 0;
   if (threadIdx.x == 0) t_next = atomicAdd(&plan->ctr[CTR_SPLIT], 1u);
   // Tiles per coarse bin and their exclusive prefix.
@@ -819,8 +822,8 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
       key[it] = 0ull;
       idx[it] = 0u;
       if (i < n) {
-        key[it] = ak[start + i];
-        idx[it] = av[start + i];
+        key[it] = ld_hint_u64(ak + start + i, pol_in);
+        idx[it] = ld_hint_u32(av + start + i, pol_in);
       }
     }
     #pragma unroll
@@ -975,59 +978,35 @@ k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
 // receives the bin totals, and the last block turns them into the bins'
 // first positions and writes the groups (first position, first bin), with a
 // closing record (s, kBins) after the last group.
-constexpr int BS_BLOCK = 256;
+constexpr int BS_BLOCK = 512;
 constexpr int BS_BINS = 32;                 // bins per block (one per lane)
 constexpr int BS_WARPS = BS_BLOCK / 32;
+constexpr int BS_RMAX = 10;                 // rows a warp loads at once
 constexpr int BS_PER = kBins / BS_BLOCK;    // bins per thread in the last block (a flag word each)
 static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole slices of at most 32 bins per thread");
 
-__global__ void __launch_bounds__(BS_BLOCK)
-k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
-          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u32* __restrict__ fcur) {
-  __shared__ u32 s_part[BS_WARPS][BS_BINS];
+// One whole block (BS_BLOCK threads): the bins' starts (bstart, and the
+// split's cursors fcur when given) from their totals, the groups of
+// consecutive bins, the survivor count.  Thread t owns bins
+// [t BS_PER, t BS_PER + BS_PER).  `totals` may be bstart itself.
+__device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
+                               u32* __restrict__ fcur) {
   __shared__ u32 s_w[BS_WARPS];
   __shared__ u32 s_last_st[BS_BLOCK], s_last_cn[BS_BLOCK];
-  __shared__ bool s_last;
-  if (plan->error & ERR_RANGE) return;
+  __shared__ __align__(16) u32 s_v[kBins];      // totals, then starts (coalesced global access)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 bin = blockIdx.x * BS_BINS + lane;
-  // Clear the look-back records of the fused second round (one per group,
-  // at most one group per bin): 8 words per record.
-  if (recs)
-    for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
-      reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
-  const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
-  const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
-  u32 sum = 0;
-  for (u32 r = r0; r < r1; ++r) sum += rows[(size_t)r * kBins + bin];
-  s_part[wid][lane] = sum;
+  static_assert(BS_PER % 4 == 0, "whole uint4 slices");
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += BS_BLOCK) s_v[q] = ld_volatile_u32(&totals[q]);
   __syncthreads();
-  u32 run = 0, tot = 0;
-  for (int w = 0; w < BS_WARPS; ++w) {
-    if (w < wid) run += s_part[w][lane];
-    tot += s_part[w][lane];
-  }
-  for (u32 r = r0; r < r1; ++r) {
-    const u32 v = rows[(size_t)r * kBins + bin];
-    rows[(size_t)r * kBins + bin] = run;
-    run += v;
-  }
-  if (wid == 0) bstart[bin] = tot;
-
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_BIN_SCAN], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // Last block: bin starts and groups.  Thread t owns bins [32t, 32t + 32).
   u32 cn[BS_PER], st[BS_PER];
   u32 tsum = 0;
   #pragma unroll
-  for (int j = 0; j < BS_PER; ++j) {
-    cn[j] = ld_volatile_u32(&bstart[threadIdx.x * BS_PER + j]);
-    tsum += cn[j];
+  for (int j = 0; j < BS_PER; j += 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(&s_v[threadIdx.x * BS_PER + j]);
+    cn[j] = v.x; cn[j + 1] = v.y; cn[j + 2] = v.z; cn[j + 3] = v.w;
   }
+  #pragma unroll
+  for (int j = 0; j < BS_PER; ++j) tsum += cn[j];
   u32 inc = tsum;
   #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1069,17 +1048,83 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   for (int w = 0; w < wid; ++w) g += s_w[w];
   #pragma unroll
   for (int j = 0; j < BS_PER; ++j) {
-    const u32 b = threadIdx.x * BS_PER + j;
-    bstart[b] = st[j];
-    if (fcur) fcur[b] = st[j];
-    if (flags & (1u << j)) groups[g++] = make_uint2(st[j], b);
+    if (flags & (1u << j)) groups[g++] = make_uint2(st[j], threadIdx.x * BS_PER + j);
+  }
+  #pragma unroll
+  for (int j = 0; j < BS_PER; j += 4)
+    *reinterpret_cast<uint4*>(&s_v[threadIdx.x * BS_PER + j]) = make_uint4(st[j], st[j + 1], st[j + 2], st[j + 3]);
+  __syncthreads();
+  for (u32 q = threadIdx.x; q < (u32)kBins; q += BS_BLOCK) {
+    const u32 v = s_v[q];
+    bstart[q] = v;
+    if (fcur) fcur[q] = v;
   }
   if (threadIdx.x == BS_BLOCK - 1) {
     groups[g] = make_uint2(acc, (u32)kBins);
+    plan->s = acc;            // the survivors: every bin's count
     plan->ngroups = g;
     plan->npasses = 0;        // no radix passes on this path;
     plan->sorted_in_b = 1;    // k3_bucket leaves the sorted survivors in the second buffer
   }
+}
+__global__ void __launch_bounds__(BS_BLOCK)
+k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
+          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u32* __restrict__ fcur) {
+  __shared__ u32 s_part[BS_WARPS][BS_BINS];
+  __shared__ bool s_last;
+  if (plan->error & ERR_RANGE) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 bin = blockIdx.x * BS_BINS + lane;
+  // Clear the look-back records of the fused second round (one per group,
+  // at most one group per bin): 8 words per record.
+  if (recs)
+    for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
+      reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
+  const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
+  const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
+  u32 sum = 0;
+  for (u32 rb = r0; rb < r1; rb += BS_RMAX) {       // the rows of a batch are loaded together
+    u32 v[BS_RMAX];
+    #pragma unroll
+    for (int q = 0; q < BS_RMAX; ++q) v[q] = rb + q < r1 ? rows[(size_t)(rb + q) * kBins + bin] : 0u;
+    #pragma unroll
+    for (int q = 0; q < BS_RMAX; ++q) sum += v[q];
+  }
+  s_part[wid][lane] = sum;
+  __syncthreads();
+  u32 run = 0, tot = 0;
+  for (int w = 0; w < BS_WARPS; ++w) {
+    if (w < wid) run += s_part[w][lane];
+    tot += s_part[w][lane];
+  }
+  for (u32 rb = r0; rb < r1; rb += BS_RMAX) {
+    u32 v[BS_RMAX];
+    #pragma unroll
+    for (int q = 0; q < BS_RMAX; ++q) v[q] = rb + q < r1 ? rows[(size_t)(rb + q) * kBins + bin] : 0u;
+    #pragma unroll
+    for (int q = 0; q < BS_RMAX; ++q) {
+      if (rb + q < r1) rows[(size_t)(rb + q) * kBins + bin] = run;
+      run += v[q];
+    }
+  }
+  if (wid == 0) bstart[bin] = tot;
+
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_BIN_SCAN], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  bins_to_groups(bstart, plan, bstart, groups, fcur);
+}
+
+// The bin starts and groups of the pipeline's bucket sort from the bins'
+// totals, which k2_count accumulated (one block).
+__global__ void __launch_bounds__(BS_BLOCK)
+k_binstart(const u32* __restrict__ btot, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
+           u32* __restrict__ fcur) {
+  if (plan->error & ERR_RANGE) return;
+  bins_to_groups(btot, plan, bstart, groups, fcur);
 }
 
 // ---- the same sort over an arbitrary key array (the stage entry point):
@@ -1184,6 +1229,11 @@ cudaError_t bucket_occupancy(int* blocks) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k3_bucket<true>, KB_BLOCK, sizeof(BucketSmem));
   *blocks = a < b ? a : b;
   return e;
+}
+
+cudaError_t launch_binstart(const u32* btot, Plan* plan, u32* bstart, uint2* groups, u32* fcur, cudaStream_t st) {
+  k_binstart<<<1, BS_BLOCK, 0, st>>>(btot, plan, bstart, groups, fcur);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,

@@ -40,14 +40,15 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 // Bucket sort (the pipeline's sort): K2 with bin rows + bin scan + scatter,
 // then one block per group of bins (k3_bucket.cu).
 cudaError_t k2_bins_occupancy(int* blocks);
-cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bstart,
-                           uint2* groups, void* recs, u32* fcur, int grid, cudaStream_t st);
+cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bcnt,
+                           u32* bstart, uint2* groups, u32* fcur, int grid, cudaStream_t st);
 cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,
                                    const u32* rows, const u32* bstart, int grid, cudaStream_t st);
 size_t bucket_smem();
 size_t bucket_scratch_words(int blocks);
 cudaError_t bucket_configure();
 cudaError_t bucket_occupancy(int* blocks);
+cudaError_t launch_binstart(const u32* btot, Plan* plan, u32* bstart, uint2* groups, u32* fcur, cudaStream_t st);
 cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
                            u32* fcur, cudaStream_t st);
 // Coarse bins (ak, av) spread over their bins into (bk, bv) through the
@@ -76,6 +77,10 @@ cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_l
                                  const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,
                                  int2* up_xy, int* up_idx, int grid, cudaStream_t st);
 int array_hist_grid(u32 m, int num_sms);
+#ifdef GBH_DEBUG_CHECKS
+// Debug builds: checks that both region lists are in strictly increasing (x, y) order.
+cudaError_t launch_check_regions(const Plan* plan, const int2* lo_xy, const int2* up_xy, cudaStream_t st);
+#endif
 cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* plan,
                               unsigned long long* key_or, u32* rows, u32* bstart, uint2* groups,
                               u64* ok, u32* ov, int grid, cudaStream_t st);

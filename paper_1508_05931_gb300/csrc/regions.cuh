@@ -164,10 +164,16 @@ __device__ __forceinline__ void region_offsets(Plan* plan, K4Chunk* chunks, u32 
   const u32 nt = blockDim.x;
   const u32 per = (nrec + nt - 1) / nt;
   const u32 lo = min(nrec, threadIdx.x * per), hi = min(nrec, lo + per);
+  // The counts of a batch of records are loaded together (one round trip).
+  constexpr int RB = 8;
   u32 sl = 0, su = 0;
-  for (u32 c = lo; c < hi; ++c) {
-    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
-    sl += q[0]; su += q[1];
+  for (u32 cb = lo; cb < hi; cb += RB) {
+    unsigned long long v[RB];
+    #pragma unroll
+    for (int q = 0; q < RB; ++q)
+      v[q] = cb + q < hi ? *reinterpret_cast<const volatile unsigned long long*>(&chunks[cb + q].cnt) : 0ull;
+    #pragma unroll
+    for (int q = 0; q < RB; ++q) { sl += (u32)v[q]; su += (u32)(v[q] >> 32); }
   }
   u32 il = sl, iu = su;
   #pragma unroll
@@ -181,11 +187,17 @@ __device__ __forceinline__ void region_offsets(Plan* plan, K4Chunk* chunks, u32 
   u32 ol = 0, ou = 0;
   for (int w = 0; w < wid; ++w) { ol += red[2 * w]; ou += red[2 * w + 1]; }
   u32 rl = ol + il - sl, ru = ou + iu - su;
-  for (u32 c = lo; c < hi; ++c) {
-    const volatile u32* q = reinterpret_cast<const volatile u32*>(&chunks[c].cnt);
-    const u32 a = q[0], b = q[1];
-    chunks[c].off = make_uint2(rl, ru);
-    rl += a; ru += b;
+  for (u32 cb = lo; cb < hi; cb += RB) {
+    unsigned long long v[RB];
+    #pragma unroll
+    for (int q = 0; q < RB; ++q)
+      v[q] = cb + q < hi ? *reinterpret_cast<const volatile unsigned long long*>(&chunks[cb + q].cnt) : 0ull;
+    #pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      if (cb + q < hi) chunks[cb + q].off = make_uint2(rl, ru);
+      rl += (u32)v[q];
+      ru += (u32)(v[q] >> 32);
+    }
   }
   if (threadIdx.x == nt - 1) {
     const u32 r_lo = ol + il, r_up = ou + iu;
