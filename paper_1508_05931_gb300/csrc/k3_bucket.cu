@@ -27,6 +27,8 @@
 // duplication, or a few points spread over a huge bounding box) the block
 // sets ERR_FALLBACK and the host reruns the call on the radix passes of
 // k3_sort.cu.
+#include <cstddef>
+
 #include "hull_internal.cuh"
 #include "kernels.h"
 #include "regions.cuh"
@@ -67,6 +69,10 @@ struct BucketSmem {
   Dir2 carry;              // prefix through the group's positions scanned so far
   u32 kwl[KB_WARPS][2];    // per-warp kept counts (lower, upper)
   u32 kept[2];             // the group's kept points so far
+  // the next group, fetched while the current one is processed
+  __align__(16) u64 ninc[2];   // its exclusive prefix words (lower, upper)
+  uint2 nab[2];            // groups[id], groups[id + 1]
+  u32 nid;                 // its id (>= the group count: none)
 };
 
 // Shared-memory slot of sorted position i: the low five bits are XORed
@@ -113,11 +119,16 @@ constexpr int kCrowdedFlag = 1, kHeavyFlag = 2;
 __device__ __forceinline__ int scan_counts(BucketSmem& S) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
+  static_assert(KB_SCAN_PER == 8, "two 16-byte words of counters per thread");
   u32 v[KB_SCAN_PER];
+  {
+    const uint4 c0 = *reinterpret_cast<const uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER]);
+    const uint4 c1 = *reinterpret_cast<const uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER + 4]);
+    v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w; v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
+  }
   u32 sum = 0, mx = 0;
   #pragma unroll
   for (int j = 0; j < KB_SCAN_PER; ++j) {
-    v[j] = S.cnt[threadIdx.x * KB_SCAN_PER + j];
     sum += v[j];
     mx = max(mx, v[j]);
   }
@@ -132,11 +143,14 @@ __device__ __forceinline__ int scan_counts(BucketSmem& S) {
   int st = __syncthreads_or(flags) != 0 ? kHeavyFlag : 0;
   if (st) st |= __syncthreads_or(flags & kCrowdedFlag) != 0 ? kCrowdedFlag : 0;
   u32 run = inc - sum + warps_before(S.wsum[lane < KB_WARPS ? lane : 0], wid);
+  u32 r[KB_SCAN_PER];
   #pragma unroll
   for (int j = 0; j < KB_SCAN_PER; ++j) {
-    S.cnt[threadIdx.x * KB_SCAN_PER + j] = run;
+    r[j] = run;
     run += v[j];
   }
+  *reinterpret_cast<uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER]) = make_uint4(r[0], r[1], r[2], r[3]);
+  *reinterpret_cast<uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER + 4]) = make_uint4(r[4], r[5], r[6], r[7]);
   if (threadIdx.x == KB_BLOCK - 1) S.cnt[kSubBins] = run;
   __syncthreads();
   return st;
@@ -315,30 +329,43 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
     p0 = min(m, threadIdx.x * R);
     p1 = min(m, p0 + R);
   }
+  // Bit j of smask: position p0 + j starts a sub-bin (sorted pairs: every
+  // position does).
+  u32 smask = 0xFFFFFFFFu;
+  if (binned) {
+    const uint4 c0 = *reinterpret_cast<const uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER]);
+    const uint4 c1 = *reinterpret_cast<const uint4*>(&S.cnt[threadIdx.x * KB_SCAN_PER + 4]);
+    const u32 st[KB_SCAN_PER] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    smask = 0u;
+    #pragma unroll
+    for (int j = 0; j < KB_SCAN_PER; ++j)
+      if (st[j] < p1) smask |= 1u << (st[j] - p0);
+  }
   const Dir2 carry = S.carry;
   Dir2 loc = carry, lsb = carry;
   u32 cand = 0;                                   // bit j: position p0 + j is a candidate
-  u32 dprev = 0xFFFFFFFFu;
-  for (u32 p = p0; p < p1; ++p) {
-    const u64 k = S.key[phys(p)];
-    if (binned) {
-      const u32 d = sub_of(f, k - klo);
-      if (d != dprev) { lsb = loc; dprev = d; }
-    } else {
-      lsb = loc;
-    }
-    int px, py;
-    const int sd = decode_side(rg, k, px, py);
-    const int vx = px - rg.bx, vy = py - rg.by;
-    if (sd < 0) {
-      if (cross2(lsb.lx, lsb.ly, vx, vy) > 0) {
-        cand |= 1u << (p - p0);
-        if (cross2(loc.lx, loc.ly, vx, vy) > 0) { loc.lx = vx; loc.ly = vy; }
-      }
-    } else if (sd > 0) {
-      if (cross2(lsb.ux, lsb.uy, vx, vy) < 0) {
-        cand |= 1u << (p - p0);
-        if (cross2(loc.ux, loc.uy, vx, vy) < 0) { loc.ux = vx; loc.uy = vy; }
+  for (u32 pb = p0; pb < p1; pb += 4) {
+    u64 kq[4];                                    // four keys loaded together
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) kq[q] = pb + q < p1 ? S.key[phys(pb + q)] : 0ull;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const u32 j = pb + q - p0;
+      if (pb + q >= p1) break;
+      if ((smask >> j) & 1u) lsb = loc;
+      int px, py;
+      const int sd = decode_side(rg, kq[q], px, py);
+      const int vx = px - rg.bx, vy = py - rg.by;
+      if (sd < 0) {
+        if (cross2(lsb.lx, lsb.ly, vx, vy) > 0) {
+          cand |= 1u << j;
+          if (cross2(loc.lx, loc.ly, vx, vy) > 0) { loc.lx = vx; loc.ly = vy; }
+        }
+      } else if (sd > 0) {
+        if (cross2(lsb.ux, lsb.uy, vx, vy) < 0) {
+          cand |= 1u << j;
+          if (cross2(loc.ux, loc.uy, vx, vy) < 0) { loc.ux = vx; loc.uy = vy; }
+        }
       }
     }
   }
@@ -409,12 +436,25 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
 }
 
 // Starts group g's second round from its exclusive prefix (one thread).
-__device__ __forceinline__ void start_group(BucketSmem& S, const Fused& F, u32 g) {
+__device__ __forceinline__ void start_group(BucketSmem& S) {
   Dir2 e;
-  unpack_dir(F.recs[g].inc_lo, e.lx, e.ly);
-  unpack_dir(F.recs[g].inc_up, e.ux, e.uy);
+  unpack_dir(S.ninc[0], e.lx, e.ly);
+  unpack_dir(S.ninc[1], e.ux, e.uy);
   S.carry = e;
   S.kept[0] = S.kept[1] = 0u;
+}
+
+// Thread 0: starts the asynchronous fetch of group g's descriptor (its
+// first position and bin, the next group's, and with DECIDE its prefix)
+// into S.nab / S.ninc, and records g in S.nid.
+template <bool DECIDE>
+__device__ __forceinline__ void fetch_group(BucketSmem& S, const Fused& F, const uint2* groups, u32 g, u32 ng) {
+  S.nid = g;
+  if (g >= ng) return;
+  cp_async8(&S.nab[0], &groups[g]);
+  cp_async8(&S.nab[1], &groups[g + 1]);
+  if (DECIDE) cp_async16(&S.ninc[0], &F.recs[g].inc_lo);
+  cp_async_commit();
 }
 
 
@@ -431,7 +471,9 @@ __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
     const SubMap f = make_submap(ktop);
     S.misc[2] = f.esh; S.misc[3] = f.lsh; S.misc[4] = f.M;
   }
-  for (u32 i = threadIdx.x; i <= (u32)kSubBins; i += KB_BLOCK) S.cnt[i] = 0u;
+  for (u32 i = threadIdx.x; i < (u32)kSubBins / 4; i += KB_BLOCK)
+    reinterpret_cast<uint4*>(S.cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (threadIdx.x == 0) S.cnt[kSubBins] = 0u;
   __syncthreads();
   const SubMap f = {S.misc[2], S.misc[3], S.misc[4]};
   // Rank: every key's sub-bin and its arrival rank there.  The keys of a
@@ -668,24 +710,32 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
   const u32 s = plan->s;
   const RG rg = make_rg(plan);
   u32* my_scratch = scratch + (size_t)blockIdx.x * kScratchWords;
-  // Thread 0 claims each group one iteration ahead, so that the claim's
-  // round trip overlaps the current group.
+  // Thread 0 claims groups two ahead and fetches each descriptor one
+  // group ahead (asynchronously, into shared memory), so that neither round
+  // trip lies on the block's path.
+  static_assert(offsetof(K4Chunk, inc_up) == offsetof(K4Chunk, inc_lo) + 8 && offsetof(K4Chunk, inc_lo) % 16 == 0,
+                "prefix words fetched as one 16-byte copy");
   u32 g_next = 0;
-  if (threadIdx.x == 0) g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
+  if (threadIdx.x == 0) {
+    fetch_group<DECIDE>(S, F, groups, atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u), ng);
+    g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
+  }
   for (;;) {
     if (threadIdx.x == 0) {
-      const u32 g = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : min(g_next, ng);
+      cp_async_wait_all();
+      const u32 g = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : min(S.nid, ng);
       S.misc[1] = g;
-      if (g < ng) {
-        g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
-        if (DECIDE) start_group(S, F, g);
-      }
+      if (DECIDE && g < ng) start_group(S);
     }
     __syncthreads();
     const u32 g = S.misc[1];
+    const uint2 a = S.nab[0], b = S.nab[1];   // (first position, first bin)
     __syncthreads();
     if (g >= ng) break;
-    const uint2 a = groups[g], b = groups[g + 1];   // (first position, first bin)
+    if (threadIdx.x == 0) {
+      fetch_group<DECIDE>(S, F, groups, g_next, ng);
+      if (g_next < ng) g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
+    }
     const u32 m = b.x - a.x;
 #ifdef GBH_DEBUG_CHECKS
     if (b.x < a.x || b.x > s || b.y <= a.y || b.y > (u32)kBins) {
@@ -988,7 +1038,9 @@ static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole 
 // One whole block (BS_BLOCK threads): the bins' starts (bstart, and the
 // split's cursors fcur when given) from their totals, the groups of
 // consecutive bins, the survivor count.  Thread t owns bins
-// [t BS_PER, t BS_PER + BS_PER).  `totals` may be bstart itself.
+// [t BS_PER, t BS_PER + BS_PER).  `totals` may be bstart itself; VOL when
+// other blocks of the same launch wrote it.
+template <bool VOL>
 __device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
                                u32* __restrict__ fcur) {
   __shared__ u32 s_w[BS_WARPS];
@@ -996,7 +1048,16 @@ __device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ 
   __shared__ __align__(16) u32 s_v[kBins];      // totals, then starts (coalesced global access)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   static_assert(BS_PER % 4 == 0, "whole uint4 slices");
-  for (u32 q = threadIdx.x; q < (u32)kBins; q += BS_BLOCK) s_v[q] = ld_volatile_u32(&totals[q]);
+  {
+    u32 v[BS_PER];
+    #pragma unroll
+    for (int j = 0; j < BS_PER; ++j) {
+      const u32* p = &totals[threadIdx.x + j * BS_BLOCK];
+      v[j] = VOL ? ld_volatile_u32(p) : *p;
+    }
+    #pragma unroll
+    for (int j = 0; j < BS_PER; ++j) s_v[threadIdx.x + j * BS_BLOCK] = v[j];
+  }
   __syncthreads();
   u32 cn[BS_PER], st[BS_PER];
   u32 tsum = 0;
@@ -1115,7 +1176,7 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  bins_to_groups(bstart, plan, bstart, groups, fcur);
+  bins_to_groups<true>(bstart, plan, bstart, groups, fcur);
 }
 
 // The bin starts and groups of the pipeline's bucket sort from the bins'
@@ -1124,7 +1185,7 @@ __global__ void __launch_bounds__(BS_BLOCK)
 k_binstart(const u32* __restrict__ btot, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
            u32* __restrict__ fcur) {
   if (plan->error & ERR_RANGE) return;
-  bins_to_groups(btot, plan, bstart, groups, fcur);
+  bins_to_groups<false>(btot, plan, bstart, groups, fcur);
 }
 
 // ---- the same sort over an arbitrary key array (the stage entry point):
