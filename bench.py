@@ -34,8 +34,8 @@ WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk
 # 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
 PAPER_MPTS = 40.0 / 0.8645
 # Kernels per hull_compute with the bucket sort: extremes, filter count, bin
-# scan, scatter into coarse bins, split into bins, group prefixes, sort (+
-# second round), compaction, finalisation.  A call rerun on the radix passes adds extremes,
+# starts, scatter into coarse bins, split into bins, group aggregates and
+# prefixes, sort (+ second round), compaction, finalisation.  A call rerun on the radix passes adds extremes,
 # filter count + write, 8 radix passes, region scan + compact, finalisation.
 LAUNCHES_PER_HULL = 9
 LAUNCHES_PER_RADIX_RERUN = 1 + 2 + 8 + 2 + 1
@@ -222,9 +222,9 @@ def kernel_traffic(kernel, units):
 # r second-round survivors (8 B per point, 12 B per (key, index) pair).
 STAGE_KERNELS = {
     "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n),
-    "filter": ("k2_count + k_binscan", lambda n, s, r: 8.0 * n),
+    "filter": ("k2_count + k_binstart", lambda n, s, r: 8.0 * n),
     "scatter": ("k2_scatter", lambda n, s, r: 8.0 * n + 12.0 * s),
-    "split": ("k3_split + k_group_prefix", lambda n, s, r: 24.0 * s),
+    "split": ("k3_split + k_group_agg_bins", lambda n, s, r: 24.0 * s),
     "sort": ("k3_bucket", lambda n, s, r: 12.0 * s + 12.0 * r),
     "regions": ("k4_compact", lambda n, s, r: 24.0 * r),
     "final": ("k5_final", lambda n, s, r: 12.0 * r),

@@ -74,7 +74,8 @@ enum CounterSlot : int {
   CTR_BIN_SCAN = 5 + kMaxPasses,          // last-block counter of the bin scan
   CTR_BIN_GROUP = 6 + kMaxPasses,         // next group of the bucket sort
   CTR_SPLIT = 7 + kMaxPasses,             // next tile of the coarse-to-fine split
-  kNumCounters = 16,
+  CTR_GROUP_AGG = 8 + kMaxPasses,         // last-block counter of the group aggregates
+  kNumCounters = 17,
 };
 
 struct ExtPartial {

@@ -264,7 +264,7 @@ __device__ __forceinline__ void add_dir(Dir2& a, const RG& g, u64 k) {
 
 
 // The second round run by the pipeline's sort: every group's record holds
-// its exclusive prefix (k_group_agg, k_group_prefix) and receives its kept
+// its exclusive prefix (k_group_agg_bins) and receives its kept
 // counts; kept points are staged in t_* and the last block turns the counts
 // into offsets and fills both ends of the region lists.
 struct Fused {
@@ -944,83 +944,98 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
 
 // Exclusive prefixes of the groups' direction aggregates: a group's
 // aggregate is the combination of the tile aggregates of its bins (tagg,
-// ctiles from k3_split; k_group_agg_bins), then one block gives record g's
-// inclusive words the combination of the aggregates of groups 0 .. g - 1
-// with d(P_0) (the identity).  Thread t takes a contiguous slice of groups.
-constexpr int GP_BLOCK = 1024;
-
-// One warp per group: the aggregates of its bins in every tile of their
-// coarse bins, combined into its record.
+// ctiles from k3_split), one warp per group; then the last block gives
+// record g's inclusive words the combination of the aggregates of groups
+// 0 .. g - 1 with d(P_0) (the identity).
 constexpr int GB_BLOCK = 256;
-__global__ void __launch_bounds__(GB_BLOCK)
-k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
-                 const u64* __restrict__ tagg, const u32* __restrict__ ctiles) {
-  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
-  const u32 ng = plan->ngroups;
-  const RG rg = make_rg(plan);
-  const int lane = threadIdx.x & 31;
-  const u32 g = blockIdx.x * (GB_BLOCK / 32) + (threadIdx.x >> 5);
-  if (g >= ng) return;
-  const u32 b0 = groups[g].y, b1 = groups[g + 1].y;
+constexpr int GB_RB = 4;                   // records a thread loads at once in the scan
+
+// One block: the exclusive scan of the groups' aggregates.  Thread t takes
+// a contiguous slice of groups.
+__device__ void group_prefix_scan(Plan* plan, K4Chunk* recs, u32 ng, const RG& rg) {
+  __shared__ Dir2 s_w[GB_BLOCK / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 per = (ng + GB_BLOCK - 1) / GB_BLOCK;
+  const u32 g0 = min(ng, threadIdx.x * per), g1 = min(ng, g0 + per);
   Dir2 t = rg.ident;
-  for (u32 c = b0 / kFinePerCoarse; c * kFinePerCoarse < b1; ++c) {
-    const u32 lo = max(b0, c * kFinePerCoarse), hi = min(b1, (c + 1) * kFinePerCoarse);
-    const u32 nb = hi - lo, t0 = ctiles[c], ntl = ctiles[c + 1] - t0;
-    for (u32 e = lane; e < nb * ntl; e += 32) {
-      const u32 tile = t0 + e / nb, d = (lo - c * kFinePerCoarse) + e % nb;
-      const u64* w = tagg + (size_t)tile * (2 * kFinePerCoarse) + 2 * d;
-      const u64 wl = w[0], wu = w[1];
-      Dir2 v = rg.ident;
-      if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
-      if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
+  for (u32 gb = g0; gb < g1; gb += GB_RB) {
+    u64 wl[GB_RB], wu[GB_RB];
+    #pragma unroll
+    for (int q = 0; q < GB_RB; ++q) {
+      wl[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_lo) : 0ull;
+      wu[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_up) : 0ull;
+    }
+    #pragma unroll
+    for (int q = 0; q < GB_RB; ++q) {
+      if (gb + q >= g1) break;
+      Dir2 v;
+      unpack_dir(wl[q], v.lx, v.ly);
+      unpack_dir(wu[q], v.ux, v.uy);
       combine(t, v);
     }
   }
-  #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
-  if (lane == 0) {
-    recs[g].agg_lo = pack_dir(t.lx, t.ly);
-    recs[g].agg_up = pack_dir(t.ux, t.uy);
-  }
-}
-
-__global__ void __launch_bounds__(GP_BLOCK)
-k_group_prefix(Plan* plan, K4Chunk* __restrict__ recs) {
-  __shared__ Dir2 s_w[GP_BLOCK / 32];
-  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
-  const u32 ng = plan->ngroups;
-  const RG rg = make_rg(plan);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 per = (ng + GP_BLOCK - 1) / GP_BLOCK;
-  const u32 g0 = min(ng, threadIdx.x * per), g1 = min(ng, g0 + per);
-  Dir2 agg[4];
-  Dir2 t = rg.ident;
-  for (u32 g = g0; g < g1; ++g) {
-    Dir2 v;
-    unpack_dir(recs[g].agg_lo, v.lx, v.ly);
-    unpack_dir(recs[g].agg_up, v.ux, v.uy);
-    if (g - g0 < 4) agg[g - g0] = v;
-    combine(t, v);
-  }
   const Dir2 inc = warp_scan_dir(t);
-  Dir2 lex = shfl_up_dir(inc, 1);
+  const Dir2 lex = shfl_up_dir(inc, 1);
   if (lane == 31) s_w[wid] = inc;
   __syncthreads();
   Dir2 run = rg.ident;
   for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
   if (lane > 0) combine(run, lex);
-  for (u32 g = g0; g < g1; ++g) {
-    recs[g].inc_lo = pack_dir(run.lx, run.ly);
-    recs[g].inc_up = pack_dir(run.ux, run.uy);
-    Dir2 v;
-    if (g - g0 < 4) {
-      v = agg[g - g0];
-    } else {
-      unpack_dir(recs[g].agg_lo, v.lx, v.ly);
-      unpack_dir(recs[g].agg_up, v.ux, v.uy);
+  for (u32 gb = g0; gb < g1; gb += GB_RB) {
+    u64 wl[GB_RB], wu[GB_RB];
+    #pragma unroll
+    for (int q = 0; q < GB_RB; ++q) {
+      wl[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_lo) : 0ull;
+      wu[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_up) : 0ull;
     }
-    combine(run, v);
+    #pragma unroll
+    for (int q = 0; q < GB_RB; ++q) {
+      if (gb + q >= g1) break;
+      recs[gb + q].inc_lo = pack_dir(run.lx, run.ly);
+      recs[gb + q].inc_up = pack_dir(run.ux, run.uy);
+      Dir2 v;
+      unpack_dir(wl[q], v.lx, v.ly);
+      unpack_dir(wu[q], v.ux, v.uy);
+      combine(run, v);
+    }
   }
+}
+
+__global__ void __launch_bounds__(GB_BLOCK)
+k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
+                 const u64* __restrict__ tagg, const u32* __restrict__ ctiles) {
+  __shared__ bool s_last;
+  if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
+  const u32 ng = plan->ngroups;
+  const RG rg = make_rg(plan);
+  const int lane = threadIdx.x & 31;
+  const u32 g = blockIdx.x * (GB_BLOCK / 32) + (threadIdx.x >> 5);
+  if (g < ng) {
+    const u32 b0 = groups[g].y, b1 = groups[g + 1].y;
+    Dir2 t = rg.ident;
+    for (u32 c = b0 / kFinePerCoarse; c * kFinePerCoarse < b1; ++c) {
+      const u32 lo = max(b0, c * kFinePerCoarse), hi = min(b1, (c + 1) * kFinePerCoarse);
+      const u32 nb = hi - lo, t0 = ctiles[c], ntl = ctiles[c + 1] - t0;
+      for (u32 e = lane; e < nb * ntl; e += 32) {
+        const u32 tile = t0 + e / nb, d = (lo - c * kFinePerCoarse) + e % nb;
+        const u64* w = tagg + (size_t)tile * (2 * kFinePerCoarse) + 2 * d;
+        const u64 wl = w[0], wu = w[1];
+        Dir2 v = rg.ident;
+        if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
+        if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
+        combine(t, v);
+      }
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
+    if (lane == 0) {
+      recs[g].agg_lo = pack_dir(t.lx, t.ly);
+      recs[g].agg_up = pack_dir(t.ux, t.uy);
+    }
+  }
+  // The last block to finish scans the aggregates.
+  if (!last_block(plan, CTR_GROUP_AGG, &s_last)) return;
+  group_prefix_scan(plan, recs, ng, rg);
 }
 
 // Per-bin prefix over the histogram rows (one per K2 block): row r, bin b
@@ -1328,7 +1343,6 @@ cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, con
   K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
   k_group_agg_bins<<<(kBins + GB_BLOCK / 32 - 1) / (GB_BLOCK / 32), GB_BLOCK, 0, st>>>(plan, R, groups, tagg,
                                                                                       ctiles);
-  k_group_prefix<<<1, GP_BLOCK, 0, st>>>(plan, R);
   return cudaGetLastError();
 }
 
