@@ -927,17 +927,19 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
         flag_error(plan, ERR_INTERNAL);
       }
     }
-    // One warp per bin: the tile's aggregates of the bin (plain stores; a
-    // word without its valid bit holds nothing).
-    for (u32 d = wid; d < (u32)kFinePerCoarse; d += SP_WARPS) {
+    // Half a warp per bin: the tile's aggregates of the bin (plain stores;
+    // a word without its valid bit holds nothing).
+    static_assert(2 * SP_WARPS == kFinePerCoarse, "two bins per warp");
+    {
+      const u32 d = 2 * wid + (lane >> 4), h = lane & 15;
       const u32 a = s_lst[d], b = s_lst[d + 1];
       Dir2 v = rg.ident;
-      for (u32 j = a + lane; j < b; j += 32) add_dir(v, rg, s_key[j]);
+      for (u32 j = a + h; j < b; j += 16) add_dir(v, rg, s_key[j]);
       #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
+      for (int o = 8; o > 0; o >>= 1) combine(v, shfl_xor_dir(v, o));
       u64* w = tagg + (size_t)t * (2 * kFinePerCoarse) + 2 * d;
-      if (lane == 0) w[0] = (v.lx != rg.ident.lx || v.ly != rg.ident.ly) ? pack_dir(v.lx, v.ly) : 0ull;
-      if (lane == 1) w[1] = (v.ux != rg.ident.ux || v.uy != rg.ident.uy) ? pack_dir(v.ux, v.uy) : 0ull;
+      if (h == 0) w[0] = (v.lx != rg.ident.lx || v.ly != rg.ident.ly) ? pack_dir(v.lx, v.ly) : 0ull;
+      if (h == 1) w[1] = (v.ux != rg.ident.ux || v.uy != rg.ident.uy) ? pack_dir(v.ux, v.uy) : 0ull;
     }
   }
 }
