@@ -197,6 +197,9 @@ __device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, u32 b
       ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
 }
 // Asynchronous global -> shared copies (no registers held while in flight).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem_dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(src) : "memory");
 }

@@ -73,6 +73,7 @@ struct BucketSmem {
   __align__(16) u64 ninc[2];   // its exclusive prefix words (lower, upper)
   uint2 nab[2];            // groups[id], groups[id + 1]
   u32 nid;                 // its id (>= the group count: none)
+  u32 nerr;                // the plan's error word, fetched with it
 };
 
 // Shared-memory slot of sorted position i: the low five bits are XORed
@@ -230,6 +231,7 @@ __device__ __forceinline__ u32 sub_of(const SubMap& f, u64 off) {
 // split line P_0 -> P_l and of the directions d(p) = p - P_l.
 struct RG {
   int x0, y0, ax, ay, bx, by, ux, uy;
+  int dx0, dy0;           // key origin minus P_l
   u32 ybits;
   u64 ymask;
   Dir2 ident;
@@ -243,6 +245,7 @@ __device__ __forceinline__ RG make_rg(const Plan* plan) {
   g.ax = plan->ext_x[0]; g.ay = plan->ext_y[0];     // P_0 = P_minx
   g.bx = plan->ext_x[1]; g.by = plan->ext_y[1];     // P_l = P_maxx
   g.ux = g.bx - g.ax; g.uy = g.by - g.ay;
+  g.dx0 = g.x0 - g.bx; g.dy0 = g.y0 - g.by;
   g.ident = {g.ax - g.bx, g.ay - g.by, g.ax - g.bx, g.ay - g.by};
   return g;
 }
@@ -255,11 +258,20 @@ __device__ __forceinline__ int decode_side(const RG& g, u64 k, int& px, int& py)
   return o < 0 ? -1 : (o > 0 ? 1 : 0);
 }
 
+// Direction d = p - P_l of a key's point, and its region: the sign of
+// cross(P_l - P_0, d), which equals cross(P_l - P_0, p - P_0) (the same
+// value as decode_side's, without decoding p).
+__device__ __forceinline__ long long key_dir(const RG& g, u64 k, int& vx, int& vy) {
+  vx = (int)(u32)(k >> g.ybits) + g.dx0;
+  vy = (int)(u32)(k & g.ymask) + g.dy0;
+  return cross2(g.ux, g.uy, vx, vy);
+}
+
 __device__ __forceinline__ void add_dir(Dir2& a, const RG& g, u64 k) {
-  int px, py;
-  const int sd = decode_side(g, k, px, py);
-  if (sd < 0) cmax(a.lx, a.ly, px - g.bx, py - g.by);
-  else if (sd > 0) cmin(a.ux, a.uy, px - g.bx, py - g.by);
+  int vx, vy;
+  const long long o = key_dir(g, k, vx, vy);
+  if (o < 0) cmax(a.lx, a.ly, vx, vy);
+  else if (o > 0) cmin(a.ux, a.uy, vx, vy);
 }
 
 
@@ -353,15 +365,14 @@ __device__ void scan_piece(BucketSmem& S, const Fused& F, u32 m, u32 slot0, u32 
       const u32 j = pb + q - p0;
       if (pb + q >= p1) break;
       if ((smask >> j) & 1u) lsb = loc;
-      int px, py;
-      const int sd = decode_side(rg, kq[q], px, py);
-      const int vx = px - rg.bx, vy = py - rg.by;
-      if (sd < 0) {
+      int vx, vy;
+      const long long o = key_dir(rg, kq[q], vx, vy);
+      if (o < 0) {
         if (cross2(lsb.lx, lsb.ly, vx, vy) > 0) {
           cand |= 1u << j;
           if (cross2(loc.lx, loc.ly, vx, vy) > 0) { loc.lx = vx; loc.ly = vy; }
         }
-      } else if (sd > 0) {
+      } else if (o > 0) {
         if (cross2(lsb.ux, lsb.uy, vx, vy) < 0) {
           cand |= 1u << j;
           if (cross2(loc.ux, loc.uy, vx, vy) < 0) { loc.ux = vx; loc.uy = vy; }
@@ -446,11 +457,15 @@ __device__ __forceinline__ void start_group(BucketSmem& S) {
 
 // Thread 0: starts the asynchronous fetch of group g's descriptor (its
 // first position and bin, the next group's, and with DECIDE its prefix)
-// into S.nab / S.ninc, and records g in S.nid.
+// into S.nab / S.ninc, with the plan's error word (a block stops claiming
+// once a group needs the radix passes; nothing depends on seeing it at
+// once), and records g in S.nid.
 template <bool DECIDE>
-__device__ __forceinline__ void fetch_group(BucketSmem& S, const Fused& F, const uint2* groups, u32 g, u32 ng) {
+__device__ __forceinline__ void fetch_group(BucketSmem& S, const Fused& F, const uint2* groups, u32 g, u32 ng,
+                                            const Plan* plan) {
   S.nid = g;
   if (g >= ng) return;
+  cp_async4(&S.nerr, &plan->error);
   cp_async8(&S.nab[0], &groups[g]);
   cp_async8(&S.nab[1], &groups[g + 1]);
   if (DECIDE) cp_async16(&S.ninc[0], &F.recs[g].inc_lo);
@@ -717,13 +732,14 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
                 "prefix words fetched as one 16-byte copy");
   u32 g_next = 0;
   if (threadIdx.x == 0) {
-    fetch_group<DECIDE>(S, F, groups, atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u), ng);
+    S.nerr = 0u;
+    fetch_group<DECIDE>(S, F, groups, atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u), ng, plan);
     g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
   }
   for (;;) {
     if (threadIdx.x == 0) {
       cp_async_wait_all();
-      const u32 g = (ld_volatile_u32(&plan->error) & ERR_FALLBACK) ? ng : min(S.nid, ng);
+      const u32 g = (S.nerr & ERR_FALLBACK) ? ng : min(S.nid, ng);
       S.misc[1] = g;
       if (DECIDE && g < ng) start_group(S);
     }
@@ -733,7 +749,7 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
     __syncthreads();
     if (g >= ng) break;
     if (threadIdx.x == 0) {
-      fetch_group<DECIDE>(S, F, groups, g_next, ng);
+      fetch_group<DECIDE>(S, F, groups, g_next, ng, plan);
       if (g_next < ng) g_next = atomicAdd(&plan->ctr[CTR_BIN_GROUP], 1u);
     }
     const u32 m = b.x - a.x;
