@@ -100,6 +100,20 @@ hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t 
 hull_status hull_compute_host(hull_ctx *ctx, const int32_t *h_xy, int64_t n, int32_t *h_out,
                               int64_t cap, int64_t *h_count, void *stream);
 
+/* Several independent hulls from device buffers in one call: for k in
+ * [0, count), d_xy[k] (device int32[n[k]][2], 8-byte aligned) and d_out[k]
+ * (device int32[cap[k]]) as in hull_compute; h_count[k] receives the hull
+ * size.  The hulls run back to back on `stream` with one synchronisation at
+ * the end (an input whose bucket sort needs the radix passes is rerun
+ * afterwards, alone).  Returns the first failing input's status (every
+ * other input is still computed; h_count as hull_compute sets it).  With
+ * profiling on (hull_set_profiling) the inputs run one call at a time.
+ * count = 0 does nothing.  Errors: those of hull_compute; EINVAL for
+ * count < 0 or NULL arrays. */
+hull_status hull_compute_multi(hull_ctx *ctx, int32_t count, const int32_t *const *d_xy,
+                               const int64_t *n, int32_t *const *d_out, const int64_t *cap,
+                               int64_t *h_count, void *stream);
+
 /* Several independent hulls from host buffers in one call, pipelined: while
  * the hull of input k is computed on `stream`, input k + 1 is copied to a
  * second device staging buffer on the context's copy stream (inputs should

@@ -95,6 +95,8 @@ struct hull_ctx {
   int occ_k2b = 1, occ_kb = 1, occ_sp = 1;  // bucket sort: K2 with bin rows, group sort, split
   Plan* plan = nullptr;        // device
   Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
+  char* h_multi = nullptr;     // pinned summaries of hull_compute_multi (one per input)
+  int32_t h_multi_cap = 0;
   Workspace ws;
   HostStage hs;
   hull_stats last{};
@@ -251,12 +253,18 @@ int grid_for(int occ, int num_sms, size_t work_tiles) {
 // `fallback`, a bucket sort that met a bin too large for it (ERR_FALLBACK,
 // no other error) sets *fallback and returns HULL_OK without recording
 // anything: the caller reruns the call on the radix passes.
+hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback);
+
 hull_status finish(hull_ctx* c, cudaStream_t st, bool* fallback = nullptr) {
   cudaError_t e = cudaMemcpyAsync(c->h_plan, c->plan, kSummaryBytes, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
-  const Plan& p = *c->h_plan;
+  return read_summary(c, *c->h_plan, fallback);
+}
+
+// The bookkeeping of finish() for one call's summary `p` (already on the host).
+hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
   if (fallback) {
     *fallback = (p.error & ERR_FALLBACK) != 0 && (p.error & (ERR_RANGE | ERR_TIMEOUT)) == 0;
     if (*fallback) return HULL_OK;
@@ -588,6 +596,7 @@ void hull_destroy(hull_ctx* c) {
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->plan) cudaFree(c->plan);
   if (c->h_plan) cudaFreeHost(c->h_plan);
+  if (c->h_multi) cudaFreeHost(c->h_multi);
   delete c;
 }
 
@@ -627,6 +636,78 @@ hull_status hull_compute(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d
     return r;
   }
   return r;
+}
+
+hull_status hull_compute_multi(hull_ctx* c, int32_t count, const int32_t* const* d_xy, const int64_t* n,
+                               int32_t* const* d_out, const int64_t* cap, int64_t* h_count, void* stream) {
+  if (!c || count < 0) return HULL_EINVAL;
+  if (count == 0) return HULL_OK;
+  if (!d_xy || !n || !d_out || !cap || !h_count) return HULL_EINVAL;
+  int64_t nmax = 1;
+  for (int32_t k = 0; k < count; ++k) {
+    h_count[k] = 0;
+    if (n[k] < 0 || cap[k] < 0 || n[k] > (int64_t)kMaxN || (n[k] > 0 && (!d_xy[k] || !aligned8(d_xy[k]))) ||
+        (cap[k] > 0 && !d_out[k]))
+      return HULL_EINVAL;
+    nmax = n[k] > nmax ? n[k] : nmax;
+  }
+  // Stage events are per call: with profiling on, one call after another.
+  if (c->prof) {
+    for (int32_t k = 0; k < count; ++k) {
+      const hull_status r = hull_compute(c, d_xy[k], n[k], d_out[k], cap[k], &h_count[k], stream);
+      if (r != HULL_OK) return r;
+    }
+    return HULL_OK;
+  }
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)nmax);
+  if (r != HULL_OK) return r;
+  if (c->h_multi_cap < count) {
+    if (c->h_multi) cudaFreeHost(c->h_multi);
+    c->h_multi = nullptr;
+    c->h_multi_cap = 0;
+    if (cudaMallocHost(&c->h_multi, (size_t)count * kSummaryBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return HULL_ENOMEM;
+    }
+    c->h_multi_cap = count;
+  }
+  // Every input's bucket-sort hull queued back to back, each summary copied
+  // to its own slot; one synchronisation.
+  for (int32_t k = 0; k < count; ++k) {
+    if (n[k] == 0) continue;
+    c->prof_pending = false;
+    r = run_front(c, d_xy[k], (u32)n[k], st, true);
+    if (r == HULL_OK) r = run_final(c, c->ws.lo_xy, c->ws.lo_idx, c->ws.up_xy, c->ws.up_idx, (size_t)n[k], d_out[k],
+                                    cap[k], st);
+    if (r != HULL_OK) return r;
+    const cudaError_t e = cudaMemcpyAsync(c->h_multi + (size_t)k * kSummaryBytes, c->plan, kSummaryBytes,
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  hull_status first = HULL_OK;
+  for (int32_t k = 0; k < count; ++k) {
+    if (n[k] == 0) {
+      if (c->cfg.collect_stats) c->last = hull_stats{};
+      continue;
+    }
+    bool fallback = false;
+    const Plan& p = *reinterpret_cast<const Plan*>(c->h_multi + (size_t)k * kSummaryBytes);
+    r = read_summary(c, p, &fallback);
+    if (fallback) {
+      // A bin too large for the bucket sort: this input again, as
+      // hull_compute does (the radix passes after the bucket attempt).
+      r = hull_compute(c, d_xy[k], n[k], d_out[k], cap[k], &h_count[k], stream);
+    } else {
+      if (c->cfg.collect_stats) c->last.sort_fallback = 0;
+      if (r == HULL_OK || r == HULL_ECAPACITY) h_count[k] = p.h;
+    }
+    if (r != HULL_OK && first == HULL_OK) first = r;
+  }
+  return first;
 }
 
 hull_status hull_stage_regions(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_lower,

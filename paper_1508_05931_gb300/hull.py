@@ -63,6 +63,7 @@ _sig = {
     "hull_compute": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_compute_host": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_compute_host_multi": ([_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "hull_compute_multi": ([_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "hull_compute_batched": ([_P, _P, _P, ctypes.c_int32, _P, _I64, _P, _P], ctypes.c_int),
     "hull_compute_noalloc": ([_P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
     "hull_last_stats": ([_P, ctypes.POINTER(hull_stats)], ctypes.c_int),
@@ -212,6 +213,23 @@ class Context:
         _check(_lib.hull_compute_host(self._h, sp, n, op, out.shape[0], ctypes.byref(cnt),
                                       _stream_handle(stream)), "hull_compute_host")
         return out[: cnt.value]
+
+    def compute_multi(self, pts_list, outs, stream=None) -> list:
+        """Hulls of several device point sets (int32 (n, 2) CUDA tensors)
+        into the device tensors `outs`, back to back with one
+        synchronisation; see hull_compute_multi.  Returns one index tensor
+        (a view of outs[i]) per input."""
+        k = len(pts_list)
+        if len(outs) != k:
+            raise ValueError("one output per input")
+        arr_p = (ctypes.c_void_p * max(k, 1))(*[int(t.data_ptr()) for t in pts_list])
+        arr_n = (ctypes.c_int64 * max(k, 1))(*[t.shape[0] for t in pts_list])
+        arr_o = (ctypes.c_void_p * max(k, 1))(*[int(o.data_ptr()) for o in outs])
+        arr_c = (ctypes.c_int64 * max(k, 1))(*[o.numel() for o in outs])
+        arr_h = (ctypes.c_int64 * max(k, 1))()
+        _check(_lib.hull_compute_multi(self._h, k, arr_p, arr_n, arr_o, arr_c, arr_h, _stream_handle(stream)),
+               "hull_compute_multi")
+        return [outs[i][: arr_h[i]] for i in range(k)]
 
     def compute_host_multi(self, pts_list, outs=None, stream=None) -> list:
         """Hulls of several host point sets (numpy arrays or CPU tensors,
@@ -465,4 +483,5 @@ hull_stage_sort = _lib.hull_stage_sort
 hull_stage_bucket_sort = _lib.hull_stage_bucket_sort
 hull_stage_second_round = _lib.hull_stage_second_round
 hull_stage_regions = _lib.hull_stage_regions
+hull_compute_multi = _lib.hull_compute_multi
 hull_stage_chain = _lib.hull_stage_chain

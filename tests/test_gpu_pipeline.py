@@ -149,6 +149,38 @@ def test_unaligned_input_view(ctx):
     assert ctx.compute(view).cpu().numpy().tolist() == oracle.hull(pts[1:]).tolist()
 
 
+def test_device_multi_entry_point(ctx, hull_lib):
+    """Several device inputs back to back with one synchronisation: every
+    result equals the oracle's, including an input the bucket sort hands to
+    the radix passes, an empty one and a one-point one; a too-small output
+    fails that input alone with a capacity error."""
+    rng = np.random.default_rng(21)
+    sets = [W.uniform_square(300_000, 1 << 29, 31), W.uniform_disk(200_000, 2.0 ** 29, 32),
+            np.full((20000, 2), 5, np.int32), np.zeros((0, 2), np.int32), np.array([[3, 4]], np.int32),
+            rng.integers(-40, 41, size=(50_000, 2)).astype(np.int32), W.near_circle(100_000, 2.0 ** 20, 33)]
+    ts = [dev(p) for p in sets]
+    outs = [torch.empty(max(len(p), 1), dtype=torch.int32, device="cuda") for p in sets]
+    res = ctx.compute_multi(ts, outs)
+    for p, h in zip(sets, res):
+        assert h.cpu().numpy().tolist() == oracle.hull(p).tolist()
+    small = [torch.empty(len(p) if i != 1 else 3, dtype=torch.int32, device="cuda").fill_(-1)
+             for i, p in enumerate(sets[:3])]
+    with pytest.raises(hull_lib.HullError) as ei:
+        ctx.compute_multi(ts[:3], small)
+    assert ei.value.code == hull_lib.HULL_ECAPACITY
+    assert small[0][: len(oracle.hull(sets[0]))].cpu().numpy().tolist() == oracle.hull(sets[0]).tolist()
+    assert small[2][:1].cpu().numpy().tolist() == oracle.hull(sets[2]).tolist()
+    assert (small[1].cpu().numpy() == -1).all()
+    # With the stage events on, the same results one call at a time.
+    ctx.set_profiling(True)
+    try:
+        res = ctx.compute_multi(ts, outs)
+    finally:
+        ctx.set_profiling(False)
+    for p, h in zip(sets, res):
+        assert h.cpu().numpy().tolist() == oracle.hull(p).tolist()
+
+
 def test_host_entry_point(ctx):
     pts = W.uniform_disk(500_000, 2.0 ** 29, 8)
     pinned = torch.as_tensor(pts).pin_memory()
