@@ -209,6 +209,17 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Bulk prefetch into L2 of elements [lo, hi) of an array of `esz`-byte
+// elements, widened to 16-byte boundaries (the allocation must extend 16
+// bytes past element hi) and cut to `cap` bytes.
+__device__ __forceinline__ void prefetch_span_l2(const void* base, u32 lo, u32 hi, u32 esz, u32 cap) {
+  if (hi <= lo) return;
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)lo * esz) & ~(uintptr_t)15;
+  const uintptr_t b = (reinterpret_cast<uintptr_t>(base) + (uintptr_t)hi * esz + 15) & ~(uintptr_t)15;
+  const u32 bytes = (u32)min((uintptr_t)cap, b - a) & ~15u;
+  if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+}
+
 // Read-only loads with an L2 eviction policy.
 __device__ __forceinline__ u64 ld_hint_u64(const u64* p, u64 pol) {
   u64 v;

@@ -764,6 +764,13 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
     if (m <= (u32)kGroupCap) {
       if (m > 0) {
         const bool binned = sort_into_smem<true>(S, ak, av, a.x, m, klo, span_top(b.y - a.y, fshift), plan, DECIDE);
+        if (threadIdx.x == 0) {      // the next group's pairs into L2 (its descriptor has arrived)
+          cp_async_wait_all();
+          if (S.nid < ng) {
+            prefetch_span_l2(ak, S.nab[0].x, S.nab[1].x, sizeof(u64), 16u * kGroupCap);
+            prefetch_span_l2(av, S.nab[0].x, S.nab[1].x, sizeof(u32), 8u * kGroupCap);
+          }
+        }
         if (DECIDE) scan_piece(S, F, m, a.x, s, rg, plan, binned, klo);
         else write_out(S, bk, bv, a.x, m);
       }
