@@ -16,6 +16,9 @@ closed forms and invariants.  Pinning status per function:
 * ``sort_survivors``  pinned (numpy lexsort; a library primitive)
 * ``second_round``    pinned (triangle witnesses, hull superset, Section
                       2.2.3's worked P_temp trace)
+* ``second_round_reverse`` pinned (triangle witnesses, hull superset, subset of
+                      the forward survivors, convex chains kept whole, a
+                      hand-derived trace)
 * ``chain``           pinned (brute force on sorted input)
 * the learned-proposal MLP (``oracle.mlp``) is pinned by finite differences
   and a closed-form tiny network.
@@ -73,6 +76,8 @@ def _load():
     lib.oracle_quad_filter.restype = I64
     lib.oracle_second_round.argtypes = [P, I64, P, P, P, P, P]
     lib.oracle_second_round.restype = ctypes.c_int
+    lib.oracle_second_round_reverse.argtypes = [P, I64, ctypes.c_int, P, P]
+    lib.oracle_second_round_reverse.restype = ctypes.c_int
     lib.oracle_sort_xyi.argtypes = [P, I64]
     lib.oracle_sort_xyi.restype = None
     _lib = lib
@@ -166,6 +171,24 @@ def second_round(xy, sorted_idx):
     return (sidx[lo_pos].astype(np.int32), sidx[up_pos].astype(np.int32), int(lp.value))
 
 
+def second_round_reverse(xy, p0, region, pl, sign: int) -> np.ndarray:
+    """The second round mirrored over one region's forward survivors (the
+    reverse pass of Figure 2, Section 2.2, applied to its own output): the
+    list P_0 (input index p0), `region` (input indices in sorted order), P_l
+    (index pl) is walked from P_l back toward P_0 with P_0 as the anchor; a
+    point is kept when it lies strictly below (sign = +1, lower region) or
+    above (sign = -1, upper) the line from the running P_temp (initially P_l)
+    to P_0, and then becomes P_temp.  Returns the kept input indices in
+    sorted order."""
+    a = _pts(xy)
+    seq = np.concatenate([[p0], np.asarray(region, dtype=np.int64), [pl]]).astype(np.int64)
+    lst = np.ascontiguousarray(a[seq])
+    keep = np.empty(max(len(seq), 1), dtype=np.int32)
+    nk = ctypes.c_int64()
+    _load().oracle_second_round_reverse(_ptr(lst), len(seq), int(sign), _ptr(keep), ctypes.byref(nk))
+    return seq[keep[: nk.value]].astype(np.int32)
+
+
 def chain(xy_seq, sign: int) -> np.ndarray:
     """Stack-based monotone chain (Section 2.1 step 8, Section 5.2) over a
     sequence of points given in lexicographic order; sign +1 = lower chain,
@@ -179,10 +202,13 @@ def chain(xy_seq, sign: int) -> np.ndarray:
     return out[:h].copy()
 
 
-def gscan_stages(xy):
+def gscan_stages(xy, reverse: bool = False):
     """The method's stages in the paper's order (Section 2.1 steps 1-8),
     each computed by the functions above.  Returns a dict of intermediates
-    and the final CCW hull built from the second-round survivors."""
+    and the final CCW hull built from the second-round survivors; with
+    `reverse`, the mirrored second round also runs over both regions
+    (keys lower_fwd / upper_fwd keep the forward survivors) and the hull is
+    built from its survivors."""
     a = _pts(xy)
     n = a.shape[0]
     out = {"n": n}
@@ -202,6 +228,11 @@ def gscan_stages(xy):
         out["hull"] = srt[:1].copy()
         return out
     p0, pl = int(srt[0]), int(srt[lpos])
+    if reverse:
+        out["lower_fwd"], out["upper_fwd"] = lo, up
+        lo = second_round_reverse(a, p0, lo, pl, +1)
+        up = second_round_reverse(a, p0, up, pl, -1)
+        out["lower"], out["upper"] = lo, up
     lo_seq = np.concatenate([[p0], lo, [pl]]).astype(np.int64)
     up_seq = np.concatenate([[p0], up, [pl]]).astype(np.int64)
     lc = lo_seq[chain(a[lo_seq], +1)]

@@ -223,6 +223,39 @@ int oracle_second_round(const int32_t *xyi, int64_t m, int32_t *lo, int64_t *n_l
     return 0;
 }
 
+/* The second round mirrored (the reverse pass of Figure 2 applied to its
+ * own survivors): p[0..m) is a region list -- P_0, the region's survivors
+ * of the forward pass in sorted order, P_l.  The walk goes from P_l back
+ * toward P_0 with P_0 as the anchor and a running P_temp that starts at
+ * P_l; p[i] is kept when orient(P_temp, P_0, p[i]) is strictly positive
+ * (lower region, sgn = +1: strictly below the line from P_temp to P_0) or
+ * strictly negative (upper region, sgn = -1), and then becomes P_temp.  It
+ * is Figure 2 on the point set reflected through x -> -x, where P_l is the
+ * first point and P_0 the last (a reflection flips orient's sign).
+ * keep[] receives the kept positions among 1 .. m - 2 in ascending order. */
+int oracle_second_round_reverse(const int32_t *xy, int64_t m, int sgn, int32_t *keep, int64_t *n_keep)
+{
+    *n_keep = 0;
+    if (m < 3) return 0;
+    const int32_t *p0 = &xy[0];
+    int64_t t = m - 1;
+    int64_t k = 0;
+    for (int64_t i = m - 2; i >= 1; --i) {
+        const int32_t *pt = &xy[2 * t], *pi = &xy[2 * i];
+        const int64_t o = ((int64_t)p0[0] - pt[0]) * ((int64_t)pi[1] - pt[1]) -
+                          ((int64_t)p0[1] - pt[1]) * ((int64_t)pi[0] - pt[0]);
+        if ((sgn > 0 && o > 0) || (sgn < 0 && o < 0)) {
+            keep[k++] = (int32_t)i;
+            t = i;
+        }
+    }
+    for (int64_t a = 0, b = k - 1; a < b; ++a, --b) {
+        const int32_t v = keep[a]; keep[a] = keep[b]; keep[b] = v;
+    }
+    *n_keep = k;
+    return 0;
+}
+
 /* Stable sort of (x, y, idx) triples by (x, y, idx); used for the sort stage. */
 void oracle_sort_xyi(int32_t *xyi, int64_t m)
 {

@@ -303,6 +303,83 @@ def test_second_round_is_safe_with_witnesses():
             assert any(_in_closed_triangle(p, A, pts[w], B) for w in wit), (t, i)
 
 
+def test_second_round_reverse_golden_trace():
+    """The mirrored second round on the hand-made points of Section 2.2.3's
+    trace (tests/golden/second_round_reverse_trace.json, derived by hand)."""
+    with open(os.path.join(GOLDEN, "second_round_reverse_trace.json")) as f:
+        g = json.load(f)
+    names, P, perm = g["names"], g["points"], g["index_permutation"]
+    pts = np.zeros((len(P), 2), np.int32)
+    for k, j in enumerate(perm):
+        pts[j] = P[k]
+    name_of = {perm[k]: names[k] for k in range(len(names))}
+    idx_of = {v: k for k, v in name_of.items()}
+    st = oracle.gscan_stages(pts, reverse=True)
+    assert [name_of[i] for i in st["lower_fwd"]] == g["forward_lower_kept"]
+    assert [name_of[i] for i in st["upper_fwd"]] == g["forward_upper_kept"]
+    assert [name_of[i] for i in st["lower"]] == g["expected_lower_reverse"]
+    assert [name_of[i] for i in st["upper"]] == g["expected_upper_reverse"]
+    assert [name_of[i] for i in st["hull"]] == g["expected_hull_ccw"]
+    lo = oracle.second_round_reverse(pts, idx_of["P0"], [idx_of[q] for q in g["forward_lower_kept"]], idx_of["Pl"], +1)
+    assert [name_of[i] for i in lo] == g["expected_lower_reverse"]
+
+
+def test_second_round_reverse_is_safe_with_witnesses():
+    """The mirrored second round keeps a subset of the forward survivors that
+    still holds every strict hull vertex, and every point it removes lies in
+    the closed triangle (P_0, P_temp, P_l), P_temp being the nearest kept
+    point after it in sorted order (or P_l)."""
+    rng = np.random.default_rng(31)
+    for t in range(200):
+        n = int(rng.integers(3, 60))
+        pts = rand_tiny(rng, n, int(rng.choice([3, 8, 1000, 1 << 29])))
+        srt = oracle.sort_survivors(pts, np.arange(n))
+        lo, up, lpos = oracle.second_round(pts, srt)
+        if lpos < 0:
+            continue
+        p0, pl = int(srt[0]), int(srt[lpos])
+        hv = set(brute_hull(pts))
+        for region, sign in ((lo, +1), (up, -1)):
+            rev = oracle.second_round_reverse(pts, p0, region, pl, sign)
+            assert set(rev.tolist()) <= set(region.tolist())
+            pos = {int(j): k for k, j in enumerate(region)}
+            assert [pos[int(j)] for j in rev] == sorted(pos[int(j)] for j in rev)
+            kept = set(rev.tolist())
+            for k, j in enumerate(region):
+                j = int(j)
+                if j in kept:
+                    continue
+                assert j not in hv, (t, j)
+                later = [int(q) for q in region[k + 1:] if int(q) in kept]
+                T = later[0] if later else pl
+                assert _in_closed_triangle(pts[j], pts[p0], pts[T], pts[pl]), (t, j)
+
+
+def test_second_round_reverse_keeps_convex_chains():
+    """On points in strictly convex position every forward survivor is a hull
+    vertex, and the mirrored pass keeps them all."""
+    par = W.parabola_lattice(1 << 10)
+    rng = np.random.default_rng(32)
+    for pts in (par, par[rng.permutation(len(par))]):
+        st = oracle.gscan_stages(pts, reverse=True)
+        assert st["lower"].tolist() == st["lower_fwd"].tolist()
+        assert st["upper"].tolist() == st["upper_fwd"].tolist()
+        assert len(st["lower"]) == len(pts) - 2
+
+
+def test_method_with_reverse_equals_definition():
+    """Both second rounds, then the stack scan, give exactly the hull."""
+    rng = np.random.default_rng(33)
+    for t in range(300):
+        n = int(rng.integers(0, 200))
+        pts = rand_tiny(rng, n, int(rng.choice([1, 3, 20, 1 << 29])))
+        assert oracle.gscan_stages(pts, reverse=True)["hull"].tolist() == oracle.hull(pts).tolist()
+    for f in (lambda: W.uniform_square(200000, 1 << 29, 41), lambda: W.uniform_disk(200000, 2.0 ** 29, 42),
+              lambda: W.near_circle(100000, 2.0 ** 20, 43), lambda: W.gaussian_clusters(100000, 44)):
+        pts = f()
+        assert oracle.gscan_stages(pts, reverse=True)["hull"].tolist() == oracle.hull(pts).tolist()
+
+
 def test_method_equals_definition():
     """Sections 2.2.2 and 5.2: the two filtering rounds followed by the stack
     scan give exactly the hull of all points."""
