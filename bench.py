@@ -275,6 +275,27 @@ def _time_hulls(ctx, t, out, stream, torch, k):
     return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], st["learned_used"]
 
 
+def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
+    """The mirrored second round (opt-in, hull_config.reverse_round) against
+    the paper's single second round: ms per hull and second-round survivors
+    r on the two 20M sets and the 4M near-circle ring (many near-hull
+    points: the case the extra round was aimed at)."""
+    from paper_1508_05931_gb300 import workloads as W
+    ring = torch.as_tensor(W.adversarial_ring()).cuda()
+    ring_out = torch.empty(ring.shape[0], dtype=torch.int32, device="cuda")
+    cases = [("square_20M", dev_sets[0], dev_outs[0]), ("disk_20M", dev_sets[1], dev_outs[1]),
+             ("near_circle_4M", ring, ring_out)]
+    res = {}
+    for rev in (False, True):
+        with hull.Context(torch.cuda.current_device(), collect_stats=True, reverse_round=rev) as c:
+            for name, t, o in cases:
+                ms, _, _ = _time_hulls(c, t, o, stream, torch, 5)
+                st = c.last_stats()
+                res.setdefault(name, {})["on" if rev else "off"] = {"ms": ms, "r": st["r_lower"] + st["r_upper"],
+                                                                   "h": st["h"]}
+    return res
+
+
 def bench_learned(hull, torch, stream, args):
     """Learned filter proposal vs the plain quadrilateral on the anisotropic
     families at 20M points (single hull) and as a 1,024-instance batch of the
@@ -485,6 +506,8 @@ def main():
         line["batched"] = bench_batched(hull, torch, stream, value, args)
     if world == 1 and not args.no_learned:
         line["learned"] = bench_learned(hull, torch, stream, args)
+    if world == 1 and not args.no_batched:
+        line["reverse_round"] = bench_reverse_round(hull, torch, stream, dev_sets, dev_outs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -60,6 +60,12 @@ typedef struct {
   int autotune;       /* 1 = time the batched kernel's block sizes per size bucket on first
                          use and cache the choice (file: $GBHULL_AUTOTUNE_CACHE, else
                          ~/.cache/gbhull_autotune.json); 0 = built-in defaults */
+  int reverse_round;  /* 1 = after the second round (Section 2.2, Figure 2) run it mirrored
+                         over each region's survivors -- walked from P_maxx back to P_minx
+                         with P_minx as the anchor -- before the final chain (hull_compute,
+                         hull_compute_multi, hull_compute_host*, hull_stage_regions; the
+                         hull is the same, r_lower / r_upper count the points it keeps);
+                         0 = the paper's single second round */
 } hull_config;
 
 typedef struct {

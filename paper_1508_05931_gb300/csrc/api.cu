@@ -353,6 +353,11 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e);
 #endif
+    if (c->cfg.reverse_round) {
+      e = launch_k4_reverse(c->plan, w.lo_xy, w.lo_idx, w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1],
+                            w.h_idx[1], st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     mark(c, 3 + kMaxPasses, st);
     return HULL_OK;
   } else {
@@ -372,6 +377,9 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   e = launch_k4(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.st_region, t4, w.lo_xy, w.lo_idx,
                 w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
                 grid_for(c->occ_k4, c->num_sms, t4), st);
+  if (e == cudaSuccess && c->cfg.reverse_round)
+    e = launch_k4_reverse(c->plan, w.lo_xy, w.lo_idx, w.up_xy, w.up_idx, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1],
+                          st);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(c, 3 + kMaxPasses, st);
   return HULL_OK;

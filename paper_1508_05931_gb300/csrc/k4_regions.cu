@@ -272,6 +272,162 @@ cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib
   return cudaGetLastError();
 }
 
+// The mirrored second round (Section 2.2, Figure 2 reflected through
+// x -> -x) over both region lists, one block each: L[0] = P_0, L[1..m] the
+// forward survivors in sorted order, L[m + 1] = P_l.  The walk goes from
+// P_l back to P_0 with directions d = p - P_0 (a half-plane: a total order
+// under the cross product); a point is kept when its direction is strictly
+// clockwise (lower region) / counter-clockwise (upper) of the running
+// extreme, which starts at P_l - P_0: the exclusive prefix extreme of a scan
+// in walk order, so the block scans it.  Thread t takes walk positions
+// [t R, t R + R) (walk position w is list position m - w).  The kept points
+// go to `stage` in ascending list order and then back over L[1..], P_l
+// after them; r_lo / r_up become the kept counts.
+constexpr int KR_BLOCK = 1024;
+constexpr int KR_WARPS = KR_BLOCK / 32;
+
+struct Dir1 {
+  int x, y;
+};
+
+// b strictly beyond a: clockwise of it for the lower region (sgn > 0),
+// counter-clockwise for the upper.
+__device__ __forceinline__ bool rev_beyond(const Dir1& a, const Dir1& b, int sgn) {
+  const long long c = cross2(a.x, a.y, b.x, b.y);
+  return sgn > 0 ? c < 0 : c > 0;
+}
+
+constexpr int KR_RB = 8;   // list entries a thread loads at once
+
+// Combination in walk order (a before b): the extreme of the two.
+__device__ __forceinline__ Dir1 rev_combine(const Dir1& a, const Dir1& b, int sgn) {
+  return rev_beyond(a, b, sgn) ? b : a;
+}
+
+__device__ __forceinline__ Dir1 shfl_up_dir1(const Dir1& v, int o) {
+  return Dir1{__shfl_up_sync(0xFFFFFFFFu, v.x, o), __shfl_up_sync(0xFFFFFFFFu, v.y, o)};
+}
+
+__global__ void __launch_bounds__(KR_BLOCK)
+k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy, int* st_lo_idx,
+           int2* st_up_xy, int* st_up_idx) {
+  __shared__ Dir1 s_d[KR_WARPS];
+  __shared__ u32 s_c[KR_WARPS];
+  if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL | ERR_FALLBACK)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int region = blockIdx.x;
+  const int sgn = region == 0 ? 1 : -1;
+  int2* L = region == 0 ? lo_xy : up_xy;
+  int* LI = region == 0 ? lo_idx : up_idx;
+  int2* SX = region == 0 ? st_lo_xy : st_up_xy;
+  int* SI = region == 0 ? st_lo_idx : st_up_idx;
+  const u32 m = region == 0 ? plan->r_lo : plan->r_up;
+  if (m == 0) return;
+  const int2 p0 = L[0], pl = L[m + 1];
+  const Dir1 u0{pl.x - p0.x, pl.y - p0.y};
+  const u32 R = (m + KR_BLOCK - 1) / KR_BLOCK;
+  const u32 w0 = min(m, threadIdx.x * R), w1 = min(m, w0 + R);
+  // The thread's extreme (it starts at u0, which every combination absorbs).
+  Dir1 loc = u0;
+  for (u32 wb = w0; wb < w1; wb += KR_RB) {
+    int2 q[KR_RB];
+    #pragma unroll
+    for (int k = 0; k < KR_RB; ++k) q[k] = wb + k < w1 ? L[m - (wb + k)] : p0;
+    #pragma unroll
+    for (int k = 0; k < KR_RB; ++k)
+      if (wb + k < w1) loc = rev_combine(loc, Dir1{q[k].x - p0.x, q[k].y - p0.y}, sgn);
+  }
+  // Its exclusive prefix: warp scan, then every warp scans the warps' totals.
+  Dir1 inc = loc;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Dir1 t = shfl_up_dir1(inc, o);
+    if (lane >= o) inc = rev_combine(t, inc, sgn);
+  }
+  const Dir1 lex = shfl_up_dir1(inc, 1);
+  if (lane == 31) s_d[wid] = inc;
+  __syncthreads();
+  Dir1 wi = s_d[lane];
+  #pragma unroll
+  for (int o = 1; o < KR_WARPS; o <<= 1) {
+    const Dir1 t = shfl_up_dir1(wi, o);
+    if (lane >= o) wi = rev_combine(t, wi, sgn);
+  }
+  const Dir1 wprev{__shfl_sync(0xFFFFFFFFu, wi.x, wid > 0 ? wid - 1 : 0),
+                   __shfl_sync(0xFFFFFFFFu, wi.y, wid > 0 ? wid - 1 : 0)};
+  Dir1 ex = wid > 0 ? wprev : u0;
+  if (lane > 0) ex = rev_combine(ex, lex, sgn);
+  // Kept points of this thread, then their exclusive count in walk order.
+  u32 cnt = 0;
+  {
+    Dir1 prev = ex;
+    for (u32 wb = w0; wb < w1; wb += KR_RB) {
+      int2 q[KR_RB];
+      #pragma unroll
+      for (int k = 0; k < KR_RB; ++k) q[k] = wb + k < w1 ? L[m - (wb + k)] : p0;
+      #pragma unroll
+      for (int k = 0; k < KR_RB; ++k) {
+        const Dir1 d{q[k].x - p0.x, q[k].y - p0.y};
+        if (wb + k < w1 && rev_beyond(prev, d, sgn)) { ++cnt; prev = d; }
+      }
+    }
+  }
+  u32 ci = cnt;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, ci, o);
+    if (lane >= o) ci += t;
+  }
+  if (lane == 31) s_c[wid] = ci;
+  __syncthreads();
+  u32 wc = s_c[lane];
+  #pragma unroll
+  for (int o = 1; o < KR_WARPS; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, wc, o);
+    if (lane >= o) wc += t;
+  }
+  const u32 total = __shfl_sync(0xFFFFFFFFu, wc, KR_WARPS - 1);
+  const u32 wbefore = __shfl_sync(0xFFFFFFFFu, wc, wid > 0 ? wid - 1 : 0);
+  const u32 before = (wid > 0 ? wbefore : 0u) + ci - cnt;
+  // The kept points in ascending list order (reverse of the walk).
+  {
+    Dir1 prev = ex;
+    u32 k = before;
+    for (u32 wb = w0; wb < w1; wb += KR_RB) {
+      int2 q[KR_RB];
+      #pragma unroll
+      for (int j = 0; j < KR_RB; ++j) q[j] = wb + j < w1 ? L[m - (wb + j)] : p0;
+      #pragma unroll
+      for (int j = 0; j < KR_RB; ++j) {
+        const Dir1 d{q[j].x - p0.x, q[j].y - p0.y};
+        if (wb + j < w1 && rev_beyond(prev, d, sgn)) {
+          const u32 out = total - 1 - k;
+          if (out < m) { SX[out] = q[j]; SI[out] = LI[m - (wb + j)]; } else flag_error(plan, ERR_INTERNAL);
+          ++k;
+          prev = d;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (u32 q = threadIdx.x; q < total; q += KR_BLOCK) {
+    L[1 + q] = SX[q];
+    LI[1 + q] = SI[q];
+  }
+  if (threadIdx.x == 0) {
+    const int pli = LI[m + 1];
+    L[total + 1] = pl;
+    LI[total + 1] = pli;
+    if (region == 0) plan->r_lo = total; else plan->r_up = total;
+  }
+}
+
+cudaError_t launch_k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy,
+                              int* st_lo_idx, int2* st_up_xy, int* st_up_idx, cudaStream_t st) {
+  k4_reverse<<<2, KR_BLOCK, 0, st>>>(plan, lo_xy, lo_idx, up_xy, up_idx, st_lo_xy, st_lo_idx, st_up_xy, st_up_idx);
+  return cudaGetLastError();
+}
+
 // The compaction after the bucket sort's fused second round (one record per group).
 cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_lo_xy, const int* t_lo_idx,
                                  const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,

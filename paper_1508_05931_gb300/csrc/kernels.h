@@ -98,6 +98,11 @@ cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib
                       int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st);
 
+// The mirrored second round over both region lists (one block each), the
+// kept points staged in st_* and copied back; r_lo / r_up updated.
+cudaError_t launch_k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy,
+                              int* st_lo_idx, int2* st_up_xy, int* st_up_idx, cudaStream_t st);
+
 int k5_chunk();
 size_t k5_dyn_smem();
 cudaError_t k5_configure(int* max_blocks_per_sm);

@@ -29,7 +29,8 @@ MAX_POINTS = (1 << 30) - 1
 
 class hull_config(ctypes.Structure):
     _fields_ = [("proposal", ctypes.c_int), ("collect_stats", ctypes.c_int),
-                ("spin_limit", ctypes.c_uint32), ("autotune", ctypes.c_int)]
+                ("spin_limit", ctypes.c_uint32), ("autotune", ctypes.c_int),
+                ("reverse_round", ctypes.c_int)]
 
 
 class hull_stats(ctypes.Structure):
@@ -144,9 +145,10 @@ class Context:
     """One hull_ctx: owns the device workspace for one GPU."""
 
     def __init__(self, device: int = 0, proposal: int = 0, collect_stats: bool = False,
-                 spin_limit: int = 0, autotune: bool = False):
+                 spin_limit: int = 0, autotune: bool = False, reverse_round: bool = False):
         self.device = int(device)
-        cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), int(bool(autotune)))
+        cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), int(bool(autotune)),
+                          int(bool(reverse_round)))
         h = ctypes.c_void_p()
         _check(_lib.hull_create(ctypes.byref(h), self.device, ctypes.byref(cfg)), "hull_create")
         self._h = h

@@ -107,6 +107,53 @@ def test_fused_second_round_lists(ctx, n, gen):
     assert np.array_equal(up.cpu().numpy(), ref["upper"])
 
 
+@pytest.fixture(scope="module")
+def rctx(hull_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hull_lib.Context(0, collect_stats=True, reverse_round=True)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n", [4097, 65537, 1_000_003])
+@pytest.mark.parametrize("gen", ["square", "disk", "ring", "gauss", "clusters", "ties", "strip"])
+def test_reverse_round_lists(rctx, n, gen):
+    """The mirrored second round on the device keeps exactly the oracle's
+    points, in order, in both regions, and the hull stays the hull."""
+    pts = _front_points(gen, n)
+    lo, up, _ = rctx.stage_regions(dev(pts))
+    ref = oracle.gscan_stages(pts, reverse=True)
+    assert np.array_equal(lo.cpu().numpy(), ref["lower"])
+    assert np.array_equal(up.cpu().numpy(), ref["upper"])
+    assert gpu_hull(rctx, pts).tolist() == ref["hull"].tolist()
+    st = rctx.last_stats()
+    assert st["r_lower"] == len(ref["lower"]) and st["r_upper"] == len(ref["upper"])
+
+
+def test_reverse_round_edge_cases(rctx):
+    """Degenerate inputs, the radix-pass rerun, the host entry points and a
+    ring whose survivors are mostly hull vertices, all with the mirrored round."""
+    for pts in (np.zeros((0, 2), np.int32), np.array([[5, 7]], np.int32), np.array([[5, 7], [1, 2]], np.int32),
+                np.full((9000, 2), 3, np.int32), W.filled_grid(300, 200, -7, 9), W.parabola_lattice(1 << 12),
+                np.array([[i * 2, i * 3] for i in range(-500, 500)], np.int32)):
+        assert gpu_hull(rctx, pts).tolist() == oracle.hull(pts).tolist()
+    rng = np.random.default_rng(9)
+    few = rng.integers(-1000, 1000, size=(40, 2)).astype(np.int32)
+    dup = few[rng.integers(0, 40, size=300_000)]
+    assert gpu_hull(rctx, dup).tolist() == oracle.hull(dup).tolist()
+    assert gpu_hull(rctx, np.full((20000, 2), 77, np.int32)).tolist() == [0]
+    assert rctx.last_stats()["sort_fallback"] == 1
+    ring = W.near_circle(400_000, 2.0 ** 22, 7)
+    ref = oracle.gscan_stages(ring, reverse=True)
+    assert rctx.compute_host(ring).tolist() == ref["hull"].tolist()
+    st = rctx.last_stats()
+    assert st["r_lower"] == len(ref["lower"]) and st["r_upper"] == len(ref["upper"])
+    sets = [W.uniform_square(200_000, 1 << 29, 3), W.uniform_disk(100_000, 2.0 ** 29, 4)]
+    for p, h in zip(sets, rctx.compute_host_multi(sets)):
+        assert h.tolist() == oracle.hull(p).tolist()
+
+
 @pytest.mark.parametrize("name", ["paper_square", "paper_disk", "adversarial_ring"])
 def test_full_size_configs(ctx, name):
     pts = getattr(W, name)()
