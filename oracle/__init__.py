@@ -16,6 +16,9 @@ closed forms and invariants.  Pinning status per function:
 * ``sort_survivors``  pinned (numpy lexsort; a library primitive)
 * ``second_round``    pinned (triangle witnesses, hull superset, Section
                       2.2.3's worked P_temp trace)
+* ``second_round_chunked`` pinned (one run = the exact second round, runs of
+                      one point keep the whole region, a superset of the exact
+                      survivors holding every hull vertex, triangle witnesses)
 * ``second_round_reverse`` pinned (triangle witnesses, hull superset, subset of
                       the forward survivors, convex chains kept whole, a
                       hand-derived trace)
@@ -76,6 +79,8 @@ def _load():
     lib.oracle_quad_filter.restype = I64
     lib.oracle_second_round.argtypes = [P, I64, P, P, P, P, P]
     lib.oracle_second_round.restype = ctypes.c_int
+    lib.oracle_second_round_chunked.argtypes = [P, I64, I64, P, P, P, P, P]
+    lib.oracle_second_round_chunked.restype = ctypes.c_int
     lib.oracle_second_round_reverse.argtypes = [P, I64, ctypes.c_int, P, P]
     lib.oracle_second_round_reverse.restype = ctypes.c_int
     lib.oracle_sort_xyi.argtypes = [P, I64]
@@ -169,6 +174,25 @@ def second_round(xy, sorted_idx):
     lo_pos = lo[: nlo.value]
     up_pos = up[: nup.value]
     return (sidx[lo_pos].astype(np.int32), sidx[up_pos].astype(np.int32), int(lp.value))
+
+
+def second_round_chunked(xy, sorted_idx, block_size: int = 1024):
+    """Section 3.4: the second round with each region split into block_size
+    runs of ceil(m / block_size) consecutive points (m = the region's
+    points), Figure 2 run over every run on its own from P_temp = P_0.
+    Returns (lower_idx, upper_idx, l_pos) like second_round."""
+    a = _pts(xy)
+    sidx = np.asarray(sorted_idx, dtype=np.int64)
+    m = sidx.shape[0]
+    xyi = np.empty((m, 3), dtype=np.int32)
+    xyi[:, :2] = a[sidx]
+    xyi[:, 2] = sidx
+    lo = np.empty(max(m, 1), dtype=np.int32)
+    up = np.empty(max(m, 1), dtype=np.int32)
+    nlo, nup, lp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _load().oracle_second_round_chunked(_ptr(xyi), m, int(block_size), _ptr(lo), ctypes.byref(nlo), _ptr(up),
+                                        ctypes.byref(nup), ctypes.byref(lp))
+    return (sidx[lo[: nlo.value]].astype(np.int32), sidx[up[: nup.value]].astype(np.int32), int(lp.value))
 
 
 def second_round_reverse(xy, p0, region, pl, sign: int) -> np.ndarray:

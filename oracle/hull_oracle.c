@@ -223,6 +223,44 @@ int oracle_second_round(const int32_t *xyi, int64_t m, int32_t *lo, int64_t *n_l
     return 0;
 }
 
+/* Section 3.4's chunked second round: the region's points (in sorted
+ * order) are split into `bs` runs of ceil(m_region / bs) consecutive points,
+ * and Figure 2 runs over every run on its own, P_temp starting at P_0.
+ * Same inputs and outputs as oracle_second_round. */
+int oracle_second_round_chunked(const int32_t *xyi, int64_t m, int64_t bs, int32_t *lo, int64_t *n_lo,
+                                int32_t *up, int64_t *n_up, int64_t *l_pos)
+{
+    const opt_t *p = (const opt_t *)xyi;
+    *n_lo = 0; *n_up = 0; *l_pos = -1;
+    if (m <= 0 || bs < 1) return 0;
+    int64_t l = m - 1;
+    while (l > 0 && same_xy(&p[l - 1], &p[m - 1])) --l;
+    if (same_xy(&p[0], &p[l])) return 0;
+    *l_pos = l;
+    for (int r = 0; r < 2; ++r) {
+        /* the region's positions, in order */
+        int64_t cnt = 0;
+        for (int64_t i = 1; i < m; ++i) {
+            const int64_t side = orient(&p[0], &p[l], &p[i]);
+            if ((r == 0 && side < 0) || (r == 1 && side > 0)) ++cnt;
+        }
+        const int64_t run = (cnt + bs - 1) / bs;
+        int64_t k = 0;
+        const opt_t *t = &p[0];
+        int32_t *out = r == 0 ? lo : up;
+        int64_t *nout = r == 0 ? n_lo : n_up;
+        for (int64_t i = 1; i < m; ++i) {
+            const int64_t side = orient(&p[0], &p[l], &p[i]);
+            if (!((r == 0 && side < 0) || (r == 1 && side > 0))) continue;
+            if (run > 0 && k % run == 0) t = &p[0];      /* a new run starts */
+            const int64_t o = orient(t, &p[l], &p[i]);
+            if ((r == 0 && o < 0) || (r == 1 && o > 0)) { out[(*nout)++] = (int32_t)i; t = &p[i]; }
+            ++k;
+        }
+    }
+    return 0;
+}
+
 /* The second round mirrored (the reverse pass of Figure 2 applied to its
  * own survivors): p[0..m) is a region list -- P_0, the region's survivors
  * of the forward pass in sorted order, P_l.  The walk goes from P_l back

@@ -303,6 +303,64 @@ def test_second_round_is_safe_with_witnesses():
             assert any(_in_closed_triangle(p, A, pts[w], B) for w in wit), (t, i)
 
 
+def test_second_round_chunked_golden_trace():
+    """Section 3.4's chunked second round on the hand-made points of Section
+    2.2.3's trace, two runs per region (tests/golden/second_round_chunked_trace.json)."""
+    with open(os.path.join(GOLDEN, "second_round_chunked_trace.json")) as f:
+        g = json.load(f)
+    names, P, perm = g["names"], g["points"], g["index_permutation"]
+    pts = np.zeros((len(P), 2), np.int32)
+    for k, j in enumerate(perm):
+        pts[j] = P[k]
+    name_of = {perm[k]: names[k] for k in range(len(names))}
+    srt = oracle.sort_survivors(pts, np.arange(len(pts)))
+    lo, up, lpos = oracle.second_round_chunked(pts, srt, g["block_size"])
+    assert [name_of[i] for i in lo] == g["expected_lower_kept"]
+    assert [name_of[i] for i in up] == g["expected_upper_kept"]
+    assert name_of[int(srt[lpos])] == "Pl"
+
+
+def test_second_round_chunked_limits_and_safety():
+    """One run per region is Figure 2 itself; runs of one point keep the
+    whole region; any run length keeps a superset of the exact survivors
+    that holds every strict hull vertex, and every point it discards lies in
+    the closed triangle (P_0, P_temp, P_l) of an earlier kept point of its
+    run (or P_0)."""
+    rng = np.random.default_rng(51)
+    for t in range(200):
+        n = int(rng.integers(3, 80))
+        pts = rand_tiny(rng, n, int(rng.choice([3, 8, 1000, 1 << 29])))
+        srt = oracle.sort_survivors(pts, np.arange(n))
+        lo, up, lpos = oracle.second_round(pts, srt)
+        c1 = oracle.second_round_chunked(pts, srt, 1)
+        assert c1[0].tolist() == lo.tolist() and c1[1].tolist() == up.tolist() and c1[2] == lpos
+        if lpos < 0:
+            continue
+        p0, pl = int(srt[0]), int(srt[lpos])
+        A, B = pts[p0], pts[pl]
+
+        def side(i):
+            p = pts[i]
+            return (int(B[0]) - int(A[0])) * (int(p[1]) - int(A[1])) - (int(B[1]) - int(A[1])) * (int(p[0]) - int(A[0]))
+
+        regions = ([int(i) for i in srt[1:] if side(int(i)) < 0], [int(i) for i in srt[1:] if side(int(i)) > 0])
+        cn = oracle.second_round_chunked(pts, srt, n)
+        assert cn[0].tolist() == regions[0] and cn[1].tolist() == regions[1]
+        hv = set(brute_hull(pts))
+        for bs in (2, 3, 7):
+            cl, cu, _ = oracle.second_round_chunked(pts, srt, bs)
+            assert set(lo.tolist()) <= set(cl.tolist()) and set(up.tolist()) <= set(cu.tolist())
+            assert hv <= set(cl.tolist()) | set(cu.tolist()) | {p0, pl}
+            for reg, kept in zip(regions, (set(cl.tolist()), set(cu.tolist()))):
+                run = (len(reg) + bs - 1) // bs
+                for k, i in enumerate(reg):
+                    if i in kept:
+                        continue
+                    start = k - k % run
+                    wit = [p0] + [j for j in reg[start:k] if j in kept]
+                    assert any(_in_closed_triangle(pts[i], A, pts[w], B) for w in wit), (t, bs, i)
+
+
 def test_second_round_reverse_golden_trace():
     """The mirrored second round on the hand-made points of Section 2.2.3's
     trace (tests/golden/second_round_reverse_trace.json, derived by hand)."""
