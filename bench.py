@@ -296,6 +296,35 @@ def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
     return res
 
 
+def bench_second_round_ablation(hull, torch, stream, dev_sets):
+    """Section 3.4's chunked second round (BLOCK_SIZE = 1024, one block per
+    region, one thread per run, as the paper runs it) against the exact scan
+    on the same sorted survivors (steps 1-4 on the device): ms and kept
+    points, and the share of the input left after each round (Figure 9's
+    quantity)."""
+    res = {}
+    names = ("square_20M", "disk_20M")
+    with hull.Context(torch.cuda.current_device()) as c:
+        for name, t in zip(names, dev_sets):
+            xy, idx = c.stage_sorted_survivors(t, stream)
+            row = {"n": int(t.shape[0]), "s": int(xy.shape[0]),
+                   "after_round1_pct": 100.0 * xy.shape[0] / t.shape[0]}
+            for label, fn in (("exact", lambda: c.stage_second_round(xy, idx, stream)),
+                              ("chunked_1024", lambda: c.stage_second_round_chunked(xy, idx, 1024, stream))):
+                lo, up = fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    lo, up = fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                r = int(lo.shape[0] + up.shape[0])
+                row[label] = {"ms": e0.elapsed_time(e1) / 3, "r": r, "after_round2_pct": 100.0 * r / t.shape[0]}
+            res[name] = row
+    return res
+
+
 def bench_learned(hull, torch, stream, args):
     """Learned filter proposal vs the plain quadrilateral on the anisotropic
     families at 20M points (single hull) and as a 1,024-instance batch of the
@@ -508,6 +537,7 @@ def main():
         line["learned"] = bench_learned(hull, torch, stream, args)
     if world == 1 and not args.no_batched:
         line["reverse_round"] = bench_reverse_round(hull, torch, stream, dev_sets, dev_outs)
+        line["second_round_ablation"] = bench_second_round_ablation(hull, torch, stream, dev_sets)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

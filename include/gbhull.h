@@ -294,6 +294,29 @@ hull_status hull_stage_second_round(hull_ctx *ctx, const int32_t *d_xy, const in
                                     int64_t m, int32_t *d_lower, int64_t *h_lower,
                                     int32_t *d_upper, int64_t *h_upper, void *stream);
 
+/* Section 2.1 steps 1-4 on n >= 1 points (d_xy device int32[n][2]): the
+ * extremes, the quadrilateral filter and the sort, through the stable
+ * compaction and the radix passes.  Writes the first-round survivors in
+ * (x, y, index) order as points to d_xy_out (device int32[cap][2]) and
+ * their input indices to d_idx_out (device int32[cap]); *h_count receives
+ * their number.  HULL_ECAPACITY when cap is smaller (count still set). */
+hull_status hull_stage_sorted_survivors(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_xy_out,
+                                        int32_t *d_idx_out, int64_t cap, int64_t *h_count, void *stream);
+
+/* Section 3.4's chunked second round, the paper's own parallelisation of
+ * Figure 2, as an ablation of the exact scan: over m >= 1 points sorted by
+ * (x, y, index) (d_xy device int32[m][2], d_idx device int32[m] their
+ * labels), each region's points are split into block_size (1 .. 1024) runs
+ * of ceil(m_region / block_size) consecutive points and Figure 2 runs over
+ * every run on its own from P_temp = P_0 (one thread per run, one block per
+ * region, as the paper does).  block_size = 1 is the exact second round.
+ * Writes the kept labels of the lower / upper region to d_lower / d_upper
+ * (device int32[m] each) in list order; counts in *h_lower, *h_upper. */
+hull_status hull_stage_second_round_chunked(hull_ctx *ctx, const int32_t *d_xy, const int32_t *d_idx,
+                                            int64_t m, int32_t block_size, int32_t *d_lower,
+                                            int64_t *h_lower, int32_t *d_upper, int64_t *h_upper,
+                                            void *stream);
+
 /* The front of hull_compute on n points (d_xy device int32[n][2]):
  * extremes, quadrilateral filter, sort and the second-round filter
  * (Section 2.1 steps 1-7, Figure 2), fused as in hull_compute.  Writes the

@@ -718,6 +718,56 @@ hull_status hull_compute_multi(hull_ctx* c, int32_t count, const int32_t* const*
   return first;
 }
 
+hull_status hull_stage_sorted_survivors(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_xy_out,
+                                        int32_t* d_idx_out, int64_t cap, int64_t* h_count, void* stream) {
+  if (!c || !d_xy || !d_xy_out || !d_idx_out || !h_count || n < 1 || cap < 0 || n > (int64_t)kMaxN || !aligned8(d_xy))
+    return HULL_EINVAL;
+  *h_count = 0;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)n);
+  if (r != HULL_OK) return r;
+  Workspace& w = c->ws;
+  cudaError_t e = launch_k1(d_xy, (u32)n, c->cfg.spin_limit, c->plan, w.partials, k1_grid((u32)n, c->num_sms), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t t2 = ((size_t)n + k2_tile() - 1) / k2_tile();
+  e = launch_k2(d_xy, c->plan, w.keys[0], w.idx[0], w.st_filter, w.mask, grid_for(c->occ_k2c, c->num_sms, t2),
+                grid_for(c->occ_k2, c->num_sms, t2), st);
+  const size_t t3 = ((size_t)n + k3_tile() - 1) / k3_tile();
+  for (u32 p = 0; e == cudaSuccess && p < (u32)kMaxPasses; ++p)
+    e = launch_k3(w.keys[p & 1], w.idx[p & 1], w.keys[(p + 1) & 1], w.idx[(p + 1) & 1], c->plan, w.st_sort, p,
+                  grid_for(c->occ_k3, c->num_sms, t3), st);
+  if (e == cudaSuccess)
+    e = launch_gather_sorted(reinterpret_cast<const int2*>(d_xy), w.idx[0], w.idx[1], c->plan,
+                             reinterpret_cast<int2*>(d_xy_out), d_idx_out, (u32)cap, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  *h_count = c->h_plan->s;
+  if (r == HULL_OK && (int64_t)c->h_plan->s > cap) r = HULL_ECAPACITY;
+  return r;
+}
+
+hull_status hull_stage_second_round_chunked(hull_ctx* c, const int32_t* d_xy, const int32_t* d_idx, int64_t m,
+                                            int32_t block_size, int32_t* d_lower, int64_t* h_lower, int32_t* d_upper,
+                                            int64_t* h_upper, void* stream) {
+  if (!c || !d_xy || !d_idx || !d_lower || !d_upper || !h_lower || !h_upper || m < 1 || m > (int64_t)kMaxN ||
+      !aligned8(d_xy) || block_size < 1 || block_size > 1024)
+    return HULL_EINVAL;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hull_status r = ensure_ws(c, (size_t)m);
+  if (r != HULL_OK) return r;
+  r = new_call_patch(c, st, PlanPatch{});
+  if (r != HULL_OK) return r;
+  const cudaError_t e = launch_k4_chunked(reinterpret_cast<const int2*>(d_xy), d_idx, (u32)m, (u32)block_size,
+                                          c->plan, c->ws.h_idx[0], c->ws.h_idx[1], d_lower, d_upper, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = finish(c, st);
+  *h_lower = c->h_plan->r_lo;
+  *h_upper = c->h_plan->r_up;
+  return r;
+}
+
 hull_status hull_stage_regions(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_lower,
                                int64_t lower_cap, int32_t* d_upper, int64_t upper_cap, int64_t* h_counts,
                                int32_t* h_fallback, void* stream) {

@@ -422,6 +422,115 @@ k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2*
   }
 }
 
+// Section 3.4's chunked second round, as the paper runs it: one block of
+// KC_BLOCK threads per region (blockIdx.x 0 lower, 1 upper) over a list
+// sorted by (x, y, index): P_l is the first of the list's last run of
+// equal points; the region's positions are collected in order into `pos`;
+// they are split into bs runs of ceil(m_region / bs) consecutive points and
+// thread t < bs checks run t with Figure 2 from P_temp = P_0, in sequence;
+// the labels of the kept points go to `out` in list order and their count
+// to plan->r_lo / r_up.
+constexpr int KC_BLOCK = 1024;
+constexpr int KC_WARPS = KC_BLOCK / 32;
+
+__device__ __forceinline__ u32 block_excl_sum(u32 v, u32* red, u32* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  u32 inc = v;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) red[wid] = inc;
+  __syncthreads();
+  u32 w = red[lane < KC_WARPS ? lane : 0];
+  if (lane >= KC_WARPS) w = 0;
+  #pragma unroll
+  for (int o = 1; o < KC_WARPS; o <<= 1) {
+    const u32 t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+    if (lane >= o) w += t;
+  }
+  *total = __shfl_sync(0xFFFFFFFFu, w, KC_WARPS - 1);
+  const u32 before = __shfl_sync(0xFFFFFFFFu, w, wid > 0 ? wid - 1 : 0);
+  __syncthreads();
+  return (wid > 0 ? before : 0u) + inc - v;
+}
+
+__global__ void __launch_bounds__(KC_BLOCK)
+k4_chunked(const int2* __restrict__ xy, const int* __restrict__ idx, u32 m, u32 bs, Plan* plan, int* pos_lo,
+           int* pos_up, int* out_lo, int* out_up) {
+  __shared__ u32 s_red[KC_WARPS];
+  __shared__ u32 s_l;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int region = blockIdx.x;
+  int* pos = region == 0 ? pos_lo : pos_up;
+  int* out = region == 0 ? out_lo : out_up;
+  // P_l: one past the last point that differs from the list's last point.
+  const int2 last = xy[m - 1];
+  u32 jl = 0;
+  for (u32 i = threadIdx.x; i < m; i += KC_BLOCK)
+    if (xy[i].x != last.x || xy[i].y != last.y) jl = max(jl, i + 1);
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) jl = max(jl, __shfl_xor_sync(0xFFFFFFFFu, jl, o));
+  if (threadIdx.x == 0) s_l = 0;
+  __syncthreads();
+  if (lane == 0) atomicMax(&s_l, jl);
+  __syncthreads();
+  const u32 l = s_l;
+  const int2 p0 = xy[0], pl = xy[l];
+  if (p0.x == pl.x && p0.y == pl.y) {
+    if (threadIdx.x == 0) { if (region == 0) plan->r_lo = 0; else plan->r_up = 0; }
+    return;
+  }
+  // The region's list positions, in order.
+  const u32 n1 = m - 1;
+  const u32 R = (n1 + KC_BLOCK - 1) / KC_BLOCK;
+  const u32 a0 = 1 + min(n1, threadIdx.x * R), a1 = 1 + min(n1, threadIdx.x * R + R);
+  const int ux = pl.x - p0.x, uy = pl.y - p0.y;
+  auto in_region = [&](const int2 p) {
+    const long long sd = cross2(ux, uy, p.x - p0.x, p.y - p0.y);
+    return region == 0 ? sd < 0 : sd > 0;
+  };
+  u32 c = 0;
+  for (u32 i = a0; i < a1; ++i) c += in_region(xy[i]) ? 1u : 0u;
+  u32 mr;
+  u32 o = block_excl_sum(c, s_red, &mr);
+  for (u32 i = a0; i < a1; ++i)
+    if (in_region(xy[i])) pos[o++] = (int)i;
+  __syncthreads();
+  // Runs of ceil(mr / bs) positions, Figure 2 over each from P_temp = P_0.
+  const u32 run = (mr + bs - 1) / bs;
+  const u32 r0 = threadIdx.x < bs ? min(mr, threadIdx.x * run) : mr;
+  const u32 r1 = threadIdx.x < bs ? min(mr, r0 + run) : mr;
+  auto kept = [&](int2& t, const int2 p) {
+    const long long ov = cross2(pl.x - t.x, pl.y - t.y, p.x - t.x, p.y - t.y);
+    const bool k = region == 0 ? ov < 0 : ov > 0;
+    if (k) t = p;
+    return k;
+  };
+  u32 kc = 0;
+  {
+    int2 t = p0;
+    for (u32 k = r0; k < r1; ++k) kc += kept(t, xy[pos[k]]) ? 1u : 0u;
+  }
+  u32 total;
+  u32 q = block_excl_sum(kc, s_red, &total);
+  {
+    int2 t = p0;
+    for (u32 k = r0; k < r1; ++k) {
+      const int i = pos[k];
+      if (kept(t, xy[i])) out[q++] = idx[i];
+    }
+  }
+  if (threadIdx.x == 0) { if (region == 0) plan->r_lo = total; else plan->r_up = total; }
+}
+
+cudaError_t launch_k4_chunked(const int2* xy, const int* idx, u32 m, u32 bs, Plan* plan, int* pos_lo, int* pos_up,
+                              int* out_lo, int* out_up, cudaStream_t st) {
+  k4_chunked<<<2, KC_BLOCK, 0, st>>>(xy, idx, m, bs, plan, pos_lo, pos_up, out_lo, out_up);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy,
                               int* st_lo_idx, int2* st_up_xy, int* st_up_idx, cudaStream_t st) {
   k4_reverse<<<2, KR_BLOCK, 0, st>>>(plan, lo_xy, lo_idx, up_xy, up_idx, st_lo_xy, st_lo_idx, st_up_xy, st_up_idx);

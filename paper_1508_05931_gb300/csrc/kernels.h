@@ -20,6 +20,8 @@ struct PlanPatch {
 cudaError_t launch_plan_patch(Plan* plan, const PlanPatch& p, cudaStream_t st);
 cudaError_t launch_hist(const u64* keys, Plan* plan, int grid, cudaStream_t st);
 cudaError_t launch_iota(int* out, u32 m, cudaStream_t st);
+cudaError_t launch_gather_sorted(const int2* xy, const u32* ia, const u32* ib, const Plan* plan, int2* out_xy,
+                                 int* out_idx, u32 cap, cudaStream_t st);
 cudaError_t launch_gather_labels(const int* pos, const int* labels, const u32* count,
                                  u32 skip_first, int* out, u32 cap, cudaStream_t st);
 
@@ -98,6 +100,10 @@ cudaError_t launch_k4(const u64* ka, const u32* ia, const u64* kb, const u32* ib
                       int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy, int* t_up_idx, int grid,
                       cudaStream_t st);
 
+// Section 3.4's chunked second round over a sorted list (one block per
+// region; pos_* scratch of m ints each; kept labels into out_*).
+cudaError_t launch_k4_chunked(const int2* xy, const int* idx, u32 m, u32 bs, Plan* plan, int* pos_lo, int* pos_up,
+                              int* out_lo, int* out_up, cudaStream_t st);
 // The mirrored second round over both region lists (one block each), the
 // kept points staged in st_* and copied back; r_lo / r_up updated.
 cudaError_t launch_k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy,

@@ -70,6 +70,29 @@ cudaError_t launch_iota(int* out, u32 m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The sorted survivors of the radix path as points: out_xy[i] = xy[idx[i]]
+// and out_idx[i] = idx[i] for i < plan->s, idx being the index buffer that
+// holds the sorted result (plan->sorted_in_b selects ib over ia).
+__global__ void k_gather_sorted(const int2* __restrict__ xy, const u32* ia, const u32* ib, const Plan* plan,
+                                int2* __restrict__ out_xy, int* __restrict__ out_idx, u32 cap) {
+  const u32 s = plan->s;
+  const u32* idx = plan->sorted_in_b ? ib : ia;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < s && i < cap; i += gridDim.x * blockDim.x) {
+    const u32 j = idx[i];
+    out_xy[i] = xy[j];
+    out_idx[i] = (int)j;
+  }
+}
+
+cudaError_t launch_gather_sorted(const int2* xy, const u32* ia, const u32* ib, const Plan* plan, int2* out_xy,
+                                 int* out_idx, u32 cap, cudaStream_t st) {
+  int grid = (int)((cap + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  k_gather_sorted<<<grid, 256, 0, st>>>(xy, ia, ib, plan, out_xy, out_idx, cap);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_labels(const int* pos, const int* labels, const u32* count,
                                  u32 skip_first, int* out, u32 cap, cudaStream_t st) {
   int grid = (int)((cap + 255) / 256);

@@ -87,6 +87,8 @@ _sig = {
     "hull_stage_sort": ([_P, _P, _P, _I64, _P], ctypes.c_int),
     "hull_stage_bucket_sort": ([_P, _P, _P, _I64, ctypes.POINTER(ctypes.c_int32), _P], ctypes.c_int),
     "hull_stage_second_round": ([_P, _P, _P, _I64, _P, _PI64, _P, _PI64, _P], ctypes.c_int),
+    "hull_stage_sorted_survivors": ([_P, _P, _I64, _P, _P, _I64, _PI64, _P], ctypes.c_int),
+    "hull_stage_second_round_chunked": ([_P, _P, _P, _I64, ctypes.c_int32, _P, _PI64, _P, _PI64, _P], ctypes.c_int),
     "hull_stage_regions": ([_P, _P, _I64, _P, _I64, _P, _I64, _PI64, ctypes.POINTER(ctypes.c_int32), _P],
                            ctypes.c_int),
     "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
@@ -425,6 +427,36 @@ class Context:
                                        ctypes.byref(fb), _stream_handle(stream)), "hull_stage_regions")
         return lo[: cnt[0]], up[: cnt[1]], bool(fb.value)
 
+    def stage_sorted_survivors(self, pts, stream=None):
+        """Steps 1-4 on the device: (survivor points sorted by (x, y, index),
+        their input indices)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(pts, dev)
+        n = xy.shape[0]
+        oxy = torch.empty((max(n, 1), 2), dtype=torch.int32, device=dev)
+        oid = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cnt = ctypes.c_int64()
+        _check(_lib.hull_stage_sorted_survivors(self._h, _ptr(xy), n, _ptr(oxy), _ptr(oid), n, ctypes.byref(cnt),
+                                                _stream_handle(stream)), "hull_stage_sorted_survivors")
+        return oxy[: cnt.value], oid[: cnt.value]
+
+    def stage_second_round_chunked(self, xy_sorted, labels, block_size=1024, stream=None):
+        """Section 3.4's chunked second round over sorted points: (lower
+        labels, upper labels)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(xy_sorted, dev)
+        lab = torch.as_tensor(labels, dtype=torch.int32).to(dev).contiguous()
+        m = xy.shape[0]
+        lo = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        up = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        nl, nu = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hull_stage_second_round_chunked(self._h, _ptr(xy), _ptr(lab), m, int(block_size), _ptr(lo),
+                                                    ctypes.byref(nl), _ptr(up), ctypes.byref(nu),
+                                                    _stream_handle(stream)), "hull_stage_second_round_chunked")
+        return lo[: nl.value], up[: nu.value]
+
     def stage_chain(self, xy_sorted, stream=None):
         """Returns (lower chain positions, upper chain positions), both from
         the first to the last point."""
@@ -485,5 +517,7 @@ hull_stage_sort = _lib.hull_stage_sort
 hull_stage_bucket_sort = _lib.hull_stage_bucket_sort
 hull_stage_second_round = _lib.hull_stage_second_round
 hull_stage_regions = _lib.hull_stage_regions
+hull_stage_second_round_chunked = _lib.hull_stage_second_round_chunked
+hull_stage_sorted_survivors = _lib.hull_stage_sorted_survivors
 hull_compute_multi = _lib.hull_compute_multi
 hull_stage_chain = _lib.hull_stage_chain

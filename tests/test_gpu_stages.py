@@ -173,6 +173,55 @@ def test_second_round_parity(ctx, n, span):
     assert np.array_equal(up.cpu().numpy(), up_ref)
 
 
+@pytest.mark.parametrize("n", [1, 2, 4097, 65537, 1_000_003])
+@pytest.mark.parametrize("gen", ["square", "disk", "ties"])
+def test_sorted_survivors_parity(ctx, n, gen):
+    """Steps 1-4 on the device (extremes, quad filter, stable compaction,
+    radix sort): the survivors in (x, y, index) order, bit-exact."""
+    rng = np.random.default_rng(n + 5)
+    pts = {"square": lambda: W.uniform_square(n, 1 << 29, n), "disk": lambda: W.uniform_disk(n, 2.0 ** 29, n),
+           "ties": lambda: rand_pts(rng, n, 5)}[gen]()
+    ref = oracle.sort_survivors(pts, oracle.quad_filter(pts))
+    xy, idx = ctx.stage_sorted_survivors(dev(pts))
+    assert np.array_equal(idx.cpu().numpy(), ref)
+    assert np.array_equal(xy.cpu().numpy(), pts[ref])
+
+
+@pytest.mark.parametrize("n", [2, 5, 4097, 300001])
+@pytest.mark.parametrize("span", [1, 100, 1 << 29])
+@pytest.mark.parametrize("bs", [1, 7, 1024])
+def test_second_round_chunked_parity(ctx, n, span, bs):
+    """Section 3.4's chunked second round on the device (one thread per run,
+    one block per region) equals the oracle's, list for list."""
+    rng = np.random.default_rng(n * 3 + span % 97 + bs)
+    pts = rand_pts(rng, n, span)
+    xy, srt = _sorted_input(pts)
+    lo_ref, up_ref, _ = oracle.second_round_chunked(pts, srt, bs)
+    lo, up = ctx.stage_second_round_chunked(xy, srt, bs)
+    assert np.array_equal(lo.cpu().numpy(), lo_ref)
+    assert np.array_equal(up.cpu().numpy(), up_ref)
+
+
+def test_second_round_chunked_golden_and_paper_shapes(ctx):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "second_round_chunked_trace.json")))
+    names, P, perm = g["names"], g["points"], g["index_permutation"]
+    pts = np.zeros((len(P), 2), np.int32)
+    for k, j in enumerate(perm):
+        pts[j] = P[k]
+    name_of = {perm[k]: names[k] for k in range(len(names))}
+    xy, srt = _sorted_input(pts)
+    lo, up = ctx.stage_second_round_chunked(xy, srt, g["block_size"])
+    assert [name_of[int(i)] for i in lo.cpu().numpy()] == g["expected_lower_kept"]
+    assert [name_of[int(i)] for i in up.cpu().numpy()] == g["expected_upper_kept"]
+    for pts in (W.uniform_square(1_000_000, 1 << 29, 61), W.uniform_disk(1_000_000, 2.0 ** 29, 62)):
+        srt = oracle.sort_survivors(pts, oracle.quad_filter(pts))
+        lo_ref, up_ref, _ = oracle.second_round_chunked(pts, srt, 1024)
+        lo, up = ctx.stage_second_round_chunked(pts[srt], srt, 1024)
+        assert np.array_equal(lo.cpu().numpy(), lo_ref) and np.array_equal(up.cpu().numpy(), up_ref)
+
+
 def test_second_round_golden_trace(ctx):
     import json
     import os
