@@ -4,18 +4,22 @@
 // by key that the paper's sort_by_key gives; the key is the lexicographic
 // (x, y) key of K2.
 //
-// The sort needs two passes over the survivors instead of one per radix
-// digit:
-//   1. while K2 counts the survivors it also counts them per bin (the top
-//      kBinBits of the key), one histogram row per block; k_binscan turns
-//      the rows into each block's first position in every bin and groups
-//      consecutive bins, and K2's scatter pass writes every survivor into
-//      its bin (any order inside a bin);
-//   2. k3_bucket sorts each group in shared memory, one block per group:
-//      a counting pass over the next kSubBits key bits places every key in
-//      its sub-bin, and the few keys of each sub-bin are then ordered by
-//      (key, index) in place.  A group whose sub-bins are crowded (many
-//      equal or nearly equal keys) is sorted by a bitonic network instead.
+// The pipeline's sort moves the survivors' pairs twice after K2 instead of
+// once per radix digit:
+//   1. while K2 counts the survivors it adds them to the bins' totals (a bin
+//      = the top kBinBits of the key) and reserves each block's run in
+//      every coarse bin (kFinePerCoarse consecutive bins); k_binstart turns
+//      the totals into bin starts and groups of consecutive bins, and K2's
+//      scatter pass writes every survivor into its coarse bin;
+//   2. k3_split spreads every coarse bin over its bins (with the tiles'
+//      direction aggregates for the second round's group prefixes, folded
+//      by k_group_agg_bins), and k3_bucket takes one group at a time into
+//      shared memory: a counting pass over kSubBins sub-bins of the group's
+//      exact key range, then either Figure 2 on the binned group (each
+//      thread owns whole sub-bins and orders only its candidates) or, for
+//      the stage entry point and crowded groups, the order inside every
+//      sub-bin by rank counting (a bitonic network when a sub-bin is
+//      crowded).
 //
 // Groups: bin b starts a new group when floor(start_b / T) differs from
 // its predecessor's (T = kGroupTarget) or when it or its predecessor holds
@@ -1063,11 +1067,13 @@ k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict
   group_prefix_scan(plan, recs, ng, rg);
 }
 
-// Per-bin prefix over the histogram rows (one per K2 block): row r, bin b
-// becomes the number of bin-b survivors of rows before r; bstart[b] first
-// receives the bin totals, and the last block turns them into the bins'
-// first positions and writes the groups (first position, first bin), with a
-// closing record (s, kBins) after the last group.
+// Bin starts and groups.  k_binstart (the pipeline, one block) takes the
+// bins' totals that k2_count accumulated.  k_binscan (the stage entry's
+// array path) takes one histogram row per histogram block: row r, bin b
+// becomes the number of bin-b pairs of rows before r, bstart[b] first
+// receives the bin totals, and its last block continues as k_binstart does.
+// Both write the bins' first positions and the groups (first position,
+// first bin), with a closing record (s, kBins) after the last group.
 constexpr int BS_BLOCK = 512;
 constexpr int BS_BINS = 32;                 // bins per block (one per lane)
 constexpr int BS_WARPS = BS_BLOCK / 32;
@@ -1170,17 +1176,12 @@ __device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ 
 }
 __global__ void __launch_bounds__(BS_BLOCK)
 k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
-          uint2* __restrict__ groups, K4Chunk* __restrict__ recs, u32* __restrict__ fcur) {
+          uint2* __restrict__ groups, u32* __restrict__ fcur) {
   __shared__ u32 s_part[BS_WARPS][BS_BINS];
   __shared__ bool s_last;
   if (plan->error & ERR_RANGE) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 bin = blockIdx.x * BS_BINS + lane;
-  // Clear the look-back records of the fused second round (one per group,
-  // at most one group per bin): 8 words per record.
-  if (recs)
-    for (u32 q = threadIdx.x; q < BS_BINS * 8u; q += BS_BLOCK)
-      reinterpret_cast<u64*>(recs + (size_t)blockIdx.x * BS_BINS)[q] = 0ull;
   const u32 per = (nrows + BS_WARPS - 1) / BS_WARPS;
   const u32 r0 = min(nrows, wid * per), r1 = min(nrows, r0 + per);
   u32 sum = 0;
@@ -1337,12 +1338,6 @@ cudaError_t launch_binstart(const u32* btot, Plan* plan, u32* bstart, uint2* gro
   return cudaGetLastError();
 }
 
-cudaError_t launch_binscan(u32* rows, u32 nrows, Plan* plan, u32* bstart, uint2* groups, void* recs,
-                           u32* fcur, cudaStream_t st) {
-  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, nrows, plan, bstart, groups,
-                                                  reinterpret_cast<K4Chunk*>(recs), fcur);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,
                                const uint2* groups, u32* scratch, int grid, cudaStream_t st) {
@@ -1393,7 +1388,7 @@ cudaError_t launch_array_bins(const u64* keys, const u32* vals, u32 m, Plan* pla
   if (e != cudaSuccess) return e;
   k3_array_keyor<<<grid, KA_BLOCK, 0, st>>>(keys, plan, key_or);
   k3_array_hist<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, plan, key_or, rows);
-  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr, nullptr);
+  k_binscan<<<kBins / BS_BINS, BS_BLOCK, 0, st>>>(rows, (u32)grid, plan, bstart, groups, nullptr);
   k3_array_scatter<<<grid, KA_BLOCK, kBins * 4, st>>>(keys, vals, plan, rows, bstart, ok, ov);
   (void)m;
   return cudaGetLastError();
