@@ -388,7 +388,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     sets = workload(args.n)
-    sample = 1_000_000
+    sample = min(1_000_000, args.n)
     times = []
     import oracle
     oracle.build()
