@@ -137,3 +137,26 @@ def test_batch_learned_exact_and_discards_more(hull_lib):
         check(parts, *run_batch(c, parts))
         c.mlp_set_params(np.zeros(OM.N_PARAMS, np.float32))
         check(parts, *run_batch(c, parts))
+
+
+def test_full_size_batch_sampled(hull_lib, tmp_path, monkeypatch):
+    """The 4,096-instance batch at its full size (2.5e8 points, the bench's
+    workload and launch configuration: one call, autotuned): the hulls of a
+    seeded sample of instances, the largest and the smallest among them,
+    computed one by one by the oracle, and every instance's hull size within
+    its own points."""
+    monkeypatch.setenv("GBHULL_AUTOTUNE_CACHE", str(tmp_path / "autotune.json"))
+    pts, offs, fam = W.batch()
+    dp = torch.as_tensor(pts).cuda()
+    with hull_lib.Context(0, autotune=True) as c:
+        o, oo = c.compute_batched(dp, torch.as_tensor(offs).cuda())
+    o, oo = o.cpu().numpy(), oo.cpu().numpy()
+    sizes = np.diff(offs)
+    assert len(oo) == len(offs) and oo[0] == 0 and (np.diff(oo) >= 1).all()
+    assert (np.diff(oo) <= sizes).all()
+    rng = np.random.default_rng(77)
+    pick = set(rng.choice(len(sizes), size=40, replace=False).tolist())
+    pick |= {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    for i in sorted(pick):
+        p = pts[offs[i]:offs[i + 1]]
+        assert o[oo[i]:oo[i + 1]].tolist() == oracle.hull(p).tolist(), (i, len(p), int(fam[i]))

@@ -93,6 +93,18 @@ def test_learned_hull_is_exact(ctx, weights, gen):
     assert h.tolist() == oracle.hull(pts).tolist()
 
 
+@pytest.mark.parametrize("family", ["aniso", "ellipse", "clusters"])
+def test_learned_hull_exact_full_size(ctx, family):
+    """The three anisotropic families at their full 20M points, learned
+    polygon in use (any weights keep the hull exact)."""
+    ctx.mlp_set_params(OM.init_params(9))
+    pts = {"aniso": lambda: W.anisotropic_gaussian(20_000_000, 5),
+           "ellipse": lambda: W.elliptic_disk(20_000_000, 6),
+           "clusters": lambda: W.gaussian_clusters(20_000_000, 7)}[family]()
+    h = ctx.compute(torch.as_tensor(pts).cuda()).cpu().numpy()
+    assert h.tolist() == oracle.hull(pts).tolist()
+
+
 def test_checkpoint_roundtrip(ctx, hull_lib, tmp_path):
     w = OM.init_params(7)
     ctx.mlp_set_params(w)
