@@ -224,7 +224,7 @@ STAGE_KERNELS = {
     "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n),
     "filter": ("k2_count + k_binstart", lambda n, s, r: 8.0 * n),
     "scatter": ("k2_scatter", lambda n, s, r: 8.0 * n + 12.0 * s),
-    "split": ("k3_split + k_group_agg_bins", lambda n, s, r: 24.0 * s),
+    "split": ("k3_split + k_bin_prefix", lambda n, s, r: 24.0 * s),
     "sort": ("k3_bucket", lambda n, s, r: 12.0 * s + 12.0 * r),
     "regions": ("k4_compact", lambda n, s, r: 24.0 * r),
     "final": ("k5_final", lambda n, s, r: 12.0 * r),

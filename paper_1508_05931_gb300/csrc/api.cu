@@ -51,6 +51,8 @@ struct Workspace {
   u64* tagg = nullptr;         // per split tile and bin: direction aggregates (lower, upper)
   u32* ctiles = nullptr;       // first split tile of every coarse bin
   u32* bcnt = nullptr;         // bins' totals, then coarse-bin cursors (k2_count)
+  u64* bagg = nullptr;         // per bin: direction aggregates (lower, upper), scratch of k_bin_prefix
+  u64* bpre = nullptr;         // per bin: exclusive second-round prefix (lower, upper)
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   unsigned long long* key_or = nullptr;
 };
@@ -196,6 +198,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_tagg = take(tiles_cap * 2 * kFinePerCoarse * 8);
   const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
   const size_t o_bcnt = take(((size_t)kBins + kCoarse) * 4);
+  const size_t o_bagg = take((size_t)kBins * 16);
+  const size_t o_bpre = take((size_t)kBins * 16);
   const size_t o_fcur = take((size_t)kBins * 4);
   const size_t total = off;
 
@@ -238,6 +242,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.tagg = reinterpret_cast<u64*>(b + o_tagg);
   w.ctiles = reinterpret_cast<u32*>(b + o_ctiles);
   w.bcnt = reinterpret_cast<u32*>(b + o_bcnt);
+  w.bagg = reinterpret_cast<u64*>(b + o_bagg);
+  w.bpre = reinterpret_cast<u64*>(b + o_bpre);
   w.fcur = reinterpret_cast<u32*>(b + o_fcur);
   return HULL_OK;
 }
@@ -337,11 +343,11 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     mark(c, 3, st);
     e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.tagg, w.ctiles,
                      c->occ_sp * c->num_sms, st);
-    if (e == cudaSuccess) e = launch_group_prefix(c->plan, w.groups, w.st_region, w.tagg, w.ctiles, st);
+    if (e == cudaSuccess) e = launch_bin_prefix(c->plan, w.groups, w.st_region, w.tagg, w.ctiles, w.bagg, w.bpre, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 4, st);
     e = launch_bucket_decide(w.keys[1], w.idx[1], w.keys[0], w.idx[0], c->plan, w.groups, w.bscratch,
-                             w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
+                             w.st_region, w.bpre, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
                              w.up_xy, w.up_idx, c->occ_kb * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     for (int p = 5; p <= 2 + kMaxPasses; ++p) mark(c, p, st);

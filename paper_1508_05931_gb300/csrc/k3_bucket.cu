@@ -12,8 +12,8 @@
 //      the totals into bin starts and groups of consecutive bins, and K2's
 //      scatter pass writes every survivor into its coarse bin;
 //   2. k3_split spreads every coarse bin over its bins (with the tiles'
-//      direction aggregates for the second round's group prefixes, folded
-//      by k_group_agg_bins), and k3_bucket takes one group at a time into
+//      direction aggregates, from which k_bin_prefix scans every bin's
+//      second-round prefix), and k3_bucket takes one group at a time into
 //      shared memory: a counting pass over kSubBins sub-bins of the group's
 //      exact key range, then either Figure 2 on the binned group (each
 //      thread owns whole sub-bins and orders only its candidates) or, for
@@ -279,14 +279,34 @@ __device__ __forceinline__ void add_dir(Dir2& a, const RG& g, u64 k) {
 }
 
 
+// A direction pair (lower, upper words; a word without its valid bit is
+// the identity's).
+__device__ __forceinline__ Dir2 unpack_pair(u64 wl, u64 wu, const RG& rg) {
+  Dir2 v = rg.ident;
+  if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
+  if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
+  return v;
+}
+
 // The second round run by the pipeline's sort: every group's record holds
-// its exclusive prefix (k_group_agg_bins) and receives its kept
+// its exclusive prefix (k_bin_prefix) and receives its kept
 // counts; kept points are staged in t_* and the last block turns the counts
 // into offsets and fills both ends of the region lists.
 struct Fused {
   K4Chunk* recs;
   int2* t_lo_xy; int* t_lo_idx; int2* t_up_xy; int* t_up_idx;
   int2* lo_xy; int* lo_idx; int2* up_xy; int* up_idx;
+  const u64* bpre;         // every bin's exclusive prefix (k_bin_prefix)
+};
+
+// The second round's early drop (the fused path): a pair whose point lies
+// within the prefix extreme of all points in earlier bins cannot be kept
+// (it does not change the running extreme either), so the sort skips it.
+// bpre == nullptr: no drop.  The group's first nb <= KB_WARPS prefixes are
+// cached in S.dirs (free until the second round).
+struct Drop {
+  const u64* bpre;
+  u32 bin0, nb, fshift;
 };
 
 // Next position to visit among the bits of `mask` (bit j: position p0 + j),
@@ -485,10 +505,14 @@ __device__ __forceinline__ void fetch_group(BucketSmem& S, const Fused& F, const
 // returns true (binned: the pairs of a sub-bin in any order).
 template <bool RO>
 __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 base, u32 m, u64 klo,
-                               u64 ktop, Plan* plan, bool allow_binned) {
+                               u64 ktop, Plan* plan, bool allow_binned, const Drop& dr, const RG& rg) {
   if (threadIdx.x == 0) {
     const SubMap f = make_submap(ktop);
     S.misc[2] = f.esh; S.misc[3] = f.lsh; S.misc[4] = f.M;
+  }
+  if (dr.bpre && threadIdx.x < min(dr.nb, (u32)KB_WARPS)) {
+    const u32 q = dr.bin0 + threadIdx.x;
+    S.dirs[threadIdx.x] = unpack_pair(__ldg(&dr.bpre[2 * q]), __ldg(&dr.bpre[2 * q + 1]), rg);
   }
   for (u32 i = threadIdx.x; i < (u32)kSubBins / 4; i += KB_BLOCK)
     reinterpret_cast<uint4*>(S.cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -516,8 +540,20 @@ __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
       if (i < m) {
         const u64 off = kk[q] - klo;
         if (off <= ktop) {
-          const u32 d = sub_of(f, off);
-          pk[h * KB_HALF + q] = (d << 13) | atomicAdd(&S.cnt[d], 1u);
+          bool keep = true;
+          if (dr.bpre) {
+            const u32 bi = (u32)(kk[q] >> dr.fshift) - dr.bin0;
+            const Dir2 e = bi < (u32)KB_WARPS ? S.dirs[bi]
+                                              : unpack_pair(__ldg(&dr.bpre[2 * (dr.bin0 + bi)]),
+                                                            __ldg(&dr.bpre[2 * (dr.bin0 + bi) + 1]), rg);
+            int vx, vy;
+            const long long o = key_dir(rg, kk[q], vx, vy);
+            keep = o < 0 ? cross2(e.lx, e.ly, vx, vy) > 0 : (o > 0 && cross2(e.ux, e.uy, vx, vy) < 0);
+          }
+          if (keep) {
+            const u32 d = sub_of(f, off);
+            pk[h * KB_HALF + q] = (d << 13) | atomicAdd(&S.cnt[d], 1u);
+          }
         } else {
           flag_error(plan, ERR_INTERNAL);
         }
@@ -613,7 +649,7 @@ __device__ bool sort_into_smem(BucketSmem& S, const u64* sk, const u32* sv, u32 
       }
     }
   } else {
-    bitonic(S, m);
+    bitonic(S, S.cnt[kSubBins]);
   }
   __syncthreads();
   return false;
@@ -702,7 +738,8 @@ __device__ void big_bin(BucketSmem& S, const u64* __restrict__ ak, const u32* __
     }
     if (pm > 0) {
       const u64 plo = klo + ((u64)d0 << sh);
-      const bool binned = sort_into_smem<false>(S, bk, bv, base + ps, pm, plo, span_top(d1 - d0, sh), plan, DECIDE);
+      const bool binned = sort_into_smem<false>(S, bk, bv, base + ps, pm, plo, span_top(d1 - d0, sh), plan, DECIDE,
+                                                Drop{nullptr, 0u, 0u, 0u}, rg);
       if (DECIDE) scan_piece(S, F, pm, base, plan->s, rg, plan, binned, plo);
       else write_out(S, bk, bv, base + ps, pm);
     }
@@ -767,7 +804,10 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
     const u32 span = fshift + ceil_log2(b.y - a.y);
     if (m <= (u32)kGroupCap) {
       if (m > 0) {
-        const bool binned = sort_into_smem<true>(S, ak, av, a.x, m, klo, span_top(b.y - a.y, fshift), plan, DECIDE);
+        const Drop dr{DECIDE ? F.bpre : nullptr, a.y, b.y - a.y, fshift};
+        const bool binned = sort_into_smem<true>(S, ak, av, a.x, m, klo, span_top(b.y - a.y, fshift), plan, DECIDE,
+                                                 dr, rg);
+        const u32 mp = S.cnt[kSubBins];        // the pairs placed (all of them without the drop)
         if (threadIdx.x == 0) {      // the next group's pairs into L2 (its descriptor has arrived)
           cp_async_wait_all();
           if (S.nid < ng) {
@@ -775,7 +815,7 @@ k3_bucket(const u64* __restrict__ ak, const u32* __restrict__ av, u64* bk, u32* 
             prefetch_span_l2(av, S.nab[0].x, S.nab[1].x, sizeof(u32), 8u * kGroupCap);
           }
         }
-        if (DECIDE) scan_piece(S, F, m, a.x, s, rg, plan, binned, klo);
+        if (DECIDE) scan_piece(S, F, mp, a.x, s, rg, plan, binned, klo);
         else write_out(S, bk, bv, a.x, m);
       }
     } else {
@@ -971,100 +1011,103 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
   }
 }
 
-// Exclusive prefixes of the groups' direction aggregates: a group's
-// aggregate is the combination of the tile aggregates of its bins (tagg,
-// ctiles from k3_split), one warp per group; then the last block gives
-// record g's inclusive words the combination of the aggregates of groups
-// 0 .. g - 1 with d(P_0) (the identity).
-constexpr int GB_BLOCK = 256;
-constexpr int GB_RB = 4;                   // records a thread loads at once in the scan
+// Exclusive prefixes of the bins' direction aggregates.  Thread b folds
+// bin b's tile aggregates (tagg, ctiles from k3_split) into bin b's
+// (lower, upper) words of bagg; the last block scans them: bin b's words of
+// bpre receive the extreme of the directions of every point in bins
+// 0 .. b - 1 together with d(P_0) (the identity), and record g's prefix
+// words the prefix of its first bin.  In the scan warp w owns bins
+// [w BP_SPAN, (w + 1) BP_SPAN), visited 32 at a time (lane l: the l-th bin
+// of a round), so every load and store is a coalesced 16-byte word pair.
+constexpr int BP_BLOCK = 512;
+constexpr int BP_WARPS = BP_BLOCK / 32;
+constexpr int BP_SPAN = kBins / BP_WARPS;  // bins per warp in the scan
+constexpr int BP_ROUNDS = BP_SPAN / 32;
+constexpr int BP_RB = 8;                   // rounds loaded together
+static_assert(BP_ROUNDS * 32 * BP_WARPS == kBins && BP_ROUNDS % BP_RB == 0, "whole rounds of 32 bins");
 
-// One block: the exclusive scan of the groups' aggregates.  Thread t takes
-// a contiguous slice of groups.
-__device__ void group_prefix_scan(Plan* plan, K4Chunk* recs, u32 ng, const RG& rg) {
-  __shared__ Dir2 s_w[GB_BLOCK / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 per = (ng + GB_BLOCK - 1) / GB_BLOCK;
-  const u32 g0 = min(ng, threadIdx.x * per), g1 = min(ng, g0 + per);
-  Dir2 t = rg.ident;
-  for (u32 gb = g0; gb < g1; gb += GB_RB) {
-    u64 wl[GB_RB], wu[GB_RB];
-    #pragma unroll
-    for (int q = 0; q < GB_RB; ++q) {
-      wl[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_lo) : 0ull;
-      wu[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_up) : 0ull;
-    }
-    #pragma unroll
-    for (int q = 0; q < GB_RB; ++q) {
-      if (gb + q >= g1) break;
-      Dir2 v;
-      unpack_dir(wl[q], v.lx, v.ly);
-      unpack_dir(wu[q], v.ux, v.uy);
-      combine(t, v);
-    }
-  }
-  const Dir2 inc = warp_scan_dir(t);
-  const Dir2 lex = shfl_up_dir(inc, 1);
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  Dir2 run = rg.ident;
-  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
-  if (lane > 0) combine(run, lex);
-  for (u32 gb = g0; gb < g1; gb += GB_RB) {
-    u64 wl[GB_RB], wu[GB_RB];
-    #pragma unroll
-    for (int q = 0; q < GB_RB; ++q) {
-      wl[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_lo) : 0ull;
-      wu[q] = gb + q < g1 ? *reinterpret_cast<const volatile u64*>(&recs[gb + q].agg_up) : 0ull;
-    }
-    #pragma unroll
-    for (int q = 0; q < GB_RB; ++q) {
-      if (gb + q >= g1) break;
-      recs[gb + q].inc_lo = pack_dir(run.lx, run.ly);
-      recs[gb + q].inc_up = pack_dir(run.ux, run.uy);
-      Dir2 v;
-      unpack_dir(wl[q], v.lx, v.ly);
-      unpack_dir(wu[q], v.ux, v.uy);
-      combine(run, v);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(GB_BLOCK)
-k_group_agg_bins(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
-                 const u64* __restrict__ tagg, const u32* __restrict__ ctiles) {
+__global__ void __launch_bounds__(BP_BLOCK)
+k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
+             const u64* __restrict__ tagg, const u32* __restrict__ ctiles, u64* __restrict__ bagg,
+             u64* __restrict__ bpre) {
   __shared__ bool s_last;
+  __shared__ Dir2 s_w[BP_WARPS];
   if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
-  const u32 ng = plan->ngroups;
   const RG rg = make_rg(plan);
-  const int lane = threadIdx.x & 31;
-  const u32 g = blockIdx.x * (GB_BLOCK / 32) + (threadIdx.x >> 5);
-  if (g < ng) {
-    const u32 b0 = groups[g].y, b1 = groups[g + 1].y;
-    Dir2 t = rg.ident;
-    for (u32 c = b0 / kFinePerCoarse; c * kFinePerCoarse < b1; ++c) {
-      const u32 lo = max(b0, c * kFinePerCoarse), hi = min(b1, (c + 1) * kFinePerCoarse);
-      const u32 nb = hi - lo, t0 = ctiles[c], ntl = ctiles[c + 1] - t0;
-      for (u32 e = lane; e < nb * ntl; e += 32) {
-        const u32 tile = t0 + e / nb, d = (lo - c * kFinePerCoarse) + e % nb;
-        const u64* w = tagg + (size_t)tile * (2 * kFinePerCoarse) + 2 * d;
-        const u64 wl = w[0], wu = w[1];
-        Dir2 v = rg.ident;
-        if (wl & kDirValid) unpack_dir(wl, v.lx, v.ly);
-        if (wu & kDirValid) unpack_dir(wu, v.ux, v.uy);
-        combine(t, v);
+  ulonglong2* a2 = reinterpret_cast<ulonglong2*>(bagg);
+  const u32 b = blockIdx.x * BP_BLOCK + threadIdx.x;
+  if (b < (u32)kBins) {
+    const u32 c = b / kFinePerCoarse, d = b % kFinePerCoarse;
+    const u32 t0 = ctiles[c], t1 = ctiles[c + 1];
+    Dir2 v = rg.ident;
+    for (u32 tb = t0; tb < t1; tb += 8) {       // eight tiles' words loaded together
+      u64 wv[16];
+      #pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const u64* w = tagg + (size_t)(tb + k) * (2 * kFinePerCoarse) + 2 * d;
+        wv[2 * k] = tb + k < t1 ? w[0] : 0ull;
+        wv[2 * k + 1] = tb + k < t1 ? w[1] : 0ull;
+      }
+      #pragma unroll
+      for (int k = 0; k < 8; ++k) combine(v, unpack_pair(wv[2 * k], wv[2 * k + 1], rg));
+    }
+    a2[b] = make_ulonglong2(pack_dir(v.lx, v.ly), pack_dir(v.ux, v.uy));
+  }
+  if (!last_block(plan, CTR_GROUP_AGG, &s_last)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 q0 = (u32)wid * BP_SPAN + lane;
+  // (L2 loads: the aggregates come from other blocks)
+  Dir2 t = rg.ident;
+  for (int r0 = 0; r0 < BP_ROUNDS; r0 += BP_RB) {
+    ulonglong2 wv[BP_RB];
+    #pragma unroll
+    for (int k = 0; k < BP_RB; ++k) wv[k] = __ldcg(&a2[q0 + (r0 + k) * 32]);
+    #pragma unroll
+    for (int k = 0; k < BP_RB; ++k) combine(t, unpack_pair(wv[k].x, wv[k].y, rg));
+  }
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
+  if (lane == 0) s_w[wid] = t;
+  __syncthreads();
+  Dir2 run = rg.ident;                          // every bin before the current round
+  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
+  ulonglong2* p2 = reinterpret_cast<ulonglong2*>(bpre);
+  for (int r0 = 0; r0 < BP_ROUNDS; r0 += BP_RB) {
+    ulonglong2 wv[BP_RB];
+    #pragma unroll
+    for (int k = 0; k < BP_RB; ++k) wv[k] = __ldcg(&a2[q0 + (r0 + k) * 32]);
+    #pragma unroll
+    for (int k = 0; k < BP_RB; ++k) {
+      const Dir2 inc = warp_scan_dir(unpack_pair(wv[k].x, wv[k].y, rg));
+      Dir2 e = run;
+      const Dir2 lex = shfl_up_dir(inc, 1);
+      if (lane > 0) combine(e, lex);
+      p2[q0 + (r0 + k) * 32] = make_ulonglong2(pack_dir(e.lx, e.ly), pack_dir(e.ux, e.uy));
+      combine(run, shfl_dir(inc, 31));
+    }
+  }
+  __syncthreads();
+  __threadfence_block();
+  const u32 ng = plan->ngroups;
+  for (u32 g0 = threadIdx.x; g0 < ng; g0 += 8 * BP_BLOCK) {   // eight groups per thread at a time
+    u32 fb[8];
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const u32 g = g0 + k * BP_BLOCK;
+      fb[k] = g < ng ? groups[g].y : 0u;
+    }
+    ulonglong2 wv[8];
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) wv[k] = __ldcg(&p2[fb[k]]);
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const u32 g = g0 + k * BP_BLOCK;
+      if (g < ng) {
+        recs[g].inc_lo = wv[k].x;
+        recs[g].inc_up = wv[k].y;
       }
     }
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
-    if (lane == 0) {
-      recs[g].agg_lo = pack_dir(t.lx, t.ly);
-      recs[g].agg_up = pack_dir(t.ux, t.uy);
-    }
   }
-  // The last block to finish scans the aggregates.
-  if (!last_block(plan, CTR_GROUP_AGG, &s_last)) return;
-  group_prefix_scan(plan, recs, ng, rg);
 }
 
 // Bin starts and groups.  k_binstart (the pipeline, one block) takes the
@@ -1358,19 +1401,18 @@ cudaError_t split_occupancy(int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k3_split, SP_BLOCK, SP_SMEM);
 }
 
-cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
-                                cudaStream_t st) {
-  K4Chunk* R = reinterpret_cast<K4Chunk*>(recs);
-  k_group_agg_bins<<<(kBins + GB_BLOCK / 32 - 1) / (GB_BLOCK / 32), GB_BLOCK, 0, st>>>(plan, R, groups, tagg,
-                                                                                      ctiles);
+cudaError_t launch_bin_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
+                              u64* bagg, u64* bpre, cudaStream_t st) {
+  k_bin_prefix<<<kBins / BP_BLOCK, BP_BLOCK, 0, st>>>(plan, reinterpret_cast<K4Chunk*>(recs), groups, tagg, ctiles,
+                                                      bagg, bpre);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
-                                 u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
-                                 int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
-                                 cudaStream_t st) {
-  Fused F{reinterpret_cast<K4Chunk*>(recs), t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx};
+                                 u32* scratch, void* recs, const u64* bpre, int2* t_lo_xy, int* t_lo_idx,
+                                 int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                                 int grid, cudaStream_t st) {
+  Fused F{reinterpret_cast<K4Chunk*>(recs), t_lo_xy, t_lo_idx, t_up_xy, t_up_idx, lo_xy, lo_idx, up_xy, up_idx, bpre};
   k3_bucket<true><<<grid, KB_BLOCK, sizeof(BucketSmem), st>>>(ak, av, bk, bv, plan, groups, scratch, F);
   return cudaGetLastError();
 }

@@ -67,12 +67,15 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
 // the bin scan) and their exclusive prefixes (one block), then the sort of
 // every group with the second round run on it (kept points into the t_*
 // staging areas; then launch_group_compact).
-cudaError_t launch_group_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
-                                cudaStream_t st);
+// Every bin's exclusive second-round prefix (bpre: 2 words per bin; bagg:
+// the bins' aggregates, scratch) from the split's tile aggregates, and the
+// groups' prefixes in their records.
+cudaError_t launch_bin_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
+                              u64* bagg, u64* bpre, cudaStream_t st);
 cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
-                                 u32* scratch, void* recs, int2* t_lo_xy, int* t_lo_idx, int2* t_up_xy,
-                                 int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int grid,
-                                 cudaStream_t st);
+                                 u32* scratch, void* recs, const u64* bpre, int2* t_lo_xy, int* t_lo_idx,
+                                 int2* t_up_xy, int* t_up_idx, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx,
+                                 int grid, cudaStream_t st);
 cudaError_t launch_group_compact(Plan* plan, const void* status, const int2* t_lo_xy, const int* t_lo_idx,
                                  const int2* t_up_xy, const int* t_up_idx, int2* lo_xy, int* lo_idx,
                                  int2* up_xy, int* up_idx, int grid, cudaStream_t st);
