@@ -51,7 +51,7 @@ struct Workspace {
   u64* tagg = nullptr;         // per split tile and bin: direction aggregates (lower, upper)
   u32* ctiles = nullptr;       // first split tile of every coarse bin
   u32* bcnt = nullptr;         // bins' totals, then coarse-bin cursors (k2_count)
-  u64* bagg = nullptr;         // per bin: direction aggregates (lower, upper), scratch of k_bin_prefix
+  u64* bagg = nullptr;         // per bin: prefix within its k_bin_prefix block (lower, upper), then block totals
   u64* bpre = nullptr;         // per bin: exclusive second-round prefix (lower, upper)
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   unsigned long long* key_or = nullptr;
@@ -198,7 +198,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_tagg = take(tiles_cap * 2 * kFinePerCoarse * 8);
   const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
   const size_t o_bcnt = take(((size_t)kBins + kCoarse) * 4);
-  const size_t o_bagg = take((size_t)kBins * 16);
+  const size_t o_bagg = take(((size_t)kBins + kBinPrefixBlocks) * 16);
   const size_t o_bpre = take((size_t)kBins * 16);
   const size_t o_fcur = take((size_t)kBins * 4);
   const size_t total = off;

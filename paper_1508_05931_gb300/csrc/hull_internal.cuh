@@ -47,6 +47,7 @@ constexpr int kSubBits = GBH_SUB_BITS;
 constexpr int kCoarseBits = 8;
 constexpr int kCoarse = 1 << kCoarseBits;
 constexpr int kFinePerCoarse = kBins / kCoarse;
+constexpr int kBinPrefixBlocks = 64;           // most block totals k_bin_prefix keeps after the bins
 constexpr int kSubBins = 1 << kSubBits;
 
 // Error bits accumulated in Plan::error by the kernels.

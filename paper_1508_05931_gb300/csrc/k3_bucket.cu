@@ -1011,20 +1011,21 @@ k3_split(const u64* __restrict__ ak, const u32* __restrict__ av, u64* __restrict
   }
 }
 
-// Exclusive prefixes of the bins' direction aggregates.  Thread b folds
-// bin b's tile aggregates (tagg, ctiles from k3_split) into bin b's
-// (lower, upper) words of bagg; the last block scans them: bin b's words of
-// bpre receive the extreme of the directions of every point in bins
-// 0 .. b - 1 together with d(P_0) (the identity), and record g's prefix
-// words the prefix of its first bin.  In the scan warp w owns bins
-// [w BP_SPAN, (w + 1) BP_SPAN), visited 32 at a time (lane l: the l-th bin
-// of a round), so every load and store is a coalesced 16-byte word pair.
+// Exclusive prefixes of the bins' direction aggregates.  Block k owns
+// bins [k BP_BLOCK, (k + 1) BP_BLOCK): thread b folds bin b's tile
+// aggregates (tagg, ctiles from k3_split), the block scans its bins and
+// writes each bin's prefix within the block to bagg and the block's total
+// after the kBins bins.  The last block scans the block totals and combines
+// each bin's prefix within its block with the totals of the blocks before
+// it: bin b's words of bpre receive the extreme of the directions of every
+// point in bins 0 .. b - 1 together with d(P_0) (the identity), lower and
+// upper region, and record g's prefix words the prefix of its first bin.
 constexpr int BP_BLOCK = 512;
+constexpr int BP_GRID = kBins / BP_BLOCK;
 constexpr int BP_WARPS = BP_BLOCK / 32;
-constexpr int BP_SPAN = kBins / BP_WARPS;  // bins per warp in the scan
-constexpr int BP_ROUNDS = BP_SPAN / 32;
-constexpr int BP_RB = 8;                   // rounds loaded together
-static_assert(BP_ROUNDS * 32 * BP_WARPS == kBins && BP_ROUNDS % BP_RB == 0, "whole rounds of 32 bins");
+constexpr int BP_PER = kBins / BP_BLOCK;   // bins per thread in the last block
+static_assert(BP_GRID * BP_BLOCK == kBins && BP_GRID <= 32 && BP_GRID <= kBinPrefixBlocks, "one lane per block total");
+static_assert(BP_PER % 8 == 0, "whole batches of eight");
 
 __global__ void __launch_bounds__(BP_BLOCK)
 k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ groups,
@@ -1032,11 +1033,13 @@ k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ g
              u64* __restrict__ bpre) {
   __shared__ bool s_last;
   __shared__ Dir2 s_w[BP_WARPS];
+  __shared__ Dir2 s_bx[BP_GRID];            // last block: exclusive prefixes of the block totals
   if (plan->error & (ERR_RANGE | ERR_FALLBACK)) return;
   const RG rg = make_rg(plan);
   ulonglong2* a2 = reinterpret_cast<ulonglong2*>(bagg);
-  const u32 b = blockIdx.x * BP_BLOCK + threadIdx.x;
-  if (b < (u32)kBins) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  {
+    const u32 b = blockIdx.x * BP_BLOCK + threadIdx.x;
     const u32 c = b / kFinePerCoarse, d = b % kFinePerCoarse;
     const u32 t0 = ctiles[c], t1 = ctiles[c + 1];
     Dir2 v = rg.ident;
@@ -1051,43 +1054,34 @@ k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ g
       #pragma unroll
       for (int k = 0; k < 8; ++k) combine(v, unpack_pair(wv[2 * k], wv[2 * k + 1], rg));
     }
-    a2[b] = make_ulonglong2(pack_dir(v.lx, v.ly), pack_dir(v.ux, v.uy));
+    const Dir2 inc = warp_scan_dir(v);
+    const Dir2 lex = shfl_up_dir(inc, 1);
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    Dir2 e = rg.ident;
+    for (int w = 0; w < wid; ++w) combine(e, s_w[w]);
+    if (threadIdx.x == BP_BLOCK - 1) {           // the block's total
+      Dir2 tot = e;
+      combine(tot, inc);
+      a2[kBins + blockIdx.x] = make_ulonglong2(pack_dir(tot.lx, tot.ly), pack_dir(tot.ux, tot.uy));
+    }
+    if (lane > 0) combine(e, lex);
+    a2[b] = make_ulonglong2(pack_dir(e.lx, e.ly), pack_dir(e.ux, e.uy));
   }
   if (!last_block(plan, CTR_GROUP_AGG, &s_last)) return;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 q0 = (u32)wid * BP_SPAN + lane;
-  // (L2 loads: the aggregates come from other blocks)
-  Dir2 t = rg.ident;
-  for (int r0 = 0; r0 < BP_ROUNDS; r0 += BP_RB) {
-    ulonglong2 wv[BP_RB];
-    #pragma unroll
-    for (int k = 0; k < BP_RB; ++k) wv[k] = __ldcg(&a2[q0 + (r0 + k) * 32]);
-    #pragma unroll
-    for (int k = 0; k < BP_RB; ++k) combine(t, unpack_pair(wv[k].x, wv[k].y, rg));
-  }
-  #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) combine(t, shfl_xor_dir(t, o));
-  if (lane == 0) s_w[wid] = t;
-  __syncthreads();
-  Dir2 run = rg.ident;                          // every bin before the current round
-  for (int w = 0; w < wid; ++w) combine(run, s_w[w]);
-  ulonglong2* p2 = reinterpret_cast<ulonglong2*>(bpre);
-  for (int r0 = 0; r0 < BP_ROUNDS; r0 += BP_RB) {
-    ulonglong2 wv[BP_RB];
-    #pragma unroll
-    for (int k = 0; k < BP_RB; ++k) wv[k] = __ldcg(&a2[q0 + (r0 + k) * 32]);
-    #pragma unroll
-    for (int k = 0; k < BP_RB; ++k) {
-      const Dir2 inc = warp_scan_dir(unpack_pair(wv[k].x, wv[k].y, rg));
-      Dir2 e = run;
-      const Dir2 lex = shfl_up_dir(inc, 1);
-      if (lane > 0) combine(e, lex);
-      p2[q0 + (r0 + k) * 32] = make_ulonglong2(pack_dir(e.lx, e.ly), pack_dir(e.ux, e.uy));
-      combine(run, shfl_dir(inc, 31));
+  // (L2 loads: the prefixes come from other blocks)
+  if (wid == 0) {
+    Dir2 t = rg.ident;
+    if (lane < BP_GRID) {
+      const ulonglong2 w = __ldcg(&a2[kBins + lane]);
+      t = unpack_pair(w.x, w.y, rg);
     }
+    const Dir2 inc = warp_scan_dir(t);
+    Dir2 ex = shfl_up_dir(inc, 1);
+    if (lane == 0) ex = rg.ident;
+    if (lane < BP_GRID) s_bx[lane] = ex;
   }
   __syncthreads();
-  __threadfence_block();
   const u32 ng = plan->ngroups;
   for (u32 g0 = threadIdx.x; g0 < ng; g0 += 8 * BP_BLOCK) {   // eight groups per thread at a time
     u32 fb[8];
@@ -1098,14 +1092,28 @@ k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ g
     }
     ulonglong2 wv[8];
     #pragma unroll
-    for (int k = 0; k < 8; ++k) wv[k] = __ldcg(&p2[fb[k]]);
+    for (int k = 0; k < 8; ++k) wv[k] = __ldcg(&a2[fb[k]]);
     #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const u32 g = g0 + k * BP_BLOCK;
       if (g < ng) {
-        recs[g].inc_lo = wv[k].x;
-        recs[g].inc_up = wv[k].y;
+        Dir2 e = s_bx[fb[k] / BP_BLOCK];
+        combine(e, unpack_pair(wv[k].x, wv[k].y, rg));
+        recs[g].inc_lo = pack_dir(e.lx, e.ly);
+        recs[g].inc_up = pack_dir(e.ux, e.uy);
       }
+    }
+  }
+  ulonglong2* p2 = reinterpret_cast<ulonglong2*>(bpre);
+  for (int k0 = 0; k0 < BP_PER; k0 += 8) {     // bin k BP_BLOCK + t: block k's prefix, then its own
+    ulonglong2 wv[8];
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) wv[k] = __ldcg(&a2[(k0 + k) * BP_BLOCK + threadIdx.x]);
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      Dir2 e = s_bx[k0 + k];
+      combine(e, unpack_pair(wv[k].x, wv[k].y, rg));
+      p2[(k0 + k) * BP_BLOCK + threadIdx.x] = make_ulonglong2(pack_dir(e.lx, e.ly), pack_dir(e.ux, e.uy));
     }
   }
 }

@@ -68,8 +68,8 @@ cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, P
 // every group with the second round run on it (kept points into the t_*
 // staging areas; then launch_group_compact).
 // Every bin's exclusive second-round prefix (bpre: 2 words per bin; bagg:
-// the bins' aggregates, scratch) from the split's tile aggregates, and the
-// groups' prefixes in their records.
+// scratch of kBins + kBinPrefixBlocks word pairs) from the split's tile
+// aggregates, and the groups' prefixes in their records.
 cudaError_t launch_bin_prefix(Plan* plan, const uint2* groups, void* recs, const u64* tagg, const u32* ctiles,
                               u64* bagg, u64* bpre, cudaStream_t st);
 cudaError_t launch_bucket_decide(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan, const uint2* groups,
