@@ -23,6 +23,11 @@ closed forms and invariants.  Pinning status per function:
                       the forward survivors, convex chains kept whole, a
                       hand-derived trace)
 * ``chain``           pinned (brute force on sorted input)
+* ``angular_sort``, ``angular_second_round``, ``graham``, ``angular_stages``
+                      (the paper's own angular ordering) pinned (exact
+                      rational slopes and fp64 atan2 for the order; the hull
+                      by definition and brute force; hull superset; a
+                      hand-derived trace of both walks)
 * the learned-proposal MLP (``oracle.mlp``) is pinned by finite differences
   and a closed-form tiny network.
 
@@ -85,6 +90,12 @@ def _load():
     lib.oracle_second_round_reverse.restype = ctypes.c_int
     lib.oracle_sort_xyi.argtypes = [P, I64]
     lib.oracle_sort_xyi.restype = None
+    lib.oracle_angular_sort.argtypes = [P, I64, P]
+    lib.oracle_angular_sort.restype = None
+    lib.oracle_angular_second_round.argtypes = [P, I64, P]
+    lib.oracle_angular_second_round.restype = I64
+    lib.oracle_graham.argtypes = [P, I64, P]
+    lib.oracle_graham.restype = I64
     _lib = lib
     return lib
 
@@ -263,3 +274,78 @@ def gscan_stages(xy, reverse: bool = False):
     uc = up_seq[chain(a[up_seq], -1)]
     out["hull"] = np.concatenate([lc, uc[1:-1][::-1]]).astype(np.int32)
     return out
+
+
+# ------------------------------------------------------- the angular variant
+
+def _triples(a: np.ndarray, idx) -> np.ndarray:
+    idx = np.asarray(idx, dtype=np.int64)
+    t = np.empty((idx.shape[0], 3), dtype=np.int32)
+    t[:, :2] = a[idx]
+    t[:, 2] = idx
+    return t
+
+
+def angular_sort(xy, idx, anchor: int) -> np.ndarray:
+    """Section 2.1 steps 3-4 (Sections 3.2-3.3): the indices `idx` ordered by
+    their angle about the point xy[anchor], ascending; points equal to the
+    anchor (the anchor included) are left out.  The anchor must be the
+    lowest point, leftmost among the lowest, so that every angle is in
+    [0, pi).  Equal angles: nearer first, then the smaller index."""
+    a = _pts(xy)
+    idx = np.asarray(idx, dtype=np.int64)
+    idx = idx[(a[idx, 0] != a[anchor, 0]) | (a[idx, 1] != a[anchor, 1])]
+    t = _triples(a, idx)
+    at = _triples(a, [anchor])
+    _load().oracle_angular_sort(_ptr(t), t.shape[0], _ptr(at))
+    return t[:, 2].copy()
+
+
+def angular_second_round(xy, order):
+    """Sections 2.1 steps 5-7 and 2.2, Figure 2 as printed, over `order` =
+    [anchor, its points in angular order]: P_l is the point farthest from
+    the anchor, the right region (positions 1 .. l - 1) is walked forward
+    from P_0, the left region (l + 1 .. m - 2) backward from P_{m-1}.
+    Returns (keep, l): keep[i] tells whether position i survives (P_0, P_l
+    and P_{m-1} always do); l = -1 when the list holds the anchor alone."""
+    a = _pts(xy)
+    t = _triples(a, order)
+    keep = np.zeros(max(t.shape[0], 1), dtype=np.uint8)
+    l = _load().oracle_angular_second_round(_ptr(t), t.shape[0], _ptr(keep))
+    return keep[: t.shape[0]].astype(bool), int(l)
+
+
+def graham(xy, seq) -> np.ndarray:
+    """Section 2.1 step 8 read as Graham's scan over `seq` = [anchor, points
+    in angular order]: returns the hull as input indices, counter-clockwise
+    from the anchor, strict vertices only."""
+    a = _pts(xy)
+    t = _triples(a, seq)
+    out = np.empty(max(t.shape[0], 1), dtype=np.int32)
+    h = _load().oracle_graham(_ptr(t), t.shape[0], _ptr(out))
+    return t[out[:h], 2].astype(np.int32)
+
+
+def angular_stages(xy):
+    """The method with the paper's angular ordering, in its order (Section
+    2.1 steps 1-8): extremes, the quadrilateral filter, the angular sort
+    about P_miny, P_longest and the two walks of Figure 2, Graham's scan.
+    Returns a dict of intermediates: anchor, keep (first-round survivors),
+    order ([anchor] + angular order), l_pos, kept (the second round's
+    survivors of `order`, a boolean mask), survivors (their indices, in
+    order) and hull (counter-clockwise from the anchor)."""
+    a = _pts(xy)
+    out = {"n": a.shape[0]}
+    if a.shape[0] == 0:
+        z = np.zeros(0, np.int32)
+        out.update(anchor=-1, keep=z, order=z, l_pos=-1, kept=np.zeros(0, bool), survivors=z, hull=z)
+        return out
+    anchor = int(extremes(a)[2])
+    keep = quad_filter(a)
+    order = np.concatenate([[anchor], angular_sort(a, keep, anchor)]).astype(np.int32)
+    kept, l = angular_second_round(a, order)
+    surv = order[kept]
+    out.update(anchor=anchor, keep=keep, order=order, l_pos=l, kept=kept, survivors=surv,
+               hull=graham(a, surv))
+    return out
+

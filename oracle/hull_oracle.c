@@ -299,3 +299,105 @@ void oracle_sort_xyi(int32_t *xyi, int64_t m)
 {
     qsort(xyi, (size_t)m, sizeof(opt_t), cmp_xyi);
 }
+
+/*
+ * The paper's own ordering (Section 2.1 steps 3-4, Sections 3.2-3.3): the
+ * points sorted by their angle about an anchor, ascending.  Readings (the
+ * paper names neither the anchor nor a tie rule): the anchor is P_miny =
+ * argmin (y, x, idx), the pivot of Graham's scan, so every other point not
+ * equal to it lies in dy > 0 or (dy == 0, dx > 0) and its angle about the
+ * anchor is in [0, pi); inside that half-plane angle(a) < angle(b) exactly
+ * when orient(anchor, a, b) > 0, so the order is decided by an exact int64
+ * cross product, never by a rounded angle.  Equal angles are ordered by the
+ * squared distance to the anchor (the distance of Section 3.2), then by
+ * index.  The triples p[0 .. m) must not coincide with the anchor.
+ */
+static opt_t g_anchor;
+
+static int cmp_angle(const void *pa, const void *pb)
+{
+    const opt_t *a = (const opt_t *)pa, *b = (const opt_t *)pb;
+    const int64_t o = orient(&g_anchor, a, b);
+    if (o != 0) return o > 0 ? -1 : 1;
+    const int64_t ax = (int64_t)a->x - g_anchor.x, ay = (int64_t)a->y - g_anchor.y;
+    const int64_t bx = (int64_t)b->x - g_anchor.x, by = (int64_t)b->y - g_anchor.y;
+    const int64_t da = ax * ax + ay * ay, db = bx * bx + by * by;
+    if (da != db) return da < db ? -1 : 1;
+    if (a->idx != b->idx) return a->idx < b->idx ? -1 : 1;
+    return 0;
+}
+
+void oracle_angular_sort(int32_t *xyi, int64_t m, const int32_t *anchor_xyi)
+{
+    g_anchor.x = anchor_xyi[0];
+    g_anchor.y = anchor_xyi[1];
+    g_anchor.idx = anchor_xyi[2];
+    qsort(xyi, (size_t)m, sizeof(opt_t), cmp_angle);
+}
+
+/*
+ * Sections 2.1 steps 5-7 and 2.2, Figure 2 as printed, over a list in the
+ * angular order above: p[0] is the anchor P_0, p[1 .. m) its points sorted
+ * by angle.  P_l is the point farthest from P_0 (step 5; the first in list
+ * order among equally far points).  The right region (step 6) is walked
+ * forward: P_temp starts at P_0 and for i = 1 .. l - 1 the point P_i is
+ * interior when it lies left of or on the directed line P_temp -> P_l,
+ * otherwise it is kept and becomes P_temp.  The left region is walked
+ * backward: P_temp starts at P_{m-1}, which stays, and for i = m - 2 down to
+ * l + 1 the point P_i is interior when it lies right of or on the line
+ * P_temp -> P_l, otherwise it is kept and becomes P_temp.  ("On the line"
+ * counts as interior: such a point lies on the segment from P_temp to P_l,
+ * so it is never a strict hull vertex.)  keep[i] receives 1 for P_0, P_l,
+ * P_{m-1} and every kept point, else 0.  Returns l, or -1 when m < 2.
+ */
+int64_t oracle_angular_second_round(const int32_t *xyi, int64_t m, uint8_t *keep)
+{
+    const opt_t *p = (const opt_t *)xyi;
+    if (m < 2) {
+        if (m == 1) keep[0] = 1;
+        return -1;
+    }
+    int64_t l = 1, best = -1;
+    for (int64_t i = 1; i < m; ++i) {
+        const int64_t dx = (int64_t)p[i].x - p[0].x, dy = (int64_t)p[i].y - p[0].y;
+        const int64_t d = dx * dx + dy * dy;
+        if (d > best) { best = d; l = i; }
+    }
+    for (int64_t i = 0; i < m; ++i) keep[i] = 0;
+    keep[0] = 1;
+    keep[l] = 1;
+    keep[m - 1] = 1;
+    const opt_t *t = &p[0];
+    for (int64_t i = 1; i < l; ++i) {
+        if (orient(t, &p[l], &p[i]) < 0) { keep[i] = 1; t = &p[i]; }
+    }
+    t = &p[m - 1];
+    for (int64_t i = m - 2; i > l; --i) {
+        if (orient(t, &p[l], &p[i]) > 0) { keep[i] = 1; t = &p[i]; }
+    }
+    return l;
+}
+
+/*
+ * Section 2.1 step 8 read as Graham's scan over the survivors in angular
+ * order (p[0] the anchor): for each point in order, a point equal to the top
+ * of the stack is skipped (the first of equal points stays), then the stack
+ * is popped while its last two points and the new one do not make a strict
+ * left turn, then the point is pushed.  No closing pass is needed: points of
+ * equal angle arrive nearer first, and a nearer point B on the ray of a
+ * farther C makes a right turn A -> B -> C with any A of smaller angle (or a
+ * straight one with A = P_0), so C pops it, on the last ray too.  Writes the
+ * hull's positions (counter-clockwise from the anchor) to out; returns their
+ * count.
+ */
+int64_t oracle_graham(const int32_t *xyi, int64_t m, int32_t *out)
+{
+    const opt_t *p = (const opt_t *)xyi;
+    int64_t h = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (h > 0 && same_xy(&p[out[h - 1]], &p[i])) continue;
+        while (h >= 2 && orient(&p[out[h - 2]], &p[out[h - 1]], &p[i]) <= 0) --h;
+        out[h++] = (int32_t)i;
+    }
+    return h;
+}
