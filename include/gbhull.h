@@ -339,6 +339,24 @@ hull_status hull_stage_regions(hull_ctx *ctx, const int32_t *d_xy, int64_t n, in
 hull_status hull_stage_chain(hull_ctx *ctx, const int32_t *d_xy, int64_t m, int32_t *d_out,
                              int64_t cap, int64_t *h_lower, int64_t *h_upper, void *stream);
 
+/* Section 2.1 steps 1-7 with the paper's own ordering (Sections 3.2-3.3:
+ * the first-round survivors sorted by angle; Figure 2 as printed: P_l the
+ * point farthest from P_0, the right region walked forward from P_0, the
+ * left region backward from the last point), on n >= 1 points (d_xy device
+ * int32[n][2], 8-byte aligned).  The anchor P_0 is P_miny = argmin (y, x,
+ * index); points equal to it are left out; the order is exact (an integer
+ * angle key, never a rounded angle) with equal angles nearer first, then by
+ * index.  Writes [P_0, the points by angle] as input indices to d_order
+ * (device int32[cap]) and 1 / 0 to d_keep (device uint8[cap]) for each
+ * position the second round keeps / discards (P_0, P_l and the last point
+ * are always kept); *h_m receives the number of positions and *h_l the
+ * position of P_l (-1 when P_0 is the only distinct point).  HULL_ECAPACITY
+ * when cap < *h_m (nothing written); HULL_ERANGE for coordinates beyond
+ * +-2^29.  Allocates and frees its temporary buffers; synchronises
+ * `stream`. */
+hull_status hull_stage_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_order,
+                               uint8_t *d_keep, int64_t cap, int64_t *h_m, int64_t *h_l, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

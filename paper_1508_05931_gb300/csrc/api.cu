@@ -753,6 +753,85 @@ hull_status hull_stage_sorted_survivors(hull_ctx* c, const int32_t* d_xy, int64_
   return r;
 }
 
+// Temporary device buffers of one stage call, freed on every return.
+struct TempBufs {
+  void* p[8] = {};
+  int k = 0;
+  cudaError_t take(size_t bytes, void** out) {
+    const cudaError_t e = cudaMalloc(out, bytes < 16 ? 16 : bytes);
+    if (e == cudaSuccess) p[k++] = *out;
+    return e;
+  }
+  ~TempBufs() {
+    for (int j = 0; j < k; ++j) cudaFree(p[j]);
+  }
+};
+
+hull_status hull_stage_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_order, uint8_t* d_keep,
+                               int64_t cap, int64_t* h_m, int64_t* h_l, void* stream) {
+  if (!c || !d_xy || !h_m || !h_l || n < 1 || cap < 0 || n > (int64_t)kMaxN || !aligned8(d_xy)) return HULL_EINVAL;
+  if (cap > 0 && (!d_order || !d_keep)) return HULL_EINVAL;
+  *h_m = 0;
+  *h_l = -1;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t ext[4];
+  hull_status r = hull_stage_extremes(c, d_xy, n, ext, stream);
+  if (r != HULL_OK) return r;
+  const u32 anchor = (u32)ext[2];
+  TempBufs t;
+  void *keep, *k1, *v1, *k2, *v2, *pts, *small, *walk;
+  const size_t nn = (size_t)n;
+  cudaError_t e = t.take(nn * 4, &keep);
+  if (e == cudaSuccess) e = t.take(nn * 8, &k1);
+  if (e == cudaSuccess) e = t.take(nn * 4, &v1);
+  if (e == cudaSuccess) e = t.take(nn * 8, &k2);
+  if (e == cudaSuccess) e = t.take(nn * 4, &v2);
+  if (e == cudaSuccess) e = t.take((nn + 1) * 8, &pts);
+  if (e == cudaSuccess) e = t.take(16, &small);     // [0] points equal to the anchor, [1] P_l's position
+  if (e == cudaSuccess) e = t.take(angle_walk_scratch_bytes((u32)n + 1), &walk);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int64_t s = 0;
+  r = hull_stage_filter(c, d_xy, n, static_cast<int32_t*>(keep), &s, stream);
+  if (r != HULL_OK) return r;
+  u32* n_same = static_cast<u32*>(small);
+  u32* lpos = n_same + 1;
+  const int2* xy2 = reinterpret_cast<const int2*>(d_xy);
+  e = cudaMemsetAsync(n_same, 0, 4, st);
+  if (e == cudaSuccess)
+    e = launch_angle_dist(xy2, static_cast<const int*>(keep), (u32)s, anchor, static_cast<u64*>(k1),
+                          static_cast<u32*>(v1), n_same, c->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = hull_stage_sort(c, static_cast<uint64_t*>(k1), static_cast<uint32_t*>(v1), s, stream);
+  if (r != HULL_OK) return r;
+  e = launch_angle_keys(xy2, static_cast<const u64*>(k1), static_cast<const u32*>(v1), (u32)s, anchor,
+                        static_cast<u64*>(k2), static_cast<u32*>(v2), c->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = hull_stage_sort(c, static_cast<uint64_t*>(k2), static_cast<uint32_t*>(v2), s, stream);
+  if (r != HULL_OK) return r;
+  u32 same = 0;
+  e = cudaMemcpyAsync(&same, n_same, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int64_t m1 = s - (int64_t)same + 1;
+  *h_m = m1;
+  if (m1 > cap) return HULL_ECAPACITY;
+  e = launch_angle_order(xy2, static_cast<const u32*>(v1), static_cast<const u32*>(v2), (u32)m1, anchor, d_order,
+                         static_cast<int2*>(pts), c->num_sms, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (m1 == 1) {
+    e = cudaMemsetAsync(d_keep, 1, 1, st);
+  } else {
+    e = launch_angle_walks(static_cast<const int2*>(pts), (u32)m1, walk, lpos, d_keep, c->num_sms, st);
+    u32 l = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, lpos, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) *h_l = (int64_t)l;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
 hull_status hull_stage_second_round_chunked(hull_ctx* c, const int32_t* d_xy, const int32_t* d_idx, int64_t m,
                                             int32_t block_size, int32_t* d_lower, int64_t* h_lower, int32_t* d_upper,
                                             int64_t* h_upper, void* stream) {

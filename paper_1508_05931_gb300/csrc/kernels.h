@@ -154,4 +154,21 @@ cudaError_t mlp_backward(const float* W, const float* X, const float* Y, int B, 
 cudaError_t mlp_adam(float* W, const float* grad, float* m, float* v, int step, float lr,
                      void* w16, cudaStream_t st);
 
+// The paper's angular ordering (angular.cu): pass-1 pairs (squared distance
+// to the anchor, index) of the first-round survivors keep[0 .. s) and the
+// count of points equal to the anchor (n_same, incremented); pass-2 pairs
+// (angle key, pass-1 rank) in pass-1 order; the order ([anchor, points by
+// angle], m1 entries) as indices and coordinates; P_longest (lpos) and the
+// two walks of Figure 2 into keep flags (m1 >= 2; scratch of
+// angle_walk_scratch_bytes(m1) bytes).
+cudaError_t launch_angle_dist(const int2* xy, const int* keep, u32 s, u32 anchor, u64* keys, u32* vals, u32* n_same,
+                              int num_sms, cudaStream_t st);
+cudaError_t launch_angle_keys(const int2* xy, const u64* dkeys, const u32* dvals, u32 s, u32 anchor, u64* keys,
+                              u32* vals, int num_sms, cudaStream_t st);
+cudaError_t launch_angle_order(const int2* xy, const u32* dvals, const u32* avals, u32 m1, u32 anchor, int* order,
+                               int2* pts, int num_sms, cudaStream_t st);
+size_t angle_walk_scratch_bytes(u32 m1);
+cudaError_t launch_angle_walks(const int2* pts, u32 m1, void* scratch, u32* lpos, unsigned char* keep, int num_sms,
+                               cudaStream_t st);
+
 }  // namespace gbh

@@ -92,6 +92,7 @@ _sig = {
     "hull_stage_regions": ([_P, _P, _I64, _P, _I64, _P, _I64, _PI64, ctypes.POINTER(ctypes.c_int32), _P],
                            ctypes.c_int),
     "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
+    "hull_stage_angular": ([_P, _P, _I64, _P, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -441,6 +442,23 @@ class Context:
                                                 _stream_handle(stream)), "hull_stage_sorted_survivors")
         return oxy[: cnt.value], oid[: cnt.value]
 
+    def stage_angular(self, pts, stream=None):
+        """Steps 1-7 with the paper's angular ordering: (order, keep, l) --
+        [P_0, the first-round survivors by angle about P_miny] as input
+        indices, the second round's keep flags for those positions (bool),
+        and the position of P_longest (-1 when P_0 is the only distinct
+        point)."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(pts, dev)
+        n = xy.shape[0]
+        order = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        keep = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        m, l = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hull_stage_angular(self._h, _ptr(xy), n, _ptr(order), _ptr(keep), max(n, 1), ctypes.byref(m),
+                                       ctypes.byref(l), _stream_handle(stream)), "hull_stage_angular")
+        return order[: m.value], keep[: m.value].bool(), int(l.value)
+
     def stage_second_round_chunked(self, xy_sorted, labels, block_size=1024, stream=None):
         """Section 3.4's chunked second round over sorted points: (lower
         labels, upper labels)."""
@@ -521,3 +539,4 @@ hull_stage_second_round_chunked = _lib.hull_stage_second_round_chunked
 hull_stage_sorted_survivors = _lib.hull_stage_sorted_survivors
 hull_compute_multi = _lib.hull_compute_multi
 hull_stage_chain = _lib.hull_stage_chain
+hull_stage_angular = _lib.hull_stage_angular

@@ -1,0 +1,87 @@
+"""Parity of the angular front (the paper's sort by angle about P_miny,
+P_longest and Figure 2's forward and backward walks), called through the C
+ABI, against the oracle on the same seeded inputs: the order, the position
+of P_longest and every keep flag, element by element (integer work:
+bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_05931_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx(hull_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hull_lib.Context(0)
+    yield c
+    c.close()
+
+
+def _check(ctx, xy):
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    order, keep, l = ctx.stage_angular(torch.as_tensor(xy).cuda())
+    st = oracle.angular_stages(xy)
+    got = order.cpu().numpy()
+    assert got.tolist() == st["order"].tolist()
+    assert l == st["l_pos"]
+    assert keep.cpu().numpy().tolist() == st["kept"].tolist()
+    return st
+
+
+def _families():
+    rng = np.random.default_rng(41)
+    yield "square_200k", W.uniform_square(200_000, 1 << 29, 42)
+    yield "disk_300k", W.uniform_disk(300_000, float(1 << 29), 43)
+    yield "near_circle_100k", W.near_circle(100_000, float(1 << 28), 44)
+    yield "gaussian_200k", W.gaussian(200_000, float(1 << 26), 45)
+    yield "clusters_200k", W.gaussian_clusters(200_000, 46)
+    yield "aniso_100k", W.anisotropic_gaussian(100_000, 47)
+    yield "grid", W.filled_grid(300, 200, -17, 5)
+    yield "lattice_dups", rng.integers(-6, 7, size=(50_000, 2)).astype(np.int32)
+    yield "extreme_coords", rng.integers(-(1 << 29), (1 << 29) + 1, size=(100_000, 2)).astype(np.int32)
+    yield "collinear", np.stack([3 * np.arange(5000) - 9000, -2 * np.arange(5000) + 7], 1).astype(np.int32)
+    yield "vertical", np.stack([np.zeros(3000, np.int64) + 5, np.arange(3000)], 1).astype(np.int32)
+    yield "horizontal", np.stack([np.arange(3000), np.zeros(3000, np.int64) - 4], 1).astype(np.int32)
+
+
+@pytest.mark.parametrize("name,xy", list(_families()), ids=[n for n, _ in _families()])
+def test_angular_front_parity(ctx, name, xy):
+    _check(ctx, xy)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 2047, 2048, 2049, 4097, 65537])
+def test_angular_front_ragged_sizes(ctx, n):
+    # sizes around the walks' tile of 2048 positions, every point surviving
+    # the first round (a ring), plus uniform points
+    _check(ctx, W.near_circle(n, float(1 << 20), 50 + n))
+    _check(ctx, W.uniform_disk(n, float(1 << 20), 60 + n))
+
+
+def test_angular_front_degenerate(ctx):
+    st = _check(ctx, np.full((100, 2), 7, np.int32))                    # one distinct point
+    assert st["l_pos"] == -1
+    _check(ctx, np.array([[3, 4]], np.int32))
+    _check(ctx, np.array([[0, 0], [5, 0]], np.int32))                   # angle 0 only
+    _check(ctx, np.array([[0, 0], [-5, 3], [5, 3]], np.int32))
+    ring = W.near_circle(4000, float(1 << 24), 70)
+    _check(ctx, np.concatenate([ring, ring, ring[:100]]))               # every point duplicated
+
+
+def test_angular_front_large(ctx):
+    # a few hundred walk tiles: 2M disk points, about 0.7M first-round survivors
+    _check(ctx, W.uniform_disk(2_000_000, float(1 << 29), 80))
+
+
+def test_angular_front_hand_trace(ctx):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "angular_second_round_trace.json")))
+    xy = np.array(g["points"], dtype=np.int32)
+    st = _check(ctx, xy)
+    names = g["names"]
+    assert [names[i] for i in st["survivors"]] == [n for n in g["expected_kept"] if n not in g["expected_first_round_removed"]]
