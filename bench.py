@@ -296,6 +296,30 @@ def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
     return res
 
 
+def bench_angular_front(hull, torch, stream, dev_sets):
+    """The paper's own ordering (steps 1-7 with the sort by angle about
+    P_miny and Figure 2's forward and backward walks) through its stage entry
+    point, on the two 20M sets: ms per call (the entry allocates its own
+    buffers and synchronises), first-round survivors and second-round
+    survivors.  Its failure never touches the main line."""
+    res = {}
+    try:
+        with hull.Context(torch.cuda.current_device()) as c:
+            for name, t in zip(("square_20M", "disk_20M"), dev_sets):
+                order, keep, l = c.stage_angular(t, stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    order, keep, l = c.stage_angular(t, stream)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) / 3 * 1e3
+                res[name] = {"ms": ms, "m": int(order.shape[0]), "kept": int(keep.sum().item()),
+                             "l_pos": int(l), "timing": "host clock around 3 synchronising calls"}
+    except Exception as exc:       # a section of its own: report, do not fail the run
+        res["error"] = str(exc)[:200]
+    return res
+
+
 def bench_second_round_ablation(hull, torch, stream, dev_sets):
     """Section 3.4's chunked second round (BLOCK_SIZE = 1024, one block per
     region, one thread per run, as the paper runs it) against the exact scan
@@ -538,6 +562,7 @@ def main():
     if world == 1 and not args.no_batched:
         line["reverse_round"] = bench_reverse_round(hull, torch, stream, dev_sets, dev_outs)
         line["second_round_ablation"] = bench_second_round_ablation(hull, torch, stream, dev_sets)
+        line["angular_front"] = bench_angular_front(hull, torch, stream, dev_sets)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

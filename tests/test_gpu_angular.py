@@ -33,25 +33,35 @@ def _check(ctx, xy):
     return st
 
 
-def _families():
+def _lattice_dups():
+    return np.random.default_rng(41).integers(-6, 7, size=(50_000, 2)).astype(np.int32)
+
+
+def _extreme_coords():
     rng = np.random.default_rng(41)
-    yield "square_200k", W.uniform_square(200_000, 1 << 29, 42)
-    yield "disk_300k", W.uniform_disk(300_000, float(1 << 29), 43)
-    yield "near_circle_100k", W.near_circle(100_000, float(1 << 28), 44)
-    yield "gaussian_200k", W.gaussian(200_000, float(1 << 26), 45)
-    yield "clusters_200k", W.gaussian_clusters(200_000, 46)
-    yield "aniso_100k", W.anisotropic_gaussian(100_000, 47)
-    yield "grid", W.filled_grid(300, 200, -17, 5)
-    yield "lattice_dups", rng.integers(-6, 7, size=(50_000, 2)).astype(np.int32)
-    yield "extreme_coords", rng.integers(-(1 << 29), (1 << 29) + 1, size=(100_000, 2)).astype(np.int32)
-    yield "collinear", np.stack([3 * np.arange(5000) - 9000, -2 * np.arange(5000) + 7], 1).astype(np.int32)
-    yield "vertical", np.stack([np.zeros(3000, np.int64) + 5, np.arange(3000)], 1).astype(np.int32)
-    yield "horizontal", np.stack([np.arange(3000), np.zeros(3000, np.int64) - 4], 1).astype(np.int32)
+    rng.integers(-6, 7, size=(50_000, 2))          # the lattice's draw comes first in the same stream
+    return rng.integers(-(1 << 29), (1 << 29) + 1, size=(100_000, 2)).astype(np.int32)
 
 
-@pytest.mark.parametrize("name,xy", list(_families()), ids=[n for n, _ in _families()])
-def test_angular_front_parity(ctx, name, xy):
-    _check(ctx, xy)
+FAMILIES = {
+    "square_200k": lambda: W.uniform_square(200_000, 1 << 29, 42),
+    "disk_300k": lambda: W.uniform_disk(300_000, float(1 << 29), 43),
+    "near_circle_100k": lambda: W.near_circle(100_000, float(1 << 28), 44),
+    "gaussian_200k": lambda: W.gaussian(200_000, float(1 << 26), 45),
+    "clusters_200k": lambda: W.gaussian_clusters(200_000, 46),
+    "aniso_100k": lambda: W.anisotropic_gaussian(100_000, 47),
+    "grid": lambda: W.filled_grid(300, 200, -17, 5),
+    "lattice_dups": _lattice_dups,
+    "extreme_coords": _extreme_coords,
+    "collinear": lambda: np.stack([3 * np.arange(5000) - 9000, -2 * np.arange(5000) + 7], 1).astype(np.int32),
+    "vertical": lambda: np.stack([np.zeros(3000, np.int64) + 5, np.arange(3000)], 1).astype(np.int32),
+    "horizontal": lambda: np.stack([np.arange(3000), np.zeros(3000, np.int64) - 4], 1).astype(np.int32),
+}
+
+
+@pytest.mark.parametrize("name", list(FAMILIES))
+def test_angular_front_parity(ctx, name):
+    _check(ctx, FAMILIES[name]())
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 2047, 2048, 2049, 4097, 65537])
