@@ -95,3 +95,23 @@ def test_angular_front_hand_trace(ctx):
     st = _check(ctx, xy)
     names = g["names"]
     assert [names[i] for i in st["survivors"]] == [n for n in g["expected_kept"] if n not in g["expected_first_round_removed"]]
+
+
+def test_angular_front_farey_directions(ctx):
+    # directions whose slopes differ by 1 / (F_k F_{k+1}) (consecutive
+    # Fibonacci ratios, close to the key's 2^-60 bound), in all four 45-degree
+    # sectors, exact sector boundaries, and equal directions at several
+    # lengths; anchor (0, -2^29), so |dx| <= 2^29 and dy <= 2^30
+    F = [0, 1]
+    while len(F) < 46:
+        F.append(F[-1] + F[-2])
+    dirs = []
+    for k in (40, 41, 42, 43):
+        a, b, c = F[k - 1], F[k], F[k + 1]
+        dirs += [(b, a), (a, F[k - 2]), (a, b), (b, c), (-a, b), (-b, c), (-b, a), (-a, F[k - 2])]
+    dirs += [(5000, 0), (1000, 1000), (999, 1000), (1000, 999), (0, 5000), (-7000, 7000), (-6999, 7000),
+             (-5000, 1), (1 << 29, 1), (-(1 << 29), 1), (1 << 29, 1 << 30), (-(1 << 29), 1 << 30)]
+    dirs += [(3 * s, 2 * s) for s in (1, 2, 5, 40)] + [(-2 * s, 3 * s) for s in (1, 3, 7)]
+    xy = np.array([(0, -(1 << 29))] + [(dx, dy - (1 << 29)) for dx, dy in dirs], dtype=np.int64)
+    assert np.abs(xy).max() <= 1 << 29
+    _check(ctx, xy.astype(np.int32))
