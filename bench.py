@@ -299,9 +299,10 @@ def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
 def bench_angular_front(hull, torch, stream, dev_sets):
     """The paper's own ordering (steps 1-7 with the sort by angle about
     P_miny and Figure 2's forward and backward walks) through its stage entry
-    point, on the two 20M sets: ms per call (the entry allocates its own
-    buffers and synchronises), first-round survivors and second-round
-    survivors.  Its failure never touches the main line."""
+    point, and the whole angular hull (steps 1-8), on the two 20M sets: ms
+    per call (the entries allocate their own buffers and synchronise),
+    first-round and second-round survivors, hull size.  Its failure never
+    touches the main line."""
     res = {}
     try:
         with hull.Context(torch.cuda.current_device()) as c:
@@ -313,8 +314,16 @@ def bench_angular_front(hull, torch, stream, dev_sets):
                     order, keep, l = c.stage_angular(t, stream)
                 torch.cuda.synchronize()
                 ms = (time.perf_counter() - t0) / 3 * 1e3
+                hull_idx = c.compute_angular(t, stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    hull_idx = c.compute_angular(t, stream)
+                torch.cuda.synchronize()
+                hull_ms = (time.perf_counter() - t0) / 3 * 1e3
                 res[name] = {"ms": ms, "m": int(order.shape[0]), "kept": int(keep.sum().item()),
-                             "l_pos": int(l), "timing": "host clock around 3 synchronising calls"}
+                             "l_pos": int(l), "hull_ms": hull_ms, "h": int(hull_idx.shape[0]),
+                             "timing": "host clock around 3 synchronising calls"}
     except Exception as exc:       # a section of its own: report, do not fail the run
         res["error"] = str(exc)[:200]
     return res

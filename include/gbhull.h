@@ -357,6 +357,19 @@ hull_status hull_stage_chain(hull_ctx *ctx, const int32_t *d_xy, int64_t m, int3
 hull_status hull_stage_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_order,
                                uint8_t *d_keep, int64_t cap, int64_t *h_m, int64_t *h_l, void *stream);
 
+/* The convex hull by the paper's angular variant, steps 1-8: the front of
+ * hull_stage_angular, then step 8 (the hull of the points the second round
+ * keeps) on the device, over those points in angular order, with the same
+ * chains as hull_compute.  d_xy: device int32[n][2] (8-byte aligned),
+ * n >= 0.  d_out: device int32[cap] receiving the hull's vertex indices,
+ * counter-clockwise from the lexicographic minimum, strict vertices only;
+ * among equal points the first in angular order is reported (the one
+ * Graham's scan keeps).  *h_count receives the hull size on HULL_OK and on
+ * HULL_ECAPACITY (then d_out is untouched).  Allocates and frees its
+ * temporary buffers; synchronises `stream`. */
+hull_status hull_compute_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out, int64_t cap,
+                                 int64_t *h_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -264,6 +264,38 @@ k_angle_mark(const int2* __restrict__ pts, u32 m1, const u32* __restrict__ lpos,
   }
 }
 
+// Step 8 of the angular variant: the kept positions (in any order; sorted
+// afterwards), their points and labels in angular order, and the hull's
+// positions mapped back to input indices.
+__global__ void __launch_bounds__(AK_BLOCK)
+k_angle_compact(const unsigned char* __restrict__ keep, u32 m1, u32* __restrict__ pos, u32* __restrict__ cnt) {
+  for (u32 p = blockIdx.x * blockDim.x + threadIdx.x; p < m1; p += gridDim.x * blockDim.x)
+    if (keep[p]) pos[atomicAdd(cnt, 1u)] = p;
+}
+
+__global__ void __launch_bounds__(AK_BLOCK)
+k_angle_poskeys(const u32* __restrict__ pos, u32 r, u64* __restrict__ keys, u32* __restrict__ vals) {
+  for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < r; j += gridDim.x * blockDim.x) {
+    keys[j] = pos[j];
+    vals[j] = pos[j];
+  }
+}
+
+__global__ void __launch_bounds__(AK_BLOCK)
+k_angle_gather(const int2* __restrict__ xy, const int* __restrict__ order, const u32* __restrict__ spos, u32 r,
+               int2* __restrict__ xy_c, int* __restrict__ lab) {
+  for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < r; j += gridDim.x * blockDim.x) {
+    const int i = order[spos[j]];
+    xy_c[j] = xy[i];
+    lab[j] = i;
+  }
+}
+
+__global__ void __launch_bounds__(AK_BLOCK)
+k_angle_label(const int* __restrict__ out_c, const int* __restrict__ lab, u32 h, int* __restrict__ out) {
+  for (u32 k = blockIdx.x * blockDim.x + threadIdx.x; k < h; k += gridDim.x * blockDim.x) out[k] = lab[out_c[k]];
+}
+
 int grid_of(u32 n, int num_sms) {
   const u32 g = (n + AK_BLOCK - 1) / AK_BLOCK;
   const u32 cap = (u32)num_sms * 8u;
@@ -287,6 +319,26 @@ cudaError_t launch_angle_keys(const int2* xy, const u64* dkeys, const u32* dvals
 cudaError_t launch_angle_order(const int2* xy, const u32* dvals, const u32* avals, u32 m1, u32 anchor, int* order,
                                int2* pts, int num_sms, cudaStream_t st) {
   k_angle_order<<<grid_of(m1, num_sms), AK_BLOCK, 0, st>>>(xy, dvals, avals, m1, anchor, order, pts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angle_compact(const unsigned char* keep, u32 m1, u32* pos, u32* cnt, int num_sms, cudaStream_t st) {
+  k_angle_compact<<<grid_of(m1, num_sms), AK_BLOCK, 0, st>>>(keep, m1, pos, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angle_gather(const int2* xy, const int* order, u32* pos, u32 r, u64* keys, u32* vals, int2* xy_c,
+                                int* lab, int num_sms, cudaStream_t st, int phase) {
+  if (phase == 0) {
+    k_angle_poskeys<<<grid_of(r, num_sms), AK_BLOCK, 0, st>>>(pos, r, keys, vals);
+  } else {
+    k_angle_gather<<<grid_of(r, num_sms), AK_BLOCK, 0, st>>>(xy, order, vals, r, xy_c, lab);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angle_label(const int* out_c, const int* lab, u32 h, int* out, int num_sms, cudaStream_t st) {
+  k_angle_label<<<grid_of(h, num_sms), AK_BLOCK, 0, st>>>(out_c, lab, h, out);
   return cudaGetLastError();
 }
 

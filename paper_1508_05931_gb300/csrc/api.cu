@@ -832,6 +832,59 @@ hull_status hull_stage_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, int3
   return e == cudaSuccess ? HULL_OK : cuda_fail(e);
 }
 
+hull_status hull_compute_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_out, int64_t cap,
+                                 int64_t* h_count, void* stream) {
+  if (!c || !h_count || n < 0 || cap < 0 || n > (int64_t)kMaxN) return HULL_EINVAL;
+  if (n > 0 && (!d_xy || !aligned8(d_xy))) return HULL_EINVAL;
+  if (cap > 0 && !d_out) return HULL_EINVAL;
+  *h_count = 0;
+  if (n == 0) return HULL_OK;
+  DevGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TempBufs t;
+  void *order, *keep, *pos, *keys, *vals, *xyc, *lab, *outc;
+  const size_t nn = (size_t)n;
+  cudaError_t e = t.take(nn * 4, &order);
+  if (e == cudaSuccess) e = t.take(nn + 16, &keep);
+  if (e == cudaSuccess) e = t.take(nn * 4 + 16, &pos);      // the count, then the positions
+  if (e == cudaSuccess) e = t.take(nn * 8, &keys);
+  if (e == cudaSuccess) e = t.take(nn * 4, &vals);
+  if (e == cudaSuccess) e = t.take(nn * 8, &xyc);
+  if (e == cudaSuccess) e = t.take(nn * 4, &lab);
+  if (e == cudaSuccess) e = t.take(nn * 4, &outc);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int64_t m1 = 0, l = -1;
+  hull_status r = hull_stage_angular(c, d_xy, n, static_cast<int32_t*>(order), static_cast<uint8_t*>(keep), n, &m1,
+                                     &l, stream);
+  if (r != HULL_OK) return r;
+  u32* cnt = static_cast<u32*>(pos);
+  u32* ppos = cnt + 4;
+  e = cudaMemsetAsync(cnt, 0, 4, st);
+  if (e == cudaSuccess)
+    e = launch_angle_compact(static_cast<const unsigned char*>(keep), (u32)m1, ppos, cnt, c->num_sms, st);
+  u32 rc = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rc, cnt, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess)
+    e = launch_angle_gather(nullptr, nullptr, ppos, rc, static_cast<u64*>(keys), static_cast<u32*>(vals), nullptr,
+                            nullptr, c->num_sms, st, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  r = hull_stage_sort(c, static_cast<uint64_t*>(keys), static_cast<uint32_t*>(vals), rc, stream);
+  if (r != HULL_OK) return r;
+  e = launch_angle_gather(reinterpret_cast<const int2*>(d_xy), static_cast<const int*>(order), ppos, rc,
+                          static_cast<u64*>(keys), static_cast<u32*>(vals), static_cast<int2*>(xyc),
+                          static_cast<int*>(lab), c->num_sms, st, 1);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int64_t h = 0;
+  r = hull_compute(c, static_cast<const int32_t*>(xyc), rc, static_cast<int32_t*>(outc), rc, &h, stream);
+  if (r != HULL_OK) return r;
+  *h_count = h;
+  if (h > cap) return HULL_ECAPACITY;
+  e = launch_angle_label(static_cast<const int*>(outc), static_cast<const int*>(lab), (u32)h, d_out, c->num_sms, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? HULL_OK : cuda_fail(e);
+}
+
 hull_status hull_stage_second_round_chunked(hull_ctx* c, const int32_t* d_xy, const int32_t* d_idx, int64_t m,
                                             int32_t block_size, int32_t* d_lower, int64_t* h_lower, int32_t* d_upper,
                                             int64_t* h_upper, void* stream) {

@@ -168,6 +168,15 @@ cudaError_t launch_angle_keys(const int2* xy, const u64* dkeys, const u32* dvals
 cudaError_t launch_angle_order(const int2* xy, const u32* dvals, const u32* avals, u32 m1, u32 anchor, int* order,
                                int2* pts, int num_sms, cudaStream_t st);
 size_t angle_walk_scratch_bytes(u32 m1);
+// Step 8 of the angular variant: the kept positions of keep[0 .. m1) into
+// pos (unordered, count in cnt); phase 0 turns them into (position,
+// position) pairs for the sort, phase 1 gathers the points and input
+// indices of the sorted positions (vals); the hull's positions out_c[0 .. h)
+// mapped to input indices.
+cudaError_t launch_angle_compact(const unsigned char* keep, u32 m1, u32* pos, u32* cnt, int num_sms, cudaStream_t st);
+cudaError_t launch_angle_gather(const int2* xy, const int* order, u32* pos, u32 r, u64* keys, u32* vals, int2* xy_c,
+                                int* lab, int num_sms, cudaStream_t st, int phase);
+cudaError_t launch_angle_label(const int* out_c, const int* lab, u32 h, int* out, int num_sms, cudaStream_t st);
 cudaError_t launch_angle_walks(const int2* pts, u32 m1, void* scratch, u32* lpos, unsigned char* keep, int num_sms,
                                cudaStream_t st);
 

@@ -93,6 +93,7 @@ _sig = {
                            ctypes.c_int),
     "hull_stage_chain": ([_P, _P, _I64, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
     "hull_stage_angular": ([_P, _P, _I64, _P, _P, _I64, _PI64, _PI64, _P], ctypes.c_int),
+    "hull_compute_angular": ([_P, _P, _I64, _P, _I64, _PI64, _P], ctypes.c_int),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -459,6 +460,19 @@ class Context:
                                        ctypes.byref(l), _stream_handle(stream)), "hull_stage_angular")
         return order[: m.value], keep[: m.value].bool(), int(l.value)
 
+    def compute_angular(self, pts, stream=None):
+        """The hull by the paper's angular variant (steps 1-8 on the device):
+        vertex indices, counter-clockwise from the lexicographic minimum."""
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        xy = _as_points(pts, dev)
+        n = xy.shape[0]
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        h = ctypes.c_int64()
+        _check(_lib.hull_compute_angular(self._h, _ptr(xy), n, _ptr(out), max(n, 1), ctypes.byref(h),
+                                         _stream_handle(stream)), "hull_compute_angular")
+        return out[: h.value]
+
     def stage_second_round_chunked(self, xy_sorted, labels, block_size=1024, stream=None):
         """Section 3.4's chunked second round over sorted points: (lower
         labels, upper labels)."""
@@ -540,3 +554,4 @@ hull_stage_sorted_survivors = _lib.hull_stage_sorted_survivors
 hull_compute_multi = _lib.hull_compute_multi
 hull_stage_chain = _lib.hull_stage_chain
 hull_stage_angular = _lib.hull_stage_angular
+hull_compute_angular = _lib.hull_compute_angular

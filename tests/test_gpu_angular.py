@@ -115,3 +115,41 @@ def test_angular_front_farey_directions(ctx):
     xy = np.array([(0, -(1 << 29))] + [(dx, dy - (1 << 29)) for dx, dy in dirs], dtype=np.int64)
     assert np.abs(xy).max() <= 1 << 29
     _check(ctx, xy.astype(np.int32))
+
+
+def _lexrot(xy, h):
+    """The cycle h rotated to begin at its lexicographically smallest point."""
+    h = [int(v) for v in h]
+    if not h:
+        return h
+    k = min(range(len(h)), key=lambda i: (int(xy[h[i], 0]), int(xy[h[i], 1])))
+    return h[k:] + h[:k]
+
+
+def _check_hull(ctx, xy):
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    got = ctx.compute_angular(torch.as_tensor(xy).cuda()).cpu().numpy().tolist()
+    st = oracle.angular_stages(xy)
+    assert got == _lexrot(xy, st["hull"])                   # Graham's scan over the oracle's survivors
+    ref = oracle.hull(xy)
+    assert sorted(map(tuple, xy[got].tolist())) == sorted(map(tuple, xy[ref].tolist()))
+
+
+@pytest.mark.parametrize("name", ["square_200k", "disk_300k", "near_circle_100k", "clusters_200k", "grid",
+                                  "lattice_dups", "extreme_coords", "collinear", "vertical", "horizontal"])
+def test_angular_hull_parity(ctx, name):
+    _check_hull(ctx, FAMILIES[name]())
+
+
+def test_angular_hull_small_and_degenerate(ctx):
+    for xy in (np.full((9, 2), 3, np.int32), np.array([[1, 2]], np.int32), np.array([[0, 0], [5, 0]], np.int32),
+               np.array([[0, 0], [-5, 3], [5, 3]], np.int32)):
+        _check_hull(ctx, xy)
+    ring = W.near_circle(4000, float(1 << 24), 70)
+    _check_hull(ctx, np.concatenate([ring, ring, ring[:100]]))
+    for seed in range(30):
+        rng = np.random.default_rng(300 + seed)
+        n = int(rng.integers(1, 60))
+        _check_hull(ctx, rng.integers(-4, 5, size=(n, 2)).astype(np.int32))
+    assert ctx.compute_angular(torch.zeros((0, 2), dtype=torch.int32).cuda()).numel() == 0
+
