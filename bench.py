@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -123,7 +124,8 @@ def oracle_timing(sets, budget_s=20.0, sample_pts=None):
 class ClockSampler:
     def __init__(self, enabled, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (the JSON line carries their summary)
+        self.path = os.environ.get("GBH_CLOCKS_CSV", os.path.join(tempfile.gettempdir(), "gbh_clocks_bench.csv"))
         if not enabled:
             return
         try:
