@@ -6,7 +6,9 @@
  * (Section 2.1 step 1), quadrilateral filter (step 2, Section 3.1), sort
  * (step 4, Section 3.3), region split and second-round filter (steps 5-7,
  * Section 2.2, Figure 2, Section 3.4) and the finalisation (step 8), every
- * step on the GPU.
+ * step on the GPU.  The paper's own angular ordering (steps 3-8 with the sort
+ * by angle, Sections 3.2-3.3) is available beside it: hull_stage_angular,
+ * hull_compute_angular.
  *
  * Conventions shared by every entry point
  *   - Points are int32 (x, y) pairs, array-of-structures, 8 bytes per point,
@@ -16,8 +18,10 @@
  *   - A hull is the list of its strict vertices (collinear boundary points
  *     excluded) as 0-based input indices, counter-clockwise, starting at the
  *     lexicographically smallest (x, y); among equal points the smallest
- *     index is reported.  n = 0 gives 0 vertices, one distinct point gives
- *     1, collinear points give the 2 endpoints.
+ *     index is reported (hull_compute_angular: the first in angular order,
+ *     which its backward walk may make a larger one).  n = 0 gives 0
+ *     vertices, one distinct point gives 1, collinear points give the 2
+ *     endpoints.
  *   - Pointers named d_* are device pointers, h_* host pointers.  The
  *     caller owns every buffer it passes; the library never frees or keeps
  *     them past the call.  A context owns its device workspace (grown on
