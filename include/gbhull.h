@@ -18,8 +18,9 @@
  *   - A hull is the list of its strict vertices (collinear boundary points
  *     excluded) as 0-based input indices, counter-clockwise, starting at the
  *     lexicographically smallest (x, y); among equal points the smallest
- *     index is reported (hull_compute_angular: the first in angular order,
- *     which its backward walk may make a larger one).  n = 0 gives 0
+ *     index is reported (hull_compute_angular: the first in angular order
+ *     among the points its second round keeps; its backward walk keeps the
+ *     largest index of equal points).  n = 0 gives 0
  *     vertices, one distinct point gives 1, collinear points give the 2
  *     endpoints.
  *   - Pointers named d_* are device pointers, h_* host pointers.  The
@@ -367,8 +368,9 @@ hull_status hull_stage_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, in
  * chains as hull_compute.  d_xy: device int32[n][2] (8-byte aligned),
  * n >= 0.  d_out: device int32[cap] receiving the hull's vertex indices,
  * counter-clockwise from the lexicographic minimum, strict vertices only;
- * among equal points the first in angular order is reported (the one
- * Graham's scan keeps).  *h_count receives the hull size on HULL_OK and on
+ * among equal points the first in angular order among those the second
+ * round keeps is reported (the one Graham's scan keeps; the backward walk
+ * keeps the largest index of equal points).  *h_count receives the hull size on HULL_OK and on
  * HULL_ECAPACITY (then d_out is untouched).  Allocates and frees its
  * temporary buffers; synchronises `stream`. */
 hull_status hull_compute_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out, int64_t cap,
