@@ -64,3 +64,17 @@ def test_null_arguments_rejected_without_gpu():
     assert hull._lib.hull_compute(None, None, 10, None, 0, ctypes.byref(cnt), None) == hull.HULL_EINVAL
     assert hull._lib.hull_last_stats(None, None) == hull.HULL_EINVAL
     hull._lib.hull_destroy(None)
+
+
+def test_stage_and_variant_entries_reject_null_context_without_gpu():
+    build.build_library()
+    from paper_1508_05931_gb300 import hull
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    E = hull.HULL_EINVAL
+    L = hull._lib
+    assert L.hull_stage_angular(None, None, 10, None, None, 0, ctypes.byref(a), ctypes.byref(b), None) == E
+    assert L.hull_compute_angular(None, None, 10, None, 0, ctypes.byref(a), None) == E
+    assert L.hull_stage_sorted_survivors(None, None, 10, None, None, 0, ctypes.byref(a), None) == E
+    assert L.hull_stage_second_round_chunked(None, None, None, 10, 1024, None, ctypes.byref(a), None,
+                                             ctypes.byref(b), None) == E
+    assert L.hull_compute_multi(None, 1, None, None, None, None, None, None) == E
