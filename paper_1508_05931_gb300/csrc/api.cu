@@ -755,9 +755,11 @@ hull_status hull_stage_sorted_survivors(hull_ctx* c, const int32_t* d_xy, int64_
 
 // Temporary device buffers of one stage call, freed on every return.
 struct TempBufs {
-  void* p[8] = {};
+  static constexpr int kSlots = 8;
+  void* p[kSlots] = {};
   int k = 0;
   cudaError_t take(size_t bytes, void** out) {
+    if (k == kSlots) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMalloc(out, bytes < 16 ? 16 : bytes);
     if (e == cudaSuccess) p[k++] = *out;
     return e;
