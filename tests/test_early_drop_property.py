@@ -105,3 +105,23 @@ def test_drop_removes_most_region_points_on_uniform_input():
     lo, up, lpos = oracle.second_round(xy, srt)
     drop = _dropped(xy, srt, lo, up, lpos, np.arange(0, len(srt), 256))
     assert len(drop) > 0.8 * len(srt)
+
+
+@pytest.mark.parametrize("name,xy", [("square", W.uniform_square(6000, 1 << 20, 22)),
+                                     ("disk", W.uniform_disk(6000, float(1 << 20), 23)),
+                                     ("dups", np.random.default_rng(24).integers(-8, 9, size=(4000, 2)).astype(np.int32))],
+                         ids=["square", "disk", "dups"])
+def test_nested_drops_are_exact(name, xy):
+    # a drop over coarse runs, then another over finer runs of what is left
+    # (each against the prefix Figure 2 holds at its run's start): the kept
+    # lists never change
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    srt = _sorted_survivors(xy)
+    lo, up, lpos = oracle.second_round(xy, srt)
+    rest = np.delete(srt, _dropped(xy, srt, lo, up, lpos, np.arange(0, len(srt), 512)))
+    lo1, up1, lpos1 = oracle.second_round(xy, rest)
+    assert lo1.tolist() == lo.tolist() and up1.tolist() == up.tolist()
+    rest2 = np.delete(rest, _dropped(xy, rest, lo1, up1, lpos1, np.arange(0, len(rest), 16)))
+    lo2, up2, _ = oracle.second_round(xy, rest2)
+    assert lo2.tolist() == lo.tolist() and up2.tolist() == up.tolist()
+    assert len(rest2) <= len(rest) <= len(srt)
