@@ -84,6 +84,10 @@ typedef struct {
   int32_t learned_used; /* 1 when the learned polygon replaced the quadrilateral */
   int32_t sort_fallback; /* 1 when the bucket sort met a bin it cannot sort in shared memory
                             and the call was rerun on the radix passes */
+  int64_t s_witness;  /* first-round survivors left by the fused filter's test against the
+                         sampled witnesses (Figure 2's test against a sampled earlier
+                         survivor of the same bin range and region; every point it removes
+                         Figure 2 removes too); equals s on the radix passes */
 } hull_stats;
 
 /* Creates a context on CUDA device `device` (cfg NULL = defaults).

@@ -54,6 +54,8 @@ struct Workspace {
   u64* bagg = nullptr;         // per bin: prefix within its k_bin_prefix block (lower, upper), then block totals
   u64* bpre = nullptr;         // per bin: exclusive second-round prefix (lower, upper)
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
+  u64* wkey = nullptr;         // per region and witness bin: the sample's best witness (follows bcnt)
+  int2* sample = nullptr;      // every kSampleStride-th point (K1 copies them out)
   unsigned long long* key_or = nullptr;
 };
 
@@ -94,7 +96,8 @@ struct hull_ctx {
   hull_config cfg{};
   int num_sms = 0;
   int occ_k2c = 1, occ_k2 = 1, occ_k3 = 1, occ_k4 = 1, occ_k5 = 1;
-  int occ_k2b = 1, occ_kb = 1, occ_sp = 1;  // bucket sort: K2 with bin rows, group sort, split
+  int occ_kb = 1, occ_sp = 1;  // bucket sort: group sort, split
+  int occ_kf = 1;              // the fused filter
   Plan* plan = nullptr;        // device
   Plan* h_plan = nullptr;      // pinned host mirror of the summary fields
   char* h_multi = nullptr;     // pinned summaries of hull_compute_multi (one per input)
@@ -188,7 +191,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_jobs = take(nchunks * 16);
   const size_t o_aux = take(cap * 4);
   const size_t o_mask = take(cap / 8 + 4096);
-  const size_t rows_cap = (size_t)c->num_sms * (size_t)std::max(c->occ_k2b, 2);
+  const size_t rows_cap = (size_t)c->num_sms * 2;   // histogram rows of the array sort (array_hist_grid)
   const size_t o_rows = take(rows_cap * kBins * 4);
   const size_t o_bstart = take((size_t)kBins * 4);
   const size_t o_groups = take(((size_t)kBins + 2) * 8);
@@ -198,6 +201,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_tagg = take(tiles_cap * 2 * kFinePerCoarse * 8);
   const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
   const size_t o_bcnt = take(((size_t)kBins + kCoarse) * 4);
+  const size_t o_wkey = take((size_t)2 * kWitnessBins * 8);   // right after bcnt: one memset clears both
+  const size_t o_sample = take((cap / kSampleStride + 1) * 8);
   const size_t o_bagg = take(((size_t)kBins + kBinPrefixBlocks) * 16);
   const size_t o_bpre = take((size_t)kBins * 16);
   const size_t o_fcur = take((size_t)kBins * 4);
@@ -245,6 +250,8 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.bagg = reinterpret_cast<u64*>(b + o_bagg);
   w.bpre = reinterpret_cast<u64*>(b + o_bpre);
   w.fcur = reinterpret_cast<u32*>(b + o_fcur);
+  w.wkey = reinterpret_cast<u64*>(b + o_wkey);
+  w.sample = reinterpret_cast<int2*>(b + o_sample);
   return HULL_OK;
 }
 
@@ -287,11 +294,12 @@ hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
     f.radix_calls += p.sorted_in_b && p.ngroups ? 0 : 1;
     f.sort_passes += p.npasses;
     f.points += p.n;
-    f.survivors += p.s;
+    f.survivors += p.s_quad;
     f.second_round += (int64_t)p.r_lo + p.r_up;
   }
   if (c->cfg.collect_stats) {
-    c->last.n = p.n; c->last.s = p.s; c->last.r_lower = p.r_lo; c->last.r_upper = p.r_up;
+    c->last.n = p.n; c->last.s = p.s_quad; c->last.s_witness = p.s;
+    c->last.r_lower = p.r_lo; c->last.r_upper = p.r_up;
     c->last.h = p.h;
     for (int j = 0; j < 4; ++j) c->last.ext[j] = p.ext_idx[j];
     c->last.ncorner = p.ncorner;
@@ -316,7 +324,8 @@ void mark(hull_ctx* c, int k, cudaStream_t st) {
 hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, bool bucket) {
   Workspace& w = c->ws;
   mark(c, 0, st);
-  cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st);
+  cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st,
+                            bucket ? w.sample : nullptr);
   if (e != cudaSuccess) return cuda_fail(e);
   if (c->cfg.proposal == 1 && c->have_weights) {
     // Learned filter polygon: sampled features, MLP, exact hull of the
@@ -328,17 +337,26 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   mark(c, 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
   if (bucket) {
-    // Survivors scattered into bins, every group's direction aggregate and
-    // their prefixes, then one block per group of bins sorts it in shared
-    // memory and runs the second round on it from its prefix.
-    // Profile slots: 1 filter (count + bin scan), 2 scatter (coarse bins),
-    // 3 split (fine bins, their aggregates, group prefixes), 4 sort (+ second
-    // round), 5..9 empty, 10 compaction.
-    const int g2 = std::min(grid_for(c->occ_k2b, c->num_sms, t2), (int)w.rows_cap);
-    e = launch_k2_bins(d_xy, c->plan, w.st_filter, w.mask, w.rows, w.bcnt, w.bstart, w.groups, w.fcur, g2, st);
+    // The fused front: witnesses from a sample, then one pass that filters,
+    // tests every first-round survivor against its bin's witness and
+    // compacts what is left with the bins' totals; the bin starts and groups;
+    // the survivors moved into coarse-bin order.  Then the split into bins
+    // (with their direction aggregates), every bin's and group's prefix, and
+    // one block per group of bins sorts it in shared memory and runs the
+    // second round on it from its prefix.
+    // Profile slots: 1 filter (witnesses, fused filter, bin scan), 2 scatter
+    // (coarse bins), 3 split (fine bins, their aggregates, group prefixes),
+    // 4 sort (+ second round), 5..9 empty, 10 compaction.
+    e = cudaMemsetAsync(w.bcnt, 0, (reinterpret_cast<char*>(w.wkey) - reinterpret_cast<char*>(w.bcnt)) +
+                                       (size_t)2 * kWitnessBins * sizeof(u64), st);
+    if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
+    if (e == cudaSuccess)
+      e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, c->cfg.collect_stats != 0,
+                          c->occ_kf * c->num_sms, st);
+    if (e == cudaSuccess) e = launch_binstart(w.bcnt, c->plan, w.bstart, w.groups, w.fcur, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
-    e = launch_k2_bins_scatter(d_xy, c->plan, w.keys[0], w.idx[0], w.mask, w.rows, w.bstart, g2, st);
+    e = launch_place(w.keys[1], w.idx[1], n, c->plan, w.bstart, w.bcnt + kBins, w.keys[0], w.idx[0], c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 3, st);
     e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.tagg, w.ctiles,
@@ -532,7 +550,8 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return cuda_fail(cudaErrorUnknown); }
   c->num_sms = prop.multiProcessorCount;
   if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess || bucket_configure() != cudaSuccess ||
-      k2_bins_occupancy(&c->occ_k2b) != cudaSuccess || bucket_occupancy(&c->occ_kb) != cudaSuccess ||
+      fused_configure() != cudaSuccess || fused_occupancy(&c->occ_kf) != cudaSuccess ||
+      bucket_occupancy(&c->occ_kb) != cudaSuccess ||
       split_occupancy(&c->occ_sp) != cudaSuccess ||
       k5_configure(&c->occ_k5) != cudaSuccess ||
       k2_occupancy(&c->occ_k2c, &c->occ_k2) != cudaSuccess || k3_occupancy(&c->occ_k3) != cudaSuccess ||
@@ -540,7 +559,10 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
     delete c;
     return cuda_fail(cudaErrorUnknown);
   }
-  if (c->occ_k5 < 1 || c->occ_k2b < 1 || c->occ_kb < 1 || c->occ_sp < 1) { delete c; return HULL_ECUDA; }
+  if (c->occ_k5 < 1 || c->occ_kb < 1 || c->occ_sp < 1 || c->occ_kf < 1) {
+    delete c;
+    return HULL_ECUDA;
+  }
   if (batch_configure(&c->occ_b256, &c->occ_b512) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->bev[0], cudaEventDisableTiming) != cudaSuccess ||

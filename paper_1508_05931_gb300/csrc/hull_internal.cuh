@@ -49,6 +49,14 @@ constexpr int kCoarse = 1 << kCoarseBits;
 constexpr int kFinePerCoarse = kBins / kCoarse;
 constexpr int kBinPrefixBlocks = 64;           // most block totals k_bin_prefix keeps after the bins
 constexpr int kSubBins = 1 << kSubBits;
+// The fused front's witnesses come from every kSampleStride-th point, which
+// K1 copies out while it reads them.
+constexpr u32 kSampleStride = 32;
+// Witness bins: the top kWitnessBits of the key (coarser than the sort's bins,
+// so that the fused filter's table of witness directions, 2 x 8 bytes per
+// bin, fits in shared memory beside its ring of input chunks).
+constexpr int kWitnessBits = 12;
+constexpr int kWitnessBins = 1 << kWitnessBits;
 
 // Error bits accumulated in Plan::error by the kernels.
 enum : u32 {
@@ -76,7 +84,9 @@ enum CounterSlot : int {
   CTR_BIN_GROUP = 6 + kMaxPasses,         // next group of the bucket sort
   CTR_SPLIT = 7 + kMaxPasses,             // next tile of the coarse-to-fine split
   CTR_GROUP_AGG = 8 + kMaxPasses,         // last-block counter of the group aggregates
-  kNumCounters = 17,
+  CTR_WITNESS = 9 + kMaxPasses,           // last-block counter of the sampled witnesses
+  CTR_FUSED = 10 + kMaxPasses,            // next output slot of the fused filter
+  kNumCounters = 19,
 };
 
 struct ExtPartial {
@@ -90,7 +100,9 @@ struct Plan {
   u32 spin_limit;
   u32 epoch;            // base epoch of the current call
   u32 error;
-  u32 s;                // survivors of the first round
+  u32 s;                // survivors of the first round (on the fused path: those left
+                        // after the sampled-witness test, the sort's input)
+  u32 s_quad;           // survivors of the first-round filter polygon alone
   u32 r_lo, r_up;       // survivors of the second round per region
   u32 h;                // hull size
   u32 h_lo, h_up;       // chain lengths (including both endpoints)
@@ -247,9 +259,10 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
   return ok != 0u;
 }
 // Waits for the given phase of `bar` to complete; false if it did not within
-// kBulkWaitLimit rounds.
-__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity) {
-  for (u32 it = 0; it < kBulkWaitLimit; ++it)
+// `limit` rounds (the call's spin limit for the waits of a ring; the fixed
+// kBulkWaitLimit for the drain at a kernel's end).
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, u32 limit = kBulkWaitLimit) {
+  for (u32 it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

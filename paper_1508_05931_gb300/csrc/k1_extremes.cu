@@ -6,6 +6,9 @@
 //   P_minx: key (x, y)        P_maxx: complement of key (x, y)
 //   P_miny: key (y, x)        P_maxy: complement of key (y, x)
 // so ties resolve lexicographically and then to the smallest index.
+// With a sample buffer it also copies every kSampleStride-th point there
+// (sample[i] = point i kSampleStride), the input of the fused front's
+// witnesses, while the points are in registers anyway.
 // Warp shuffles, then a block reduction, then the last block to finish
 // reduces the per-block partials and builds the Plan: the range check, the
 // counter-clockwise filter polygon, the radix-key layout, the epoch, and
@@ -132,25 +135,40 @@ __device__ void finish_plan(Plan* plan, const Best& b) {
 template <int BLOCK, bool VEC>
 __global__ void __launch_bounds__(BLOCK)
 k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
-            ExtPartial* __restrict__ partials) {
+            ExtPartial* __restrict__ partials, int2* __restrict__ sample) {
+  constexpr u32 kPairStride = kSampleStride / 2;   // pair j holds sample point j / kPairStride
+  static_assert(kSampleStride % 2 == 0, "sampled points start a pair");
   Best b;
   best_init(b);
   const u32 tid = blockIdx.x * BLOCK + threadIdx.x;
   const u32 nthreads = gridDim.x * BLOCK;
   {
     // Seed every thread's skip box with the bounding box of a strided
-    // sample: a point strictly inside the box spanned by input points
-    // cannot be an extreme.  (The sample points themselves still reach
-    // their owners as candidates: they lie on or outside that box.)
+    // sample of kBoxSample points (the same points in every block, so all
+    // but the first reads come from L2): a point strictly inside the box
+    // spanned by input points cannot be an extreme.  (The sample points
+    // themselves still reach their owners as candidates: they lie on or
+    // outside that box.)  A larger sample leaves fewer points outside the
+    // box, and a warp whose points all lie inside skips them with one vote.
+    constexpr u32 kBoxSample = 16 * BLOCK;
     __shared__ int s_box[4];
     if (threadIdx.x == 0) { s_box[0] = 0x7FFFFFFF; s_box[1] = (int)0x80000000; s_box[2] = 0x7FFFFFFF; s_box[3] = (int)0x80000000; }
     __syncthreads();
-    const u32 step = n / BLOCK + 1;
-    const u32 j = threadIdx.x * step;
+    const u32 step = n / kBoxSample + 1;
     int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
-    if (j < n) {
-      const int2 p = reinterpret_cast<const int2*>(xy)[j];
-      x0 = x1 = p.x; y0 = y1 = p.y;
+    int2 sp[kBoxSample / BLOCK];
+    #pragma unroll
+    for (u32 q = 0; q < kBoxSample / BLOCK; ++q) {
+      const u32 j = (threadIdx.x + q * BLOCK) * step;
+      sp[q] = j < n ? reinterpret_cast<const int2*>(xy)[j] : make_int2(x0, y0);
+    }
+    #pragma unroll
+    for (u32 q = 0; q < kBoxSample / BLOCK; ++q) {
+      const u32 j = (threadIdx.x + q * BLOCK) * step;
+      if (j < n) {
+        x0 = min(x0, sp[q].x); x1 = max(x1, sp[q].x);
+        y0 = min(y0, sp[q].y); y1 = max(y1, sp[q].y);
+      }
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -177,18 +195,28 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
       for (int u = 0; u < 8; ++u) v[u] = p4[j + u * nthreads];
       #pragma unroll
       for (int u = 0; u < 8; ++u) consider2(b, v[u], 2 * (j + u * nthreads));
+      if (sample) {
+        #pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if ((j + u * nthreads) % kPairStride == 0) sample[(j + u * nthreads) / kPairStride] = make_int2(v[u].x, v[u].y);
+      }
     }
     for (; j < npair; j += nthreads) {
       int4 v = p4[j];
       consider(b, v.x, v.y, 2 * j);
       consider(b, v.z, v.w, 2 * j + 1);
+      if (sample && j % kPairStride == 0) sample[j / kPairStride] = make_int2(v.x, v.y);
     }
-    if ((n & 1u) && tid == 0) consider(b, xy[2 * (n - 1)], xy[2 * (n - 1) + 1], n - 1);
+    if ((n & 1u) && tid == 0) {
+      consider(b, xy[2 * (n - 1)], xy[2 * (n - 1) + 1], n - 1);
+      if (sample && (n - 1) % kSampleStride == 0) sample[(n - 1) / kSampleStride] = make_int2(xy[2 * (n - 1)], xy[2 * (n - 1) + 1]);
+    }
   } else {
     const int2* p2 = reinterpret_cast<const int2*>(xy);
     for (u32 j = tid; j < n; j += nthreads) {
       int2 v = p2[j];
       consider(b, v.x, v.y, j);
+      if (sample && j % kSampleStride == 0) sample[j / kSampleStride] = v;
     }
   }
   warp_reduce(b);
@@ -243,7 +271,7 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
     plan->spin_limit = spin_limit;
     finish_plan(plan, b);
     plan->epoch += kEpochStride;
-    plan->s = 0; plan->r_lo = 0; plan->r_up = 0; plan->h = 0; plan->h_lo = 0; plan->h_up = 0;
+    plan->s = 0; plan->s_quad = 0; plan->r_lo = 0; plan->r_up = 0; plan->h = 0; plan->h_lo = 0; plan->h_up = 0;
     plan->learned_used = 0;
     plan->k1_done = 0;
   }
@@ -270,12 +298,12 @@ int k1_grid(u32 n, int num_sms) {
 }
 
 cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials,
-                      int grid, cudaStream_t st) {
+                      int grid, cudaStream_t st, int2* sample) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   if (vec)
-    k1_extremes<512, true><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials);
+    k1_extremes<512, true><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials, sample);
   else
-    k1_extremes<512, false><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials);
+    k1_extremes<512, false><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials, sample);
   return cudaGetLastError();
 }
 

@@ -22,10 +22,16 @@
 //      crowded).
 //
 // Groups: bin b starts a new group when floor(start_b / T) differs from
-// its predecessor's (T = kGroupTarget) or when it or its predecessor holds
-// more than T survivors.  A group of small bins then starts and ends inside
+// its predecessor's (T = kGroupTarget), when it or its predecessor holds
+// more than T survivors, or when b starts a coarse bin (kFinePerCoarse
+// consecutive bins).  A group of small bins then starts and ends inside
 // one window of T positions plus its last bin, so it holds fewer than 2T =
-// kGroupCap survivors; a larger bin is a group of its own.  A bin above
+// kGroupCap survivors; a larger bin is a group of its own.  Since a group
+// spans at most kFinePerCoarse bins, each bin's key range takes at least
+// kSubBins / kFinePerCoarse sub-bins of the group's map, so a bin of up to
+// T points spread over its range cannot crowd them (one dense bin in a
+// group of many sparse ones used to send the whole group to the bitonic
+// network).  A bin above
 // kGroupCap is split once more through global memory by its next kSubBits
 // key bits; if one of those sub-bins is still above kGroupCap (heavy
 // duplication, or a few points spread over a huge bounding box) the block
@@ -1189,7 +1195,7 @@ __device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ 
     if (j) { pst = st[j - 1]; pcn = cn[j - 1]; }
     else if (threadIdx.x) { pst = s_last_st[threadIdx.x - 1]; pcn = s_last_cn[threadIdx.x - 1]; }
     else { pst = 0; pcn = 0; }
-    const bool f = b == 0 || st[j] / T != pst / T || cn[j] > T || pcn > T;
+    const bool f = b % kFinePerCoarse == 0 || st[j] / T != pst / T || cn[j] > T || pcn > T;
     flags |= (u32)f << j;
   }
   const u32 nf = __popc(flags);

@@ -31,21 +31,28 @@ cudaError_t k3_occupancy(int* blocks);
 cudaError_t k4_occupancy(int* blocks);
 
 int k1_grid(u32 n, int num_sms);
+// sample (optional): receives every kSampleStride-th point, ceil(n / kSampleStride) of them.
 cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials,
-                      int grid, cudaStream_t st);
+                      int grid, cudaStream_t st, int2* sample = nullptr);
 
 int k2_tile();
 cudaError_t k2_configure();
 cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u64* status,
                       unsigned char* mask, int grid_count, int grid_write, cudaStream_t st);
 
-// Bucket sort (the pipeline's sort): K2 with bin rows + bin scan + scatter,
-// then one block per group of bins (k3_bucket.cu).
-cudaError_t k2_bins_occupancy(int* blocks);
-cudaError_t launch_k2_bins(const int* xy, Plan* plan, u64* status, unsigned char* mask, u32* rows, u32* bcnt,
-                           u32* bstart, uint2* groups, u32* fcur, int grid, cudaStream_t st);
-cudaError_t launch_k2_bins_scatter(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, const unsigned char* mask,
-                                   const u32* rows, const u32* bstart, int grid, cudaStream_t st);
+// The fused front (k2_fused.cu): the sample's best witness per witness bin
+// and region (wkey: 2 kWitnessBins words, zeroed before the launch; the
+// sample from K1), the fused filter writing (key, index) pairs in any order
+// with the bins' totals (btot, zeroed; count: also count the first-round
+// survivors into the plan), and after the bin scan the move into coarse-bin
+// order (ccur: kCoarse cursors, zeroed).
+cudaError_t fused_configure();
+cudaError_t fused_occupancy(int* blocks);
+cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st);
+cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
+                            u32* oidx, u32* btot, bool count, int grid, cudaStream_t st);
+cudaError_t launch_place(const u64* ak, const u32* ai, u32 n, Plan* plan, const u32* bstart, u32* ccur, u64* ok,
+                         u32* oi, int num_sms, cudaStream_t st);
 size_t bucket_smem();
 size_t bucket_scratch_words(int blocks);
 cudaError_t bucket_configure();

@@ -37,7 +37,7 @@ class hull_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("s", ctypes.c_int64), ("r_lower", ctypes.c_int64),
                 ("r_upper", ctypes.c_int64), ("h", ctypes.c_int64), ("ext", ctypes.c_int32 * 4),
                 ("ncorner", ctypes.c_int32), ("learned_used", ctypes.c_int32),
-                ("sort_fallback", ctypes.c_int32)]
+                ("sort_fallback", ctypes.c_int32), ("s_witness", ctypes.c_int64)]
 
 
 NUM_STAGES = 12
@@ -284,7 +284,7 @@ class Context:
         _check(_lib.hull_last_stats(self._h, ctypes.byref(st)), "hull_last_stats")
         return {"n": st.n, "s": st.s, "r_lower": st.r_lower, "r_upper": st.r_upper, "h": st.h,
                 "ext": list(st.ext), "ncorner": st.ncorner, "learned_used": st.learned_used,
-                "sort_fallback": st.sort_fallback}
+                "sort_fallback": st.sort_fallback, "s_witness": st.s_witness}
 
     def set_profiling(self, enable: bool = True):
         _check(_lib.hull_set_profiling(self._h, int(bool(enable))), "hull_set_profiling")

@@ -302,22 +302,39 @@ def test_invalid_arguments(ctx, hull_lib):
 
 
 def test_forced_wait_timeouts_recover(hull_lib):
-    """Fault injection from the host: a spin limit of one iteration makes any
-    device wait that is not satisfied at once give up; the call must report
-    HULL_ETIMEOUT (or succeed exactly) and never hang or trap, and a context
-    with the normal limit must keep working afterwards."""
-    pts = W.uniform_square(4_000_000, 1 << 29, 9)
+    """Failure detection, injected from the host: with a spin limit of one
+    iteration, every bounded device wait that is not satisfied at once gives
+    up.  The radix passes look back at earlier tiles (4M keys, thousands of
+    tiles on a few hundred blocks) and the final chain of the 4M near-circle
+    set crosses grid barriers over many blocks, so such waits must run out:
+    at least one call has to report HULL_ETIMEOUT, every other result must be
+    exact, no call may hang or trap, and a context with the normal limit must
+    give the oracle's hull afterwards."""
+    pts = W.near_circle(4_000_000, 2.0 ** 28, 3)
     ref = oracle.hull(pts)
     t = dev(pts)
-    saw_timeout = False
+    rng = np.random.default_rng(7)
+    keys_np = rng.integers(0, 1 << 62, size=4_000_000, dtype=np.int64)
+    order = np.argsort(keys_np, kind="stable")
+    codes = []
     with hull_lib.Context(0, spin_limit=1) as c:
         for _ in range(3):
             try:
                 h = c.compute(t).cpu().numpy()
                 assert h.tolist() == ref.tolist()
+                codes.append(hull_lib.HULL_OK)
             except hull_lib.HullError as e:
                 assert e.code == hull_lib.HULL_ETIMEOUT
-                saw_timeout = True
+                codes.append(e.code)
+            k = torch.as_tensor(keys_np).cuda()
+            v = torch.arange(len(keys_np), dtype=torch.int32, device="cuda")
+            try:
+                c.stage_sort(k, v)
+                assert v.cpu().numpy().tolist() == order.tolist()
+                codes.append(hull_lib.HULL_OK)
+            except hull_lib.HullError as e:
+                assert e.code == hull_lib.HULL_ETIMEOUT
+                codes.append(e.code)
+    assert hull_lib.HULL_ETIMEOUT in codes, codes
     with hull_lib.Context(0) as c:
         assert c.compute(t).cpu().numpy().tolist() == ref.tolist()
-    print("timeout observed:", saw_timeout)
