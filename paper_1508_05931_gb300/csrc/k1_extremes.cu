@@ -142,34 +142,18 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
   best_init(b);
   const u32 tid = blockIdx.x * BLOCK + threadIdx.x;
   const u32 nthreads = gridDim.x * BLOCK;
-  {
-    // Seed every thread's skip box with the bounding box of a strided
-    // sample of kBoxSample points (the same points in every block, so all
-    // but the first reads come from L2): a point strictly inside the box
-    // spanned by input points cannot be an extreme.  (The sample points
-    // themselves still reach their owners as candidates: they lie on or
-    // outside that box.)  A larger sample leaves fewer points outside the
-    // box, and a warp whose points all lie inside skips them with one vote.
-    constexpr u32 kBoxSample = 16 * BLOCK;
-    __shared__ int s_box[4];
-    if (threadIdx.x == 0) { s_box[0] = 0x7FFFFFFF; s_box[1] = (int)0x80000000; s_box[2] = 0x7FFFFFFF; s_box[3] = (int)0x80000000; }
-    __syncthreads();
-    const u32 step = n / kBoxSample + 1;
-    int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
-    int2 sp[kBoxSample / BLOCK];
-    #pragma unroll
-    for (u32 q = 0; q < kBoxSample / BLOCK; ++q) {
-      const u32 j = (threadIdx.x + q * BLOCK) * step;
-      sp[q] = j < n ? reinterpret_cast<const int2*>(xy)[j] : make_int2(x0, y0);
-    }
-    #pragma unroll
-    for (u32 q = 0; q < kBoxSample / BLOCK; ++q) {
-      const u32 j = (threadIdx.x + q * BLOCK) * step;
-      if (j < n) {
-        x0 = min(x0, sp[q].x); x1 = max(x1, sp[q].x);
-        y0 = min(y0, sp[q].y); y1 = max(y1, sp[q].y);
-      }
-    }
+  // Every thread's skip box starts as the bounding box of points the block
+  // has read: a point strictly inside a box spanned by input points cannot
+  // be an extreme.  (The points that span it still reach their owners as
+  // candidates: they lie on or outside that box.)  With 16-byte alignment
+  // the box comes from the block's first round of loads (8 int4 per thread,
+  // 16 * BLOCK points, read anyway); otherwise from a strided sample of
+  // BLOCK points.  A box from thousands of points leaves few points outside
+  // it, and a warp whose points all lie inside skips them with one vote.
+  __shared__ int s_box[4];
+  if (threadIdx.x == 0) { s_box[0] = 0x7FFFFFFF; s_box[1] = (int)0x80000000; s_box[2] = 0x7FFFFFFF; s_box[3] = (int)0x80000000; }
+  __syncthreads();
+  auto seed_box = [&](int x0, int x1, int y0, int y1) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       x0 = min(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o));
@@ -183,29 +167,50 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
     }
     __syncthreads();
     b.bx0 = s_box[0]; b.bx1 = s_box[1]; b.by0 = s_box[2]; b.by1 = s_box[3];
-  }
+  };
   if (VEC) {
     // 16-byte aligned: pair j holds points 2j and 2j + 1.
     const int4* p4 = reinterpret_cast<const int4*>(xy);
     const u32 npair = n >> 1;
     u32 j = tid;
-    for (; j + 7 * nthreads < npair; j += 8 * nthreads) {
-      int4 v[8];
+    int4 v[8];
+    const bool first = j + 7 * nthreads < npair;
+    {
+      int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
+      if (first) {
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p4[j + u * nthreads];
+        #pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          x0 = min(x0, min(v[u].x, v[u].z)); x1 = max(x1, max(v[u].x, v[u].z));
+          y0 = min(y0, min(v[u].y, v[u].w)); y1 = max(y1, max(v[u].y, v[u].w));
+        }
+      }
+      seed_box(x0, x1, y0, y1);
+    }
+    auto take8 = [&](u32 jj) {
       #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = p4[j + u * nthreads];
-      #pragma unroll
-      for (int u = 0; u < 8; ++u) consider2(b, v[u], 2 * (j + u * nthreads));
+      for (int u = 0; u < 8; ++u) consider2(b, v[u], 2 * (jj + u * nthreads));
       if (sample) {
         #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if ((j + u * nthreads) % kPairStride == 0) sample[(j + u * nthreads) / kPairStride] = make_int2(v[u].x, v[u].y);
+          if ((jj + u * nthreads) % kPairStride == 0) sample[(jj + u * nthreads) / kPairStride] = make_int2(v[u].x, v[u].y);
       }
+    };
+    if (first) {
+      take8(j);
+      j += 8 * nthreads;
+    }
+    for (; j + 7 * nthreads < npair; j += 8 * nthreads) {
+      #pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p4[j + u * nthreads];
+      take8(j);
     }
     for (; j < npair; j += nthreads) {
-      int4 v = p4[j];
-      consider(b, v.x, v.y, 2 * j);
-      consider(b, v.z, v.w, 2 * j + 1);
-      if (sample && j % kPairStride == 0) sample[j / kPairStride] = make_int2(v.x, v.y);
+      int4 w = p4[j];
+      consider(b, w.x, w.y, 2 * j);
+      consider(b, w.z, w.w, 2 * j + 1);
+      if (sample && j % kPairStride == 0) sample[j / kPairStride] = make_int2(w.x, w.y);
     }
     if ((n & 1u) && tid == 0) {
       consider(b, xy[2 * (n - 1)], xy[2 * (n - 1) + 1], n - 1);
@@ -213,6 +218,13 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
     }
   } else {
     const int2* p2 = reinterpret_cast<const int2*>(xy);
+    {
+      const u32 step = n / BLOCK + 1;
+      const u32 jj = threadIdx.x * step;
+      int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
+      if (jj < n) { const int2 q = p2[jj]; x0 = x1 = q.x; y0 = y1 = q.y; }
+      seed_box(x0, x1, y0, y1);
+    }
     for (u32 j = tid; j < n; j += nthreads) {
       int2 v = p2[j];
       consider(b, v.x, v.y, j);
