@@ -351,9 +351,8 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
                                        (size_t)2 * kWitnessBins * sizeof(u64), st);
     if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
     if (e == cudaSuccess)
-      e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, c->cfg.collect_stats != 0,
-                          c->occ_kf * c->num_sms, st);
-    if (e == cudaSuccess) e = launch_binstart(w.bcnt, c->plan, w.bstart, w.groups, w.fcur, st);
+      e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
+                          w.fcur, c->cfg.collect_stats != 0, c->occ_kf * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
     e = launch_place(w.keys[1], w.idx[1], n, c->plan, w.bstart, w.bcnt + kBins, w.keys[0], w.idx[0], c->num_sms, st);

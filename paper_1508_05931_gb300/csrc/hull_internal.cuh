@@ -86,7 +86,8 @@ enum CounterSlot : int {
   CTR_GROUP_AGG = 8 + kMaxPasses,         // last-block counter of the group aggregates
   CTR_WITNESS = 9 + kMaxPasses,           // last-block counter of the sampled witnesses
   CTR_FUSED = 10 + kMaxPasses,            // next output slot of the fused filter
-  kNumCounters = 19,
+  CTR_FUSED_DONE = 11 + kMaxPasses,       // last-block counter of the fused filter
+  kNumCounters = 20,
 };
 
 struct ExtPartial {

@@ -37,7 +37,9 @@
 //              bins' totals to btot.  The polygon test, the costlier of the
 //              two, thus runs on about one point in fifty.  With COUNT the
 //              polygon is also tested on every point, to count the
-//              first-round survivors for the statistics.
+//              first-round survivors for the statistics.  The last block to
+//              finish turns the bins' totals into bin starts and groups
+//              (bins_to_groups, in the table's shared memory, free by then).
 //   k2_place   after the bin scan, moves the output into coarse-bin order
 //              (one reservation per coarse bin and chunk), the input of
 //              k3_split.
@@ -45,6 +47,7 @@
 // them.
 #include <cstddef>
 
+#include "bins.cuh"
 #include "filter.cuh"
 #include "hull_internal.cuh"
 #include "kernels.h"
@@ -371,10 +374,12 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
 template <bool VEC, bool COUNT>
 __global__ void __launch_bounds__(KF_BLOCK, 2)
 k2_fused(const int* __restrict__ xy, Plan* plan, const u64* __restrict__ wkey, const int2* __restrict__ sample,
-         u64* __restrict__ okey, u32* __restrict__ oidx, u32* __restrict__ btot) {
+         u64* __restrict__ okey, u32* __restrict__ oidx, u32* __restrict__ btot, u32* __restrict__ bstart,
+         uint2* __restrict__ groups, u32* __restrict__ fcur) {
   extern __shared__ __align__(128) unsigned char kf_smem[];
   KFSmem& S = *reinterpret_cast<KFSmem*>(kf_smem);
   __shared__ u64 s_wm[KF_WARPS];
+  __shared__ bool s_last;
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -400,6 +405,15 @@ k2_fused(const int* __restrict__ xy, Plan* plan, const u64* __restrict__ wkey, c
     for (int o = 16; o > 0; o >>= 1) nq += __shfl_xor_sync(0xFFFFFFFFu, nq, o);
     if (lane == 0 && nq) atomicAdd(&plan->s_quad, nq);
   }
+  // The last block turns the bins' totals into bin starts and groups.
+  static_assert(sizeof(BinScanSmem) <= sizeof(KFSmem::wt) && KF_BLOCK == BS_BLOCK, "bin scan in the table's place");
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&plan->ctr[CTR_FUSED_DONE], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  bins_to_groups<true>(btot, plan, bstart, groups, fcur, *reinterpret_cast<BinScanSmem*>(&S.wt[0]));
 }
 
 // ---- k2_place: the fused filter's output into coarse-bin order.
@@ -503,16 +517,17 @@ cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int
 }
 
 cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
-                            u32* oidx, u32* btot, bool count, int grid, cudaStream_t st) {
+                            u32* oidx, u32* btot, u32* bstart, uint2* groups, u32* fcur, bool count, int grid,
+                            cudaStream_t st) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   const u32 rounds = ((n + 1) / 2 + KF_BLOCK * KF_V - 1) / (KF_BLOCK * KF_V);   // blocks with a full round
   if ((u32)grid > rounds) grid = (int)(rounds < 1 ? 1 : rounds);
   if (vec) {
-    if (count) k2_fused<true, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot);
-    else k2_fused<true, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot);
+    if (count) k2_fused<true, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
+    else k2_fused<true, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
   } else {
-    if (count) k2_fused<false, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot);
-    else k2_fused<false, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot);
+    if (count) k2_fused<false, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
+    else k2_fused<false, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
   }
   return cudaGetLastError();
 }

@@ -41,6 +41,7 @@
 
 #include "hull_internal.cuh"
 #include "kernels.h"
+#include "bins.cuh"
 #include "regions.cuh"
 
 #ifdef GBH_DEBUG_CHECKS
@@ -1125,112 +1126,16 @@ k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ g
 }
 
 // Bin starts and groups.  k_binstart (the pipeline, one block) takes the
-// bins' totals that k2_count accumulated.  k_binscan (the stage entry's
-// array path) takes one histogram row per histogram block: row r, bin b
-// becomes the number of bin-b pairs of rows before r, bstart[b] first
-// receives the bin totals, and its last block continues as k_binstart does.
-// Both write the bins' first positions and the groups (first position,
-// first bin), with a closing record (s, kBins) after the last group.
-constexpr int BS_BLOCK = 512;
+// bins' totals that the fused filter accumulated.  k_binscan (the stage
+// entry's array path) takes one histogram row per histogram block: row r,
+// bin b becomes the number of bin-b pairs of rows before r, bstart[b]
+// first receives the bin totals, and its last block continues as
+// k_binstart does.  Both write the bins' first positions and the groups
+// (first position, first bin), with a closing record (s, kBins) after the
+// last group (bins_to_groups, bins.cuh).
 constexpr int BS_BINS = 32;                 // bins per block (one per lane)
-constexpr int BS_WARPS = BS_BLOCK / 32;
 constexpr int BS_RMAX = 10;                 // rows a warp loads at once
-constexpr int BS_PER = kBins / BS_BLOCK;    // bins per thread in the last block (a flag word each)
-static_assert(BS_PER >= 1 && BS_PER <= 32 && BS_PER * BS_BLOCK == kBins, "whole slices of at most 32 bins per thread");
 
-// One whole block (BS_BLOCK threads): the bins' starts (bstart, and the
-// split's cursors fcur when given) from their totals, the groups of
-// consecutive bins, the survivor count.  Thread t owns bins
-// [t BS_PER, t BS_PER + BS_PER).  `totals` may be bstart itself; VOL when
-// other blocks of the same launch wrote it.
-template <bool VOL>
-__device__ void bins_to_groups(const u32* totals, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
-                               u32* __restrict__ fcur) {
-  __shared__ u32 s_w[BS_WARPS];
-  __shared__ u32 s_last_st[BS_BLOCK], s_last_cn[BS_BLOCK];
-  __shared__ __align__(16) u32 s_v[kBins];      // totals, then starts (coalesced global access)
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  static_assert(BS_PER % 4 == 0, "whole uint4 slices");
-  {
-    u32 v[BS_PER];
-    #pragma unroll
-    for (int j = 0; j < BS_PER; ++j) {
-      const u32* p = &totals[threadIdx.x + j * BS_BLOCK];
-      v[j] = VOL ? ld_volatile_u32(p) : *p;
-    }
-    #pragma unroll
-    for (int j = 0; j < BS_PER; ++j) s_v[threadIdx.x + j * BS_BLOCK] = v[j];
-  }
-  __syncthreads();
-  u32 cn[BS_PER], st[BS_PER];
-  u32 tsum = 0;
-  #pragma unroll
-  for (int j = 0; j < BS_PER; j += 4) {
-    const uint4 v = *reinterpret_cast<const uint4*>(&s_v[threadIdx.x * BS_PER + j]);
-    cn[j] = v.x; cn[j + 1] = v.y; cn[j + 2] = v.z; cn[j + 3] = v.w;
-  }
-  #pragma unroll
-  for (int j = 0; j < BS_PER; ++j) tsum += cn[j];
-  u32 inc = tsum;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  u32 acc = inc - tsum;
-  for (int w = 0; w < wid; ++w) acc += s_w[w];
-  #pragma unroll
-  for (int j = 0; j < BS_PER; ++j) { st[j] = acc; acc += cn[j]; }
-  s_last_st[threadIdx.x] = st[BS_PER - 1];
-  s_last_cn[threadIdx.x] = cn[BS_PER - 1];
-  __syncthreads();
-  const u32 T = (u32)kGroupTarget;
-  u32 flags = 0;
-  #pragma unroll
-  for (int j = 0; j < BS_PER; ++j) {
-    const u32 b = threadIdx.x * BS_PER + j;
-    u32 pst, pcn;
-    if (j) { pst = st[j - 1]; pcn = cn[j - 1]; }
-    else if (threadIdx.x) { pst = s_last_st[threadIdx.x - 1]; pcn = s_last_cn[threadIdx.x - 1]; }
-    else { pst = 0; pcn = 0; }
-    const bool f = b % kFinePerCoarse == 0 || st[j] / T != pst / T || cn[j] > T || pcn > T;
-    flags |= (u32)f << j;
-  }
-  const u32 nf = __popc(flags);
-  u32 finc = nf;
-  #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 t = __shfl_up_sync(0xFFFFFFFFu, finc, o);
-    if (lane >= o) finc += t;
-  }
-  __syncthreads();
-  if (lane == 31) s_w[wid] = finc;
-  __syncthreads();
-  u32 g = finc - nf;
-  for (int w = 0; w < wid; ++w) g += s_w[w];
-  #pragma unroll
-  for (int j = 0; j < BS_PER; ++j) {
-    if (flags & (1u << j)) groups[g++] = make_uint2(st[j], threadIdx.x * BS_PER + j);
-  }
-  #pragma unroll
-  for (int j = 0; j < BS_PER; j += 4)
-    *reinterpret_cast<uint4*>(&s_v[threadIdx.x * BS_PER + j]) = make_uint4(st[j], st[j + 1], st[j + 2], st[j + 3]);
-  __syncthreads();
-  for (u32 q = threadIdx.x; q < (u32)kBins; q += BS_BLOCK) {
-    const u32 v = s_v[q];
-    bstart[q] = v;
-    if (fcur) fcur[q] = v;
-  }
-  if (threadIdx.x == BS_BLOCK - 1) {
-    groups[g] = make_uint2(acc, (u32)kBins);
-    plan->s = acc;            // the survivors: every bin's count
-    plan->ngroups = g;
-    plan->npasses = 0;        // no radix passes on this path;
-    plan->sorted_in_b = 1;    // k3_bucket leaves the sorted survivors in the second buffer
-  }
-}
 __global__ void __launch_bounds__(BS_BLOCK)
 k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstart,
           uint2* __restrict__ groups, u32* __restrict__ fcur) {
@@ -1274,7 +1179,8 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  bins_to_groups<true>(bstart, plan, bstart, groups, fcur);
+  __shared__ BinScanSmem B;
+  bins_to_groups<true>(bstart, plan, bstart, groups, fcur, B);
 }
 
 // The bin starts and groups of the pipeline's bucket sort from the bins'
@@ -1283,7 +1189,8 @@ __global__ void __launch_bounds__(BS_BLOCK)
 k_binstart(const u32* __restrict__ btot, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
            u32* __restrict__ fcur) {
   if (plan->error & ERR_RANGE) return;
-  bins_to_groups<false>(btot, plan, bstart, groups, fcur);
+  __shared__ BinScanSmem B;
+  bins_to_groups<false>(btot, plan, bstart, groups, fcur, B);
 }
 
 // ---- the same sort over an arbitrary key array (the stage entry point):

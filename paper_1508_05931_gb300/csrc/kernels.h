@@ -45,12 +45,14 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 // sample from K1), the fused filter writing (key, index) pairs in any order
 // with the bins' totals (btot, zeroed; count: also count the first-round
 // survivors into the plan), and after the bin scan the move into coarse-bin
-// order (ccur: kCoarse cursors, zeroed).
+// order (ccur: kCoarse cursors, zeroed).  The fused filter's last block also
+// writes the bin starts, the groups and the split's cursors (fcur).
 cudaError_t fused_configure();
 cudaError_t fused_occupancy(int* blocks);
 cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st);
 cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
-                            u32* oidx, u32* btot, bool count, int grid, cudaStream_t st);
+                            u32* oidx, u32* btot, u32* bstart, uint2* groups, u32* fcur, bool count, int grid,
+                            cudaStream_t st);
 cudaError_t launch_place(const u64* ak, const u32* ai, u32 n, Plan* plan, const u32* bstart, u32* ccur, u64* ok,
                          u32* oi, int num_sms, cudaStream_t st);
 size_t bucket_smem();
