@@ -121,6 +121,55 @@ def oracle_timing(sets, budget_s=20.0, sample_pts=None):
     return done, secs, "oracle.hull (qsort + monotone chain, 1 thread) on %s points" % "+".join(map(str, parts))
 
 
+def _oracle_shard_hull(job):
+    """One shard's hull by the oracle: job = (shared-memory name, points in
+    the set, first point, end point); returns the hull's points."""
+    from multiprocessing import shared_memory
+    import numpy as np
+    import oracle
+    name, n, a, b = job
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        pts = np.ndarray((n, 2), dtype=np.int32, buffer=shm.buf)[a:b]
+        return pts[oracle.hull(pts)].copy()
+    finally:
+        shm.close()
+
+
+def oracle_timing_parallel(sets, cores):
+    """The oracle on all host cores: every set (in shared memory) cut into
+    `cores` contiguous shards whose hulls (oracle.hull, one process each) are
+    merged by oracle.hull over their union (the hull of a union is the hull
+    of the parts' hulls).  Returns (points, seconds, cores, description)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")          # the parent already drives the GPU
+    done, secs = 0, 0.0
+    with ctx.Pool(cores) as pool:
+        for pts in sets:
+            n = len(pts)
+            shm = shared_memory.SharedMemory(create=True, size=max(n * 8, 8))
+            try:
+                np.ndarray((n, 2), dtype=np.int32, buffer=shm.buf)[:] = pts
+                cuts = np.linspace(0, n, cores + 1).astype(np.int64)
+                jobs = [(shm.name, n, int(cuts[i]), int(cuts[i + 1])) for i in range(cores)]
+                pool.map(_oracle_shard_hull, [(shm.name, n, 0, min(n, 4))] * cores)   # workers up and warm
+                t = time.perf_counter()
+                parts = pool.map(_oracle_shard_hull, jobs)
+                oracle.hull(np.concatenate(parts))
+                secs += time.perf_counter() - t
+                done += n
+            finally:
+                shm.close()
+                shm.unlink()
+    return done, secs, cores, ("oracle.hull on %d contiguous shards per set (shared memory) in %d processes, "
+                               "then on the union of the shard hulls; %s points"
+                               % (cores, cores, "+".join(str(len(p)) for p in sets)))
+
+
 class ClockSampler:
     def __init__(self, enabled, index):
         self.proc = None
@@ -220,17 +269,24 @@ def kernel_traffic(kernel, units):
 
 
 # Kernel(s) behind each profile stage of the bucket-sort path, and the
-# algorithmic bytes each moves per hull: n points, s first-round survivors,
-# r second-round survivors (8 B per point, 12 B per (key, index) pair).
+# algorithmic bytes each moves per hull: n points, s pairs the fused filter
+# passes on (the bucket sort's input), r second-round survivors (8 B per
+# point, 12 B per (key, index) pair; K1 copies every 32nd point out for the
+# witnesses, which read them back).
+SAMPLE_STRIDE = 32
+# The last field names the units a committed DRAM traffic record scales by:
+# the points a launch reads, or the pairs it moves.
 STAGE_KERNELS = {
-    "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n),
-    "filter": ("k2_count + k_binstart", lambda n, s, r: 8.0 * n),
-    "scatter": ("k2_scatter", lambda n, s, r: 8.0 * n + 12.0 * s),
-    "split": ("k3_split + k_bin_prefix", lambda n, s, r: 24.0 * s),
-    "sort": ("k3_bucket", lambda n, s, r: 12.0 * s + 12.0 * r),
-    "regions": ("k4_compact", lambda n, s, r: 24.0 * r),
-    "final": ("k5_final", lambda n, s, r: 12.0 * r),
+    "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n + 8.0 * n / SAMPLE_STRIDE, "points"),
+    "witness": ("k_witness", lambda n, s, r: 8.0 * n / SAMPLE_STRIDE, "points"),
+    "filter": ("k2_fused", lambda n, s, r: 8.0 * n + 12.0 * s, "points"),
+    "scatter": ("k2_place", lambda n, s, r: 24.0 * s, "pairs"),
+    "split": ("k3_split + k_bin_prefix", lambda n, s, r: 24.0 * s, "pairs"),
+    "sort": ("k3_bucket", lambda n, s, r: 12.0 * s + 12.0 * r, "pairs"),
+    "regions": ("k4_compact", lambda n, s, r: 24.0 * r, "pairs"),
+    "final": ("k5_final", lambda n, s, r: 12.0 * r, "pairs"),
 }
+DOMINANT_CANDIDATES = ("extremes", "witness", "filter", "scatter", "split", "sort")
 
 
 def roofline_of(prof, hbm, peak_src):
@@ -238,24 +294,24 @@ def roofline_of(prof, hbm, peak_src):
     launch stream, recorded by the library between kernels) and the
     roofline entry of the dominant one (the longest stage)."""
     calls = max(prof["calls"], 1)
-    n, s, r = prof["points"] / calls, prof["survivors"] / calls, prof["second_round"] / calls
+    n, s, r = prof["points"] / calls, prof["witness_survivors"] / calls, prof["second_round"] / calls
     stage_ms = {k: v / calls for k, v in prof["ms"].items() if not k.startswith("-")}
     if prof["radix_calls"]:
         return {"bound": "hbm", "kernel": "mixed (calls rerun on the radix passes)", "achieved": None,
                 "peak": hbm, "unit": "GB/s", "frac": None, "peak_source": peak_src, "traffic": None,
                 "stage_ms_per_hull": stage_ms}
     kernels = {}
-    for name, (kern, nbytes) in STAGE_KERNELS.items():
+    for name, (kern, nbytes, unit) in STAGE_KERNELS.items():
         ms = stage_ms.get(name, 0.0)
         b = nbytes(n, s, r)
-        kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b,
+        kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b, "units": n if unit == "points" else s,
                          "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else None}
-    dom = max(("scatter", "sort", "filter", "extremes", "split"), key=lambda k: kernels[k]["ms"])
+    dom = max(DOMINANT_CANDIDATES, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     achieved = d["gbs"] or 0.0
     return {"bound": "hbm", "kernel": d["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": kernel_traffic(d["kernel"].split()[0], s),
+            "traffic": kernel_traffic(d["kernel"].split()[0], d["units"]),
             "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
             "stage_ms_per_hull": stage_ms, "stages": kernels,
             "timing": "CUDA events between the kernels on the launch stream, over a second pass of the timed steps",
@@ -275,6 +331,43 @@ def _time_hulls(ctx, t, out, stream, torch, k):
     torch.cuda.synchronize()
     st = ctx.last_stats()
     return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], st["learned_used"]
+
+
+def bench_configs(hull, torch, stream, hbm, peak_src, k=20):
+    """The other two plain configurations, one hull per step: 100,000
+    points uniform in [-2^20, 2^20)^2 (seed 0; its 800 KB stay in L2 between
+    steps) and the 4M near-circle ring (seed 3; 32 MB).  Device time per
+    hull, throughput, stage times and the roofline entry of each."""
+    from paper_1508_05931_gb300 import workloads as W
+    res = {}
+    for name, pts in (("small_square_100k", W.small_square()), ("near_circle_4M", W.adversarial_ring())):
+        t = torch.as_tensor(pts).cuda()
+        o = torch.empty(t.shape[0], dtype=torch.int32, device="cuda")
+        with hull.Context(torch.cuda.current_device()) as c:
+            for _ in range(3):
+                c.compute_raw(t, o, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                c.compute_raw(t, o, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            c.set_profiling(True)
+            for _ in range(k):
+                c.compute_raw(t, o, stream)
+            torch.cuda.synchronize()
+            prof = c.profile()
+        with hull.Context(torch.cuda.current_device(), collect_stats=True) as c:
+            c.compute_raw(t, o, stream)
+            torch.cuda.synchronize()
+            st = c.last_stats()
+        res[name] = {"value": len(pts) / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_hull": ms, "n": len(pts),
+                     "first_round_survivors": st["s"], "witness_survivors": st["s_witness"],
+                     "second_round": st["r_lower"] + st["r_upper"], "hull_vertices": st["h"],
+                     "roofline": roofline_of(prof, hbm, peak_src)}
+    return res
 
 
 def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
@@ -548,7 +641,16 @@ def main():
 
     roofline = roofline_of(prof, hbm, peak_src)
     calls = max(prof["calls"], 1)
-    surv = prof["survivors"]
+    # First-round survivors: the fused filter counts them only for a context
+    # that collects statistics (one untimed hull per set).
+    first_round, witness = [], []
+    with hull.Context(local, collect_stats=True) as sc:
+        for t in dev_sets:
+            sc.compute_raw(t, out, stream)
+            torch.cuda.synchronize()
+            st = sc.last_stats()
+            first_round.append(st["s"])
+            witness.append(st["s_witness"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -556,7 +658,8 @@ def main():
             "config": {"workload": WORKLOAD, "points_per_step": pts_step, "hulls_per_step": len(sets),
                        "l2": "inputs larger than L2 (160 MB each, alternating)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "survivors_per_hull": surv / calls,
+                       "survivors_per_hull": sum(first_round) / len(first_round),
+                       "witness_survivors_per_hull": prof["witness_survivors"] / calls,
                        "second_round_per_hull": prof["second_round"] / calls},
             "gpu_launches": prof["calls"] * LAUNCHES_PER_HULL + prof["radix_calls"] * LAUNCHES_PER_RADIX_RERUN,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
@@ -570,6 +673,8 @@ def main():
         line["batched"] = bench_batched(hull, torch, stream, value, args)
     if world == 1 and not args.no_learned:
         line["learned"] = bench_learned(hull, torch, stream, args)
+    if world == 1:
+        line["configs"] = bench_configs(hull, torch, stream, hbm, peak_src)
     if world == 1 and not args.no_batched:
         line["reverse_round"] = bench_reverse_round(hull, torch, stream, dev_sets, dev_outs)
         line["second_round_ablation"] = bench_second_round_ablation(hull, torch, stream, dev_sets)
@@ -578,6 +683,9 @@ def main():
         done, secs, desc = oracle_timing(sets)
         line["cpu_baseline"] = {"value": done / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc, "cpu": cpu_info(), "nproc": os.cpu_count()}
+        pdone, psecs, pcores, pdesc = oracle_timing_parallel(sets, os.cpu_count() or 1)
+        line["cpu_baseline_all_cores"] = {"value": pdone / psecs / 1e6, "unit": UNIT, "cores": pcores,
+                                          "kind": "oracle", "sample": pdesc}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -211,14 +211,19 @@ typedef struct {
                                     call whose bins the bucket sort could not take) */
   int64_t sort_passes;           /* radix passes that did work, summed over calls */
   int64_t points;                /* input points, summed */
-  int64_t survivors;             /* first-round survivors, summed */
+  int64_t survivors;             /* first-round survivors, summed (counted only by a context
+                                    with collect_stats; 0 otherwise) */
   int64_t second_round;          /* second-round survivors, summed */
   double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): extremes,
-                                    filter (first round counted, bins scanned), scatter (survivors
-                                    into coarse bins), split (coarse bins into bins, their aggregates,
-                                    the groups' prefixes), sort (groups sorted, second round),
-                                    5 empty slots, regions (compaction), final; on the radix
-                                    passes: extremes, filter, radix pass 0..7, regions, final */
+                                    witnesses (the sample's best witness per bin), filter (the
+                                    fused filter: witness test, filter polygon, compaction, bin
+                                    scan), scatter (survivors into coarse bins), split (coarse bins
+                                    into bins, their aggregates, the groups' prefixes), sort (groups
+                                    sorted, second round), 4 empty slots, regions (compaction),
+                                    final; on the radix passes: extremes, filter, radix pass 0..7,
+                                    regions, final */
+  int64_t witness_survivors;     /* survivors of the fused filter (the bucket sort's input),
+                                    summed; the first-round survivors on the radix passes */
 } hull_profile;
 
 hull_status hull_set_profiling(hull_ctx *ctx, int enable);

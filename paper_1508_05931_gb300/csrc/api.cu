@@ -296,6 +296,7 @@ hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
     f.points += p.n;
     f.survivors += p.s_quad;
     f.second_round += (int64_t)p.r_lo + p.r_up;
+    f.witness_survivors += p.s;
   }
   if (c->cfg.collect_stats) {
     c->last.n = p.n; c->last.s = p.s_quad; c->last.s_witness = p.s;
@@ -344,30 +345,31 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // (with their direction aggregates), every bin's and group's prefix, and
     // one block per group of bins sorts it in shared memory and runs the
     // second round on it from its prefix.
-    // Profile slots: 1 filter (witnesses, fused filter, bin scan), 2 scatter
-    // (coarse bins), 3 split (fine bins, their aggregates, group prefixes),
-    // 4 sort (+ second round), 5..9 empty, 10 compaction.
+    // Profile slots: 1 witnesses, 2 filter (the fused filter and its bin
+    // scan), 3 scatter (coarse bins), 4 split (fine bins, their aggregates,
+    // group prefixes), 5 sort (+ second round), 6..9 empty, 10 compaction.
     e = cudaMemsetAsync(w.bcnt, 0, (reinterpret_cast<char*>(w.wkey) - reinterpret_cast<char*>(w.bcnt)) +
                                        (size_t)2 * kWitnessBins * sizeof(u64), st);
     if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
-    if (e == cudaSuccess)
-      e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
-                          w.fcur, c->cfg.collect_stats != 0, c->occ_kf * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
-    e = launch_place(w.keys[1], w.idx[1], n, c->plan, w.bstart, w.bcnt + kBins, w.keys[0], w.idx[0], c->num_sms, st);
+    e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
+                          w.fcur, c->cfg.collect_stats != 0, c->occ_kf * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 3, st);
+    e = launch_place(w.keys[1], w.idx[1], n, c->plan, w.bstart, w.bcnt + kBins, w.keys[0], w.idx[0], c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    mark(c, 4, st);
     e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.tagg, w.ctiles,
                      c->occ_sp * c->num_sms, st);
     if (e == cudaSuccess) e = launch_bin_prefix(c->plan, w.groups, w.st_region, w.tagg, w.ctiles, w.bagg, w.bpre, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 4, st);
+    mark(c, 5, st);
     e = launch_bucket_decide(w.keys[1], w.idx[1], w.keys[0], w.idx[0], c->plan, w.groups, w.bscratch,
                              w.st_region, w.bpre, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
                              w.up_xy, w.up_idx, c->occ_kb * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    for (int p = 5; p <= 2 + kMaxPasses; ++p) mark(c, p, st);
+    for (int p = 6; p <= 2 + kMaxPasses; ++p) mark(c, p, st);
     e = launch_group_compact(c->plan, w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy,
                              w.lo_idx, w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, kBins), st);
     if (e != cudaSuccess) return cuda_fail(e);

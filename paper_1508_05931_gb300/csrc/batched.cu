@@ -5,8 +5,16 @@
 // whole pipeline of Section 2.1 on one instance by itself, each step as a
 // block-level loop over chunks in order, so no block ever waits for another:
 //   1. extremes (step 1): block reduction;
-//   2. quadrilateral filter + compaction (steps 2-3) with a running offset,
-//      plus the digit histograms of the survivors' keys;
+//   1b. witnesses: every 32nd point (copied out during step 1) that survives
+//      the filter polygon is a witness for every later witness bin of its
+//      region; the block keeps each bin's most advanced one and turns them
+//      into every bin's exclusive prefix (as the single-hull front does,
+//      k2_fused.cu: a point not strictly beyond a first-round survivor
+//      before it is one Figure 2 discards, so the second round's result is
+//      unchanged);
+//   2. quadrilateral filter and the witness test + compaction (steps 2-3)
+//      with a running offset, plus the digit histograms of the survivors'
+//      keys;
 //   3. stable LSD radix sort (step 4): per 8-bit digit, tiles in order,
 //      per-warp early counts give each warp's positions, the highest lane of
 //      each group of equal digits reserves positions with one shared atomic;
@@ -33,6 +41,9 @@ constexpr int BT_ITEMS = 16;        // sort keys per thread per tile
 constexpr int BT_FITEMS = 8;        // filter / second-round items per thread per chunk
 constexpr int BT_LEAF = 8;          // chain points per thread
 constexpr int BT_MAX_CHUNKS = 1024; // chain chunks per instance (bounds n_i)
+constexpr int BW_BITS = 9;          // witness bins per instance: the top BW_BITS of the key
+constexpr int BW_BINS = 1 << BW_BITS;
+constexpr u32 BW_STRIDE = 32;       // one sampled point in every BW_STRIDE
 
 struct BestX {
   u64 k[4];
@@ -84,6 +95,7 @@ struct IPlan {
   int learned;
   int x0, y0;
   u32 ybits, npasses;
+  u32 kbits;
   int bad;
 };
 
@@ -127,7 +139,12 @@ struct Smem {
       int ext_xy[2 * learned::NB];
       int ext_idx[learned::NB];
     };
+    struct {                         // witnesses (steps 1b-2)
+      u64 wkey[2 * BW_BINS];         // the sample's best witness per (region, bin)
+      int2 wtab[2 * BW_BINS];        // witness direction of (bin, region)
+    };
   };
+  u64 wmax[W];
   int ccnt[BLOCK];                   // per-thread chain lengths inside a chunk
   int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
@@ -253,12 +270,15 @@ k_batch(BatchArgs a) {
       continue;
     }
 
-    // ---- 1. extremes
+    // ---- 1. extremes (every BW_STRIDE-th point copied to the sort's second
+    // key buffer, free until step 3, for the witnesses)
+    int2* smp = reinterpret_cast<int2*>(a.kb + sl);
     BestX b;
     bx_init(b);
     for (u32 j = threadIdx.x; j < n; j += BLOCK) {
       const int2 p = P[j];
       bx_point(b, p.x, p.y, j);
+      if (j % BW_STRIDE == 0) smp[j / BW_STRIDE] = p;
     }
     bx_warp(b);
     if (lane == 0)
@@ -291,6 +311,7 @@ k_batch(BatchArgs a) {
       pl.x0 = ex[0]; pl.y0 = ey[2];
       const u32 yb = bitlen32((u32)(ey[3] - ey[2])), xb = bitlen32((u32)(ex[1] - ex[0]));
       pl.ybits = yb;
+      pl.kbits = xb + yb;
       pl.npasses = (xb + yb + kRadixBits - 1) / kRadixBits;
       if (pl.bad) atomicOr(a.error, ERR_RANGE);
     }
@@ -333,6 +354,74 @@ k_batch(BatchArgs a) {
     }
     const IPlan pl = S.plan;
 
+    // ---- 1b. witnesses of the sampled first-round survivors
+    const int ax = pl.ext_x[0], ay = pl.ext_y[0], bxp = pl.ext_x[1], byp = pl.ext_y[1];
+    const int ux = bxp - ax, uy = byp - ay, d0x = ax - bxp, d0y = ay - byp;
+    const u32 wshift = pl.kbits > (u32)BW_BITS ? pl.kbits - (u32)BW_BITS : 0u;
+    for (int q = threadIdx.x; q < 2 * BW_BINS; q += BLOCK) S.wkey[q] = 0ull;
+    __syncthreads();
+    {
+      const u32 ns = (n + BW_STRIDE - 1) / BW_STRIDE;
+      for (u32 i = threadIdx.x; i < ns; i += BLOCK) {
+        const int2 p = __ldcg(&smp[i]);
+        bool in = pl.ncorner >= 3;
+        for (int e = 0; e < kMaxCorners && in; ++e) {
+          if (e >= pl.ncorner) break;
+          in = (long long)pl.ex[e] * p.y + (long long)pl.ney[e] * p.x + pl.nc[e] > 0;
+        }
+        if (in) continue;                                        // not a first-round survivor
+        const int dx = p.x - bxp, dy = p.y - byp;
+        const long long c = cross2(d0x, d0y, dx, dy);            // > 0 lower, < 0 upper
+        if (c == 0) continue;
+        const long long e2 = (long long)d0x * dx + (long long)d0y * dy;
+        const float fc = fabsf((float)c), fe = (float)e2;
+        const float qa = 1.0f - fe / (fabsf(fe) + fc);           // monotone pseudo-angle from P_0 - P_l
+        const u32 quant = (u32)fminf(fmaxf(qa, 0.0f) * 2147483648.0f, 4294967040.0f);
+        const u64 key = ((u64)(u32)(p.x - pl.x0) << pl.ybits) | (u64)(u32)(p.y - pl.y0);
+        const u32 wbin = (u32)(key >> wshift);
+        atomicMax(&S.wkey[(c > 0 ? 0 : BW_BINS) + wbin], ((u64)quant << 32) | (u64)(i + 1u));
+      }
+    }
+    __syncthreads();
+    // Every bin's exclusive prefix maximum, per region (thread t owns bins
+    // [t BW_PER, (t + 1) BW_PER)), and its witness direction.
+    {
+      constexpr int BW_PER = (BW_BINS + BLOCK - 1) / BLOCK;
+      for (int r = 0; r < 2; ++r) {
+        u64 v[BW_PER];
+        u64 tot = 0;
+        #pragma unroll
+        for (int q = 0; q < BW_PER; ++q) {
+          const int bq = threadIdx.x * BW_PER + q;
+          v[q] = bq < BW_BINS ? S.wkey[r * BW_BINS + bq] : 0ull;
+          tot = v[q] > tot ? v[q] : tot;
+        }
+        u64 inc = tot;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u64 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= o && t > inc) inc = t;
+        }
+        u64 ex = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+        if (lane == 0) ex = 0;
+        if (lane == 31) S.wmax[wid] = inc;
+        __syncthreads();
+        for (int w = 0; w < wid; ++w) ex = S.wmax[w] > ex ? S.wmax[w] : ex;
+        #pragma unroll
+        for (int q = 0; q < BW_PER; ++q) {
+          const int bq = threadIdx.x * BW_PER + q;
+          const u32 wi = (u32)ex;                // sample index + 1, 0: none (P_0 itself)
+          if (bq < BW_BINS) {
+            int2 w = make_int2(d0x, d0y);
+            if (wi) { const int2 p = __ldcg(&smp[wi - 1u]); w = make_int2(p.x - bxp, p.y - byp); }
+            S.wtab[2 * bq + r] = w;
+          }
+          ex = v[q] > ex ? v[q] : ex;
+        }
+        __syncthreads();
+      }
+    }
+
     // ---- 2. filter + compaction (+ digit histograms)
     u32 run = 0;
     for (u32 base = 0; base < n; base += FCH) {
@@ -355,6 +444,14 @@ k_batch(BatchArgs a) {
           }
         }
         keep[r] = (j < n) && !in;
+        if (keep[r]) {                  // the witness test of the point's bin and region
+          const int dx = px[r] - bxp, dy = py[r] - byp;
+          const long long c = cross2(d0x, d0y, dx, dy);
+          const u64 key = ((u64)(u32)(px[r] - pl.x0) << pl.ybits) | (u64)(u32)(py[r] - pl.y0);
+          const int2 w = S.wtab[2 * (u32)(key >> wshift) + (c < 0 ? 1u : 0u)];
+          const long long t = cross2(w.x, w.y, dx, dy);
+          keep[r] = c == 0 || (c > 0 ? t > 0 : t < 0);
+        }
         const u32 bal = __ballot_sync(0xFFFFFFFFu, keep[r]);
         pre[r] = __popc(bal & lt_mask);
         if (lane == 0) S.red[r * W + wid] = __popc(bal);
@@ -450,7 +547,6 @@ k_batch(BatchArgs a) {
     // sorted keys are in src_*
 
     // ---- 4. region split + second round (running prefix of directions)
-    const int ax = pl.ext_x[0], ay = pl.ext_y[0], bxp = pl.ext_x[1], byp = pl.ext_y[1];
     int2* LX = a.lxy + sl; int* LI = a.lidx + sl;
     int2* UX = a.uxy + sl; int* UI = a.uidx + sl;
     if (ax == bxp && ay == byp) {   // every point equal: one vertex
@@ -458,7 +554,6 @@ k_batch(BatchArgs a) {
       __syncthreads();
       continue;
     }
-    const int ux = bxp - ax, uy = byp - ay, d0x = ax - bxp, d0y = ay - byp;
     const u64 ymask = pl.ybits ? ((~0ull) >> (64 - pl.ybits)) : 0ull;
     Dir2b R = {d0x, d0y, d0x, d0y};
     u32 rl = 0, ru = 0;

@@ -43,7 +43,7 @@ class hull_stats(ctypes.Structure):
 NUM_STAGES = 12
 # Stage slots of hull_profile.ms on the bucket-sort path (the default) and on
 # the radix-pass path (a call whose bins the bucket sort could not take).
-STAGE_NAMES = ["extremes", "filter", "scatter", "split", "sort"] + ["-%d" % i for i in range(5, 10)] + [
+STAGE_NAMES = ["extremes", "witness", "filter", "scatter", "split", "sort"] + ["-%d" % i for i in range(6, 10)] + [
     "regions", "final"]
 RADIX_STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8)] + ["regions", "final"]
 
@@ -51,7 +51,7 @@ RADIX_STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8
 class hull_profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("radix_calls", ctypes.c_int64), ("sort_passes", ctypes.c_int64),
                 ("points", ctypes.c_int64), ("survivors", ctypes.c_int64), ("second_round", ctypes.c_int64),
-                ("ms", ctypes.c_double * NUM_STAGES)]
+                ("ms", ctypes.c_double * NUM_STAGES), ("witness_survivors", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -295,6 +295,7 @@ class Context:
         names = STAGE_NAMES if p.radix_calls == 0 else RADIX_STAGE_NAMES
         return {"calls": p.calls, "radix_calls": p.radix_calls, "sort_passes": p.sort_passes, "points": p.points,
                 "survivors": p.survivors, "second_round": p.second_round,
+                "witness_survivors": p.witness_survivors,
                 "ms": {names[k]: p.ms[k] for k in range(NUM_STAGES)}}
 
     # ------------------------------------------------------------ learned

@@ -16,10 +16,10 @@ import bench  # noqa: E402
 
 def _prof(sort_ms=0.17, radix_calls=0):
     calls = 4
-    per_hull = {"extremes": 0.04, "filter": 0.10, "scatter": 0.09, "split": 0.12,
-                "sort": sort_ms, "-5": 0.0, "regions": 0.01, "final": 0.035}
+    per_hull = {"extremes": 0.04, "witness": 0.01, "filter": 0.10, "scatter": 0.09, "split": 0.12,
+                "sort": sort_ms, "-6": 0.0, "regions": 0.01, "final": 0.035}
     return {"calls": calls, "radix_calls": radix_calls, "points": 20_000_000 * calls,
-            "survivors": 8_000_000 * calls, "second_round": 300_000 * calls,
+            "survivors": 0, "witness_survivors": 8_000_000 * calls, "second_round": 300_000 * calls,
             "ms": {k: v * calls for k, v in per_hull.items()}}
 
 
@@ -31,7 +31,7 @@ def test_dominant_stage_and_its_bandwidth():
     assert r["achieved"] == pytest.approx(b / 0.17e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
     assert set(r["stages"]) == set(bench.STAGE_KERNELS)
-    assert "-5" not in r["stage_ms_per_hull"]
+    assert "-6" not in r["stage_ms_per_hull"]
     # the pipeline figure: all stages' algorithmic bytes over their summed time
     tot_b = sum(k["algorithmic_bytes"] for k in r["stages"].values())
     tot_ms = sum(r["stage_ms_per_hull"].values())
@@ -41,6 +41,9 @@ def test_dominant_stage_and_its_bandwidth():
 def test_another_stage_can_dominate():
     r = bench.roofline_of(_prof(sort_ms=0.05), 6000.0, "measured")
     assert r["kernel"].startswith("k3_split")
+    # the fused filter's bytes: one read of the points and the pairs it writes
+    assert r["stages"]["filter"]["algorithmic_bytes"] == pytest.approx(8.0 * 20_000_000 + 12.0 * 8_000_000)
+    assert r["stages"]["filter"]["units"] == pytest.approx(20_000_000)
 
 
 def test_rerun_on_radix_passes_reports_no_single_kernel():
