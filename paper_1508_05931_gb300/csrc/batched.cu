@@ -272,13 +272,25 @@ k_batch(BatchArgs a) {
 
     // ---- 1. extremes (every BW_STRIDE-th point copied to the sort's second
     // key buffer, free until step 3, for the witnesses)
+    // (BT_FITEMS points per thread and round, loaded before any is used).
     int2* smp = reinterpret_cast<int2*>(a.kb + sl);
     BestX b;
     bx_init(b);
-    for (u32 j = threadIdx.x; j < n; j += BLOCK) {
-      const int2 p = P[j];
-      bx_point(b, p.x, p.y, j);
-      if (j % BW_STRIDE == 0) smp[j / BW_STRIDE] = p;
+    for (u32 base = 0; base < n; base += FCH) {
+      int2 p[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + r * BLOCK + threadIdx.x;
+        p[r] = j < n ? P[j] : make_int2(0, 0);
+      }
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + r * BLOCK + threadIdx.x;
+        if (j < n) {
+          bx_point(b, p[r].x, p[r].y, j);
+          if (j % BW_STRIDE == 0) smp[j / BW_STRIDE] = p[r];
+        }
+      }
     }
     bx_warp(b);
     if (lane == 0)
@@ -362,8 +374,18 @@ k_batch(BatchArgs a) {
     __syncthreads();
     {
       const u32 ns = (n + BW_STRIDE - 1) / BW_STRIDE;
-      for (u32 i = threadIdx.x; i < ns; i += BLOCK) {
-        const int2 p = __ldcg(&smp[i]);
+      for (u32 i0 = 0; i0 < ns; i0 += FCH) {
+      int2 sp[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 i = i0 + r * BLOCK + threadIdx.x;
+        sp[r] = i < ns ? __ldcg(&smp[i]) : make_int2(0, 0);
+      }
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 i = i0 + r * BLOCK + threadIdx.x;
+        if (i >= ns) continue;
+        const int2 p = sp[r];
         bool in = pl.ncorner >= 3;
         for (int e = 0; e < kMaxCorners && in; ++e) {
           if (e >= pl.ncorner) break;
@@ -380,6 +402,7 @@ k_batch(BatchArgs a) {
         const u64 key = ((u64)(u32)(p.x - pl.x0) << pl.ybits) | (u64)(u32)(p.y - pl.y0);
         const u32 wbin = (u32)(key >> wshift);
         atomicMax(&S.wkey[(c > 0 ? 0 : BW_BINS) + wbin], ((u64)quant << 32) | (u64)(i + 1u));
+      }
       }
     }
     __syncthreads();
