@@ -44,6 +44,7 @@ constexpr int BT_MAX_CHUNKS = 1024; // chain chunks per instance (bounds n_i)
 constexpr int BW_BITS = 9;          // witness bins per instance: the top BW_BITS of the key
 constexpr int BW_BINS = 1 << BW_BITS;
 constexpr u32 BW_STRIDE = 32;       // one sampled point in every BW_STRIDE
+constexpr u32 BT_BIGBIN = 1024;     // larger witness bins are sorted by the whole block
 
 struct BestX {
   u64 k[4];
@@ -85,19 +86,83 @@ __device__ __forceinline__ void bx_warp(BestX& b) {
 
 __device__ __forceinline__ u32 bitlen32(u32 v) { return v ? 32u - (u32)__clz(v) : 0u; }
 
+// Strictly inside the filter polygon (k >= 3 edges in shared memory, each
+// {e_x, -e_y, low and high words of the constant}: the edge's cross product
+// with the point, positive strictly inside).
+__device__ __forceinline__ bool in_polygon(const int4* E, int k, int x, int y) {
+  bool in = k >= 3;
+  for (int e = 0; e < k && in; ++e) {
+    const int4 q = E[e];
+    const long long c = (long long)(((u64)(u32)q.w << 32) | (u64)(u32)q.z);
+    in = (long long)q.x * y + (long long)q.y * x + c > 0;
+  }
+  return in;
+}
+
 // Per-instance parameters, built by thread 0 from the extremes.
 struct IPlan {
   int ext_idx[4];
   int ext_x[4], ext_y[4];
   int ncorner;
-  int ex[kMaxCorners], ney[kMaxCorners];
-  long long nc[kMaxCorners];
   int learned;
   int x0, y0;
   u32 ybits, npasses;
   u32 kbits;
   int bad;
 };
+
+// Sorting (key, index) pairs in shared memory; pairs are distinct because
+// the indices are.
+__device__ __forceinline__ bool pair_lt(u64 ka, u32 va, u64 kb, u32 vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+__device__ __forceinline__ void pair_ce(u64* K, u32* V, u32 i, u32 l) {
+  const u64 ki = K[i], kl = K[l];
+  const u32 vi = V[i], vl = V[l];
+  if (pair_lt(kl, vl, ki, vi)) { K[i] = kl; K[l] = ki; V[i] = vl; V[l] = vi; }
+}
+// Bitonic network of the next power of two N >= m in its form without
+// direction flags (the first step of every merge compares an element with
+// its mirror in the merged block, the rest are half-cleaners, every
+// compare-exchange puts the smaller pair first).  The slots past m hold an
+// implicit maximum that no compare-exchange would move, so exchanges that
+// reach past m are skipped.  Lanes [0, nthr) of the calling group (warp or
+// block) take the pairs of every step; sync() separates the steps.
+template <typename Sync>
+__device__ __forceinline__ void bitonic_pairs(u64* K, u32* V, u32 m, u32 t0, u32 nthr, Sync sync) {
+  u32 N = 1;
+  while (N < m) N <<= 1;
+  for (u32 k = 2; k <= N; k <<= 1) {
+    for (u32 j = k >> 1; j > 0; j >>= 1) {
+      const u32 lj = (u32)__ffs(j) - 1u;
+      for (u32 t = t0; t < N / 2; t += nthr) {
+        const u32 g = t >> lj, o = t & (j - 1u);
+        u32 i, l;
+        if (j == k >> 1) { i = g * k + o; l = g * k + k - 1u - o; }
+        else { i = g * 2u * j + o; l = i + j; }
+        if (l < m) pair_ce(K, V, i, l);
+      }
+      sync();
+    }
+  }
+}
+// At most 32 pairs by one warp in registers (shuffle bitonic network).
+__device__ __forceinline__ void warp_sort32(u64* K, u32* V, u32 c, int lane) {
+  u64 k = (u32)lane < c ? K[lane] : ~0ull;
+  u32 v = (u32)lane < c ? V[lane] : ~0u;
+  #pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+    #pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const u64 pk = __shfl_xor_sync(0xFFFFFFFFu, k, j);
+      const u32 pv = __shfl_xor_sync(0xFFFFFFFFu, v, j);
+      const bool up = (lane & kk) == 0, lower = (lane & j) == 0;
+      const bool psmall = pair_lt(pk, pv, k, v);
+      if ((lower == up) ? psmall : !psmall) { k = pk; v = pv; }
+    }
+  }
+  if ((u32)lane < c) { K[lane] = k; V[lane] = v; }
+}
 
 struct Dir2b {
   int lx, ly, ux, uy;
@@ -119,6 +184,7 @@ template <int BLOCK>
 struct Smem {
   static constexpr int W = BLOCK / 32;
   static constexpr int CHUNK = BLOCK * BT_LEAF;   // chain points per shared-memory chunk
+  static constexpr int SCAP = BLOCK == 512 ? 14336 : 6144;   // survivors sorted in shared memory
   u32 wpos[W][kRadix];
   u32 hist[kMaxPasses][kRadix];
   u32 cur[kRadix];
@@ -143,10 +209,17 @@ struct Smem {
       u64 wkey[2 * BW_BINS];         // the sample's best witness per (region, bin)
       int2 wtab[2 * BW_BINS];        // witness direction of (bin, region)
     };
+    struct {                         // sort by bins (steps 3-4)
+      u64 bk[SCAP];
+      u32 bi[SCAP];
+    };
   };
   u64 wmax[W];
   int ccnt[BLOCK];                   // per-thread chain lengths inside a chunk
   int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
+  int4 edge[kMaxCorners];            // the filter polygon's edges (in_polygon)
+  u32 nbig;                          // witness bins above BT_BIGBIN survivors
+  unsigned short big[BW_BINS];
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
   int4 pair[BT_MAX_CHUNKS / 2];      // bridge results of one merge level
 };
@@ -353,8 +426,8 @@ k_batch(BatchArgs a) {
       for (int j = 0; j < kMaxCorners; ++j) {
         const int jj = j < k ? j : 0, jn = (j + 1 < k) ? j + 1 : 0;
         const int e_x = S.corner_x[jn] - S.corner_x[jj], e_y = S.corner_y[jn] - S.corner_y[jj];
-        pl.ex[j] = e_x; pl.ney[j] = -e_y;
-        pl.nc[j] = -((long long)e_x * S.corner_y[jj] - (long long)e_y * S.corner_x[jj]);
+        const long long c = -((long long)e_x * S.corner_y[jj] - (long long)e_y * S.corner_x[jj]);
+        S.edge[j] = make_int4(e_x, -e_y, (int)(u32)(u64)c, (int)(u32)((u64)c >> 32));
       }
     }
     for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
@@ -364,12 +437,16 @@ k_batch(BatchArgs a) {
       __syncthreads();
       continue;
     }
-    const IPlan pl = S.plan;
+    // The plan's scalars in registers (nothing indexed at run time: no
+    // local-memory copy); the polygon's edges stay in shared memory.
+    const int ax = S.plan.ext_x[0], ay = S.plan.ext_y[0], bxp = S.plan.ext_x[1], byp = S.plan.ext_y[1];
+    const int ext0 = S.plan.ext_idx[0], ext1 = S.plan.ext_idx[1];
+    const int x0 = S.plan.x0, y0 = S.plan.y0, ncorner = S.plan.ncorner;
+    const u32 ybits = S.plan.ybits, npasses = S.plan.npasses, kbits = S.plan.kbits;
 
     // ---- 1b. witnesses of the sampled first-round survivors
-    const int ax = pl.ext_x[0], ay = pl.ext_y[0], bxp = pl.ext_x[1], byp = pl.ext_y[1];
     const int ux = bxp - ax, uy = byp - ay, d0x = ax - bxp, d0y = ay - byp;
-    const u32 wshift = pl.kbits > (u32)BW_BITS ? pl.kbits - (u32)BW_BITS : 0u;
+    const u32 wshift = kbits > (u32)BW_BITS ? kbits - (u32)BW_BITS : 0u;
     for (int q = threadIdx.x; q < 2 * BW_BINS; q += BLOCK) S.wkey[q] = 0ull;
     __syncthreads();
     {
@@ -386,12 +463,7 @@ k_batch(BatchArgs a) {
         const u32 i = i0 + r * BLOCK + threadIdx.x;
         if (i >= ns) continue;
         const int2 p = sp[r];
-        bool in = pl.ncorner >= 3;
-        for (int e = 0; e < kMaxCorners && in; ++e) {
-          if (e >= pl.ncorner) break;
-          in = (long long)pl.ex[e] * p.y + (long long)pl.ney[e] * p.x + pl.nc[e] > 0;
-        }
-        if (in) continue;                                        // not a first-round survivor
+        if (in_polygon(S.edge, ncorner, p.x, p.y)) continue;    // not a first-round survivor
         const int dx = p.x - bxp, dy = p.y - byp;
         const long long c = cross2(d0x, d0y, dx, dy);            // > 0 lower, < 0 upper
         if (c == 0) continue;
@@ -399,7 +471,7 @@ k_batch(BatchArgs a) {
         const float fc = fabsf((float)c), fe = (float)e2;
         const float qa = 1.0f - fe / (fabsf(fe) + fc);           // monotone pseudo-angle from P_0 - P_l
         const u32 quant = (u32)fminf(fmaxf(qa, 0.0f) * 2147483648.0f, 4294967040.0f);
-        const u64 key = ((u64)(u32)(p.x - pl.x0) << pl.ybits) | (u64)(u32)(p.y - pl.y0);
+        const u64 key = ((u64)(u32)(p.x - x0) << ybits) | (u64)(u32)(p.y - y0);
         const u32 wbin = (u32)(key >> wshift);
         atomicMax(&S.wkey[(c > 0 ? 0 : BW_BINS) + wbin], ((u64)quant << 32) | (u64)(i + 1u));
       }
@@ -445,69 +517,160 @@ k_batch(BatchArgs a) {
       }
     }
 
-    // ---- 2. filter + compaction (+ digit histograms)
+    // ---- 2. witness test, filter polygon and compaction (+ digit
+    // histograms).  Warp w takes the round's points [base + w WSPAN, base +
+    // (w + 1) WSPAN), so the survivors come out in input order; the next
+    // round's points are loaded before this round's scan.
+    constexpr u32 WSPAN = 32u * BT_FITEMS;
+    u32* bcnt = &S.hist[0][0];          // survivors per witness bin (zeroed with the histograms)
+    u32* bcur = &S.hist[2][0];
     u32 run = 0;
-    for (u32 base = 0; base < n; base += FCH) {
-      int px[BT_FITEMS], py[BT_FITEMS];
-      bool keep[BT_FITEMS];
-      u32 pre[BT_FITEMS];
+    int2 cur[BT_FITEMS];
+    #pragma unroll
+    for (int r = 0; r < BT_FITEMS; ++r) {
+      const u32 j = wid * WSPAN + r * 32 + lane;
+      cur[r] = j < n ? P[j] : make_int2(0, 0);
+    }
+    u32 parity = 0;
+    for (u32 base = 0; base < n; base += FCH, parity ^= 1u) {
+      const u32 j0 = base + wid * WSPAN + lane;
+      u32 kmask = 0;
       #pragma unroll
-      for (int r = 0; r < BT_FITEMS; ++r) {
-        const u32 j = base + r * BLOCK + threadIdx.x;
-        px[r] = 0; py[r] = 0;
-        bool in = false;
-        if (j < n) {
-          const int2 p = P[j];
-          px[r] = p.x; py[r] = p.y;
-          in = pl.ncorner >= 3;
-          for (int e = 0; e < kMaxCorners && in; ++e) {
-            if (e >= pl.ncorner) break;
-            const long long o = (long long)pl.ex[e] * p.y + (long long)pl.ney[e] * p.x + pl.nc[e];
-            in = o > 0;
-          }
-        }
-        keep[r] = (j < n) && !in;
-        if (keep[r]) {                  // the witness test of the point's bin and region
-          const int dx = px[r] - bxp, dy = py[r] - byp;
+      for (int r = 0; r < BT_FITEMS; ++r) {        // the witness test of the point's bin and region
+        if (j0 + r * 32 < n) {
+          const int dx = cur[r].x - bxp, dy = cur[r].y - byp;
           const long long c = cross2(d0x, d0y, dx, dy);
-          const u64 key = ((u64)(u32)(px[r] - pl.x0) << pl.ybits) | (u64)(u32)(py[r] - pl.y0);
+          const u64 key = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
           const int2 w = S.wtab[2 * (u32)(key >> wshift) + (c < 0 ? 1u : 0u)];
           const long long t = cross2(w.x, w.y, dx, dy);
-          keep[r] = c == 0 || (c > 0 ? t > 0 : t < 0);
+          if (c == 0 || (c > 0 ? t > 0 : t < 0)) kmask |= 1u << r;
         }
-        const u32 bal = __ballot_sync(0xFFFFFFFFu, keep[r]);
-        pre[r] = __popc(bal & lt_mask);
-        if (lane == 0) S.red[r * W + wid] = __popc(bal);
       }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        u32 t = 0;
-        for (int q = 0; q < BT_FITEMS * W; ++q) { const u32 c = S.red[q]; S.red[q] = t; t += c; }
-        S.red[BT_FITEMS * W] = t;
-      }
-      __syncthreads();
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r)          // the first round on the witness survivors
+        if (((kmask >> r) & 1u) && in_polygon(S.edge, ncorner, cur[r].x, cur[r].y)) kmask &= ~(1u << r);
+      u32 bal[BT_FITEMS], wc = 0;
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) {
-        if (keep[r]) {
-          const u32 pos = run + S.red[r * W + wid] + pre[r];
-          const u64 key = ((u64)(u32)(px[r] - pl.x0) << pl.ybits) | (u64)(u32)(py[r] - pl.y0);
-          if (pos < n) {
-            a.ka[sl + pos] = key;
-            a.ia[sl + pos] = base + r * BLOCK + threadIdx.x;
-          }
-          for (u32 p = 0; p < pl.npasses; ++p)
-            atomicAdd(&S.hist[p][(u32)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
-        }
+        bal[r] = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
+        wc += __popc(bal[r]);
       }
-      run += S.red[BT_FITEMS * W];
+      u32* red = S.red + parity * (W + 1);
+      if (lane == 0) red[wid] = wc;
+      int2 nxt[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = j0 + FCH + r * 32;
+        nxt[r] = j < n ? P[j] : make_int2(0, 0);
+      }
       __syncthreads();
+      if (wid == 0) {
+        const u32 v = lane < W ? red[lane] : 0u;
+        u32 inc = v;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= o) inc += t;
+        }
+        if (lane < W) red[lane] = inc - v;
+        if (lane == W - 1) red[W] = inc;
+      }
+      __syncthreads();
+      u32 pos = run + red[wid];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        if ((kmask >> r) & 1u) {
+          const u32 q = pos + __popc(bal[r] & lt_mask);
+          const u64 key = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
+          if (q < n) {
+            a.ka[sl + q] = key;
+            a.ia[sl + q] = j0 + r * 32;
+          }
+          atomicAdd(&bcnt[(u32)(key >> wshift)], 1u);
+        }
+        pos += __popc(bal[r]);
+      }
+      run += red[W];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
     }
+    __syncthreads();
     const u32 s = run;
 
-    // ---- 3. stable LSD radix sort of (key, idx), tiles in order
+    // ---- 3. sort (step 4) by (key, index), the order of a stable sort of
+    // the keys in input order.  Up to SCAP survivors: moved into shared
+    // memory by witness bin (the key's top bits, so the bins are in key
+    // order), then every bin sorted in place (a warp per bin, the whole block
+    // for bins above BT_BIGBIN).  More: a stable LSD radix sort through the
+    // scratch region (digit histograms first).
+    const u64* rs_k;
+    const u32* rs_i;
+    if (s <= (u32)Smem<BLOCK>::SCAP) {
+      {
+        constexpr int PER = BW_BINS / BLOCK > 0 ? BW_BINS / BLOCK : 1;
+        u32 v[PER], tot = 0;
+        #pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int b = threadIdx.x * PER + q;
+          v[q] = b < BW_BINS ? bcnt[b] : 0u;
+          tot += v[q];
+        }
+        u32 inc = tot;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= o) inc += t;
+        }
+        if (lane == 31) S.red[wid] = inc;
+        if (threadIdx.x == 0) S.nbig = 0;
+        __syncthreads();
+        u32 ex = inc - tot;
+        for (int w = 0; w < wid; ++w) ex += S.red[w];
+        #pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int b = threadIdx.x * PER + q;
+          if (b < BW_BINS) bcur[b] = ex;
+          ex += v[q];
+        }
+        __syncthreads();
+      }
+      for (u32 i = threadIdx.x; i < s; i += BLOCK) {
+        const u64 k = __ldcg(&a.ka[sl + i]);
+        const u32 q = atomicAdd(&bcur[(u32)(k >> wshift)], 1u);
+        S.bk[q] = k;
+        S.bi[q] = __ldcg(&a.ia[sl + i]);
+      }
+      __syncthreads();
+      for (int b = wid; b < BW_BINS; b += W) {   // bcur[b]: the bin's end now
+        const u32 c = bcnt[b], b0 = bcur[b] - c;
+        if (c <= 1u) continue;
+        if (c <= 32u) {
+          warp_sort32(S.bk + b0, S.bi + b0, c, lane);
+        } else if (c <= BT_BIGBIN) {
+          bitonic_pairs(S.bk + b0, S.bi + b0, c, (u32)lane, 32u, [] { __syncwarp(); });
+        } else if (lane == 0) {
+          S.big[atomicAdd(&S.nbig, 1u)] = (unsigned short)b;
+        }
+      }
+      __syncthreads();
+      for (u32 q = 0; q < S.nbig; ++q) {
+        const u32 b = S.big[q], c = bcnt[b], b0 = bcur[b] - c;
+        bitonic_pairs(S.bk + b0, S.bi + b0, c, threadIdx.x, (u32)BLOCK, [] { __syncthreads(); });
+      }
+      rs_k = S.bk;
+      rs_i = S.bi;
+    } else {
+    for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < s; i += BLOCK) {
+      const u64 key = __ldcg(&a.ka[sl + i]);
+      for (u32 p = 0; p < npasses; ++p)
+        atomicAdd(&S.hist[p][(u32)(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
     u64* src_k = a.ka + sl; u32* src_i = a.ia + sl;
     u64* dst_k = a.kb + sl; u32* dst_i = a.ib + sl;
-    for (u32 pass = 0; pass < pl.npasses; ++pass) {
+    for (u32 pass = 0; pass < npasses; ++pass) {
       const u32 shift = pass * kRadixBits;
       // Exclusive start of every digit inside the instance's range.
       u32 hv = 0, hinc = 0;
@@ -567,17 +730,20 @@ k_batch(BatchArgs a) {
       u64* tk = src_k; src_k = dst_k; dst_k = tk;
       u32* ti = src_i; src_i = dst_i; dst_i = ti;
     }
-    // sorted keys are in src_*
+    rs_k = src_k;
+    rs_i = src_i;
+    }
+    __syncthreads();
 
     // ---- 4. region split + second round (running prefix of directions)
     int2* LX = a.lxy + sl; int* LI = a.lidx + sl;
     int2* UX = a.uxy + sl; int* UI = a.uidx + sl;
     if (ax == bxp && ay == byp) {   // every point equal: one vertex
-      if (threadIdx.x == 0) { a.out_tmp[sl] = pl.ext_idx[0]; a.hcount[inst] = 1; }
+      if (threadIdx.x == 0) { a.out_tmp[sl] = ext0; a.hcount[inst] = 1; }
       __syncthreads();
       continue;
     }
-    const u64 ymask = pl.ybits ? ((~0ull) >> (64 - pl.ybits)) : 0ull;
+    const u64 ymask = ybits ? ((~0ull) >> (64 - ybits)) : 0ull;
     Dir2b R = {d0x, d0y, d0x, d0y};
     u32 rl = 0, ru = 0;
     for (u32 cb = 0; cb < s; cb += FCH) {
@@ -590,10 +756,10 @@ k_batch(BatchArgs a) {
         const u32 p = first + i;
         side[i] = 0; px[i] = 0; py[i] = 0; pi[i] = 0;
         if (p < s) {
-          const u64 k = src_k[p];
-          px[i] = pl.x0 + (int)(u32)(k >> pl.ybits);
-          py[i] = pl.y0 + (int)(u32)(k & ymask);
-          pi[i] = (int)src_i[p];
+          const u64 k = rs_k[p];
+          px[i] = x0 + (int)(u32)(k >> ybits);
+          py[i] = y0 + (int)(u32)(k & ymask);
+          pi[i] = (int)rs_i[p];
           const long long o = cross2(ux, uy, px[i] - ax, py[i] - ay);
           side[i] = o < 0 ? -1 : (o > 0 ? 1 : 0);
           const int vx = px[i] - bxp, vy = py[i] - byp;
@@ -650,10 +816,10 @@ k_batch(BatchArgs a) {
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      LX[0] = make_int2(ax, ay); LI[0] = pl.ext_idx[0];
-      UX[0] = make_int2(ax, ay); UI[0] = pl.ext_idx[0];
-      LX[rl + 1] = make_int2(bxp, byp); LI[rl + 1] = pl.ext_idx[1];
-      UX[ru + 1] = make_int2(bxp, byp); UI[ru + 1] = pl.ext_idx[1];
+      LX[0] = make_int2(ax, ay); LI[0] = ext0;
+      UX[0] = make_int2(ax, ay); UI[0] = ext0;
+      LX[rl + 1] = make_int2(bxp, byp); LI[rl + 1] = ext1;
+      UX[ru + 1] = make_int2(bxp, byp); UI[ru + 1] = ext1;
     }
     __syncthreads();
 

@@ -160,3 +160,30 @@ def test_full_size_batch_sampled(hull_lib, tmp_path, monkeypatch):
     for i in sorted(pick):
         p = pts[offs[i]:offs[i + 1]]
         assert o[oo[i]:oo[i + 1]].tolist() == oracle.hull(p).tolist(), (i, len(p), int(fam[i]))
+
+
+def sort_path_parts():
+    """Instances for every branch of the batched sort: survivors above both
+    block sizes' shared-memory capacities (the radix fallback), between them,
+    a witness bin above the per-warp limit (3,000 copies of the leftmost
+    point), and mid-sized bins (near-circle sets)."""
+    rng = np.random.default_rng(41)
+    crowd = np.concatenate([np.tile(np.array([[-1000, 0]], np.int32), (3000, 1)),
+                            rng.integers(-500, 501, size=(2000, 2)).astype(np.int32)])
+    crowd = crowd[rng.permutation(len(crowd))]
+    return [W.parabola_lattice(20000), W.parabola_lattice(5000), crowd,
+            W.near_circle(30000, 2.0 ** 20, 43), W.near_circle(9000, 2.0 ** 16, 44),
+            W.uniform_disk(200000, 2.0 ** 28, 45)]
+
+
+@pytest.mark.parametrize("block", [256, 512])
+def test_batch_sort_paths_both_block_sizes(hull_lib, tmp_path, monkeypatch, block):
+    import re
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("GBHULL_AUTOTUNE_CACHE", str(cache))
+    parts = sort_path_parts()
+    with hull_lib.Context(0, autotune=True) as c:        # writes the cache for this device
+        run_batch(c, parts)
+    cache.write_text(re.sub(r'(batched_(?:small|large)": )\d+', r"\g<1>%d" % block, cache.read_text()))
+    with hull_lib.Context(0, autotune=True) as c:        # both buckets at the forced block size
+        check(parts, *run_batch(c, parts))
