@@ -20,8 +20,6 @@ using namespace gbh;
 
 namespace {
 
-constexpr uint32_t kDefaultSpin = 1u << 22;
-
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Device workspace for up to `cap` points, carved out of one allocation.
@@ -546,7 +544,7 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   if (!c) return HULL_ENOMEM;
   c->device = device;
   if (cfg) c->cfg = *cfg;
-  if (c->cfg.spin_limit == 0) c->cfg.spin_limit = kDefaultSpin;
+  if (c->cfg.spin_limit == 0) c->cfg.spin_limit = kDefaultSpinLimit;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return cuda_fail(cudaErrorUnknown); }
   c->num_sms = prop.multiProcessorCount;

@@ -162,6 +162,10 @@ __device__ __forceinline__ long long cross2(int ax, int ay, int bx, int by) {
   return (long long)ax * by - (long long)ay * bx;
 }
 
+// Rounds a device-side wait (look-back, grid barrier) spins before it gives
+// up with ERR_TIMEOUT, unless the caller's configuration sets another limit;
+// every entry point that launches the pipeline uses it.
+constexpr u32 kDefaultSpinLimit = 1u << 22;
 // Look-back status word: [epoch:32 | flag:2 | count:30].
 constexpr u32 ST_AGG = 1, ST_INCL = 2;
 // ---- Bulk asynchronous copies (TMA, non-tensor) into shared memory.

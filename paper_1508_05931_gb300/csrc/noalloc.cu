@@ -164,7 +164,7 @@ extern "C" hull_status hull_compute_noalloc(const int32_t* d_xy, int64_t n, int3
 
   cudaError_t e = cudaMemsetAsync(c.plan, 0, c.zero_bytes, st);
   if (e == cudaSuccess)
-    e = launch_k1(d_xy, un, 1u << 22, c.plan, c.partials, k1_grid(un, d->num_sms), st);
+    e = launch_k1(d_xy, un, kDefaultSpinLimit, c.plan, c.partials, k1_grid(un, d->num_sms), st);
   const size_t t2 = (un + k2_tile() - 1) / k2_tile();
   if (e == cudaSuccess)
     e = launch_k2(d_xy, c.plan, c.keys[0], c.idx[0], c.st_filter, c.mask, grid_for(d->occ_k2c, d->num_sms, t2),
