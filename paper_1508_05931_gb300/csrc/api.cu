@@ -168,7 +168,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t t3 = (cap + k3_tile() - 1) / k3_tile() + 1;
   const size_t t4 = (cap + k4_tile() - 1) / k4_tile() + 1;
   const size_t slots = cap + 4 + 2 * chunk;
-  const size_t nchunks = slots / chunk + 2;
+  const size_t nchunks = slots / (size_t)k5_min_chunk() + 2;
   const size_t parts = (size_t)c->num_sms * 4 + 8;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };

@@ -247,7 +247,7 @@ __device__ int build_chain(Smem<BLOCK>& S, const int2* xy, const int* idx, int m
     S.ccnt[threadIdx.x] = leaf_chain(S.sx, S.sy, S.si, b, max(0, min(BT_LEAF, len - b)), sgn);
     __syncthreads();
     const int nleaf = (len + BT_LEAF - 1) / BT_LEAF;
-    merge_tree<BT_LEAF>(S.sx, S.sy, S.si, S.ccnt, nleaf, sgn);
+    merge_tree<BT_LEAF>(S.sx, S.sy, S.si, S.ccnt, S.pair, nleaf, sgn);
     const int hc = S.ccnt[0];
     if (nch == 1) { *where = 0; return hc; }
     for (int i = threadIdx.x; i < hc; i += BLOCK) {

@@ -117,13 +117,17 @@ __device__ __forceinline__ int leaf_chain(int* sx, int* sy, int* si, int b, int 
 #define CHAIN_WALK_MAX 64
 #endif
 
-// Merges nleaf leaf chains held in shared memory (leaf l at [l * LEAF, ...),
-// cnt[l] points) level by level into one chain at [0, cnt[0]).  While the
-// chains of a level come from at most CHAIN_WALK_MAX points each, one thread
-// merges a pair with walk_bridge; longer ones take a warp each (bridge).
-// Called by every thread of the block.
+// Merges nleaf <= blockDim.x leaf chains held in shared memory (leaf l at
+// [l * LEAF, ...), cnt[l] points) level by level into one chain at
+// [0, cnt[0]).  Every level first finds the bridge of every pair: while the
+// chains of a level come from at most CHAIN_WALK_MAX points each, one
+// thread per pair with walk_bridge, then one warp per pair (bridge); the
+// pair's move (destination, source, count) goes to pairs[] (nleaf / 2 + 1
+// entries).  Then the whole block moves the kept part of every right-hand
+// chain behind the kept part of its left-hand one, each thread taking one
+// slot per round.  Called by every thread of the block.
 template <int LEAF>
-__device__ __forceinline__ void merge_tree(int* sx, int* sy, int* si, int* cnt, int nleaf, int sgn) {
+__device__ __forceinline__ void merge_tree(int* sx, int* sy, int* si, int* cnt, int4* pairs, int nleaf, int sgn) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nthreads = blockDim.x, nwarps = nthreads >> 5;
   for (int step = 1; step < nleaf; step <<= 1) {
@@ -131,38 +135,49 @@ __device__ __forceinline__ void merge_tree(int* sx, int* sy, int* si, int* cnt, 
     if (step * LEAF <= CHAIN_WALK_MAX) {
       for (int p = threadIdx.x; p < npair; p += nthreads) {
         const int la = 2 * p * step, lb = la + step;
-        if (lb >= nleaf) continue;
-        const int aB = la * LEAF, bB = lb * LEAF;
-        const int alpha = cnt[la], beta = cnt[lb];
-        SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
-        int is, js;
-        walk_bridge(A, alpha, B, beta, sgn, is, js);
-        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
-        for (int q = 0; q < n2; ++q) {
-          sx[dst + q] = sx[src + q]; sy[dst + q] = sy[src + q]; si[dst + q] = si[src + q];
+        int4 mv = make_int4(0, 0, 0, 0);
+        if (lb < nleaf) {
+          const int aB = la * LEAF, bB = lb * LEAF;
+          const int alpha = cnt[la], beta = cnt[lb];
+          SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
+          int is, js;
+          walk_bridge(A, alpha, B, beta, sgn, is, js);
+          mv = make_int4(aB + is + 1, bB + js, beta - js, 0);
+          cnt[la] = is + 1 + (beta - js);
         }
-        cnt[la] = is + 1 + n2;
+        pairs[p] = mv;
       }
     } else {
       for (int p = wid; p < npair; p += nwarps) {
         const int la = 2 * p * step, lb = la + step;
-        if (lb >= nleaf) continue;
-        const int aB = la * LEAF, bB = lb * LEAF;
-        const int alpha = cnt[la], beta = cnt[lb];
-        SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
-        int is, js;
-        bridge(A, alpha, B, beta, sgn, is, js);
-        const int dst = aB + is + 1, src = bB + js, n2 = beta - js;
-        for (int o = 0; o < n2; o += 32) {
-          const int q = o + lane;
-          int vx = 0, vy = 0, vi = 0;
-          if (q < n2) { vx = sx[src + q]; vy = sy[src + q]; vi = si[src + q]; }
-          __syncwarp();
-          if (q < n2) { sx[dst + q] = vx; sy[dst + q] = vy; si[dst + q] = vi; }
-          __syncwarp();
+        int4 mv = make_int4(0, 0, 0, 0);
+        if (lb < nleaf) {
+          const int aB = la * LEAF, bB = lb * LEAF;
+          const int alpha = cnt[la], beta = cnt[lb];
+          SmemChain A{sx + aB, sy + aB}, B{sx + bB, sy + bB};
+          int is, js;
+          bridge(A, alpha, B, beta, sgn, is, js);
+          mv = make_int4(aB + is + 1, bB + js, beta - js, 0);
+          if (lane == 0) cnt[la] = is + 1 + (beta - js);
         }
-        if (lane == 0) cnt[la] = is + 1 + n2;
+        if (lane == 0) pairs[p] = mv;
       }
+    }
+    __syncthreads();
+    // Rounds of blockDim.x slots in increasing order: a destination never
+    // lies after its source, so a round writes nothing a later round reads.
+    const int span = 2 * step * LEAF;
+    #pragma unroll
+    for (int r = 0; r < LEAF; ++r) {
+      const int q = threadIdx.x + r * nthreads;
+      int d = -1, vx = 0, vy = 0, vi = 0;
+      if (q < nleaf * LEAF && (q % span) >= step * LEAF) {   // a slot of a right-hand chain
+        const int4 mv = pairs[q / span];
+        const int off = q - mv.y;
+        if (off >= 0 && off < mv.z) { vx = sx[q]; vy = sy[q]; vi = si[q]; d = mv.x + off; }
+      }
+      __syncthreads();
+      if (d >= 0) { sx[d] = vx; sy[d] = vy; si[d] = vi; }
     }
     __syncthreads();
   }

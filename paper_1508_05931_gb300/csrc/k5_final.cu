@@ -2,8 +2,11 @@
 // the CPU as a stack-based scan of the pre-sorted survivors).  Here it runs
 // on the device as a parallel monotone chain:
 //
-//   phase A  each block takes chunks of K5_CHUNK consecutive points of a
-//            chain, every thread builds the chain of its K5_LEAF points with
+//   phase A  each block takes chunks of C consecutive points of a chain
+//            (C the smallest power of two from K5_MIN_CHUNK to K5_CHUNK that
+//            gives every block at most one chunk: short lists are spread
+//            over many SMs and every chunk's merge tree stays shallow);
+//            every thread builds the chain of its K5_LEAF points with
 //            the stack rule (pop while the turn is not strict), and adjacent
 //            sub-chains are merged level by level in shared memory (one
 //            thread per pair while they are short, then one warp per pair);
@@ -39,10 +42,14 @@ constexpr int K5_WARPS = K5_BLOCK / 32;
 #define K5_LEAF_CFG 2
 #endif
 constexpr int K5_LEAF = K5_LEAF_CFG;
-constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // points per chunk
+constexpr int K5_CHUNK = K5_BLOCK * K5_LEAF;   // points per chunk, at most
+#ifndef K5_MIN_CHUNK_CFG
+#define K5_MIN_CHUNK_CFG 256
+#endif
+constexpr int K5_MIN_CHUNK = K5_MIN_CHUNK_CFG;   // points per chunk, at least
 // Points block 0 can hold for the shared-memory phase B (and the size of
 // every block's chunk buffer).
-constexpr int K5_SMEM_PTS = K5_CHUNK > 4096 ? K5_CHUNK : 4096;
+constexpr int K5_SMEM_PTS = K5_CHUNK > 16384 ? K5_CHUNK : 16384;
 
 // Barrier over the first `nblocks` blocks of the (co-resident) grid.
 __device__ bool grid_barrier(Plan* plan, u32 spin, u32 nblocks) {
@@ -96,6 +103,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
   __shared__ int s_cnt[K5_BLOCK];
   __shared__ int s_start[K5_BLOCK];
   __shared__ int s_wsum[K5_WARPS];
+  __shared__ int4 s_pair[K5_BLOCK / 2 + 1];
 
   if (plan->error & (ERR_RANGE | ERR_TIMEOUT | ERR_INTERNAL | ERR_FALLBACK)) return;
   const u32 spin = plan->spin_limit;
@@ -106,9 +114,11 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
   cs.in_xy[1] = up_xy; cs.in_idx[1] = up_idx;
   cs.m[0] = plan->r_lo + 2;
   cs.m[1] = plan->r_up + 2;
-  for (int c = 0; c < 2; ++c) cs.nchunk[c] = (cs.m[c] + K5_CHUNK - 1) / K5_CHUNK;
+  u32 C = K5_MIN_CHUNK;
+  while (C < (u32)K5_CHUNK && (cs.m[0] + C - 1) / C + (cs.m[1] + C - 1) / C > gridDim.x) C <<= 1;
+  for (int c = 0; c < 2; ++c) cs.nchunk[c] = (cs.m[c] + C - 1) / C;
   cs.slot0[0] = 0;
-  cs.slot0[1] = cs.nchunk[0] * K5_CHUNK;
+  cs.slot0[1] = cs.nchunk[0] * C;
 
   // Every point equal: the hull is the single point P_0.
   {
@@ -134,8 +144,8 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     const int c = ch < cs.nchunk[0] ? 0 : 1;
     const u32 local = c == 0 ? ch : ch - cs.nchunk[0];
     const int sgn = c == 0 ? 1 : -1;
-    const u32 first = local * K5_CHUNK;
-    const int len = (int)min((u32)K5_CHUNK, cs.m[c] - first);
+    const u32 first = local * C;
+    const int len = (int)min(C, cs.m[c] - first);
     for (int i = threadIdx.x; i < len; i += K5_BLOCK) {
       const int2 p = cs.in_xy[c][first + i];
       sx[i] = p.x; sy[i] = p.y; si[i] = cs.in_idx[c][first + i];
@@ -147,14 +157,14 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     }
     __syncthreads();
     const int nleaf = (len + K5_LEAF - 1) / K5_LEAF;
-    merge_tree<K5_LEAF>(sx, sy, si, s_cnt, nleaf, sgn);
+    merge_tree<K5_LEAF>(sx, sy, si, s_cnt, s_pair, nleaf, sgn);
     const int hc = s_cnt[0];
     const u32 out0 = cs.slot0[c] + first;
     for (int i = threadIdx.x; i < hc; i += K5_BLOCK) {
       h0_xy[out0 + i] = make_int2(sx[i], sy[i]);
       h0_idx[out0 + i] = si[i];
     }
-    if (threadIdx.x == 0) cnt0[cs.slot0[c] / K5_CHUNK + local] = (u32)hc;
+    if (threadIdx.x == 0) cnt0[cs.slot0[c] / C + local] = (u32)hc;
     __syncthreads();
   }
 
@@ -183,7 +193,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
       __syncthreads();
       // Gather: warp w copies chunk chains w, w + K5_WARPS, ...
       for (u32 ch = wid; ch < total_chunks; ch += K5_WARPS) {
-        const u32 src = ch < cs.nchunk[0] ? ch * K5_CHUNK : cs.slot0[1] + (ch - cs.nchunk[0]) * K5_CHUNK;
+        const u32 src = ch < cs.nchunk[0] ? ch * C : cs.slot0[1] + (ch - cs.nchunk[0]) * C;
         const int dst = s_start[ch];
         for (int q = lane; q < s_cnt[ch]; q += 32) {
           const int2 p = __ldcg(&h0_xy[src + q]);
@@ -248,13 +258,13 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
       const u32 p = c == 0 ? job : job - np0;
       const int sgn = c == 0 ? 1 : -1;
       const u32 ca = 2 * p * step, cb = ca + step;
-      const u32 gca = cs.slot0[c] / K5_CHUNK + ca;
+      const u32 gca = cs.slot0[c] / C + ca;
       const int alpha = (int)__ldcg(&cur_cnt[gca]);
       int is = alpha - 1, js = 0, beta = 0;
       if (cb < cs.nchunk[c]) {
-        const u32 gcb = cs.slot0[c] / K5_CHUNK + cb;
+        const u32 gcb = cs.slot0[c] / C + cb;
         beta = (int)__ldcg(&cur_cnt[gcb]);
-        GlobalChain A{cur_xy + (size_t)gca * K5_CHUNK}, B{cur_xy + (size_t)gcb * K5_CHUNK};
+        GlobalChain A{cur_xy + (size_t)gca * C}, B{cur_xy + (size_t)gcb * C};
         bridge(A, alpha, B, beta, sgn, is, js);
       }
       if (lane == 0) {
@@ -264,8 +274,8 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
     }
     if (!grid_barrier(plan, spin, nblk)) return;
     // B2: gather every merged node into the other buffer.
-    const u32 span = 2 * step * K5_CHUNK;
-    const u32 total_slots = (cs.nchunk[0] + cs.nchunk[1]) * K5_CHUNK;
+    const u32 span = 2 * step * C;
+    const u32 total_slots = (cs.nchunk[0] + cs.nchunk[1]) * C;
     for (u32 q = blockIdx.x * K5_BLOCK + threadIdx.x; q < total_slots; q += nblk * K5_BLOCK) {
       const int c = q < cs.slot0[1] ? 0 : 1;
       const u32 rel = q - cs.slot0[c];
@@ -277,7 +287,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
       const u32 abase = cs.slot0[c] + p * span;
       u32 src;
       if (o <= (u32)jd.x) src = abase + o;
-      else src = abase + step * K5_CHUNK + (u32)jd.y + (o - (u32)jd.x - 1);
+      else src = abase + step * C + (u32)jd.y + (o - (u32)jd.x - 1);
       nxt_xy[q] = __ldcg(&cur_xy[src]);
       nxt_idx[q] = __ldcg(&cur_idx[src]);
     }
@@ -289,7 +299,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
 
   // ---------------- output: lower chain, then the upper chain reversed
   const u32 hl = __ldcg(&cur_cnt[0]);
-  const u32 hu = __ldcg(&cur_cnt[cs.slot0[1] / K5_CHUNK]);
+  const u32 hu = __ldcg(&cur_cnt[cs.slot0[1] / C]);
   const long long h = (long long)hl + (long long)hu - 2;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     plan->h = (u32)h; plan->h_lo = hl; plan->h_up = hu;
@@ -307,6 +317,7 @@ k5_final(const int2* __restrict__ lo_xy, const int* __restrict__ lo_idx,
 }  // namespace
 
 int k5_chunk() { return K5_CHUNK; }
+int k5_min_chunk() { return K5_MIN_CHUNK; }
 size_t k5_dyn_smem() { return (size_t)K5_SMEM_PTS * 3 * sizeof(int); }
 
 cudaError_t k5_configure(int* max_blocks_per_sm) {

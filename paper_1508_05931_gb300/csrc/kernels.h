@@ -119,7 +119,8 @@ cudaError_t launch_k4_chunked(const int2* xy, const int* idx, u32 m, u32 bs, Pla
 cudaError_t launch_k4_reverse(Plan* plan, int2* lo_xy, int* lo_idx, int2* up_xy, int* up_idx, int2* st_lo_xy,
                               int* st_lo_idx, int2* st_up_xy, int* st_up_idx, cudaStream_t st);
 
-int k5_chunk();
+int k5_chunk();       // points per chain chunk, at most
+int k5_min_chunk();   // and at least (the chunk-count arrays are sized for it)
 size_t k5_dyn_smem();
 cudaError_t k5_configure(int* max_blocks_per_sm);
 cudaError_t launch_k5(const int2* lo_xy, const int* lo_idx, const int2* up_xy, const int* up_idx,

@@ -78,7 +78,7 @@ Carve carve(unsigned char* base, int num_sms) {
   const size_t t3 = (cap + k3_tile() - 1) / k3_tile() + 1;
   const size_t t4 = (cap + k4_tile() - 1) / k4_tile() + 1;
   const size_t slots = cap + 4 + 2 * chunk;
-  const size_t nchunks = slots / chunk + 2;
+  const size_t nchunks = slots / (size_t)k5_min_chunk() + 2;
   const size_t parts = (size_t)num_sms * 4 + 8;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = up256(off + bytes); return base + o; };
