@@ -578,8 +578,9 @@ def main():
         return
 
     def step():
-        for t, o in zip(dev_sets, dev_outs):
-            ctx.compute_raw(t, o, stream)
+        # One hull_compute_multi call per step: the step's hulls run on the
+        # library's two lanes.
+        ctx.compute_multi(dev_sets, dev_outs, stream)
 
     for _ in range(max(args.warmup, 3)):
         step()

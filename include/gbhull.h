@@ -118,9 +118,15 @@ hull_status hull_compute_host(hull_ctx *ctx, const int32_t *h_xy, int64_t n, int
 /* Several independent hulls from device buffers in one call: for k in
  * [0, count), d_xy[k] (device int32[n[k]][2], 8-byte aligned) and d_out[k]
  * (device int32[cap[k]]) as in hull_compute; h_count[k] receives the hull
- * size.  The hulls run back to back on `stream` with one synchronisation at
- * the end (an input whose bucket sort needs the radix passes is rerun
- * afterwards, alone).  Returns the first failing input's status (every
+ * size.  With two inputs or more (and no learned proposal) the inputs
+ * alternate between two lanes that run concurrently: even inputs on
+ * `stream`, odd ones on an internal stream that first waits for the work
+ * queued on `stream` before the call; each lane has its own workspace (the
+ * second is allocated by the first such call and kept).  One
+ * synchronisation at the end, after both lanes (an input whose bucket sort
+ * needs the radix passes is rerun afterwards, alone).  With a single input
+ * or the learned proposal, the hulls run back to back on `stream`.
+ * Returns the first failing input's status (every
  * other input is still computed; h_count as hull_compute sets it).  With
  * profiling on (hull_set_profiling) the inputs run one call at a time.
  * count = 0 does nothing.  Errors: those of hull_compute; EINVAL for

@@ -101,6 +101,10 @@ struct hull_ctx {
   char* h_multi = nullptr;     // pinned summaries of hull_compute_multi (one per input)
   int32_t h_multi_cap = 0;
   Workspace ws;
+  // Second lane of hull_compute_multi: its own workspace and Plan, used on
+  // the aux stream while lane 0 runs on the caller's stream.
+  Workspace ws2;
+  Plan* plan2 = nullptr;
   HostStage hs;
   hull_stats last{};
   int64_t fallbacks = 0;       // calls rerun on the radix passes
@@ -606,6 +610,8 @@ void hull_destroy(hull_ctx* c) {
   DevGuard g(c->device);
   cudaDeviceSynchronize();
   free_ws(c->ws);
+  free_ws(c->ws2);
+  if (c->plan2) cudaFree(c->plan2);
   if (c->hs.d_in) cudaFree(c->hs.d_in);
   if (c->hs.d_out) cudaFree(c->hs.d_out);
   if (c->hs.d_in2) cudaFree(c->hs.d_in2);
@@ -708,17 +714,51 @@ hull_status hull_compute_multi(hull_ctx* c, int32_t count, const int32_t* const*
     }
     c->h_multi_cap = count;
   }
-  // Every input's bucket-sort hull queued back to back, each summary copied
-  // to its own slot; one synchronisation.
+  // Two lanes when there are two inputs or more (and no learned proposal,
+  // whose buffers are per context): input k runs on lane k % 2, lane 0 on
+  // the caller's stream with the context's workspace and Plan, lane 1 on
+  // the aux stream with the second ones, so that one hull's latency-bound
+  // back half overlaps the other's streaming front.  Every summary is
+  // copied to its own slot; one synchronisation.
+  const bool two = count >= 2 && !(c->cfg.proposal == 1 && c->have_weights);
+  if (two) {
+    std::swap(c->ws, c->ws2);
+    r = ensure_ws(c, (size_t)nmax);
+    std::swap(c->ws, c->ws2);
+    if (r != HULL_OK) return r;
+    if (!c->plan2) {
+      if (cudaMalloc(&c->plan2, sizeof(Plan)) != cudaSuccess) {
+        cudaGetLastError();
+        return HULL_ENOMEM;
+      }
+      if (cudaMemsetAsync(c->plan2, 0, sizeof(Plan), st) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    }
+    cudaError_t e = cudaEventRecord(c->bev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->bev[0], 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   for (int32_t k = 0; k < count; ++k) {
     if (n[k] == 0) continue;
+    const bool lane1 = two && (k & 1);
+    const cudaStream_t ls = lane1 ? c->aux : st;
+    if (lane1) { std::swap(c->ws, c->ws2); std::swap(c->plan, c->plan2); }
     c->prof_pending = false;
-    r = run_front(c, d_xy[k], (u32)n[k], st, true);
+    r = run_front(c, d_xy[k], (u32)n[k], ls, true);
     if (r == HULL_OK) r = run_final(c, c->ws.lo_xy, c->ws.lo_idx, c->ws.up_xy, c->ws.up_idx, (size_t)n[k], d_out[k],
-                                    cap[k], st);
-    if (r != HULL_OK) return r;
-    const cudaError_t e = cudaMemcpyAsync(c->h_multi + (size_t)k * kSummaryBytes, c->plan, kSummaryBytes,
-                                          cudaMemcpyDeviceToHost, st);
+                                    cap[k], ls);
+    cudaError_t e = cudaSuccess;
+    if (r == HULL_OK)
+      e = cudaMemcpyAsync(c->h_multi + (size_t)k * kSummaryBytes, c->plan, kSummaryBytes, cudaMemcpyDeviceToHost, ls);
+    if (lane1) { std::swap(c->ws, c->ws2); std::swap(c->plan, c->plan2); }
+    if (r != HULL_OK) {
+      if (two) cudaStreamSynchronize(c->aux);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (two) {
+    cudaError_t e = cudaEventRecord(c->bev[1], c->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->bev[1], 0);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   const cudaError_t e = cudaStreamSynchronize(st);

@@ -228,6 +228,18 @@ def test_device_multi_entry_point(ctx, hull_lib):
         assert h.cpu().numpy().tolist() == oracle.hull(p).tolist()
 
 
+def test_device_multi_full_size_two_lanes(ctx):
+    """The bench's step: the 20M square, the 20M disk and the 4M ring in one
+    multi call (both lanes, at full size), each hull equal to the oracle's."""
+    sets = [W.paper_square(), W.paper_disk(), W.adversarial_ring()]
+    ts = [dev(p) for p in sets]
+    outs = [torch.empty(len(p), dtype=torch.int32, device="cuda") for p in sets]
+    for _ in range(2):
+        res = ctx.compute_multi(ts, outs)
+        for p, h in zip(sets, res):
+            assert h.cpu().numpy().tolist() == oracle.hull(p).tolist()
+
+
 def test_host_entry_point(ctx):
     pts = W.uniform_disk(500_000, 2.0 ** 29, 8)
     pinned = torch.as_tensor(pts).pin_memory()
