@@ -395,7 +395,7 @@ def bench_angular_front(hull, torch, stream, dev_sets):
     """The paper's own ordering (steps 1-7 with the sort by angle about
     P_miny and Figure 2's forward and backward walks) through its stage entry
     point, and the whole angular hull (steps 1-8), on the two 20M sets: ms
-    per call (the entries allocate their own buffers and synchronise),
+    per call (the entries reuse the context's scratch and synchronise),
     first-round and second-round survivors, hull size.  Its failure never
     touches the main line."""
     res = {}

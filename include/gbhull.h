@@ -372,7 +372,10 @@ hull_status hull_stage_chain(hull_ctx *ctx, const int32_t *d_xy, int64_t m, int3
  * are always kept); *h_m receives the number of positions and *h_l the
  * position of P_l (-1 when P_0 is the only distinct point).  HULL_ECAPACITY
  * when cap < *h_m (nothing written); HULL_ERANGE for coordinates beyond
- * +-2^29.  Allocates and frees its temporary buffers; synchronises
+ * +-2^29; HULL_ENOMEM when its scratch cannot be allocated.  Its scratch
+ * (a few tens of bytes per point) lives in a context-owned area that the first
+ * call of a given size allocates and later calls reuse (it grows, after a
+ * device synchronisation, only when a larger call comes); synchronises
  * `stream`. */
 hull_status hull_stage_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_order,
                                uint8_t *d_keep, int64_t cap, int64_t *h_m, int64_t *h_l, void *stream);
@@ -386,8 +389,9 @@ hull_status hull_stage_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, in
  * among equal points the first in angular order among those the second
  * round keeps is reported (the one Graham's scan keeps; the backward walk
  * keeps the largest index of equal points).  *h_count receives the hull size on HULL_OK and on
- * HULL_ECAPACITY (then d_out is untouched).  Allocates and frees its
- * temporary buffers; synchronises `stream`. */
+ * HULL_ECAPACITY (then d_out is untouched).  Scratch as hull_stage_angular,
+ * plus about 40 bytes per point, in the same context-owned area; synchronises
+ * `stream`. */
 hull_status hull_compute_angular(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out, int64_t cap,
                                  int64_t *h_count, void *stream);
 

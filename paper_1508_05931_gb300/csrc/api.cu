@@ -105,6 +105,10 @@ struct hull_ctx {
   // the aux stream while lane 0 runs on the caller's stream.
   Workspace ws2;
   Plan* plan2 = nullptr;
+  // Scratch of the angular variant (hull_stage_angular and
+  // hull_compute_angular): grown to the largest call, kept.
+  void* ang = nullptr;
+  size_t ang_bytes = 0;
   HostStage hs;
   hull_stats last{};
   int64_t fallbacks = 0;       // calls rerun on the radix passes
@@ -332,9 +336,9 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   if (e != cudaSuccess) return cuda_fail(e);
   if (c->cfg.proposal == 1 && c->have_weights) {
     // Learned filter polygon: sampled features, MLP, exact hull of the
-    // chosen extremes and the quadrilateral's corners.
-    e = launch_features(d_xy, n, c->feat, c->ext, c->ext_xy, st);
-    if (e == cudaSuccess) e = launch_infer(c->feat, c->W16, c->ext_xy, c->plan, st);
+    // chosen extremes and the quadrilateral's corners, unless the gate finds
+    // the quadrilateral already discarding nearly all of a sample.
+    e = launch_propose(d_xy, n, c->W16, c->feat, c->ext, c->ext_xy, c->plan, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   mark(c, 1, st);
@@ -612,6 +616,7 @@ void hull_destroy(hull_ctx* c) {
   free_ws(c->ws);
   free_ws(c->ws2);
   if (c->plan2) cudaFree(c->plan2);
+  if (c->ang) cudaFree(c->ang);
   if (c->hs.d_in) cudaFree(c->hs.d_in);
   if (c->hs.d_out) cudaFree(c->hs.d_out);
   if (c->hs.d_in2) cudaFree(c->hs.d_in2);
@@ -814,21 +819,51 @@ hull_status hull_stage_sorted_survivors(hull_ctx* c, const int32_t* d_xy, int64_
   return r;
 }
 
-// Temporary device buffers of one stage call, freed on every return.
-struct TempBufs {
-  static constexpr int kSlots = 8;
-  void* p[kSlots] = {};
-  int k = 0;
-  cudaError_t take(size_t bytes, void** out) {
-    if (k == kSlots) return cudaErrorInvalidValue;
-    const cudaError_t e = cudaMalloc(out, bytes < 16 ? 16 : bytes);
-    if (e == cudaSuccess) p[k++] = *out;
-    return e;
-  }
-  ~TempBufs() {
-    for (int j = 0; j < k; ++j) cudaFree(p[j]);
+// The angular variant's scratch: carved in order from the context's
+// angular area, which grows (after a device synchronisation) when a call
+// needs more and is then kept.  Two carvers may share the area: the
+// outer call (hull_compute_angular) carves first and passes its end as the
+// inner call's start.
+struct AngCarve {
+  hull_ctx* c;
+  size_t off;
+  size_t need = 0;
+  bool measure;
+  AngCarve(hull_ctx* cc, size_t start, bool m) : c(cc), off(start), measure(m) {}
+  void* take(size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + (bytes < 16 ? 16 : bytes), 256);
+    need = off;
+    return measure ? nullptr : static_cast<char*>(c->ang) + o;
   }
 };
+
+cudaError_t ang_reserve(hull_ctx* c, size_t bytes) {
+  if (bytes <= c->ang_bytes && c->ang) return cudaSuccess;
+  cudaDeviceSynchronize();
+  if (c->ang) cudaFree(c->ang);
+  c->ang = nullptr;
+  c->ang_bytes = 0;
+  const size_t b = align_up(bytes, (size_t)1 << 20);
+  const cudaError_t e = cudaMalloc(&c->ang, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  c->ang_bytes = b;
+  return cudaSuccess;
+}
+
+// Bytes of hull_stage_angular's scratch for n points.
+size_t ang_stage_bytes(size_t n) {
+  AngCarve m(nullptr, 0, true);
+  m.take(n * 4); m.take(n * 8); m.take(n * 4); m.take(n * 8); m.take(n * 4); m.take((n + 1) * 8); m.take(16);
+  m.take(angle_walk_scratch_bytes((u32)n + 1));
+  return m.need;
+}
+
+hull_status ang_stage(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_order, uint8_t* d_keep,
+                      int64_t cap, int64_t* h_m, int64_t* h_l, void* stream, size_t start);
 
 hull_status hull_stage_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_order, uint8_t* d_keep,
                                int64_t cap, int64_t* h_m, int64_t* h_l, void* stream) {
@@ -837,23 +872,30 @@ hull_status hull_stage_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, int3
   *h_m = 0;
   *h_l = -1;
   DevGuard g(c->device);
+  if (ang_reserve(c, ang_stage_bytes((size_t)n)) != cudaSuccess) return HULL_ENOMEM;
+  return ang_stage(c, d_xy, n, d_order, d_keep, cap, h_m, h_l, stream, 0);
+}
+
+hull_status ang_stage(hull_ctx* c, const int32_t* d_xy, int64_t n, int32_t* d_order, uint8_t* d_keep,
+                      int64_t cap, int64_t* h_m, int64_t* h_l, void* stream, size_t start) {
+  *h_m = 0;
+  *h_l = -1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int32_t ext[4];
   hull_status r = hull_stage_extremes(c, d_xy, n, ext, stream);
   if (r != HULL_OK) return r;
   const u32 anchor = (u32)ext[2];
-  TempBufs t;
-  void *keep, *k1, *v1, *k2, *v2, *pts, *small, *walk;
   const size_t nn = (size_t)n;
-  cudaError_t e = t.take(nn * 4, &keep);
-  if (e == cudaSuccess) e = t.take(nn * 8, &k1);
-  if (e == cudaSuccess) e = t.take(nn * 4, &v1);
-  if (e == cudaSuccess) e = t.take(nn * 8, &k2);
-  if (e == cudaSuccess) e = t.take(nn * 4, &v2);
-  if (e == cudaSuccess) e = t.take((nn + 1) * 8, &pts);
-  if (e == cudaSuccess) e = t.take(16, &small);     // [0] points equal to the anchor, [1] P_l's position
-  if (e == cudaSuccess) e = t.take(angle_walk_scratch_bytes((u32)n + 1), &walk);
-  if (e != cudaSuccess) return cuda_fail(e);
+  AngCarve t(c, start, false);
+  void* keep = t.take(nn * 4);
+  void* k1 = t.take(nn * 8);
+  void* v1 = t.take(nn * 4);
+  void* k2 = t.take(nn * 8);
+  void* v2 = t.take(nn * 4);
+  void* pts = t.take((nn + 1) * 8);
+  void* small = t.take(16);     // [0] points equal to the anchor, [1] P_l's position
+  void* walk = t.take(angle_walk_scratch_bytes((u32)n + 1));
+  cudaError_t e = cudaSuccess;
   int64_t s = 0;
   r = hull_stage_filter(c, d_xy, n, static_cast<int32_t*>(keep), &s, stream);
   if (r != HULL_OK) return r;
@@ -904,21 +946,24 @@ hull_status hull_compute_angular(hull_ctx* c, const int32_t* d_xy, int64_t n, in
   if (n == 0) return HULL_OK;
   DevGuard g(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  TempBufs t;
-  void *order, *keep, *pos, *keys, *vals, *xyc, *lab, *outc;
   const size_t nn = (size_t)n;
-  cudaError_t e = t.take(nn * 4, &order);
-  if (e == cudaSuccess) e = t.take(nn + 16, &keep);
-  if (e == cudaSuccess) e = t.take(nn * 4 + 16, &pos);      // the count, then the positions
-  if (e == cudaSuccess) e = t.take(nn * 8, &keys);
-  if (e == cudaSuccess) e = t.take(nn * 4, &vals);
-  if (e == cudaSuccess) e = t.take(nn * 8, &xyc);
-  if (e == cudaSuccess) e = t.take(nn * 4, &lab);
-  if (e == cudaSuccess) e = t.take(nn * 4, &outc);
-  if (e != cudaSuccess) return cuda_fail(e);
+  AngCarve m(c, 0, true);
+  m.take(nn * 4); m.take(nn + 16); m.take(nn * 4 + 16); m.take(nn * 8); m.take(nn * 4); m.take(nn * 8);
+  m.take(nn * 4); m.take(nn * 4);
+  if (ang_reserve(c, m.need + ang_stage_bytes(nn)) != cudaSuccess) return HULL_ENOMEM;
+  AngCarve t(c, 0, false);
+  void* order = t.take(nn * 4);
+  void* keep = t.take(nn + 16);
+  void* pos = t.take(nn * 4 + 16);      // the count, then the positions
+  void* keys = t.take(nn * 8);
+  void* vals = t.take(nn * 4);
+  void* xyc = t.take(nn * 8);
+  void* lab = t.take(nn * 4);
+  void* outc = t.take(nn * 4);
+  cudaError_t e = cudaSuccess;
   int64_t m1 = 0, l = -1;
-  hull_status r = hull_stage_angular(c, d_xy, n, static_cast<int32_t*>(order), static_cast<uint8_t*>(keep), n, &m1,
-                                     &l, stream);
+  hull_status r = ang_stage(c, d_xy, n, static_cast<int32_t*>(order), static_cast<uint8_t*>(keep), n, &m1, &l,
+                            stream, t.off);
   if (r != HULL_OK) return r;
   u32* cnt = static_cast<u32*>(pos);
   u32* ppos = cnt + 4;

@@ -66,6 +66,54 @@ k8_infer(const float* __restrict__ feat, const __half* __restrict__ w16, const i
   }
 }
 
+// K6 + K8 in one launch behind a gate (the pipeline's path): the
+// quadrilateral's discard on PG_SAMPLE strided points i_k = floor(k n / G)
+// first; when it discards PG_DISCARD of them or more, there is too little
+// left for a larger polygon to discard and the quadrilateral stays (no
+// features, no inference: the call costs this one short launch).
+// Otherwise the features, the MLP and the polygon exactly as K6 and K8.
+constexpr int PG_SAMPLE = F_BLOCK;
+constexpr float PG_DISCARD = 0.95f;
+
+__global__ void __launch_bounds__(F_BLOCK)
+k6_propose(const int* __restrict__ xy, u32 n, const __half* __restrict__ w16, float* __restrict__ feat,
+           int* __restrict__ ext, int* __restrict__ ext_xy, Plan* plan) {
+  __shared__ FeatSmem sm;
+  __shared__ MlpSmem msm;
+  __shared__ u32 s_in;
+  if (plan->error & ERR_RANGE) return;
+  const int2* P = reinterpret_cast<const int2*>(xy);
+  const int k = plan->ncorner < 4 ? plan->ncorner : 4;
+  if (threadIdx.x == 0) s_in = 0;
+  __syncthreads();
+  const u32 G = n < (u32)PG_SAMPLE ? n : (u32)PG_SAMPLE;
+  if (threadIdx.x < G && k >= 3) {
+    const int2 p = P[(u32)(((unsigned long long)threadIdx.x * n) / G)];
+    bool in = true;
+    for (int j = 0; j < k && in; ++j) {
+      const int jn = j + 1 < k ? j + 1 : 0;
+      in = orient(plan->cx[j], plan->cy[j], plan->cx[jn], plan->cy[jn], p.x, p.y) > 0;
+    }
+    if (in) atomicAdd(&s_in, 1u);
+  }
+  __syncthreads();
+  if ((float)s_in >= PG_DISCARD * (float)G) return;
+  const u32 S = n < (u32)F_SAMPLE ? n : (u32)F_SAMPLE;
+  block_features<F_BLOCK>(P, n, S, sm, msm.x, ext_xy, ext);
+  if (threadIdx.x < D0) feat[threadIdx.x] = msm.x[threadIdx.x];
+  __syncthreads();
+  block_mlp(w16, msm);
+  if (threadIdx.x != 0) return;
+  int qx[4], qy[4], ox[kMaxCorners], oy[kMaxCorners];
+  for (int j = 0; j < k; ++j) { qx[j] = plan->cx[j]; qy[j] = plan->cy[j]; }
+  const int kk = learned_polygon(msm.z, ext_xy, qx, qy, k, ox, oy);
+  if (kk > 0) {
+    plan->ncorner = kk;
+    for (int j = 0; j < kk; ++j) { plan->cx[j] = ox[j]; plan->cy[j] = oy[j]; }
+    plan->learned_used = 1;
+  }
+}
+
 // K10: exact counts of points strictly inside the quadrilateral (slot 32)
 // and inside hull(quad corners + e_j) (slot j), for one instance.
 __global__ void __launch_bounds__(256)
@@ -197,6 +245,12 @@ int mlp_num_params() { return N_PARAMS; }
 
 cudaError_t launch_features(const int* xy, u32 n, float* feat, int* ext, int* ext_xy, cudaStream_t st) {
   k6_features<<<1, F_BLOCK, 0, st>>>(xy, n, feat, ext, ext_xy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propose(const int* xy, u32 n, const void* w16, float* feat, int* ext, int* ext_xy, Plan* plan,
+                           cudaStream_t st) {
+  k6_propose<<<1, F_BLOCK, 0, st>>>(xy, n, reinterpret_cast<const __half*>(w16), feat, ext, ext_xy, plan);
   return cudaGetLastError();
 }
 
