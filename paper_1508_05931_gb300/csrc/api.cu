@@ -1636,7 +1636,8 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
       cudaEvent_t t0, t1;
       cudaEventCreate(&t0);
       cudaEventCreate(&t1);
-      for (int rep = 0; rep < 2; ++rep) {
+      // One warm-up round, then the best of two timed rounds per block size.
+      for (int rep = 0; rep < 3; ++rep) {
         for (int blk : {256, 512}) {
           cudaMemsetAsync(w.ctl, 0, 64, st);
           cudaEventRecord(t0, st);
@@ -1645,7 +1646,7 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
           cudaEventSynchronize(t1);
           float ms = 0.f;
           cudaEventElapsedTime(&ms, t0, t1);
-          if (rep == 1 && ms < best) { best = ms; best_b = blk; }
+          if (rep >= 1 && ms < best) { best = ms; best_b = blk; }
         }
       }
       cudaEventDestroy(t0);

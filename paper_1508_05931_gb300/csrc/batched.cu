@@ -219,6 +219,7 @@ struct Smem {
   int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
   int4 edge[kMaxCorners];            // the filter polygon's edges (in_polygon)
   u32 nbig;                          // witness bins above BT_BIGBIN survivors
+  int bbox[4];                       // the skip box of step 1
   unsigned short big[BW_BINS];
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
   int4 pair[BT_MAX_CHUNKS / 2];      // bridge results of one merge level
@@ -346,24 +347,61 @@ k_batch(BatchArgs a) {
     // ---- 1. extremes (every BW_STRIDE-th point copied to the sort's second
     // key buffer, free until step 3, for the witnesses)
     // (BT_FITEMS points per thread and round, loaded before any is used).
+    // The skip box is the bounding box of the first round's points: a point
+    // strictly inside a box spanned by input points is no extreme, so only
+    // the points on or outside it go through the extreme updates.
     int2* smp = reinterpret_cast<int2*>(a.kb + sl);
     BestX b;
     bx_init(b);
-    for (u32 base = 0; base < n; base += FCH) {
-      int2 p[BT_FITEMS];
+    if (threadIdx.x == 0) {
+      S.bbox[0] = 0x7FFFFFFF; S.bbox[1] = (int)0x80000000; S.bbox[2] = 0x7FFFFFFF; S.bbox[3] = (int)0x80000000;
+    }
+    __syncthreads();
+    {
+      int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) {
-        const u32 j = base + r * BLOCK + threadIdx.x;
-        p[r] = j < n ? P[j] : make_int2(0, 0);
+        const u32 j = r * BLOCK + threadIdx.x;
+        if (j < n) {
+          const int2 q = P[j];
+          x0 = min(x0, q.x); x1 = max(x1, q.x); y0 = min(y0, q.y); y1 = max(y1, q.y);
+        }
+      }
+      #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x0 = min(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o)); x1 = max(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o));
+        y0 = min(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o)); y1 = max(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o));
+      }
+      if (lane == 0 && x0 <= x1) {
+        atomicMin(&S.bbox[0], x0); atomicMax(&S.bbox[1], x1); atomicMin(&S.bbox[2], y0); atomicMax(&S.bbox[3], y1);
+      }
+    }
+    __syncthreads();
+    const int kx0 = S.bbox[0], kx1 = S.bbox[1], ky0 = S.bbox[2], ky1 = S.bbox[3];
+    // The next round's points are loaded before this round's are used.
+    int2 p[BT_FITEMS];
+    #pragma unroll
+    for (int r = 0; r < BT_FITEMS; ++r) {
+      const u32 j = r * BLOCK + threadIdx.x;
+      p[r] = j < n ? P[j] : make_int2(0, 0);
+    }
+    for (u32 base = 0; base < n; base += FCH) {
+      int2 q[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + FCH + r * BLOCK + threadIdx.x;
+        q[r] = j < n ? P[j] : make_int2(0, 0);
       }
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) {
         const u32 j = base + r * BLOCK + threadIdx.x;
         if (j < n) {
-          bx_point(b, p[r].x, p[r].y, j);
+          if (!(p[r].x > kx0 && p[r].x < kx1 && p[r].y > ky0 && p[r].y < ky1)) bx_point(b, p[r].x, p[r].y, j);
           if (j % BW_STRIDE == 0) smp[j / BW_STRIDE] = p[r];
         }
       }
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) p[r] = q[r];
     }
     bx_warp(b);
     if (lane == 0)
@@ -447,6 +485,10 @@ k_batch(BatchArgs a) {
     // ---- 1b. witnesses of the sampled first-round survivors
     const int ux = bxp - ax, uy = byp - ay, d0x = ax - bxp, d0y = ay - byp;
     const u32 wshift = kbits > (u32)BW_BITS ? kbits - (u32)BW_BITS : 0u;
+    // The witness bin key >> wshift in 32-bit words: x's bits alone when the
+    // shift drops all of y's, else x's shifted up beside y's top bits.
+    const bool wx_only = wshift >= ybits;
+    const u32 wsx = wx_only ? wshift - ybits : ybits - wshift;
     for (int q = threadIdx.x; q < 2 * BW_BINS; q += BLOCK) S.wkey[q] = 0ull;
     __syncthreads();
     {
@@ -540,8 +582,9 @@ k_batch(BatchArgs a) {
         if (j0 + r * 32 < n) {
           const int dx = cur[r].x - bxp, dy = cur[r].y - byp;
           const long long c = cross2(d0x, d0y, dx, dy);
-          const u64 key = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
-          const int2 w = S.wtab[2 * (u32)(key >> wshift) + (c < 0 ? 1u : 0u)];
+          const u32 xr = (u32)(cur[r].x - x0);
+          const u32 wb = wx_only ? xr >> wsx : (xr << wsx) | ((u32)(cur[r].y - y0) >> wshift);
+          const int2 w = S.wtab[2 * wb + (c < 0 ? 1u : 0u)];
           const long long t = cross2(w.x, w.y, dx, dy);
           if (c == 0 || (c > 0 ? t > 0 : t < 0)) kmask |= 1u << r;
         }
