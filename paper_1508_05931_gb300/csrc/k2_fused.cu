@@ -24,7 +24,7 @@
 //              float pseudo-angle, sample index + 1).  The pseudo-angle only
 //              chooses among valid witnesses, so its rounding can cost a
 //              little discarding, never exactness.
-//   k2_fused   (two blocks per SM) first turns those maxima into every
+//   k2_fused   (one block per SM) first turns those maxima into every
 //              witness bin's exclusive prefix, a table of witness directions
 //              in shared memory (the direction of P_0 - P_l where no sample
 //              point precedes).  Every point then meets the witness test of
@@ -108,16 +108,31 @@ k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey) {
 }
 
 // ---- k2_fused
-// Two blocks per SM, each with its own copy of the witness table; every
-// thread streams the points with 128-bit loads, KF_V at a time.  A warp
+// One block per SM with its copy of the witness table; every thread streams
+// the points with 128-bit loads, KF_V at a time, the next round's loads
+// issued before the current round is tested (the registers this takes are
+// why the block has the SM to itself: 116 a thread).  A warp
 // stages the points that pass the witness test in its own slice of the
 // staging area (no block-wide barrier in the stream) and flushes the slice
 // by itself when the next batch would not fit, and at the end.
 constexpr int KF_BLOCK = 512;
 constexpr int KF_WARPS = KF_BLOCK / 32;
-constexpr int KF_V = 4;                                // int4 (two points) per thread per round
+#ifndef KF_V_CFG
+#define KF_V_CFG 4
+#endif
+#ifndef KF_PF_CFG
+#define KF_PF_CFG 1
+#endif
+#ifndef KF_MINB_CFG
+#define KF_MINB_CFG 1
+#endif
+constexpr int KF_V = KF_V_CFG;                         // int4 (two points) per thread per round
+constexpr bool KF_PF = KF_PF_CFG != 0;                 // load the next full round before computing this one
+// (Measured on the 20M square and disk: 65 / 64 us a launch against 70 / 69
+// for two blocks per SM at 64 registers without the early loads.)
 constexpr int KF_PTS = 2 * KF_V;                       // points per thread per round
-constexpr int KF_SLICE = 32 * KF_PTS;                  // staged points per warp: a whole round of survivors
+constexpr int KF_SLICE = 256;                          // staged points per warp: at least a whole round of survivors
+static_assert(KF_SLICE >= 32 * KF_PTS, "a round's survivors fit a slice");
 constexpr int KF_WPER = (kWitnessBins + KF_BLOCK - 1) / KF_BLOCK;   // witness bins per thread in the prologue
 struct KFEdge {
   int ex, ney;
@@ -313,19 +328,24 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
   // range inside the bounding box.
   const u32 nfull = n / 2;                 // units with both points present
   const u32 nunit = (n + 1) / 2;
-  auto round = [&](u32 j0, bool guarded) {
-    int px[KF_PTS], py[KF_PTS];
+  auto load = [&](u32 j0, bool guarded, int4* v) {
     #pragma unroll
     for (int r = 0; r < KF_V; ++r) {
       const u32 j = j0 + r * nt;
-      int4 v = make_int4(F.bx, F.by, F.bx, F.by);
+      v[r] = make_int4(F.bx, F.by, F.bx, F.by);
       if (!guarded && VEC) {
-        v = reinterpret_cast<const int4*>(xy)[j];
+        v[r] = reinterpret_cast<const int4*>(xy)[j];
       } else {
-        if (2 * j < n) { const int2 a = reinterpret_cast<const int2*>(xy)[2 * j]; v.x = a.x; v.y = a.y; }
-        if (2 * j + 1 < n) { const int2 b = reinterpret_cast<const int2*>(xy)[2 * j + 1]; v.z = b.x; v.w = b.y; }
+        if (2 * j < n) { const int2 a = reinterpret_cast<const int2*>(xy)[2 * j]; v[r].x = a.x; v[r].y = a.y; }
+        if (2 * j + 1 < n) { const int2 b = reinterpret_cast<const int2*>(xy)[2 * j + 1]; v[r].z = b.x; v[r].w = b.y; }
       }
-      px[2 * r] = v.x; py[2 * r] = v.y; px[2 * r + 1] = v.z; py[2 * r + 1] = v.w;
+    }
+  };
+  auto round = [&](u32 j0, bool guarded, const int4* v) {
+    int px[KF_PTS], py[KF_PTS];
+    #pragma unroll
+    for (int r = 0; r < KF_V; ++r) {
+      px[2 * r] = v[r].x; py[2 * r] = v[r].y; px[2 * r + 1] = v[r].z; py[2 * r + 1] = v[r].w;
     }
     bool pass[KF_PTS];
     u32 cnt = 0;
@@ -365,14 +385,42 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
   // (checked on the warp's last lane, so the branch is uniform).
   const u32 lane_last = j0 - lane + 31;
   u32 jl = lane_last;
-  for (; jl + (KF_V - 1) * nt < nfull; jl += KF_V * nt, j0 += KF_V * nt) round(j0, false);
-  for (; j0 - lane < nunit; j0 += KF_V * nt) round(j0, true);
+  if (KF_PF) {
+    // The next full round's loads go out before this round is computed.
+    int4 cur[KF_V];
+    bool have = jl + (KF_V - 1) * nt < nfull;
+    if (have) load(j0, false, cur);
+    while (have) {
+      const bool more = jl + KF_V * nt + (KF_V - 1) * nt < nfull;   // uniform over the warp
+      int4 nxt[KF_V];
+      if (more) load(j0 + KF_V * nt, false, nxt);
+      round(j0, false, cur);
+      jl += KF_V * nt;
+      j0 += KF_V * nt;
+      if (more) {
+        #pragma unroll
+        for (int r = 0; r < KF_V; ++r) cur[r] = nxt[r];
+      }
+      have = more;
+    }
+  } else {
+    for (; jl + (KF_V - 1) * nt < nfull; jl += KF_V * nt, j0 += KF_V * nt) {
+      int4 v[KF_V];
+      load(j0, false, v);
+      round(j0, false, v);
+    }
+  }
+  for (; j0 - lane < nunit; j0 += KF_V * nt) {
+    int4 v[KF_V];
+    load(j0, true, v);
+    round(j0, true, v);
+  }
   if (fill) warp_flush(S, skey, sidx, fill, plan, F, n, okey, oidx, btot);
   *nq_out = nq;
 }
 
 template <bool VEC, bool COUNT>
-__global__ void __launch_bounds__(KF_BLOCK, 2)
+__global__ void __launch_bounds__(KF_BLOCK, KF_MINB_CFG)
 k2_fused(const int* __restrict__ xy, Plan* plan, const u64* __restrict__ wkey, const int2* __restrict__ sample,
          u64* __restrict__ okey, u32* __restrict__ oidx, u32* __restrict__ btot, u32* __restrict__ bstart,
          uint2* __restrict__ groups, u32* __restrict__ fcur) {
