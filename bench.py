@@ -170,6 +170,17 @@ def oracle_timing_parallel(sets, cores):
                                % (cores, cores, "+".join(str(len(p)) for p in sets)))
 
 
+CLOCK_PAD_S = 0.5
+
+
+def busy_for(step, seconds):
+    """Untimed steps for about `seconds` of wall clock (each step ends with
+    a synchronisation)."""
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        step()
+
+
 class ClockSampler:
     def __init__(self, enabled, index):
         self.proc = None
@@ -185,7 +196,7 @@ class ClockSampler:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -217,7 +228,9 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm),
+                "window": "every 100 ms from %.1f s before to %.1f s after the timed steps, "
+                          "the GPU busy with untimed steps throughout" % (CLOCK_PAD_S, CLOCK_PAD_S)}
 
 
 def bench_batched(hull, torch, stream, plain_value, args):
@@ -584,7 +597,13 @@ def main():
 
     for _ in range(max(args.warmup, 3)):
         step()
+    # The clock samples (every 100 ms) bracket the timed steps: untimed steps
+    # keep the GPU busy for CLOCK_PAD_S before and after them, so that a
+    # timed region shorter than the sampling interval still has samples
+    # taken under the same load around it.
     sampler = ClockSampler(not args.no_clocks and rank == 0, local)
+    if sampler.proc is not None:
+        busy_for(step, CLOCK_PAD_S)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -592,6 +611,8 @@ def main():
         step()
     e1.record(stream)
     barrier()
+    if sampler.proc is not None:
+        busy_for(step, CLOCK_PAD_S)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     # Stage durations: the same steps again with the library's CUDA events
