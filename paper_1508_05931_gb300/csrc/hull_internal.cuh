@@ -42,8 +42,9 @@ constexpr int kBins = 1 << kBinBits;
 constexpr int kGroupCap = GBH_GROUP_CAP;     // survivors sorted in shared memory at once
 constexpr int kGroupTarget = kGroupCap / 2;  // window of the group rule (see k3_bucket.cu)
 constexpr int kSubBits = GBH_SUB_BITS;
-// The first round scatters into kCoarse coarse bins (the top kCoarseBits of
-// a bin); k3_split then spreads every coarse bin over its fine bins.
+// The filter's survivors are placed into kCoarse coarse bins (the top
+// kCoarseBits of a bin); k3_split then spreads every coarse bin over its
+// fine bins.
 constexpr int kCoarseBits = 8;
 constexpr int kCoarse = 1 << kCoarseBits;
 constexpr int kFinePerCoarse = kBins / kCoarse;
@@ -54,7 +55,7 @@ constexpr int kSubBins = 1 << kSubBits;
 constexpr u32 kSampleStride = 32;
 // Witness bins: the top kWitnessBits of the key (coarser than the sort's bins,
 // so that the fused filter's table of witness directions, 2 x 8 bytes per
-// bin, fits in shared memory beside its ring of input chunks).
+// bin, fits in shared memory beside its per-warp staging slices).
 constexpr int kWitnessBits = 12;
 constexpr int kWitnessBins = 1 << kWitnessBits;
 

@@ -1,16 +1,15 @@
-// K3 of the hull pipeline: bucket sort of the first round's survivors
-// (Section 2.1 step 4, Section 3.3), ascending by (key, index).  The
-// survivors arrive in index order, so this order is exactly the stable sort
-// by key that the paper's sort_by_key gives; the key is the lexicographic
-// (x, y) key of K2.
+// K3 of the hull pipeline: bucket sort of the filter's survivors (Section
+// 2.1 step 4, Section 3.3), ascending by (key, index): the order of a stable
+// sort by key of the survivors in index order, which is the order the
+// paper's sort_by_key gives; the key is the lexicographic (x, y) key.
 //
-// The pipeline's sort moves the survivors' pairs twice after K2 instead of
-// once per radix digit:
-//   1. while K2 counts the survivors it adds them to the bins' totals (a bin
-//      = the top kBinBits of the key) and reserves each block's run in
-//      every coarse bin (kFinePerCoarse consecutive bins); k_binstart turns
-//      the totals into bin starts and groups of consecutive bins, and K2's
-//      scatter pass writes every survivor into its coarse bin;
+// The pipeline's sort moves the survivors' pairs twice after the filter
+// instead of once per radix digit:
+//   1. the fused filter (k2_fused.cu) adds every survivor to its bin's total
+//      (a bin = the top kBinBits of the key) and writes its (key, index)
+//      pair in any order; its last block turns the totals into bin starts
+//      and groups of consecutive bins (bins.cuh), and k2_place moves every
+//      pair into its coarse bin (kFinePerCoarse consecutive bins);
 //   2. k3_split spreads every coarse bin over its bins (with the tiles'
 //      direction aggregates, from which k_bin_prefix scans every bin's
 //      second-round prefix), and k3_bucket takes one group at a time into
@@ -20,6 +19,8 @@
 //      the stage entry point and crowded groups, the order inside every
 //      sub-bin by rank counting (a bitonic network when a sub-bin is
 //      crowded).
+// The radix-pass path (hull_stage_bucket_sort, the array sort) bins an
+// index-ordered survivor array itself (launch_array_bins).
 //
 // Groups: bin b starts a new group when floor(start_b / T) differs from
 // its predecessor's (T = kGroupTarget), when it or its predecessor holds
@@ -1125,14 +1126,13 @@ k_bin_prefix(Plan* plan, K4Chunk* __restrict__ recs, const uint2* __restrict__ g
   }
 }
 
-// Bin starts and groups.  k_binstart (the pipeline, one block) takes the
-// bins' totals that the fused filter accumulated.  k_binscan (the stage
-// entry's array path) takes one histogram row per histogram block: row r,
-// bin b becomes the number of bin-b pairs of rows before r, bstart[b]
-// first receives the bin totals, and its last block continues as
-// k_binstart does.  Both write the bins' first positions and the groups
-// (first position, first bin), with a closing record (s, kBins) after the
-// last group (bins_to_groups, bins.cuh).
+// Bin starts and groups of the array path (the stage entry point; the
+// pipeline's come from the fused filter's last block).  k_binscan takes one
+// histogram row per histogram block: row r, bin b becomes the number of
+// bin-b pairs of rows before r, bstart[b] first receives the bin totals, and
+// its last block writes the bins' first positions and the groups (first
+// position, first bin), with a closing record (s, kBins) after the last
+// group (bins_to_groups, bins.cuh).
 constexpr int BS_BINS = 32;                 // bins per block (one per lane)
 constexpr int BS_RMAX = 10;                 // rows a warp loads at once
 
@@ -1181,16 +1181,6 @@ k_binscan(u32* __restrict__ rows, u32 nrows, Plan* plan, u32* __restrict__ bstar
   __threadfence();
   __shared__ BinScanSmem B;
   bins_to_groups<true>(bstart, plan, bstart, groups, fcur, B);
-}
-
-// The bin starts and groups of the pipeline's bucket sort from the bins'
-// totals, which k2_count accumulated (one block).
-__global__ void __launch_bounds__(BS_BLOCK)
-k_binstart(const u32* __restrict__ btot, Plan* plan, u32* __restrict__ bstart, uint2* __restrict__ groups,
-           u32* __restrict__ fcur) {
-  if (plan->error & ERR_RANGE) return;
-  __shared__ BinScanSmem B;
-  bins_to_groups<false>(btot, plan, bstart, groups, fcur, B);
 }
 
 // ---- the same sort over an arbitrary key array (the stage entry point):
@@ -1297,10 +1287,6 @@ cudaError_t bucket_occupancy(int* blocks) {
   return e;
 }
 
-cudaError_t launch_binstart(const u32* btot, Plan* plan, u32* bstart, uint2* groups, u32* fcur, cudaStream_t st) {
-  k_binstart<<<1, BS_BLOCK, 0, st>>>(btot, plan, bstart, groups, fcur);
-  return cudaGetLastError();
-}
 
 
 cudaError_t launch_bucket_sort(const u64* ak, const u32* av, u64* bk, u32* bv, Plan* plan,

@@ -59,7 +59,6 @@ size_t bucket_smem();
 size_t bucket_scratch_words(int blocks);
 cudaError_t bucket_configure();
 cudaError_t bucket_occupancy(int* blocks);
-cudaError_t launch_binstart(const u32* btot, Plan* plan, u32* bstart, uint2* groups, u32* fcur, cudaStream_t st);
 // Coarse bins (ak, av) spread over their bins into (bk, bv) through the
 // bins' cursors (fcur, seeded by the bin scan), with every tile's direction
 // aggregates per bin (tagg: 2 split_tile()-tile words per bin of the tile's
