@@ -128,6 +128,12 @@ constexpr int KF_WARPS = KF_BLOCK / 32;
 #endif
 constexpr int KF_V = KF_V_CFG;                         // int4 (two points) per thread per round
 constexpr bool KF_PF = KF_PF_CFG != 0;                 // load the next full round before computing this one
+#ifndef KF_CONTIG_CFG
+#define KF_CONTIG_CFG 1
+#endif
+constexpr bool KF_CONTIG = KF_CONTIG_CFG != 0;      // every warp reads one contiguous run per round
+// (Measured: 62.7 / 60.6 us per launch on the 20M square / disk against
+// 65.1 / 63.5 with slot r of all threads contiguous instead.)
 // (Measured on the 20M square and disk: 65 / 64 us a launch against 70 / 69
 // for two blocks per SM at 64 registers without the early loads.)
 constexpr int KF_PTS = 2 * KF_V;                       // points per thread per round
@@ -320,6 +326,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
   u64* skey = S.key[wid];
   u32* sidx = S.idx[wid];
   const u32 nt = gridDim.x * KF_BLOCK;
+  const u32 kstr = KF_CONTIG ? 32u : nt;   // units between a thread's slots of one round
   u32 fill = 0, nq = 0;
   // Unit j: points 2j and 2j + 1 (an int4 when VEC).  A round takes units
   // j0, j0 + nt, ..., j0 + (KF_V - 1) nt; the rounds whose units all lie
@@ -331,7 +338,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
   auto load = [&](u32 j0, bool guarded, int4* v) {
     #pragma unroll
     for (int r = 0; r < KF_V; ++r) {
-      const u32 j = j0 + r * nt;
+      const u32 j = j0 + r * kstr;
       v[r] = make_int4(F.bx, F.by, F.bx, F.by);
       if (!guarded && VEC) {
         v[r] = reinterpret_cast<const int4*>(xy)[j];
@@ -351,7 +358,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
     u32 cnt = 0;
     #pragma unroll
     for (int e = 0; e < KF_PTS; ++e) {
-      const bool in = !guarded || 2u * (j0 + (e >> 1) * nt) + (u32)(e & 1) < n;
+      const bool in = !guarded || 2u * (j0 + (e >> 1) * kstr) + (u32)(e & 1) < n;
       pass[e] = in && witness_pass<XONLY>(F, S.wt, px[e], py[e]);
       if (COUNT && in) nq += inside_polygon(S, px[e], py[e]) ? 0u : 1u;
       cnt += pass[e] ? 1u : 0u;
@@ -373,14 +380,16 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
       for (int e = 0; e < KF_PTS; ++e) {
         if (pass[e]) {
           skey[pos] = ((u64)(u32)(px[e] - F.x0) << F.ybits) | (u64)(u32)(py[e] - F.y0);
-          sidx[pos] = 2u * (j0 + (e >> 1) * nt) + (u32)(e & 1);
+          sidx[pos] = 2u * (j0 + (e >> 1) * kstr) + (u32)(e & 1);
           ++pos;
         }
       }
       fill += tot;
     }
   };
-  u32 j0 = blockIdx.x * KF_BLOCK + threadIdx.x;
+  // Unit of round 0, slot r: KF_CONTIG gives every warp one contiguous run
+  // of 32 KF_V units per round, else slot r of all threads is contiguous.
+  u32 j0 = KF_CONTIG ? (blockIdx.x * KF_BLOCK + (threadIdx.x & ~31u)) * KF_V + lane : blockIdx.x * KF_BLOCK + threadIdx.x;
   // Full rounds: every thread of the warp has all KF_V units below nfull
   // (checked on the warp's last lane, so the branch is uniform).
   const u32 lane_last = j0 - lane + 31;
@@ -388,10 +397,10 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
   if (KF_PF) {
     // The next full round's loads go out before this round is computed.
     int4 cur[KF_V];
-    bool have = jl + (KF_V - 1) * nt < nfull;
+    bool have = jl + (KF_V - 1) * kstr < nfull;
     if (have) load(j0, false, cur);
     while (have) {
-      const bool more = jl + KF_V * nt + (KF_V - 1) * nt < nfull;   // uniform over the warp
+      const bool more = jl + KF_V * nt + (KF_V - 1) * kstr < nfull;   // uniform over the warp
       int4 nxt[KF_V];
       if (more) load(j0 + KF_V * nt, false, nxt);
       round(j0, false, cur);
@@ -404,7 +413,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
       have = more;
     }
   } else {
-    for (; jl + (KF_V - 1) * nt < nfull; jl += KF_V * nt, j0 += KF_V * nt) {
+    for (; jl + (KF_V - 1) * kstr < nfull; jl += KF_V * nt, j0 += KF_V * nt) {
       int4 v[KF_V];
       load(j0, false, v);
       round(j0, false, v);
