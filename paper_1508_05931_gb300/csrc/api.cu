@@ -53,7 +53,8 @@ struct Workspace {
   u64* bpre = nullptr;         // per bin: exclusive second-round prefix (lower, upper)
   u32* fcur = nullptr;         // per bin: next position of the coarse-to-fine split
   u64* wkey = nullptr;         // per region and witness bin: the sample's best witness (follows bcnt)
-  int2* sample = nullptr;      // every kSampleStride-th point (K1 copies them out)
+  int2* sample = nullptr;      // every kSampleStride-th point (K1 or k0 copies them out)
+  PolyTab* poly = nullptr;     // the single-read front's sample polygon (follows wkey)
   unsigned long long* key_or = nullptr;
 };
 
@@ -208,6 +209,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   const size_t o_ctiles = take(((size_t)kCoarse + 1) * 4);
   const size_t o_bcnt = take(((size_t)kBins + kCoarse) * 4);
   const size_t o_wkey = take((size_t)2 * kWitnessBins * 8);   // right after bcnt: one memset clears both
+  const size_t o_poly = take(sizeof(PolyTab));                 // right after wkey: the same memset clears its head
   const size_t o_sample = take((cap / kSampleStride + 1) * 8);
   const size_t o_bagg = take(((size_t)kBins + kBinPrefixBlocks) * 16);
   const size_t o_bpre = take((size_t)kBins * 16);
@@ -257,6 +259,7 @@ hull_status ensure_ws(hull_ctx* c, size_t n) {
   w.bpre = reinterpret_cast<u64*>(b + o_bpre);
   w.fcur = reinterpret_cast<u32*>(b + o_fcur);
   w.wkey = reinterpret_cast<u64*>(b + o_wkey);
+  w.poly = reinterpret_cast<PolyTab*>(b + o_poly);
   w.sample = reinterpret_cast<int2*>(b + o_sample);
   return HULL_OK;
 }
@@ -300,7 +303,7 @@ hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
     f.radix_calls += p.sorted_in_b && p.ngroups ? 0 : 1;
     f.sort_passes += p.npasses;
     f.points += p.n;
-    f.survivors += p.s_quad;
+    f.survivors += p.s_raw ? p.s_raw : p.s_quad;
     f.second_round += (int64_t)p.r_lo + p.r_up;
     f.witness_survivors += p.s;
   }
@@ -325,14 +328,40 @@ void mark(hull_ctx* c, int k, cudaStream_t st) {
   if (c->prof_pending) cudaEventRecord(c->ev[k], st);
 }
 
+// Inputs from this size up (16-byte aligned, no statistics asked for) take
+// the single-read front on the bucket-sort path.
+constexpr u32 kSingleReadMin = 1u << 16;
+
 // K1 .. K4 of the pipeline on d_xy (n >= 1).  `bucket` selects the bucket
 // sort (K2 scatters the survivors into bins, one block sorts each group of
 // bins); otherwise K2 compacts them in index order for the radix passes.
-hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, bool bucket) {
+// `exact_lists`: the region lists must be exactly Figure 2's on every
+// first-round survivor (the two-read front; the single-read front's lists
+// are Figure 2's on a subset of them, which keeps every hull vertex).
+hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, bool bucket,
+                      bool exact_lists = false) {
   Workspace& w = c->ws;
+  const bool single = bucket && !exact_lists && !c->cfg.collect_stats && n >= kSingleReadMin &&
+                      (reinterpret_cast<uintptr_t>(d_xy) & 15u) == 0;
+  const size_t clear_bytes = (reinterpret_cast<char*>(w.wkey) - reinterpret_cast<char*>(w.bcnt)) +
+                             (size_t)2 * kWitnessBins * sizeof(u64) + kPolyClearBytes;
   mark(c, 0, st);
-  cudaError_t e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st,
-                            bucket ? w.sample : nullptr);
+  cudaError_t e = cudaSuccess;
+  if (single) {
+    // The single-read front: the sample polygon (from every 256th point),
+    // then one pass for the extremes that drops the points strictly inside
+    // that polygon, writes the rest (raw survivors, ~0.1-1 % of a uniform
+    // input) to the chain buffers, free until the group sort, and copies
+    // every 32nd point out as the witness sample.
+    e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
+    if (e == cudaSuccess) e = launch_poly(d_xy, n, w.poly, c->num_sms, st);
+    if (e == cudaSuccess)
+      e = launch_k1_poly(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, w.poly, &w.poly->raw_count, w.h_xy[0],
+                         reinterpret_cast<u32*>(w.h_idx[0]), w.sample, c->num_sms, st);
+  } else {
+    e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st,
+                  bucket ? w.sample : nullptr);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if (c->cfg.proposal == 1 && c->have_weights) {
     // Learned filter polygon: sampled features, MLP, exact hull of the
@@ -354,12 +383,16 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // Profile slots: 1 witnesses, 2 filter (the fused filter and its bin
     // scan), 3 scatter (coarse bins), 4 split (fine bins, their aggregates,
     // group prefixes), 5 sort (+ second round), 6..9 empty, 10 compaction.
-    e = cudaMemsetAsync(w.bcnt, 0, (reinterpret_cast<char*>(w.wkey) - reinterpret_cast<char*>(w.bcnt)) +
-                                       (size_t)2 * kWitnessBins * sizeof(u64), st);
+    if (!single) e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
     if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 2, st);
-    e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
+    if (single)   // the fused filter over the raw survivors, indices mapped back to the input's
+      e = launch_k2_fused(reinterpret_cast<const int*>(w.h_xy[0]), n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1],
+                          w.bcnt, w.bstart, w.groups, w.fcur, false, c->occ_kf * c->num_sms, st, &w.poly->raw_count,
+                          reinterpret_cast<const u32*>(w.h_idx[0]));
+    else
+      e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
                           w.fcur, c->cfg.collect_stats != 0, c->occ_kf * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 3, st);
@@ -558,6 +591,7 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
   c->num_sms = prop.multiProcessorCount;
   if (k2_configure() != cudaSuccess || k3_configure() != cudaSuccess || bucket_configure() != cudaSuccess ||
       fused_configure() != cudaSuccess || fused_occupancy(&c->occ_kf) != cudaSuccess ||
+      k1_poly_configure() != cudaSuccess ||
       bucket_occupancy(&c->occ_kb) != cudaSuccess ||
       split_occupancy(&c->occ_sp) != cudaSuccess ||
       k5_configure(&c->occ_k5) != cudaSuccess ||
@@ -1030,7 +1064,7 @@ hull_status hull_stage_regions(hull_ctx* c, const int32_t* d_xy, int64_t n, int3
   for (int attempt = 0; attempt < 2; ++attempt) {
     const bool bucket = attempt == 0;
     c->prof_pending = false;
-    r = run_front(c, d_xy, (u32)n, st, bucket);
+    r = run_front(c, d_xy, (u32)n, st, bucket, true);   // Figure 2's lists on every first-round survivor
     if (r != HULL_OK) return r;
     bool fallback = false;
     r = finish(c, st, bucket ? &fallback : nullptr);

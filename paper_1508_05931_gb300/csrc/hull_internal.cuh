@@ -10,6 +10,7 @@
 // kernel to the next, so the host never synchronises inside a call.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -96,6 +97,28 @@ struct ExtPartial {
   u32 idx[4];
 };
 
+// The single-read front's sample polygon (k0_poly.cu builds it, K1 filters
+// with it).  The first part is cleared before every call with the bins.
+constexpr int kPolyDirs = 32;          // directions of the sample's extreme points
+constexpr int kPolySlabs = 4096;       // most x slabs of the polygon's table
+struct PolyTab {
+  // cleared per call
+  u64 best[kPolyDirs];   // per direction: (ordered projection << 32 | ~sample index), maximum
+  u32 raw_count;         // K1's survivors: points on or outside the polygon
+  u32 done;              // last-block counter of k0
+  u32 pad[2];
+  // written by k0's last block
+  int ok;                // 1: at least 3 corners and an x range with an interior
+  int k;                 // corners (counter-clockwise from the lexicographic minimum)
+  int xl, xr;            // x of the leftmost and of the rightmost corner
+  u32 sh;                // slab s holds x in [xl + s 2^sh, xl + (s + 1) 2^sh)
+  u32 nslab;
+  u32 pad2[2];
+  int2 yb[kPolySlabs];    // per slab (ylo, yhi): a point of the slab with ylo < y < yhi is strictly
+                         // inside (ylo >= the lower chain, yhi <= the upper chain over the slab)
+};
+constexpr size_t kPolyClearBytes = offsetof(PolyTab, ok);
+
 struct Plan {
   // summary fields first: the host copies back everything before `ctr`
   u32 n;
@@ -105,6 +128,7 @@ struct Plan {
   u32 s;                // survivors of the first round (on the fused path: those left
                         // after the sampled-witness test, the sort's input)
   u32 s_quad;           // survivors of the first-round filter polygon alone
+  u32 s_raw;            // single-read front: points on or outside the sample polygon
   u32 r_lo, r_up;       // survivors of the second round per region
   u32 h;                // hull size
   u32 h_lo, h_up;       // chain lengths (including both endpoints)

@@ -132,6 +132,70 @@ __device__ void finish_plan(Plan* plan, const Best& b) {
   plan->ngroups = 0;
 }
 
+// Warp, block and grid reduction of the extremes; the last block to finish
+// reduces the per-block partials and builds the Plan.
+template <int BLOCK>
+__device__ void k1_reduce_finish(Best& b, u32 n, u32 spin_limit, Plan* plan, ExtPartial* __restrict__ partials,
+                                 const u32* raw_count = nullptr) {
+  warp_reduce(b);
+
+  constexpr int NW = BLOCK / 32;
+  __shared__ u64 sk[NW][4];
+  __shared__ u32 si[NW][4];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
+  __syncthreads();
+  if (wid == 0) {
+    best_init(b);
+    if (lane < NW) {
+      u64 k[4]; u32 i[4];
+      for (int q = 0; q < 4; ++q) { k[q] = sk[lane][q]; i[q] = si[lane][q]; }
+      merge_best(b, k, i);
+    }
+    warp_reduce(b);
+    if (lane == 0) {
+      ExtPartial* P = &partials[blockIdx.x];
+      for (int q = 0; q < 4; ++q) { P->key[q] = b.k[q]; P->idx[q] = b.i[q]; }
+      __threadfence();
+      u32 t = atomicAdd(&plan->k1_done, 1u);
+      am_last = (t == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!am_last) return;
+
+  // Last block: reduce all partials and build the Plan.
+  __threadfence();
+  best_init(b);
+  for (u32 p = threadIdx.x; p < gridDim.x; p += BLOCK) {
+    const volatile ExtPartial* P = &partials[p];
+    u64 k[4]; u32 i[4];
+    for (int q = 0; q < 4; ++q) { k[q] = P->key[q]; i[q] = P->idx[q]; }
+    merge_best(b, k, i);
+  }
+  warp_reduce(b);
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
+  __syncthreads();
+  // Zero the per-call counters and histograms for the later kernels.
+  for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&plan->hist[0][0])[q] = 0u;
+  for (int q = threadIdx.x; q < kNumCounters; q += BLOCK) plan->ctr[q] = 0u;
+  if (threadIdx.x == 0) {
+    best_init(b);
+    for (int w = 0; w < NW; ++w) merge_best(b, sk[w], si[w]);
+    plan->n = n;
+    plan->spin_limit = spin_limit;
+    finish_plan(plan, b);
+    plan->epoch += kEpochStride;
+    plan->s = 0; plan->s_quad = 0; plan->r_lo = 0; plan->r_up = 0; plan->h = 0; plan->h_lo = 0; plan->h_up = 0;
+    plan->s_raw = raw_count ? ld_volatile_u32(raw_count) : 0u;
+    plan->learned_used = 0;
+    plan->k1_done = 0;
+  }
+}
+
 template <int BLOCK, bool VEC>
 __global__ void __launch_bounds__(BLOCK)
 k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
@@ -231,62 +295,148 @@ k1_extremes(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan,
       if (sample && j % kSampleStride == 0) sample[j / kSampleStride] = v;
     }
   }
-  warp_reduce(b);
+  k1_reduce_finish<BLOCK>(b, n, spin_limit, plan, partials);
+}
 
-  constexpr int NW = BLOCK / 32;
-  __shared__ u64 sk[NW][4];
-  __shared__ u32 si[NW][4];
-  __shared__ bool am_last;
+// ---- K1 of the single-read front: the extremes and the sample polygon's
+// filter in one pass.  A point strictly inside the sample polygon (PolyTab,
+// k0_poly.cu: xl < x < xr and strictly inside its slab's y interval) is
+// strictly inside the hull, so it is neither an extreme nor a vertex: it is
+// dropped.  Every other point is a candidate for the
+// extremes and is staged in its warp's slice of shared memory; a warp
+// flushes its slice with one atomic reservation into (rxy, ridx), in no
+// particular order (the later kernels order the survivors themselves).
+// Each warp streams one contiguous run of 8 x 32 pairs per round (16-byte
+// aligned input); the rest, and an odd last point, go one pair per lane.
+constexpr int K1P_BLOCK = 512;
+constexpr int K1P_WARPS = K1P_BLOCK / 32;
+constexpr int K1P_SLICE = 256;                 // staged points per warp (a half round: 32 x 8)
+
+struct K1PSmem {
+  int2 sxy[K1P_WARPS][K1P_SLICE];
+  u32 sidx[K1P_WARPS][K1P_SLICE];
+  int2 yb[kPolySlabs];
+};
+
+__global__ void __launch_bounds__(K1P_BLOCK, 2)
+k1_poly(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* __restrict__ partials,
+        const PolyTab* __restrict__ T, u32* raw_count, int2* __restrict__ rxy, u32* __restrict__ ridx,
+        int2* __restrict__ sample) {
+  constexpr u32 kPairStride = kSampleStride / 2;   // pair j holds sample point j / kPairStride
+  extern __shared__ __align__(16) unsigned char k1p_smem[];
+  K1PSmem& S = *reinterpret_cast<K1PSmem*>(k1p_smem);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
-  __syncthreads();
-  if (wid == 0) {
-    best_init(b);
-    if (lane < NW) {
-      u64 k[4]; u32 i[4];
-      for (int q = 0; q < 4; ++q) { k[q] = sk[lane][q]; i[q] = si[lane][q]; }
-      merge_best(b, k, i);
-    }
-    warp_reduce(b);
-    if (lane == 0) {
-      ExtPartial* P = &partials[blockIdx.x];
-      for (int q = 0; q < 4; ++q) { P->key[q] = b.k[q]; P->idx[q] = b.i[q]; }
-      __threadfence();
-      u32 t = atomicAdd(&plan->k1_done, 1u);
-      am_last = (t == gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  if (!am_last) return;
+  const u32 lt = (1u << lane) - 1u;
+  const int ok = T->ok;
+  const int xl = T->xl, xr = T->xr;
+  const u32 sh = T->sh;
 
-  // Last block: reduce all partials and build the Plan.
-  __threadfence();
-  best_init(b);
-  for (u32 p = threadIdx.x; p < gridDim.x; p += BLOCK) {
-    const volatile ExtPartial* P = &partials[p];
-    u64 k[4]; u32 i[4];
-    for (int q = 0; q < 4; ++q) { k[q] = P->key[q]; i[q] = P->idx[q]; }
-    merge_best(b, k, i);
+  if (ok) {
+    const u32 nslab = T->nslab;
+    for (u32 q = threadIdx.x; q < nslab; q += K1P_BLOCK) S.yb[q] = T->yb[q];
   }
-  warp_reduce(b);
-  if (lane == 0)
-    for (int q = 0; q < 4; ++q) { sk[wid][q] = b.k[q]; si[wid][q] = b.i[q]; }
   __syncthreads();
-  // Zero the per-call counters and histograms for the later kernels.
-  for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&plan->hist[0][0])[q] = 0u;
-  for (int q = threadIdx.x; q < kNumCounters; q += BLOCK) plan->ctr[q] = 0u;
-  if (threadIdx.x == 0) {
-    best_init(b);
-    for (int w = 0; w < NW; ++w) merge_best(b, sk[w], si[w]);
-    plan->n = n;
-    plan->spin_limit = spin_limit;
-    finish_plan(plan, b);
-    plan->epoch += kEpochStride;
-    plan->s = 0; plan->s_quad = 0; plan->r_lo = 0; plan->r_up = 0; plan->h = 0; plan->h_lo = 0; plan->h_up = 0;
-    plan->learned_used = 0;
-    plan->k1_done = 0;
+  // Branch-free: every lane looks its slab up (slab 0 when x is outside the
+  // range, whose answer is then ignored), so a warp never splits here.
+  auto inside = [&](int x, int y) -> bool {
+    const bool inx = ok && x > xl && x < xr;
+    const int2 q = S.yb[inx ? (u32)(x - xl) >> sh : 0u];
+    return inx & (y > q.x) & (y < q.y);
+  };
+  Best b;
+  best_init(b);
+  int2* sxy = S.sxy[wid];
+  u32* sidx = S.sidx[wid];
+  u32 fill = 0;                                   // uniform over the warp
+  auto flush = [&]() {
+    __syncwarp();
+    u32 base = 0;
+    if (lane == 0) base = atomicAdd(raw_count, fill);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (u32 q = lane; q < fill; q += 32) {
+      if (base + q < n) { rxy[base + q] = sxy[q]; ridx[base + q] = sidx[q]; }
+      else flag_error(plan, ERR_INTERNAL);
+    }
+    __syncwarp();
+    fill = 0;
+  };
+  // Up to 8 points per lane (validity in `valid`): the survivors become
+  // extreme candidates and are staged (the whole warp calls it).
+  auto take = [&](const int* px, const int* py, const u32* pi, u32 valid, int cntpts) {
+    u32 keep = 0;
+    for (int e = 0; e < cntpts; ++e)
+      if (((valid >> e) & 1u) && !inside(px[e], py[e])) keep |= 1u << e;
+    if (!__any_sync(0xFFFFFFFFu, keep != 0)) return;
+    for (int e = 0; e < cntpts; ++e)
+      if ((keep >> e) & 1u) consider(b, px[e], py[e], pi[e]);
+    const u32 cnt = __popc(keep);
+    u32 inc = cnt;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (fill + tot > (u32)K1P_SLICE) flush();
+    u32 pos = fill + inc - cnt;
+    for (int e = 0; e < cntpts; ++e)
+      if ((keep >> e) & 1u) { sxy[pos] = make_int2(px[e], py[e]); sidx[pos] = pi[e]; ++pos; }
+    fill += tot;
+  };
+  const int4* p4 = reinterpret_cast<const int4*>(xy);
+  const u32 npair = n >> 1;
+  const u32 nthreads = gridDim.x * K1P_BLOCK;
+  const u32 gw = (blockIdx.x * K1P_BLOCK + threadIdx.x) >> 5, nwarps = nthreads >> 5;
+  u32 R = 0;
+  for (; R + 8u * nthreads <= npair; R += 8u * nthreads) {
+    const u32 u0 = R + gw * 256u + lane;
+    int4 v[8];
+    #pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = p4[u0 + 32u * u];
+    #pragma unroll
+    for (int u = 0; u < 8; ++u)          // the witness sample: every kSampleStride-th point
+      if ((u0 + 32u * u) % kPairStride == 0) sample[(u0 + 32u * u) / kPairStride] = make_int2(v[u].x, v[u].y);
+    #pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int px[8], py[8];
+      u32 pi[8];
+      #pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int4 w = v[4 * h + q];
+        const u32 j = u0 + 32u * (4 * h + q);
+        px[2 * q] = w.x; py[2 * q] = w.y; pi[2 * q] = 2u * j;
+        px[2 * q + 1] = w.z; py[2 * q + 1] = w.w; pi[2 * q + 1] = 2u * j + 1u;
+      }
+      take(px, py, pi, 0xFFu, 8);
+    }
   }
+  // The rest of the pairs, one per lane; then the odd last point.
+  for (u32 wb = R + gw * 32u; wb < npair; wb += nwarps * 32u) {
+    const u32 j = wb + lane;
+    int px[2] = {0, 0}, py[2] = {0, 0};
+    u32 pi[2] = {2u * j, 2u * j + 1u};
+    u32 valid = 0;
+    if (j < npair) {
+      const int4 w = p4[j];
+      px[0] = w.x; py[0] = w.y; px[1] = w.z; py[1] = w.w;
+      valid = 3u;
+      if (j % kPairStride == 0) sample[j / kPairStride] = make_int2(w.x, w.y);
+    }
+    take(px, py, pi, valid, 2);
+  }
+  if ((n & 1u) && gw == 0) {
+    int px[1] = {0}, py[1] = {0};
+    u32 pi[1] = {n - 1};
+    u32 valid = 0;
+    if (lane == 0) {
+      px[0] = xy[2 * (n - 1)]; py[0] = xy[2 * (n - 1) + 1]; valid = 1u;
+      if ((n - 1) % kSampleStride == 0) sample[(n - 1) / kSampleStride] = make_int2(px[0], py[0]);
+    }
+    take(px, py, pi, valid, 1);
+  }
+  if (fill) flush();
+  __threadfence();
+  k1_reduce_finish<K1P_BLOCK>(b, n, spin_limit, plan, partials, raw_count);
 }
 
 }  // namespace
@@ -316,6 +466,18 @@ cudaError_t launch_k1(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtParti
     k1_extremes<512, true><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials, sample);
   else
     k1_extremes<512, false><<<grid, 512, 0, st>>>(xy, n, spin_limit, plan, partials, sample);
+  return cudaGetLastError();
+}
+
+
+cudaError_t k1_poly_configure() {
+  return cudaFuncSetAttribute(k1_poly, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1PSmem));
+}
+
+cudaError_t launch_k1_poly(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials, const PolyTab* T,
+                           u32* raw_count, int2* rxy, u32* ridx, int2* sample, int num_sms, cudaStream_t st) {
+  k1_poly<<<num_sms * 2, K1P_BLOCK, sizeof(K1PSmem), st>>>(xy, n, spin_limit, plan, partials, T, raw_count, rxy, ridx,
+                                                           sample);
   return cudaGetLastError();
 }
 

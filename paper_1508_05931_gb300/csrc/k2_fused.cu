@@ -270,7 +270,7 @@ __device__ __forceinline__ bool inside_polygon(const KFSmem& S, int x, int y) {
 // to btot.
 __device__ __noinline__ void warp_flush(const KFSmem& S, u64* skey, u32* sidx, u32 fill, Plan* plan,
                                         const Front& F, u32 cap, u64* __restrict__ okey, u32* __restrict__ oidx,
-                                        u32* __restrict__ btot) {
+                                        u32* __restrict__ btot, const u32* __restrict__ imap) {
   const int lane = threadIdx.x & 31;
   constexpr int PER = KF_SLICE / 32;
   __syncwarp();
@@ -305,7 +305,7 @@ __device__ __noinline__ void warp_flush(const KFSmem& S, u64* skey, u32* sidx, u
       const u64 key = skey[j];
       if (pos < cap) {
         okey[pos] = key;
-        oidx[pos] = sidx[j];
+        oidx[pos] = imap ? __ldg(&imap[sidx[j]]) : sidx[j];
         atomicAdd(&btot[(u32)(key >> F.fshift)], 1u);
       } else {
         flag_error(plan, ERR_INTERNAL);
@@ -318,10 +318,9 @@ __device__ __noinline__ void warp_flush(const KFSmem& S, u64* skey, u32* sidx, u
 
 // The stream of points of one block (every thread of the block calls it).
 template <bool VEC, bool COUNT, bool XONLY>
-__device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* plan, const Front& F, KFSmem& S,
+__device__ __forceinline__ void stream_points(const int* __restrict__ xy, u32 n, Plan* plan, const Front& F, KFSmem& S,
                                               u64* __restrict__ okey, u32* __restrict__ oidx,
-                                              u32* __restrict__ btot, u32* nq_out) {
-  const u32 n = plan->n;
+                                              u32* __restrict__ btot, const u32* __restrict__ imap, u32* nq_out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   u64* skey = S.key[wid];
   u32* sidx = S.idx[wid];
@@ -372,7 +371,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
       }
       const u32 tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
       if (fill + tot > (u32)KF_SLICE) {            // uniform over the warp
-        warp_flush(S, skey, sidx, fill, plan, F, n, okey, oidx, btot);
+        warp_flush(S, skey, sidx, fill, plan, F, plan->n, okey, oidx, btot, imap);
         fill = 0;
       }
       u32 pos = fill + inc - cnt;
@@ -424,7 +423,7 @@ __device__ __forceinline__ void stream_points(const int* __restrict__ xy, Plan* 
     load(j0, true, v);
     round(j0, true, v);
   }
-  if (fill) warp_flush(S, skey, sidx, fill, plan, F, n, okey, oidx, btot);
+  if (fill) warp_flush(S, skey, sidx, fill, plan, F, plan->n, okey, oidx, btot, imap);
   *nq_out = nq;
 }
 
@@ -432,13 +431,16 @@ template <bool VEC, bool COUNT>
 __global__ void __launch_bounds__(KF_BLOCK, KF_MINB_CFG)
 k2_fused(const int* __restrict__ xy, Plan* plan, const u64* __restrict__ wkey, const int2* __restrict__ sample,
          u64* __restrict__ okey, u32* __restrict__ oidx, u32* __restrict__ btot, u32* __restrict__ bstart,
-         uint2* __restrict__ groups, u32* __restrict__ fcur) {
+         uint2* __restrict__ groups, u32* __restrict__ fcur, const u32* __restrict__ ncount,
+         const u32* __restrict__ imap) {
   extern __shared__ __align__(128) unsigned char kf_smem[];
   KFSmem& S = *reinterpret_cast<KFSmem*>(kf_smem);
   __shared__ u64 s_wm[KF_WARPS];
   __shared__ bool s_last;
   if (plan->error & ERR_RANGE) return;
-  const u32 n = plan->n;
+  // The points: the input (n = plan->n), or the single-read front's raw
+  // survivors (n = *ncount, their input indices in imap).
+  const u32 n = ncount ? *ncount : plan->n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const Front F = make_front(plan);
   if (threadIdx.x < kMaxCorners) {
@@ -454,9 +456,9 @@ k2_fused(const int* __restrict__ xy, Plan* plan, const u64* __restrict__ wkey, c
   build_witness_table(wkey, sample, F, S, s_wm);   // its barriers also publish the polygon
   u32 nq = 0;
   if (F.s2 == 0 && F.ysh >= F.ybits)      // uniform: the witness bin depends on x alone
-    stream_points<VEC, COUNT, true>(xy, plan, F, S, okey, oidx, btot, &nq);
+    stream_points<VEC, COUNT, true>(xy, n, plan, F, S, okey, oidx, btot, imap, &nq);
   else
-    stream_points<VEC, COUNT, false>(xy, plan, F, S, okey, oidx, btot, &nq);
+    stream_points<VEC, COUNT, false>(xy, n, plan, F, S, okey, oidx, btot, imap, &nq);
   if (COUNT) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nq += __shfl_xor_sync(0xFFFFFFFFu, nq, o);
@@ -575,16 +577,16 @@ cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int
 
 cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
                             u32* oidx, u32* btot, u32* bstart, uint2* groups, u32* fcur, bool count, int grid,
-                            cudaStream_t st) {
+                            cudaStream_t st, const u32* ncount, const u32* imap) {
   const bool vec = (reinterpret_cast<uintptr_t>(xy) & 15u) == 0;
   const u32 rounds = ((n + 1) / 2 + KF_BLOCK * KF_V - 1) / (KF_BLOCK * KF_V);   // blocks with a full round
   if ((u32)grid > rounds) grid = (int)(rounds < 1 ? 1 : rounds);
   if (vec) {
-    if (count) k2_fused<true, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
-    else k2_fused<true, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
+    if (count) k2_fused<true, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur, ncount, imap);
+    else k2_fused<true, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur, ncount, imap);
   } else {
-    if (count) k2_fused<false, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
-    else k2_fused<false, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur);
+    if (count) k2_fused<false, true><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur, ncount, imap);
+    else k2_fused<false, false><<<grid, KF_BLOCK, KF_SMEM, st>>>(xy, plan, wkey, sample, okey, oidx, btot, bstart, groups, fcur, ncount, imap);
   }
   return cudaGetLastError();
 }

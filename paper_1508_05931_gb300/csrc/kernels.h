@@ -50,9 +50,19 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 cudaError_t fused_configure();
 cudaError_t fused_occupancy(int* blocks);
 cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st);
+// With ncount and imap the points are the single-read front's raw survivors:
+// *ncount of them at xy (n bounds the count), their input indices in imap.
 cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
                             u32* oidx, u32* btot, u32* bstart, uint2* groups, u32* fcur, bool count, int grid,
-                            cudaStream_t st);
+                            cudaStream_t st, const u32* ncount = nullptr, const u32* imap = nullptr);
+// The single-read front: the sample polygon (k0_poly.cu), then K1 with that
+// polygon as its filter, writing the points on or outside it to (rxy, ridx)
+// (count in T->raw_count, which must be zero before k0) and the witness
+// sample (every kSampleStride-th point) to `sample`.
+cudaError_t launch_poly(const int* xy, u32 n, PolyTab* T, int num_sms, cudaStream_t st);
+cudaError_t k1_poly_configure();
+cudaError_t launch_k1_poly(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials, const PolyTab* T,
+                           u32* raw_count, int2* rxy, u32* ridx, int2* sample, int num_sms, cudaStream_t st);
 cudaError_t launch_place(const u64* ak, const u32* ai, u32 n, Plan* plan, const u32* bstart, u32* ccur, u64* ok,
                          u32* oi, int num_sms, cudaStream_t st);
 size_t bucket_smem();

@@ -14,10 +14,23 @@ torch = pytest.importorskip("torch")
 
 
 @pytest.fixture(scope="module")
-def ctx(hull_lib):
+def sctx(hull_lib):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     c = hull_lib.Context(0, collect_stats=True)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module", params=["stats", "single_read"])
+def ctx(hull_lib, request):
+    """The hull tests run twice: with statistics (the two-read front, which
+    counts every first-round survivor) and without (inputs of 65,536 points
+    or more then take the single-read front)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = hull_lib.Context(0, collect_stats=request.param == "stats")
+    c.with_stats = request.param == "stats"
     yield c
     c.close()
 
@@ -71,7 +84,8 @@ def test_ragged_sizes(ctx, n, gen):
     assert gpu_hull(ctx, pts).tolist() == oracle.hull(pts).tolist()
 
 
-def test_small_square_config(ctx):
+def test_small_square_config(sctx):
+    ctx = sctx
     pts = W.small_square()
     h = gpu_hull(ctx, pts)
     assert h.tolist() == oracle.hull(pts).tolist()
@@ -96,12 +110,12 @@ def _front_points(gen, n):
 
 @pytest.mark.parametrize("n", [4097, 65537, 300_001, 1_000_003])
 @pytest.mark.parametrize("gen", ["square", "disk", "ring", "gauss", "clusters", "ties", "strip"])
-def test_fused_second_round_lists(ctx, n, gen):
+def test_fused_second_round_lists(sctx, n, gen):
     """The second round fused into the sort (Figure 2 run on every sorted
     or binned group from its prefix) keeps exactly the oracle's points, in
     the oracle's order, in both regions."""
     pts = _front_points(gen, n)
-    lo, up, _ = ctx.stage_regions(dev(pts))
+    lo, up, _ = sctx.stage_regions(dev(pts))
     ref = oracle.gscan_stages(pts)
     assert np.array_equal(lo.cpu().numpy(), ref["lower"])
     assert np.array_equal(up.cpu().numpy(), ref["upper"])
@@ -161,10 +175,12 @@ def test_full_size_configs(ctx, name):
     out = torch.empty(len(pts), dtype=torch.int32, device="cuda")
     h = ctx.compute(t, out=out).cpu().numpy()
     assert h.tolist() == oracle.hull(pts).tolist()
-    assert ctx.last_stats()["sort_fallback"] == 0
+    if ctx.with_stats:
+        assert ctx.last_stats()["sort_fallback"] == 0
 
 
-def test_sort_fallback_only_when_needed(ctx):
+def test_sort_fallback_only_when_needed(sctx):
+    ctx = sctx
     """The bucket sort takes the paper-shaped inputs itself; identical or
     heavily duplicated points (a bin it cannot split) are rerun on the radix
     passes, with the same hull."""
@@ -350,3 +366,36 @@ def test_forced_wait_timeouts_recover(hull_lib):
     assert hull_lib.HULL_ETIMEOUT in codes, codes
     with hull_lib.Context(0) as c:
         assert c.compute(t).cpu().numpy().tolist() == ref.tolist()
+
+
+def test_single_read_front_edge_cases(ctx):
+    """Inputs of 65,536 points or more (16-byte aligned, no statistics) take
+    the single-read front: the sample polygon drops the points strictly
+    inside it during the extremes pass.  Its degenerate and boundary cases,
+    each against the oracle: identical, collinear and two-column inputs (no
+    polygon with an interior: nothing is dropped), a filled lattice whose
+    sample polygon has lattice points on its edges, a thin sliver, a tight
+    cluster with a sparse halo, heavy duplicates, odd sizes just above the
+    threshold, and an unaligned view (the two-read front)."""
+    rng = np.random.default_rng(61)
+    t = np.arange(-100_000, 100_000)
+    sets = {
+        "identical": np.full((200_000, 2), -123, np.int32),
+        "collinear": np.stack([t * 3, t * 7], axis=1).astype(np.int32),
+        "two_columns": np.stack([rng.integers(0, 2, 150_000), rng.integers(-1 << 29, 1 << 29, 150_000)],
+                                axis=1).astype(np.int32),
+        "lattice": W.filled_grid(400, 400, -200, -150),
+        "sliver": np.stack([t, t // 1000 + rng.integers(0, 3, t.size)], axis=1).astype(np.int32),
+        "cluster_halo": np.concatenate([rng.integers(-50, 51, size=(300_000, 2)),
+                                        rng.integers(-(1 << 28), 1 << 28, size=(3_000, 2))]).astype(np.int32),
+        "duplicates": rng.integers(-1000, 1000, size=(60, 2)).astype(np.int32)[rng.integers(0, 60, size=400_000)],
+        "odd_above": W.uniform_disk(65_537, 2.0 ** 29, 62),
+        "odd_large": W.uniform_square(1_000_001, 1 << 29, 63),
+    }
+    for name, pts in sets.items():
+        assert gpu_hull(ctx, pts).tolist() == oracle.hull(pts).tolist(), name
+    pts = W.uniform_disk(300_001, 2.0 ** 29, 64)
+    buf = torch.as_tensor(np.concatenate([np.zeros((1, 2), np.int32), pts])).cuda()
+    view = buf[1:]
+    assert view.data_ptr() % 16 == 8
+    assert ctx.compute(view).cpu().numpy().tolist() == oracle.hull(pts).tolist()
