@@ -34,9 +34,9 @@ namespace gbh {
 
 namespace {
 
-constexpr int K0_BLOCK = 256;
+constexpr int K0_BLOCK = 1024;
 constexpr int K0_WARPS = K0_BLOCK / 32;
-constexpr int K0_ITEMS = 8;          // sampled points a lane loads at once
+constexpr int K0_ITEMS = 1;          // sampled points a lane loads at once
 constexpr u32 kPolyStride = 1024;    // one point in every kPolyStride is sampled
 constexpr int kPolyMargin = 2048;    // units the slab bounds move outwards (> the float error)
 
@@ -222,7 +222,7 @@ k0_poly(const int2* __restrict__ P, u32 n, PolyTab* __restrict__ T) {
 cudaError_t launch_poly(const int* xy, u32 n, PolyTab* T, int num_sms, cudaStream_t st) {
   const u32 ns = (n + kPolyStride - 1) / kPolyStride;
   u32 grid = (ns + K0_BLOCK * K0_ITEMS - 1) / (K0_BLOCK * K0_ITEMS);
-  const u32 cap = (u32)num_sms * 8;
+  const u32 cap = (u32)num_sms * 2;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   k0_poly<<<grid, K0_BLOCK, 0, st>>>(reinterpret_cast<const int2*>(xy), n, T);
