@@ -299,6 +299,17 @@ STAGE_KERNELS = {
     "regions": ("k4_compact", lambda n, s, r: 24.0 * r, "pairs"),
     "final": ("k5_final", lambda n, s, r: 12.0 * r, "pairs"),
 }
+# The single-read front (inputs of 65,536 points or more, aligned, no
+# statistics): the sample polygon (every 1024th point read) and the extremes
+# pass that filters with it form the "extremes" stage (8 B per point read,
+# the every-32nd witness sample and the q raw survivors, 12 B each, written);
+# the fused filter then reads those q raw survivors and writes the s pairs.
+POLY_STRIDE = 1024
+SINGLE_STAGE_KERNELS = dict(STAGE_KERNELS)
+SINGLE_STAGE_KERNELS["extremes"] = ("k1_poly (+ k0_poly)",
+                                    lambda n, s, r, q: 8.0 * n + 8.0 * n / POLY_STRIDE + 8.0 * n / SAMPLE_STRIDE
+                                    + 12.0 * q, "points")
+SINGLE_STAGE_KERNELS["filter"] = ("k2_fused", lambda n, s, r, q: 12.0 * q + 12.0 * s, "raw")
 DOMINANT_CANDIDATES = ("extremes", "witness", "filter", "scatter", "split", "sort")
 
 
@@ -308,22 +319,27 @@ def roofline_of(prof, hbm, peak_src):
     roofline entry of the dominant one (the longest stage)."""
     calls = max(prof["calls"], 1)
     n, s, r = prof["points"] / calls, prof["witness_survivors"] / calls, prof["second_round"] / calls
+    single = prof.get("single_read_calls", 0) == prof["calls"] and prof["calls"] > 0
+    q = prof.get("raw_survivors", 0) / calls
+    table = SINGLE_STAGE_KERNELS if single else STAGE_KERNELS
     stage_ms = {k: v / calls for k, v in prof["ms"].items() if not k.startswith("-")}
     if prof["radix_calls"]:
         return {"bound": "hbm", "kernel": "mixed (calls rerun on the radix passes)", "achieved": None,
                 "peak": hbm, "unit": "GB/s", "frac": None, "peak_source": peak_src, "traffic": None,
                 "stage_ms_per_hull": stage_ms}
     kernels = {}
-    for name, (kern, nbytes, unit) in STAGE_KERNELS.items():
+    for name, (kern, nbytes, unit) in table.items():
         ms = stage_ms.get(name, 0.0)
-        b = nbytes(n, s, r)
-        kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b, "units": n if unit == "points" else s,
+        b = nbytes(n, s, r, q) if single and name in ("extremes", "filter") else nbytes(n, s, r)
+        units = n if unit == "points" else (q if unit == "raw" else s)
+        kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b, "units": units,
                          "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else None}
     dom = max(DOMINANT_CANDIDATES, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     achieved = d["gbs"] or 0.0
     return {"bound": "hbm", "kernel": d["kernel"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": peak_src,
+            "front": "single-read" if single else "two-read", "raw_survivors_per_hull": q if single else None,
             "traffic": kernel_traffic(d["kernel"].split()[0], d["units"]),
             "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
             "stage_ms_per_hull": stage_ms, "stages": kernels,

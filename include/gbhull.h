@@ -220,8 +220,10 @@ typedef struct {
   int64_t survivors;             /* first-round survivors, summed (counted only by a context
                                     with collect_stats; 0 otherwise) */
   int64_t second_round;          /* second-round survivors, summed */
-  double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): extremes,
-                                    witnesses (the sample's best witness per bin), filter (the
+  double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): extremes
+                                    (on the single-read front: the sample polygon and the
+                                    extremes pass that filters with it), witnesses (the
+                                    sample's best witness per bin), filter (the
                                     fused filter: witness test, filter polygon, compaction, bin
                                     scan), scatter (survivors into coarse bins), split (coarse bins
                                     into bins, their aggregates, the groups' prefixes), sort (groups
@@ -230,6 +232,10 @@ typedef struct {
                                     regions, final */
   int64_t witness_survivors;     /* survivors of the fused filter (the bucket sort's input),
                                     summed; the first-round survivors on the radix passes */
+  int64_t raw_survivors;         /* single-read front: points on or outside the sample polygon
+                                    (the fused filter's input), summed; 0 for calls on the
+                                    two-read front */
+  int64_t single_read_calls;     /* calls that took the single-read front */
 } hull_profile;
 
 hull_status hull_set_profiling(hull_ctx *ctx, int enable);

@@ -303,7 +303,9 @@ hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
     f.radix_calls += p.sorted_in_b && p.ngroups ? 0 : 1;
     f.sort_passes += p.npasses;
     f.points += p.n;
-    f.survivors += p.s_raw ? p.s_raw : p.s_quad;
+    f.survivors += p.s_quad;
+    f.raw_survivors += p.s_raw;
+    f.single_read_calls += p.s_raw ? 1 : 0;
     f.second_round += (int64_t)p.r_lo + p.r_up;
     f.witness_survivors += p.s;
   }

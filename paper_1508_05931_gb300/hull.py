@@ -51,7 +51,8 @@ RADIX_STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8
 class hull_profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("radix_calls", ctypes.c_int64), ("sort_passes", ctypes.c_int64),
                 ("points", ctypes.c_int64), ("survivors", ctypes.c_int64), ("second_round", ctypes.c_int64),
-                ("ms", ctypes.c_double * NUM_STAGES), ("witness_survivors", ctypes.c_int64)]
+                ("ms", ctypes.c_double * NUM_STAGES), ("witness_survivors", ctypes.c_int64),
+                ("raw_survivors", ctypes.c_int64), ("single_read_calls", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -296,6 +297,7 @@ class Context:
         return {"calls": p.calls, "radix_calls": p.radix_calls, "sort_passes": p.sort_passes, "points": p.points,
                 "survivors": p.survivors, "second_round": p.second_round,
                 "witness_survivors": p.witness_survivors,
+                "raw_survivors": p.raw_survivors, "single_read_calls": p.single_read_calls,
                 "ms": {names[k]: p.ms[k] for k in range(NUM_STAGES)}}
 
     # ------------------------------------------------------------ learned
