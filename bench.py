@@ -34,10 +34,12 @@ WORKLOAD = "paper-scale: 2 hulls per step, 20M uniform-square + 20M uniform-disk
 # The paper's best 20M-point times for the same two workloads (Table 3 square
 # 446.4 ms, Table 5 circle 418.1 ms, GT 640): 40M points / 864.5 ms.
 PAPER_MPTS = 40.0 / 0.8645
-# Kernels per hull_compute with the bucket sort: extremes, filter count, bin
-# starts, scatter into coarse bins, split into bins, group aggregates and
-# prefixes, sort (+ second round), compaction, finalisation.  A call rerun on the radix passes adds extremes,
-# filter count + write, 8 radix passes, region scan + compact, finalisation.
+# Kernels per hull_compute with the bucket sort, two-read front: extremes,
+# witnesses, fused filter (+ bin scan), placement into coarse bins, split
+# into bins, bin prefixes, sort (+ second round), compaction, finalisation;
+# the single-read front adds the sample polygon before its extremes pass.  A
+# call rerun on the radix passes adds extremes, filter count + write, 8
+# radix passes, region scan + compact, finalisation.
 LAUNCHES_PER_HULL = 9
 LAUNCHES_PER_RADIX_RERUN = 1 + 2 + 8 + 2 + 1
 
@@ -699,7 +701,8 @@ def main():
                        "survivors_per_hull": sum(first_round) / len(first_round),
                        "witness_survivors_per_hull": prof["witness_survivors"] / calls,
                        "second_round_per_hull": prof["second_round"] / calls},
-            "gpu_launches": prof["calls"] * LAUNCHES_PER_HULL + prof["radix_calls"] * LAUNCHES_PER_RADIX_RERUN,
+            "gpu_launches": prof["calls"] * LAUNCHES_PER_HULL + prof.get("single_read_calls", 0)
+            + prof["radix_calls"] * LAUNCHES_PER_RADIX_RERUN,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * pts_step,
                     "d2h_bytes_per_step": 4 * sum(h_counts), "api": "hull_compute_host_multi"},
             "roofline": roofline}
