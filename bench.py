@@ -258,9 +258,23 @@ def bench_batched(hull, torch, stream, plain_value, args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k
     v = len(pts) / (ms / 1e3) / 1e6
+    sizes = np.diff(offs)
+    tuned = {}
+    try:    # the autotuner's choices (its cache: block sizes, segmented-path boundary)
+        path = os.environ.get("GBHULL_AUTOTUNE_CACHE") or os.path.expanduser("~/.cache/gbhull_autotune.json")
+        with open(path) as f:
+            tuned = {k.split("|")[-1]: v_ for k, v_ in json.load(f).items()}
+    except (OSError, ValueError):
+        pass
+    seg_min = tuned.get("batched_seg_min")
+    paths = None
+    if seg_min:
+        seg = sizes >= seg_min
+        paths = {"segmented": {"instances": int(seg.sum()), "points": int(sizes[seg].sum())},
+                 "one_block": {"instances": int((~seg).sum()), "points": int(sizes[~seg].sum())}}
     return {"value": v, "unit": "Mpoints/s", "ms_per_batch": ms, "instances": len(offs) - 1,
             "points": int(len(pts)), "hull_vertices": int(oo[-1].item()), "steps": k,
-            "vs_plain": v / plain_value,
+            "vs_plain": v / plain_value, "autotuned": tuned, "paths": paths,
             "config": "4096 instances, sizes log-uniform [1e3,1e6] capped at 2.5e8 points total, "
                       "families square/disk/gaussian(2^26), seed 4; one call per step, autotuned"}
 
@@ -350,7 +364,11 @@ def roofline_of(prof, hbm, peak_src):
             / (sum(stage_ms.values()) / 1e3) / 1e9 if sum(stage_ms.values()) > 0 else None}
 
 
-def _time_hulls(ctx, t, out, stream, torch, k):
+def _time_hulls(ctx, sctx, t, out, stream, torch, k):
+    """ms per hull of `ctx` (no statistics: the path a caller runs), whether
+    its learned polygon was used, and the first-round discard fraction of
+    its filter polygon from one call of `sctx` (same proposal, statistics
+    on: the two-read front, which counts the filter's survivors)."""
     for _ in range(2):
         ctx.compute_raw(t, out, stream)
     torch.cuda.synchronize()
@@ -360,8 +378,10 @@ def _time_hulls(ctx, t, out, stream, torch, k):
         ctx.compute_raw(t, out, stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    st = ctx.last_stats()
-    return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], st["learned_used"]
+    used = ctx.last_stats()["learned_used"]
+    sctx.compute_raw(t, out, stream)
+    st = sctx.last_stats()
+    return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], used
 
 
 def bench_configs(hull, torch, stream, hbm, peak_src, k=20):
@@ -415,7 +435,7 @@ def bench_reverse_round(hull, torch, stream, dev_sets, dev_outs):
     for rev in (False, True):
         with hull.Context(torch.cuda.current_device(), collect_stats=True, reverse_round=rev) as c:
             for name, t, o in cases:
-                ms, _, _ = _time_hulls(c, t, o, stream, torch, 5)
+                ms, _, _ = _time_hulls(c, c, t, o, stream, torch, 5)
                 st = c.last_stats()
                 res.setdefault(name, {})["on" if rev else "off"] = {"ms": ms, "r": st["r_lower"] + st["r_upper"],
                                                                    "h": st["h"]}
@@ -492,12 +512,14 @@ def bench_learned(hull, torch, stream, args):
     from paper_1508_05931_gb300 import learned as L
     dev = torch.cuda.current_device()
     res = {"families": {}}
-    with hull.Context(dev, proposal=1, collect_stats=True) as lc, hull.Context(dev, collect_stats=True) as pc:
+    with hull.Context(dev, proposal=1, collect_stats=True) as lcs, hull.Context(dev, collect_stats=True) as pcs, \
+            hull.Context(dev, proposal=1) as lc, hull.Context(dev) as pc:
         t0 = time.perf_counter()
-        X, Y = L.make_dataset(lc, 192, seed0=1000, lo=1e5, hi=4e5)
+        X, Y = L.make_dataset(lcs, 192, seed0=1000, lo=1e5, hi=4e5)
         t1 = time.perf_counter()
-        losses = L.train(lc, X, Y, steps=3000, lr=2e-3, batch=64)
+        losses = L.train(lcs, X, Y, steps=3000, lr=2e-3, batch=64)
         torch.cuda.synchronize()
+        lc.mlp_set_params(lcs.mlp_get_params())
         res["training"] = {"instances": 192, "steps": 3000, "data_s": t1 - t0,
                            "train_s": time.perf_counter() - t1,
                            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-50:]))}
@@ -507,8 +529,8 @@ def bench_learned(hull, torch, stream, args):
         tot_p = tot_l = 0.0
         for fam in range(3):
             pts = torch.as_tensor(L.instance(fam, 20_000_000, 5 + fam)).cuda()
-            mp, dp_, _ = _time_hulls(pc, pts, out, stream, torch, k)
-            ml, dl, used = _time_hulls(lc, pts, out, stream, torch, k)
+            mp, dp_, _ = _time_hulls(pc, pcs, pts, out, stream, torch, k)
+            ml, dl, used = _time_hulls(lc, lcs, pts, out, stream, torch, k)
             tot_p += mp; tot_l += ml
             res["families"][names[fam]] = {"plain_ms": mp, "learned_ms": ml, "speedup": mp / ml,
                                            "plain_discard": dp_, "learned_discard": dl, "learned_used": used,

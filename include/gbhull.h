@@ -81,7 +81,8 @@ typedef struct {
   int64_t h;          /* hull vertices */
   int32_t ext[4];     /* indices of P_minx, P_maxx, P_miny, P_maxy (Section 2.1 step 1) */
   int32_t ncorner;    /* distinct corners of the filter polygon */
-  int32_t learned_used; /* 1 when the learned polygon replaced the quadrilateral */
+  int32_t learned_used; /* 1 when the learned polygon replaced the quadrilateral (set on
+                           every single-hull call, also without collect_stats) */
   int32_t sort_fallback; /* 1 when the bucket sort met a bin it cannot sort in shared memory
                             and the call was rerun on the radix passes */
   int64_t s_witness;  /* first-round survivors left by the fused filter's test against the

@@ -83,10 +83,25 @@ struct BatchWs {
   long long* h_off = nullptr;
   long long* h_slot0 = nullptr;
   int* h_order = nullptr;
+  int* h_tfirst = nullptr;
   u32* h_ctl = nullptr;
+  // segmented path of the largest instances: tile extremes and counts,
+  // per-instance records, first tile of every instance
+  size_t cap_tiles = 0, cap_seg = 0;
+  void* seg = nullptr;
+  void* text = nullptr;
+  u32* tcnt = nullptr;
+  void* rec = nullptr;
+  int* tfirst = nullptr;
 };
 
 constexpr int64_t kSmallInstance = 16384;   // size bucket boundary
+// Instances of this many points or more take the segmented path (flat
+// streaming passes over all their tiles) unless the autotuner chose another
+// boundary among kSegCandidates (the last one: no instance takes it).
+constexpr int64_t kSegDefault = 65536;
+constexpr int64_t kSegOff = (int64_t)1 << 40;
+constexpr int64_t kSegCandidates[4] = {32768, 131072, 262144, kSegOff};
 
 }  // namespace
 
@@ -123,7 +138,9 @@ struct hull_ctx {
   cudaStream_t aux = nullptr;
   cudaEvent_t bev[2] = {nullptr, nullptr};
   int occ_b256 = 1, occ_b512 = 1;
-  int tuned_block[2] = {0, 0};  // per bucket (small, large); 0 = not tuned yet
+  int occ_sx = 1, occ_sf = 1;   // segmented streaming passes
+  int tuned_block[3] = {0, 0, 0};  // per bucket (small, large, segmented); 0 = not tuned yet
+  int64_t tuned_seg = 0;        // smallest instance of the segmented path; 0 = not tuned yet
   // learned proposal
   bool have_weights = false;
   float* W = nullptr;           // FP32 master parameters
@@ -315,8 +332,8 @@ hull_status read_summary(hull_ctx* c, const Plan& p, bool* fallback) {
     c->last.h = p.h;
     for (int j = 0; j < 4; ++j) c->last.ext[j] = p.ext_idx[j];
     c->last.ncorner = p.ncorner;
-    c->last.learned_used = p.learned_used;
   }
+  c->last.learned_used = p.learned_used;
   if (p.error & ERR_RANGE) return HULL_ERANGE;
   if (p.error & ERR_TIMEOUT) return HULL_ETIMEOUT;
   if (p.error & ERR_INTERNAL) return HULL_EINTERNAL;
@@ -368,8 +385,10 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   if (c->cfg.proposal == 1 && c->have_weights) {
     // Learned filter polygon: sampled features, MLP, exact hull of the
     // chosen extremes and the quadrilateral's corners, unless the gate finds
-    // the quadrilateral already discarding nearly all of a sample.
-    e = launch_propose(d_xy, n, c->W16, c->feat, c->ext, c->ext_xy, c->plan, st);
+    // nearly all of the input discarded already (by the single-read front's
+    // sample polygon, else by the quadrilateral on a sample).
+    e = launch_propose(d_xy, n, c->W16, c->feat, c->ext, c->ext_xy, c->plan, single ? &w.poly->raw_count : nullptr,
+                       st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   mark(c, 1, st);
@@ -500,13 +519,21 @@ void autotune_load(hull_ctx* c) {
   while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, r);
   std::fclose(f);
   const std::string dk = device_key(c);
-  const char* names[2] = {"batched_small", "batched_large"};
-  for (int b = 0; b < 2; ++b) {
+  const char* names[3] = {"batched_small", "batched_large", "batched_seg_block"};
+  for (int b = 0; b < 3; ++b) {
     const std::string key = "\"" + dk + "|" + names[b] + "\":";
     const size_t pos = txt.find(key);
     if (pos == std::string::npos) continue;
     const int v = std::atoi(txt.c_str() + pos + key.size());
     if (v == 256 || v == 512) c->tuned_block[b] = v;
+  }
+  const std::string key = "\"" + dk + "|batched_seg_min\":";
+  const size_t pos = txt.find(key);
+  if (pos != std::string::npos) {
+    const long long v = std::atoll(txt.c_str() + pos + key.size());
+    for (int64_t cand : kSegCandidates)
+      if (v == cand) c->tuned_seg = v;
+    if (v == kSegDefault) c->tuned_seg = v;
   }
 }
 
@@ -517,9 +544,12 @@ void autotune_save(const hull_ctx* c) {
   FILE* f = std::fopen(path.c_str(), "w");
   if (!f) return;
   const std::string dk = device_key(c);
-  std::fprintf(f, "{\"%s|batched_small\": %d, \"%s|batched_large\": %d}\n", dk.c_str(),
-               c->tuned_block[0] ? c->tuned_block[0] : 256, dk.c_str(),
-               c->tuned_block[1] ? c->tuned_block[1] : 256);
+  std::fprintf(f,
+               "{\"%s|batched_small\": %d, \"%s|batched_large\": %d, \"%s|batched_seg_block\": %d, "
+               "\"%s|batched_seg_min\": %lld}\n",
+               dk.c_str(), c->tuned_block[0] ? c->tuned_block[0] : 256, dk.c_str(),
+               c->tuned_block[1] ? c->tuned_block[1] : 256, dk.c_str(), c->tuned_block[2] ? c->tuned_block[2] : 256,
+               dk.c_str(), (long long)(c->tuned_seg ? c->tuned_seg : kSegDefault));
   std::fclose(f);
 }
 
@@ -607,6 +637,7 @@ hull_status hull_create(hull_ctx** out, int device, const hull_config* cfg) {
     return HULL_ECUDA;
   }
   if (batch_configure(&c->occ_b256, &c->occ_b512) != cudaSuccess ||
+      seg_configure(&c->occ_sx, &c->occ_sf) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->bev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->bev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -673,6 +704,8 @@ void hull_destroy(hull_ctx* c) {
   if (c->bw.h_slot0) cudaFreeHost(c->bw.h_slot0);
   if (c->bw.h_order) cudaFreeHost(c->bw.h_order);
   if (c->bw.h_ctl) cudaFreeHost(c->bw.h_ctl);
+  if (c->bw.h_tfirst) cudaFreeHost(c->bw.h_tfirst);
+  if (c->bw.seg) cudaFree(c->bw.seg);
   for (int k = 0; k < 2; ++k)
     if (c->bev[k]) cudaEventDestroy(c->bev[k]);
   if (c->aux) cudaStreamDestroy(c->aux);
@@ -1569,10 +1602,13 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
     if (w.h_slot0) cudaFreeHost(w.h_slot0);
     if (w.h_order) cudaFreeHost(w.h_order);
     if (w.h_ctl) cudaFreeHost(w.h_ctl);
-    w.h_off = nullptr; w.h_slot0 = nullptr; w.h_order = nullptr; w.h_ctl = nullptr; w.h_cap = 0;
+    if (w.h_tfirst) cudaFreeHost(w.h_tfirst);
+    w.h_off = nullptr; w.h_slot0 = nullptr; w.h_order = nullptr; w.h_ctl = nullptr; w.h_tfirst = nullptr;
+    w.h_cap = 0;
     const size_t hc = (size_t)B + 1024;
     if (cudaMallocHost(&w.h_off, hc * 8) != cudaSuccess || cudaMallocHost(&w.h_slot0, hc * 8) != cudaSuccess ||
-        cudaMallocHost(&w.h_order, hc * 4) != cudaSuccess || cudaMallocHost(&w.h_ctl, 64) != cudaSuccess) {
+        cudaMallocHost(&w.h_order, hc * 4) != cudaSuccess || cudaMallocHost(&w.h_ctl, 64) != cudaSuccess ||
+        cudaMallocHost(&w.h_tfirst, hc * 4) != cudaSuccess) {
       cudaGetLastError();
       return HULL_ENOMEM;
     }
@@ -1584,14 +1620,14 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
   if (w.h_off[0] != 0) return HULL_EINVAL;
   const int64_t maxi = (int64_t)batch_max_instance();
   const int64_t pad = batch_pad();
-  int64_t slots = 0;
-  std::vector<int> small, large;
+  const int64_t tile = seg_tile();
+  int64_t slots = 0, tiles_all = 0;
   for (int i = 0; i < B; ++i) {
     const int64_t ni = w.h_off[i + 1] - w.h_off[i];
     if (ni < 0 || ni > maxi || w.h_off[i + 1] > (int64_t)kMaxN) return HULL_EINVAL;
     w.h_slot0[i] = slots;
     slots += ni + pad;
-    (ni <= kSmallInstance ? small : large).push_back(i);
+    tiles_all += (ni + tile - 1) / tile;
   }
   if (B == 0) {
     long long zero = 0;
@@ -1600,14 +1636,6 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
     return e == cudaSuccess ? HULL_OK : cuda_fail(e);
   }
   if (!d_xy) return HULL_EINVAL;
-  auto by_size = [&](int a, int b) {
-    const int64_t na = w.h_off[a + 1] - w.h_off[a], nb = w.h_off[b + 1] - w.h_off[b];
-    return na != nb ? na > nb : a < b;
-  };
-  std::sort(large.begin(), large.end(), by_size);
-  std::sort(small.begin(), small.end(), by_size);
-  std::copy(large.begin(), large.end(), w.h_order);
-  std::copy(small.begin(), small.end(), w.h_order + large.size());
   // Workspace.
   if ((size_t)slots > w.cap_slots || (size_t)B > w.cap_b) {
     cudaDeviceSynchronize();
@@ -1641,10 +1669,65 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
     w.cap_slots = cs;
     w.cap_b = (size_t)B;
   }
+  // Segmented path: room for every instance's tiles and record, whatever
+  // the boundary.
+  if ((size_t)tiles_all > w.cap_tiles || (size_t)B > w.cap_seg) {
+    cudaDeviceSynchronize();
+    if (w.seg) cudaFree(w.seg);
+    w.seg = nullptr; w.cap_tiles = 0; w.cap_seg = 0;
+    const size_t ct = (size_t)tiles_all + 1024, cb = (size_t)B + 1024;
+    const size_t b_text = align_up(ct * seg_text_bytes(), 256), b_tcnt = align_up(ct * 4, 256);
+    const size_t b_rec = align_up(cb * seg_rec_bytes(), 256), b_tf = align_up((cb + 1) * 4, 256);
+    if (cudaMalloc(&w.seg, b_text + b_tcnt + b_rec + b_tf) != cudaSuccess) {
+      cudaGetLastError();
+      w.seg = nullptr;
+      return HULL_ENOMEM;
+    }
+    char* b = static_cast<char*>(w.seg);
+    w.text = b; b += b_text;
+    w.tcnt = reinterpret_cast<u32*>(b); b += b_tcnt;
+    w.rec = b; b += b_rec;
+    w.tfirst = reinterpret_cast<int*>(b);
+    w.cap_tiles = (size_t)tiles_all;
+    w.cap_seg = (size_t)B;
+  }
   e = cudaMemcpyAsync(w.slot0, w.h_slot0, (size_t)B * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(w.order, w.h_order, (size_t)B * 4, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, 64, st);
   if (e != cudaSuccess) return cuda_fail(e);
+
+  // Size buckets: the segmented path (seg_min points or more), large
+  // (more than kSmallInstance) and small instances; `order` lists them in
+  // that order, each bucket largest first.  The host arrays are rewritten
+  // only after the stream has finished the copies of the previous layout.
+  int nh = 0, nl = 0, ns = 0, ntiles = 0;
+  auto layout = [&](int64_t seg_min) -> cudaError_t {
+    cudaError_t r = cudaStreamSynchronize(st);
+    if (r != cudaSuccess) return r;
+    std::vector<int> huge, large, small;
+    for (int i = 0; i < B; ++i) {
+      const int64_t ni = w.h_off[i + 1] - w.h_off[i];
+      (ni >= seg_min ? huge : ni <= kSmallInstance ? small : large).push_back(i);
+    }
+    auto by_size = [&](int a, int b) {
+      const int64_t na = w.h_off[a + 1] - w.h_off[a], nb = w.h_off[b + 1] - w.h_off[b];
+      return na != nb ? na > nb : a < b;
+    };
+    std::sort(huge.begin(), huge.end(), by_size);
+    std::sort(large.begin(), large.end(), by_size);
+    std::sort(small.begin(), small.end(), by_size);
+    std::copy(huge.begin(), huge.end(), w.h_order);
+    std::copy(large.begin(), large.end(), w.h_order + huge.size());
+    std::copy(small.begin(), small.end(), w.h_order + huge.size() + large.size());
+    nh = (int)huge.size(); nl = (int)large.size(); ns = (int)small.size();
+    ntiles = 0;
+    for (int h = 0; h < nh; ++h) {
+      w.h_tfirst[h] = ntiles;
+      ntiles += (int)((w.h_off[huge[h] + 1] - w.h_off[huge[h]] + tile - 1) / tile);
+    }
+    w.h_tfirst[nh] = ntiles;
+    r = cudaMemcpyAsync(w.order, w.h_order, (size_t)B * 4, cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(w.tfirst, w.h_tfirst, ((size_t)nh + 1) * 4, cudaMemcpyHostToDevice, st);
+    return r;
+  };
 
   BatchLaunch L{};
   L.xy = d_xy; L.offsets = reinterpret_cast<const long long*>(d_offsets);
@@ -1652,57 +1735,114 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
   L.lxy = w.lxy; L.lidx = w.lidx; L.uxy = w.uxy; L.uidx = w.uidx;
   L.out_tmp = w.out_tmp; L.hcount = w.hcount; L.error = w.ctl + 2;
   L.w16 = (c->cfg.proposal == 1 && c->have_weights) ? c->W16 : nullptr;
-  const int nl = (int)large.size(), ns = (int)small.size();
-  auto run_bucket = [&](int bucket, int block, cudaStream_t s2, u32* queue) -> cudaError_t {
+  L.tfirst = w.tfirst; L.text = w.text; L.tcnt = w.tcnt; L.rec = w.rec;
+  // bucket 0 small, 1 large (one block per instance), 2 segmented (the
+  // streaming passes over all tiles, plans, the second pass, the gathers)
+  // front (bucket 2 only): 1 the streaming passes and the plans, 0 the
+  // gathers and back halves, -1 both.
+  auto run_bucket = [&](int bucket, int block, cudaStream_t s2, int front = -1) -> cudaError_t {
     BatchLaunch M = L;
-    M.order = w.order + (bucket == 1 ? 0 : nl);
-    M.nb = bucket == 1 ? nl : ns;
-    M.queue = queue;
     const int occ = block == 512 ? c->occ_b512 : c->occ_b256;
+    if (bucket == 2) {
+      M.order = w.order;
+      M.nb = nh;
+      const int grid = std::max(1, std::min(nh, occ * c->num_sms));
+      cudaError_t r = cudaSuccess;
+      if (front != 0) {
+        r = launch_seg_ext(M, ntiles, c->occ_sx * c->num_sms, s2);
+        M.mode = 1; M.queue = w.ctl + 3;
+        if (r == cudaSuccess) r = launch_batch(block, grid, M, s2);
+        if (r == cudaSuccess) r = launch_seg_filter(M, ntiles, c->occ_sf * c->num_sms, s2);
+      }
+      M.mode = 2; M.queue = w.ctl + 4;
+      if (r == cudaSuccess && front != 1) r = launch_batch(block, grid, M, s2);
+      return r;
+    }
+    M.order = w.order + nh + (bucket == 1 ? 0 : nl);
+    M.nb = bucket == 1 ? nl : ns;
+    M.queue = w.ctl + bucket;
     const int grid = std::max(1, std::min(M.nb, occ * c->num_sms));
     return launch_batch(block, grid, M, s2);
   };
-  // Autotuning: time each block size per bucket once, on this batch.
-  if (c->cfg.autotune && (c->tuned_block[0] == 0 || c->tuned_block[1] == 0)) {
+  auto block_of = [&](int bucket) { return c->tuned_block[bucket] ? c->tuned_block[bucket] : 256; };
+  // The whole batch.  The segmented bucket's streaming passes run alone on
+  // the caller's stream (the one-block kernels are persistent: started
+  // beside them they would hold the SMs until their queues drain); then its
+  // gathers and back halves run there while the large and then the small
+  // instances run on the context's second stream, so that the back halves
+  // (latency) share the SMs with those instances' streaming.
+  auto run_all = [&]() -> cudaError_t {
+    cudaError_t r = cudaMemsetAsync(w.ctl, 0, 64, st);
+    if (r == cudaSuccess && nh > 0) r = run_bucket(2, block_of(2), st, 1);
+    if (r == cudaSuccess) r = cudaEventRecord(c->bev[0], st);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(c->aux, c->bev[0], 0);
+    if (r == cudaSuccess && nh > 0) r = run_bucket(2, block_of(2), st, 0);
+    if (r == cudaSuccess && nl > 0) r = run_bucket(1, block_of(1), c->aux);
+    if (r == cudaSuccess && ns > 0) r = run_bucket(0, block_of(0), c->aux);
+    if (r == cudaSuccess) r = cudaEventRecord(c->bev[1], c->aux);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(st, c->bev[1], 0);
+    return r;
+  };
+  auto timed = [&](auto&& fn) -> float {
+    // One warm-up round, then the best of two timed rounds.
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(t0, st);
+      fn();
+      cudaEventRecord(t1, st);
+      cudaEventSynchronize(t1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (rep >= 1 && ms < best) best = ms;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return best;
+  };
+  // Autotuning on the first batch: the block size per bucket (each bucket
+  // timed alone at the default boundary), then the segmented path's
+  // boundary (the whole batch timed at each candidate).
+  if (c->cfg.autotune && (c->tuned_block[0] == 0 || c->tuned_block[1] == 0 || c->tuned_block[2] == 0 ||
+                          c->tuned_seg == 0)) {
     autotune_load(c);
-    for (int bucket = 0; bucket < 2; ++bucket) {
-      if (c->tuned_block[bucket] != 0 || (bucket == 0 ? ns : nl) == 0) continue;
+    e = layout(c->tuned_seg ? c->tuned_seg : kSegDefault);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int bucket = 0; bucket < 3; ++bucket) {
+      if (c->tuned_block[bucket] != 0) continue;
+      if ((bucket == 0 ? ns : bucket == 1 ? nl : nh) == 0) continue;
       float best = 1e30f;
       int best_b = 256;
-      cudaEvent_t t0, t1;
-      cudaEventCreate(&t0);
-      cudaEventCreate(&t1);
-      // One warm-up round, then the best of two timed rounds per block size.
-      for (int rep = 0; rep < 3; ++rep) {
-        for (int blk : {256, 512}) {
+      for (int blk : {256, 512}) {
+        const float ms = timed([&] {
           cudaMemsetAsync(w.ctl, 0, 64, st);
-          cudaEventRecord(t0, st);
-          run_bucket(bucket, blk, st, w.ctl);
-          cudaEventRecord(t1, st);
-          cudaEventSynchronize(t1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, t0, t1);
-          if (rep >= 1 && ms < best) { best = ms; best_b = blk; }
-        }
+          run_bucket(bucket, blk, st);
+        });
+        if (ms < best) { best = ms; best_b = blk; }
       }
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
       c->tuned_block[bucket] = best_b;
     }
+    if (c->tuned_seg == 0) {
+      float best = 1e30f;
+      int64_t best_t = kSegDefault;
+      const int64_t cands[5] = {kSegDefault, kSegCandidates[0], kSegCandidates[1], kSegCandidates[2],
+                                kSegCandidates[3]};
+      for (int64_t tc : cands) {
+        e = layout(tc);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const float ms = timed(run_all);
+        if (ms < best) { best = ms; best_t = tc; }
+      }
+      c->tuned_seg = best_t;
+    }
     autotune_save(c);
-    e = cudaMemsetAsync(w.ctl, 0, 64, st);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  const int blk_small = c->tuned_block[0] ? c->tuned_block[0] : 256;
-  const int blk_large = c->tuned_block[1] ? c->tuned_block[1] : 256;
-  // Large instances on the caller's stream, small ones concurrently on the
-  // context's second stream.
-  e = cudaEventRecord(c->bev[0], st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->bev[0], 0);
-  if (e == cudaSuccess && nl > 0) e = run_bucket(1, blk_large, st, w.ctl);
-  if (e == cudaSuccess && ns > 0) e = run_bucket(0, blk_small, c->aux, w.ctl + 1);
-  if (e == cudaSuccess) e = cudaEventRecord(c->bev[1], c->aux);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->bev[1], 0);
+  e = layout(c->tuned_seg ? c->tuned_seg : kSegDefault);
+  if (e == cudaSuccess) e = run_all();
   if (e == cudaSuccess)
     e = launch_batch_output(w.hcount, w.slot0, w.out_tmp, B, reinterpret_cast<long long*>(d_out_offsets),
                             d_out, (long long)cap, w.ctl + 2, c->num_sms * 4, st);

@@ -45,6 +45,7 @@ constexpr int BW_BITS = 9;          // witness bins per instance: the top BW_BIT
 constexpr int BW_BINS = 1 << BW_BITS;
 constexpr u32 BW_STRIDE = 32;       // one sampled point in every BW_STRIDE
 constexpr u32 BT_BIGBIN = 1024;     // larger witness bins are sorted by the whole block
+constexpr u32 BL_MIN_N = 262144;    // smallest instance the learned proposal runs on
 
 struct BestX {
   u64 k[4];
@@ -193,6 +194,7 @@ struct Smem {
   u32 wcnt[W][2];
   IPlan plan;
   int inst;
+  int hq;                            // position of the instance in `order`
   u64 rk[W][4];
   u32 ri[W][4];
   union {
@@ -224,6 +226,48 @@ struct Smem {
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
   int4 pair[BT_MAX_CHUNKS / 2];      // bridge results of one merge level
 };
+
+// The learned proposal's fixed cost (features of a 4,096-point sample and
+// the MLP) is paid only by instances of at least BL_MIN_N points whose
+// quadrilateral leaves more than 5 % of a strided 512-point sample (the gate
+// of the single-hull proposal).  Past the gate: features of a sample of the
+// instance, the MLP, the exact hull of the quadrilateral and the 8 chosen
+// extremes.  Kept out of line: it runs once per instance and its locals
+// would crowd the streaming loops' registers.
+template <int BLOCK>
+__device__ __noinline__ void learned_step(Smem<BLOCK>& S, const int2* P, u32 n, const __half* w16) {
+  if (threadIdx.x == 0) S.nbig = 0;
+  __syncthreads();
+  if (S.plan.ncorner >= 3) {
+    constexpr u32 G = 512;
+    for (u32 t = threadIdx.x; t < G; t += BLOCK) {
+      const int2 q = P[(u32)(((unsigned long long)t * n) / G)];
+      bool in = true;
+      for (int j = 0; j < S.plan.ncorner && in; ++j) {
+        const int jn = j + 1 < S.plan.ncorner ? j + 1 : 0;
+        in = orient(S.corner_x[j], S.corner_y[j], S.corner_x[jn], S.corner_y[jn], q.x, q.y) > 0;
+      }
+      if (in) atomicAdd(&S.nbig, 1u);
+    }
+  }
+  __syncthreads();
+  if (S.nbig >= 487u) return;   // 487 / 512 > 95 %
+  const u32 smp = n < 4096u ? n : 4096u;
+  learned::block_features<BLOCK>(P, n, smp, S.feat, S.mlp.x, S.ext_xy, S.ext_idx);
+  learned::block_mlp(w16, S.mlp);
+  if (threadIdx.x == 0) {
+    int qx[4], qy[4], ox[kMaxCorners], oy[kMaxCorners];
+    const int nq = S.plan.ncorner < 4 ? S.plan.ncorner : 4;
+    for (int j = 0; j < nq; ++j) { qx[j] = S.corner_x[j]; qy[j] = S.corner_y[j]; }
+    const int k2 = learned::learned_polygon(S.mlp.z, S.ext_xy, qx, qy, nq, ox, oy);
+    if (k2 > 0) {
+      S.plan.ncorner = k2;
+      S.plan.learned = 1;
+      for (int j = 0; j < k2; ++j) { S.corner_x[j] = ox[j]; S.corner_y[j] = oy[j]; }
+    }
+  }
+  __syncthreads();
+}
 
 // Chain over m points (xy, idx) in lexicographic order.  Short chains are
 // built in shared memory and left there; longer ones are built in chunks
@@ -300,6 +344,20 @@ __device__ int build_chain(Smem<BLOCK>& S, const int2* xy, const int* idx, int m
   return S.chunk_cnt[0];
 }
 
+// The segmented path (instances of batch_seg_min() points or more): the
+// extremes of every tile run, and every instance's record for the second
+// streaming pass and the gather.
+constexpr u32 SEG_TILE = 16384;     // points per tile (a multiple of 512 x BT_FITEMS)
+struct SegTileExt {
+  u64 k[4];
+  u32 i[4];
+};
+struct SegRec {
+  IPlan plan;
+  int4 edge[kMaxCorners];
+  int2 wtab[2 * BW_BINS];
+};
+
 struct BatchArgs {
   const int* xy;
   const long long* offsets;   // [B + 1]
@@ -313,9 +371,14 @@ struct BatchArgs {
   u32* hcount;                // [B]
   u32* error;
   const __half* w16;          // learned proposal weights (null: quadrilateral)
+  int mode;                   // 0 whole pipeline, 1 plan + witnesses from tiles, 2 gather + back half
+  const int* tfirst;          // [nb + 1] first tile of every instance of `order` (modes 1, 2)
+  SegTileExt* text;
+  u32* tcnt;
+  SegRec* rec;                // [nb], indexed like `order`
 };
 
-template <int BLOCK>
+template <int BLOCK, int MODE>
 __global__ void __launch_bounds__(BLOCK)
 k_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char bt_smem[];
@@ -330,6 +393,7 @@ k_batch(BatchArgs a) {
     if (threadIdx.x == 0) {
       const u32 q = atomicAdd(a.queue, 1u);
       S.inst = q < (u32)a.nb ? a.order[q] : -1;
+      S.hq = (int)q;
     }
     __syncthreads();
     const int inst = S.inst;
@@ -351,8 +415,20 @@ k_batch(BatchArgs a) {
     // strictly inside a box spanned by input points is no extreme, so only
     // the points on or outside it go through the extreme updates.
     int2* smp = reinterpret_cast<int2*>(a.kb + sl);
+    if (MODE == 2) {
+      // The plan, polygon and witnesses were built by mode 1 and used by
+      // k_seg_filter; only the plan is needed from here on.
+      if (threadIdx.x == 0) S.plan = a.rec[S.hq].plan;
+      for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
+      __syncthreads();
+    } else {
     BestX b;
     bx_init(b);
+    if (MODE == 1) {
+      // The tile runs' extremes from k_seg_ext.
+      const int tf = a.tfirst[S.hq], te = a.tfirst[S.hq + 1];
+      for (int t = tf + (int)threadIdx.x; t < te; t += BLOCK) bx_merge(b, a.text[t].k, a.text[t].i);
+    } else {
     if (threadIdx.x == 0) {
       S.bbox[0] = 0x7FFFFFFF; S.bbox[1] = (int)0x80000000; S.bbox[2] = 0x7FFFFFFF; S.bbox[3] = (int)0x80000000;
     }
@@ -403,6 +479,7 @@ k_batch(BatchArgs a) {
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) p[r] = q[r];
     }
+    }   // mode 0
     bx_warp(b);
     if (lane == 0)
       for (int q = 0; q < 4; ++q) { S.rk[wid][q] = b.k[q]; S.ri[wid][q] = b.i[q]; }
@@ -439,25 +516,7 @@ k_batch(BatchArgs a) {
       if (pl.bad) atomicOr(a.error, ERR_RANGE);
     }
     __syncthreads();
-    if (a.w16 != nullptr && !S.plan.bad) {
-      // Learned polygon: features of a sample of this instance, the MLP,
-      // the exact hull of the quadrilateral and the 8 chosen extremes.
-      const u32 smp = n < 4096u ? n : 4096u;
-      learned::block_features<BLOCK>(P, n, smp, S.feat, S.mlp.x, S.ext_xy, S.ext_idx);
-      learned::block_mlp(a.w16, S.mlp);
-      if (threadIdx.x == 0) {
-        int qx[4], qy[4], ox[kMaxCorners], oy[kMaxCorners];
-        const int nq = S.plan.ncorner < 4 ? S.plan.ncorner : 4;
-        for (int j = 0; j < nq; ++j) { qx[j] = S.corner_x[j]; qy[j] = S.corner_y[j]; }
-        const int k2 = learned::learned_polygon(S.mlp.z, S.ext_xy, qx, qy, nq, ox, oy);
-        if (k2 > 0) {
-          S.plan.ncorner = k2;
-          S.plan.learned = 1;
-          for (int j = 0; j < k2; ++j) { S.corner_x[j] = ox[j]; S.corner_y[j] = oy[j]; }
-        }
-      }
-      __syncthreads();
-    }
+    if (a.w16 != nullptr && !S.plan.bad && n >= BL_MIN_N) learned_step<BLOCK>(S, P, n, a.w16);
     if (threadIdx.x == 0) {
       IPlan& pl = S.plan;
       const int k = pl.ncorner;
@@ -470,8 +529,12 @@ k_batch(BatchArgs a) {
     }
     for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
     __syncthreads();
+    }   // modes 0, 1
     if (S.plan.bad) {
-      if (threadIdx.x == 0) a.hcount[inst] = 0;
+      if (threadIdx.x == 0) {
+        a.hcount[inst] = 0;
+        if (MODE == 1) a.rec[S.hq].plan = S.plan;
+      }
       __syncthreads();
       continue;
     }
@@ -489,6 +552,7 @@ k_batch(BatchArgs a) {
     // shift drops all of y's, else x's shifted up beside y's top bits.
     const bool wx_only = wshift >= ybits;
     const u32 wsx = wx_only ? wshift - ybits : ybits - wshift;
+    if (MODE != 2) {
     for (int q = threadIdx.x; q < 2 * BW_BINS; q += BLOCK) S.wkey[q] = 0ull;
     __syncthreads();
     {
@@ -558,6 +622,16 @@ k_batch(BatchArgs a) {
         __syncthreads();
       }
     }
+    if (MODE == 1) {
+      // The record k_seg_filter and mode 2 read: plan, edges, witness table.
+      SegRec& R = a.rec[S.hq];
+      if (threadIdx.x == 0) R.plan = S.plan;
+      for (int q = threadIdx.x; q < kMaxCorners; q += BLOCK) R.edge[q] = S.edge[q];
+      for (int q = threadIdx.x; q < 2 * BW_BINS; q += BLOCK) R.wtab[q] = S.wtab[q];
+      __syncthreads();
+      continue;
+    }
+    }   // modes 0, 1
 
     // ---- 2. witness test, filter polygon and compaction (+ digit
     // histograms).  Warp w takes the round's points [base + w WSPAN, base +
@@ -567,6 +641,40 @@ k_batch(BatchArgs a) {
     u32* bcnt = &S.hist[0][0];          // survivors per witness bin (zeroed with the histograms)
     u32* bcur = &S.hist[2][0];
     u32 run = 0;
+    if (MODE == 2) {
+      // The survivors k_seg_filter left at the start of every tile run
+      // (in input order within the run; runs in tile order), gathered in
+      // input order, counted per witness bin.  An instance has at most
+      // 129 tiles (batch_max_instance() points), fewer than BLOCK.
+      const int tf = a.tfirst[S.hq], nt = a.tfirst[S.hq + 1] - tf;
+      const u32 c = (int)threadIdx.x < nt ? a.tcnt[tf + threadIdx.x] : 0u;
+      u32 inc = c;
+      #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (lane == 31) S.red[wid] = inc;
+      __syncthreads();
+      u32 ex = inc - c, tot = 0;
+      for (int w = 0; w < W; ++w) { if (w < wid) ex += S.red[w]; tot += S.red[w]; }
+      if ((int)threadIdx.x < nt) S.chunk_cnt[threadIdx.x] = (int)ex;
+      __syncthreads();
+      for (int t = wid; t < nt; t += W) {
+        const u32 ct = a.tcnt[tf + t], dst = (u32)S.chunk_cnt[t];
+        const long long src = sl + (long long)t * SEG_TILE;
+        for (u32 q = lane; q < ct; q += 32) {
+          const u64 k = __ldcg(&a.kb[src + q]);
+          if (dst + q < n) {
+            a.ka[sl + dst + q] = k;
+            a.ia[sl + dst + q] = __ldcg(&a.ib[src + q]);
+          }
+          atomicAdd(&bcnt[(u32)(k >> wshift)], 1u);
+        }
+      }
+      run = tot < n ? tot : n;
+      __syncthreads();
+    } else {
     int2 cur[BT_FITEMS];
     #pragma unroll
     for (int r = 0; r < BT_FITEMS; ++r) {
@@ -637,6 +745,7 @@ k_batch(BatchArgs a) {
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
     }
+    }   // mode 0
     __syncthreads();
     const u32 s = run;
 
@@ -926,7 +1035,265 @@ __global__ void k_batch_copy(const u32* __restrict__ hcount, const long long* __
   }
 }
 
+// ---------------------------------------------------------------- segmented
+// The two streaming passes of the largest instances, flat over all their
+// tiles: block b takes the consecutive tiles [b T / G, (b + 1) T / G), split
+// into runs of one instance each, so every block streams an equal share of
+// the points whatever the instances' sizes.
+
+// The instance (position in `order`) of tile t: the last h with tfirst[h] <= t.
+__device__ __forceinline__ int seg_of_tile(const int* __restrict__ tfirst, int nh, int t) {
+  int lo = 0, hi = nh - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tfirst[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int SEG_BLOCK = 512;
+
+// Pass 1: the extremes of every tile run (step 1: as the whole-pipeline
+// kernel, with the skip box of the run's first round), written to the run's
+// first tile (the run's other tiles get none), and every BW_STRIDE-th point
+// of the instance copied to its sample.
+__global__ void __launch_bounds__(SEG_BLOCK)
+k_seg_ext(BatchArgs a, int ntiles) {
+  constexpr int W = SEG_BLOCK / 32;
+  constexpr u32 FCH = SEG_BLOCK * BT_FITEMS;
+  __shared__ int s_box[4];
+  __shared__ u64 s_rk[W][4];
+  __shared__ u32 s_ri[W][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t1 = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  int t = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+  while (t < t1) {
+    const int h = seg_of_tile(a.tfirst, a.nb, t);
+    const int tf = a.tfirst[h], te = min(t1, a.tfirst[h + 1]);
+    const int inst = a.order[h];
+    const long long off = a.offsets[inst];
+    const u32 n = (u32)(a.offsets[inst + 1] - off);
+    const int2* P = reinterpret_cast<const int2*>(a.xy) + off;
+    int2* smp = reinterpret_cast<int2*>(a.kb + a.slot0[inst]);
+    const u32 lo = (u32)(t - tf) * SEG_TILE;
+    const u32 hi = min(n, (u32)(te - tf) * SEG_TILE);
+    if (threadIdx.x == 0) {
+      s_box[0] = 0x7FFFFFFF; s_box[1] = (int)0x80000000; s_box[2] = 0x7FFFFFFF; s_box[3] = (int)0x80000000;
+    }
+    __syncthreads();
+    int2 p[BT_FITEMS];
+    {
+      int x0 = 0x7FFFFFFF, x1 = (int)0x80000000, y0 = 0x7FFFFFFF, y1 = (int)0x80000000;
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = lo + r * SEG_BLOCK + threadIdx.x;
+        p[r] = j < hi ? P[j] : make_int2(0, 0);
+        if (j < hi) {
+          x0 = min(x0, p[r].x); x1 = max(x1, p[r].x); y0 = min(y0, p[r].y); y1 = max(y1, p[r].y);
+        }
+      }
+      #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x0 = min(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o)); x1 = max(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o));
+        y0 = min(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o)); y1 = max(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o));
+      }
+      if (lane == 0 && x0 <= x1) {
+        atomicMin(&s_box[0], x0); atomicMax(&s_box[1], x1); atomicMin(&s_box[2], y0); atomicMax(&s_box[3], y1);
+      }
+    }
+    __syncthreads();
+    const int kx0 = s_box[0], kx1 = s_box[1], ky0 = s_box[2], ky1 = s_box[3];
+    BestX b;
+    bx_init(b);
+    for (u32 base = lo; base < hi; base += FCH) {
+      int2 q[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + FCH + r * SEG_BLOCK + threadIdx.x;
+        q[r] = j < hi ? P[j] : make_int2(0, 0);
+      }
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = base + r * SEG_BLOCK + threadIdx.x;
+        if (j < hi) {
+          if (!(p[r].x > kx0 && p[r].x < kx1 && p[r].y > ky0 && p[r].y < ky1)) bx_point(b, p[r].x, p[r].y, j);
+          if (j % BW_STRIDE == 0) smp[j / BW_STRIDE] = p[r];
+        }
+      }
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) p[r] = q[r];
+    }
+    bx_warp(b);
+    if (lane == 0)
+      for (int q = 0; q < 4; ++q) { s_rk[wid][q] = b.k[q]; s_ri[wid][q] = b.i[q]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bx_init(b);
+      for (int w = 0; w < W; ++w) bx_merge(b, s_rk[w], s_ri[w]);
+      for (int j = 0; j < 4; ++j) { a.text[t].k[j] = b.k[j]; a.text[t].i[j] = b.i[j]; }
+    }
+    for (int u = t + 1 + (int)threadIdx.x; u < te; u += SEG_BLOCK)
+      for (int j = 0; j < 4; ++j) { a.text[u].k[j] = ~0ull; a.text[u].i[j] = 0xFFFFFFFFu; }
+    __syncthreads();
+    t = te;
+  }
+}
+
+// Pass 2: the witness test of the point's bin and region, then the filter
+// polygon on the witness survivors (step 2 of the whole-pipeline kernel,
+// from the instance's record), compacted in input order to the start of
+// the run's range of the instance's second key / index buffers; the count
+// goes to the run's first tile (0 for its other tiles).
+__global__ void __launch_bounds__(SEG_BLOCK)
+k_seg_filter(BatchArgs a, int ntiles) {
+  constexpr int W = SEG_BLOCK / 32;
+  constexpr u32 FCH = SEG_BLOCK * BT_FITEMS;
+  constexpr u32 WSPAN = 32u * BT_FITEMS;
+  __shared__ IPlan s_plan;
+  __shared__ int4 s_edge[kMaxCorners];
+  __shared__ int2 s_wtab[2 * BW_BINS];
+  __shared__ u32 s_red[2 * (W + 1)];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 lt_mask = (1u << lane) - 1u;
+  const int t1 = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  int t = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
+  while (t < t1) {
+    const int h = seg_of_tile(a.tfirst, a.nb, t);
+    const int tf = a.tfirst[h], te = min(t1, a.tfirst[h + 1]);
+    const int inst = a.order[h];
+    const long long off = a.offsets[inst];
+    const u32 n = (u32)(a.offsets[inst + 1] - off);
+    const long long sl = a.slot0[inst];
+    const int2* P = reinterpret_cast<const int2*>(a.xy) + off;
+    const SegRec& R = a.rec[h];
+    if (threadIdx.x == 0) s_plan = R.plan;
+    for (int q = threadIdx.x; q < kMaxCorners; q += SEG_BLOCK) s_edge[q] = R.edge[q];
+    for (int q = threadIdx.x; q < 2 * BW_BINS; q += SEG_BLOCK) s_wtab[q] = R.wtab[q];
+    __syncthreads();
+    const u32 lo = (u32)(t - tf) * SEG_TILE;
+    const u32 hi = min(n, (u32)(te - tf) * SEG_TILE);
+    u32 run = 0;
+    if (!s_plan.bad) {
+      const int bxp = s_plan.ext_x[1], byp = s_plan.ext_y[1];
+      const int d0x = s_plan.ext_x[0] - bxp, d0y = s_plan.ext_y[0] - byp;
+      const int x0 = s_plan.x0, y0 = s_plan.y0, ncorner = s_plan.ncorner;
+      const u32 ybits = s_plan.ybits, kbits = s_plan.kbits;
+      const u32 wshift = kbits > (u32)BW_BITS ? kbits - (u32)BW_BITS : 0u;
+      const bool wx_only = wshift >= ybits;
+      const u32 wsx = wx_only ? wshift - ybits : ybits - wshift;
+      int2 cur[BT_FITEMS];
+      #pragma unroll
+      for (int r = 0; r < BT_FITEMS; ++r) {
+        const u32 j = lo + wid * WSPAN + r * 32 + lane;
+        cur[r] = j < hi ? P[j] : make_int2(0, 0);
+      }
+      u32 parity = 0;
+      for (u32 base = lo; base < hi; base += FCH, parity ^= 1u) {
+        const u32 j0 = base + wid * WSPAN + lane;
+        u32 kmask = 0;
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r) {
+          if (j0 + r * 32 < hi) {
+            const int dx = cur[r].x - bxp, dy = cur[r].y - byp;
+            const long long c = cross2(d0x, d0y, dx, dy);
+            const u32 xr = (u32)(cur[r].x - x0);
+            const u32 wb = wx_only ? xr >> wsx : (xr << wsx) | ((u32)(cur[r].y - y0) >> wshift);
+            const int2 w = s_wtab[2 * wb + (c < 0 ? 1u : 0u)];
+            const long long tt = cross2(w.x, w.y, dx, dy);
+            if (c == 0 || (c > 0 ? tt > 0 : tt < 0)) kmask |= 1u << r;
+          }
+        }
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r)
+          if (((kmask >> r) & 1u) && in_polygon(s_edge, ncorner, cur[r].x, cur[r].y)) kmask &= ~(1u << r);
+        u32 bal[BT_FITEMS], wc = 0;
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r) {
+          bal[r] = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
+          wc += __popc(bal[r]);
+        }
+        u32* red = s_red + parity * (W + 1);
+        if (lane == 0) red[wid] = wc;
+        int2 nxt[BT_FITEMS];
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r) {
+          const u32 j = j0 + FCH + r * 32;
+          nxt[r] = j < hi ? P[j] : make_int2(0, 0);
+        }
+        __syncthreads();
+        if (wid == 0) {
+          const u32 v = lane < W ? red[lane] : 0u;
+          u32 inc = v;
+          #pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const u32 tt = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += tt;
+          }
+          if (lane < W) red[lane] = inc - v;
+          if (lane == W - 1) red[W] = inc;
+        }
+        __syncthreads();
+        u32 pos = run + red[wid];
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r) {
+          if ((kmask >> r) & 1u) {
+            const u32 q = pos + __popc(bal[r] & lt_mask);
+            if (lo + q < n) {
+              a.kb[sl + lo + q] = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
+              a.ib[sl + lo + q] = j0 + r * 32;
+            }
+          }
+          pos += __popc(bal[r]);
+        }
+        run += red[W];
+        #pragma unroll
+        for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
+      }
+    }
+    if (threadIdx.x == 0) a.tcnt[t] = run;
+    for (int u = t + 1 + (int)threadIdx.x; u < te; u += SEG_BLOCK) a.tcnt[u] = 0;
+    __syncthreads();
+    t = te;
+  }
+}
+
+BatchArgs batch_args(const BatchLaunch& L) {
+  BatchArgs a;
+  a.xy = L.xy; a.offsets = L.offsets; a.order = L.order; a.nb = L.nb; a.queue = L.queue;
+  a.slot0 = L.slot0; a.ka = L.ka; a.kb = L.kb; a.ia = L.ia; a.ib = L.ib;
+  a.lxy = L.lxy; a.lidx = L.lidx; a.uxy = L.uxy; a.uidx = L.uidx;
+  a.out_tmp = L.out_tmp; a.hcount = L.hcount; a.error = L.error;
+  a.w16 = reinterpret_cast<const __half*>(L.w16);
+  a.mode = L.mode; a.tfirst = L.tfirst;
+  a.text = reinterpret_cast<SegTileExt*>(L.text);
+  a.tcnt = L.tcnt;
+  a.rec = reinterpret_cast<SegRec*>(L.rec);
+  return a;
+}
+
 }  // namespace
+
+int seg_tile() { return (int)SEG_TILE; }
+size_t seg_rec_bytes() { return sizeof(SegRec); }
+size_t seg_text_bytes() { return sizeof(SegTileExt); }
+
+cudaError_t seg_configure(int* occ_ext, int* occ_filter) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_ext, k_seg_ext, SEG_BLOCK, 0);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_filter, k_seg_filter, SEG_BLOCK, 0);
+}
+
+cudaError_t launch_seg_ext(const BatchLaunch& L, int ntiles, int grid, cudaStream_t st) {
+  if (L.nb <= 0 || ntiles <= 0) return cudaSuccess;
+  k_seg_ext<<<grid < ntiles ? grid : ntiles, SEG_BLOCK, 0, st>>>(batch_args(L), ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_filter(const BatchLaunch& L, int ntiles, int grid, cudaStream_t st) {
+  if (L.nb <= 0 || ntiles <= 0) return cudaSuccess;
+  k_seg_filter<<<grid < ntiles ? grid : ntiles, SEG_BLOCK, 0, st>>>(batch_args(L), ntiles);
+  return cudaGetLastError();
+}
 
 int batch_pad() { return 2 * Smem<512>::CHUNK + 16; }
 int batch_max_instance() { return BT_MAX_CHUNKS * Smem<256>::CHUNK - 8; }
@@ -936,27 +1303,32 @@ size_t batch_smem(int block) {
 }
 
 cudaError_t batch_configure(int* occ256, int* occ512) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem<256>));
+  const void* k256[3] = {(const void*)k_batch<256, 0>, (const void*)k_batch<256, 1>, (const void*)k_batch<256, 2>};
+  const void* k512[3] = {(const void*)k_batch<512, 0>, (const void*)k_batch<512, 1>, (const void*)k_batch<512, 2>};
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+    e = cudaFuncSetAttribute(k256[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k512[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<512>));
+  }
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(Smem<512>));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ256, k_batch<256, 0>, 256, sizeof(Smem<256>));
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ256, k_batch<256>, 256, sizeof(Smem<256>));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ512, k_batch<512>, 512, sizeof(Smem<512>));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ512, k_batch<512, 0>, 512, sizeof(Smem<512>));
 }
 
 cudaError_t launch_batch(int block, int grid, const BatchLaunch& L, cudaStream_t st) {
-  BatchArgs a;
-  a.xy = L.xy; a.offsets = L.offsets; a.order = L.order; a.nb = L.nb; a.queue = L.queue;
-  a.slot0 = L.slot0; a.ka = L.ka; a.kb = L.kb; a.ia = L.ia; a.ib = L.ib;
-  a.lxy = L.lxy; a.lidx = L.lidx; a.uxy = L.uxy; a.uidx = L.uidx;
-  a.out_tmp = L.out_tmp; a.hcount = L.hcount; a.error = L.error;
-  a.w16 = reinterpret_cast<const __half*>(L.w16);
+  const BatchArgs a = batch_args(L);
   if (L.nb <= 0) return cudaSuccess;
-  if (block == 512) k_batch<512><<<grid, 512, sizeof(Smem<512>), st>>>(a);
-  else k_batch<256><<<grid, 256, sizeof(Smem<256>), st>>>(a);
+  if (block == 512) {
+    if (L.mode == 1) k_batch<512, 1><<<grid, 512, sizeof(Smem<512>), st>>>(a);
+    else if (L.mode == 2) k_batch<512, 2><<<grid, 512, sizeof(Smem<512>), st>>>(a);
+    else k_batch<512, 0><<<grid, 512, sizeof(Smem<512>), st>>>(a);
+  } else {
+    if (L.mode == 1) k_batch<256, 1><<<grid, 256, sizeof(Smem<256>), st>>>(a);
+    else if (L.mode == 2) k_batch<256, 2><<<grid, 256, sizeof(Smem<256>), st>>>(a);
+    else k_batch<256, 0><<<grid, 256, sizeof(Smem<256>), st>>>(a);
+  }
   return cudaGetLastError();
 }
 

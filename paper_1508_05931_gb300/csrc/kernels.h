@@ -149,9 +149,26 @@ struct BatchLaunch {
   u32* hcount;
   u32* error;
   const void* w16;   // learned proposal weights, or null
+  // The segmented path of the largest instances (mode 0: the whole
+  // pipeline per block).  k_seg_ext streams all their tiles first; mode 1
+  // reduces every instance's tile extremes into its plan, filter polygon
+  // and witness table (rec); k_seg_filter streams the tiles again with
+  // the witness test and the polygon; mode 2 gathers every instance's
+  // survivors and runs the sort, the second round and the chains.
+  int mode;
+  const int* tfirst;  // [nb + 1]: first tile of every instance of `order`
+  void* text;         // per-tile extremes
+  u32* tcnt;          // per-tile survivor counts
+  void* rec;          // per-instance plan, polygon edges and witness table
 };
 
 int batch_pad();
+int seg_tile();             // points per tile of the segmented path
+size_t seg_rec_bytes();     // bytes of one instance's record
+size_t seg_text_bytes();    // bytes of one tile's extremes
+cudaError_t seg_configure(int* occ_ext, int* occ_filter);
+cudaError_t launch_seg_ext(const BatchLaunch& L, int ntiles, int grid, cudaStream_t st);
+cudaError_t launch_seg_filter(const BatchLaunch& L, int ntiles, int grid, cudaStream_t st);
 int batch_max_instance();
 size_t batch_smem(int block);
 cudaError_t batch_configure(int* occ256, int* occ512);
@@ -167,8 +184,9 @@ cudaError_t launch_infer(const float* feat, const void* w16, const int* ext_xy, 
 // The pipeline's proposal: the gate on a strided sample (the quadrilateral
 // kept when it already discards nearly all of it), else features, inference
 // and the learned polygon, in one launch.
+// raw_count: the single-read front's survivor count (device), or null.
 cudaError_t launch_propose(const int* xy, u32 n, const void* w16, float* feat, int* ext, int* ext_xy, Plan* plan,
-                           cudaStream_t st);
+                           const u32* raw_count, cudaStream_t st);
 cudaError_t launch_labels(const int* xy, u32 n, const int* quad, int nq, const int* ext_xy,
                           unsigned long long* counts, int grid, cudaStream_t st);
 cudaError_t launch_to_half(const float* w, void* w16, int count, cudaStream_t st);

@@ -126,12 +126,15 @@ def test_batch_autotune(hull_lib, tmp_path):
 
 def test_batch_learned_exact_and_discards_more(hull_lib):
     """The learned polygon inside the batched kernel: exact hulls, and it
-    never discards less than the quadrilateral."""
+    never discards less than the quadrilateral.  The three 300,000-point
+    instances are above the size from which the batched kernel runs the
+    proposal; the smaller ones take the quadrilateral."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from oracle import mlp as OM
     from paper_1508_05931_gb300 import learned as L
     parts = [L.instance(k % 3, 20000 + 997 * k, 300 + k) for k in range(24)] + mixed_parts(5)
+    parts += [L.instance(k, 300_000, 400 + k) for k in range(3)]
     with hull_lib.Context(0, proposal=1) as c:
         c.mlp_set_params(OM.init_params(11))
         check(parts, *run_batch(c, parts))
@@ -184,6 +187,76 @@ def test_batch_sort_paths_both_block_sizes(hull_lib, tmp_path, monkeypatch, bloc
     parts = sort_path_parts()
     with hull_lib.Context(0, autotune=True) as c:        # writes the cache for this device
         run_batch(c, parts)
-    cache.write_text(re.sub(r'(batched_(?:small|large)": )\d+', r"\g<1>%d" % block, cache.read_text()))
+    cache.write_text(re.sub(r'(batched_(?:small|large|seg_block)": )\d+', r"\g<1>%d" % block, cache.read_text()))
     with hull_lib.Context(0, autotune=True) as c:        # both buckets at the forced block size
+        check(parts, *run_batch(c, parts))
+
+
+def seg_parts(seed):
+    """Instances of the segmented path (65,536 points or more at the default
+    boundary): whole and ragged 16,384-point tiles, every family, degenerate
+    sets, one with more survivors than the shared-memory sort holds, and a
+    few small instances so that every size bucket runs in the same call."""
+    parts = []
+    sizes = [65536, 65537, 81919, 98304, 131071, 250001]
+    for k, n in enumerate(sizes):
+        fam = k % 4
+        if fam == 0:
+            parts.append(W.uniform_square(n, 1 << 29, seed + k))
+        elif fam == 1:
+            parts.append(W.uniform_disk(n, 2.0 ** 29, seed + k))
+        elif fam == 2:
+            parts.append(W.gaussian(n, 2.0 ** 26, seed + k))
+        else:
+            parts.append(W.near_circle(n, 2.0 ** 22, seed + k))
+    parts.append(np.array([[-5, 9]] * 70000, np.int32))                  # all identical
+    t = np.arange(-40000, 40000)
+    parts.append(np.stack([t, -2 * t], axis=1).astype(np.int32))         # collinear
+    parts.append(W.filled_grid(300, 300, -150, -150))                    # 4 corners
+    parts.append(W.near_circle(150000, 2.0 ** 20, seed + 50))            # many survivors
+    parts += [W.uniform_disk(5, 100, seed + 60), W.uniform_square(20000, 1 << 20, seed + 61)]
+    return parts
+
+
+def test_segmented_path(ctx):
+    parts = seg_parts(31)
+    check(parts, *run_batch(ctx, parts))
+
+
+def test_segmented_largest_instance(ctx, hull_lib):
+    """An instance of the largest size the batched call accepts (129 tiles),
+    beside a small one."""
+    n = int(hull_lib.hull_batched_max_instance())
+    parts = [W.uniform_disk(n, 2.0 ** 29, 71), W.uniform_square(3000, 1000, 72)]
+    check(parts, *run_batch(ctx, parts))
+
+
+def test_segmented_range_error(ctx, hull_lib):
+    """A point out of range inside a segmented instance fails the call with
+    HULL_ERANGE; the next call on the context is exact."""
+    bad = W.uniform_square(70000, 1 << 20, 81).copy()
+    bad[40000] = [(1 << 29) + 1, 0]
+    with pytest.raises(hull_lib.HullError) as e:
+        run_batch(ctx, [W.uniform_square(100, 10, 1), bad])
+    assert e.value.code == hull_lib.HULL_ERANGE
+    parts = seg_parts(83)
+    check(parts, *run_batch(ctx, parts))
+
+
+@pytest.mark.parametrize("seg_min", [32768, 131072, 524288])
+def test_segmented_boundary_choices(hull_lib, tmp_path, monkeypatch, seg_min):
+    """Every boundary the autotuner may choose, forced through its cache:
+    the same instances move between the segmented and the one-block paths
+    (at 32,768 an all-vertex instance of 40,001 points takes the segmented
+    path and the radix sort after the gather)."""
+    import re
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("GBHULL_AUTOTUNE_CACHE", str(cache))
+    parts = seg_parts(91) + mixed_parts(92) + [W.parabola_lattice(20000)]
+    with hull_lib.Context(0, autotune=True) as c:        # writes the cache for this device
+        run_batch(c, parts)
+    txt = cache.read_text()
+    assert "batched_seg_min" in txt and "batched_seg_block" in txt
+    cache.write_text(re.sub(r'(batched_seg_min": )\d+', r"\g<1>%d" % seg_min, txt))
+    with hull_lib.Context(0, autotune=True) as c:
         check(parts, *run_batch(c, parts))
