@@ -221,6 +221,7 @@ struct Smem {
   int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
   int4 edge[kMaxCorners];            // the filter polygon's edges (in_polygon)
   u32 nbig;                          // witness bins above BT_BIGBIN survivors
+  u32 ngrp;                          // groups of bins sorted one at a time (more than SCAP survivors)
   int bbox[4];                       // the skip box of step 1
   unsigned short big[BW_BINS];
   int chunk_cnt[BT_MAX_CHUNKS];      // chain length of every chunk
@@ -663,13 +664,26 @@ k_batch(BatchArgs a) {
       for (int t = wid; t < nt; t += W) {
         const u32 ct = a.tcnt[tf + t], dst = (u32)S.chunk_cnt[t];
         const long long src = sl + (long long)t * SEG_TILE;
-        for (u32 q = lane; q < ct; q += 32) {
-          const u64 k = __ldcg(&a.kb[src + q]);
-          if (dst + q < n) {
-            a.ka[sl + dst + q] = k;
-            a.ia[sl + dst + q] = __ldcg(&a.ib[src + q]);
+        for (u32 q0 = lane; q0 < ct; q0 += 128) {   // four loads in flight per lane
+          u64 k[4];
+          u32 v[4];
+          #pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const u32 q = q0 + 32 * r;
+            k[r] = q < ct ? __ldcg(&a.kb[src + q]) : 0ull;
+            v[r] = q < ct ? __ldcg(&a.ib[src + q]) : 0u;
           }
-          atomicAdd(&bcnt[(u32)(k >> wshift)], 1u);
+          #pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const u32 q = q0 + 32 * r;
+            if (q < ct) {
+              if (dst + q < n) {
+                a.ka[sl + dst + q] = k[r];
+                a.ia[sl + dst + q] = v[r];
+              }
+              atomicAdd(&bcnt[(u32)(k[r] >> wshift)], 1u);
+            }
+          }
         }
       }
       run = tot < n ? tot : n;
@@ -753,12 +767,14 @@ k_batch(BatchArgs a) {
     // the keys in input order.  Up to SCAP survivors: moved into shared
     // memory by witness bin (the key's top bits, so the bins are in key
     // order), then every bin sorted in place (a warp per bin, the whole block
-    // for bins above BT_BIGBIN).  More: a stable LSD radix sort through the
-    // scratch region (digit histograms first).
+    // for bins above BT_BIGBIN).  More, with no bin above SCAP: moved into
+    // bin order in the scratch region, then groups of consecutive bins of at
+    // most SCAP survivors each sorted the same way through shared memory.
+    // Otherwise (thousands of equal keys): a stable LSD radix sort through
+    // the scratch region (digit histograms first).
     const u64* rs_k;
     const u32* rs_i;
-    if (s <= (u32)Smem<BLOCK>::SCAP) {
-      {
+    {
         constexpr int PER = BW_BINS / BLOCK > 0 ? BW_BINS / BLOCK : 1;
         u32 v[PER], tot = 0;
         #pragma unroll
@@ -784,8 +800,24 @@ k_batch(BatchArgs a) {
           if (b < BW_BINS) bcur[b] = ex;
           ex += v[q];
         }
+        if (threadIdx.x == 0) S.ngrp = 0;
         __syncthreads();
+    }
+    if (s > (u32)Smem<BLOCK>::SCAP && threadIdx.x == 0) {
+      // Groups of consecutive bins, greedily up to SCAP survivors each
+      // (their first bins in S.big); none when a bin alone exceeds SCAP.
+      u32 ng = 0, acc = 0;
+      bool ok = true;
+      for (u32 b = 0; b < (u32)BW_BINS && ok; ++b) {
+        const u32 c = bcnt[b];
+        ok = c <= (u32)Smem<BLOCK>::SCAP;
+        if (ng == 0 || acc + c > (u32)Smem<BLOCK>::SCAP) { S.big[ng++] = (unsigned short)b; acc = 0; }
+        acc += c;
       }
+      S.ngrp = ok ? ng : 0u;
+    }
+    __syncthreads();
+    if (s <= (u32)Smem<BLOCK>::SCAP) {
       for (u32 i = threadIdx.x; i < s; i += BLOCK) {
         const u64 k = __ldcg(&a.ka[sl + i]);
         const u32 q = atomicAdd(&bcur[(u32)(k >> wshift)], 1u);
@@ -811,6 +843,56 @@ k_batch(BatchArgs a) {
       }
       rs_k = S.bk;
       rs_i = S.bi;
+    } else if (S.ngrp > 0) {
+      for (u32 i0 = threadIdx.x; i0 < s; i0 += 4 * BLOCK) {   // four loads in flight per thread
+        u64 k[4];
+        u32 v[4];
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const u32 i = i0 + r * BLOCK;
+          k[r] = i < s ? __ldcg(&a.ka[sl + i]) : 0ull;
+          v[r] = i < s ? __ldcg(&a.ia[sl + i]) : 0u;
+        }
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (i0 + r * BLOCK < s) {
+            const u32 q = atomicAdd(&bcur[(u32)(k[r] >> wshift)], 1u);   // bcur[b]: the bin's end after
+            a.kb[sl + q] = k[r];
+            a.ib[sl + q] = v[r];
+          }
+        }
+      }
+      __syncthreads();
+      const u32 ng = S.ngrp;
+      for (u32 g = 0; g < ng; ++g) {
+        const u32 g0 = S.big[g], g1 = g + 1 < ng ? (u32)S.big[g + 1] : (u32)BW_BINS;
+        const u32 p0 = bcur[g0] - bcnt[g0], p1 = bcur[g1 - 1];
+        for (u32 i = threadIdx.x; i < p1 - p0; i += BLOCK) {
+          S.bk[i] = __ldcg(&a.kb[sl + p0 + i]);
+          S.bi[i] = __ldcg(&a.ib[sl + p0 + i]);
+        }
+        __syncthreads();
+        for (u32 b = g0 + wid; b < g1; b += W) {
+          const u32 c = bcnt[b], b0 = bcur[b] - c - p0;
+          if (c <= 1u) continue;
+          if (c <= 32u) warp_sort32(S.bk + b0, S.bi + b0, c, lane);
+          else if (c <= BT_BIGBIN) bitonic_pairs(S.bk + b0, S.bi + b0, c, (u32)lane, 32u, [] { __syncwarp(); });
+        }
+        __syncthreads();
+        for (u32 b = g0; b < g1; ++b) {
+          const u32 c = bcnt[b];
+          if (c > BT_BIGBIN)
+            bitonic_pairs(S.bk + (bcur[b] - c - p0), S.bi + (bcur[b] - c - p0), c, threadIdx.x, (u32)BLOCK,
+                          [] { __syncthreads(); });
+        }
+        for (u32 i = threadIdx.x; i < p1 - p0; i += BLOCK) {
+          a.kb[sl + p0 + i] = S.bk[i];
+          a.ib[sl + p0 + i] = S.bi[i];
+        }
+        __syncthreads();
+      }
+      rs_k = a.kb + sl;
+      rs_i = a.ib + sl;
     } else {
     for (int q = threadIdx.x; q < kMaxPasses * kRadix; q += BLOCK) (&S.hist[0][0])[q] = 0u;
     __syncthreads();

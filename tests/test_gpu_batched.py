@@ -167,14 +167,19 @@ def test_full_size_batch_sampled(hull_lib, tmp_path, monkeypatch):
 
 def sort_path_parts():
     """Instances for every branch of the batched sort: survivors above both
-    block sizes' shared-memory capacities (the radix fallback), between them,
-    a witness bin above the per-warp limit (3,000 copies of the leftmost
+    block sizes' shared-memory capacities in bins that fit (the sort by
+    groups of bins), a bin above both capacities (16,000 copies of the
+    leftmost point: the radix fallback), survivors between the capacities, a
+    witness bin above the per-warp limit (3,000 copies of the leftmost
     point), and mid-sized bins (near-circle sets)."""
     rng = np.random.default_rng(41)
     crowd = np.concatenate([np.tile(np.array([[-1000, 0]], np.int32), (3000, 1)),
                             rng.integers(-500, 501, size=(2000, 2)).astype(np.int32)])
     crowd = crowd[rng.permutation(len(crowd))]
-    return [W.parabola_lattice(20000), W.parabola_lattice(5000), crowd,
+    big = np.concatenate([np.tile(np.array([[-100000, 7]], np.int32), (16000, 1)),
+                          W.near_circle(4000, 2.0 ** 16, 46)])
+    big = big[rng.permutation(len(big))]
+    return [W.parabola_lattice(20000), W.parabola_lattice(5000), crowd, big,
             W.near_circle(30000, 2.0 ** 20, 43), W.near_circle(9000, 2.0 ** 16, 44),
             W.uniform_disk(200000, 2.0 ** 28, 45)]
 
