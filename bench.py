@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed hull per input set, for a profiler to capture; prints no JSON")
+    ap.add_argument("--profile-batched", type=int, default=0, metavar="SEG_MIN",
+                    help="two untimed batched calls on a 600-instance batch (sizes log-uniform in "
+                         "[1e3, 1e6], 4e7 points at most, seed 11) with the segmented path from SEG_MIN "
+                         "points, for a profiler to capture; prints no JSON")
     return ap.parse_args()
 
 
@@ -306,6 +310,7 @@ SAMPLE_STRIDE = 32
 # The last field names the units a committed DRAM traffic record scales by:
 # the points a launch reads, or the pairs it moves.
 STAGE_KERNELS = {
+    "polygon": ("k0_poly", lambda n, s, r: 0.0, "points"),
     "extremes": ("k1_extremes", lambda n, s, r: 8.0 * n + 8.0 * n / SAMPLE_STRIDE, "points"),
     "witness": ("k_witness", lambda n, s, r: 8.0 * n / SAMPLE_STRIDE, "points"),
     "filter": ("k2_fused", lambda n, s, r: 8.0 * n + 12.0 * s, "points"),
@@ -316,17 +321,19 @@ STAGE_KERNELS = {
     "final": ("k5_final", lambda n, s, r: 12.0 * r, "pairs"),
 }
 # The single-read front (inputs of 65,536 points or more, aligned, no
-# statistics): the sample polygon (every 1024th point read) and the extremes
-# pass that filters with it form the "extremes" stage (8 B per point read,
-# the every-32nd witness sample and the q raw survivors, 12 B each, written);
-# the fused filter then reads those q raw survivors and writes the s pairs.
+# statistics): the "polygon" stage is the sample polygon (every 1024th point
+# read, 8 B each); the "extremes" stage is the extremes pass that filters
+# with it (8 B per point read, the every-32nd witness sample, 8 B each, and
+# the q raw survivors, 12 B each, written); the fused filter then reads
+# those q raw survivors and writes the s pairs.  On the two-read front the
+# polygon stage is empty.
 POLY_STRIDE = 1024
 SINGLE_STAGE_KERNELS = dict(STAGE_KERNELS)
-SINGLE_STAGE_KERNELS["extremes"] = ("k1_poly (+ k0_poly)",
-                                    lambda n, s, r, q: 8.0 * n + 8.0 * n / POLY_STRIDE + 8.0 * n / SAMPLE_STRIDE
-                                    + 12.0 * q, "points")
+SINGLE_STAGE_KERNELS["polygon"] = ("k0_poly", lambda n, s, r, q: 8.0 * n / POLY_STRIDE, "points")
+SINGLE_STAGE_KERNELS["extremes"] = ("k1_poly", lambda n, s, r, q: 8.0 * n + 8.0 * n / SAMPLE_STRIDE + 12.0 * q,
+                                    "points")
 SINGLE_STAGE_KERNELS["filter"] = ("k2_fused", lambda n, s, r, q: 12.0 * q + 12.0 * s, "raw")
-DOMINANT_CANDIDATES = ("extremes", "witness", "filter", "scatter", "split", "sort")
+DOMINANT_CANDIDATES = ("polygon", "extremes", "witness", "filter", "scatter", "split", "sort")
 
 
 def roofline_of(prof, hbm, peak_src):
@@ -346,7 +353,7 @@ def roofline_of(prof, hbm, peak_src):
     kernels = {}
     for name, (kern, nbytes, unit) in table.items():
         ms = stage_ms.get(name, 0.0)
-        b = nbytes(n, s, r, q) if single and name in ("extremes", "filter") else nbytes(n, s, r)
+        b = nbytes(n, s, r, q) if single and name in ("polygon", "extremes", "filter") else nbytes(n, s, r)
         units = n if unit == "points" else (q if unit == "raw" else s)
         kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b, "units": units,
                          "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else None}
@@ -607,6 +614,16 @@ def main():
     from paper_1508_05931_gb300 import hull
 
     torch.cuda.set_device(local)
+    if args.profile_batched:
+        from paper_1508_05931_gb300 import workloads as W
+        pts, offs, _ = W.batch(b=600, seed=11, cap=4e7)
+        dp, do = torch.as_tensor(pts).cuda(), torch.as_tensor(offs).cuda()
+        bout = torch.empty(len(pts), dtype=torch.int32, device="cuda")
+        with hull.Context(local, batched_seg_min=args.profile_batched) as c:
+            for _ in range(2):
+                c.compute_batched(dp, do, out=bout)
+        torch.cuda.synchronize()
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -62,15 +62,20 @@ typedef struct {
   int proposal;       /* 0 = quadrilateral of the four extremes (the paper), 1 = learned */
   int collect_stats;  /* 1 = keep survivor counts of the last call for hull_last_stats */
   uint32_t spin_limit;/* iteration limit of every device wait; 0 = default (1 << 22) */
-  int autotune;       /* 1 = time the batched kernel's block sizes per size bucket on first
-                         use and cache the choice (file: $GBHULL_AUTOTUNE_CACHE, else
-                         ~/.cache/gbhull_autotune.json); 0 = built-in defaults */
+  int autotune;       /* 1 = time the batched kernels' block sizes per size bucket and the
+                         boundary of the segmented path on first use and cache the choice
+                         (file: $GBHULL_AUTOTUNE_CACHE, else ~/.cache/gbhull_autotune.json);
+                         0 = built-in defaults */
   int reverse_round;  /* 1 = after the second round (Section 2.2, Figure 2) run it mirrored
                          over each region's survivors -- walked from P_maxx back to P_minx
                          with P_minx as the anchor -- before the final chain (hull_compute,
                          hull_compute_multi, hull_compute_host*, hull_stage_regions; the
                          hull is the same, r_lower / r_upper count the points it keeps);
                          0 = the paper's single second round */
+  int batched_seg_min;/* hull_compute_batched: instances of at least this many points take
+                         the segmented path (streaming passes over all their tiles at once);
+                         0 = the autotuned boundary (autotune = 1) or 65,536; above
+                         hull_batched_max_instance(): no instance takes it */
 } hull_config;
 
 typedef struct {
@@ -221,14 +226,15 @@ typedef struct {
   int64_t survivors;             /* first-round survivors, summed (counted only by a context
                                     with collect_stats; 0 otherwise) */
   int64_t second_round;          /* second-round survivors, summed */
-  double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): extremes
-                                    (on the single-read front: the sample polygon and the
-                                    extremes pass that filters with it), witnesses (the
+  double ms[HULL_NUM_STAGES];    /* per stage; with the bucket sort (the default): polygon
+                                    (single-read front: the sample polygon; empty on the
+                                    two-read front), extremes (single-read front: the extremes
+                                    pass that filters with the polygon), witnesses (the
                                     sample's best witness per bin), filter (the
                                     fused filter: witness test, filter polygon, compaction, bin
                                     scan), scatter (survivors into coarse bins), split (coarse bins
                                     into bins, their aggregates, the groups' prefixes), sort (groups
-                                    sorted, second round), 4 empty slots, regions (compaction),
+                                    sorted, second round), 3 empty slots, regions (compaction),
                                     final; on the radix passes: extremes, filter, radix pass 0..7,
                                     regions, final */
   int64_t witness_survivors;     /* survivors of the fused filter (the bucket sort's input),

@@ -374,10 +374,12 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // every 32nd point out as the witness sample.
     e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
     if (e == cudaSuccess) e = launch_poly(d_xy, n, w.poly, c->num_sms, st);
+    mark(c, 1, st);
     if (e == cudaSuccess)
       e = launch_k1_poly(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, w.poly, &w.poly->raw_count, w.h_xy[0],
                          reinterpret_cast<u32*>(w.h_idx[0]), w.sample, c->num_sms, st);
   } else {
+    if (bucket) mark(c, 1, st);     // no sample polygon: an empty stage
     e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st,
                   bucket ? w.sample : nullptr);
   }
@@ -391,7 +393,7 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
                        st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  mark(c, 1, st);
+  mark(c, bucket ? 2 : 1, st);
   const size_t t2 = (n + k2_tile() - 1) / k2_tile();
   if (bucket) {
     // The fused front: witnesses from a sample, then one pass that filters,
@@ -401,13 +403,14 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // (with their direction aggregates), every bin's and group's prefix, and
     // one block per group of bins sorts it in shared memory and runs the
     // second round on it from its prefix.
-    // Profile slots: 1 witnesses, 2 filter (the fused filter and its bin
-    // scan), 3 scatter (coarse bins), 4 split (fine bins, their aggregates,
-    // group prefixes), 5 sort (+ second round), 6..9 empty, 10 compaction.
+    // Profile slots: 0 sample polygon, 1 extremes, 2 witnesses, 3 filter
+    // (the fused filter and its bin scan), 4 scatter (coarse bins), 5 split
+    // (fine bins, their aggregates, group prefixes), 6 sort (+ second
+    // round), 7..9 empty, 10 compaction.
     if (!single) e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
     if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 2, st);
+    mark(c, 3, st);
     if (single)   // the fused filter over the raw survivors, indices mapped back to the input's
       e = launch_k2_fused(reinterpret_cast<const int*>(w.h_xy[0]), n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1],
                           w.bcnt, w.bstart, w.groups, w.fcur, false, c->occ_kf * c->num_sms, st, &w.poly->raw_count,
@@ -416,20 +419,20 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
       e = launch_k2_fused(d_xy, n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1], w.bcnt, w.bstart, w.groups,
                           w.fcur, c->cfg.collect_stats != 0, c->occ_kf * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 3, st);
+    mark(c, 4, st);
     e = launch_place(w.keys[1], w.idx[1], n, c->plan, w.bstart, w.bcnt + kBins, w.keys[0], w.idx[0], c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 4, st);
+    mark(c, 5, st);
     e = launch_split(w.keys[0], w.idx[0], w.keys[1], w.idx[1], c->plan, w.bstart, w.fcur, w.tagg, w.ctiles,
                      c->occ_sp * c->num_sms, st);
     if (e == cudaSuccess) e = launch_bin_prefix(c->plan, w.groups, w.st_region, w.tagg, w.ctiles, w.bagg, w.bpre, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    mark(c, 5, st);
+    mark(c, 6, st);
     e = launch_bucket_decide(w.keys[1], w.idx[1], w.keys[0], w.idx[0], c->plan, w.groups, w.bscratch,
                              w.st_region, w.bpre, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy, w.lo_idx,
                              w.up_xy, w.up_idx, c->occ_kb * c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    for (int p = 6; p <= 2 + kMaxPasses; ++p) mark(c, p, st);
+    for (int p = 7; p <= 2 + kMaxPasses; ++p) mark(c, p, st);
     e = launch_group_compact(c->plan, w.st_region, w.h_xy[0], w.h_idx[0], w.h_xy[1], w.h_idx[1], w.lo_xy,
                              w.lo_idx, w.up_xy, w.up_idx, grid_for(c->occ_k4, c->num_sms, kBins), st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -544,12 +547,11 @@ void autotune_save(const hull_ctx* c) {
   FILE* f = std::fopen(path.c_str(), "w");
   if (!f) return;
   const std::string dk = device_key(c);
-  std::fprintf(f,
-               "{\"%s|batched_small\": %d, \"%s|batched_large\": %d, \"%s|batched_seg_block\": %d, "
-               "\"%s|batched_seg_min\": %lld}\n",
+  std::fprintf(f, "{\"%s|batched_small\": %d, \"%s|batched_large\": %d, \"%s|batched_seg_block\": %d",
                dk.c_str(), c->tuned_block[0] ? c->tuned_block[0] : 256, dk.c_str(),
-               c->tuned_block[1] ? c->tuned_block[1] : 256, dk.c_str(), c->tuned_block[2] ? c->tuned_block[2] : 256,
-               dk.c_str(), (long long)(c->tuned_seg ? c->tuned_seg : kSegDefault));
+               c->tuned_block[1] ? c->tuned_block[1] : 256, dk.c_str(), c->tuned_block[2] ? c->tuned_block[2] : 256);
+  if (c->tuned_seg) std::fprintf(f, ", \"%s|batched_seg_min\": %lld", dk.c_str(), (long long)c->tuned_seg);
+  std::fprintf(f, "}\n");
   std::fclose(f);
 }
 
@@ -1805,10 +1807,14 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
   // Autotuning on the first batch: the block size per bucket (each bucket
   // timed alone at the default boundary), then the segmented path's
   // boundary (the whole batch timed at each candidate).
+  // The boundary: the caller's (hull_config.batched_seg_min), else the
+  // tuned one, else the default.
+  const int64_t fixed_seg = c->cfg.batched_seg_min > 0 ? (int64_t)c->cfg.batched_seg_min : 0;
+  auto seg_boundary = [&]() { return fixed_seg ? fixed_seg : (c->tuned_seg ? c->tuned_seg : kSegDefault); };
   if (c->cfg.autotune && (c->tuned_block[0] == 0 || c->tuned_block[1] == 0 || c->tuned_block[2] == 0 ||
-                          c->tuned_seg == 0)) {
+                          (c->tuned_seg == 0 && !fixed_seg))) {
     autotune_load(c);
-    e = layout(c->tuned_seg ? c->tuned_seg : kSegDefault);
+    e = layout(seg_boundary());
     if (e != cudaSuccess) return cuda_fail(e);
     for (int bucket = 0; bucket < 3; ++bucket) {
       if (c->tuned_block[bucket] != 0) continue;
@@ -1824,7 +1830,7 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
       }
       c->tuned_block[bucket] = best_b;
     }
-    if (c->tuned_seg == 0) {
+    if (c->tuned_seg == 0 && !fixed_seg) {
       float best = 1e30f;
       int64_t best_t = kSegDefault;
       const int64_t cands[5] = {kSegDefault, kSegCandidates[0], kSegCandidates[1], kSegCandidates[2],
@@ -1841,7 +1847,7 @@ hull_status hull_compute_batched(hull_ctx* c, const int32_t* d_xy, const int64_t
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  e = layout(c->tuned_seg ? c->tuned_seg : kSegDefault);
+  e = layout(seg_boundary());
   if (e == cudaSuccess) e = run_all();
   if (e == cudaSuccess)
     e = launch_batch_output(w.hcount, w.slot0, w.out_tmp, B, reinterpret_cast<long long*>(d_out_offsets),

@@ -44,7 +44,7 @@ constexpr int BT_MAX_CHUNKS = 1024; // chain chunks per instance (bounds n_i)
 constexpr int BW_BITS = 9;          // witness bins per instance: the top BW_BITS of the key
 constexpr int BW_BINS = 1 << BW_BITS;
 constexpr u32 BW_STRIDE = 32;       // one sampled point in every BW_STRIDE
-constexpr u32 BT_BIGBIN = 1024;     // larger witness bins are sorted by the whole block
+constexpr u32 BT_RANKMAX = 64;      // witness bins up to this size are sorted by rank, larger ones by the block
 constexpr u32 BL_MIN_N = 262144;    // smallest instance the learned proposal runs on
 
 struct BestX {
@@ -147,24 +147,6 @@ __device__ __forceinline__ void bitonic_pairs(u64* K, u32* V, u32 m, u32 t0, u32
     }
   }
 }
-// At most 32 pairs by one warp in registers (shuffle bitonic network).
-__device__ __forceinline__ void warp_sort32(u64* K, u32* V, u32 c, int lane) {
-  u64 k = (u32)lane < c ? K[lane] : ~0ull;
-  u32 v = (u32)lane < c ? V[lane] : ~0u;
-  #pragma unroll
-  for (int kk = 2; kk <= 32; kk <<= 1) {
-    #pragma unroll
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      const u64 pk = __shfl_xor_sync(0xFFFFFFFFu, k, j);
-      const u32 pv = __shfl_xor_sync(0xFFFFFFFFu, v, j);
-      const bool up = (lane & kk) == 0, lower = (lane & j) == 0;
-      const bool psmall = pair_lt(pk, pv, k, v);
-      if ((lower == up) ? psmall : !psmall) { k = pk; v = pv; }
-    }
-  }
-  if ((u32)lane < c) { K[lane] = k; V[lane] = v; }
-}
-
 struct Dir2b {
   int lx, ly, ux, uy;
 };
@@ -220,7 +202,8 @@ struct Smem {
   int ccnt[BLOCK];                   // per-thread chain lengths inside a chunk
   int corner_x[kMaxCorners + 4], corner_y[kMaxCorners + 4];
   int4 edge[kMaxCorners];            // the filter polygon's edges (in_polygon)
-  u32 nbig;                          // witness bins above BT_BIGBIN survivors
+  u32 nbig;                          // witness bins above BT_RANKMAX survivors
+  unsigned short bigl[BW_BINS];      // those bins
   u32 ngrp;                          // groups of bins sorted one at a time (more than SCAP survivors)
   int bbox[4];                       // the skip box of step 1
   unsigned short big[BW_BINS];
@@ -265,6 +248,45 @@ __device__ __noinline__ void learned_step(Smem<BLOCK>& S, const int2* P, u32 n, 
       S.plan.ncorner = k2;
       S.plan.learned = 1;
       for (int j = 0; j < k2; ++j) { S.corner_x[j] = ox[j]; S.corner_y[j] = oy[j]; }
+    }
+  }
+  __syncthreads();
+}
+
+// Sorts the pairs of bins [g0, g1) staged in shared memory (S.bk / S.bi
+// [0, m): the bins in order, bin b at [bend[b] - bcnt[b] - p0, bend[b] -
+// p0), its pairs in any order) by (key, index) into dk / di [p0, p0 + m).
+// A pair of a bin of at most BT_RANKMAX pairs goes straight to its place:
+// its bin's start plus the number of the bin's pairs below it (pairs are
+// distinct: the indices are).  Larger bins are sorted in place by the whole
+// block's bitonic network, one at a time, and copied out.
+template <int BLOCK>
+__device__ void sort_bins_out(Smem<BLOCK>& S, const u32* bcnt, const u32* bend, u32 g0, u32 g1, u32 p0, u32 m,
+                              u32 wshift, u64* dk, u32* di) {
+  if (threadIdx.x == 0) S.nbig = 0;
+  __syncthreads();
+  for (u32 b = g0 + threadIdx.x; b < g1; b += BLOCK)
+    if (bcnt[b] > BT_RANKMAX) S.bigl[atomicAdd(&S.nbig, 1u)] = (unsigned short)b;
+  for (u32 i = threadIdx.x; i < m; i += BLOCK) {
+    const u64 k = S.bk[i];
+    const u32 v = S.bi[i];
+    const u32 b = (u32)(k >> wshift);
+    const u32 c = bcnt[b];
+    if (c > BT_RANKMAX) continue;
+    const u32 b0 = bend[b] - c - p0;
+    u32 r = 0;
+    for (u32 j = b0; j < b0 + c; ++j) r += pair_lt(S.bk[j], S.bi[j], k, v) ? 1u : 0u;
+    dk[p0 + b0 + r] = k;
+    di[p0 + b0 + r] = v;
+  }
+  __syncthreads();
+  const u32 nb = S.nbig;
+  for (u32 q = 0; q < nb; ++q) {
+    const u32 b = S.bigl[q], c = bcnt[b], b0 = bend[b] - c - p0;
+    bitonic_pairs(S.bk + b0, S.bi + b0, c, threadIdx.x, (u32)BLOCK, [] { __syncthreads(); });
+    for (u32 i = threadIdx.x; i < c; i += BLOCK) {
+      dk[p0 + b0 + i] = S.bk[b0 + i];
+      di[p0 + b0 + i] = S.bi[b0 + i];
     }
   }
   __syncthreads();
@@ -764,14 +786,15 @@ k_batch(BatchArgs a) {
     const u32 s = run;
 
     // ---- 3. sort (step 4) by (key, index), the order of a stable sort of
-    // the keys in input order.  Up to SCAP survivors: moved into shared
-    // memory by witness bin (the key's top bits, so the bins are in key
-    // order), then every bin sorted in place (a warp per bin, the whole block
-    // for bins above BT_BIGBIN).  More, with no bin above SCAP: moved into
-    // bin order in the scratch region, then groups of consecutive bins of at
-    // most SCAP survivors each sorted the same way through shared memory.
-    // Otherwise (thousands of equal keys): a stable LSD radix sort through
-    // the scratch region (digit histograms first).
+    // the keys in input order, into the second key / index buffers.  Up to
+    // SCAP survivors: moved into shared memory by witness bin (the key's top
+    // bits, so the bins are in key order), then every bin sorted
+    // (sort_bins_out: by rank, or by the block's bitonic network).  More,
+    // with no bin above SCAP: moved into bin order in the scratch region,
+    // then groups of consecutive bins of at most SCAP survivors each sorted
+    // the same way through shared memory.  Otherwise (thousands of equal
+    // keys): a stable LSD radix sort through the scratch region (digit
+    // histograms first).
     const u64* rs_k;
     const u32* rs_i;
     {
@@ -820,29 +843,14 @@ k_batch(BatchArgs a) {
     if (s <= (u32)Smem<BLOCK>::SCAP) {
       for (u32 i = threadIdx.x; i < s; i += BLOCK) {
         const u64 k = __ldcg(&a.ka[sl + i]);
-        const u32 q = atomicAdd(&bcur[(u32)(k >> wshift)], 1u);
+        const u32 q = atomicAdd(&bcur[(u32)(k >> wshift)], 1u);   // bcur[b]: the bin's end after
         S.bk[q] = k;
         S.bi[q] = __ldcg(&a.ia[sl + i]);
       }
       __syncthreads();
-      for (int b = wid; b < BW_BINS; b += W) {   // bcur[b]: the bin's end now
-        const u32 c = bcnt[b], b0 = bcur[b] - c;
-        if (c <= 1u) continue;
-        if (c <= 32u) {
-          warp_sort32(S.bk + b0, S.bi + b0, c, lane);
-        } else if (c <= BT_BIGBIN) {
-          bitonic_pairs(S.bk + b0, S.bi + b0, c, (u32)lane, 32u, [] { __syncwarp(); });
-        } else if (lane == 0) {
-          S.big[atomicAdd(&S.nbig, 1u)] = (unsigned short)b;
-        }
-      }
-      __syncthreads();
-      for (u32 q = 0; q < S.nbig; ++q) {
-        const u32 b = S.big[q], c = bcnt[b], b0 = bcur[b] - c;
-        bitonic_pairs(S.bk + b0, S.bi + b0, c, threadIdx.x, (u32)BLOCK, [] { __syncthreads(); });
-      }
-      rs_k = S.bk;
-      rs_i = S.bi;
+      sort_bins_out<BLOCK>(S, bcnt, bcur, 0u, (u32)BW_BINS, 0u, s, wshift, a.kb + sl, a.ib + sl);
+      rs_k = a.kb + sl;
+      rs_i = a.ib + sl;
     } else if (S.ngrp > 0) {
       for (u32 i0 = threadIdx.x; i0 < s; i0 += 4 * BLOCK) {   // four loads in flight per thread
         u64 k[4];
@@ -872,24 +880,7 @@ k_batch(BatchArgs a) {
           S.bi[i] = __ldcg(&a.ib[sl + p0 + i]);
         }
         __syncthreads();
-        for (u32 b = g0 + wid; b < g1; b += W) {
-          const u32 c = bcnt[b], b0 = bcur[b] - c - p0;
-          if (c <= 1u) continue;
-          if (c <= 32u) warp_sort32(S.bk + b0, S.bi + b0, c, lane);
-          else if (c <= BT_BIGBIN) bitonic_pairs(S.bk + b0, S.bi + b0, c, (u32)lane, 32u, [] { __syncwarp(); });
-        }
-        __syncthreads();
-        for (u32 b = g0; b < g1; ++b) {
-          const u32 c = bcnt[b];
-          if (c > BT_BIGBIN)
-            bitonic_pairs(S.bk + (bcur[b] - c - p0), S.bi + (bcur[b] - c - p0), c, threadIdx.x, (u32)BLOCK,
-                          [] { __syncthreads(); });
-        }
-        for (u32 i = threadIdx.x; i < p1 - p0; i += BLOCK) {
-          a.kb[sl + p0 + i] = S.bk[i];
-          a.ib[sl + p0 + i] = S.bi[i];
-        }
-        __syncthreads();
+        sort_bins_out<BLOCK>(S, bcnt, bcur, g0, g1, p0, p1 - p0, wshift, a.kb + sl, a.ib + sl);
       }
       rs_k = a.kb + sl;
       rs_i = a.ib + sl;

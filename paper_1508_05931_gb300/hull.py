@@ -30,7 +30,7 @@ MAX_POINTS = (1 << 30) - 1
 class hull_config(ctypes.Structure):
     _fields_ = [("proposal", ctypes.c_int), ("collect_stats", ctypes.c_int),
                 ("spin_limit", ctypes.c_uint32), ("autotune", ctypes.c_int),
-                ("reverse_round", ctypes.c_int)]
+                ("reverse_round", ctypes.c_int), ("batched_seg_min", ctypes.c_int)]
 
 
 class hull_stats(ctypes.Structure):
@@ -43,7 +43,7 @@ class hull_stats(ctypes.Structure):
 NUM_STAGES = 12
 # Stage slots of hull_profile.ms on the bucket-sort path (the default) and on
 # the radix-pass path (a call whose bins the bucket sort could not take).
-STAGE_NAMES = ["extremes", "witness", "filter", "scatter", "split", "sort"] + ["-%d" % i for i in range(6, 10)] + [
+STAGE_NAMES = ["polygon", "extremes", "witness", "filter", "scatter", "split", "sort"] + ["-%d" % i for i in range(7, 10)] + [
     "regions", "final"]
 RADIX_STAGE_NAMES = ["extremes", "filter"] + ["sort_pass%d" % i for i in range(8)] + ["regions", "final"]
 
@@ -150,10 +150,11 @@ class Context:
     """One hull_ctx: owns the device workspace for one GPU."""
 
     def __init__(self, device: int = 0, proposal: int = 0, collect_stats: bool = False,
-                 spin_limit: int = 0, autotune: bool = False, reverse_round: bool = False):
+                 spin_limit: int = 0, autotune: bool = False, reverse_round: bool = False,
+                 batched_seg_min: int = 0):
         self.device = int(device)
         cfg = hull_config(int(proposal), int(bool(collect_stats)), int(spin_limit), int(bool(autotune)),
-                          int(bool(reverse_round)))
+                          int(bool(reverse_round)), int(batched_seg_min))
         h = ctypes.c_void_p()
         _check(_lib.hull_create(ctypes.byref(h), self.device, ctypes.byref(cfg)), "hull_create")
         self._h = h

@@ -248,20 +248,33 @@ def test_segmented_range_error(ctx, hull_lib):
     check(parts, *run_batch(ctx, parts))
 
 
-@pytest.mark.parametrize("seg_min", [32768, 131072, 524288])
-def test_segmented_boundary_choices(hull_lib, tmp_path, monkeypatch, seg_min):
-    """Every boundary the autotuner may choose, forced through its cache:
-    the same instances move between the segmented and the one-block paths
-    (at 32,768 an all-vertex instance of 40,001 points takes the segmented
-    path and the radix sort after the gather)."""
+@pytest.mark.parametrize("seg_min", [1, 16385, 32768, 131072, 524288, 1 << 30])
+def test_segmented_boundary_choices(hull_lib, seg_min):
+    """Boundaries of the segmented path set by the caller
+    (hull_config.batched_seg_min): the same instances move between the
+    segmented and the one-block paths (from 1 every non-empty instance takes
+    it, the degenerate ones of one, two and three points included; from
+    16,385 every instance above the small bucket, and an all-vertex instance
+    of 40,001 points sorts by groups after the gather; from 2^30 none)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    parts = seg_parts(91) + mixed_parts(92) + [W.parabola_lattice(20000)]
+    with hull_lib.Context(0, batched_seg_min=seg_min) as c:
+        check(parts, *run_batch(c, parts))
+
+
+def test_segmented_boundary_from_autotune_cache(hull_lib, tmp_path, monkeypatch):
+    """The autotuner times the boundaries and caches its choice beside the
+    block sizes; a boundary written into the cache is used by the next
+    context."""
     import re
     cache = tmp_path / "tune.json"
     monkeypatch.setenv("GBHULL_AUTOTUNE_CACHE", str(cache))
-    parts = seg_parts(91) + mixed_parts(92) + [W.parabola_lattice(20000)]
+    parts = seg_parts(93) + mixed_parts(94)
     with hull_lib.Context(0, autotune=True) as c:        # writes the cache for this device
-        run_batch(c, parts)
+        check(parts, *run_batch(c, parts))
     txt = cache.read_text()
     assert "batched_seg_min" in txt and "batched_seg_block" in txt
-    cache.write_text(re.sub(r'(batched_seg_min": )\d+', r"\g<1>%d" % seg_min, txt))
+    cache.write_text(re.sub(r'(batched_seg_min": )\d+', r"\g<1>32768", txt))
     with hull_lib.Context(0, autotune=True) as c:
         check(parts, *run_batch(c, parts))
