@@ -164,11 +164,14 @@ __device__ __forceinline__ void merge_tree(int* sx, int* sy, int* si, int* cnt, 
       }
     }
     __syncthreads();
-    // Rounds of blockDim.x slots in increasing order: a destination never
-    // lies after its source, so a round writes nothing a later round reads.
+    // Rounds of blockDim.x slots in increasing order, as many as the leaves'
+    // slots need: a destination never lies after its source, so a round
+    // writes nothing a later round reads.
     const int span = 2 * step * LEAF;
+    const int rounds = (nleaf * LEAF + nthreads - 1) / nthreads;   // <= LEAF: nleaf <= nthreads
     #pragma unroll
     for (int r = 0; r < LEAF; ++r) {
+      if (r >= rounds) break;
       const int q = threadIdx.x + r * nthreads;
       int d = -1, vx = 0, vy = 0, vi = 0;
       if (q < nleaf * LEAF && (q % span) >= step * LEAF) {   // a slot of a right-hand chain

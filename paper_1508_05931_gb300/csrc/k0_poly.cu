@@ -9,9 +9,9 @@
 // polygon whose corners are input points).  The float projections only
 // choose the corners; the polygon and the table built from it are exact.
 //
-// The last block builds the polygon (Andrew's monotone chain over at most
-// kPolyDirs points, strict turns, counter-clockwise from the lexicographic
-// minimum) and, for K1, a table over its x range (xl, xr) cut into slabs of
+// The last block builds the polygon (the strict convex hull of at most
+// kPolyDirs points, counter-clockwise from the lexicographic minimum, one
+// lane per point) and, for K1, a table over its x range (xl, xr) cut into slabs of
 // 2^sh columns: for slab s an integer interval (ylo, yhi) with ylo at or
 // above the lower chain and yhi at or below the upper chain everywhere in
 // the slab.  The lower chain is convex and the upper chain concave, so over
@@ -81,24 +81,51 @@ __device__ void build_poly(PolyTab* T, const int2* __restrict__ P) {
     if (lane == 0) s_m = __popc(km);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int m = s_m;
-    const int* px = s_px;
-    const int* py = s_py;
-    int k = 0;
-    for (int i = 0; i < m; ++i) {          // lower chain
-      while (k >= 2 && orient(s_hx[k - 2], s_hy[k - 2], s_hx[k - 1], s_hy[k - 1], px[i], py[i]) <= 0) --k;
-      s_hx[k] = px[i]; s_hy[k] = py[i]; ++k;
+  if (threadIdx.x < 32) {
+    // The convex hull of the m <= 32 sorted distinct candidates, one lane
+    // per point.  With d_j = p_i - p_j (j < i) and e_k = p_k - p_i (k > i),
+    // all in the half-plane of angles (-90, 90] (sorted and distinct), p_i
+    // is a strict lower-hull vertex when the most counter-clockwise d_j is
+    // strictly clockwise of the most clockwise e_k (every left slope below
+    // every right slope), and a strict upper-hull vertex when the most
+    // clockwise d_j is strictly counter-clockwise of the most
+    // counter-clockwise e_k; p_0 and p_m-1 end both chains.  The hull,
+    // counter-clockwise from p_0: the lower vertices in increasing index,
+    // then the upper ones in decreasing index (what Andrew's chain with
+    // strict turns gives).
+    const int lane = threadIdx.x, m = s_m;
+    const int px = lane < m ? s_px[lane] : 0, py = lane < m ? s_py[lane] : 0;
+    int ljx = 0, ljy = 0, ujx = 0, ujy = 0, lkx = 0, lky = 0, ukx = 0, uky = 0;
+    bool hj = false, hk = false;
+    for (int q = 0; q < m; ++q) {
+      const int qx = __shfl_sync(0xFFFFFFFFu, px, q), qy = __shfl_sync(0xFFFFFFFFu, py, q);
+      if (q < lane) {
+        const int dx = px - qx, dy = py - qy;
+        if (!hj) { ljx = ujx = dx; ljy = ujy = dy; hj = true; }
+        if (cross2(ljx, ljy, dx, dy) > 0) { ljx = dx; ljy = dy; }
+        if (cross2(ujx, ujy, dx, dy) < 0) { ujx = dx; ujy = dy; }
+      } else if (q > lane) {
+        const int ex = qx - px, ey = qy - py;
+        if (!hk) { lkx = ukx = ex; lky = uky = ey; hk = true; }
+        if (cross2(lkx, lky, ex, ey) < 0) { lkx = ex; lky = ey; }
+        if (cross2(ukx, uky, ex, ey) > 0) { ukx = ex; uky = ey; }
+      }
     }
-    const int nlow = k;
-    for (int i = m - 2, t = k + 1; i >= 0; --i) {   // upper chain
-      while (k >= t && orient(s_hx[k - 2], s_hy[k - 2], s_hx[k - 1], s_hy[k - 1], px[i], py[i]) <= 0) --k;
-      s_hx[k] = px[i]; s_hy[k] = py[i]; ++k;
+    const bool endp = lane == 0 || lane == m - 1;
+    const bool lo = lane < m && (endp || cross2(ljx, ljy, lkx, lky) > 0);
+    const bool up = lane < m && !endp && cross2(ujx, ujy, ukx, uky) < 0;
+    const u32 L = __ballot_sync(0xFFFFFFFFu, lo), U = __ballot_sync(0xFFFFFFFFu, up);
+    const int nl = __popc(L);
+    const u32 lt = (1u << lane) - 1u, gt = lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1));
+    if (lo) { const int q = __popc(L & lt); s_hx[q] = px; s_hy[q] = py; }
+    if (up) { const int q = nl + __popc(U & gt); s_hx[q] = px; s_hy[q] = py; }
+    const int xfirst = __shfl_sync(0xFFFFFFFFu, px, 0), xlast = __shfl_sync(0xFFFFFFFFu, px, m > 0 ? m - 1 : 0);
+    if (lane == 0) {
+      const int k = nl + __popc(U);
+      s_k = k;
+      s_ir = nl - 1;                       // the rightmost corner ends the lower chain
+      s_ok = (k >= 3 && m >= 3 && xlast - xfirst >= 2) ? 1 : 0;
     }
-    if (m > 1) --k;                        // the last point repeats the first
-    s_k = k;
-    s_ir = nlow - 1;                       // the rightmost corner ends the lower chain
-    s_ok = (k >= 3 && m >= 3 && s_hx[nlow - 1] - s_hx[0] >= 2) ? 1 : 0;
   }
   __syncthreads();
   const int k = s_k, ir = s_ir;
@@ -203,17 +230,19 @@ k0_poly(const int2* __restrict__ P, u32 n, PolyTab* __restrict__ T) {
   }
   s_best[wid][lane] = bi == 0xFFFFFFFFu ? 0ull : (((u64)ord_f(bp) << 32) | (u64)(~bi));
   __syncthreads();
+  // The threads that update T->best order their updates before the block's
+  // arrival; those of the last block order the arrivals before their reads.
   if (threadIdx.x < kPolyDirs) {
     u64 v = 0;
     for (int w = 0; w < K0_WARPS; ++w) v = s_best[w][threadIdx.x] > v ? s_best[w][threadIdx.x] : v;
     if (v) atomicMax(reinterpret_cast<unsigned long long*>(&T->best[threadIdx.x]), (unsigned long long)v);
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&T->done, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
+  if (threadIdx.x < kPolyDirs) __threadfence();
   build_poly(T, P);
 }
 

@@ -102,11 +102,7 @@ k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey) {
       const long long e = (long long)ux * dx + (long long)uy * dy;
       const u64 key = ((u64)(u32)(p[q].x - x0) << ybits) | (u64)(u32)(p[q].y - y0);
       const u32 wb = (u32)(key >> wshift);
-      // The slot only grows: a candidate not above its current value is no
-      // new maximum, and most are not, so they skip the atomic.
-      u64* slot = &wkey[(c > 0 ? 0u : (u32)kWitnessBins) + wb];
-      const u64 v = ((u64)pseudo_angle(c, e) << 32) | (u64)(i + 1u);
-      if (v > ld_relaxed_u64(slot)) atomicMax(slot, v);
+      atomicMax(&wkey[(c > 0 ? 0u : (u32)kWitnessBins) + wb], ((u64)pseudo_angle(c, e) << 32) | (u64)(i + 1u));
     }
   }
 }
