@@ -895,12 +895,23 @@ k_batch(BatchArgs a) {
     __syncthreads();
     u64* src_k = a.ka + sl; u32* src_i = a.ia + sl;
     u64* dst_k = a.kb + sl; u32* dst_i = a.ib + sl;
-    for (u32 pass = 0; pass < npasses; ++pass) {
-      const u32 shift = pass * kRadixBits;
+    // Mode 2's survivors are in no particular order within a tile run:
+    // passes over the index digits come first, so that the stable passes
+    // over the key leave equal keys in index order.
+    const u32 ipasses = MODE == 2 ? (bitlen32(n - 1u) + kRadixBits - 1) / kRadixBits : 0u;
+    for (u32 pass = 0; pass < ipasses + npasses; ++pass) {
+      const bool by_idx = MODE == 2 && pass < ipasses;
+      const u32 shift = (by_idx ? pass : pass - ipasses) * kRadixBits;
+      if (by_idx) {   // the index digits' histogram, in the first warp slot of the tile counters
+        for (int q = threadIdx.x; q < kRadix; q += BLOCK) S.wpos[0][q] = 0u;
+        __syncthreads();
+        for (u32 i = threadIdx.x; i < s; i += BLOCK) atomicAdd(&S.wpos[0][(src_i[i] >> shift) & (kRadix - 1)], 1u);
+        __syncthreads();
+      }
       // Exclusive start of every digit inside the instance's range.
       u32 hv = 0, hinc = 0;
       if (threadIdx.x < kRadix) {
-        hv = S.hist[pass][threadIdx.x];
+        hv = by_idx ? S.wpos[0][threadIdx.x] : S.hist[pass - ipasses][threadIdx.x];
         hinc = hv;
         #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -927,7 +938,8 @@ k_batch(BatchArgs a) {
           const u32 p = wb + it * 32 + lane;
           key[it] = p < s ? src_k[p] : 0ull;
           idv[it] = p < s ? src_i[p] : 0u;
-          if (p < s) atomicAdd(&S.wpos[wid][(u32)(key[it] >> shift) & (kRadix - 1)], 1u);
+          const u32 dg = by_idx ? (idv[it] >> shift) & (kRadix - 1) : (u32)(key[it] >> shift) & (kRadix - 1);
+          if (p < s) atomicAdd(&S.wpos[wid][dg], 1u);
         }
         __syncthreads();
         if (threadIdx.x < kRadix) {
@@ -942,7 +954,7 @@ k_batch(BatchArgs a) {
         for (int it = 0; it < BT_ITEMS; ++it) {
           const u32 p = wb + it * 32 + lane;
           const bool valid = p < s;
-          const u32 dg = (u32)(key[it] >> shift) & (kRadix - 1);
+          const u32 dg = by_idx ? (idv[it] >> shift) & (kRadix - 1) : (u32)(key[it] >> shift) & (kRadix - 1);
           const u32 peers = warp_digit_peers(dg) & __ballot_sync(0xFFFFFFFFu, valid);
           const int leader = 31 - __clz(peers);
           u32 pos = 0;
@@ -1214,18 +1226,21 @@ k_seg_ext(BatchArgs a, int ntiles) {
 
 // Pass 2: the witness test of the point's bin and region, then the filter
 // polygon on the witness survivors (step 2 of the whole-pipeline kernel,
-// from the instance's record), compacted in input order to the start of
-// the run's range of the instance's second key / index buffers; the count
-// goes to the run's first tile (0 for its other tiles).
+// from the instance's record), compacted to the start of the run's range of
+// the instance's second key / index buffers: every warp reserves its
+// round's survivors with one shared-memory atomic, so no block barrier
+// stands in the stream and the survivors of a run are in no particular
+// order (the sort orders (key, index) pairs; its radix fallback sorts by
+// index first).  The count goes to the run's first tile (0 for its other
+// tiles).
 __global__ void __launch_bounds__(SEG_BLOCK)
 k_seg_filter(BatchArgs a, int ntiles) {
-  constexpr int W = SEG_BLOCK / 32;
   constexpr u32 FCH = SEG_BLOCK * BT_FITEMS;
   constexpr u32 WSPAN = 32u * BT_FITEMS;
   __shared__ IPlan s_plan;
   __shared__ int4 s_edge[kMaxCorners];
   __shared__ int2 s_wtab[2 * BW_BINS];
-  __shared__ u32 s_red[2 * (W + 1)];
+  __shared__ u32 s_cnt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
   const int t1 = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x);
@@ -1239,13 +1254,12 @@ k_seg_filter(BatchArgs a, int ntiles) {
     const long long sl = a.slot0[inst];
     const int2* P = reinterpret_cast<const int2*>(a.xy) + off;
     const SegRec& R = a.rec[h];
-    if (threadIdx.x == 0) s_plan = R.plan;
+    if (threadIdx.x == 0) { s_plan = R.plan; s_cnt = 0; }
     for (int q = threadIdx.x; q < kMaxCorners; q += SEG_BLOCK) s_edge[q] = R.edge[q];
     for (int q = threadIdx.x; q < 2 * BW_BINS; q += SEG_BLOCK) s_wtab[q] = R.wtab[q];
     __syncthreads();
     const u32 lo = (u32)(t - tf) * SEG_TILE;
     const u32 hi = min(n, (u32)(te - tf) * SEG_TILE);
-    u32 run = 0;
     if (!s_plan.bad) {
       const int bxp = s_plan.ext_x[1], byp = s_plan.ext_y[1];
       const int d0x = s_plan.ext_x[0] - bxp, d0y = s_plan.ext_y[0] - byp;
@@ -1260,8 +1274,7 @@ k_seg_filter(BatchArgs a, int ntiles) {
         const u32 j = lo + wid * WSPAN + r * 32 + lane;
         cur[r] = j < hi ? P[j] : make_int2(0, 0);
       }
-      u32 parity = 0;
-      for (u32 base = lo; base < hi; base += FCH, parity ^= 1u) {
+      for (u32 base = lo; base < hi; base += FCH) {
         const u32 j0 = base + wid * WSPAN + lane;
         u32 kmask = 0;
         #pragma unroll
@@ -1285,28 +1298,15 @@ k_seg_filter(BatchArgs a, int ntiles) {
           bal[r] = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
           wc += __popc(bal[r]);
         }
-        u32* red = s_red + parity * (W + 1);
-        if (lane == 0) red[wid] = wc;
         int2 nxt[BT_FITEMS];
         #pragma unroll
         for (int r = 0; r < BT_FITEMS; ++r) {
           const u32 j = j0 + FCH + r * 32;
           nxt[r] = j < hi ? P[j] : make_int2(0, 0);
         }
-        __syncthreads();
-        if (wid == 0) {
-          const u32 v = lane < W ? red[lane] : 0u;
-          u32 inc = v;
-          #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const u32 tt = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-            if (lane >= o) inc += tt;
-          }
-          if (lane < W) red[lane] = inc - v;
-          if (lane == W - 1) red[W] = inc;
-        }
-        __syncthreads();
-        u32 pos = run + red[wid];
+        u32 pos = 0;
+        if (lane == 0 && wc) pos = atomicAdd(&s_cnt, wc);
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
         #pragma unroll
         for (int r = 0; r < BT_FITEMS; ++r) {
           if ((kmask >> r) & 1u) {
@@ -1318,12 +1318,12 @@ k_seg_filter(BatchArgs a, int ntiles) {
           }
           pos += __popc(bal[r]);
         }
-        run += red[W];
         #pragma unroll
         for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
       }
     }
-    if (threadIdx.x == 0) a.tcnt[t] = run;
+    __syncthreads();
+    if (threadIdx.x == 0) a.tcnt[t] = s_cnt;
     for (int u = t + 1 + (int)threadIdx.x; u < te; u += SEG_BLOCK) a.tcnt[u] = 0;
     __syncthreads();
     t = te;

@@ -200,8 +200,9 @@ def test_batch_sort_paths_both_block_sizes(hull_lib, tmp_path, monkeypatch, bloc
 def seg_parts(seed):
     """Instances of the segmented path (65,536 points or more at the default
     boundary): whole and ragged 16,384-point tiles, every family, degenerate
-    sets, one with more survivors than the shared-memory sort holds, and a
-    few small instances so that every size bucket runs in the same call."""
+    sets, one with more survivors than the shared-memory sort holds, one
+    whose duplicated vertex needs the radix fallback, and a few small
+    instances so that every size bucket runs in the same call."""
     parts = []
     sizes = [65536, 65537, 81919, 98304, 131071, 250001]
     for k, n in enumerate(sizes):
@@ -219,6 +220,12 @@ def seg_parts(seed):
     parts.append(np.stack([t, -2 * t], axis=1).astype(np.int32))         # collinear
     parts.append(W.filled_grid(300, 300, -150, -150))                    # 4 corners
     parts.append(W.near_circle(150000, 2.0 ** 20, seed + 50))            # many survivors
+    # A hull vertex with 16,000 copies spread over every tile: one witness
+    # bin above both shared-memory capacities (the radix fallback), where
+    # the smallest of the copies' indices must come out.
+    top = np.concatenate([np.tile(np.array([[3, 1 << 20]], np.int32), (16000, 1)),
+                          W.uniform_disk(60000, 2.0 ** 19, seed + 70)])
+    parts.append(top[np.random.default_rng(seed + 71).permutation(len(top))])
     parts += [W.uniform_disk(5, 100, seed + 60), W.uniform_square(20000, 1 << 20, seed + 61)]
     return parts
 
