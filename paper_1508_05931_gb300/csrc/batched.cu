@@ -190,8 +190,14 @@ struct Smem {
       int ext_idx[learned::NB];
     };
     struct {                         // witnesses (steps 1b-2)
-      u64 wkey[2 * BW_BINS];         // the sample's best witness per (region, bin)
       int2 wtab[2 * BW_BINS];        // witness direction of (bin, region)
+      union {
+        u64 wkey[2 * BW_BINS];       // step 1b: the sample's best witness per (region, bin)
+        struct {                     // step 2: every warp's witness survivors of a round
+          int2 sxy[W][32 * BT_FITEMS];
+          u32 sidx[W][32 * BT_FITEMS];
+        } st;
+      };
     };
     struct {                         // sort by bins (steps 3-4)
       u64 bk[SCAP];
@@ -733,17 +739,36 @@ k_batch(BatchArgs a) {
           if (c == 0 || (c > 0 ? t > 0 : t < 0)) kmask |= 1u << r;
         }
       }
-      #pragma unroll
-      for (int r = 0; r < BT_FITEMS; ++r)          // the first round on the witness survivors
-        if (((kmask >> r) & 1u) && in_polygon(S.edge, ncorner, cur[r].x, cur[r].y)) kmask &= ~(1u << r);
-      u32 bal[BT_FITEMS], wc = 0;
+      // The witness survivors staged in the warp's slice, in input order
+      // (a few per round); the filter polygon on them, one per lane; the
+      // warps' kept counts scanned across the block; the kept ones written
+      // in input order.
+      u32 wc = 0;
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) {
-        bal[r] = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
-        wc += __popc(bal[r]);
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
+        if ((kmask >> r) & 1u) {
+          const u32 q = wc + __popc(bal & lt_mask);
+          S.st.sxy[wid][q] = cur[r];
+          S.st.sidx[wid][q] = j0 + r * 32;
+        }
+        wc += __popc(bal);
+      }
+      __syncwarp();
+      u32 kb[BT_FITEMS], kc = 0;
+      #pragma unroll
+      for (int c = 0; c < BT_FITEMS; ++c) {
+        const u32 q = c * 32 + lane;
+        bool keep = false;
+        if (q < wc) {
+          const int2 p = S.st.sxy[wid][q];
+          keep = !in_polygon(S.edge, ncorner, p.x, p.y);
+        }
+        kb[c] = (u32)c * 32 < wc ? __ballot_sync(0xFFFFFFFFu, keep) : 0u;
+        kc += __popc(kb[c]);
       }
       u32* red = S.red + parity * (W + 1);
-      if (lane == 0) red[wid] = wc;
+      if (lane == 0) red[wid] = kc;
       int2 nxt[BT_FITEMS];
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) {
@@ -765,18 +790,21 @@ k_batch(BatchArgs a) {
       __syncthreads();
       u32 pos = run + red[wid];
       #pragma unroll
-      for (int r = 0; r < BT_FITEMS; ++r) {
-        if ((kmask >> r) & 1u) {
-          const u32 q = pos + __popc(bal[r] & lt_mask);
-          const u64 key = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
-          if (q < n) {
-            a.ka[sl + q] = key;
-            a.ia[sl + q] = j0 + r * 32;
+      for (int c = 0; c < BT_FITEMS; ++c) {
+        if ((kb[c] >> lane) & 1u) {
+          const u32 q = c * 32 + lane;
+          const int2 p = S.st.sxy[wid][q];
+          const u32 o = pos + __popc(kb[c] & lt_mask);
+          const u64 key = ((u64)(u32)(p.x - x0) << ybits) | (u64)(u32)(p.y - y0);
+          if (o < n) {
+            a.ka[sl + o] = key;
+            a.ia[sl + o] = S.st.sidx[wid][q];
           }
           atomicAdd(&bcnt[(u32)(key >> wshift)], 1u);
         }
-        pos += __popc(bal[r]);
+        pos += __popc(kb[c]);
       }
+      __syncwarp();
       run += red[W];
       #pragma unroll
       for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
@@ -1237,9 +1265,12 @@ __global__ void __launch_bounds__(SEG_BLOCK)
 k_seg_filter(BatchArgs a, int ntiles) {
   constexpr u32 FCH = SEG_BLOCK * BT_FITEMS;
   constexpr u32 WSPAN = 32u * BT_FITEMS;
+  constexpr int W = SEG_BLOCK / 32;
   __shared__ IPlan s_plan;
   __shared__ int4 s_edge[kMaxCorners];
   __shared__ int2 s_wtab[2 * BW_BINS];
+  __shared__ int2 s_sxy[W][WSPAN];   // per warp: the round's witness survivors, staged
+  __shared__ u32 s_sidx[W][WSPAN];
   __shared__ u32 s_cnt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
@@ -1289,14 +1320,19 @@ k_seg_filter(BatchArgs a, int ntiles) {
             if (c == 0 || (c > 0 ? tt > 0 : tt < 0)) kmask |= 1u << r;
           }
         }
-        #pragma unroll
-        for (int r = 0; r < BT_FITEMS; ++r)
-          if (((kmask >> r) & 1u) && in_polygon(s_edge, ncorner, cur[r].x, cur[r].y)) kmask &= ~(1u << r);
-        u32 bal[BT_FITEMS], wc = 0;
+        // The witness survivors staged in the warp's slice (a few per
+        // round), then the filter polygon on them, one per lane, and the
+        // kept ones reserved with one shared-memory atomic per 32.
+        u32 wc = 0;
         #pragma unroll
         for (int r = 0; r < BT_FITEMS; ++r) {
-          bal[r] = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
-          wc += __popc(bal[r]);
+          const u32 bal = __ballot_sync(0xFFFFFFFFu, (kmask >> r) & 1u);
+          if ((kmask >> r) & 1u) {
+            const u32 q = wc + __popc(bal & lt_mask);
+            s_sxy[wid][q] = cur[r];
+            s_sidx[wid][q] = j0 + r * 32;
+          }
+          wc += __popc(bal);
         }
         int2 nxt[BT_FITEMS];
         #pragma unroll
@@ -1304,20 +1340,25 @@ k_seg_filter(BatchArgs a, int ntiles) {
           const u32 j = j0 + FCH + r * 32;
           nxt[r] = j < hi ? P[j] : make_int2(0, 0);
         }
-        u32 pos = 0;
-        if (lane == 0 && wc) pos = atomicAdd(&s_cnt, wc);
-        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
-        #pragma unroll
-        for (int r = 0; r < BT_FITEMS; ++r) {
-          if ((kmask >> r) & 1u) {
-            const u32 q = pos + __popc(bal[r] & lt_mask);
-            if (lo + q < n) {
-              a.kb[sl + lo + q] = ((u64)(u32)(cur[r].x - x0) << ybits) | (u64)(u32)(cur[r].y - y0);
-              a.ib[sl + lo + q] = j0 + r * 32;
-            }
+        __syncwarp();
+        for (u32 q0 = 0; q0 < wc; q0 += 32) {
+          const u32 q = q0 + lane;
+          int2 p = make_int2(0, 0);
+          bool keep = false;
+          if (q < wc) {
+            p = s_sxy[wid][q];
+            keep = !in_polygon(s_edge, ncorner, p.x, p.y);
           }
-          pos += __popc(bal[r]);
+          const u32 kb = __ballot_sync(0xFFFFFFFFu, keep);
+          u32 pos = 0;
+          if (lane == 0 && kb) pos = atomicAdd(&s_cnt, (u32)__popc(kb));
+          pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + __popc(kb & lt_mask);
+          if (keep && lo + pos < n) {
+            a.kb[sl + lo + pos] = ((u64)(u32)(p.x - x0) << ybits) | (u64)(u32)(p.y - y0);
+            a.ib[sl + lo + pos] = s_sidx[wid][q];
+          }
         }
+        __syncwarp();
         #pragma unroll
         for (int r = 0; r < BT_FITEMS; ++r) cur[r] = nxt[r];
       }
