@@ -371,11 +371,7 @@ def roofline_of(prof, hbm, peak_src):
             / (sum(stage_ms.values()) / 1e3) / 1e9 if sum(stage_ms.values()) > 0 else None}
 
 
-def _time_hulls(ctx, sctx, t, out, stream, torch, k):
-    """ms per hull of `ctx` (no statistics: the path a caller runs), whether
-    its learned polygon was used, and the first-round discard fraction of
-    its filter polygon from one call of `sctx` (same proposal, statistics
-    on: the two-read front, which counts the filter's survivors)."""
+def _ms_per_hull(ctx, t, out, stream, torch, k):
     for _ in range(2):
         ctx.compute_raw(t, out, stream)
     torch.cuda.synchronize()
@@ -385,10 +381,19 @@ def _time_hulls(ctx, sctx, t, out, stream, torch, k):
         ctx.compute_raw(t, out, stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def _time_hulls(ctx, sctx, t, out, stream, torch, k):
+    """ms per hull of `ctx` (no statistics: the path a caller runs), whether
+    its learned polygon was used, and the first-round discard fraction of
+    its filter polygon from one call of `sctx` (same proposal, statistics
+    on: the two-read front, which counts the filter's survivors)."""
+    ms = _ms_per_hull(ctx, t, out, stream, torch, k)
     used = ctx.last_stats()["learned_used"]
     sctx.compute_raw(t, out, stream)
     st = sctx.last_stats()
-    return e0.elapsed_time(e1) / k, 1.0 - st["s"] / st["n"], used
+    return ms, 1.0 - st["s"] / st["n"], used
 
 
 def bench_configs(hull, torch, stream, hbm, peak_src, k=20):
@@ -513,9 +518,11 @@ def bench_second_round_ablation(hull, torch, stream, dev_sets):
 
 def bench_learned(hull, torch, stream, args):
     """Learned filter proposal vs the plain quadrilateral on the anisotropic
-    families at 20M points (single hull) and as a 1,024-instance batch of the
-    same 20M points.  The network is trained first, on the GPU, by the
-    library's own kernels (fixed seeds)."""
+    families at 20M points (single hull: on the path a caller runs, the
+    single-read front, where the proposal does not run, and on the two-read
+    front, where it does) and as a 1,024-instance batch of the same 20M
+    points.  The network is trained first, on the GPU, by the library's own
+    kernels (fixed seeds)."""
     from paper_1508_05931_gb300 import learned as L
     dev = torch.cuda.current_device()
     res = {"families": {}}
@@ -538,10 +545,16 @@ def bench_learned(hull, torch, stream, args):
             pts = torch.as_tensor(L.instance(fam, 20_000_000, 5 + fam)).cuda()
             mp, dp_, _ = _time_hulls(pc, pcs, pts, out, stream, torch, k)
             ml, dl, used = _time_hulls(lc, lcs, pts, out, stream, torch, k)
+            # the two-read front (statistics on), where the proposal runs
+            mp2 = _ms_per_hull(pcs, pts, out, stream, torch, k)
+            ml2 = _ms_per_hull(lcs, pts, out, stream, torch, k)
+            used2 = lcs.last_stats()["learned_used"]
             tot_p += mp; tot_l += ml
             res["families"][names[fam]] = {"plain_ms": mp, "learned_ms": ml, "speedup": mp / ml,
                                            "plain_discard": dp_, "learned_discard": dl, "learned_used": used,
-                                           "plain_mpts": 20.0 / mp * 1e3, "learned_mpts": 20.0 / ml * 1e3}
+                                           "plain_mpts": 20.0 / mp * 1e3, "learned_mpts": 20.0 / ml * 1e3,
+                                           "two_read_front": {"plain_ms": mp2, "learned_ms": ml2,
+                                                              "speedup": mp2 / ml2, "learned_used": used2}}
             del pts
         res["single_hull"] = {"plain_mpts": 60.0 / tot_p * 1e3, "learned_mpts": 60.0 / tot_l * 1e3,
                               "speedup": tot_p / tot_l}

@@ -59,7 +59,9 @@ typedef enum {
 } hull_status;
 
 typedef struct {
-  int proposal;       /* 0 = quadrilateral of the four extremes (the paper), 1 = learned */
+  int proposal;       /* 0 = quadrilateral of the four extremes (the paper), 1 = learned
+                         (on the two-read front and in batched mode; the single-read
+                         front's sample polygon and witness test leave it nothing to gain) */
   int collect_stats;  /* 1 = keep survivor counts of the last call for hull_last_stats */
   uint32_t spin_limit;/* iteration limit of every device wait; 0 = default (1 << 22) */
   int autotune;       /* 1 = time the batched kernels' block sizes per size bucket and the
@@ -108,10 +110,15 @@ void hull_destroy(hull_ctx *ctx);
  * Section 2.1).  d_xy: device int32[n][2], read-only.  d_out: device
  * int32[cap] receiving the CCW vertex indices.  *h_count (host) receives the
  * hull size on HULL_OK and on HULL_ECAPACITY (then d_out is untouched).
- * Synchronises `stream` before returning.  n must be < 2^30.  The survivors
- * are sorted by the bucket sort (hull_stage_bucket_sort); an input it
- * cannot handle in shared memory is rerun on the radix passes
- * (hull_stats.sort_fallback), with the same result. */
+ * Synchronises `stream` before returning.  n must be < 2^30.  Inputs of
+ * 65,536 points or more, 16-byte aligned, in a context without
+ * collect_stats take the single-read front (one pass over the input after a
+ * sample polygon drops the points strictly inside a polygon spanned by
+ * sampled input points); the others the two-read front (the extremes pass,
+ * then the filter pass over the input).  The survivors are sorted by the
+ * bucket sort (hull_stage_bucket_sort); an input it cannot handle in shared
+ * memory is rerun on the radix passes (hull_stats.sort_fallback), with the
+ * same result. */
 hull_status hull_compute(hull_ctx *ctx, const int32_t *d_xy, int64_t n, int32_t *d_out,
                          int64_t cap, int64_t *h_count, void *stream);
 

@@ -384,13 +384,14 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
                   bucket ? w.sample : nullptr);
   }
   if (e != cudaSuccess) return cuda_fail(e);
-  if (c->cfg.proposal == 1 && c->have_weights) {
+  if (c->cfg.proposal == 1 && c->have_weights && !single) {
     // Learned filter polygon: sampled features, MLP, exact hull of the
     // chosen extremes and the quadrilateral's corners, unless the gate finds
-    // nearly all of the input discarded already (by the single-read front's
-    // sample polygon, else by the quadrilateral on a sample).
-    e = launch_propose(d_xy, n, c->W16, c->feat, c->ext, c->ext_xy, c->plan, single ? &w.poly->raw_count : nullptr,
-                       st);
+    // the quadrilateral already discarding nearly all of a sample.  Not on
+    // the single-read front: there the filter polygon only meets the raw
+    // survivors of the sample polygon (32 directions) after the witness
+    // test, and a larger polygon cannot pay for its features and inference.
+    e = launch_propose(d_xy, n, c->W16, c->feat, c->ext, c->ext_xy, c->plan, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   mark(c, bucket ? 2 : 1, st);

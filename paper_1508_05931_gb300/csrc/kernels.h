@@ -184,9 +184,8 @@ cudaError_t launch_infer(const float* feat, const void* w16, const int* ext_xy, 
 // The pipeline's proposal: the gate on a strided sample (the quadrilateral
 // kept when it already discards nearly all of it), else features, inference
 // and the learned polygon, in one launch.
-// raw_count: the single-read front's survivor count (device), or null.
 cudaError_t launch_propose(const int* xy, u32 n, const void* w16, float* feat, int* ext, int* ext_xy, Plan* plan,
-                           const u32* raw_count, cudaStream_t st);
+                           cudaStream_t st);
 cudaError_t launch_labels(const int* xy, u32 n, const int* quad, int nq, const int* ext_xy,
                           unsigned long long* counts, int grid, cudaStream_t st);
 cudaError_t launch_to_half(const float* w, void* w16, int count, cudaStream_t st);

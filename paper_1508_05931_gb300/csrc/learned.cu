@@ -66,26 +66,22 @@ k8_infer(const float* __restrict__ feat, const __half* __restrict__ w16, const i
   }
 }
 
-// K6 + K8 in one launch behind a gate (the pipeline's path).  With the
-// single-read front (`raw_count` set) the sample polygon has already
-// filtered the input: when its survivors are at most (1 - PG_DISCARD) n,
-// the polygon the proposal would build can only act on those few points,
-// and the call keeps the quadrilateral after this one short launch.
-// Otherwise the quadrilateral's discard on PG_SAMPLE strided points i_k =
-// floor(k n / G) is the gate: at PG_DISCARD of them or more there is too
-// little left for a larger polygon to discard.  Past the gate, the features,
-// the MLP and the polygon exactly as K6 and K8.
+// K6 + K8 in one launch behind a gate (the pipeline's path): the
+// quadrilateral's discard on PG_SAMPLE strided points i_k = floor(k n / G)
+// first; when it discards PG_DISCARD of them or more, there is too little
+// left for a larger polygon to discard and the quadrilateral stays (no
+// features, no inference: the call costs this one short launch).
+// Otherwise the features, the MLP and the polygon exactly as K6 and K8.
 constexpr int PG_SAMPLE = F_BLOCK;
 constexpr float PG_DISCARD = 0.95f;
 
 __global__ void __launch_bounds__(F_BLOCK)
 k6_propose(const int* __restrict__ xy, u32 n, const __half* __restrict__ w16, float* __restrict__ feat,
-           int* __restrict__ ext, int* __restrict__ ext_xy, Plan* plan, const u32* __restrict__ raw_count) {
+           int* __restrict__ ext, int* __restrict__ ext_xy, Plan* plan) {
   __shared__ FeatSmem sm;
   __shared__ MlpSmem msm;
   __shared__ u32 s_in;
   if (plan->error & ERR_RANGE) return;
-  if (raw_count != nullptr && (float)*raw_count <= (1.0f - PG_DISCARD) * (float)n) return;
   const int2* P = reinterpret_cast<const int2*>(xy);
   const int k = plan->ncorner < 4 ? plan->ncorner : 4;
   if (threadIdx.x == 0) s_in = 0;
@@ -253,9 +249,8 @@ cudaError_t launch_features(const int* xy, u32 n, float* feat, int* ext, int* ex
 }
 
 cudaError_t launch_propose(const int* xy, u32 n, const void* w16, float* feat, int* ext, int* ext_xy, Plan* plan,
-                           const u32* raw_count, cudaStream_t st) {
-  k6_propose<<<1, F_BLOCK, 0, st>>>(xy, n, reinterpret_cast<const __half*>(w16), feat, ext, ext_xy, plan,
-                                    raw_count);
+                           cudaStream_t st) {
+  k6_propose<<<1, F_BLOCK, 0, st>>>(xy, n, reinterpret_cast<const __half*>(w16), feat, ext, ext_xy, plan);
   return cudaGetLastError();
 }
 
