@@ -323,15 +323,15 @@ STAGE_KERNELS = {
 # The single-read front (inputs of 65,536 points or more, aligned, no
 # statistics): the "polygon" stage is the sample polygon (every 1024th point
 # read, 8 B each); the "extremes" stage is the extremes pass that filters
-# with it (8 B per point read, the every-32nd witness sample, 8 B each, and
-# the q raw survivors, 12 B each, written); the fused filter then reads
-# those q raw survivors and writes the s pairs.  On the two-read front the
-# polygon stage is empty.
+# with it (8 B per point read, the q raw survivors, 12 B each, written); the
+# witnesses come from the raw survivors' points (8 B each read); the fused
+# filter then reads those q raw survivors and writes the s pairs.  On the
+# two-read front the polygon stage is empty.
 POLY_STRIDE = 1024
 SINGLE_STAGE_KERNELS = dict(STAGE_KERNELS)
 SINGLE_STAGE_KERNELS["polygon"] = ("k0_poly", lambda n, s, r, q: 8.0 * n / POLY_STRIDE, "points")
-SINGLE_STAGE_KERNELS["extremes"] = ("k1_poly", lambda n, s, r, q: 8.0 * n + 8.0 * n / SAMPLE_STRIDE + 12.0 * q,
-                                    "points")
+SINGLE_STAGE_KERNELS["extremes"] = ("k1_poly", lambda n, s, r, q: 8.0 * n + 12.0 * q, "points")
+SINGLE_STAGE_KERNELS["witness"] = ("k_witness", lambda n, s, r, q: 8.0 * q, "raw")
 SINGLE_STAGE_KERNELS["filter"] = ("k2_fused", lambda n, s, r, q: 12.0 * q + 12.0 * s, "raw")
 DOMINANT_CANDIDATES = ("polygon", "extremes", "witness", "filter", "scatter", "split", "sort")
 
@@ -353,7 +353,7 @@ def roofline_of(prof, hbm, peak_src):
     kernels = {}
     for name, (kern, nbytes, unit) in table.items():
         ms = stage_ms.get(name, 0.0)
-        b = nbytes(n, s, r, q) if single and name in ("polygon", "extremes", "filter") else nbytes(n, s, r)
+        b = nbytes(n, s, r, q) if single and name in ("polygon", "extremes", "witness", "filter") else nbytes(n, s, r)
         units = n if unit == "points" else (q if unit == "raw" else s)
         kernels[name] = {"kernel": kern, "ms": ms, "algorithmic_bytes": b, "units": units,
                          "gbs": b / (ms / 1e3) / 1e9 if ms > 0 else None}

@@ -367,17 +367,17 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
   mark(c, 0, st);
   cudaError_t e = cudaSuccess;
   if (single) {
-    // The single-read front: the sample polygon (from every 256th point),
+    // The single-read front: the sample polygon (from every 1024th point),
     // then one pass for the extremes that drops the points strictly inside
-    // that polygon, writes the rest (raw survivors, ~0.1-1 % of a uniform
-    // input) to the chain buffers, free until the group sort, and copies
-    // every 32nd point out as the witness sample.
+    // that polygon and writes the rest (raw survivors, ~0.1-1 % of a uniform
+    // input) to the chain buffers, free until the group sort; the raw
+    // survivors are also the witnesses' candidates.
     e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
     if (e == cudaSuccess) e = launch_poly(d_xy, n, w.poly, c->num_sms, st);
     mark(c, 1, st);
     if (e == cudaSuccess)
       e = launch_k1_poly(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, w.poly, &w.poly->raw_count, w.h_xy[0],
-                         reinterpret_cast<u32*>(w.h_idx[0]), w.sample, c->num_sms, st);
+                         reinterpret_cast<u32*>(w.h_idx[0]), c->num_sms, st);
   } else {
     if (bucket) mark(c, 1, st);     // no sample polygon: an empty stage
     e = launch_k1(d_xy, n, c->cfg.spin_limit, c->plan, w.partials, k1_grid(n, c->num_sms), st,
@@ -409,11 +409,16 @@ hull_status run_front(hull_ctx* c, const int32_t* d_xy, u32 n, cudaStream_t st, 
     // (fine bins, their aggregates, group prefixes), 6 sort (+ second
     // round), 7..9 empty, 10 compaction.
     if (!single) e = cudaMemsetAsync(w.bcnt, 0, clear_bytes, st);
-    if (e == cudaSuccess) e = launch_witness(w.sample, n, c->plan, w.wkey, c->num_sms, st);
+    // Witnesses: on the single-read front from every raw survivor (the
+    // points nearest the hull, a small fraction of the input), else from
+    // the every-32nd-point sample.
+    const int2* wsrc = single ? reinterpret_cast<const int2*>(w.h_xy[0]) : w.sample;
+    if (e == cudaSuccess)
+      e = launch_witness(wsrc, n, c->plan, w.wkey, c->num_sms, st, single ? &w.poly->raw_count : nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(c, 3, st);
     if (single)   // the fused filter over the raw survivors, indices mapped back to the input's
-      e = launch_k2_fused(reinterpret_cast<const int*>(w.h_xy[0]), n, c->plan, w.wkey, w.sample, w.keys[1], w.idx[1],
+      e = launch_k2_fused(reinterpret_cast<const int*>(w.h_xy[0]), n, c->plan, w.wkey, wsrc, w.keys[1], w.idx[1],
                           w.bcnt, w.bstart, w.groups, w.fcur, false, c->occ_kf * c->num_sms, st, &w.poly->raw_count,
                           reinterpret_cast<const u32*>(w.h_idx[0]));
     else

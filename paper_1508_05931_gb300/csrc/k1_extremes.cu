@@ -320,9 +320,7 @@ struct K1PSmem {
 
 __global__ void __launch_bounds__(K1P_BLOCK, 2)
 k1_poly(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* __restrict__ partials,
-        const PolyTab* __restrict__ T, u32* raw_count, int2* __restrict__ rxy, u32* __restrict__ ridx,
-        int2* __restrict__ sample) {
-  constexpr u32 kPairStride = kSampleStride / 2;   // pair j holds sample point j / kPairStride
+        const PolyTab* __restrict__ T, u32* raw_count, int2* __restrict__ rxy, u32* __restrict__ ridx) {
   extern __shared__ __align__(16) unsigned char k1p_smem[];
   K1PSmem& S = *reinterpret_cast<K1PSmem*>(k1p_smem);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -394,9 +392,6 @@ k1_poly(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan, ExtPartia
     #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = p4[u0 + 32u * u];
     #pragma unroll
-    for (int u = 0; u < 8; ++u)          // the witness sample: every kSampleStride-th point
-      if ((u0 + 32u * u) % kPairStride == 0) sample[(u0 + 32u * u) / kPairStride] = make_int2(v[u].x, v[u].y);
-    #pragma unroll
     for (int h = 0; h < 2; ++h) {
       int px[8], py[8];
       u32 pi[8];
@@ -420,7 +415,6 @@ k1_poly(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan, ExtPartia
       const int4 w = p4[j];
       px[0] = w.x; py[0] = w.y; px[1] = w.z; py[1] = w.w;
       valid = 3u;
-      if (j % kPairStride == 0) sample[j / kPairStride] = make_int2(w.x, w.y);
     }
     take(px, py, pi, valid, 2);
   }
@@ -430,7 +424,6 @@ k1_poly(const int* __restrict__ xy, u32 n, u32 spin_limit, Plan* plan, ExtPartia
     u32 valid = 0;
     if (lane == 0) {
       px[0] = xy[2 * (n - 1)]; py[0] = xy[2 * (n - 1) + 1]; valid = 1u;
-      if ((n - 1) % kSampleStride == 0) sample[(n - 1) / kSampleStride] = make_int2(px[0], py[0]);
     }
     take(px, py, pi, valid, 1);
   }
@@ -475,9 +468,8 @@ cudaError_t k1_poly_configure() {
 }
 
 cudaError_t launch_k1_poly(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials, const PolyTab* T,
-                           u32* raw_count, int2* rxy, u32* ridx, int2* sample, int num_sms, cudaStream_t st) {
-  k1_poly<<<num_sms * 2, K1P_BLOCK, sizeof(K1PSmem), st>>>(xy, n, spin_limit, plan, partials, T, raw_count, rxy, ridx,
-                                                           sample);
+                           u32* raw_count, int2* rxy, u32* ridx, int num_sms, cudaStream_t st) {
+  k1_poly<<<num_sms * 2, K1P_BLOCK, sizeof(K1PSmem), st>>>(xy, n, spin_limit, plan, partials, T, raw_count, rxy, ridx);
   return cudaGetLastError();
 }
 

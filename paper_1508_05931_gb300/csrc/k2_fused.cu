@@ -16,9 +16,11 @@
 // both tests; the order of the two tests is free.
 //
 //   k_witness  reads the sample of every kSampleStride-th point (copied out
-//              by K1); a sampled point that survives the filter polygon and
-//              lies off the line P_0 P_l is a witness for every later
-//              witness bin (the top kWitnessBits of the key) of its region.
+//              by K1), or on the single-read front every raw survivor of
+//              the sample polygon (the points nearest the hull); a point
+//              that survives the filter polygon and lies off the line
+//              P_0 P_l is a witness for every later witness bin (the top
+//              kWitnessBits of the key) of its region.
 //              Per witness bin and region the sample's most advanced
 //              direction is kept by one 64-bit atomic maximum of (a monotone
 //              float pseudo-angle, sample index + 1).  The pseudo-angle only
@@ -76,10 +78,10 @@ constexpr int SW_BLOCK = 256;
 constexpr int SW_ITEMS = 4;                   // sampled points per thread and round, loaded together
 
 __global__ void __launch_bounds__(SW_BLOCK)
-k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey) {
+k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey, const u32* __restrict__ ncount) {
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
-  const u32 S = (n + kSampleStride - 1) / kSampleStride;
+  const u32 S = ncount ? *ncount : (n + kSampleStride - 1) / kSampleStride;
   const int K = plan->ncorner;
   Edges E;
   load_edges(plan, K, E);
@@ -566,12 +568,13 @@ cudaError_t fused_occupancy(int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k2_fused<true, false>, KF_BLOCK, KF_SMEM);
 }
 
-cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st) {
-  const u32 samples = (n + kSampleStride - 1) / kSampleStride;
+cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st,
+                           const u32* ncount) {
+  const u32 samples = ncount ? n : (n + kSampleStride - 1) / kSampleStride;   // a bound with ncount
   u32 grid = (samples + SW_BLOCK * SW_ITEMS - 1) / (SW_BLOCK * SW_ITEMS);   // one round per thread
   const u32 cap = (u32)num_sms * 4u;
   grid = grid < 1 ? 1 : (grid > cap ? cap : grid);
-  k_witness<<<grid, SW_BLOCK, 0, st>>>(sample, plan, wkey);
+  k_witness<<<grid, SW_BLOCK, 0, st>>>(sample, plan, wkey, ncount);
   return cudaGetLastError();
 }
 

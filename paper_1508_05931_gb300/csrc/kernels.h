@@ -49,7 +49,10 @@ cudaError_t launch_k2(const int* xy, Plan* plan, u64* keys_out, u32* idx_out, u6
 // writes the bin starts, the groups and the split's cursors (fcur).
 cudaError_t fused_configure();
 cudaError_t fused_occupancy(int* blocks);
-cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st);
+// ncount (device), when given: the candidates are sample[0, *ncount) (the
+// single-read front's raw survivors; n then bounds their number).
+cudaError_t launch_witness(const int2* sample, u32 n, Plan* plan, u64* wkey, int num_sms, cudaStream_t st,
+                           const u32* ncount = nullptr);
 // With ncount and imap the points are the single-read front's raw survivors:
 // *ncount of them at xy (n bounds the count), their input indices in imap.
 cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, const int2* sample, u64* okey,
@@ -62,7 +65,7 @@ cudaError_t launch_k2_fused(const int* xy, u32 n, Plan* plan, const u64* wkey, c
 cudaError_t launch_poly(const int* xy, u32 n, PolyTab* T, int num_sms, cudaStream_t st);
 cudaError_t k1_poly_configure();
 cudaError_t launch_k1_poly(const int* xy, u32 n, u32 spin_limit, Plan* plan, ExtPartial* partials, const PolyTab* T,
-                           u32* raw_count, int2* rxy, u32* ridx, int2* sample, int num_sms, cudaStream_t st);
+                           u32* raw_count, int2* rxy, u32* ridx, int num_sms, cudaStream_t st);
 cudaError_t launch_place(const u64* ak, const u32* ai, u32 n, Plan* plan, const u32* bstart, u32* ccur, u64* ok,
                          u32* oi, int num_sms, cudaStream_t st);
 size_t bucket_smem();

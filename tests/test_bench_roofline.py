@@ -68,10 +68,10 @@ def test_traffic_record_scaled_and_invalidated(tmp_path, monkeypatch):
 
 def test_single_read_front_stage_bytes():
     """Calls on the single-read front: the extremes stage reads every point
-    once and writes the witness sample and the raw survivors; the polygon
-    stage reads the sample polygon's 1/1024 sample; the fused filter reads
-    the raw survivors and writes the pairs, its units being the raw
-    survivors."""
+    once and writes the raw survivors; the polygon stage reads the sample
+    polygon's 1/1024 sample; the witnesses read the raw survivors' points;
+    the fused filter reads the raw survivors and writes the pairs, its
+    units being the raw survivors."""
     p = _prof()
     calls = p["calls"]
     p["raw_survivors"] = 200_000 * calls
@@ -82,8 +82,9 @@ def test_single_read_front_stage_bytes():
     n, q, s = 20_000_000, 200_000, 8_000_000
     assert r["front"] == "single-read" and r["raw_survivors_per_hull"] == pytest.approx(q)
     assert r["kernel"] == "k1_poly"
-    b = 8.0 * n + 8.0 * n / 32 + 12.0 * q
+    b = 8.0 * n + 12.0 * q
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(b)
+    assert r["stages"]["witness"]["algorithmic_bytes"] == pytest.approx(8.0 * q)
     assert r["stages"]["polygon"]["algorithmic_bytes"] == pytest.approx(8.0 * n / 1024)
     assert r["stages"]["polygon"]["gbs"] == pytest.approx(8.0 * n / 1024 / 0.01e-3 / 1e9)
     assert r["stages"]["filter"]["algorithmic_bytes"] == pytest.approx(12.0 * q + 12.0 * s)
