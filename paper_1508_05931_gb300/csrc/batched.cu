@@ -672,9 +672,11 @@ k_batch(BatchArgs a) {
     u32 run = 0;
     if (MODE == 2) {
       // The survivors k_seg_filter left at the start of every tile run
-      // (in input order within the run; runs in tile order), gathered in
-      // input order, counted per witness bin.  An instance has at most
-      // 129 tiles (batch_max_instance() points), fewer than BLOCK.
+      // (runs in tile order, each run's survivors in no particular order),
+      // gathered and counted per witness bin: the instance's survivor i (in
+      // run order) lies in the last tile whose run start is at most i.  An
+      // instance has at most 128 tiles (batch_max_instance() points), fewer
+      // than BLOCK.
       const int tf = a.tfirst[S.hq], nt = a.tfirst[S.hq + 1] - tf;
       const u32 c = (int)threadIdx.x < nt ? a.tcnt[tf + threadIdx.x] : 0u;
       u32 inc = c;
@@ -689,28 +691,34 @@ k_batch(BatchArgs a) {
       for (int w = 0; w < W; ++w) { if (w < wid) ex += S.red[w]; tot += S.red[w]; }
       if ((int)threadIdx.x < nt) S.chunk_cnt[threadIdx.x] = (int)ex;
       __syncthreads();
-      for (int t = wid; t < nt; t += W) {
-        const u32 ct = a.tcnt[tf + t], dst = (u32)S.chunk_cnt[t];
-        const long long src = sl + (long long)t * SEG_TILE;
-        for (u32 q0 = lane; q0 < ct; q0 += 128) {   // four loads in flight per lane
-          u64 k[4];
-          u32 v[4];
-          #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const u32 q = q0 + 32 * r;
-            k[r] = q < ct ? __ldcg(&a.kb[src + q]) : 0ull;
-            v[r] = q < ct ? __ldcg(&a.ib[src + q]) : 0u;
-          }
-          #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const u32 q = q0 + 32 * r;
-            if (q < ct) {
-              if (dst + q < n) {
-                a.ka[sl + dst + q] = k[r];
-                a.ia[sl + dst + q] = v[r];
-              }
-              atomicAdd(&bcnt[(u32)(k[r] >> wshift)], 1u);
+      for (u32 i0 = threadIdx.x; i0 < tot; i0 += 4 * BLOCK) {   // four loads in flight per thread
+        u64 k[4];
+        u32 v[4];
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const u32 i = i0 + r * BLOCK;
+          k[r] = 0ull;
+          v[r] = 0u;
+          if (i < tot) {
+            int lo = 0, hi = nt - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if ((u32)S.chunk_cnt[mid] <= i) lo = mid; else hi = mid - 1;
             }
+            const long long src = sl + (long long)lo * SEG_TILE + (i - (u32)S.chunk_cnt[lo]);
+            k[r] = __ldcg(&a.kb[src]);
+            v[r] = __ldcg(&a.ib[src]);
+          }
+        }
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const u32 i = i0 + r * BLOCK;
+          if (i < tot) {
+            if (i < n) {
+              a.ka[sl + i] = k[r];
+              a.ia[sl + i] = v[r];
+            }
+            atomicAdd(&bcnt[(u32)(k[r] >> wshift)], 1u);
           }
         }
       }
