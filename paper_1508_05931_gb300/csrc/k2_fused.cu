@@ -16,8 +16,9 @@
 // both tests; the order of the two tests is free.
 //
 //   k_witness  reads the sample of every kSampleStride-th point (copied out
-//              by K1), or on the single-read front every raw survivor of
-//              the sample polygon (the points nearest the hull); a point
+//              by K1), or on the single-read front the raw survivors of
+//              the sample polygon (the points nearest the hull; every st-th
+//              of them when they outnumber that sample); a point
 //              that survives the filter polygon and lies off the line
 //              P_0 P_l is a witness for every later witness bin (the top
 //              kWitnessBits of the key) of its region.
@@ -81,7 +82,14 @@ __global__ void __launch_bounds__(SW_BLOCK)
 k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey, const u32* __restrict__ ncount) {
   if (plan->error & ERR_RANGE) return;
   const u32 n = plan->n;
-  const u32 S = ncount ? *ncount : (n + kSampleStride - 1) / kSampleStride;
+  // The candidates: sample[0, S) with a stride; with ncount, at most as
+  // many as the every-32nd-point sample would hold (every st-th raw
+  // survivor when there are more: any subset of the first-round survivors
+  // gives valid witnesses).
+  const u32 cap = (n + kSampleStride - 1) / kSampleStride;
+  const u32 R = ncount ? *ncount : cap;
+  const u32 st = R > cap ? (R + cap - 1) / cap : 1u;
+  const u32 S = (R + st - 1) / st;
   const int K = plan->ncorner;
   Edges E;
   load_edges(plan, K, E);
@@ -93,11 +101,11 @@ k_witness(const int2* __restrict__ sample, Plan* plan, u64* __restrict__ wkey, c
   for (u32 i0 = blockIdx.x * SW_BLOCK + threadIdx.x; i0 < S; i0 += SW_ITEMS * T) {
     int2 p[SW_ITEMS];
     #pragma unroll
-    for (int q = 0; q < SW_ITEMS; ++q) p[q] = i0 + q * T < S ? sample[i0 + q * T] : make_int2(0, 0);
+    for (int q = 0; q < SW_ITEMS; ++q) p[q] = i0 + q * T < S ? sample[(i0 + q * T) * st] : make_int2(0, 0);
     #pragma unroll
     for (int q = 0; q < SW_ITEMS; ++q) {
-      const u32 i = i0 + q * T;
-      if (i >= S || strictly_inside_rt(E, K, p[q].x, p[q].y)) continue;   // not a first-round survivor
+      const u32 i = (i0 + q * T) * st;    // the candidate's position in sample[]
+      if (i0 + q * T >= S || strictly_inside_rt(E, K, p[q].x, p[q].y)) continue;   // not a first-round survivor
       const int dx = p[q].x - bx, dy = p[q].y - by;
       const long long c = cross2(ux, uy, dx, dy);
       if (c == 0) continue;                                             // on the line P_0 P_l: no region
