@@ -161,9 +161,15 @@ hull_status hull_compute_host_multi(hull_ctx *ctx, int32_t count, const int32_t 
                                     const int64_t *n, int32_t *const *h_out, const int64_t *cap,
                                     int64_t *h_count, void *stream);
 
-/* B independent hulls in one call (one persistent launch per size bucket:
- * each block runs the whole pipeline on one instance at a time, instances
- * taken largest first).  d_offsets: device int64[B+1], instance b is points
+/* B independent hulls in one call (Section 2.1's pipeline on every
+ * instance).  Instances of at least hull_config.batched_seg_min points (or
+ * the autotuned / default boundary) take the segmented path: two flat
+ * streaming passes over all their 16,384-point tiles at once (extremes;
+ * witness test and filter polygon), with one block per instance for its
+ * plan and, after the passes, for its sort, second round and chains.  The
+ * others go one block per instance through a persistent launch per size
+ * bucket (up to 16,384 points, more), instances taken largest first, on
+ * the context's second stream.  d_offsets: device int64[B+1], instance b is points
  * [d_offsets[b], d_offsets[b+1]) of d_xy (non-decreasing, d_offsets[0] = 0).
  * Vertex indices are relative to their instance and are written to d_out at
  * d_out_offsets[b] (device int64[B+1], written by the call;
