@@ -396,6 +396,31 @@ def _time_hulls(ctx, sctx, t, out, stream, torch, k):
     return ms, 1.0 - st["s"] / st["n"], used
 
 
+def bench_radix_fallback(hull, torch, stream, k=10):
+    """The cost of the radix-pass rerun: 4M points drawn from 40 distinct
+    points (coordinates in [-1000, 1000), seed 9), whose duplicates fill a
+    bin the bucket sort cannot split, so the call is rerun on the radix
+    passes; beside it a 4M uniform disk (seed 12) that the bucket sort takes
+    itself.  ms per hull (one call per step) and whether the rerun ran."""
+    from paper_1508_05931_gb300 import workloads as W
+    rng = np.random.default_rng(9)
+    few = rng.integers(-1000, 1000, size=(40, 2)).astype(np.int32)
+    cases = [("duplicates_4M", few[rng.integers(0, 40, size=4_000_000)]),
+             ("disk_4M", W.uniform_disk(4_000_000, 2.0 ** 29, 12))]
+    res = {}
+    for name, pts in cases:
+        t = torch.as_tensor(np.ascontiguousarray(pts)).cuda()
+        o = torch.empty(t.shape[0], dtype=torch.int32, device="cuda")
+        with hull.Context(torch.cuda.current_device()) as c:
+            ms = _ms_per_hull(c, t, o, stream, torch, k)
+        with hull.Context(torch.cuda.current_device(), collect_stats=True) as c:
+            c.compute_raw(t, o, stream)
+            fb = c.last_stats()["sort_fallback"]
+        res[name] = {"ms_per_hull": ms, "sort_fallback": int(fb), "n": int(len(pts))}
+    res["rerun_over_disk"] = res["duplicates_4M"]["ms_per_hull"] / res["disk_4M"]["ms_per_hull"]
+    return res
+
+
 def bench_configs(hull, torch, stream, hbm, peak_src, k=20):
     """The other two plain configurations, one hull per step: 100,000
     points uniform in [-2^20, 2^20)^2 (seed 0; its 800 KB stay in L2 between
@@ -768,6 +793,7 @@ def main():
         line["learned"] = bench_learned(hull, torch, stream, args)
     if world == 1:
         line["configs"] = bench_configs(hull, torch, stream, hbm, peak_src)
+        line["radix_fallback"] = bench_radix_fallback(hull, torch, stream)
     if world == 1 and not args.no_batched:
         line["reverse_round"] = bench_reverse_round(hull, torch, stream, dev_sets, dev_outs)
         line["second_round_ablation"] = bench_second_round_ablation(hull, torch, stream, dev_sets)
