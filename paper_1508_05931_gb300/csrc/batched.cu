@@ -1,28 +1,34 @@
-// Batched hulls: many independent point sets in one persistent launch.
+// Batched hulls: many independent point sets in one call.
 //
-// Every block takes instances from a queue ordered largest first (so the
-// longest jobs start early and the small ones fill the tail) and runs the
-// whole pipeline of Section 2.1 on one instance by itself, each step as a
-// block-level loop over chunks in order, so no block ever waits for another:
-//   1. extremes (step 1): block reduction;
-//   1b. witnesses: every 32nd point (copied out during step 1) that survives
-//      the filter polygon is a witness for every later witness bin of its
-//      region; the block keeps each bin's most advanced one and turns them
-//      into every bin's exclusive prefix (as the single-hull front does,
-//      k2_fused.cu: a point not strictly beyond a first-round survivor
-//      before it is one Figure 2 discards, so the second round's result is
-//      unchanged);
-//   2. quadrilateral filter and the witness test + compaction (steps 2-3)
-//      with a running offset, plus the digit histograms of the survivors'
-//      keys;
-//   3. stable LSD radix sort (step 4): per 8-bit digit, tiles in order,
-//      per-warp early counts give each warp's positions, the highest lane of
-//      each group of equal digits reserves positions with one shared atomic;
+// k_batch, mode 0: every block takes instances from a queue ordered largest
+// first (so the longest jobs start early and the small ones fill the tail)
+// and runs the whole pipeline of Section 2.1 on one instance by itself, each
+// step as a block-level loop over chunks in order, so no block ever waits
+// for another:
+//   1. extremes (step 1): block reduction, every 32nd point copied out;
+//   1b. witnesses: every sampled point that survives the filter polygon is
+//      a witness for every later witness bin of its region; the block keeps
+//      each bin's most advanced one and turns them into every bin's
+//      exclusive prefix (as the single-hull front does, k2_fused.cu: a point
+//      not strictly beyond a first-round survivor before it is one Figure 2
+//      discards, so the second round's result is unchanged);
+//   2. the witness test, then the filter polygon (steps 2-3) on the witness
+//      survivors staged per warp, compaction in input order, survivors
+//      counted per witness bin;
+//   3. the sort (step 4) by (key, index): survivors moved into shared
+//      memory by witness bin and every bin sorted there (by rank, or by the
+//      block's bitonic network), in groups of bins when they do not fit at
+//      once; a stable LSD radix sort through the scratch region when one
+//      bin alone does not fit;
 //   4. region split + second round (steps 5-7) as a running prefix
 //      max/min of directions seen from P_l (exactly Figure 2's survivors);
 //   5. lower and upper chains (step 8): chunks of the chain built in shared
 //      memory (per-thread stacks, warp bridge merges), then chunk chains
 //      merged level by level through global scratch.
+// The segmented path of the largest instances splits this: k_seg_ext
+// (step 1, flat over all their tiles), k_batch mode 1 (the plan and step
+// 1b per instance), k_seg_filter (step 2, flat over the tiles) and k_batch
+// mode 2 (the survivors gathered, then steps 3-5 per instance).
 // Each instance owns a scratch region of its size plus a fixed pad; its
 // hull (CCW indices relative to the instance) is staged there and a second
 // kernel compacts all hulls into the output with their offsets.
